@@ -1,0 +1,104 @@
+/*
+ * zkvc.h -- C ABI of a GB300 (sm_103a) prover for zkVC's CRPC matrix-multiplication
+ * circuit under Groth16 over BN254.
+ *
+ * zkVC ("zkVC: Fast Zero-Knowledge Proof for Private and Verifiable Computing",
+ * arXiv 2504.12217) proves Y = X W with the Constraint-reduced Polynomial Circuit (CRPC,
+ * Sec. III-A) and Prefix-Sum Query (PSQ, Sec. III-B), and runs Groth16 Gen / Prove /
+ * Verify (Sec. II) as its zkVC-G backend (Sec. IV).  This library exposes that problem
+ * statement (setup / prove / verify on a matmul shape) and the kernels underneath it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Field elements cross the ABI in canonical (non-Montgomery) form: 32 bytes,
+ *    little-endian, value < modulus.  Fr is the BN254 scalar field (order r), Fp the base
+ *    field (modulus p).
+ *  - G1 points are affine x || y (64 bytes); G2 points are x.c0 || x.c1 || y.c0 || y.c1
+ *    (128 bytes) with Fp2 = Fp[i]/(i^2 + 1).  The point at infinity is all zero bytes.
+ *  - "d_" pointers are CUDA device pointers owned by the caller; other pointers are host
+ *    pointers owned by the caller.  Handles (zkvc_pk, zkvc_vk) are owned by the library.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Unless a
+ *    function says it synchronises, work is only enqueued on `stream`.
+ *  - Every function returns ZKVC_OK (0) or a negative status; zkvc_last_error() then
+ *    describes the failure (thread-local, valid until the next call on that thread).
+ *  - Workspaces are caller-provided device buffers of at least the size the matching
+ *    *_workspace_bytes() function reports; the library never allocates inside a call
+ *    that takes a workspace, except for a per-device domain table built once on first
+ *    use of each NTT size (so warm up before capturing such a call in a CUDA graph).
+ */
+#ifndef ZKVC_H_
+#define ZKVC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define ZKVC_OK 0
+#define ZKVC_EINVAL (-1)   /* bad argument: shape, size, pointer, encoding              */
+#define ZKVC_ENOMEM (-2)   /* a device or host allocation failed                        */
+#define ZKVC_ECUDA (-3)    /* a CUDA runtime call failed                                 */
+#define ZKVC_ETIMEOUT (-4) /* a bounded device-side wait ran out                         */
+#define ZKVC_EUNSAT (-5)   /* the witness does not satisfy the CRPC constraints          */
+#define ZKVC_EIO (-6)      /* serialisation: short buffer, bad header or checksum        */
+
+/* Description of the last failure on the calling thread ("" after success). */
+const char* zkvc_last_error(void);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int zkvc_version(void);
+
+/* ------------------------------------------------------------------ field kernels
+ * Elementwise products of n canonical elements: d_out[i] = d_a[i] * d_b[i] mod the
+ * field's modulus (Fr: scalar field r; Fp: base field p; Fp2: pairs c0 || c1, 64 bytes
+ * per element, with i^2 = -1).  Inputs must be canonical.  d_out may alias d_a or d_b.
+ * These are the Montgomery multiplication kernels of the prover (BN254 arithmetic of the
+ * groth16 backend, Sec. IV) exposed for verification.
+ */
+int zkvc_fr_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream);
+int zkvc_fp_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream);
+int zkvc_fp2_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream);
+
+/* ------------------------------------------------------------------ NTT over Fr
+ * In-place transform of N = 2^log_n canonical Fr elements in natural order
+ * (1 <= log_n <= 28), over the domain H = <omega_N>, omega_N = 5^((r-1)/2^28)^(2^28/N),
+ * and the coset gH with g = 5 -- the domain on which the QAP of the CRPC R1CS is
+ * interpolated (Sec. II) and whose coset carries the quotient h(x):
+ *   ZKVC_NTT_FORWARD        v_k = sum_i a_i omega^(ik)
+ *   ZKVC_NTT_INVERSE        a_i = N^-1 sum_k v_k omega^(-ik)
+ *   ZKVC_NTT_COSET_FORWARD  v_k = sum_i a_i g^i omega^(ik)
+ *   ZKVC_NTT_COSET_INVERSE  a_i = g^-i N^-1 sum_k v_k omega^(-ik)
+ * No workspace; the first call for a given log_n on a device builds and caches that
+ * domain's tables (allocates and synchronises).
+ */
+#define ZKVC_NTT_FORWARD 0
+#define ZKVC_NTT_INVERSE 1
+#define ZKVC_NTT_COSET_FORWARD 2
+#define ZKVC_NTT_COSET_INVERSE 3
+int zkvc_ntt(uint8_t* d_data, uint32_t log_n, int kind, void* stream);
+
+/* ------------------------------------------------------------------ MSM
+ * Variable-base multi-scalar multiplication out = sum_i s_i P_i (Pippenger, signed
+ * c-bit windows, bucket sort and parallel reduction) -- the kernel behind the A, B, L
+ * and H queries of Groth16 Prove (Sec. II).
+ *   d_points   n affine points (64 bytes each for G1, 128 for G2), canonical, on the curve
+ *              (not checked); infinity allowed
+ *   d_scalars  n canonical Fr scalars (32 bytes each)
+ *   d_ws       device workspace of zkvc_msm_workspace_bytes(n, group) bytes
+ *   out        host buffer of 64 (G1) or 128 (G2) bytes; the call synchronises `stream`
+ * group = 1 for G1, 2 for G2.  n may be 0 (out = infinity).
+ */
+size_t zkvc_msm_workspace_bytes(size_t n, int group);
+int zkvc_msm_g1(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
+                uint8_t out[64], void* stream);
+int zkvc_msm_g2(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
+                uint8_t out[128], void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZKVC_H_ */

@@ -1,0 +1,201 @@
+// C-ABI entry points for the kernel layer: field products, NTT, variable-base MSM.
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "msm.h"
+#include "ntt.h"
+
+namespace zkvc {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+static void clear_error() { g_err.clear(); }
+
+// ------------------------------------------------------------------ field products
+template <class C>
+__global__ void k_field_mul(const Field<C>* a, const Field<C>* b, Field<C>* out, size_t n) {
+  size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // (a R) b / R = a b: one conversion and one Montgomery product, canonical in and out
+  st_field(out + i, f_mul(f_to_mont(ld_field(a + i)), ld_field(b + i)));
+}
+
+__global__ void k_fp2_mul(const Fp2* a, const Fp2* b, Fp2* out, size_t n) {
+  size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Fp2 x = ld_field(a + i);
+  x = f_to_mont(x);
+  st_field(out + i, f_mul(x, ld_field(b + i)));
+}
+
+// ------------------------------------------------------------------ points
+template <class F>
+__global__ void k_points_to_mont(const Affine<F>* in, Affine<F>* out, size_t n) {
+  size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Affine<F> p = ld_field(in + i);
+  p.x = f_to_mont(p.x);
+  p.y = f_to_mont(p.y);
+  st_field(out + i, p);
+}
+
+template <class F>
+__global__ void k_export_point(const XYZZ<F>* in, Affine<F>* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Affine<F> a = p_to_affine(ld_field(in));
+  a.x = f_from_mont(a.x);
+  a.y = f_from_mont(a.y);
+  st_field(out, a);
+}
+
+static uint32_t window_bits(size_t n) {
+  uint32_t lg = ceil_log2(n < 2 ? 2 : n);
+  int c = (int)lg - 3;
+  if (c < 4) c = 4;
+  if (c > 16) c = 16;
+  return (uint32_t)c;
+}
+
+static MsmPlan variable_base_plan(size_t n, const void* scalars) {
+  MsmPlan p;
+  uint32_t c = window_bits(n);
+  MsmOut o{};
+  o.c = c;
+  o.win_keys = (255 + c - 1) / c;
+  p.outs.push_back(o);
+  MsmSeg s{};
+  s.base_off = 0;
+  s.count = (uint32_t)n;
+  s.nwin = 1;
+  s.out = 0;
+  s.kind = SK_FR_CANON;
+  s.scalars = scalars;
+  s.skip = 0xffffffffu;
+  p.segs.push_back(s);
+  msm_plan_finalize(p);
+  return p;
+}
+
+template <class F>
+static size_t msm_api_ws(size_t n) {
+  MsmPlan p = variable_base_plan(n, nullptr);
+  return msm_workspace_bytes<F>(p) + ((n * sizeof(Affine<F>) + 255) & ~size_t(255)) + 2 * 256 +
+         sizeof(XYZZ<F>) + sizeof(Affine<F>);
+}
+
+template <class F>
+static int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
+                   uint8_t* out, cudaStream_t st) {
+  ZK_CHECK(out != nullptr, ZKVC_EINVAL, "msm: null output");
+  ZK_CHECK(n < (1ull << 31), ZKVC_EINVAL, "msm: n = %zu too large", n);
+  if (n == 0) {
+    memset(out, 0, sizeof(Affine<F>));
+    return ZKVC_OK;
+  }
+  ZK_CHECK(d_points && d_scalars && d_ws, ZKVC_EINVAL, "msm: null device pointer");
+  size_t need = msm_api_ws<F>(n);
+  ZK_CHECK(ws_bytes >= need, ZKVC_EINVAL, "msm: workspace %zu < %zu bytes", ws_bytes, need);
+  Arena a;
+  a.base = reinterpret_cast<uint8_t*>(d_ws);
+  a.cap = ws_bytes;
+  Affine<F>* bases = a.take<Affine<F>>(n);
+  XYZZ<F>* res = a.take<XYZZ<F>>(1);
+  Affine<F>* aff = a.take<Affine<F>>(1);
+  uint8_t* rest = a.base + a.off;
+  size_t rest_bytes = ws_bytes - a.off;
+  k_points_to_mont<F><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const Affine<F>*>(d_points), bases, n);
+  ZK_CUDA(cudaGetLastError());
+  MsmPlan p = variable_base_plan(n, d_scalars);
+  ZK_TRY(msm_run<F>(p, bases, rest, rest_bytes, res, st));
+  k_export_point<F><<<1, 32, 0, st>>>(res, aff);
+  ZK_CUDA(cudaGetLastError());
+  ZK_CUDA(cudaMemcpyAsync(out, aff, sizeof(Affine<F>), cudaMemcpyDeviceToHost, st));
+  ZK_CUDA(cudaStreamSynchronize(st));
+  return ZKVC_OK;
+}
+
+}  // namespace zkvc
+
+using namespace zkvc;
+
+extern "C" {
+
+const char* zkvc_last_error(void) { return g_err.c_str(); }
+
+int zkvc_version(void) { return 100; }
+
+int zkvc_fr_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream) {
+  clear_error();
+  if (n == 0) return ZKVC_OK;
+  ZK_CHECK(d_a && d_b && d_out, ZKVC_EINVAL, "fr_mul: null pointer");
+  k_field_mul<FrCfg><<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      (const Fr*)d_a, (const Fr*)d_b, (Fr*)d_out, n);
+  ZK_CUDA(cudaGetLastError());
+  return ZKVC_OK;
+}
+
+int zkvc_fp_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream) {
+  clear_error();
+  if (n == 0) return ZKVC_OK;
+  ZK_CHECK(d_a && d_b && d_out, ZKVC_EINVAL, "fp_mul: null pointer");
+  k_field_mul<FpCfg><<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      (const Fp*)d_a, (const Fp*)d_b, (Fp*)d_out, n);
+  ZK_CUDA(cudaGetLastError());
+  return ZKVC_OK;
+}
+
+int zkvc_fp2_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream) {
+  clear_error();
+  if (n == 0) return ZKVC_OK;
+  ZK_CHECK(d_a && d_b && d_out, ZKVC_EINVAL, "fp2_mul: null pointer");
+  k_fp2_mul<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>((const Fp2*)d_a, (const Fp2*)d_b,
+                                                                            (Fp2*)d_out, n);
+  ZK_CUDA(cudaGetLastError());
+  return ZKVC_OK;
+}
+
+int zkvc_ntt(uint8_t* d_data, uint32_t log_n, int kind, void* stream) {
+  clear_error();
+  ZK_CHECK(d_data != nullptr, ZKVC_EINVAL, "ntt: null pointer");
+  ZK_CHECK(kind >= 0 && kind <= 3, ZKVC_EINVAL, "ntt: kind %d", kind);
+  const NttDomain* d = nullptr;
+  ZK_TRY(ntt_domain(log_n, &d));
+  cudaStream_t st = (cudaStream_t)stream;
+  Fr* x = reinterpret_cast<Fr*>(d_data);
+  bool inverse = kind == ZKVC_NTT_INVERSE || kind == ZKVC_NTT_COSET_INVERSE;
+  int load_scale = kind == ZKVC_NTT_COSET_FORWARD ? SC_G : SC_NONE;
+  int out_scale = kind == ZKVC_NTT_INVERSE ? SC_N : (kind == ZKVC_NTT_COSET_INVERSE ? SC_NGI : SC_NONE);
+  ZK_TRY(ntt_dif(x, 1, 0, d, inverse, load_scale, SC_NONE, true, st));
+  ZK_TRY(ntt_bitrev(x, d, out_scale, true, st));
+  return ZKVC_OK;
+}
+
+size_t zkvc_msm_workspace_bytes(size_t n, int group) {
+  if (n == 0) return 0;
+  return group == 2 ? msm_api_ws<Fp2>(n) : msm_api_ws<Fp>(n);
+}
+
+int zkvc_msm_g1(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
+                uint8_t out[64], void* stream) {
+  clear_error();
+  return msm_api<Fp>(d_points, d_scalars, n, d_ws, ws_bytes, out, (cudaStream_t)stream);
+}
+
+int zkvc_msm_g2(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
+                uint8_t out[128], void* stream) {
+  clear_error();
+  return msm_api<Fp2>(d_points, d_scalars, n, d_ws, ws_bytes, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,389 @@
+// BN254 prime fields on 8 x 32-bit limbs in Montgomery form, and Fp2 = Fp[i]/(i^2 + 1).
+//
+// The Groth16 prover of zkVC (Sec. IV: libsnark's groth16 backend) works in the scalar
+// field Fr (witness, QAP polynomials, NTT) and the base field Fp (curve coordinates).
+// Both moduli are below 2^254, which the bounds below rely on.
+//
+// Multiplication is CIOS Montgomery (coarsely integrated operand scanning): for each
+// limb b_i of the multiplier the row t += a * b_i is two carry chains of mad.lo / mad.hi
+// (PTX mad.lo.cc / madc.hi.cc, one IMAD each), then m = t_0 * (-N^-1 mod 2^32) and
+// t = (t + m N) / 2^32 the same way.  With a, b < N < 2^254 every intermediate stays
+// below 2^288, so a 9-word accumulator never carries out and the result is < 2N before
+// the single conditional subtraction.  Cost: 4 * 8 * 8 + 8 = 264 IMADs per product.
+#pragma once
+#include <cstdint>
+
+namespace zkvc {
+
+// ------------------------------------------------------------------ compile-time bignum
+struct U256c {
+  uint32_t w[8];
+};
+
+constexpr U256c cx_dbl_mod(U256c x, U256c m) {
+  U256c r{};
+  uint32_t c = 0;
+  for (int i = 0; i < 8; i++) {
+    uint64_t v = ((uint64_t)x.w[i] << 1) | c;
+    r.w[i] = (uint32_t)v;
+    c = (uint32_t)(v >> 32);
+  }
+  bool ge = c != 0;
+  if (!ge) {
+    ge = true;
+    for (int i = 7; i >= 0; i--) {
+      if (r.w[i] != m.w[i]) {
+        ge = r.w[i] > m.w[i];
+        break;
+      }
+    }
+  }
+  if (ge) {
+    uint64_t br = 0;
+    for (int i = 0; i < 8; i++) {
+      uint64_t v = (uint64_t)r.w[i] - m.w[i] - br;
+      r.w[i] = (uint32_t)v;
+      br = (v >> 63) & 1;
+    }
+  }
+  return r;
+}
+
+constexpr U256c cx_pow2_mod(int k, U256c m) {
+  U256c x{};
+  x.w[0] = 1;
+  for (int i = 0; i < k; i++) x = cx_dbl_mod(x, m);
+  return x;
+}
+
+constexpr uint32_t cx_neg_inv32(uint32_t m0) {
+  uint32_t x = m0;  // Newton iteration for m0^-1 mod 2^32 (m0 odd)
+  for (int i = 0; i < 5; i++) x = x * (2u - m0 * x);
+  return 0u - x;
+}
+
+constexpr U256c cx_sub1(U256c m) {  // m - 2, used for Fermat exponents
+  U256c r = m;
+  uint64_t br = 2;
+  for (int i = 0; i < 8; i++) {
+    uint64_t v = (uint64_t)r.w[i] - br;
+    r.w[i] = (uint32_t)v;
+    br = (v >> 63) & 1;
+  }
+  return r;
+}
+
+// ------------------------------------------------------------------ field parameters
+// p and r of BN254 (alt_bn128), little-endian 32-bit limbs.
+struct FpCfg {
+  static constexpr U256c MOD = {{0xd87cfd47u, 0x3c208c16u, 0x6871ca8du, 0x97816a91u,
+                                 0x8181585du, 0xb85045b6u, 0xe131a029u, 0x30644e72u}};
+  static constexpr U256c R1 = cx_pow2_mod(256, MOD);
+  static constexpr U256c R2 = cx_pow2_mod(512, MOD);
+  static constexpr U256c MOD_M2 = cx_sub1(MOD);
+  static constexpr uint32_t INV = cx_neg_inv32(MOD.w[0]);
+};
+
+struct FrCfg {
+  static constexpr U256c MOD = {{0xf0000001u, 0x43e1f593u, 0x79b97091u, 0x2833e848u,
+                                 0x8181585du, 0xb85045b6u, 0xe131a029u, 0x30644e72u}};
+  static constexpr U256c R1 = cx_pow2_mod(256, MOD);
+  static constexpr U256c R2 = cx_pow2_mod(512, MOD);
+  static constexpr U256c MOD_M2 = cx_sub1(MOD);
+  static constexpr uint32_t INV = cx_neg_inv32(MOD.w[0]);
+};
+
+#define ZKVC_LIMB_SWITCH(ARR, i)                                               \
+  switch (i) {                                                                 \
+    case 0: return ARR.w[0];                                                   \
+    case 1: return ARR.w[1];                                                   \
+    case 2: return ARR.w[2];                                                   \
+    case 3: return ARR.w[3];                                                   \
+    case 4: return ARR.w[4];                                                   \
+    case 5: return ARR.w[5];                                                   \
+    case 6: return ARR.w[6];                                                   \
+    default: return ARR.w[7];                                                  \
+  }
+
+template <class C>
+__host__ __device__ __forceinline__ constexpr uint32_t mod_limb(int i) { ZKVC_LIMB_SWITCH(C::MOD, i) }
+template <class C>
+__host__ __device__ __forceinline__ constexpr uint32_t r1_limb(int i) { ZKVC_LIMB_SWITCH(C::R1, i) }
+template <class C>
+__host__ __device__ __forceinline__ constexpr uint32_t r2_limb(int i) { ZKVC_LIMB_SWITCH(C::R2, i) }
+template <class C>
+__host__ __device__ __forceinline__ constexpr uint32_t modm2_limb(int i) { ZKVC_LIMB_SWITCH(C::MOD_M2, i) }
+
+// ------------------------------------------------------------------ carry-chain rows
+// t[0..8] += a[0..7] * b : low halves into t[0..7] (carry into t[8]), then high halves
+// into t[1..8].  The caller guarantees that the 288-bit sum fits.
+__device__ __forceinline__ void mac_row(uint32_t (&t)[9], const uint32_t (&a)[8], uint32_t b) {
+  asm("mad.lo.cc.u32  %0, %9,  %17, %0;\n\t"
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+      "addc.u32       %8, %8, 0;\n\t"
+      "mad.hi.cc.u32  %1, %9,  %17, %1;\n\t"
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
+      "madc.hi.u32    %8, %16, %17, %8;"
+      : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]),
+        "+r"(t[7]), "+r"(t[8])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+        "r"(b));
+}
+
+// r = a + b over 8 limbs; returns the carry out.
+__device__ __forceinline__ uint32_t add8(uint32_t (&r)[8], const uint32_t (&a)[8], const uint32_t (&b)[8]) {
+  uint32_t c;
+  asm("add.cc.u32  %0, %9,  %17;\n\t"
+      "addc.cc.u32 %1, %10, %18;\n\t"
+      "addc.cc.u32 %2, %11, %19;\n\t"
+      "addc.cc.u32 %3, %12, %20;\n\t"
+      "addc.cc.u32 %4, %13, %21;\n\t"
+      "addc.cc.u32 %5, %14, %22;\n\t"
+      "addc.cc.u32 %6, %15, %23;\n\t"
+      "addc.cc.u32 %7, %16, %24;\n\t"
+      "addc.u32    %8, 0, 0;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(c)
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+        "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+  return c;
+}
+
+// r = a - b over 8 limbs; returns 1 if it borrowed (a < b).
+__device__ __forceinline__ uint32_t sub8(uint32_t (&r)[8], const uint32_t (&a)[8], const uint32_t (&b)[8]) {
+  uint32_t br;
+  asm("sub.cc.u32  %0, %9,  %17;\n\t"
+      "subc.cc.u32 %1, %10, %18;\n\t"
+      "subc.cc.u32 %2, %11, %19;\n\t"
+      "subc.cc.u32 %3, %12, %20;\n\t"
+      "subc.cc.u32 %4, %13, %21;\n\t"
+      "subc.cc.u32 %5, %14, %22;\n\t"
+      "subc.cc.u32 %6, %15, %23;\n\t"
+      "subc.cc.u32 %7, %16, %24;\n\t"
+      "subc.u32    %8, 0, 0;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(br)
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),
+        "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+  return br & 1u;
+}
+
+// ------------------------------------------------------------------ prime field element
+template <class C>
+struct Field {
+  uint32_t v[8];
+
+  __device__ __forceinline__ static Field zero() {
+    Field r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = 0;
+    return r;
+  }
+  __device__ __forceinline__ static Field one() {  // R mod N (Montgomery form of 1)
+    Field r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = r1_limb<C>(i);
+    return r;
+  }
+  __device__ __forceinline__ static Field modulus() {
+    Field r;
+#pragma unroll
+    for (int i = 0; i < 8; i++) r.v[i] = mod_limb<C>(i);
+    return r;
+  }
+  __device__ __forceinline__ bool is_zero() const {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc |= v[i];
+    return acc == 0;
+  }
+  __device__ __forceinline__ bool operator==(const Field& o) const {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc |= v[i] ^ o.v[i];
+    return acc == 0;
+  }
+  __device__ __forceinline__ bool operator!=(const Field& o) const { return !(*this == o); }
+};
+
+template <class C>
+__device__ __forceinline__ Field<C> f_add(const Field<C>& a, const Field<C>& b) {
+  Field<C> s, d;
+  add8(s.v, a.v, b.v);  // a + b < 2N < 2^255: no carry out
+  const Field<C> m = Field<C>::modulus();
+  uint32_t br = sub8(d.v, s.v, m.v);
+  return br ? s : d;
+}
+
+template <class C>
+__device__ __forceinline__ Field<C> f_sub(const Field<C>& a, const Field<C>& b) {
+  Field<C> d, e;
+  uint32_t br = sub8(d.v, a.v, b.v);
+  const Field<C> m = Field<C>::modulus();
+  add8(e.v, d.v, m.v);
+  return br ? e : d;
+}
+
+template <class C>
+__device__ __forceinline__ Field<C> f_neg(const Field<C>& a) {
+  return f_sub(Field<C>::zero(), a);
+}
+
+template <class C>
+__device__ __forceinline__ Field<C> f_dbl(const Field<C>& a) { return f_add(a, a); }
+
+// Montgomery product a b R^-1 mod N.
+template <class C>
+__device__ __forceinline__ Field<C> f_mul(const Field<C>& a, const Field<C>& b) {
+  uint32_t t[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) t[i] = 0;
+  uint32_t m[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) m[i] = mod_limb<C>(i);
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    mac_row(t, a.v, b.v[i]);
+    uint32_t q = t[0] * C::INV;
+    mac_row(t, m, q);  // t[0] becomes 0
+#pragma unroll
+    for (int j = 0; j < 8; j++) t[j] = t[j + 1];
+    t[8] = 0;
+  }
+  Field<C> r, d;
+#pragma unroll
+  for (int i = 0; i < 8; i++) r.v[i] = t[i];
+  uint32_t br = sub8(d.v, r.v, m);
+  return br ? r : d;
+}
+
+template <class C>
+__device__ __forceinline__ Field<C> f_sqr(const Field<C>& a) { return f_mul(a, a); }
+
+template <class C>
+__device__ __forceinline__ Field<C> f_to_mont(const Field<C>& a) {
+  Field<C> r2;
+#pragma unroll
+  for (int i = 0; i < 8; i++) r2.v[i] = r2_limb<C>(i);
+  return f_mul(a, r2);
+}
+
+template <class C>
+__device__ __forceinline__ Field<C> f_from_mont(const Field<C>& a) {
+  Field<C> one_raw = Field<C>::zero();
+  one_raw.v[0] = 1;
+  return f_mul(a, one_raw);
+}
+
+// Canonical value from a small signed integer (|v| < 2^31), already in Montgomery form.
+template <class C>
+__device__ __forceinline__ Field<C> f_from_int(int32_t v) {
+  Field<C> x = Field<C>::zero();
+  uint32_t mag = v < 0 ? (uint32_t)(-(int64_t)v) : (uint32_t)v;
+  x.v[0] = mag;
+  x = f_to_mont(x);
+  return v < 0 ? f_neg(x) : x;
+}
+
+// a^e for an exponent given as 8 limbs (plain square-and-multiply, MSB first).
+template <class C>
+__device__ __forceinline__ Field<C> f_pow(const Field<C>& a, const uint32_t (&e)[8]) {
+  Field<C> r = Field<C>::one();
+  for (int i = 7; i >= 0; i--) {
+    for (int bit = 31; bit >= 0; bit--) {
+      r = f_sqr(r);
+      if ((e[i] >> bit) & 1u) r = f_mul(r, a);
+    }
+  }
+  return r;
+}
+
+// Inverse by Fermat's little theorem, a^(N-2); a = 0 maps to 0.
+template <class C>
+__device__ __noinline__ Field<C> f_inv(const Field<C>& a) {
+  uint32_t e[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) e[i] = modm2_limb<C>(i);
+  return f_pow(a, e);
+}
+
+using Fp = Field<FpCfg>;
+using Fr = Field<FrCfg>;
+
+// ------------------------------------------------------------------ Fp2 = Fp[i]/(i^2+1)
+struct Fp2 {
+  Fp c0, c1;
+  __device__ __forceinline__ static Fp2 zero() { return {Fp::zero(), Fp::zero()}; }
+  __device__ __forceinline__ static Fp2 one() { return {Fp::one(), Fp::zero()}; }
+  __device__ __forceinline__ bool is_zero() const { return c0.is_zero() && c1.is_zero(); }
+  __device__ __forceinline__ bool operator==(const Fp2& o) const { return c0 == o.c0 && c1 == o.c1; }
+  __device__ __forceinline__ bool operator!=(const Fp2& o) const { return !(*this == o); }
+};
+
+__device__ __forceinline__ Fp2 f_add(const Fp2& a, const Fp2& b) { return {f_add(a.c0, b.c0), f_add(a.c1, b.c1)}; }
+__device__ __forceinline__ Fp2 f_sub(const Fp2& a, const Fp2& b) { return {f_sub(a.c0, b.c0), f_sub(a.c1, b.c1)}; }
+__device__ __forceinline__ Fp2 f_neg(const Fp2& a) { return {f_neg(a.c0), f_neg(a.c1)}; }
+__device__ __forceinline__ Fp2 f_dbl(const Fp2& a) { return {f_dbl(a.c0), f_dbl(a.c1)}; }
+
+// Karatsuba: (a0 + a1 i)(b0 + b1 i) = (a0 b0 - a1 b1) + ((a0 + a1)(b0 + b1) - a0 b0 - a1 b1) i
+// (out of line: G2 formulas call it ~14 times each)
+static __device__ __noinline__ Fp2 f_mul(Fp2 a, Fp2 b) {
+  Fp t0 = f_mul(a.c0, b.c0);
+  Fp t1 = f_mul(a.c1, b.c1);
+  Fp t2 = f_mul(f_add(a.c0, a.c1), f_add(b.c0, b.c1));
+  return {f_sub(t0, t1), f_sub(f_sub(t2, t0), t1)};
+}
+
+// (a0 + a1 i)^2 = (a0 + a1)(a0 - a1) + 2 a0 a1 i
+static __device__ __noinline__ Fp2 f_sqr(Fp2 a) {
+  Fp t = f_mul(a.c0, a.c1);
+  return {f_mul(f_add(a.c0, a.c1), f_sub(a.c0, a.c1)), f_dbl(t)};
+}
+
+__device__ __forceinline__ Fp2 f_inv(const Fp2& a) {
+  Fp n = f_add(f_sqr(a.c0), f_sqr(a.c1));
+  Fp ni = f_inv(n);
+  return {f_mul(a.c0, ni), f_neg(f_mul(a.c1, ni))};
+}
+
+__device__ __forceinline__ Fp2 f_to_mont(const Fp2& a) { return {f_to_mont(a.c0), f_to_mont(a.c1)}; }
+__device__ __forceinline__ Fp2 f_from_mont(const Fp2& a) { return {f_from_mont(a.c0), f_from_mont(a.c1)}; }
+
+// ------------------------------------------------------------------ memory helpers
+template <class F>
+__device__ __forceinline__ F ld_field(const F* p) {
+  static_assert(sizeof(F) % 16 == 0, "16-byte vector loads");
+  F r;
+  uint32_t* d = reinterpret_cast<uint32_t*>(&r);
+  const uint4* s = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(F) / 16); i++) {
+    uint4 q = s[i];
+    d[4 * i] = q.x;
+    d[4 * i + 1] = q.y;
+    d[4 * i + 2] = q.z;
+    d[4 * i + 3] = q.w;
+  }
+  return r;
+}
+
+template <class F>
+__device__ __forceinline__ void st_field(F* p, const F& x) {
+  uint4* d = reinterpret_cast<uint4*>(p);
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(&x);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(F) / 16); i++) d[i] = make_uint4(s[4 * i], s[4 * i + 1], s[4 * i + 2], s[4 * i + 3]);
+}
+
+}  // namespace zkvc

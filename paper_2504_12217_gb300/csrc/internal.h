@@ -1,0 +1,61 @@
+// Internal declarations shared by the translation units of libzkvc (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/zkvc.h"
+
+namespace zkvc {
+
+void set_error(const char* fmt, ...);
+
+#define ZK_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      ::zkvc::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return ZKVC_ECUDA;                                                                    \
+    }                                                                                       \
+  } while (0)
+
+#define ZK_CHECK(cond, code, ...)       \
+  do {                                  \
+    if (!(cond)) {                      \
+      ::zkvc::set_error(__VA_ARGS__);   \
+      return (code);                    \
+    }                                   \
+  } while (0)
+
+#define ZK_TRY(expr)             \
+  do {                           \
+    int rc_ = (expr);            \
+    if (rc_ != ZKVC_OK) return rc_; \
+  } while (0)
+
+// Bump allocator over a caller-provided device workspace (256-byte aligned slices).
+struct Arena {
+  uint8_t* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  bool measuring = false;  // when true only sizes are accumulated
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    size_t at = off;
+    off += bytes;
+    if (measuring || base == nullptr) return nullptr;
+    if (off > cap) return nullptr;
+    return reinterpret_cast<T*>(base + at);
+  }
+  bool overflow() const { return !measuring && off > cap; }
+};
+
+inline uint32_t ceil_log2(size_t n) {
+  uint32_t l = 0;
+  while ((size_t(1) << l) < n) l++;
+  return l;
+}
+
+}  // namespace zkvc

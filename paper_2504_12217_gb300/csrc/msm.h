@@ -1,0 +1,66 @@
+// Pippenger multi-scalar multiplication engine (internal).
+#pragma once
+#include <vector>
+
+#include "curve.cuh"
+#include "internal.h"
+
+namespace zkvc {
+
+enum ScalarKind : int32_t {
+  SK_ONE = 0,       // the scalar 1 (no array)
+  SK_I8 = 1,        // int8 array, signed
+  SK_I32 = 2,       // int32 array, signed, |v| < 2^31
+  SK_FR_MONT = 3,   // Fr array in Montgomery form
+  SK_FR_CANON = 4,  // Fr array, canonical little-endian 8 x u32
+};
+
+// One run of points sharing a scalar kind and an output.
+struct MsmSeg {
+  uint64_t base_off;   // index of window 0 of point 0 in the base array
+  uint32_t count;      // points
+  uint32_t nwin;       // bases stored per point: 2^(c w) multiples for w < nwin
+  uint32_t out;        // output index
+  int32_t kind;        // ScalarKind
+  const void* scalars; // device array (unused for SK_ONE)
+  uint32_t skip;       // point whose scalar is ignored (0xffffffff: none)
+  uint32_t nd;         // digits per scalar (planner)
+  uint64_t slot_off;   // first digit slot (planner)
+  uint32_t point_off;  // cumulative points before this segment (planner)
+  uint32_t pad;
+};
+
+struct MsmOut {
+  uint32_t c;          // window bits; digit magnitudes 1 .. 2^(c-1)
+  uint32_t win_keys;   // >1: windows get their own buckets (variable base) and are
+                       // combined by Horner's rule; 1: windows use precomputed bases
+  uint32_t key_off;    // planner
+  uint32_t nkeys;      // planner: win_keys * 2^(c-1)
+};
+
+struct MsmPlan {
+  std::vector<MsmSeg> segs;
+  std::vector<MsmOut> outs;
+  uint64_t slots = 0;
+  uint32_t keys = 0;
+  uint32_t points = 0;
+  uint32_t max_nd = 0;
+};
+
+// Fills the planner fields; returns ZKVC_EINVAL on an inconsistent plan.
+int msm_plan_finalize(MsmPlan& p);
+
+// Device workspace the run needs (bytes), for a finalized plan and coordinate field.
+template <class F>
+size_t msm_workspace_bytes(const MsmPlan& p);
+
+// Runs every output of the plan; results[o] receives output o (XYZZ, device).
+template <class F>
+int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results,
+            cudaStream_t st);
+
+// Exclusive scan of n uint32 values into out[0..n] (out[n] = total); temp from the arena.
+int scan_u32(const uint32_t* in, uint32_t* out, size_t n, Arena& a, cudaStream_t st);
+size_t scan_u32_temp_bytes(size_t n);
+
+}  // namespace zkvc

@@ -1,0 +1,167 @@
+"""Thin ctypes binding of libzkvc.so: the C ABI of ``include/zkvc.h`` under the same names.
+
+Only argument marshalling happens here: device tensors become raw pointers, the current
+torch CUDA stream becomes the ``stream`` argument, and non-zero status codes become
+``ZkvcError``.  Every computation runs in the library's CUDA kernels; there is no
+fallback.  If ``libzkvc.so`` has not been built, loading raises immediately.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libzkvc.so")
+
+ZKVC_OK = 0
+ZKVC_EINVAL = -1
+ZKVC_ENOMEM = -2
+ZKVC_ECUDA = -3
+ZKVC_ETIMEOUT = -4
+ZKVC_EUNSAT = -5
+ZKVC_EIO = -6
+
+ZKVC_NTT_FORWARD = 0
+ZKVC_NTT_INVERSE = 1
+ZKVC_NTT_COSET_FORWARD = 2
+ZKVC_NTT_COSET_INVERSE = 3
+
+_c_p = ctypes.c_void_p
+_c_sz = ctypes.c_size_t
+_c_int = ctypes.c_int
+_c_u32 = ctypes.c_uint32
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "zkvc_last_error": (ctypes.c_char_p, []),
+    "zkvc_version": (_c_int, []),
+    "zkvc_fr_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
+    "zkvc_fp_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
+    "zkvc_fp2_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
+    "zkvc_ntt": (_c_int, [_c_p, _c_u32, _c_int, _c_p]),
+    "zkvc_msm_workspace_bytes": (_c_sz, [_c_sz, _c_int]),
+    "zkvc_msm_g1": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
+    "zkvc_msm_g2": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
+}
+
+
+class ZkvcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"zkvc status {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2504_12217_gb300.build.build()")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def check(rc):
+    if rc != ZKVC_OK:
+        raise ZkvcError(rc, lib().zkvc_last_error().decode())
+    return rc
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_ptr(t):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _u8(t, width):
+    torch = _torch()
+    if t.dtype != torch.uint8 or t.dim() != 2 or t.shape[1] != width:
+        raise ValueError(f"expected a uint8 tensor of shape [n, {width}]")
+    return t
+
+
+# ------------------------------------------------------------------ kernel layer
+def zkvc_version():
+    return lib().zkvc_version()
+
+
+def zkvc_fr_mul(a, b, out=None):
+    """Elementwise a * b mod r of [n, 32] canonical uint8 CUDA tensors."""
+    return _field_mul("zkvc_fr_mul", a, b, out, 32)
+
+
+def zkvc_fp_mul(a, b, out=None):
+    return _field_mul("zkvc_fp_mul", a, b, out, 32)
+
+
+def zkvc_fp2_mul(a, b, out=None):
+    return _field_mul("zkvc_fp2_mul", a, b, out, 64)
+
+
+def _field_mul(name, a, b, out, width):
+    _u8(a, width)
+    _u8(b, width)
+    if out is None:
+        out = _torch().empty_like(a)
+    check(getattr(lib(), name)(_dev_ptr(a), _dev_ptr(b), _dev_ptr(out), a.shape[0], _stream()))
+    return out
+
+
+def zkvc_ntt(data, kind):
+    """In-place NTT of a [2^k, 32] canonical Fr CUDA tensor (kind: ZKVC_NTT_*)."""
+    _u8(data, 32)
+    n = data.shape[0]
+    log_n = n.bit_length() - 1
+    if n != 1 << log_n:
+        raise ValueError("length must be a power of two")
+    check(lib().zkvc_ntt(_dev_ptr(data), log_n, kind, _stream()))
+    return data
+
+
+def zkvc_msm_workspace_bytes(n, group):
+    return lib().zkvc_msm_workspace_bytes(n, group)
+
+
+def _msm(name, group, points, scalars, workspace=None):
+    torch = _torch()
+    width = 64 if group == 1 else 128
+    _u8(points, width)
+    _u8(scalars, 32)
+    n = points.shape[0]
+    if scalars.shape[0] != n:
+        raise ValueError("points and scalars differ in length")
+    need = zkvc_msm_workspace_bytes(n, group)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=points.device)
+    out = (ctypes.c_uint8 * width)()
+    check(getattr(lib(), name)(_dev_ptr(points), _dev_ptr(scalars), n, _dev_ptr(workspace),
+                               workspace.numel(), out, _stream()))
+    return bytes(out)
+
+
+def zkvc_msm_g1(points, scalars, workspace=None):
+    """sum_i s_i P_i over G1: points [n, 64], scalars [n, 32]; returns 64 bytes."""
+    return _msm("zkvc_msm_g1", 1, points, scalars, workspace)
+
+
+def zkvc_msm_g2(points, scalars, workspace=None):
+    """sum_i s_i Q_i over G2: points [n, 128], scalars [n, 32]; returns 128 bytes."""
+    return _msm("zkvc_msm_g2", 2, points, scalars, workspace)
