@@ -97,6 +97,79 @@ int zkvc_msm_g1(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, voi
 int zkvc_msm_g2(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
                 uint8_t out[128], void* stream);
 
+/* ------------------------------------------------------------------ Groth16 over CRPC
+ * The circuit (Sec. III-A general CRPC equation with Sec. III-B prefix sums) for
+ * Y = X W, X of a x n and W of n x b (int8), has n multiplication constraints
+ *     row k < n-1:  a_k b_k = S_k - S_(k-1)        (S_(-1) = 0)
+ *     row n-1:      a_(n-1) b_(n-1) = Y(z) - S_(n-2)
+ * with a_k = sum_i z^(ib) x_ik, b_k = sum_j z^j w_kj, Y(z) = sum_ij z^(ib+j) y_ij, plus
+ * l + 1 public-input rows (A = [variable v], v = 0 .. l).  Variables: 0 = one, then X
+ * row-major and Y row-major (public, l = a n + a b), then W row-major and S_0 .. S_(n-2)
+ * (private).  Integers enter Fr as v >= 0 -> v, v < 0 -> r - |v|.  The QAP domain has
+ * N = 2^ceil(log2(n + l + 1)) points.
+ */
+typedef struct zkvc_pk zkvc_pk; /* proving key: resident on the device that built it */
+typedef struct zkvc_vk zkvc_vk; /* verifying key: host memory                         */
+
+/* Gen (Sec. II).  toxic = tau || alpha || beta || gamma || delta || z, six canonical Fr
+ * values (192 bytes, host); z is the CRPC evaluation point of Sec. III-A.  Rejected with
+ * ZKVC_EINVAL: non-canonical values, tau^N = 1, alpha..delta = 0, z in {0, 1}.  Allocates
+ * the key on the current device, synchronises `stream`, and returns library-owned
+ * handles (release with zkvc_pk_free / zkvc_vk_free).
+ */
+int zkvc_setup(int a, int n, int b, const uint8_t toxic[192], void* stream, zkvc_pk** pk, zkvc_vk** vk);
+void zkvc_pk_free(zkvc_pk* pk);
+void zkvc_vk_free(zkvc_vk* vk);
+
+/* Shape of a proving key, its domain size log2 N and its stored base counts. */
+int zkvc_pk_info(const zkvc_pk* pk, int* a, int* n, int* b, uint32_t* log_domain, size_t* g1_bases,
+                 size_t* g2_bases);
+
+/* Copies proving-key entries [start, start + count) of one query to host memory as
+ * canonical affine encodings (64 bytes for G1, 128 for G2), in variable order:
+ *   ZKVC_Q_A   [A_v(tau)]1, v = 0 .. l          ZKVC_Q_B1 / B2  [B_v(tau)]1,2 for W
+ *   ZKVC_Q_L   [(beta A + alpha B + C)_v(tau)/delta]1, W variables then S variables
+ *   ZKVC_Q_H   [tau^j t(tau)/delta]1, j = 0 .. N-2
+ *   ZKVC_Q_ALPHA1 .. ZKVC_Q_DELTA2  the single points [alpha]1, [beta]1, [beta]2,
+ *                                   [delta]1, [delta]2 (start = 0, count = 1)
+ * Synchronises the device.  Make the key's device current first.
+ */
+#define ZKVC_Q_A 0
+#define ZKVC_Q_B1 1
+#define ZKVC_Q_B2 2
+#define ZKVC_Q_L 3
+#define ZKVC_Q_H 4
+#define ZKVC_Q_ALPHA1 5
+#define ZKVC_Q_BETA1 6
+#define ZKVC_Q_BETA2 7
+#define ZKVC_Q_DELTA1 8
+#define ZKVC_Q_DELTA2 9
+int zkvc_pk_export(const zkvc_pk* pk, int query, size_t start, size_t count, uint8_t* out);
+
+/* Verifying-key entries: IC_v = [(beta A + alpha B + C)_v(tau)/gamma]1 (v = 0 .. l) and
+ * the points [alpha]1, [beta]2, [gamma]2, [delta]2.  Host copy, no device work.
+ */
+#define ZKVC_VK_IC 0
+#define ZKVC_VK_ALPHA1 1
+#define ZKVC_VK_BETA2 2
+#define ZKVC_VK_GAMMA2 3
+#define ZKVC_VK_DELTA2 4
+int zkvc_vk_export(const zkvc_vk* vk, int query, size_t start, size_t count, uint8_t* out);
+
+/* Prove (Sec. II) for the key's shape.
+ *   d_X   a x n int8, row-major (device)          d_W  n x b int8, row-major (device)
+ *   rs    r || s, two canonical Fr values (64 bytes, host): the prover's randomness
+ *   d_Y   a x b int32 output (device): receives Y = X W, the proven product
+ *   d_ws  device workspace of zkvc_prove_workspace_bytes(pk) bytes
+ *   proof 256-byte host output: A (G1, 64) || B (G2, 128) || C (G1, 64), canonical affine
+ * Synchronises `stream`.  ZKVC_EUNSAT if the device-side checks find the witness does
+ * not satisfy the constraints (the PSQ chain must close against Y(z) and h must have
+ * degree < N - 1).  The proof is a deterministic function of (pk, X, W, r, s).
+ */
+size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk);
+int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64], int32_t* d_Y,
+               void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream);
+
 #ifdef __cplusplus
 }
 #endif

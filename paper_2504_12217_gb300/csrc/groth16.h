@@ -1,0 +1,89 @@
+// Proving / verifying key layout of the CRPC + PSQ Groth16 prover (internal).
+#pragma once
+#include <vector>
+
+#include "curve.cuh"
+#include "internal.h"
+#include "ntt.h"
+
+// Window widths of the fixed-base MSMs: int8 scalars take one signed 8-bit digit;
+// Y (int32) takes four; full Fr scalars take 32 digits of 8 bits (small queries and the
+// randomisation bases) or 16 digits of 16 bits (the H query).
+#define ZKVC_C_SMALL 8u
+#define ZKVC_W_I32 4u
+#define ZKVC_W_FULL8 32u
+#define ZKVC_C_H 16u
+#define ZKVC_W_H 16u
+
+namespace zkvc {
+
+// Regions of the G1 base array, in order.  Every entry stores nwin consecutive bases
+// 2^(c w) P (w < nwin) so that all windows of one MSM share one bucket set.
+enum G1Region : int {
+  R1_A0 = 0,   // A-query, variable 0 (the constant one)        1 entry
+  R1_AX,       // A-query, X variables                         a n
+  R1_AY,       // A-query, Y variables                         a b     x4 windows
+  R1_ALPHA,    // [alpha]1                                     1
+  R1_DELTA,    // [delta]1                                     1       x32 windows
+  R1_B,        // B-query in G1, W variables                   n b
+  R1_BETA,     // [beta]1                                      1
+  R1_LW,       // L-query, W variables                         n b
+  R1_LS,       // L-query, S variables (prefix sums)           n - 1   x32 windows
+  R1_H,        // H-query, bit-reversed positions              N       x16 windows (c = 16)
+  R1_COUNT
+};
+
+enum G2Region : int {
+  R2_B = 0,    // B-query in G2                                n b
+  R2_BETA,     // [beta]2                                      1
+  R2_DELTA,    // [delta]2                                     1       x32 windows
+  R2_GAMMA,    // [gamma]2 (verifying key only)                1
+  R2_COUNT
+};
+
+struct Region {
+  uint64_t off;    // first base
+  uint32_t count;  // entries
+  uint32_t nwin;   // windows per entry
+  uint32_t c;      // window bits
+  int32_t kind;    // G1Region / G2Region / IC
+};
+
+struct Shape {
+  int a = 0, n = 0, b = 0;
+  uint32_t l = 0;       // public inputs a n + a b
+  uint32_t n_vars = 0;  // 1 + l + n b + n - 1
+  uint32_t rows = 0;    // n + l + 1
+  uint32_t logN = 0;
+  size_t N = 0;
+};
+
+int make_shape(int a, int n, int b, Shape* s);
+
+struct Layout {
+  Region g1[R1_COUNT];
+  Region g2[R2_COUNT];
+  uint64_t n_g1 = 0, n_g2 = 0;
+};
+
+Layout make_layout(const Shape& s);
+
+}  // namespace zkvc
+
+struct zkvc_pk {
+  zkvc::Shape shape;
+  zkvc::Layout lay;
+  int device = 0;
+  zkvc::G1A* g1 = nullptr;   // device, Montgomery affine
+  zkvc::G2A* g2 = nullptr;
+  zkvc::Fr* zA = nullptr;    // z^(i b), i < a
+  zkvc::Fr* zB = nullptr;    // z^j, j < b
+  const zkvc::NttDomain* dom = nullptr;
+};
+
+struct zkvc_vk {
+  zkvc::Shape shape;
+  // canonical affine encodings (host)
+  std::vector<uint8_t> alpha1, beta2, gamma2, delta2;  // 64 / 128 / 128 / 128 bytes
+  std::vector<uint8_t> ic;                             // (l + 1) x 64 bytes
+};

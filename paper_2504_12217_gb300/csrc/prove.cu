@@ -1,0 +1,362 @@
+// Groth16 Prove for the CRPC + PSQ matmul circuit (zkVC Sec. II: Prove; Sec. III-A: CRPC;
+// Sec. III-B: PSQ), as one stream-ordered chain of kernels:
+//
+//  1. Y = X W exactly (int8 x int8 -> int32), the computation being proven.
+//  2. CRPC evaluations a_k = sum_i z^(ib) x_ik, b_k = sum_j z^j w_kj and
+//     Y(z) = sum_i z^(ib) sum_j z^j y_ij (block reductions of small-integer x Fr products).
+//  3. PSQ prefix sums S_k = S_(k-1) + a_k b_k (one-block scan); the closing constraint
+//     S_(n-2) + a_(n-1) b_(n-1) = Y(z) is checked on the device (ZKVC_EUNSAT otherwise).
+//  4. QAP evaluations on the domain: A_ev = (a_k | 1, X, Y), B_ev = (b_k), C_ev = (a_k b_k).
+//  5. h = (A B - C) / t via INTT (DIF, bit-reversed out, scaled by g^i / N), coset NTT
+//     (DIT back to natural order), pointwise division by g^N - 1, coset INTT (DIF, scaled
+//     by g^-i / N).  h stays in bit-reversed order; the H query is stored in that order.
+//     h at natural index N - 1 must vanish (checked).
+//  6. One merged G1 MSM with four outputs -- A (with [alpha]1 and r [delta]1 folded in as
+//     extra bases), B1 (with [beta]1 and s [delta]1), L (with -rs [delta]1) and H -- and
+//     one G2 MSM for B (with [beta]2 and s [delta]2).
+//  7. C = L + H + s A + r B1, affine conversion, canonical 256-byte encoding.
+#include <cstring>
+
+#include "groth16.h"
+#include "msm.h"
+
+namespace zkvc {
+
+// ------------------------------------------------------------------ witness
+__global__ void k_matmul_i8(const int8_t* __restrict__ X, const int8_t* __restrict__ W, int32_t* __restrict__ Y,
+                            int a, int n, int b) {
+  __shared__ int8_t xs[32][33];
+  __shared__ int8_t ws[32][33];
+  int tj = threadIdx.x, ti = threadIdx.y;  // 32 x 8 threads, 32 x 32 output tile
+  int j = blockIdx.x * 32 + tj;
+  int i0 = blockIdx.y * 32;
+  int32_t acc[4] = {0, 0, 0, 0};
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int r = ti; r < 32; r += 8) {
+      int xi = i0 + r, xk = k0 + tj;
+      xs[r][tj] = (xi < a && xk < n) ? X[size_t(xi) * n + xk] : 0;
+      int wk = k0 + r, wj = blockIdx.x * 32 + tj;
+      ws[r][tj] = (wk < n && wj < b) ? W[size_t(wk) * b + wj] : 0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; kk++) {
+      int32_t w = ws[kk][tj];
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc[q] += int32_t(xs[ti + 8 * q][kk]) * w;
+    }
+    __syncthreads();
+  }
+  for (int q = 0; q < 4; q++) {
+    int i = i0 + ti + 8 * q;
+    if (i < a && j < b) Y[size_t(i) * b + j] = acc[q];
+  }
+}
+
+// sum over the block of per-thread Fr values (blockDim.x = 256)
+__device__ Fr block_sum(Fr v, Fr* sh) {
+  st_field(sh + threadIdx.x, v);
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) st_field(sh + threadIdx.x, f_add(ld_field(sh + threadIdx.x), ld_field(sh + threadIdx.x + s)));
+    __syncthreads();
+  }
+  Fr r = ld_field(sh);
+  __syncthreads();
+  return r;
+}
+
+// block k < n: a_k and b_k
+__global__ void __launch_bounds__(256) k_crpc_ab(const int8_t* __restrict__ X, const int8_t* __restrict__ W,
+                                                 const Fr* __restrict__ zA, const Fr* __restrict__ zB, int a, int n, int b,
+                                                 Fr* ak, Fr* bk) {
+  __shared__ Fr sh[256];
+  int k = blockIdx.x;
+  Fr s = Fr::zero();
+  for (int i = threadIdx.x; i < a; i += blockDim.x)
+    s = f_add(s, f_mul(ld_field(zA + i), f_from_int<FrCfg>(X[size_t(i) * n + k])));
+  Fr av = block_sum(s, sh);
+  s = Fr::zero();
+  for (int j = threadIdx.x; j < b; j += blockDim.x)
+    s = f_add(s, f_mul(ld_field(zB + j), f_from_int<FrCfg>(W[size_t(k) * b + j])));
+  Fr bv = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    st_field(ak + k, av);
+    st_field(bk + k, bv);
+  }
+}
+
+// block i < a: z^(ib) sum_j z^j y_ij
+__global__ void __launch_bounds__(256) k_crpc_y(const int32_t* __restrict__ Y, const Fr* __restrict__ zA,
+                                                const Fr* __restrict__ zB, int b, Fr* part) {
+  __shared__ Fr sh[256];
+  int i = blockIdx.x;
+  Fr s = Fr::zero();
+  for (int j = threadIdx.x; j < b; j += blockDim.x)
+    s = f_add(s, f_mul(ld_field(zB + j), f_from_int<FrCfg>(Y[size_t(i) * b + j])));
+  Fr v = block_sum(s, sh);
+  if (threadIdx.x == 0) st_field(part + i, f_mul(v, ld_field(zA + i)));
+}
+
+// One block of 1024 threads: c_k = a_k b_k, S_k = c_0 + ... + c_k (k <= n - 2), the
+// closing check against Y(z), and the first n domain evaluations.
+__global__ void __launch_bounds__(1024) k_psq(const Fr* __restrict__ ak, const Fr* __restrict__ bk,
+                                              const Fr* __restrict__ ypart, int a, int n, Fr* S, Fr* Aev, Fr* Bev,
+                                              Fr* Cev, int* flags) {
+  __shared__ Fr sh[1024];
+  const int T = blockDim.x;
+  const int per = (n + T - 1) / T;
+  const int k0 = threadIdx.x * per;
+  Fr local = Fr::zero();
+  for (int k = k0; k < k0 + per && k < n; k++) {
+    Fr a_ = ld_field(ak + k), b_ = ld_field(bk + k);
+    Fr c = f_mul(a_, b_);
+    st_field(Aev + k, a_);
+    st_field(Bev + k, b_);
+    st_field(Cev + k, c);
+    local = f_add(local, c);
+  }
+  // inclusive scan of the per-thread sums (Hillis-Steele)
+  st_field(sh + threadIdx.x, local);
+  __syncthreads();
+  for (int d = 1; d < T; d <<= 1) {
+    Fr v = ld_field(sh + threadIdx.x);
+    if ((int)threadIdx.x >= d) v = f_add(v, ld_field(sh + threadIdx.x - d));
+    __syncthreads();
+    st_field(sh + threadIdx.x, v);
+    __syncthreads();
+  }
+  Fr run = threadIdx.x ? ld_field(sh + threadIdx.x - 1) : Fr::zero();
+  for (int k = k0; k < k0 + per && k < n; k++) {
+    run = f_add(run, f_mul(ld_field(ak + k), ld_field(bk + k)));
+    if (k < n - 1) st_field(S + k, run);
+  }
+  if (threadIdx.x == 0) {
+    Fr total = ld_field(sh + T - 1);  // S_(n-2) + c_(n-1)
+    Fr yz = Fr::zero();
+    for (int i = 0; i < a; i++) yz = f_add(yz, ld_field(ypart + i));
+    if (total != yz) atomicOr(flags, 1);
+  }
+}
+
+// domain rows n .. N-1: A_ev[n + v] = w_v for v = 0 .. l (one, X, Y), zeros elsewhere
+__global__ void k_domain_rest(const int8_t* __restrict__ X, const int32_t* __restrict__ Y, int n, uint32_t an,
+                              uint32_t l, size_t N, Fr* Aev, Fr* Bev, Fr* Cev) {
+  size_t k = n + size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  size_t v = k - n;
+  Fr w = Fr::zero();
+  if (v == 0)
+    w = Fr::one();
+  else if (v <= an)
+    w = f_from_int<FrCfg>(X[v - 1]);
+  else if (v <= l)
+    w = f_from_int<FrCfg>(Y[v - 1 - an]);
+  st_field(Aev + k, w);
+  st_field(Bev + k, Fr::zero());
+  st_field(Cev + k, Fr::zero());
+}
+
+__global__ void k_check_h(const Fr* H, size_t N, int* flags) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && !ld_field(H + (N - 1)).is_zero()) atomicOr(flags, 2);
+}
+
+__device__ __forceinline__ bool canonical_fr(const Fr& x) {
+  for (int i = 7; i >= 0; i--) {
+    uint32_t m = mod_limb<FrCfg>(i);
+    if (x.v[i] != m) return x.v[i] < m;
+  }
+  return false;
+}
+
+// rs[0] = r, rs[1] = s (canonical, from the caller); rs[2] = -r s (canonical)
+__global__ void k_randomness(Fr* rs, int* flags) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Fr r = ld_field(rs), s = ld_field(rs + 1);
+  if (!canonical_fr(r) || !canonical_fr(s)) atomicOr(flags, 4);
+  Fr prod = f_mul(f_to_mont(r), s);  // r s (canonical)
+  st_field(rs + 2, f_neg(prod));
+}
+
+__device__ __forceinline__ void write_canon(uint8_t* out, const Fp& x) {
+  Fp c = f_from_mont(x);
+  for (int i = 0; i < 8; i++) {
+    out[4 * i] = (uint8_t)c.v[i];
+    out[4 * i + 1] = (uint8_t)(c.v[i] >> 8);
+    out[4 * i + 2] = (uint8_t)(c.v[i] >> 16);
+    out[4 * i + 3] = (uint8_t)(c.v[i] >> 24);
+  }
+}
+
+// C = L + H + s A + r B1 (joint double-and-add over the bits of s and r), then the
+// proof encoding A || B || C.
+__global__ void k_combine(const G1J* res1, const G2J* res2, const Fr* rs, uint8_t* proof) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  G1J A = ld_field(res1 + 0), B1 = ld_field(res1 + 1), L = ld_field(res1 + 2), H = ld_field(res1 + 3);
+  Fr r = ld_field(rs), s = ld_field(rs + 1);
+  G1J AB = p_add(A, B1);
+  G1J acc = G1J::inf();
+  for (int i = 7; i >= 0; i--) {
+    for (int bit = 31; bit >= 0; bit--) {
+      acc = p_dbl(acc);
+      uint32_t sb = (s.v[i] >> bit) & 1u, rb = (r.v[i] >> bit) & 1u;
+      if (sb && rb) acc = p_add(acc, AB);
+      else if (sb) acc = p_add(acc, A);
+      else if (rb) acc = p_add(acc, B1);
+    }
+  }
+  G1J C = p_add(p_add(L, H), acc);
+  G1A a = p_to_affine(A), c = p_to_affine(C);
+  G2A bb = p_to_affine(ld_field(res2));
+  write_canon(proof + 0, a.x);
+  write_canon(proof + 32, a.y);
+  write_canon(proof + 64, bb.x.c0);
+  write_canon(proof + 96, bb.x.c1);
+  write_canon(proof + 128, bb.y.c0);
+  write_canon(proof + 160, bb.y.c1);
+  write_canon(proof + 192, c.x);
+  write_canon(proof + 224, c.y);
+}
+
+// ------------------------------------------------------------------ plans and workspace
+struct ProveBufs {
+  Fr *ak, *bk, *yz, *S, *ev, *rs;
+  int* flags;
+  G1J* res1;
+  G2J* res2;
+  uint8_t* proof;
+  void* ws1;
+  size_t ws1_bytes;
+  void* ws2;
+  size_t ws2_bytes;
+};
+
+static void plans(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const int32_t* dY, const Fr* S, const Fr* h,
+                  const Fr* rs, MsmPlan* p1, MsmPlan* p2) {
+  const Shape& sh = pk->shape;
+  const Region* g = pk->lay.g1;
+  const uint32_t an = sh.a * sh.n, ab = sh.a * sh.b, nb = sh.n * sh.b;
+  const uint32_t NONE = 0xffffffffu;
+  p1->outs = {{ZKVC_C_SMALL, 1, 0, 0}, {ZKVC_C_SMALL, 1, 0, 0}, {ZKVC_C_SMALL, 1, 0, 0}, {ZKVC_C_H, 1, 0, 0}};
+  auto seg = [&](const Region& r, uint32_t count, uint32_t out, int kind, const void* sc, uint32_t skip = 0xffffffffu) {
+    MsmSeg s{};
+    s.base_off = r.off;
+    s.count = count;
+    s.nwin = r.nwin;
+    s.out = out;
+    s.kind = kind;
+    s.scalars = sc;
+    s.skip = skip;
+    return s;
+  };
+  p1->segs = {
+      seg(g[R1_A0], 1, 0, SK_ONE, nullptr),
+      seg(g[R1_AX], an, 0, SK_I8, dX),
+      seg(g[R1_AY], ab, 0, SK_I32, dY),
+      seg(g[R1_ALPHA], 1, 0, SK_ONE, nullptr),
+      seg(g[R1_DELTA], 1, 0, SK_FR_CANON, rs + 0),
+      seg(g[R1_B], nb, 1, SK_I8, dW),
+      seg(g[R1_BETA], 1, 1, SK_ONE, nullptr),
+      seg(g[R1_DELTA], 1, 1, SK_FR_CANON, rs + 1),
+      seg(g[R1_LW], nb, 2, SK_I8, dW),
+      seg(g[R1_LS], (uint32_t)(sh.n - 1), 2, SK_FR_MONT, S),
+      seg(g[R1_DELTA], 1, 2, SK_FR_CANON, rs + 2),
+      seg(g[R1_H], (uint32_t)sh.N, 3, SK_FR_MONT, h, (uint32_t)sh.N - 1),
+  };
+  (void)NONE;
+  const Region* g2 = pk->lay.g2;
+  p2->outs = {{ZKVC_C_SMALL, 1, 0, 0}};
+  p2->segs = {
+      seg(g2[R2_B], nb, 0, SK_I8, dW),
+      seg(g2[R2_BETA], 1, 0, SK_ONE, nullptr),
+      seg(g2[R2_DELTA], 1, 0, SK_FR_CANON, rs + 1),
+  };
+  msm_plan_finalize(*p1);
+  msm_plan_finalize(*p2);
+}
+
+static size_t carve(const zkvc_pk* pk, void* base, size_t cap, ProveBufs* B, bool measuring) {
+  const Shape& sh = pk->shape;
+  Arena a;
+  a.base = reinterpret_cast<uint8_t*>(base);
+  a.cap = cap;
+  a.measuring = measuring;
+  B->ak = a.take<Fr>(sh.n);
+  B->bk = a.take<Fr>(sh.n);
+  B->yz = a.take<Fr>(sh.a);
+  B->S = a.take<Fr>(sh.n);
+  B->ev = a.take<Fr>(4 * sh.N);
+  B->rs = a.take<Fr>(4);
+  B->flags = a.take<int>(4);
+  B->res1 = a.take<G1J>(4);
+  B->res2 = a.take<G2J>(1);
+  B->proof = a.take<uint8_t>(256);
+  MsmPlan p1, p2;
+  plans(pk, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &p1, &p2);
+  B->ws1_bytes = msm_workspace_bytes<Fp>(p1);
+  B->ws2_bytes = msm_workspace_bytes<Fp2>(p2);
+  B->ws1 = a.take<uint8_t>(B->ws1_bytes);
+  B->ws2 = a.take<uint8_t>(B->ws2_bytes);
+  return a.off;
+}
+
+size_t prove_workspace_bytes(const zkvc_pk* pk) {
+  ProveBufs B;
+  return carve(pk, nullptr, 0, &B, true);
+}
+
+int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host, int32_t* dY, void* ws,
+               size_t ws_bytes, uint8_t* proof_host, cudaStream_t st) {
+  ZK_CHECK(pk && dX && dW && rs_host && dY && ws && proof_host, ZKVC_EINVAL, "prove: null argument");
+  size_t need = prove_workspace_bytes(pk);
+  ZK_CHECK(ws_bytes >= need, ZKVC_EINVAL, "prove: workspace %zu < %zu bytes", ws_bytes, need);
+  const Shape& sh = pk->shape;
+  ProveBufs B;
+  carve(pk, ws, ws_bytes, &B, false);
+  const size_t N = sh.N;
+  Fr* Aev = B.ev;
+  Fr* Bev = B.ev + N;
+  Fr* Cev = B.ev + 2 * N;
+  Fr* Hev = B.ev + 3 * N;
+
+  ZK_CUDA(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), st));
+  ZK_CUDA(cudaMemcpyAsync(B.rs, rs_host, 64, cudaMemcpyHostToDevice, st));
+  k_randomness<<<1, 1, 0, st>>>(B.rs, B.flags);
+  // 1. Y = X W
+  dim3 mg((sh.b + 31) / 32, (sh.a + 31) / 32);
+  k_matmul_i8<<<mg, dim3(32, 8), 0, st>>>(dX, dW, dY, sh.a, sh.n, sh.b);
+  // 2-3. CRPC evaluations and PSQ prefix sums
+  k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk);
+  k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz);
+  k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, B.S, Aev, Bev, Cev, B.flags);
+  // 4. remaining domain evaluations
+  size_t rest = N - sh.n;
+  k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev);
+  ZK_CUDA(cudaGetLastError());
+  // 5. quotient
+  const NttDomain* d = pk->dom;
+  ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, st));
+  ZK_TRY(ntt_dit(Aev, 3, N, d, false, st));
+  ZK_TRY(ntt_quotient(Aev, Bev, Cev, Hev, d, st));
+  ZK_TRY(ntt_dif(Hev, 1, N, d, true, SC_NONE, SC_NGI, false, st));
+  k_check_h<<<1, 32, 0, st>>>(Hev, N, B.flags);
+  ZK_CUDA(cudaGetLastError());
+  // 6. MSMs
+  MsmPlan p1, p2;
+  plans(pk, dX, dW, dY, B.S, Hev, B.rs, &p1, &p2);
+  ZK_TRY(msm_run<Fp>(p1, pk->g1, B.ws1, B.ws1_bytes, B.res1, st));
+  ZK_TRY(msm_run<Fp2>(p2, pk->g2, B.ws2, B.ws2_bytes, B.res2, st));
+  // 7. combine and encode
+  k_combine<<<1, 32, 0, st>>>(B.res1, B.res2, B.rs, B.proof);
+  ZK_CUDA(cudaGetLastError());
+  int flags = 0;
+  ZK_CUDA(cudaMemcpyAsync(proof_host, B.proof, 256, cudaMemcpyDeviceToHost, st));
+  ZK_CUDA(cudaMemcpyAsync(&flags, B.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ZK_CUDA(cudaStreamSynchronize(st));
+  ZK_CHECK(!(flags & 4), ZKVC_EINVAL, "prove: r or s is not a canonical Fr element");
+  ZK_CHECK(!(flags & 1), ZKVC_EUNSAT, "prove: the PSQ chain does not close against Y(z)");
+  ZK_CHECK(!(flags & 2), ZKVC_EUNSAT, "prove: the quotient has degree N - 1 (QAP not satisfied)");
+  return ZKVC_OK;
+}
+
+}  // namespace zkvc

@@ -40,7 +40,22 @@ SIGNATURES = {
     "zkvc_msm_workspace_bytes": (_c_sz, [_c_sz, _c_int]),
     "zkvc_msm_g1": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_msm_g2": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
+    "zkvc_setup": (_c_int, [_c_int, _c_int, _c_int, _c_p, _c_p, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p)]),
+    "zkvc_pk_free": (None, [_c_p]),
+    "zkvc_vk_free": (None, [_c_p]),
+    "zkvc_pk_info": (_c_int, [_c_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                              ctypes.POINTER(_c_u32), ctypes.POINTER(_c_sz), ctypes.POINTER(_c_sz)]),
+    "zkvc_pk_export": (_c_int, [_c_p, _c_int, _c_sz, _c_sz, _c_p]),
+    "zkvc_vk_export": (_c_int, [_c_p, _c_int, _c_sz, _c_sz, _c_p]),
+    "zkvc_prove_workspace_bytes": (_c_sz, [_c_p]),
+    "zkvc_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
 }
+
+ZKVC_Q_A, ZKVC_Q_B1, ZKVC_Q_B2, ZKVC_Q_L, ZKVC_Q_H = 0, 1, 2, 3, 4
+ZKVC_Q_ALPHA1, ZKVC_Q_BETA1, ZKVC_Q_BETA2, ZKVC_Q_DELTA1, ZKVC_Q_DELTA2 = 5, 6, 7, 8, 9
+ZKVC_VK_IC, ZKVC_VK_ALPHA1, ZKVC_VK_BETA2, ZKVC_VK_GAMMA2, ZKVC_VK_DELTA2 = 0, 1, 2, 3, 4
+_G2_QUERIES = {ZKVC_Q_B2, ZKVC_Q_BETA2, ZKVC_Q_DELTA2}
+_G2_VK = {ZKVC_VK_BETA2, ZKVC_VK_GAMMA2, ZKVC_VK_DELTA2}
 
 
 class ZkvcError(RuntimeError):
@@ -165,3 +180,91 @@ def zkvc_msm_g1(points, scalars, workspace=None):
 def zkvc_msm_g2(points, scalars, workspace=None):
     """sum_i s_i Q_i over G2: points [n, 128], scalars [n, 32]; returns 128 bytes."""
     return _msm("zkvc_msm_g2", 2, points, scalars, workspace)
+
+
+# ------------------------------------------------------------------ Groth16 layer
+class ProvingKey:
+    """Owns a zkvc_pk handle (device-resident proving key); freed with the object."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        info = zkvc_pk_info(self)
+        self.shape = (info["a"], info["n"], info["b"])
+        self.log_domain = info["log_domain"]
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.zkvc_pk_free(self.handle)
+            self.handle = None
+
+
+class VerifyingKey:
+    """Owns a zkvc_vk handle (host memory)."""
+
+    def __init__(self, handle, shape):
+        self.handle = handle
+        self.shape = shape
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.zkvc_vk_free(self.handle)
+            self.handle = None
+
+
+def zkvc_setup(a, n, b, toxic):
+    """Gen for the (a, n, b) matmul circuit; toxic: 192 bytes (tau, alpha, beta, gamma,
+    delta, z canonical little-endian).  Returns (ProvingKey, VerifyingKey)."""
+    if len(toxic) != 192:
+        raise ValueError("toxic must be 192 bytes")
+    pk, vk = _c_p(), _c_p()
+    buf = ctypes.create_string_buffer(bytes(toxic), 192)
+    check(lib().zkvc_setup(a, n, b, buf, _stream(), ctypes.byref(pk), ctypes.byref(vk)))
+    return ProvingKey(pk), VerifyingKey(vk, (a, n, b))
+
+
+def zkvc_pk_info(pk):
+    a, n, b = _c_int(), _c_int(), _c_int()
+    logd, g1, g2 = _c_u32(), _c_sz(), _c_sz()
+    check(lib().zkvc_pk_info(pk.handle, ctypes.byref(a), ctypes.byref(n), ctypes.byref(b), ctypes.byref(logd),
+                             ctypes.byref(g1), ctypes.byref(g2)))
+    return {"a": a.value, "n": n.value, "b": b.value, "log_domain": logd.value, "g1_bases": g1.value,
+            "g2_bases": g2.value}
+
+
+def zkvc_pk_export(pk, query, start, count):
+    width = 128 if query in _G2_QUERIES else 64
+    out = ctypes.create_string_buffer(max(1, width * count))
+    check(lib().zkvc_pk_export(pk.handle, query, start, count, out))
+    return out.raw[: width * count]
+
+
+def zkvc_vk_export(vk, query, start, count):
+    width = 128 if query in _G2_VK else 64
+    out = ctypes.create_string_buffer(max(1, width * count))
+    check(lib().zkvc_vk_export(vk.handle, query, start, count, out))
+    return out.raw[: width * count]
+
+
+def zkvc_prove_workspace_bytes(pk):
+    return lib().zkvc_prove_workspace_bytes(pk.handle)
+
+
+def zkvc_prove(pk, X, W, rs, Y=None, workspace=None):
+    """Prove Y = X W.  X: [a, n] int8 CUDA tensor, W: [n, b] int8, rs: 64 bytes (r || s).
+    Returns (proof bytes, Y as an [a, b] int32 CUDA tensor)."""
+    torch = _torch()
+    a, n, b = pk.shape
+    if X.dtype != torch.int8 or tuple(X.shape) != (a, n) or W.dtype != torch.int8 or tuple(W.shape) != (n, b):
+        raise ValueError(f"expected X int8 [{a}, {n}] and W int8 [{n}, {b}]")
+    if len(rs) != 64:
+        raise ValueError("rs must be 64 bytes")
+    if Y is None:
+        Y = torch.empty((a, b), dtype=torch.int32, device=X.device)
+    need = zkvc_prove_workspace_bytes(pk)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=X.device)
+    proof = ctypes.create_string_buffer(256)
+    rsb = ctypes.create_string_buffer(bytes(rs), 64)
+    check(lib().zkvc_prove(pk.handle, _dev_ptr(X), _dev_ptr(W), rsb, _dev_ptr(Y), _dev_ptr(workspace),
+                           workspace.numel(), proof, _stream()))
+    return proof.raw, Y

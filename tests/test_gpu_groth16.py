@@ -1,0 +1,147 @@
+"""GPU parity of Groth16 setup and prove for the CRPC + PSQ circuit against the oracle.
+
+Keys and proofs are compared byte for byte (field and group results are exact).  Small
+shapes compare every key entry and the naive oracle proof; the full [49,320]x[320,512]
+workload compares the proof with the oracle's closed-form proof (computed from the toxic
+waste in the exponent) and sampled key entries, each computed one by one."""
+import random
+
+import numpy as np
+import pytest
+
+from oracle import bn254 as bn
+from oracle import crpc, groth16 as og
+from paper_2504_12217_gb300 import inputs
+from tests import _util
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nv():
+    import torch
+    assert torch.cuda.is_available()
+    return _util.native()
+
+
+def _mats(X, W):
+    return X.astype(int).tolist(), W.astype(int).tolist()
+
+
+def _gpu_prove(nv, pk, X, W, rs):
+    import torch
+    proof, Y = nv.zkvc_prove(pk, torch.from_numpy(X).cuda(), torch.from_numpy(W).cuda(), rs)
+    return proof, Y.cpu().numpy()
+
+
+def _check_keys(nv, pk, vk, opk, ovk, sh):
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_A, 0, len(opk.A)) == b"".join(bn.g1_bytes(p) for p in opk.A)
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_B1, 0, len(opk.B1)) == b"".join(bn.g1_bytes(p) for p in opk.B1)
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_B2, 0, len(opk.B2)) == b"".join(bn.g2_bytes(p) for p in opk.B2)
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_L, 0, len(opk.L)) == b"".join(bn.g1_bytes(p) for p in opk.L)
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_H, 0, len(opk.H)) == b"".join(bn.g1_bytes(p) for p in opk.H)
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_ALPHA1, 0, 1) == bn.g1_bytes(opk.alpha1)
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_BETA1, 0, 1) == bn.g1_bytes(opk.beta1)
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_BETA2, 0, 1) == bn.g2_bytes(opk.beta2)
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_DELTA1, 0, 1) == bn.g1_bytes(opk.delta1)
+    assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_DELTA2, 0, 1) == bn.g2_bytes(opk.delta2)
+    assert nv.zkvc_vk_export(vk, nv.ZKVC_VK_IC, 0, len(ovk.IC)) == b"".join(bn.g1_bytes(p) for p in ovk.IC)
+    assert nv.zkvc_vk_export(vk, nv.ZKVC_VK_GAMMA2, 0, 1) == bn.g2_bytes(ovk.gamma2)
+    assert nv.zkvc_vk_export(vk, nv.ZKVC_VK_ALPHA1, 0, 1) == bn.g1_bytes(ovk.alpha1)
+    assert nv.zkvc_vk_export(vk, nv.ZKVC_VK_BETA2, 0, 1) == bn.g2_bytes(ovk.beta2)
+    assert nv.zkvc_vk_export(vk, nv.ZKVC_VK_DELTA2, 0, 1) == bn.g2_bytes(ovk.delta2)
+
+
+def test_config1_keys_and_proof(nv):
+    """[4,16] x [16,8]: every key entry and the proof equal the oracle's."""
+    seed = inputs.SEED_CFG[1]
+    a, n, b = inputs.SHAPE_CFG1
+    inst = inputs.instance(seed, (a, n, b))
+    toxic, rs = inst["toxic"], inst["rs"]
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(toxic))
+    sh = crpc.Shape(a, n, b)
+    assert pk.log_domain == 7
+    opk, ovk = og.setup(sh, toxic)
+    _check_keys(nv, pk, vk, opk, ovk, sh)
+    proof, Y = _gpu_prove(nv, pk, inst["X"], inst["W"], inputs.to_bytes32(rs))
+    assert np.array_equal(Y, inst["X"].astype(np.int64) @ inst["W"].astype(np.int64))
+    X, W = _mats(inst["X"], inst["W"])
+    oproof, _, _ = og.prove(opk, X, W, *rs)
+    assert proof == og.proof_bytes(oproof)
+    assert og.verify(ovk, X, Y.tolist(), og.proof_from_bytes(proof))
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 1, 3), (1, 5, 1), (3, 2, 2), (5, 7, 3), (2, 33, 40)])
+def test_small_shapes_keys_and_proof(nv, shape):
+    a, n, b = shape
+    seed = 1000 + a * 100 + n * 10 + b
+    inst = inputs.instance(seed, shape)
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(inst["toxic"]))
+    opk, ovk = og.setup(crpc.Shape(a, n, b), inst["toxic"])
+    _check_keys(nv, pk, vk, opk, ovk, crpc.Shape(a, n, b))
+    X, W = _mats(inst["X"], inst["W"])
+    for rs in (inst["rs"], [0, 0], [bn.R - 1, 1]):
+        proof, Y = _gpu_prove(nv, pk, inst["X"], inst["W"], inputs.to_bytes32(rs))
+        oproof, oY, _ = og.prove(opk, X, W, *rs)
+        assert Y.tolist() == oY
+        assert proof == og.proof_bytes(oproof), rs
+
+
+def test_extreme_matrices(nv):
+    """All -128 entries give the largest |y| (n 2^14) and one bucket per MSM."""
+    a, n, b = 3, 40, 5
+    inst = inputs.instance(77, (a, n, b))
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(inst["toxic"]))
+    sh = crpc.Shape(a, n, b)
+    for fill in (-128, 127, 0):
+        X = np.full((a, n), fill, dtype=np.int8)
+        W = np.full((n, b), fill, dtype=np.int8)
+        proof, Y = _gpu_prove(nv, pk, X, W, inputs.to_bytes32(inst["rs"]))
+        cf, _ = og.closed_form_proof(sh, inst["toxic"], X.astype(int).tolist(), W.astype(int).tolist(), *inst["rs"])
+        assert proof == og.proof_bytes(cf), fill
+
+
+def test_config2_full_size(nv):
+    """[49,320] x [320,512] (N = 2^16): proof equals the closed-form proof; key entries
+    sampled across every query equal [scalar]G computed one by one."""
+    a, n, b = inputs.SHAPE_CFG2
+    inst = inputs.instance(inputs.SEED_CFG[2], (a, n, b))
+    toxic, rs = inst["toxic"], inst["rs"]
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(toxic))
+    assert pk.log_domain == 16
+    proof, Y = _gpu_prove(nv, pk, inst["X"], inst["W"], inputs.to_bytes32(rs))
+    assert np.array_equal(Y, inst["X"].astype(np.int64) @ inst["W"].astype(np.int64))
+    sh = crpc.Shape(a, n, b)
+    X, W = _mats(inst["X"], inst["W"])
+    cf, _ = og.closed_form_proof(sh, toxic, X, W, *rs)
+    assert proof == og.proof_bytes(cf)
+    rng = random.Random(2)
+    sizes = {"A": sh.n_public + 1, "B": n * b, "L": n * b + n - 1, "H": sh.domain - 1, "IC": sh.n_public + 1}
+    qids = {"A": nv.ZKVC_Q_A, "B": nv.ZKVC_Q_B1, "L": nv.ZKVC_Q_L, "H": nv.ZKVC_Q_H}
+    for q, size in sizes.items():
+        idx = sorted(set([0, size - 1] + [rng.randrange(size) for _ in range(6)]))
+        scal = og.pk_entry_scalars(sh, toxic, q, idx)
+        for i, s in zip(idx, scal):
+            if q == "IC":
+                got = nv.zkvc_vk_export(vk, nv.ZKVC_VK_IC, i, 1)
+            else:
+                got = nv.zkvc_pk_export(pk, qids[q], i, 1)
+            assert got == bn.g1_bytes(bn.g1_mul(bn.G1_GEN, s)), (q, i)
+            if q == "B":
+                assert nv.zkvc_pk_export(pk, nv.ZKVC_Q_B2, i, 1) == bn.g2_bytes(bn.g2_mul(bn.G2_GEN, s))
+
+
+def test_rejected_inputs(nv):
+    a, n, b = 2, 3, 2
+    inst = inputs.instance(5, (a, n, b))
+    good = list(inst["toxic"])
+    for bad in ([bn.R] + good[1:], good[:1] + [0] + good[2:], good[:5] + [1], good[:5] + [0]):
+        with pytest.raises(nv.ZkvcError) as e:
+            nv.zkvc_setup(a, n, b, inputs.to_bytes32(bad))
+        assert e.value.code == nv.ZKVC_EINVAL
+    with pytest.raises(nv.ZkvcError):
+        nv.zkvc_setup(0, 3, 2, inputs.to_bytes32(good))
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(good))
+    with pytest.raises(nv.ZkvcError) as e:
+        _gpu_prove(nv, pk, inst["X"], inst["W"], inputs.to_bytes32([bn.R, 1]))
+    assert e.value.code == nv.ZKVC_EINVAL
