@@ -1,0 +1,356 @@
+"""Benchmark: CRPC-matmul Groth16 proofs/s (BN254) with p50/p99 latency on GB300.
+
+Workload: one Groth16 proof of the CRPC + PSQ circuit for Y = X W with X int8 [49, 320]
+and W int8 [320, 512] (entries uniform in [-128, 127], seeded SplitMix64; setup toxic
+waste and prover (r, s) seeded the same way).  A step is one full prove: witness, CRPC
+and PSQ evaluation, the NTT chain to h(x), every MSM, and the proof encoding.
+
+* ``value``   proofs/s over the timed steps, inputs resident in HBM (device-timed with
+              CUDA events on the prover's stream; L2 flushed by a 256 MiB write between
+              steps, outside the events).
+* ``e2e``     the same metric through the public API with pinned host inputs: every
+              step copies X and W host->device and reads Y and the proof back.
+* ``roofline`` the bucket-accumulation kernel (the dominant kernel), timed live with CUDA
+              events on its stream; its algorithmic work is one mixed point addition per
+              bucket term (10 Montgomery products of 264 32-bit IMADs in G1).
+* ``cpu_baseline`` the oracle (tests' reference implementation) on a bounded sample of
+              the same workload, extrapolated to one proof.
+
+With ``--gpus N`` under torchrun every rank proves its own instances (replicas: proofs
+are independent, no collective on the data path); value = all proofs / max rank time.
+``--impl reference`` times the oracle instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CRPC-matmul Groth16 proofs/s + p50/p99 latency; MSM/NTT % of roofline"
+UNIT = "proofs/s"
+SHAPE = (49, 320, 512)
+SMS = 152
+IMAD_PER_CLK_SM = 64          # 32-bit integer multiply-add issue rate per SM per clock
+SM_MAX_MHZ = 2070.0
+MONT_IMAD = 4 * 8 * 8 + 8     # CIOS product on 8 x 32-bit limbs
+G1_MADD_PRODUCTS = 10         # madd-2008-s: 8M + 2S
+G2_MADD_PRODUCTS = 30         # the same over Fp2, 3 Fp products per Fp2 product
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle baseline
+def oracle_sample(seed, frac=1.0):
+    """Time the oracle on a bounded sample of one proof and extrapolate to the whole proof.
+
+    Sample: matmul on 2 of the 49 rows; CRPC evaluations in full; one textbook NTT of
+    2^14 points scaled to the seven 2^16-point transforms by N log N; naive scalar
+    multiplications on 64 points of each scalar type (int8 X/W, int32 Y, full Fr S/h, G2
+    int8) scaled by the term counts of each query.  Returns (seconds per proof, details).
+    """
+    import random
+
+    from oracle import bn254 as bn
+    from oracle import crpc
+    from oracle import ntt as ont
+    from paper_2504_12217_gb300 import inputs
+
+    a, n, b = SHAPE
+    inst = inputs.instance(seed, SHAPE)
+    X = inst["X"].astype(int).tolist()
+    W = inst["W"].astype(int).tolist()
+    z = inst["toxic"][5]
+    rng = random.Random(seed)
+    parts = {}
+    m = max(8, int(64 * frac))
+
+    t = time.perf_counter()
+    rows = 2
+    crpc.matmul_int(X[:rows], W)
+    parts["matmul"] = (time.perf_counter() - t) * a / rows
+
+    t = time.perf_counter()
+    crpc.crpc_evaluations(X, W, z)
+    parts["crpc_eval"] = time.perf_counter() - t
+
+    N = 1 << 16
+    ns = 1 << 14
+    vec = [rng.randrange(bn.R) for _ in range(ns)]
+    t = time.perf_counter()
+    ont.ntt(vec)
+    parts["ntt"] = (time.perf_counter() - t) * 7 * (N * 16) / (ns * 14)
+
+    P1 = bn.g1_mul(bn.G1_GEN, rng.randrange(1, bn.R))
+    P2 = bn.g2_mul(bn.G2_GEN, rng.randrange(1, bn.R))
+
+    def per_op(fn, scalars):
+        t0 = time.perf_counter()
+        for s in scalars:
+            fn(s)
+        return (time.perf_counter() - t0) / len(scalars)
+
+    i8 = [bn.fr_from_int(rng.randint(-128, 127)) for _ in range(m)]
+    i32 = [bn.fr_from_int(rng.randint(-(1 << 22), 1 << 22)) for _ in range(m)]
+    full = [rng.randrange(bn.R) for _ in range(m)]
+    c_i8 = per_op(lambda s: bn.g1_mul(P1, s), i8)
+    c_i32 = per_op(lambda s: bn.g1_mul(P1, s), i32)
+    c_full = per_op(lambda s: bn.g1_mul(P1, s), full)
+    c_g2_i8 = per_op(lambda s: bn.g2_mul(P2, s), i8)
+    c_g2_full = per_op(lambda s: bn.g2_mul(P2, s), full[: max(4, m // 8)])
+    an, ab, nb = a * n, a * b, n * b
+    parts["msm_A"] = c_i8 * an + c_i32 * ab + c_full
+    parts["msm_B1"] = c_i8 * nb + c_full
+    parts["msm_B2"] = c_g2_i8 * nb + c_g2_full
+    parts["msm_L"] = c_i8 * nb + c_full * (n - 1)
+    parts["msm_H"] = c_full * (N - 1)
+    parts["randomisation"] = c_full * 4
+    total = sum(parts.values())
+    return total, parts
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from paper_2504_12217_gb300 import inputs
+    seed = inputs.SEED_CFG[2]
+    for _ in range(args.warmup):
+        oracle_sample(seed, frac=0.25)
+    times = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sec, _ = oracle_sample(seed, frac=0.25)
+        times.append(sec)
+    wall = time.perf_counter() - t0
+    per_proof = statistics.median(times)
+    value = 1.0 / per_proof
+    sample = ("per step: matmul on 2 of 49 rows, full CRPC evaluations, one 2^14-point textbook NTT "
+              "scaled to seven 2^16 transforms, 16 naive scalar multiplications per scalar type scaled "
+              "by each query's term count; extrapolated to one [49,320]x[320,512] proof")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_proof * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "python-int (exact)", "data": "synthetic",
+        "config": {"workload": "crpc_groth16_bn254_49x320x512", "a": SHAPE[0], "n": SHAPE[1], "b": SHAPE[2],
+                   "log_domain": 16},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "wall_s": wall},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+
+    from paper_2504_12217_gb300 import inputs
+    from paper_2504_12217_gb300 import native as nv
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    a, n, b = SHAPE
+    seed = inputs.SEED_CFG[2] + rank
+    inst = inputs.instance(seed, SHAPE)
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(inst["toxic"]))
+    Xd = torch.from_numpy(inst["X"]).cuda()
+    Wd = torch.from_numpy(inst["W"]).cuda()
+    Yd = torch.empty((a, b), dtype=torch.int32, device="cuda")
+    ws = torch.empty(nv.zkvc_prove_workspace_bytes(pk), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    total_steps = args.warmup + args.steps
+    rs_list = [inputs.to_bytes32(inputs.prover_values(seed * 1000 + i)) for i in range(total_steps)]
+
+    for i in range(args.warmup):
+        nv.zkvc_prove(pk, Xd, Wd, rs_list[i], Y=Yd, workspace=ws)
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps, inputs resident
+    nv.zkvc_profile_enable(True)
+    launches0 = nv.zkvc_kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record()
+        nv.zkvc_prove(pk, Xd, Wd, rs_list[args.warmup + i], Y=Yd, workspace=ws)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    launches = nv.zkvc_kernel_launches() - launches0
+    prof = nv.zkvc_profile_read()
+    nv.zkvc_profile_enable(False)
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+
+    # ---- end to end through the public API: pinned host inputs, results read back
+    Xh = torch.from_numpy(inst["X"]).pin_memory()
+    Wh = torch.from_numpy(inst["W"]).pin_memory()
+    Yh = torch.empty((a, b), dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, args.steps)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        Xd.copy_(Xh, non_blocking=True)
+        Wd.copy_(Wh, non_blocking=True)
+        proof, _ = nv.zkvc_prove(pk, Xd, Wd, rs_list[i % total_steps], Y=Yd, workspace=ws)
+        Yh.copy_(Yd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": a * n + n * b,
+           "d2h_bytes_per_step": 256 + 4 * a * b}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (bucket accumulation), timed live
+    g1 = prof.get("msm_g1_bucket_accum", {"ms": 0, "units": 0, "calls": 0})
+    g2 = prof.get("msm_g2_bucket_accum", {"ms": 0, "units": 0, "calls": 0})
+    w1 = g1["units"] * G1_MADD_PRODUCTS * MONT_IMAD
+    w2 = g2["units"] * G2_MADD_PRODUCTS * MONT_IMAD
+    dom, work, ms, calls = ("k_accum0<G1>", w1, g1["ms"], g1["calls"]) if g1["ms"] >= g2["ms"] else \
+        ("k_accum0<G2>", w2, g2["ms"], g2["calls"])
+    peak = SMS * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = (work / calls) / (ms / calls / 1e3) / 1e12 if ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (nominal unit count and max clock)",
+                "algorithmic_imad_per_launch": work / max(calls, 1),
+                "launch_ms": ms / max(calls, 1)}
+    stages = {k: round(v["ms"] / max(v["calls"], 1), 4) for k, v in prof.items()}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        secs = [oracle_sample(inputs.SEED_CFG[2])[0] for _ in range(2)]
+        per = statistics.median(secs)
+        cpu = {"value": 1.0 / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "matmul on 2 of 49 rows, full CRPC evaluations, one 2^14-point textbook NTT scaled "
+                         "to seven 2^16 transforms, 64 naive scalar multiplications per scalar type scaled by "
+                         "each query's term count; extrapolated to one [49,320]x[320,512] proof"}
+
+    srt = sorted(step_ms)
+    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 limbs (exact Fr/Fp arithmetic)",
+        "data": "synthetic",
+        "config": {"workload": "crpc_groth16_bn254_49x320x512", "a": a, "n": n, "b": b, "log_domain": 16,
+                   "l2": "flushed by a 256 MiB write between steps", "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
+        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
+        "gpu_launches_per_step": launches / args.steps, "clocks": clk, "stage_ms": stages,
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

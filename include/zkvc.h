@@ -51,6 +51,20 @@ const char* zkvc_last_error(void);
 /* Library ABI version (major * 10000 + minor * 100 + patch). */
 int zkvc_version(void);
 
+/* Number of CUDA kernels the library has launched in this process so far (all devices,
+ * all threads); a diagnostic for launch-count accounting. */
+uint64_t zkvc_kernel_launches(void);
+
+/* Stage timers for the prover: when enabled, zkvc_prove records CUDA events on its
+ * stream around each stage and accumulates their elapsed times after its final
+ * synchronisation.  Stages 0..6: witness, ntt, msm_g1, msm_g1_bucket_accum, msm_g2,
+ * msm_g2_bucket_accum, combine.  The two bucket_accum stages time the bucket-accumulation
+ * kernel alone and count its units (bucket terms, one mixed point addition each).
+ * Enabling resets the counters.  A single-threaded diagnostic: not for concurrent provers.
+ */
+void zkvc_profile_enable(int on);
+int zkvc_profile_read(int stage, const char** name, double* ms, uint64_t* calls, uint64_t* units);
+
 /* ------------------------------------------------------------------ field kernels
  * Elementwise products of n canonical elements: d_out[i] = d_a[i] * d_b[i] mod the
  * field's modulus (Fr: scalar field r; Fp: base field p; Fp2: pairs c0 || c1, 64 bytes
@@ -155,6 +169,22 @@ int zkvc_pk_export(const zkvc_pk* pk, int query, size_t start, size_t count, uin
 #define ZKVC_VK_GAMMA2 3
 #define ZKVC_VK_DELTA2 4
 int zkvc_vk_export(const zkvc_vk* vk, int query, size_t start, size_t count, uint8_t* out);
+
+/* Builds a verifying key for shape (a, n, b) from canonical encodings (host memory,
+ * copied): [alpha]1, [beta]2, [gamma]2, [delta]2 and IC_0 .. IC_l (n_ic = l + 1 points of
+ * 64 bytes).  No device work.  Release with zkvc_vk_free.
+ */
+int zkvc_vk_import(int a, int n, int b, const uint8_t alpha1[64], const uint8_t beta2[128], const uint8_t gamma2[128],
+                   const uint8_t delta2[128], const uint8_t* ic, size_t n_ic, zkvc_vk** vk);
+
+/* Verify (Sec. II): decides e(A, B) = e(alpha, beta) e(IC(x), gamma) e(C, delta) with the
+ * public input x = X (a x n int8, row-major) then Y (a x b int32, row-major), host
+ * pointers.  Runs on the host (optimal-ate pairing over BN254), no device work.
+ * Returns ZKVC_OK with *ok = 1 for a valid proof and *ok = 0 otherwise -- including
+ * proofs whose points are not canonical, not on the curve, or (B) not in the order-r
+ * subgroup.  ZKVC_EIO for a malformed key.
+ */
+int zkvc_verify(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint8_t proof[256], int* ok);
 
 /* Prove (Sec. II) for the key's shape.
  *   d_X   a x n int8, row-major (device)          d_W  n x b int8, row-major (device)

@@ -11,6 +11,25 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
 template <class F>
 int export_points(const Affine<F>* src, const std::vector<uint64_t>& idx, uint8_t* host_out, cudaStream_t st);
 
+int verify_impl(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint8_t* proof, int* ok);
+
+int vk_get(const zkvc_vk* vk, int* a, int* n, int* b, const uint8_t** alpha1, const uint8_t** beta2,
+           const uint8_t** gamma2, const uint8_t** delta2, const uint8_t** ic, size_t* n_ic) {
+  ZK_CHECK(vk && vk->alpha1.size() == 64 && vk->beta2.size() == 128 && vk->gamma2.size() == 128 &&
+               vk->delta2.size() == 128 && vk->ic.size() % 64 == 0,
+           ZKVC_EIO, "verify: malformed verifying key");
+  *a = vk->shape.a;
+  *n = vk->shape.n;
+  *b = vk->shape.b;
+  *alpha1 = vk->alpha1.data();
+  *beta2 = vk->beta2.data();
+  *gamma2 = vk->gamma2.data();
+  *delta2 = vk->delta2.data();
+  *ic = vk->ic.data();
+  *n_ic = vk->ic.size() / 64;
+  return ZKVC_OK;
+}
+
 static int device_guard(int dev) {
   int cur = -1;
   ZK_CUDA(cudaGetDevice(&cur));
@@ -62,7 +81,7 @@ int zkvc_pk_export(const zkvc_pk* pk, int query, size_t start, size_t count, uin
   const Shape& sh = pk->shape;
   const Region* g = pk->lay.g1;
   const Region* g2 = pk->lay.g2;
-  const uint64_t nb = uint64_t(sh.n) * sh.b, an = uint64_t(sh.a) * sh.n;
+  const uint64_t nb = uint64_t(sh.n) * sh.b;
   uint64_t total = 0;
   switch (query) {
     case ZKVC_Q_A: total = sh.l + 1; break;
@@ -80,12 +99,8 @@ int zkvc_pk_export(const zkvc_pk* pk, int query, size_t start, size_t count, uin
     uint64_t e = start + q;
     uint64_t o = 0;
     switch (query) {
-      case ZKVC_Q_A:
-        if (e == 0) o = g[R1_A0].off;
-        else if (e <= an) o = g[R1_AX].off + (e - 1);
-        else o = g[R1_AY].off + (e - 1 - an) * g[R1_AY].nwin;
-        break;
-      case ZKVC_Q_B1: o = g[R1_B].off + e; break;
+      case ZKVC_Q_A: o = g[R1_A].off + e * g[R1_A].nwin; break;
+      case ZKVC_Q_B1: o = g[R1_B].off + e * g[R1_B].nwin; break;
       case ZKVC_Q_B2: o = g2[R2_B].off + e; break;
       case ZKVC_Q_L: o = e < nb ? g[R1_LW].off + e : g[R1_LS].off + (e - nb) * g[R1_LS].nwin; break;
       case ZKVC_Q_H: {
@@ -124,6 +139,30 @@ int zkvc_vk_export(const zkvc_vk* vk, int query, size_t start, size_t count, uin
   ZK_CHECK(start <= total && count <= total - start, ZKVC_EINVAL, "vk_export: range outside %zu entries", total);
   memcpy(out, src->data() + start * width, count * width);
   return ZKVC_OK;
+}
+
+int zkvc_vk_import(int a, int n, int b, const uint8_t alpha1[64], const uint8_t beta2[128], const uint8_t gamma2[128],
+                   const uint8_t delta2[128], const uint8_t* ic, size_t n_ic, zkvc_vk** vk) {
+  set_error("%s", "");
+  ZK_CHECK(alpha1 && beta2 && gamma2 && delta2 && ic && vk, ZKVC_EINVAL, "vk_import: null argument");
+  Shape sh;
+  ZK_TRY(make_shape(a, n, b, &sh));
+  ZK_CHECK(n_ic == size_t(sh.l) + 1, ZKVC_EINVAL, "vk_import: %zu IC points for %u public inputs", n_ic, sh.l);
+  zkvc_vk* v = new zkvc_vk();
+  v->shape = sh;
+  v->alpha1.assign(alpha1, alpha1 + 64);
+  v->beta2.assign(beta2, beta2 + 128);
+  v->gamma2.assign(gamma2, gamma2 + 128);
+  v->delta2.assign(delta2, delta2 + 128);
+  v->ic.assign(ic, ic + 64 * n_ic);
+  *vk = v;
+  return ZKVC_OK;
+}
+
+int zkvc_verify(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint8_t proof[256], int* ok) {
+  set_error("%s", "");
+  ZK_CHECK(vk && X && Y && proof && ok, ZKVC_EINVAL, "verify: null argument");
+  return verify_impl(vk, X, Y, proof, ok);
 }
 
 size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk) { return pk ? prove_workspace_bytes(pk) : 0; }

@@ -1,4 +1,5 @@
 // C-ABI entry points for the kernel layer: field products, NTT, variable-base MSM.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -20,6 +21,52 @@ void set_error(const char* fmt, ...) {
 }
 
 static void clear_error() { g_err.clear(); }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct ProfSlot {
+  const char* name;
+  cudaEvent_t b = nullptr, e = nullptr;
+  uint32_t* host_units = nullptr;
+  bool pending = false;
+  double ms = 0;
+  unsigned long long calls = 0, units = 0;
+};
+static ProfSlot g_prof_slots[PS_COUNT] = {{"witness"},   {"ntt"},    {"msm_g1"},  {"msm_g1_bucket_accum"},
+                                          {"msm_g2"},    {"msm_g2_bucket_accum"}, {"combine"}};
+static std::atomic<bool> g_prof{false};
+
+void prof_mark(int stage, bool begin, cudaStream_t st) {
+  if (!g_prof.load(std::memory_order_relaxed)) return;
+  ProfSlot& x = g_prof_slots[stage];
+  if (!x.b) {
+    cudaEventCreate(&x.b);
+    cudaEventCreate(&x.e);
+    cudaMallocHost(&x.host_units, sizeof(uint32_t));
+    *x.host_units = 0;
+  }
+  cudaEventRecord(begin ? x.b : x.e, st);
+  if (!begin) x.pending = true;
+}
+
+uint32_t* prof_units(int stage) {
+  if (!g_prof.load(std::memory_order_relaxed)) return nullptr;
+  return g_prof_slots[stage].host_units;
+}
+
+void prof_collect() {
+  if (!g_prof.load(std::memory_order_relaxed)) return;
+  for (auto& x : g_prof_slots) {
+    if (!x.pending) continue;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, x.b, x.e) == cudaSuccess) x.ms += ms;
+    x.calls++;
+    x.units += *x.host_units;
+    *x.host_units = 0;
+    x.pending = false;
+  }
+}
 
 // ------------------------------------------------------------------ field products
 template <class C>
@@ -114,11 +161,11 @@ static int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, 
   uint8_t* rest = a.base + a.off;
   size_t rest_bytes = ws_bytes - a.off;
   k_points_to_mont<F><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-      reinterpret_cast<const Affine<F>*>(d_points), bases, n);
+      reinterpret_cast<const Affine<F>*>(d_points), bases, n); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   MsmPlan p = variable_base_plan(n, d_scalars);
   ZK_TRY(msm_run<F>(p, bases, rest, rest_bytes, res, st));
-  k_export_point<F><<<1, 32, 0, st>>>(res, aff);
+  k_export_point<F><<<1, 32, 0, st>>>(res, aff); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   ZK_CUDA(cudaMemcpyAsync(out, aff, sizeof(Affine<F>), cudaMemcpyDeviceToHost, st));
   ZK_CUDA(cudaStreamSynchronize(st));
@@ -135,12 +182,34 @@ const char* zkvc_last_error(void) { return g_err.c_str(); }
 
 int zkvc_version(void) { return 100; }
 
+uint64_t zkvc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void zkvc_profile_enable(int on) {
+  for (auto& x : g_prof_slots) {
+    x.ms = 0;
+    x.calls = x.units = 0;
+    x.pending = false;
+  }
+  g_prof.store(on != 0);
+}
+
+int zkvc_profile_read(int stage, const char** name, double* ms, uint64_t* calls, uint64_t* units) {
+  clear_error();
+  ZK_CHECK(stage >= 0 && stage < PS_COUNT, ZKVC_EINVAL, "profile: stage %d outside [0, %d)", stage, (int)PS_COUNT);
+  const ProfSlot& x = g_prof_slots[stage];
+  if (name) *name = x.name;
+  if (ms) *ms = x.ms;
+  if (calls) *calls = x.calls;
+  if (units) *units = x.units;
+  return ZKVC_OK;
+}
+
 int zkvc_fr_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream) {
   clear_error();
   if (n == 0) return ZKVC_OK;
   ZK_CHECK(d_a && d_b && d_out, ZKVC_EINVAL, "fr_mul: null pointer");
   k_field_mul<FrCfg><<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-      (const Fr*)d_a, (const Fr*)d_b, (Fr*)d_out, n);
+      (const Fr*)d_a, (const Fr*)d_b, (Fr*)d_out, n); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }
@@ -150,7 +219,7 @@ int zkvc_fp_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n
   if (n == 0) return ZKVC_OK;
   ZK_CHECK(d_a && d_b && d_out, ZKVC_EINVAL, "fp_mul: null pointer");
   k_field_mul<FpCfg><<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-      (const Fp*)d_a, (const Fp*)d_b, (Fp*)d_out, n);
+      (const Fp*)d_a, (const Fp*)d_b, (Fp*)d_out, n); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }
@@ -160,7 +229,7 @@ int zkvc_fp2_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t 
   if (n == 0) return ZKVC_OK;
   ZK_CHECK(d_a && d_b && d_out, ZKVC_EINVAL, "fp2_mul: null pointer");
   k_fp2_mul<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>((const Fp2*)d_a, (const Fp2*)d_b,
-                                                                            (Fp2*)d_out, n);
+                                                                            (Fp2*)d_out, n); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }

@@ -80,6 +80,7 @@ struct FpCfg {
                                  0x8181585du, 0xb85045b6u, 0xe131a029u, 0x30644e72u}};
   static constexpr U256c R1 = cx_pow2_mod(256, MOD);
   static constexpr U256c R2 = cx_pow2_mod(512, MOD);
+  static constexpr U256c R3 = cx_pow2_mod(768, MOD);
   static constexpr U256c MOD_M2 = cx_sub1(MOD);
   static constexpr uint32_t INV = cx_neg_inv32(MOD.w[0]);
 };
@@ -89,6 +90,7 @@ struct FrCfg {
                                  0x8181585du, 0xb85045b6u, 0xe131a029u, 0x30644e72u}};
   static constexpr U256c R1 = cx_pow2_mod(256, MOD);
   static constexpr U256c R2 = cx_pow2_mod(512, MOD);
+  static constexpr U256c R3 = cx_pow2_mod(768, MOD);
   static constexpr U256c MOD_M2 = cx_sub1(MOD);
   static constexpr uint32_t INV = cx_neg_inv32(MOD.w[0]);
 };
@@ -113,6 +115,8 @@ template <class C>
 __host__ __device__ __forceinline__ constexpr uint32_t r2_limb(int i) { ZKVC_LIMB_SWITCH(C::R2, i) }
 template <class C>
 __host__ __device__ __forceinline__ constexpr uint32_t modm2_limb(int i) { ZKVC_LIMB_SWITCH(C::MOD_M2, i) }
+template <class C>
+__host__ __device__ __forceinline__ constexpr uint32_t r3_limb(int i) { ZKVC_LIMB_SWITCH(C::R3, i) }
 
 // ------------------------------------------------------------------ carry-chain rows
 // t[0..8] += a[0..7] * b : low halves into t[0..7] (carry into t[8]), then high halves
@@ -309,13 +313,81 @@ __device__ __forceinline__ Field<C> f_pow(const Field<C>& a, const uint32_t (&e)
   return r;
 }
 
-// Inverse by Fermat's little theorem, a^(N-2); a = 0 maps to 0.
+// Inverse of a Montgomery-form element (a R -> a^-1 R); 0 maps to 0.
+// Binary extended Euclidean algorithm on (u, v) = (a R, N) with Bezout coefficients
+// (x1, x2) kept in [0, N): each step halves an even value or subtracts the smaller
+// value, about 2 log2 N cheap 8-limb steps instead of a 254-bit exponentiation.  The
+// result (a R)^-1 = a^-1 R^-1 is brought back to Montgomery form by a product with R^3.
+// Not constant-time.
+__device__ __forceinline__ void shr1_8(uint32_t (&x)[8], uint32_t top) {
+#pragma unroll
+  for (int i = 0; i < 7; i++) x[i] = (x[i] >> 1) | (x[i + 1] << 31);
+  x[7] = (x[7] >> 1) | (top << 31);
+}
+
+__device__ __forceinline__ bool is_one8(const uint32_t (&x)[8]) {
+  uint32_t acc = x[0] ^ 1u;
+#pragma unroll
+  for (int i = 1; i < 8; i++) acc |= x[i];
+  return acc == 0;
+}
+
 template <class C>
 __device__ __noinline__ Field<C> f_inv(const Field<C>& a) {
-  uint32_t e[8];
+  if (a.is_zero()) return Field<C>::zero();
+  uint32_t p[8], u[8], v[8], x1[8], x2[8];
 #pragma unroll
-  for (int i = 0; i < 8; i++) e[i] = modm2_limb<C>(i);
-  return f_pow(a, e);
+  for (int i = 0; i < 8; i++) {
+    p[i] = mod_limb<C>(i);
+    u[i] = a.v[i];
+    v[i] = p[i];
+    x1[i] = 0;
+    x2[i] = 0;
+  }
+  x1[0] = 1;
+  while (!is_one8(u) && !is_one8(v)) {
+    while ((u[0] & 1u) == 0) {
+      shr1_8(u, 0);
+      if (x1[0] & 1u) {
+        uint32_t c = add8(x1, x1, p);
+        shr1_8(x1, c);
+      } else {
+        shr1_8(x1, 0);
+      }
+    }
+    while ((v[0] & 1u) == 0) {
+      shr1_8(v, 0);
+      if (x2[0] & 1u) {
+        uint32_t c = add8(x2, x2, p);
+        shr1_8(x2, c);
+      } else {
+        shr1_8(x2, 0);
+      }
+    }
+    uint32_t d[8];
+    if (!sub8(d, u, v)) {  // u >= v
+#pragma unroll
+      for (int i = 0; i < 8; i++) u[i] = d[i];
+      if (sub8(d, x1, x2)) add8(d, d, p);
+#pragma unroll
+      for (int i = 0; i < 8; i++) x1[i] = d[i];
+    } else {
+      sub8(d, v, u);
+#pragma unroll
+      for (int i = 0; i < 8; i++) v[i] = d[i];
+      if (sub8(d, x2, x1)) add8(d, d, p);
+#pragma unroll
+      for (int i = 0; i < 8; i++) x2[i] = d[i];
+    }
+  }
+  Field<C> r, r3;
+  const bool uone = is_one8(u);
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    r.v[i] = uone ? x1[i] : x2[i];
+    r3.v[i] = r3_limb<C>(i);
+  }
+  return f_mul(r, r3);
 }
 
 using Fp = Field<FpCfg>;

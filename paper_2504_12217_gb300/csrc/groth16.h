@@ -6,38 +6,36 @@
 #include "internal.h"
 #include "ntt.h"
 
-// Window widths of the fixed-base MSMs: int8 scalars take one signed 8-bit digit;
-// Y (int32) takes four; full Fr scalars take 32 digits of 8 bits (small queries and the
-// randomisation bases) or 16 digits of 16 bits (the H query).
-#define ZKVC_C_SMALL 8u
-#define ZKVC_W_I32 4u
-#define ZKVC_W_FULL8 32u
-#define ZKVC_C_H 16u
-#define ZKVC_W_H 16u
+// Window widths of the fixed-base MSMs.  The G1 MSMs use signed 16-bit digits: int8
+// and int32 scalars take one and two digits, full Fr scalars 16.  Every G1 base that a
+// full scalar can meet stores its 16 multiples 2^(16 w) P.  The G2 MSM (int8 scalars
+// plus the s [delta]2 term) uses 8-bit digits.
+#define ZKVC_C1 16u
+#define ZKVC_W1 16u
+#define ZKVC_C2 8u
+#define ZKVC_W2_FULL 32u
 
 namespace zkvc {
 
-// Regions of the G1 base array, in order.  Every entry stores nwin consecutive bases
-// 2^(c w) P (w < nwin) so that all windows of one MSM share one bucket set.
+// Regions of the G1 base array, in order.  An entry stores nwin consecutive bases
+// 2^(c w) P (w < nwin) so that every window of one MSM shares one bucket set.
 enum G1Region : int {
-  R1_A0 = 0,   // A-query, variable 0 (the constant one)        1 entry
-  R1_AX,       // A-query, X variables                         a n
-  R1_AY,       // A-query, Y variables                         a b     x4 windows
-  R1_ALPHA,    // [alpha]1                                     1
-  R1_DELTA,    // [delta]1                                     1       x32 windows
-  R1_B,        // B-query in G1, W variables                   n b
-  R1_BETA,     // [beta]1                                      1
-  R1_LW,       // L-query, W variables                         n b
-  R1_LS,       // L-query, S variables (prefix sums)           n - 1   x32 windows
-  R1_H,        // H-query, bit-reversed positions              N       x16 windows (c = 16)
+  R1_A = 0,    // A-query, variables v = 0 .. l (one, X, Y)      l + 1   x16
+  R1_ALPHA,    // [alpha]1                                       1       x16
+  R1_BETA,     // [beta]1                                        1       x16
+  R1_DELTA,    // [delta]1                                       1       x16
+  R1_B,        // B-query in G1, W variables                     n b     x16
+  R1_LW,       // L-query, W variables                           n b     x1
+  R1_LS,       // L-query, S variables (prefix sums)             n - 1   x16
+  R1_H,        // H-query, bit-reversed positions                N       x16
   R1_COUNT
 };
 
 enum G2Region : int {
-  R2_B = 0,    // B-query in G2                                n b
-  R2_BETA,     // [beta]2                                      1
-  R2_DELTA,    // [delta]2                                     1       x32 windows
-  R2_GAMMA,    // [gamma]2 (verifying key only)                1
+  R2_B = 0,    // B-query in G2                                  n b     x1   (c = 8)
+  R2_BETA,     // [beta]2                                        1
+  R2_DELTA,    // [delta]2                                       1       x32  (c = 8)
+  R2_GAMMA,    // [gamma]2 (verifying key only)                  1
   R2_COUNT
 };
 

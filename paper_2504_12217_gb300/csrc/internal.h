@@ -11,6 +11,26 @@ namespace zkvc {
 
 void set_error(const char* fmt, ...);
 
+// Number of kernels this library has launched in the process (diagnostics).
+void count_launch();
+#define ZK_COUNT_LAUNCH() ::zkvc::count_launch()
+
+// Optional stage timers (CUDA events on the launching stream), enabled by
+// zkvc_profile_enable; collected after the synchronising end of a prove call.
+enum ProfStage : int {
+  PS_WITNESS = 0,
+  PS_NTT,
+  PS_MSM_G1,
+  PS_ACCUM_G1,   // the G1 bucket-accumulation kernel alone; units = bucket terms
+  PS_MSM_G2,
+  PS_ACCUM_G2,   // the G2 bucket-accumulation kernel alone; units = bucket terms
+  PS_COMBINE,
+  PS_COUNT
+};
+void prof_mark(int stage, bool begin, cudaStream_t st);
+uint32_t* prof_units(int stage);  // pinned host slot for the stage's unit count, or null
+void prof_collect();
+
 #define ZK_CUDA(call)                                                                       \
   do {                                                                                      \
     cudaError_t e_ = (call);                                                                \

@@ -6,11 +6,13 @@
 // becomes one term (bucket key, base index | sign).  Terms are counting-sorted by key
 // (histogram, scan, atomic scatter), then each bucket's terms are summed by a
 // load-balanced segmented reduction: level 0 gives every chunk of T0 consecutive terms
-// of a bucket to one thread (mixed XYZZ + affine additions), and later levels fold T
-// partial sums at a time until one remains per bucket, so heavily skewed buckets (int8
-// scalars put ~1300 points in each of 128 buckets) cost no more depth than uniform ones.
-// A window's result is sum_v v B_v: threads take runs of `sz` buckets (running sums plus
-// a short multiplication by the run's offset) and a strided in-place tree adds the runs.
+// of a bucket to one thread (mixed XYZZ + affine additions), and binary in-place folds
+// then add each bucket's partial sums, so heavily skewed buckets (int8 scalars put ~1300
+// terms in each of 128 buckets) cost only log2 of their chunk count in depth.
+// A window's result sum_v v B_v is evaluated as sum_b 2^b U_b with U_b the sum of the
+// buckets whose index has bit b set: wide trees for the U_b, b doublings per bit in
+// parallel, and a short tree over the bits -- log-depth instead of a running sum, since a
+// single thread's point addition is long-latency (~14 us) on the GPU.
 //
 // Fixed-base MSMs (proving-key queries) store the multiples 2^(c w) P of each base, so all
 // windows share one bucket set and no doubling chain follows; variable-base MSMs keep
@@ -22,8 +24,7 @@
 namespace zkvc {
 
 static constexpr uint32_t KEY_NONE = 0xffffffffu;
-static constexpr uint32_t T0 = 16;  // terms per level-0 chunk
-static constexpr uint32_t TL = 8;   // partial sums folded per later level
+static constexpr uint32_t T0 = 32;  // terms per level-0 chunk
 
 // ------------------------------------------------------------------ scan
 __global__ void k_scan_blocks(const uint32_t* in, size_t n_in, uint32_t* out, size_t n_out, uint32_t* sums) {
@@ -63,7 +64,7 @@ static int scan_rec(const uint32_t* in, size_t n_in, uint32_t* out, size_t n_out
   size_t blocks = (n_out + 1023) / 1024;
   if (blocks <= 1) {
     if (!a.measuring) {
-      k_scan_blocks<<<1, 1024, 0, st>>>(in, n_in, out, n_out, nullptr);
+      k_scan_blocks<<<1, 1024, 0, st>>>(in, n_in, out, n_out, nullptr); ZK_COUNT_LAUNCH();
       ZK_CUDA(cudaGetLastError());
     }
     return ZKVC_OK;
@@ -72,12 +73,12 @@ static int scan_rec(const uint32_t* in, size_t n_in, uint32_t* out, size_t n_out
   uint32_t* sums_x = a.take<uint32_t>(blocks);
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "scan: workspace too small");
   if (!a.measuring) {
-    k_scan_blocks<<<(unsigned)blocks, 1024, 0, st>>>(in, n_in, out, n_out, sums);
+    k_scan_blocks<<<(unsigned)blocks, 1024, 0, st>>>(in, n_in, out, n_out, sums); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
   ZK_TRY(scan_rec(sums, blocks, sums_x, blocks, a, st));
   if (!a.measuring) {
-    k_scan_add<<<(unsigned)blocks, 1024, 0, st>>>(out, n_out, sums_x);
+    k_scan_add<<<(unsigned)blocks, 1024, 0, st>>>(out, n_out, sums_x); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
   return ZKVC_OK;
@@ -253,13 +254,22 @@ __device__ __forceinline__ uint32_t find_key(const uint32_t* off, uint32_t K, ui
 }
 
 // ------------------------------------------------------------------ bucket sums
+__global__ void k_chunk_keys(const uint32_t* __restrict__ choff, uint32_t K, uint32_t* chunk_key, uint32_t* max_chunks) {
+  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  uint32_t a = choff[k], b = choff[k + 1];
+  for (uint32_t q = a; q < b; q++) chunk_key[q] = k;
+  if (b > a) atomicMax(max_chunks, b - a);
+}
+
+// level 0: chunk q sums up to T0 consecutive terms of its bucket (mixed additions)
 template <class F>
 __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ offs,
-                                                const uint32_t* __restrict__ choff, uint32_t K,
-                                                const Affine<F>* __restrict__ bases, XYZZ<F>* part) {
+                                                const uint32_t* __restrict__ choff, const uint32_t* __restrict__ chunk_key,
+                                                uint32_t K, const Affine<F>* __restrict__ bases, XYZZ<F>* part) {
   uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= choff[K]) return;
-  uint32_t k = find_key(choff, K, q);
+  uint32_t k = chunk_key[q];
   uint32_t j = q - choff[k];
   uint32_t start = offs[k] + j * T0;
   uint32_t end = min(start + T0, offs[k + 1]);
@@ -273,22 +283,20 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
   st_field(part + q, acc);
 }
 
+// binary fold of the partial sums of each bucket, in place: at level l the partial at
+// local index i (a multiple of 2^(l+1)) absorbs the one at i + 2^l.  Levels at or above
+// log2 of the largest chunk count exit at once (the count is only known on the device).
 template <class F>
-__global__ void __launch_bounds__(256) k_accum_level(const XYZZ<F>* __restrict__ in, XYZZ<F>* out,
-                                                     const uint32_t* __restrict__ counts,
-                                                     const uint32_t* __restrict__ choff, uint32_t K, uint32_t D) {
+__global__ void __launch_bounds__(256) k_fold(XYZZ<F>* part, const uint32_t* __restrict__ choff,
+                                              const uint32_t* __restrict__ chunk_key, uint32_t K,
+                                              const uint32_t* __restrict__ max_chunks, uint32_t l) {
   uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= choff[K]) return;
-  uint32_t k = find_key(choff, K, q);
-  uint32_t j = q - choff[k];
-  uint32_t pc = (uint32_t)((uint64_t(counts[k]) + D - 1) / D);  // inputs at this level
-  uint32_t np = (pc + TL - 1) / TL;
-  if (j >= np) return;
-  uint32_t b = choff[k];
-  uint32_t s = j * TL, e = min(s + TL, pc);
-  XYZZ<F> acc = ld_field(in + b + s);
-  for (uint32_t i = s + 1; i < e; i++) acc = p_add(acc, ld_field(in + b + i));
-  st_field(out + b + j, acc);
+  const uint32_t step = 1u << l;
+  if (step >= *max_chunks || q >= choff[K]) return;
+  uint32_t k = chunk_key[q];
+  uint32_t base = choff[k], i = q - base, np = choff[k + 1] - base;
+  if ((i & (2 * step - 1)) != 0 || i + step >= np) return;
+  st_field(part + q, p_add(ld_field(part + q), ld_field(part + q + step)));
 }
 
 template <class F>
@@ -298,40 +306,50 @@ __device__ __forceinline__ XYZZ<F> bucket_at(const XYZZ<F>* fin, const uint32_t*
   return ld_field(fin + choff[key]);
 }
 
-template <class F>
-__device__ __forceinline__ XYZZ<F> p_mul_small(const XYZZ<F>& p, uint32_t k) {
-  XYZZ<F> r = XYZZ<F>::inf();
-  if (k == 0) return r;
-  int top = 31 - __clz(k);
-  r = p;
-  for (int b = top - 1; b >= 0; b--) {
-    r = p_dbl(r);
-    if ((k >> b) & 1u) r = p_add(r, p);
-  }
-  return r;
-}
-
-struct GroupItem {  // one run of buckets: output o, window w, buckets [v0, v0 + sz)
-  uint32_t key0;    // key of bucket v0
-  uint32_t v0;
-  uint32_t sz;
+// Window result sum_{v=1}^{NB} v B_v = sum_b 2^b U_b with U_b = sum_{v : bit b of v} B_v.
+// One BitSeg per (output, window, bit): the U_b sum starts as pairs of buckets and is
+// finished by strided tree levels; then 2^b U_b (b doublings, all bits in parallel) and a
+// tree over the bits of each (output, window).
+struct BitSeg {
+  uint32_t key0;  // key of bucket v = 1 of this (output, window)
+  uint32_t b, c;  // bit, window bits
+  uint32_t uoff;  // first pair in the U buffer
+  uint32_t dslot; // slot of 2^b U_b in the D buffer
 };
 
-// R = sum_{v in run} (v - v0 + 1) B_v + (v0 - 1) sum_{v in run} B_v = sum_{v in run} v B_v
+__device__ __forceinline__ uint32_t nth_with_bit(uint32_t b, uint32_t c, uint32_t idx) {
+  if (b == c - 1) return 1u << (c - 1);
+  return ((idx >> b) << (b + 1)) | (1u << b) | (idx & ((1u << b) - 1u));
+}
+
 template <class F>
-__global__ void __launch_bounds__(256) k_bucket_runs(const XYZZ<F>* __restrict__ fin, const uint32_t* __restrict__ counts,
-                                                     const uint32_t* __restrict__ choff, const GroupItem* __restrict__ items,
-                                                     uint32_t nitems, XYZZ<F>* grp) {
+__global__ void __launch_bounds__(256) k_bits_first(const XYZZ<F>* __restrict__ fin, const uint32_t* __restrict__ counts,
+                                                    const uint32_t* __restrict__ choff, const BitSeg* __restrict__ segs,
+                                                    uint32_t nseg, uint32_t total, XYZZ<F>* U) {
   uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nitems) return;
-  GroupItem it = items[t];
-  XYZZ<F> acc = XYZZ<F>::inf(), sum = XYZZ<F>::inf();
-  for (int v = (int)it.sz - 1; v >= 0; v--) {
-    acc = p_add(acc, bucket_at(fin, counts, choff, it.key0 + (uint32_t)v));
-    sum = p_add(sum, acc);
+  if (t >= total) return;
+  uint32_t lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi + 1) >> 1;
+    if (segs[mid].uoff <= t) lo = mid; else hi = mid - 1;
   }
-  if (it.v0 > 1) sum = p_add(sum, p_mul_small(acc, it.v0 - 1));
-  st_field(grp + t, sum);
+  const BitSeg s = segs[lo];
+  const uint32_t j = t - s.uoff;
+  const uint32_t cnt = (s.b == s.c - 1) ? 1u : (1u << (s.c - 2));
+  XYZZ<F> acc = bucket_at(fin, counts, choff, s.key0 + nth_with_bit(s.b, s.c, 2 * j) - 1);
+  if (2 * j + 1 < cnt) acc = p_add(acc, bucket_at(fin, counts, choff, s.key0 + nth_with_bit(s.b, s.c, 2 * j + 1) - 1));
+  st_field(U + t, acc);
+}
+
+template <class F>
+__global__ void __launch_bounds__(64) k_bits_scale(const XYZZ<F>* __restrict__ U, const BitSeg* __restrict__ segs,
+                                                   uint32_t nseg, XYZZ<F>* D) {
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nseg) return;
+  BitSeg s = segs[t];
+  XYZZ<F> x = ld_field(U + s.uoff);
+  for (uint32_t i = 0; i < s.b; i++) x = p_dbl(x);
+  st_field(D + s.dslot, x);
 }
 
 // In-place strided tree over segments: at level l, element i*2^(l+1) absorbs
@@ -362,42 +380,80 @@ __global__ void __launch_bounds__(256) k_tree_level(XYZZ<F>* x, const TreeSeg* s
 
 // results[o] = sum_w 2^(c w) W[o][w] by Horner's rule (windows of variable-base outputs).
 struct OutItem {
-  uint32_t first;     // index of window 0's tree result in grp
-  uint32_t stride;    // distance between windows' tree results
+  uint32_t first;     // index of window 0's result in D
+  uint32_t stride;    // distance between windows' results
   uint32_t nwin;
   uint32_t c;
 };
 
 template <class F>
-__global__ void k_combine_windows(const XYZZ<F>* grp, const OutItem* outs, uint32_t nouts, XYZZ<F>* results) {
+__global__ void k_combine_windows(const XYZZ<F>* D, const OutItem* outs, uint32_t nouts, XYZZ<F>* results) {
   uint32_t o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= nouts) return;
   OutItem it = outs[o];
-  XYZZ<F> acc = ld_field(grp + it.first + (it.nwin - 1) * it.stride);
+  XYZZ<F> acc = ld_field(D + it.first + (it.nwin - 1) * it.stride);
   for (int w = (int)it.nwin - 2; w >= 0; w--) {
     for (uint32_t i = 0; i < it.c; i++) acc = p_dbl(acc);
-    acc = p_add(acc, ld_field(grp + it.first + uint32_t(w) * it.stride));
+    acc = p_add(acc, ld_field(D + it.first + uint32_t(w) * it.stride));
   }
   st_field(results + o, acc);
 }
 
 // ------------------------------------------------------------------ driver
-static uint32_t run_size(uint32_t nb) { return nb < 8 ? nb : 8; }
-
 struct Layout {
-  uint32_t *keys, *vals, *sorted, *counts, *offs, *cursor, *nch, *choff;
-  void *partA, *partB, *grp;
+  uint32_t *keys, *vals, *sorted, *counts, *offs, *cursor, *nch, *choff, *chunk_key, *max_chunks;
+  void *part, *U, *D;
   MsmSeg* segs;
   MsmOut* outs;
-  GroupItem* items;
-  TreeSeg* tsegs;
+  BitSeg* bsegs;
+  TreeSeg* utree;
+  TreeSeg* dtree;
   OutItem* oitems;
-  uint32_t qmax, nitems, ntseg, ttotal, maxlen;
+  uint32_t qmax, nbits, utotal, dtotal, utree_threads, dtree_threads, umaxlen, dmaxlen;
 };
 
+struct HostTables {
+  std::vector<BitSeg> bsegs;
+  std::vector<TreeSeg> utree, dtree;
+  std::vector<OutItem> oitems;
+};
+
+static void tables(const MsmPlan& p, HostTables& h, Layout& L) {
+  h.bsegs.clear();
+  h.utree.clear();
+  h.dtree.clear();
+  h.oitems.clear();
+  uint32_t uoff = 0, dslot = 0, ucum = 0, dcum = 0;
+  L.umaxlen = 1;
+  L.dmaxlen = 1;
+  for (const auto& o : p.outs) {
+    const uint32_t nb = 1u << (o.c - 1);
+    h.oitems.push_back({dslot, o.c, o.win_keys, o.c});
+    for (uint32_t w = 0; w < o.win_keys; w++) {
+      h.dtree.push_back({dslot, o.c, dcum});
+      dcum += (o.c + 1) / 2;
+      L.dmaxlen = std::max(L.dmaxlen, o.c);
+      for (uint32_t b = 0; b < o.c; b++) {
+        uint32_t cnt = (b == o.c - 1) ? 1u : (1u << (o.c - 2));
+        uint32_t pairs = (cnt + 1) / 2;
+        h.bsegs.push_back({o.key_off + w * nb, b, o.c, uoff, dslot + b});
+        h.utree.push_back({uoff, pairs, ucum});
+        ucum += (pairs + 1) / 2;
+        L.umaxlen = std::max(L.umaxlen, pairs);
+        uoff += pairs;
+      }
+      dslot += o.c;
+    }
+  }
+  L.nbits = (uint32_t)h.bsegs.size();
+  L.utotal = uoff;
+  L.dtotal = dslot;
+  L.utree_threads = ucum;
+  L.dtree_threads = dcum;
+}
+
 template <class F>
-static int layout(const MsmPlan& p, Arena& a, Layout& L, std::vector<GroupItem>* items,
-                  std::vector<TreeSeg>* tsegs, std::vector<OutItem>* oitems) {
+static void layout(const MsmPlan& p, Arena& a, Layout& L, HostTables& h) {
   const size_t S = p.slots, K = p.keys;
   L.keys = a.take<uint32_t>(S);
   L.vals = a.take<uint32_t>(S);
@@ -408,38 +464,18 @@ static int layout(const MsmPlan& p, Arena& a, Layout& L, std::vector<GroupItem>*
   L.nch = a.take<uint32_t>(K);
   L.choff = a.take<uint32_t>(K + 1);
   L.qmax = (uint32_t)(S / T0 + K + 1);
-  L.partA = a.take<XYZZ<F>>(L.qmax);
-  L.partB = a.take<XYZZ<F>>(L.qmax);
-  // bucket runs: one item per run of sz buckets of every (output, window)
-  items->clear();
-  tsegs->clear();
-  oitems->clear();
-  uint32_t cum = 0;
-  L.maxlen = 1;
-  for (const auto& o : p.outs) {
-    uint32_t nb = 1u << (o.c - 1);
-    uint32_t sz = run_size(nb);
-    uint32_t runs = nb / sz;
-    OutItem oi{(uint32_t)items->size(), runs, o.win_keys, o.c};
-    for (uint32_t w = 0; w < o.win_keys; w++) {
-      TreeSeg ts{(uint32_t)items->size(), runs, cum};
-      cum += (runs + 1) / 2;
-      tsegs->push_back(ts);
-      L.maxlen = std::max(L.maxlen, runs);
-      for (uint32_t r = 0; r < runs; r++) items->push_back({o.key_off + w * nb + r * sz, r * sz + 1, sz});
-    }
-    oitems->push_back(oi);
-  }
-  L.nitems = (uint32_t)items->size();
-  L.ntseg = (uint32_t)tsegs->size();
-  L.ttotal = cum;
-  L.grp = a.take<XYZZ<F>>(L.nitems);
+  L.chunk_key = a.take<uint32_t>(L.qmax);
+  L.max_chunks = a.take<uint32_t>(1);
+  L.part = a.take<XYZZ<F>>(L.qmax);
+  tables(p, h, L);
+  L.U = a.take<XYZZ<F>>(L.utotal);
+  L.D = a.take<XYZZ<F>>(L.dtotal);
   L.segs = a.take<MsmSeg>(p.segs.size());
   L.outs = a.take<MsmOut>(p.outs.size());
-  L.items = a.take<GroupItem>(L.nitems);
-  L.tsegs = a.take<TreeSeg>(L.ntseg);
-  L.oitems = a.take<OutItem>(p.outs.size());
-  return ZKVC_OK;
+  L.bsegs = a.take<BitSeg>(h.bsegs.size());
+  L.utree = a.take<TreeSeg>(h.utree.size());
+  L.dtree = a.take<TreeSeg>(h.dtree.size());
+  L.oitems = a.take<OutItem>(h.oitems.size());
 }
 
 template <class F>
@@ -447,86 +483,98 @@ size_t msm_workspace_bytes(const MsmPlan& p) {
   Arena a;
   a.measuring = true;
   Layout L;
-  std::vector<GroupItem> items;
-  std::vector<TreeSeg> tsegs;
-  std::vector<OutItem> oitems;
-  layout<F>(p, a, L, &items, &tsegs, &oitems);
+  HostTables h;
+  layout<F>(p, a, L, h);
   a.off += scan_u32_temp_bytes(p.keys) + scan_u32_temp_bytes(p.keys) + 256;
   return a.off;
 }
 
+static uint32_t ceil_log2_u32(uint32_t x) {
+  uint32_t l = 0;
+  while ((1u << l) < x) l++;
+  return l;
+}
+
 template <class F>
-int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results, cudaStream_t st) {
+int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results, cudaStream_t st,
+            int accum_stage) {
   ZK_CHECK(p.keys > 0 && !p.outs.empty(), ZKVC_EINVAL, "msm: empty plan");
   Arena a;
   a.base = reinterpret_cast<uint8_t*>(ws);
   a.cap = ws_bytes;
   Layout L;
-  std::vector<GroupItem> items;
-  std::vector<TreeSeg> tsegs;
-  std::vector<OutItem> oitems;
-  layout<F>(p, a, L, &items, &tsegs, &oitems);
+  HostTables h;
+  layout<F>(p, a, L, h);
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace of %zu bytes is too small", ws_bytes);
   const uint32_t K = p.keys;
   const uint64_t S = p.slots;
 
   ZK_CUDA(cudaMemcpyAsync(L.segs, p.segs.data(), p.segs.size() * sizeof(MsmSeg), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.outs, p.outs.data(), p.outs.size() * sizeof(MsmOut), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.items, items.data(), items.size() * sizeof(GroupItem), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.tsegs, tsegs.data(), tsegs.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.oitems, oitems.data(), oitems.size() * sizeof(OutItem), cudaMemcpyHostToDevice, st));
+  ZK_CUDA(cudaMemcpyAsync(L.bsegs, h.bsegs.data(), h.bsegs.size() * sizeof(BitSeg), cudaMemcpyHostToDevice, st));
+  ZK_CUDA(cudaMemcpyAsync(L.utree, h.utree.data(), h.utree.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
+  ZK_CUDA(cudaMemcpyAsync(L.dtree, h.dtree.data(), h.dtree.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
+  ZK_CUDA(cudaMemcpyAsync(L.oitems, h.oitems.data(), h.oitems.size() * sizeof(OutItem), cudaMemcpyHostToDevice, st));
 
   // digits -> terms
   if (p.points > 0) {
-    k_digits<<<(p.points + 255) / 256, 256, 0, st>>>(L.segs, (int)p.segs.size(), L.outs, p.points, L.keys, L.vals);
+    k_digits<<<(p.points + 255) / 256, 256, 0, st>>>(L.segs, (int)p.segs.size(), L.outs, p.points, L.keys, L.vals); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
   // counting sort by bucket key
   ZK_CUDA(cudaMemsetAsync(L.counts, 0, size_t(K) * sizeof(uint32_t), st));
+  ZK_CUDA(cudaMemsetAsync(L.max_chunks, 0, sizeof(uint32_t), st));
   unsigned sb = (unsigned)((S + 255) / 256);
   if (S > 0) {
-    k_hist<<<sb, 256, 0, st>>>(L.keys, S, L.counts);
+    k_hist<<<sb, 256, 0, st>>>(L.keys, S, L.counts); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
   ZK_TRY(scan_u32(L.counts, L.offs, K, a, st));
   ZK_CUDA(cudaMemcpyAsync(L.cursor, L.offs, size_t(K) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
   if (S > 0) {
-    k_scatter<<<sb, 256, 0, st>>>(L.keys, L.vals, S, L.cursor, L.sorted);
+    k_scatter<<<sb, 256, 0, st>>>(L.keys, L.vals, S, L.cursor, L.sorted); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
   // chunks of T0 terms per bucket
-  k_chunks<<<(K + 255) / 256, 256, 0, st>>>(L.counts, K, L.nch);
+  k_chunks<<<(K + 255) / 256, 256, 0, st>>>(L.counts, K, L.nch); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   ZK_TRY(scan_u32(L.nch, L.choff, K, a, st));
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace too small for scans");
-  XYZZ<F>* pa = reinterpret_cast<XYZZ<F>*>(L.partA);
-  XYZZ<F>* pb = reinterpret_cast<XYZZ<F>*>(L.partB);
+  k_chunk_keys<<<(K + 255) / 256, 256, 0, st>>>(L.choff, K, L.chunk_key, L.max_chunks); ZK_COUNT_LAUNCH();
+  XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
   unsigned qb = (L.qmax + 255) / 256;
-  k_accum0<F><<<qb, 256, 0, st>>>(L.sorted, L.offs, L.choff, K, bases, pa);
-  ZK_CUDA(cudaGetLastError());
-  uint64_t D = T0;
-  while (D < S) {
-    k_accum_level<F><<<qb, 256, 0, st>>>(pa, pb, L.counts, L.choff, K, (uint32_t)D);
-    ZK_CUDA(cudaGetLastError());
-    std::swap(pa, pb);
-    D *= TL;
+  if (accum_stage >= 0) prof_mark(accum_stage, true, st);
+  k_accum0<F><<<qb, 256, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, bases, part); ZK_COUNT_LAUNCH();
+  if (accum_stage >= 0) {
+    prof_mark(accum_stage, false, st);
+    if (uint32_t* hu = prof_units(accum_stage)) ZK_CUDA(cudaMemcpyAsync(hu, L.offs + K, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   }
-  // sum_v v B_v per (output, window)
-  XYZZ<F>* grp = reinterpret_cast<XYZZ<F>*>(L.grp);
-  k_bucket_runs<F><<<(L.nitems + 255) / 256, 256, 0, st>>>(pa, L.counts, L.choff, L.items, L.nitems, grp);
   ZK_CUDA(cudaGetLastError());
-  for (uint32_t l = 0; (1u << l) < L.maxlen; l++) {
-    k_tree_level<F><<<(L.ttotal + 255) / 256, 256, 0, st>>>(grp, L.tsegs, L.ntseg, L.ttotal, l);
-    ZK_CUDA(cudaGetLastError());
+  // fold partials: enough levels for the largest possible chunk count
+  uint32_t levels = ceil_log2_u32((uint32_t)((S + T0 - 1) / T0 + 1));
+  for (uint32_t l = 0; l < levels; l++) {
+    k_fold<F><<<qb, 256, 0, st>>>(part, L.choff, L.chunk_key, K, L.max_chunks, l); ZK_COUNT_LAUNCH();
   }
-  k_combine_windows<F><<<((uint32_t)p.outs.size() + 63) / 64, 64, 0, st>>>(grp, L.oitems, (uint32_t)p.outs.size(), results);
+  ZK_CUDA(cudaGetLastError());
+  // sum_v v B_v per (output, window) by bit decomposition
+  XYZZ<F>* U = reinterpret_cast<XYZZ<F>*>(L.U);
+  XYZZ<F>* D = reinterpret_cast<XYZZ<F>*>(L.D);
+  k_bits_first<F><<<(L.utotal + 255) / 256, 256, 0, st>>>(part, L.counts, L.choff, L.bsegs, L.nbits, L.utotal, U); ZK_COUNT_LAUNCH();
+  for (uint32_t l = 0; (1u << l) < L.umaxlen; l++) {
+    k_tree_level<F><<<(L.utree_threads + 255) / 256, 256, 0, st>>>(U, L.utree, L.nbits, L.utree_threads, l); ZK_COUNT_LAUNCH();
+  }
+  k_bits_scale<F><<<(L.nbits + 63) / 64, 64, 0, st>>>(U, L.bsegs, L.nbits, D); ZK_COUNT_LAUNCH();
+  for (uint32_t l = 0; (1u << l) < L.dmaxlen; l++) {
+    k_tree_level<F><<<(L.dtree_threads + 255) / 256, 256, 0, st>>>(D, L.dtree, (uint32_t)h.dtree.size(), L.dtree_threads, l); ZK_COUNT_LAUNCH();
+  }
+  k_combine_windows<F><<<((uint32_t)p.outs.size() + 63) / 64, 64, 0, st>>>(D, L.oitems, (uint32_t)p.outs.size(), results); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }
 
 template size_t msm_workspace_bytes<Fp>(const MsmPlan&);
 template size_t msm_workspace_bytes<Fp2>(const MsmPlan&);
-template int msm_run<Fp>(const MsmPlan&, const Affine<Fp>*, void*, size_t, XYZZ<Fp>*, cudaStream_t);
-template int msm_run<Fp2>(const MsmPlan&, const Affine<Fp2>*, void*, size_t, XYZZ<Fp2>*, cudaStream_t);
+template int msm_run<Fp>(const MsmPlan&, const Affine<Fp>*, void*, size_t, XYZZ<Fp>*, cudaStream_t, int);
+template int msm_run<Fp2>(const MsmPlan&, const Affine<Fp2>*, void*, size_t, XYZZ<Fp2>*, cudaStream_t, int);
 
 }  // namespace zkvc

@@ -57,7 +57,7 @@ size_t msm_workspace_bytes(const MsmPlan& p);
 // Runs every output of the plan; results[o] receives output o (XYZZ, device).
 template <class F>
 int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results,
-            cudaStream_t st);
+            cudaStream_t st, int accum_stage = -1);
 
 // Exclusive scan of n uint32 values into out[0..n] (out[n] = total); temp from the arena.
 int scan_u32(const uint32_t* in, uint32_t* out, size_t n, Arena& a, cudaStream_t st);

@@ -100,7 +100,7 @@ __global__ void k_fill_pows(Fr* out, size_t count, const Fr* base_p, const Fr* m
 static int fill_pows(Fr* out, size_t count, const Fr* base, const Fr* mult, cudaStream_t st) {
   size_t runs = (count + 15) / 16;
   unsigned blocks = (unsigned)((runs + 127) / 128);
-  k_fill_pows<<<blocks, 128, 0, st>>>(out, count, base, mult);
+  k_fill_pows<<<blocks, 128, 0, st>>>(out, count, base, mult); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }
@@ -133,7 +133,7 @@ int ntt_domain(uint32_t logN, const NttDomain** out) {
   ZK_CUDA(cudaMalloc(&d->g_hi, hi * sizeof(Fr)));
   ZK_CUDA(cudaMalloc(&d->g_hi_n, hi * sizeof(Fr)));
   ZK_CUDA(cudaMalloc(&d->gi_hi_n, hi * sizeof(Fr)));
-  k_domain_consts<<<1, 1, 0, st>>>(d->consts, logN);
+  k_domain_consts<<<1, 1, 0, st>>>(d->consts, logN); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   const Fr* c = d->consts;
   ZK_TRY(fill_pows(d->tw_fwd, half, c + 2, c + 8, st));
@@ -256,6 +256,7 @@ static int run_passes(bool dit, Fr* data, int batch, size_t bstride, const NttDo
       k_ntt_pass<true><<<grid, threads, smem, st>>>(data, bstride, tw, L, s0, k, logG, ls, ss, tm, tabs);
     else
       k_ntt_pass<false><<<grid, threads, smem, st>>>(data, bstride, tw, L, s0, k, logG, ls, ss, tm, tabs);
+    ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
     s0 += k;
   }
@@ -293,7 +294,7 @@ __global__ void k_bitrev(Fr* a, uint32_t logN, int scale, int from_mont, ScaleTa
 
 int ntt_bitrev(Fr* data, const NttDomain* d, int scale, bool from_mont, cudaStream_t st) {
   unsigned blocks = (unsigned)((d->N + 255) / 256);
-  k_bitrev<<<blocks, 256, 0, st>>>(data, d->logN, scale, from_mont ? 1 : 0, tabs_of(d));
+  k_bitrev<<<blocks, 256, 0, st>>>(data, d->logN, scale, from_mont ? 1 : 0, tabs_of(d)); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }
@@ -309,7 +310,7 @@ __global__ void k_quotient(const Fr* __restrict__ A, const Fr* __restrict__ B, c
 
 int ntt_quotient(const Fr* A, const Fr* B, const Fr* C, Fr* H, const NttDomain* d, cudaStream_t st) {
   unsigned blocks = (unsigned)((d->N + 255) / 256);
-  k_quotient<<<blocks, 256, 0, st>>>(A, B, C, H, d->N, d->consts);
+  k_quotient<<<blocks, 256, 0, st>>>(A, B, C, H, d->N, d->consts); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }

@@ -11,10 +11,17 @@
 //     (DIT back to natural order), pointwise division by g^N - 1, coset INTT (DIF, scaled
 //     by g^-i / N).  h stays in bit-reversed order; the H query is stored in that order.
 //     h at natural index N - 1 must vanish (checked).
-//  6. One merged G1 MSM with four outputs -- A (with [alpha]1 and r [delta]1 folded in as
-//     extra bases), B1 (with [beta]1 and s [delta]1), L (with -rs [delta]1) and H -- and
-//     one G2 MSM for B (with [beta]2 and s [delta]2).
-//  7. C = L + H + s A + r B1, affine conversion, canonical 256-byte encoding.
+//  6. One merged G1 MSM with two outputs and one G2 MSM (on a side stream, overlapping
+//     steps 1-6).  By linearity the randomised Groth16 elements become fixed-base sums:
+//        A = [alpha]1 + sum_v w_v [A_v]1 + r [delta]1
+//        B = [beta]2  + sum_W w_e [B_e]2 + s [delta]2
+//        C = sum_priv w_i [L_i]1 + sum_j h_j [H_j]1 + s A + r B1 - r s [delta]1
+//          = sum w_i [L_i]1 + sum h_j [H_j]1 + s [alpha]1 + r [beta]1 + r s [delta]1
+//            + sum_v (s w_v) [A_v]1 + sum_W (r w_e) [B_e]1,
+//     so no variable-base multiplication (and no serial doubling chain) remains: every
+//     base is a proving-key point stored with its 2^(16 w) multiples.
+//  7. Affine conversion (one inversion per point, in parallel) and the canonical
+//     256-byte encoding A || B || C.
 #include <cstring>
 
 #include "groth16.h"
@@ -169,13 +176,29 @@ __device__ __forceinline__ bool canonical_fr(const Fr& x) {
   return false;
 }
 
-// rs[0] = r, rs[1] = s (canonical, from the caller); rs[2] = -r s (canonical)
+// rs[0] = r, rs[1] = s (canonical, from the caller); rs[2] = r s (canonical)
 __global__ void k_randomness(Fr* rs, int* flags) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Fr r = ld_field(rs), s = ld_field(rs + 1);
   if (!canonical_fr(r) || !canonical_fr(s)) atomicOr(flags, 4);
-  Fr prod = f_mul(f_to_mont(r), s);  // r s (canonical)
-  st_field(rs + 2, f_neg(prod));
+  st_field(rs + 2, f_mul(f_to_mont(r), s));  // (r R) s / R = r s, canonical
+}
+
+// sw[v] = s w_v for v = 0 .. l (one, X, Y) and rw[e] = r w_e for the W variables, in
+// Montgomery form: the scalars of the C terms s sum w_v A_v and r sum w_e B_e.
+__global__ void k_scaled_witness(const int8_t* __restrict__ X, const int32_t* __restrict__ Y,
+                                 const int8_t* __restrict__ W, const Fr* __restrict__ rs, uint32_t an, uint32_t l,
+                                 uint32_t nb, Fr* sw, Fr* rw) {
+  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= l) {
+    Fr s = f_to_mont(ld_field(rs + 1));
+    Fr w = t == 0 ? Fr::one() : (t <= an ? f_from_int<FrCfg>(X[t - 1]) : f_from_int<FrCfg>(Y[t - 1 - an]));
+    st_field(sw + t, f_mul(s, w));
+  } else if (t < l + 1 + nb) {
+    uint32_t e = t - l - 1;
+    Fr r = f_to_mont(ld_field(rs));
+    st_field(rw + e, f_mul(r, f_from_int<FrCfg>(W[e])));
+  }
 }
 
 __device__ __forceinline__ void write_canon(uint8_t* out, const Fp& x) {
@@ -188,39 +211,37 @@ __device__ __forceinline__ void write_canon(uint8_t* out, const Fp& x) {
   }
 }
 
-// C = L + H + s A + r B1 (joint double-and-add over the bits of s and r), then the
-// proof encoding A || B || C.
-__global__ void k_combine(const G1J* res1, const G2J* res2, const Fr* rs, uint8_t* proof) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  G1J A = ld_field(res1 + 0), B1 = ld_field(res1 + 1), L = ld_field(res1 + 2), H = ld_field(res1 + 3);
-  Fr r = ld_field(rs), s = ld_field(rs + 1);
-  G1J AB = p_add(A, B1);
-  G1J acc = G1J::inf();
-  for (int i = 7; i >= 0; i--) {
-    for (int bit = 31; bit >= 0; bit--) {
-      acc = p_dbl(acc);
-      uint32_t sb = (s.v[i] >> bit) & 1u, rb = (r.v[i] >> bit) & 1u;
-      if (sb && rb) acc = p_add(acc, AB);
-      else if (sb) acc = p_add(acc, A);
-      else if (rb) acc = p_add(acc, B1);
-    }
+__device__ __forceinline__ G1A g1_affine_with(const G1J& p, const Fp& inv_zz_zzz) {
+  if (p.is_inf()) return G1A::inf();
+  return {f_mul(p.X, f_mul(inv_zz_zzz, p.ZZZ)), f_mul(p.Y, f_mul(inv_zz_zzz, p.ZZ))};
+}
+
+// Proof encoding.  Warp 0 converts A and C with one shared inversion (Montgomery's
+// trick); warp 1 converts B concurrently.
+__global__ void k_encode(const G1J* res1, const G2J* res2, uint8_t* proof) {
+  if (threadIdx.x == 0) {
+    G1J A = ld_field(res1), C = ld_field(res1 + 1);
+    Fp za = A.is_inf() ? Fp::one() : f_mul(A.ZZ, A.ZZZ);
+    Fp zc = C.is_inf() ? Fp::one() : f_mul(C.ZZ, C.ZZZ);
+    Fp inv = f_inv(f_mul(za, zc));
+    G1A a = g1_affine_with(A, f_mul(inv, zc));
+    G1A c = g1_affine_with(C, f_mul(inv, za));
+    write_canon(proof + 0, a.x);
+    write_canon(proof + 32, a.y);
+    write_canon(proof + 192, c.x);
+    write_canon(proof + 224, c.y);
+  } else if (threadIdx.x == 32) {
+    G2A q = p_to_affine(ld_field(res2));
+    write_canon(proof + 64, q.x.c0);
+    write_canon(proof + 96, q.x.c1);
+    write_canon(proof + 128, q.y.c0);
+    write_canon(proof + 160, q.y.c1);
   }
-  G1J C = p_add(p_add(L, H), acc);
-  G1A a = p_to_affine(A), c = p_to_affine(C);
-  G2A bb = p_to_affine(ld_field(res2));
-  write_canon(proof + 0, a.x);
-  write_canon(proof + 32, a.y);
-  write_canon(proof + 64, bb.x.c0);
-  write_canon(proof + 96, bb.x.c1);
-  write_canon(proof + 128, bb.y.c0);
-  write_canon(proof + 160, bb.y.c1);
-  write_canon(proof + 192, c.x);
-  write_canon(proof + 224, c.y);
 }
 
 // ------------------------------------------------------------------ plans and workspace
 struct ProveBufs {
-  Fr *ak, *bk, *yz, *S, *ev, *rs;
+  Fr *ak, *bk, *yz, *S, *ev, *rs, *sw, *rw;
   int* flags;
   G1J* res1;
   G2J* res2;
@@ -231,45 +252,49 @@ struct ProveBufs {
   size_t ws2_bytes;
 };
 
+static MsmSeg seg_of(const Region& r, uint32_t first, uint32_t count, uint32_t out, int kind, const void* sc,
+                     uint32_t skip = 0xffffffffu) {
+  MsmSeg s{};
+  s.base_off = r.off + uint64_t(first) * r.nwin;
+  s.count = count;
+  s.nwin = r.nwin;
+  s.out = out;
+  s.kind = kind;
+  s.scalars = sc;
+  s.skip = skip;
+  return s;
+}
+
+// G1 outputs: 0 = A, 1 = C.  G2 output: 0 = B.
 static void plans(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const int32_t* dY, const Fr* S, const Fr* h,
-                  const Fr* rs, MsmPlan* p1, MsmPlan* p2) {
+                  const Fr* rs, const Fr* sw, const Fr* rw, MsmPlan* p1, MsmPlan* p2) {
   const Shape& sh = pk->shape;
   const Region* g = pk->lay.g1;
   const uint32_t an = sh.a * sh.n, ab = sh.a * sh.b, nb = sh.n * sh.b;
-  const uint32_t NONE = 0xffffffffu;
-  p1->outs = {{ZKVC_C_SMALL, 1, 0, 0}, {ZKVC_C_SMALL, 1, 0, 0}, {ZKVC_C_SMALL, 1, 0, 0}, {ZKVC_C_H, 1, 0, 0}};
-  auto seg = [&](const Region& r, uint32_t count, uint32_t out, int kind, const void* sc, uint32_t skip = 0xffffffffu) {
-    MsmSeg s{};
-    s.base_off = r.off;
-    s.count = count;
-    s.nwin = r.nwin;
-    s.out = out;
-    s.kind = kind;
-    s.scalars = sc;
-    s.skip = skip;
-    return s;
-  };
+  p1->outs = {{ZKVC_C1, 1, 0, 0}, {ZKVC_C1, 1, 0, 0}};
   p1->segs = {
-      seg(g[R1_A0], 1, 0, SK_ONE, nullptr),
-      seg(g[R1_AX], an, 0, SK_I8, dX),
-      seg(g[R1_AY], ab, 0, SK_I32, dY),
-      seg(g[R1_ALPHA], 1, 0, SK_ONE, nullptr),
-      seg(g[R1_DELTA], 1, 0, SK_FR_CANON, rs + 0),
-      seg(g[R1_B], nb, 1, SK_I8, dW),
-      seg(g[R1_BETA], 1, 1, SK_ONE, nullptr),
-      seg(g[R1_DELTA], 1, 1, SK_FR_CANON, rs + 1),
-      seg(g[R1_LW], nb, 2, SK_I8, dW),
-      seg(g[R1_LS], (uint32_t)(sh.n - 1), 2, SK_FR_MONT, S),
-      seg(g[R1_DELTA], 1, 2, SK_FR_CANON, rs + 2),
-      seg(g[R1_H], (uint32_t)sh.N, 3, SK_FR_MONT, h, (uint32_t)sh.N - 1),
+      // A = [alpha]1 + sum_v w_v [A_v]1 + r [delta]1
+      seg_of(g[R1_A], 0, 1, 0, SK_ONE, nullptr),
+      seg_of(g[R1_A], 1, an, 0, SK_I8, dX),
+      seg_of(g[R1_A], 1 + an, ab, 0, SK_I32, dY),
+      seg_of(g[R1_ALPHA], 0, 1, 0, SK_ONE, nullptr),
+      seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 0),
+      // C (see the file comment)
+      seg_of(g[R1_LW], 0, nb, 1, SK_I8, dW),
+      seg_of(g[R1_LS], 0, (uint32_t)(sh.n - 1), 1, SK_FR_MONT, S),
+      seg_of(g[R1_H], 0, (uint32_t)sh.N, 1, SK_FR_MONT, h, (uint32_t)sh.N - 1),
+      seg_of(g[R1_A], 0, sh.l + 1, 1, SK_FR_MONT, sw),
+      seg_of(g[R1_B], 0, nb, 1, SK_FR_MONT, rw),
+      seg_of(g[R1_ALPHA], 0, 1, 1, SK_FR_CANON, rs + 1),
+      seg_of(g[R1_BETA], 0, 1, 1, SK_FR_CANON, rs + 0),
+      seg_of(g[R1_DELTA], 0, 1, 1, SK_FR_CANON, rs + 2),
   };
-  (void)NONE;
   const Region* g2 = pk->lay.g2;
-  p2->outs = {{ZKVC_C_SMALL, 1, 0, 0}};
+  p2->outs = {{ZKVC_C2, 1, 0, 0}};
   p2->segs = {
-      seg(g2[R2_B], nb, 0, SK_I8, dW),
-      seg(g2[R2_BETA], 1, 0, SK_ONE, nullptr),
-      seg(g2[R2_DELTA], 1, 0, SK_FR_CANON, rs + 1),
+      seg_of(g2[R2_B], 0, nb, 0, SK_I8, dW),
+      seg_of(g2[R2_BETA], 0, 1, 0, SK_ONE, nullptr),
+      seg_of(g2[R2_DELTA], 0, 1, 0, SK_FR_CANON, rs + 1),
   };
   msm_plan_finalize(*p1);
   msm_plan_finalize(*p2);
@@ -287,17 +312,40 @@ static size_t carve(const zkvc_pk* pk, void* base, size_t cap, ProveBufs* B, boo
   B->S = a.take<Fr>(sh.n);
   B->ev = a.take<Fr>(4 * sh.N);
   B->rs = a.take<Fr>(4);
+  B->sw = a.take<Fr>(sh.l + 1);
+  B->rw = a.take<Fr>(size_t(sh.n) * sh.b);
   B->flags = a.take<int>(4);
-  B->res1 = a.take<G1J>(4);
+  B->res1 = a.take<G1J>(2);
   B->res2 = a.take<G2J>(1);
   B->proof = a.take<uint8_t>(256);
   MsmPlan p1, p2;
-  plans(pk, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &p1, &p2);
+  plans(pk, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &p1, &p2);
   B->ws1_bytes = msm_workspace_bytes<Fp>(p1);
   B->ws2_bytes = msm_workspace_bytes<Fp2>(p2);
   B->ws1 = a.take<uint8_t>(B->ws1_bytes);
   B->ws2 = a.take<uint8_t>(B->ws2_bytes);
   return a.off;
+}
+
+// Per-thread side stream and fork/join events (created on first use on each device).
+struct SideStream {
+  int dev = -1;
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static thread_local SideStream t_side;
+
+static int side_stream(SideStream** out) {
+  int dev = 0;
+  ZK_CUDA(cudaGetDevice(&dev));
+  if (t_side.st == nullptr || t_side.dev != dev) {
+    t_side.dev = dev;
+    ZK_CUDA(cudaStreamCreateWithFlags(&t_side.st, cudaStreamNonBlocking));
+    ZK_CUDA(cudaEventCreateWithFlags(&t_side.fork, cudaEventDisableTiming));
+    ZK_CUDA(cudaEventCreateWithFlags(&t_side.join, cudaEventDisableTiming));
+  }
+  *out = &t_side;
+  return ZKVC_OK;
 }
 
 size_t prove_workspace_bytes(const zkvc_pk* pk) {
@@ -319,40 +367,61 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   Fr* Cev = B.ev + 2 * N;
   Fr* Hev = B.ev + 3 * N;
 
+  prof_mark(PS_WITNESS, true, st);
   ZK_CUDA(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), st));
   ZK_CUDA(cudaMemcpyAsync(B.rs, rs_host, 64, cudaMemcpyHostToDevice, st));
-  k_randomness<<<1, 1, 0, st>>>(B.rs, B.flags);
+  k_randomness<<<1, 1, 0, st>>>(B.rs, B.flags); ZK_COUNT_LAUNCH();
+  // G2 MSM on the side stream: it needs only W and s
+  SideStream* side = nullptr;
+  ZK_TRY(side_stream(&side));
+  MsmPlan p1, p2;
+  plans(pk, dX, dW, dY, B.S, Hev, B.rs, B.sw, B.rw, &p1, &p2);
+  ZK_CUDA(cudaEventRecord(side->fork, st));
+  ZK_CUDA(cudaStreamWaitEvent(side->st, side->fork, 0));
+  prof_mark(PS_MSM_G2, true, side->st);
+  ZK_TRY(msm_run<Fp2>(p2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st, PS_ACCUM_G2));
+  prof_mark(PS_MSM_G2, false, side->st);
+  ZK_CUDA(cudaEventRecord(side->join, side->st));
   // 1. Y = X W
   dim3 mg((sh.b + 31) / 32, (sh.a + 31) / 32);
-  k_matmul_i8<<<mg, dim3(32, 8), 0, st>>>(dX, dW, dY, sh.a, sh.n, sh.b);
+  k_matmul_i8<<<mg, dim3(32, 8), 0, st>>>(dX, dW, dY, sh.a, sh.n, sh.b); ZK_COUNT_LAUNCH();
   // 2-3. CRPC evaluations and PSQ prefix sums
-  k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk);
-  k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz);
-  k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, B.S, Aev, Bev, Cev, B.flags);
+  k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
+  k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz); ZK_COUNT_LAUNCH();
+  k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, B.S, Aev, Bev, Cev, B.flags); ZK_COUNT_LAUNCH();
   // 4. remaining domain evaluations
   size_t rest = N - sh.n;
-  k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev);
+  k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev); ZK_COUNT_LAUNCH();
+  uint32_t nsc = sh.l + 1 + uint32_t(sh.n) * sh.b;
+  k_scaled_witness<<<(nsc + 255) / 256, 256, 0, st>>>(dX, dY, dW, B.rs, sh.a * sh.n, sh.l, uint32_t(sh.n) * sh.b, B.sw,
+                                                      B.rw); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
+  prof_mark(PS_WITNESS, false, st);
   // 5. quotient
+  prof_mark(PS_NTT, true, st);
   const NttDomain* d = pk->dom;
   ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, st));
   ZK_TRY(ntt_dit(Aev, 3, N, d, false, st));
   ZK_TRY(ntt_quotient(Aev, Bev, Cev, Hev, d, st));
   ZK_TRY(ntt_dif(Hev, 1, N, d, true, SC_NONE, SC_NGI, false, st));
-  k_check_h<<<1, 32, 0, st>>>(Hev, N, B.flags);
+  k_check_h<<<1, 32, 0, st>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  // 6. MSMs
-  MsmPlan p1, p2;
-  plans(pk, dX, dW, dY, B.S, Hev, B.rs, &p1, &p2);
-  ZK_TRY(msm_run<Fp>(p1, pk->g1, B.ws1, B.ws1_bytes, B.res1, st));
-  ZK_TRY(msm_run<Fp2>(p2, pk->g2, B.ws2, B.ws2_bytes, B.res2, st));
-  // 7. combine and encode
-  k_combine<<<1, 32, 0, st>>>(B.res1, B.res2, B.rs, B.proof);
+  prof_mark(PS_NTT, false, st);
+  // 6. G1 MSM (A and C); join the G2 MSM
+  prof_mark(PS_MSM_G1, true, st);
+  ZK_TRY(msm_run<Fp>(p1, pk->g1, B.ws1, B.ws1_bytes, B.res1, st, PS_ACCUM_G1));
+  prof_mark(PS_MSM_G1, false, st);
+  ZK_CUDA(cudaStreamWaitEvent(st, side->join, 0));
+  // 7. encode
+  prof_mark(PS_COMBINE, true, st);
+  k_encode<<<1, 64, 0, st>>>(B.res1, B.res2, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
+  prof_mark(PS_COMBINE, false, st);
   int flags = 0;
   ZK_CUDA(cudaMemcpyAsync(proof_host, B.proof, 256, cudaMemcpyDeviceToHost, st));
   ZK_CUDA(cudaMemcpyAsync(&flags, B.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
   ZK_CUDA(cudaStreamSynchronize(st));
+  prof_collect();
   ZK_CHECK(!(flags & 4), ZKVC_EINVAL, "prove: r or s is not a canonical Fr element");
   ZK_CHECK(!(flags & 1), ZKVC_EUNSAT, "prove: the PSQ chain does not close against Y(z)");
   ZK_CHECK(!(flags & 2), ZKVC_EUNSAT, "prove: the quotient has degree N - 1 (QAP not satisfied)");

@@ -41,21 +41,20 @@ int make_shape(int a, int n, int b, Shape* s) {
 
 Layout make_layout(const Shape& s) {
   Layout L{};
-  const uint32_t an = s.a * s.n, ab = s.a * s.b, nb = s.n * s.b;
-  const uint32_t cnt1[R1_COUNT] = {1, an, ab, 1, 1, nb, 1, nb, (uint32_t)(s.n - 1), (uint32_t)s.N};
-  const uint32_t win1[R1_COUNT] = {1, 1, ZKVC_W_I32, 1, ZKVC_W_FULL8, 1, 1, 1, ZKVC_W_FULL8, ZKVC_W_H};
+  const uint32_t nb = s.n * s.b;
+  const uint32_t cnt1[R1_COUNT] = {s.l + 1, 1, 1, 1, nb, nb, (uint32_t)(s.n - 1), (uint32_t)s.N};
+  const uint32_t win1[R1_COUNT] = {ZKVC_W1, ZKVC_W1, ZKVC_W1, ZKVC_W1, ZKVC_W1, 1, ZKVC_W1, ZKVC_W1};
   uint64_t off = 0;
   for (int r = 0; r < R1_COUNT; r++) {
-    uint32_t c = (r == R1_H) ? ZKVC_C_H : ZKVC_C_SMALL;
-    L.g1[r] = {off, cnt1[r], win1[r], c, r};
+    L.g1[r] = {off, cnt1[r], win1[r], ZKVC_C1, r};
     off += uint64_t(cnt1[r]) * win1[r];
   }
   L.n_g1 = off;
   const uint32_t cnt2[R2_COUNT] = {nb, 1, 1, 1};
-  const uint32_t win2[R2_COUNT] = {1, 1, ZKVC_W_FULL8, 1};
+  const uint32_t win2[R2_COUNT] = {1, 1, ZKVC_W2_FULL, 1};
   off = 0;
   for (int r = 0; r < R2_COUNT; r++) {
-    L.g2[r] = {off, cnt2[r], win2[r], ZKVC_C_SMALL, r};
+    L.g2[r] = {off, cnt2[r], win2[r], ZKVC_C2, r};
     off += uint64_t(cnt2[r]) * win2[r];
   }
   L.n_g2 = off;
@@ -181,16 +180,21 @@ __global__ void k_query_scalars(RegionTab tab, int group, const SetupConsts* __r
   Fr s = Fr::zero();
   if (group == GRP_G1) {
     switch (rg.kind) {
-      case R1_A0: s = ld_field(L + n); break;
-      case R1_AX: {
-        uint32_t i = e / n, k = e % n, v = 1 + e;
-        s = f_add(f_mul(ld_field(zA + i), ld_field(L + k)), ld_field(L + n + v));
+      case R1_A: {
+        uint32_t v = e;
+        if (v == 0) {
+          s = ld_field(L + n);
+        } else if (v <= an) {
+          uint32_t i = (v - 1) / n, k = (v - 1) % n;
+          s = f_add(f_mul(ld_field(zA + i), ld_field(L + k)), ld_field(L + n + v));
+        } else {
+          s = ld_field(L + n + v);
+        }
         break;
       }
-      case R1_AY: s = ld_field(L + n + 1 + an + e); break;
       case R1_ALPHA: s = sc.alpha; break;
-      case R1_DELTA: s = sc.delta; break;
       case R1_BETA: s = sc.beta; break;
+      case R1_DELTA: s = sc.delta; break;
       case R1_B: s = f_mul(ld_field(zB + e % b), ld_field(L + e / b)); break;
       case R1_LW: s = f_mul(f_mul(sc.alpha, sc.dinv), f_mul(ld_field(zB + e % b), ld_field(L + e / b))); break;
       case R1_LS: s = f_mul(f_sub(ld_field(L + e), ld_field(L + e + 1)), sc.dinv); break;
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(256) k_fixed_base(const Fr* __restrict__ scal,
 template <class F>
 static int normalize(const XYZZ<F>* in, Affine<F>* out, size_t n, cudaStream_t st) {
   size_t chunks = (n + NORM_CHUNK - 1) / NORM_CHUNK;
-  k_normalize<F><<<(unsigned)((chunks + 127) / 128), 128, 0, st>>>(in, out, n);
+  k_normalize<F><<<(unsigned)((chunks + 127) / 128), 128, 0, st>>>(in, out, n); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }
@@ -319,9 +323,9 @@ static int build_table(Affine<F>** out, cudaStream_t st) {
   XYZZ<F>* tmp = nullptr;
   ZK_CUDA(cudaMalloc(&tmp, 32 * 256 * sizeof(XYZZ<F>)));
   ZK_CUDA(cudaMalloc(out, 32 * 256 * sizeof(Affine<F>)));
-  k_fb_seed<F><<<1, 1, 0, st>>>(tmp);
+  k_fb_seed<F><<<1, 1, 0, st>>>(tmp); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  k_fb_fill<F><<<1, 32, 0, st>>>(tmp);
+  k_fb_fill<F><<<1, 32, 0, st>>>(tmp); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   ZK_TRY(normalize<F>(tmp, *out, 32 * 256, st));
   ZK_CUDA(cudaStreamSynchronize(st));
@@ -352,7 +356,7 @@ static int points_from_scalars(const Fr* scal, size_t n, const Affine<F>* T, Aff
                                size_t chunk, cudaStream_t st) {
   for (size_t s = 0; s < n; s += chunk) {
     size_t m = n - s < chunk ? n - s : chunk;
-    k_fixed_base<F><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(scal + s, m, T, tmp);
+    k_fixed_base<F><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(scal + s, m, T, tmp); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
     ZK_TRY(normalize<F>(tmp, out + s, m, st));
   }
@@ -390,7 +394,7 @@ int export_points(const Affine<F>* src, const std::vector<uint64_t>& idx, uint8_
   ZK_CUDA(cudaMalloc(&d_idx, idx.size() * sizeof(uint64_t)));
   ZK_CUDA(cudaMalloc(&d_out, idx.size() * sizeof(Affine<F>)));
   ZK_CUDA(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-  k_export<F><<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(src, d_idx, idx.size(), d_out);
+  k_export<F><<<(unsigned)((idx.size() + 255) / 256), 256, 0, st>>>(src, d_idx, idx.size(), d_out); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   ZK_CUDA(cudaMemcpyAsync(host_out, d_out, idx.size() * sizeof(Affine<F>), cudaMemcpyDeviceToHost, st));
   ZK_CUDA(cudaStreamSynchronize(st));
@@ -438,7 +442,7 @@ int setup_impl(int a, int n, int b, const uint8_t* toxic, cudaStream_t st, zkvc_
   ZK_TRY(tmp.alloc(&d_sc, 1));
   ZK_TRY(tmp.alloc(&d_L, sh.rows));
   ZK_CUDA(cudaMemcpyAsync(d_toxic, toxic, 6 * 32, cudaMemcpyHostToDevice, st));
-  k_setup_consts<<<1, 1, 0, st>>>(d_toxic, d_sc, sh.logN, dom->consts);
+  k_setup_consts<<<1, 1, 0, st>>>(d_toxic, d_sc, sh.logN, dom->consts); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   int bad = 0;
   ZK_CUDA(cudaMemcpyAsync(&bad, &d_sc->bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -469,9 +473,9 @@ int setup_impl(int a, int n, int b, const uint8_t* toxic, cudaStream_t st, zkvc_
   }
   int rc = ZKVC_OK;
   do {
-    k_zpows<<<(sh.a + sh.b + 127) / 128, 128, 0, st>>>(d_sc, pk->zA, sh.a, pk->zB, sh.b);
+    k_zpows<<<(sh.a + sh.b + 127) / 128, 128, 0, st>>>(d_sc, pk->zA, sh.a, pk->zB, sh.b); ZK_COUNT_LAUNCH();
     size_t lag_threads = (sh.rows + LAG_CHUNK - 1) / LAG_CHUNK;
-    k_lagrange<<<(unsigned)((lag_threads + 127) / 128), 128, 0, st>>>(d_sc, dom->tw_fwd, sh.N, sh.rows, d_L);
+    k_lagrange<<<(unsigned)((lag_threads + 127) / 128), 128, 0, st>>>(d_sc, dom->tw_fwd, sh.N, sh.rows, d_L); ZK_COUNT_LAUNCH();
     if (cudaGetLastError() != cudaSuccess) {
       rc = ZKVC_ECUDA;
       break;
@@ -484,18 +488,18 @@ int setup_impl(int a, int n, int b, const uint8_t* toxic, cudaStream_t st, zkvc_
     XYZZ<Fp2>* xtmp = nullptr;  // large enough for G1 or G2 chunks
     if ((rc = tmp.alloc(&xtmp, chunk)) != ZKVC_OK) break;
     RegionTab t1 = region_tab(lay.g1, R1_COUNT);
-    k_query_scalars<<<(t1.entry_off[R1_COUNT] + 255) / 256, 256, 0, st>>>(t1, GRP_G1, d_sc, d_L, pk->zA, pk->zB, sh, scal);
+    k_query_scalars<<<(t1.entry_off[R1_COUNT] + 255) / 256, 256, 0, st>>>(t1, GRP_G1, d_sc, d_L, pk->zA, pk->zB, sh, scal); ZK_COUNT_LAUNCH();
     if ((rc = points_from_scalars<Fp>(scal, lay.n_g1, T1, pk->g1, reinterpret_cast<XYZZ<Fp>*>(xtmp), 2 * chunk, st)) != ZKVC_OK) break;
     // G2
     RegionTab t2 = region_tab(lay.g2, R2_COUNT);
-    k_query_scalars<<<(t2.entry_off[R2_COUNT] + 255) / 256, 256, 0, st>>>(t2, GRP_G2, d_sc, d_L, pk->zA, pk->zB, sh, scal);
+    k_query_scalars<<<(t2.entry_off[R2_COUNT] + 255) / 256, 256, 0, st>>>(t2, GRP_G2, d_sc, d_L, pk->zA, pk->zB, sh, scal); ZK_COUNT_LAUNCH();
     if ((rc = points_from_scalars<Fp2>(scal, lay.n_g2, T2, pk->g2, xtmp, chunk, st)) != ZKVC_OK) break;
     // verifying key: IC_v for v = 0 .. l
-    Region ric{0, sh.l + 1, 1, ZKVC_C_SMALL, 0};
+    Region ric{0, sh.l + 1, 1, ZKVC_C2, 0};
     RegionTab t3 = region_tab(&ric, 1);
     G1A* ic = nullptr;
     if ((rc = tmp.alloc(&ic, sh.l + 1)) != ZKVC_OK) break;
-    k_query_scalars<<<(sh.l + 1 + 255) / 256, 256, 0, st>>>(t3, GRP_IC, d_sc, d_L, pk->zA, pk->zB, sh, scal);
+    k_query_scalars<<<(sh.l + 1 + 255) / 256, 256, 0, st>>>(t3, GRP_IC, d_sc, d_L, pk->zA, pk->zB, sh, scal); ZK_COUNT_LAUNCH();
     if ((rc = points_from_scalars<Fp>(scal, sh.l + 1, T1, ic, reinterpret_cast<XYZZ<Fp>*>(xtmp), 2 * chunk, st)) != ZKVC_OK) break;
     if (cudaGetLastError() != cudaSuccess) {
       rc = ZKVC_ECUDA;

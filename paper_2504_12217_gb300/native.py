@@ -33,6 +33,10 @@ _c_u32 = ctypes.c_uint32
 SIGNATURES = {
     "zkvc_last_error": (ctypes.c_char_p, []),
     "zkvc_version": (_c_int, []),
+    "zkvc_kernel_launches": (ctypes.c_uint64, []),
+    "zkvc_profile_enable": (None, [_c_int]),
+    "zkvc_profile_read": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "zkvc_fr_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_fp_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_fp2_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
@@ -47,6 +51,8 @@ SIGNATURES = {
                               ctypes.POINTER(_c_u32), ctypes.POINTER(_c_sz), ctypes.POINTER(_c_sz)]),
     "zkvc_pk_export": (_c_int, [_c_p, _c_int, _c_sz, _c_sz, _c_p]),
     "zkvc_vk_export": (_c_int, [_c_p, _c_int, _c_sz, _c_sz, _c_p]),
+    "zkvc_vk_import": (_c_int, [_c_int, _c_int, _c_int, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, ctypes.POINTER(_c_p)]),
+    "zkvc_verify": (_c_int, [_c_p, _c_p, _c_p, _c_p, ctypes.POINTER(_c_int)]),
     "zkvc_prove_workspace_bytes": (_c_sz, [_c_p]),
     "zkvc_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
 }
@@ -116,6 +122,29 @@ def _u8(t, width):
 # ------------------------------------------------------------------ kernel layer
 def zkvc_version():
     return lib().zkvc_version()
+
+
+def zkvc_kernel_launches():
+    return lib().zkvc_kernel_launches()
+
+
+def zkvc_profile_enable(on):
+    lib().zkvc_profile_enable(1 if on else 0)
+
+
+def zkvc_profile_read():
+    """{stage name: {"ms": total ms, "calls": n, "units": accumulated units}}"""
+    out = {}
+    stage = 0
+    while True:
+        name, ms = ctypes.c_char_p(), ctypes.c_double()
+        calls, units = ctypes.c_uint64(), ctypes.c_uint64()
+        rc = lib().zkvc_profile_read(stage, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(calls),
+                                     ctypes.byref(units))
+        if rc != ZKVC_OK:
+            return out
+        out[name.value.decode()] = {"ms": ms.value, "calls": calls.value, "units": units.value}
+        stage += 1
 
 
 def zkvc_fr_mul(a, b, out=None):
@@ -243,6 +272,30 @@ def zkvc_vk_export(vk, query, start, count):
     out = ctypes.create_string_buffer(max(1, width * count))
     check(lib().zkvc_vk_export(vk.handle, query, start, count, out))
     return out.raw[: width * count]
+
+
+def zkvc_vk_import(a, n, b, alpha1, beta2, gamma2, delta2, ic):
+    """VerifyingKey from canonical encodings (bytes); ic holds l + 1 points of 64 bytes."""
+    if len(ic) % 64:
+        raise ValueError("ic must be a multiple of 64 bytes")
+    vk = _c_p()
+    check(lib().zkvc_vk_import(a, n, b, bytes(alpha1), bytes(beta2), bytes(gamma2), bytes(delta2), bytes(ic),
+                               len(ic) // 64, ctypes.byref(vk)))
+    return VerifyingKey(vk, (a, n, b))
+
+
+def zkvc_verify(vk, X, Y, proof):
+    """Host-side verification; X: int8 [a, n], Y: int32 [a, b] (numpy or CPU tensors)."""
+    import numpy as np
+    a, n, b = vk.shape
+    Xn = np.ascontiguousarray(np.asarray(X, dtype=np.int8).reshape(a, n))
+    Yn = np.ascontiguousarray(np.asarray(Y, dtype=np.int32).reshape(a, b))
+    if len(proof) != 256:
+        raise ValueError("proof must be 256 bytes")
+    ok = _c_int(0)
+    check(lib().zkvc_verify(vk.handle, Xn.ctypes.data_as(_c_p), Yn.ctypes.data_as(_c_p), bytes(proof),
+                            ctypes.byref(ok)))
+    return bool(ok.value)
 
 
 def zkvc_prove_workspace_bytes(pk):
