@@ -163,6 +163,7 @@ int zkvc_pk_export(const zkvc_pk* pk, int query, size_t start, size_t count, uin
 /* Verifying-key entries: IC_v = [(beta A + alpha B + C)_v(tau)/gamma]1 (v = 0 .. l) and
  * the points [alpha]1, [beta]2, [gamma]2, [delta]2.  Host copy, no device work.
  */
+int zkvc_vk_info(const zkvc_vk* vk, int* a, int* n, int* b);
 #define ZKVC_VK_IC 0
 #define ZKVC_VK_ALPHA1 1
 #define ZKVC_VK_BETA2 2
@@ -185,6 +186,18 @@ int zkvc_vk_import(int a, int n, int b, const uint8_t alpha1[64], const uint8_t 
  * subgroup.  ZKVC_EIO for a malformed key.
  */
 int zkvc_verify(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint8_t proof[256], int* ok);
+
+/* Key files: a versioned header (magic, version, shape, counts), the payload, and an
+ * FNV-1a-64 checksum of the payload.  pk files hold the device representation of this
+ * library version (Montgomery-form bases with their precomputed windows) so that a key
+ * built once by zkvc_setup can be reloaded instead of recomputed; vk files hold the
+ * canonical encodings.  zkvc_pk_load allocates the key on the current device and
+ * synchronises; ZKVC_EIO for a missing, truncated, corrupt or mismatched file.
+ */
+int zkvc_pk_save(const zkvc_pk* pk, const char* path);
+int zkvc_pk_load(const char* path, void* stream, zkvc_pk** pk);
+int zkvc_vk_save(const zkvc_vk* vk, const char* path);
+int zkvc_vk_load(const char* path, zkvc_vk** vk);
 
 /* Prove (Sec. II) for the key's shape.
  *   d_X   a x n int8, row-major (device)          d_W  n x b int8, row-major (device)

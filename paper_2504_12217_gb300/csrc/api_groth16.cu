@@ -1,4 +1,6 @@
 // C-ABI entry points of the Groth16 layer: setup, prove, key export and release.
+#include <algorithm>
+#include <cstdio>
 #include <cstring>
 
 #include "groth16.h"
@@ -27,6 +29,63 @@ int vk_get(const zkvc_vk* vk, int* a, int* n, int* b, const uint8_t** alpha1, co
   *delta2 = vk->delta2.data();
   *ic = vk->ic.data();
   *n_ic = vk->ic.size() / 64;
+  return ZKVC_OK;
+}
+
+// ------------------------------------------------------------------ key files
+// Layout: 8-byte magic, u32 version, u32 header words, then i32 a, n, b, u32 log N,
+// u64 counts, the payload, and a trailing FNV-1a-64 checksum of the payload.
+static const char PK_MAGIC[8] = {'Z', 'K', 'V', 'C', 'P', 'K', '\0', '\1'};
+static const char VK_MAGIC[8] = {'Z', 'K', 'V', 'C', 'V', 'K', '\0', '\1'};
+static const uint32_t KEY_VERSION = 1;
+
+struct Fnv {
+  uint64_t h = 1469598103934665603ull;
+  void add(const void* p, size_t n) {
+    const uint8_t* b = reinterpret_cast<const uint8_t*>(p);
+    for (size_t i = 0; i < n; i++) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  }
+};
+
+struct FileGuard {
+  FILE* f = nullptr;
+  ~FileGuard() {
+    if (f) fclose(f);
+  }
+};
+
+static bool wr(FILE* f, const void* p, size_t n, Fnv* h) {
+  if (h) h->add(p, n);
+  return fwrite(p, 1, n, f) == n;
+}
+
+static bool rd(FILE* f, void* p, size_t n, Fnv* h) {
+  if (fread(p, 1, n, f) != n) return false;
+  if (h) h->add(p, n);
+  return true;
+}
+
+// device array <-> file in 64 MiB pieces through a host buffer
+static int dev_to_file(FILE* f, const void* d, size_t bytes, Fnv* h) {
+  std::vector<uint8_t> buf(std::min<size_t>(bytes, size_t(64) << 20));
+  for (size_t off = 0; off < bytes; off += buf.size()) {
+    size_t m = std::min(buf.size(), bytes - off);
+    ZK_CUDA(cudaMemcpy(buf.data(), reinterpret_cast<const uint8_t*>(d) + off, m, cudaMemcpyDeviceToHost));
+    ZK_CHECK(wr(f, buf.data(), m, h), ZKVC_EIO, "key file: write failed");
+  }
+  return ZKVC_OK;
+}
+
+static int file_to_dev(FILE* f, void* d, size_t bytes, Fnv* h) {
+  std::vector<uint8_t> buf(std::min<size_t>(bytes, size_t(64) << 20));
+  for (size_t off = 0; off < bytes; off += buf.size()) {
+    size_t m = std::min(buf.size(), bytes - off);
+    ZK_CHECK(rd(f, buf.data(), m, h), ZKVC_EIO, "key file: truncated payload");
+    ZK_CUDA(cudaMemcpy(reinterpret_cast<uint8_t*>(d) + off, buf.data(), m, cudaMemcpyHostToDevice));
+  }
   return ZKVC_OK;
 }
 
@@ -122,6 +181,15 @@ int zkvc_pk_export(const zkvc_pk* pk, int query, size_t start, size_t count, uin
   return export_points<Fp>(pk->g1, idx, out, 0);
 }
 
+int zkvc_vk_info(const zkvc_vk* vk, int* a, int* n, int* b) {
+  set_error("%s", "");
+  ZK_CHECK(vk, ZKVC_EINVAL, "vk_info: null key");
+  if (a) *a = vk->shape.a;
+  if (n) *n = vk->shape.n;
+  if (b) *b = vk->shape.b;
+  return ZKVC_OK;
+}
+
 int zkvc_vk_export(const zkvc_vk* vk, int query, size_t start, size_t count, uint8_t* out) {
   set_error("%s", "");
   ZK_CHECK(vk && (out || count == 0), ZKVC_EINVAL, "vk_export: null argument");
@@ -163,6 +231,138 @@ int zkvc_verify(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint
   set_error("%s", "");
   ZK_CHECK(vk && X && Y && proof && ok, ZKVC_EINVAL, "verify: null argument");
   return verify_impl(vk, X, Y, proof, ok);
+}
+
+int zkvc_pk_save(const zkvc_pk* pk, const char* path) {
+  set_error("%s", "");
+  ZK_CHECK(pk && path, ZKVC_EINVAL, "pk_save: null argument");
+  ZK_TRY(device_guard(pk->device));
+  ZK_CUDA(cudaDeviceSynchronize());
+  FileGuard g;
+  g.f = fopen(path, "wb");
+  ZK_CHECK(g.f, ZKVC_EIO, "pk_save: cannot open %s", path);
+  const Shape& sh = pk->shape;
+  int32_t dims[3] = {sh.a, sh.n, sh.b};
+  uint64_t counts[2] = {pk->lay.n_g1, pk->lay.n_g2};
+  uint32_t hdr[2] = {KEY_VERSION, 0};
+  ZK_CHECK(wr(g.f, PK_MAGIC, 8, nullptr) && wr(g.f, hdr, 8, nullptr) && wr(g.f, dims, 12, nullptr) &&
+               wr(g.f, &sh.logN, 4, nullptr) && wr(g.f, counts, 16, nullptr),
+           ZKVC_EIO, "pk_save: write failed");
+  Fnv h;
+  ZK_TRY(dev_to_file(g.f, pk->g1, pk->lay.n_g1 * sizeof(G1A), &h));
+  ZK_TRY(dev_to_file(g.f, pk->g2, pk->lay.n_g2 * sizeof(G2A), &h));
+  ZK_TRY(dev_to_file(g.f, pk->zA, size_t(sh.a) * sizeof(Fr), &h));
+  ZK_TRY(dev_to_file(g.f, pk->zB, size_t(sh.b) * sizeof(Fr), &h));
+  ZK_CHECK(wr(g.f, &h.h, 8, nullptr), ZKVC_EIO, "pk_save: write failed");
+  ZK_CHECK(fflush(g.f) == 0, ZKVC_EIO, "pk_save: flush failed");
+  return ZKVC_OK;
+}
+
+int zkvc_pk_load(const char* path, void* stream, zkvc_pk** out) {
+  set_error("%s", "");
+  ZK_CHECK(path && out, ZKVC_EINVAL, "pk_load: null argument");
+  (void)stream;
+  *out = nullptr;
+  FileGuard g;
+  g.f = fopen(path, "rb");
+  ZK_CHECK(g.f, ZKVC_EIO, "pk_load: cannot open %s", path);
+  char magic[8];
+  uint32_t hdr[2], logN;
+  int32_t dims[3];
+  uint64_t counts[2];
+  ZK_CHECK(rd(g.f, magic, 8, nullptr) && memcmp(magic, PK_MAGIC, 8) == 0, ZKVC_EIO, "pk_load: not a proving-key file");
+  ZK_CHECK(rd(g.f, hdr, 8, nullptr) && hdr[0] == KEY_VERSION, ZKVC_EIO, "pk_load: unsupported version");
+  ZK_CHECK(rd(g.f, dims, 12, nullptr) && rd(g.f, &logN, 4, nullptr) && rd(g.f, counts, 16, nullptr), ZKVC_EIO,
+           "pk_load: truncated header");
+  Shape sh;
+  ZK_CHECK(make_shape(dims[0], dims[1], dims[2], &sh) == ZKVC_OK, ZKVC_EIO, "pk_load: bad shape in header");
+  Layout lay = make_layout(sh);
+  ZK_CHECK(sh.logN == logN && lay.n_g1 == counts[0] && lay.n_g2 == counts[1], ZKVC_EIO,
+           "pk_load: header does not match the layout of this library version");
+  zkvc_pk* pk = new zkvc_pk();
+  pk->shape = sh;
+  pk->lay = lay;
+  int rc = ntt_domain(sh.logN, &pk->dom);
+  if (rc == ZKVC_OK) rc = cudaGetDevice(&pk->device) == cudaSuccess ? ZKVC_OK : ZKVC_ECUDA;
+  if (rc == ZKVC_OK && (cudaMalloc(&pk->g1, lay.n_g1 * sizeof(G1A)) != cudaSuccess ||
+                        cudaMalloc(&pk->g2, lay.n_g2 * sizeof(G2A)) != cudaSuccess ||
+                        cudaMalloc(&pk->zA, sh.a * sizeof(Fr)) != cudaSuccess ||
+                        cudaMalloc(&pk->zB, sh.b * sizeof(Fr)) != cudaSuccess)) {
+    set_error("pk_load: device allocation failed");
+    rc = ZKVC_ENOMEM;
+  }
+  Fnv h;
+  if (rc == ZKVC_OK) rc = file_to_dev(g.f, pk->g1, lay.n_g1 * sizeof(G1A), &h);
+  if (rc == ZKVC_OK) rc = file_to_dev(g.f, pk->g2, lay.n_g2 * sizeof(G2A), &h);
+  if (rc == ZKVC_OK) rc = file_to_dev(g.f, pk->zA, size_t(sh.a) * sizeof(Fr), &h);
+  if (rc == ZKVC_OK) rc = file_to_dev(g.f, pk->zB, size_t(sh.b) * sizeof(Fr), &h);
+  uint64_t sum = 0;
+  if (rc == ZKVC_OK && !(rd(g.f, &sum, 8, nullptr) && sum == h.h)) {
+    set_error("pk_load: checksum mismatch (corrupt file)");
+    rc = ZKVC_EIO;
+  }
+  if (rc != ZKVC_OK) {
+    zkvc_pk_free(pk);
+    return rc;
+  }
+  *out = pk;
+  return ZKVC_OK;
+}
+
+int zkvc_vk_save(const zkvc_vk* vk, const char* path) {
+  set_error("%s", "");
+  ZK_CHECK(vk && path, ZKVC_EINVAL, "vk_save: null argument");
+  FileGuard g;
+  g.f = fopen(path, "wb");
+  ZK_CHECK(g.f, ZKVC_EIO, "vk_save: cannot open %s", path);
+  int32_t dims[3] = {vk->shape.a, vk->shape.n, vk->shape.b};
+  uint64_t n_ic = vk->ic.size() / 64;
+  uint32_t hdr[2] = {KEY_VERSION, 0};
+  Fnv h;
+  bool ok = wr(g.f, VK_MAGIC, 8, nullptr) && wr(g.f, hdr, 8, nullptr) && wr(g.f, dims, 12, nullptr) &&
+            wr(g.f, &n_ic, 8, nullptr) && wr(g.f, vk->alpha1.data(), 64, &h) && wr(g.f, vk->beta2.data(), 128, &h) &&
+            wr(g.f, vk->gamma2.data(), 128, &h) && wr(g.f, vk->delta2.data(), 128, &h) &&
+            wr(g.f, vk->ic.data(), vk->ic.size(), &h) && wr(g.f, &h.h, 8, nullptr);
+  ZK_CHECK(ok && fflush(g.f) == 0, ZKVC_EIO, "vk_save: write failed");
+  return ZKVC_OK;
+}
+
+int zkvc_vk_load(const char* path, zkvc_vk** out) {
+  set_error("%s", "");
+  ZK_CHECK(path && out, ZKVC_EINVAL, "vk_load: null argument");
+  *out = nullptr;
+  FileGuard g;
+  g.f = fopen(path, "rb");
+  ZK_CHECK(g.f, ZKVC_EIO, "vk_load: cannot open %s", path);
+  char magic[8];
+  uint32_t hdr[2];
+  int32_t dims[3];
+  uint64_t n_ic = 0;
+  ZK_CHECK(rd(g.f, magic, 8, nullptr) && memcmp(magic, VK_MAGIC, 8) == 0, ZKVC_EIO, "vk_load: not a verifying-key file");
+  ZK_CHECK(rd(g.f, hdr, 8, nullptr) && hdr[0] == KEY_VERSION, ZKVC_EIO, "vk_load: unsupported version");
+  ZK_CHECK(rd(g.f, dims, 12, nullptr) && rd(g.f, &n_ic, 8, nullptr), ZKVC_EIO, "vk_load: truncated header");
+  Shape sh;
+  ZK_CHECK(make_shape(dims[0], dims[1], dims[2], &sh) == ZKVC_OK && n_ic == uint64_t(sh.l) + 1, ZKVC_EIO,
+           "vk_load: inconsistent header");
+  zkvc_vk* vk = new zkvc_vk();
+  vk->shape = sh;
+  vk->alpha1.resize(64);
+  vk->beta2.resize(128);
+  vk->gamma2.resize(128);
+  vk->delta2.resize(128);
+  vk->ic.resize(n_ic * 64);
+  Fnv h;
+  uint64_t sum = 0;
+  bool ok = rd(g.f, vk->alpha1.data(), 64, &h) && rd(g.f, vk->beta2.data(), 128, &h) &&
+            rd(g.f, vk->gamma2.data(), 128, &h) && rd(g.f, vk->delta2.data(), 128, &h) &&
+            rd(g.f, vk->ic.data(), vk->ic.size(), &h) && rd(g.f, &sum, 8, nullptr) && sum == h.h;
+  if (!ok) {
+    delete vk;
+    set_error("vk_load: truncated or corrupt file");
+    return ZKVC_EIO;
+  }
+  *out = vk;
+  return ZKVC_OK;
 }
 
 size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk) { return pk ? prove_workspace_bytes(pk) : 0; }

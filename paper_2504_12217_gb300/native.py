@@ -51,8 +51,13 @@ SIGNATURES = {
                               ctypes.POINTER(_c_u32), ctypes.POINTER(_c_sz), ctypes.POINTER(_c_sz)]),
     "zkvc_pk_export": (_c_int, [_c_p, _c_int, _c_sz, _c_sz, _c_p]),
     "zkvc_vk_export": (_c_int, [_c_p, _c_int, _c_sz, _c_sz, _c_p]),
+    "zkvc_vk_info": (_c_int, [_c_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "zkvc_vk_import": (_c_int, [_c_int, _c_int, _c_int, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, ctypes.POINTER(_c_p)]),
     "zkvc_verify": (_c_int, [_c_p, _c_p, _c_p, _c_p, ctypes.POINTER(_c_int)]),
+    "zkvc_pk_save": (_c_int, [_c_p, ctypes.c_char_p]),
+    "zkvc_pk_load": (_c_int, [ctypes.c_char_p, _c_p, ctypes.POINTER(_c_p)]),
+    "zkvc_vk_save": (_c_int, [_c_p, ctypes.c_char_p]),
+    "zkvc_vk_load": (_c_int, [ctypes.c_char_p, ctypes.POINTER(_c_p)]),
     "zkvc_prove_workspace_bytes": (_c_sz, [_c_p]),
     "zkvc_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
 }
@@ -296,6 +301,28 @@ def zkvc_verify(vk, X, Y, proof):
     check(lib().zkvc_verify(vk.handle, Xn.ctypes.data_as(_c_p), Yn.ctypes.data_as(_c_p), bytes(proof),
                             ctypes.byref(ok)))
     return bool(ok.value)
+
+
+def zkvc_pk_save(pk, path):
+    check(lib().zkvc_pk_save(pk.handle, os.fsencode(path)))
+
+
+def zkvc_pk_load(path):
+    pk = _c_p()
+    check(lib().zkvc_pk_load(os.fsencode(path), _stream(), ctypes.byref(pk)))
+    return ProvingKey(pk)
+
+
+def zkvc_vk_save(vk, path):
+    check(lib().zkvc_vk_save(vk.handle, os.fsencode(path)))
+
+
+def zkvc_vk_load(path):
+    vk = _c_p()
+    check(lib().zkvc_vk_load(os.fsencode(path), ctypes.byref(vk)))
+    a, n, b = _c_int(), _c_int(), _c_int()
+    check(lib().zkvc_vk_info(vk, ctypes.byref(a), ctypes.byref(n), ctypes.byref(b)))
+    return VerifyingKey(vk, (a.value, n.value, b.value))
 
 
 def zkvc_prove_workspace_bytes(pk):

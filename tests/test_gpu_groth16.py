@@ -145,3 +145,40 @@ def test_rejected_inputs(nv):
     with pytest.raises(nv.ZkvcError) as e:
         _gpu_prove(nv, pk, inst["X"], inst["W"], inputs.to_bytes32([bn.R, 1]))
     assert e.value.code == nv.ZKVC_EINVAL
+
+
+def test_pk_save_load_and_verify(nv, tmp_path):
+    """A reloaded proving key proves the same bytes; the library verifier accepts GPU
+    proofs and rejects a tampered statement; corrupt key files are refused."""
+    a, n, b = 3, 9, 6
+    inst = inputs.instance(4242, (a, n, b))
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(inst["toxic"]))
+    rs = inputs.to_bytes32(inst["rs"])
+    proof, Y = _gpu_prove(nv, pk, inst["X"], inst["W"], rs)
+    assert nv.zkvc_verify(vk, inst["X"], Y, proof)
+    Yt = Y.copy()
+    Yt[0, 0] ^= 1
+    assert not nv.zkvc_verify(vk, inst["X"], Yt, proof)
+    path = tmp_path / "k.pk"
+    nv.zkvc_pk_save(pk, str(path))
+    pk2 = nv.zkvc_pk_load(str(path))
+    assert pk2.shape == pk.shape
+    proof2, _ = _gpu_prove(nv, pk2, inst["X"], inst["W"], rs)
+    assert proof2 == proof
+    raw = bytearray(path.read_bytes())
+    raw[len(raw) // 2] ^= 1
+    bad = tmp_path / "bad.pk"
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(nv.ZkvcError) as e:
+        nv.zkvc_pk_load(str(bad))
+    assert e.value.code == nv.ZKVC_EIO
+
+
+def test_verifier_accepts_config2_gpu_proof(nv):
+    a, n, b = inputs.SHAPE_CFG2
+    inst = inputs.instance(inputs.SEED_CFG[2], (a, n, b))
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(inst["toxic"]))
+    proof, Y = _gpu_prove(nv, pk, inst["X"], inst["W"], inputs.to_bytes32(inst["rs"]))
+    assert nv.zkvc_verify(vk, inst["X"], Y, proof)
+    bad = proof[:192] + bn.g1_bytes(bn.g1_add(bn.g1_from_bytes(proof[192:]), bn.G1_GEN))
+    assert not nv.zkvc_verify(vk, inst["X"], Y, bad)

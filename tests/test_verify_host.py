@@ -94,3 +94,27 @@ def test_import_rejects_wrong_ic_count():
     nv = _util.native()
     with pytest.raises(nv.ZkvcError):
         nv.zkvc_vk_import(2, 2, 2, bytes(64), bytes(128), bytes(128), bytes(128), bytes(64 * 3))
+
+
+def test_vk_save_load_round_trip(setup1, tmp_path):
+    nv, vk, X, Y, proof = setup1
+    path = tmp_path / "key.vk"
+    nv.zkvc_vk_save(vk, str(path))
+    vk2 = nv.zkvc_vk_load(str(path))
+    assert vk2.shape == vk.shape
+    assert nv.zkvc_verify(vk2, X, Y, proof)
+    for q, cnt in ((nv.ZKVC_VK_IC, 3 * 5 + 3 * 4 + 1), (nv.ZKVC_VK_DELTA2, 1)):
+        assert nv.zkvc_vk_export(vk2, q, 0, cnt) == nv.zkvc_vk_export(vk, q, 0, cnt)
+    raw = bytearray(path.read_bytes())
+    raw[100] ^= 0x40                                # corrupt the payload
+    bad = tmp_path / "bad.vk"
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(nv.ZkvcError) as e:
+        nv.zkvc_vk_load(str(bad))
+    assert e.value.code == nv.ZKVC_EIO
+    short = tmp_path / "short.vk"
+    short.write_bytes(path.read_bytes()[:200])      # truncated
+    with pytest.raises(nv.ZkvcError):
+        nv.zkvc_vk_load(str(short))
+    with pytest.raises(nv.ZkvcError):
+        nv.zkvc_vk_load(str(tmp_path / "missing.vk"))
