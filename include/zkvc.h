@@ -111,6 +111,25 @@ int zkvc_msm_g1(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, voi
 int zkvc_msm_g2(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
                 uint8_t out[128], void* stream);
 
+/* Allocation-free variant of zkvc_msm_g1, for callers that cannot allocate device memory
+ * (code inside a CUDA graph being captured, runtimes without an allocator, processes
+ * whose device memory another framework has reserved).  The paper has no counterpart;
+ * it is a deployment convenience of this library.
+ *   - Same arguments and result as zkvc_msm_g1, minus the workspace: the scratch is one
+ *     8 MiB array in device memory, part of the library image, held on every GPU that
+ *     loads the library until the process exits.
+ *   - n <= ZKVC_MSM_NOALLOC_MAX_POINTS; larger n returns ZKVC_EINVAL.
+ *   - Calls no allocator (CUDA's or any framework's); the result is copied to `out` and
+ *     `stream` is synchronised.
+ *   - The first call on a device (with that device current) looks up the array's device
+ *     address and caches it; make that first call before any stream capture.
+ *   - All calls share the array, which keeps the previous call's contents (each call
+ *     initialises what it reads).  Calls whose GPU work overlaps race on it: issue them
+ *     one at a time.
+ */
+#define ZKVC_MSM_NOALLOC_MAX_POINTS 4096
+int zkvc_msm_g1_noalloc(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, uint8_t out[64], void* stream);
+
 /* ------------------------------------------------------------------ Groth16 over CRPC
  * The circuit (Sec. III-A general CRPC equation with Sec. III-B prefix sums) for
  * Y = X W, X of a x n and W of n x b (int8), has n multiplication constraints

@@ -134,15 +134,15 @@ static MsmPlan variable_base_plan(size_t n, const void* scalars) {
 }
 
 template <class F>
-static size_t msm_api_ws(size_t n) {
+size_t msm_api_ws(size_t n) {
   MsmPlan p = variable_base_plan(n, nullptr);
   return msm_workspace_bytes<F>(p) + ((n * sizeof(Affine<F>) + 255) & ~size_t(255)) + 2 * 256 +
          sizeof(XYZZ<F>) + sizeof(Affine<F>);
 }
 
 template <class F>
-static int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
-                   uint8_t* out, cudaStream_t st) {
+int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
+            uint8_t* out, cudaStream_t st) {
   ZK_CHECK(out != nullptr, ZKVC_EINVAL, "msm: null output");
   ZK_CHECK(n < (1ull << 31), ZKVC_EINVAL, "msm: n = %zu too large", n);
   if (n == 0) {
@@ -171,6 +171,9 @@ static int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, 
   ZK_CUDA(cudaStreamSynchronize(st));
   return ZKVC_OK;
 }
+
+template int msm_api<Fp>(const uint8_t*, const uint8_t*, size_t, void*, size_t, uint8_t*, cudaStream_t);
+template size_t msm_api_ws<Fp>(size_t);
 
 }  // namespace zkvc
 

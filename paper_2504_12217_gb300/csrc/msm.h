@@ -59,6 +59,14 @@ template <class F>
 int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results,
             cudaStream_t st, int accum_stage = -1);
 
+// The variable-base MSM behind zkvc_msm_g1 / zkvc_msm_g2: canonical points and scalars
+// in, canonical affine result out (host), using the caller's workspace.
+template <class F>
+int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
+            uint8_t* out, cudaStream_t st);
+template <class F>
+size_t msm_api_ws(size_t n);
+
 // Exclusive scan of n uint32 values into out[0..n] (out[n] = total); temp from the arena.
 int scan_u32(const uint32_t* in, uint32_t* out, size_t n, Arena& a, cudaStream_t st);
 size_t scan_u32_temp_bytes(size_t n);

@@ -44,6 +44,7 @@ SIGNATURES = {
     "zkvc_msm_workspace_bytes": (_c_sz, [_c_sz, _c_int]),
     "zkvc_msm_g1": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_msm_g2": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
+    "zkvc_msm_g1_noalloc": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_setup": (_c_int, [_c_int, _c_int, _c_int, _c_p, _c_p, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p)]),
     "zkvc_pk_free": (None, [_c_p]),
     "zkvc_vk_free": (None, [_c_p]),
@@ -214,6 +215,23 @@ def zkvc_msm_g1(points, scalars, workspace=None):
 def zkvc_msm_g2(points, scalars, workspace=None):
     """sum_i s_i Q_i over G2: points [n, 128], scalars [n, 32]; returns 128 bytes."""
     return _msm("zkvc_msm_g2", 2, points, scalars, workspace)
+
+
+ZKVC_MSM_NOALLOC_MAX_POINTS = 4096
+
+
+def zkvc_msm_g1_noalloc(points, scalars):
+    """sum_i s_i P_i over G1 for n <= ZKVC_MSM_NOALLOC_MAX_POINTS without any device
+    allocation (the library's built-in scratch array is used); returns 64 bytes."""
+    _u8(points, 64)
+    _u8(scalars, 32)
+    n = points.shape[0]
+    if scalars.shape[0] != n:
+        raise ValueError("points and scalars differ in length")
+    out = (ctypes.c_uint8 * 64)()
+    check(lib().zkvc_msm_g1_noalloc(_dev_ptr(points) if n else None, _dev_ptr(scalars) if n else None, n, out,
+                                    _stream()))
+    return bytes(out)
 
 
 # ------------------------------------------------------------------ Groth16 layer
