@@ -111,6 +111,19 @@ int zkvc_msm_g1(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, voi
 int zkvc_msm_g2(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
                 uint8_t out[128], void* stream);
 
+/* Fixed-base multiplication of the group generators: d_points[i] = [k_i] G for n
+ * canonical Fr scalars (device), written as canonical affine points (64 bytes for G1,
+ * 128 for G2).  The comb of 32 byte-windows that Gen (Sec. II) uses to build proving
+ * keys, exposed for callers that need many generator multiples.  Workspace:
+ * zkvc_generator_mul_workspace_bytes(n, group).  The first call on a device builds and
+ * caches the comb tables (allocates and synchronises).
+ */
+size_t zkvc_generator_mul_workspace_bytes(size_t n, int group);
+int zkvc_g1_generator_mul(const uint8_t* d_scalars, size_t n, uint8_t* d_points, void* d_ws, size_t ws_bytes,
+                          void* stream);
+int zkvc_g2_generator_mul(const uint8_t* d_scalars, size_t n, uint8_t* d_points, void* d_ws, size_t ws_bytes,
+                          void* stream);
+
 /* Allocation-free variant of zkvc_msm_g1, for callers that cannot allocate device memory
  * (code inside a CUDA graph being captured, runtimes without an allocator, processes
  * whose device memory another framework has reserved).  The paper has no counterpart;

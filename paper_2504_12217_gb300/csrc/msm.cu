@@ -24,7 +24,6 @@
 namespace zkvc {
 
 static constexpr uint32_t KEY_NONE = 0xffffffffu;
-static constexpr uint32_t T0 = 32;  // terms per level-0 chunk
 
 // ------------------------------------------------------------------ scan
 __global__ void k_scan_blocks(const uint32_t* in, size_t n_in, uint32_t* out, size_t n_out, uint32_t* sums) {
@@ -136,6 +135,7 @@ int msm_plan_finalize(MsmPlan& p) {
     p.max_nd = std::max(p.max_nd, nd);
   }
   ZK_CHECK(slot < 0xffffffffull, ZKVC_EINVAL, "msm: too many digit slots");
+  if (p.chunk == 0) p.chunk = slot < (2u << 20) ? 16u : 32u;
   p.slots = slot;
   p.points = pts;
   return ZKVC_OK;
@@ -238,7 +238,7 @@ __global__ void k_scatter(const uint32_t* keys, const uint32_t* vals, uint64_t n
   sorted[pos] = vals[i];
 }
 
-__global__ void k_chunks(const uint32_t* counts, uint32_t K, uint32_t* nch) {
+__global__ void k_chunks(const uint32_t* counts, uint32_t K, uint32_t T0, uint32_t* nch) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < K) nch[k] = (counts[k] + T0 - 1) / T0;
 }
@@ -259,14 +259,15 @@ __global__ void k_chunk_keys(const uint32_t* __restrict__ choff, uint32_t K, uin
   if (k >= K) return;
   uint32_t a = choff[k], b = choff[k + 1];
   for (uint32_t q = a; q < b; q++) chunk_key[q] = k;
-  if (b > a) atomicMax(max_chunks, b - a);
+  if (b > a + 1) atomicMax(max_chunks, b - a);
 }
 
 // level 0: chunk q sums up to T0 consecutive terms of its bucket (mixed additions)
 template <class F>
 __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ offs,
                                                 const uint32_t* __restrict__ choff, const uint32_t* __restrict__ chunk_key,
-                                                uint32_t K, const Affine<F>* __restrict__ bases, XYZZ<F>* part) {
+                                                uint32_t K, uint32_t T0, const Affine<F>* __restrict__ bases,
+                                                XYZZ<F>* part) {
   uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= choff[K]) return;
   uint32_t k = chunk_key[q];
@@ -286,6 +287,8 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
 // binary fold of the partial sums of each bucket, in place: at level l the partial at
 // local index i (a multiple of 2^(l+1)) absorbs the one at i + 2^l.  Levels at or above
 // log2 of the largest chunk count exit at once (the count is only known on the device).
+// (A block-per-heavy-bucket variant measured slower on GB300: barrier stalls while one
+// warp finishes each block's tree.)
 template <class F>
 __global__ void __launch_bounds__(256) k_fold(XYZZ<F>* part, const uint32_t* __restrict__ choff,
                                               const uint32_t* __restrict__ chunk_key, uint32_t K,
@@ -352,31 +355,55 @@ __global__ void __launch_bounds__(64) k_bits_scale(const XYZZ<F>* __restrict__ U
   st_field(D + s.dslot, x);
 }
 
-// In-place strided tree over segments: at level l, element i*2^(l+1) absorbs
-// element i*2^(l+1) + 2^l of the same segment.
+// In-place tree over segments: at level l, element i*2^(l+1) absorbs element
+// i*2^(l+1) + 2^l of the same segment.  Threads map only to pairs that exist at this
+// level (cum[s] counts the pairs of the segments before s), so no lane is idle.
 struct TreeSeg {
   uint32_t off;  // first element
   uint32_t len;  // elements
-  uint32_t cum;  // cumulative len/2 rounded up, for the thread mapping
 };
 
 template <class F>
-__global__ void __launch_bounds__(256) k_tree_level(XYZZ<F>* x, const TreeSeg* segs, uint32_t nseg, uint32_t total,
+__global__ void __launch_bounds__(256) k_tree_level(XYZZ<F>* x, const TreeSeg* __restrict__ segs,
+                                                    const uint32_t* __restrict__ cum, uint32_t nseg, uint32_t total,
                                                     uint32_t l) {
   uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   uint32_t lo = 0, hi = nseg - 1;
   while (lo < hi) {
     uint32_t mid = (lo + hi + 1) >> 1;
-    if (segs[mid].cum <= t) lo = mid; else hi = mid - 1;
+    if (cum[mid] <= t) lo = mid; else hi = mid - 1;
   }
   TreeSeg s = segs[lo];
-  uint32_t i = t - s.cum;
-  uint64_t a = uint64_t(i) << (l + 1), b = a + (1ull << l);
-  if (b >= s.len) return;
-  XYZZ<F> u = ld_field(x + s.off + a), v = ld_field(x + s.off + b);
-  st_field(x + s.off + a, p_add(u, v));
+  uint32_t i = t - cum[lo];
+  uint64_t a = s.off + (uint64_t(i) << (l + 1)), b = a + (1ull << l);
+  st_field(x + a, p_add(ld_field(x + a), ld_field(x + b)));
 }
+
+// host-side per-level pair counts of a tree over segments
+struct TreePlan {
+  std::vector<TreeSeg> segs;
+  std::vector<uint32_t> cum;     // levels x nseg
+  std::vector<uint32_t> totals;  // per level
+  uint32_t levels = 0;
+  void finish() {
+    uint32_t maxlen = 1;
+    for (auto& s : segs) maxlen = std::max(maxlen, s.len);
+    levels = 0;
+    while ((1u << levels) < maxlen) levels++;
+    cum.assign(size_t(levels) * segs.size(), 0);
+    totals.assign(levels, 0);
+    for (uint32_t l = 0; l < levels; l++) {
+      uint32_t acc = 0, step = 1u << l;
+      for (size_t s = 0; s < segs.size(); s++) {
+        cum[size_t(l) * segs.size() + s] = acc;
+        uint32_t len = segs[s].len;
+        acc += len > step ? (len - step + 2 * step - 1) / (2 * step) : 0;
+      }
+      totals[l] = acc;
+    }
+  }
+};
 
 // results[o] = sum_w 2^(c w) W[o][w] by Horner's rule (windows of variable-base outputs).
 struct OutItem {
@@ -406,55 +433,50 @@ struct Layout {
   MsmSeg* segs;
   MsmOut* outs;
   BitSeg* bsegs;
-  TreeSeg* utree;
-  TreeSeg* dtree;
+  TreeSeg *useg, *dseg;
+  uint32_t *ucum, *dcum;
   OutItem* oitems;
-  uint32_t qmax, nbits, utotal, dtotal, utree_threads, dtree_threads, umaxlen, dmaxlen;
+  uint32_t qmax, nbits, utotal, dtotal;
 };
 
 struct HostTables {
   std::vector<BitSeg> bsegs;
-  std::vector<TreeSeg> utree, dtree;
+  TreePlan ut, dt;
   std::vector<OutItem> oitems;
 };
 
 static void tables(const MsmPlan& p, HostTables& h, Layout& L) {
   h.bsegs.clear();
-  h.utree.clear();
-  h.dtree.clear();
+  h.ut = TreePlan();
+  h.dt = TreePlan();
   h.oitems.clear();
-  uint32_t uoff = 0, dslot = 0, ucum = 0, dcum = 0;
-  L.umaxlen = 1;
-  L.dmaxlen = 1;
+  uint32_t uoff = 0, dslot = 0;
   for (const auto& o : p.outs) {
     const uint32_t nb = 1u << (o.c - 1);
     h.oitems.push_back({dslot, o.c, o.win_keys, o.c});
     for (uint32_t w = 0; w < o.win_keys; w++) {
-      h.dtree.push_back({dslot, o.c, dcum});
-      dcum += (o.c + 1) / 2;
-      L.dmaxlen = std::max(L.dmaxlen, o.c);
+      h.dt.segs.push_back({dslot, o.c});
       for (uint32_t b = 0; b < o.c; b++) {
         uint32_t cnt = (b == o.c - 1) ? 1u : (1u << (o.c - 2));
         uint32_t pairs = (cnt + 1) / 2;
         h.bsegs.push_back({o.key_off + w * nb, b, o.c, uoff, dslot + b});
-        h.utree.push_back({uoff, pairs, ucum});
-        ucum += (pairs + 1) / 2;
-        L.umaxlen = std::max(L.umaxlen, pairs);
+        h.ut.segs.push_back({uoff, pairs});
         uoff += pairs;
       }
       dslot += o.c;
     }
   }
+  h.ut.finish();
+  h.dt.finish();
   L.nbits = (uint32_t)h.bsegs.size();
   L.utotal = uoff;
   L.dtotal = dslot;
-  L.utree_threads = ucum;
-  L.dtree_threads = dcum;
 }
 
 template <class F>
 static void layout(const MsmPlan& p, Arena& a, Layout& L, HostTables& h) {
   const size_t S = p.slots, K = p.keys;
+  const uint32_t T0 = p.chunk ? p.chunk : 32;
   L.keys = a.take<uint32_t>(S);
   L.vals = a.take<uint32_t>(S);
   L.sorted = a.take<uint32_t>(S);
@@ -473,8 +495,10 @@ static void layout(const MsmPlan& p, Arena& a, Layout& L, HostTables& h) {
   L.segs = a.take<MsmSeg>(p.segs.size());
   L.outs = a.take<MsmOut>(p.outs.size());
   L.bsegs = a.take<BitSeg>(h.bsegs.size());
-  L.utree = a.take<TreeSeg>(h.utree.size());
-  L.dtree = a.take<TreeSeg>(h.dtree.size());
+  L.useg = a.take<TreeSeg>(h.ut.segs.size());
+  L.ucum = a.take<uint32_t>(std::max<size_t>(1, h.ut.cum.size()));
+  L.dseg = a.take<TreeSeg>(h.dt.segs.size());
+  L.dcum = a.take<uint32_t>(std::max<size_t>(1, h.dt.cum.size()));
   L.oitems = a.take<OutItem>(h.oitems.size());
 }
 
@@ -489,10 +513,16 @@ size_t msm_workspace_bytes(const MsmPlan& p) {
   return a.off;
 }
 
-static uint32_t ceil_log2_u32(uint32_t x) {
-  uint32_t l = 0;
-  while ((1u << l) < x) l++;
-  return l;
+template <class F>
+static int run_tree(XYZZ<F>* x, const TreePlan& t, const TreeSeg* dsegs, const uint32_t* dcum, cudaStream_t st) {
+  const uint32_t nseg = (uint32_t)t.segs.size();
+  for (uint32_t l = 0; l < t.levels; l++) {
+    uint32_t total = t.totals[l];
+    if (total == 0) continue;
+    k_tree_level<F><<<(total + 255) / 256, 256, 0, st>>>(x, dsegs, dcum + size_t(l) * nseg, nseg, total, l); ZK_COUNT_LAUNCH();
+  }
+  ZK_CUDA(cudaGetLastError());
+  return ZKVC_OK;
 }
 
 template <class F>
@@ -508,12 +538,17 @@ int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes,
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace of %zu bytes is too small", ws_bytes);
   const uint32_t K = p.keys;
   const uint64_t S = p.slots;
+  const uint32_t T0 = p.chunk ? p.chunk : 32;
 
   ZK_CUDA(cudaMemcpyAsync(L.segs, p.segs.data(), p.segs.size() * sizeof(MsmSeg), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.outs, p.outs.data(), p.outs.size() * sizeof(MsmOut), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.bsegs, h.bsegs.data(), h.bsegs.size() * sizeof(BitSeg), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.utree, h.utree.data(), h.utree.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.dtree, h.dtree.data(), h.dtree.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
+  ZK_CUDA(cudaMemcpyAsync(L.useg, h.ut.segs.data(), h.ut.segs.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
+  if (!h.ut.cum.empty())
+    ZK_CUDA(cudaMemcpyAsync(L.ucum, h.ut.cum.data(), h.ut.cum.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  ZK_CUDA(cudaMemcpyAsync(L.dseg, h.dt.segs.data(), h.dt.segs.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
+  if (!h.dt.cum.empty())
+    ZK_CUDA(cudaMemcpyAsync(L.dcum, h.dt.cum.data(), h.dt.cum.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.oitems, h.oitems.data(), h.oitems.size() * sizeof(OutItem), cudaMemcpyHostToDevice, st));
 
   // digits -> terms
@@ -536,37 +571,35 @@ int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes,
     ZK_CUDA(cudaGetLastError());
   }
   // chunks of T0 terms per bucket
-  k_chunks<<<(K + 255) / 256, 256, 0, st>>>(L.counts, K, L.nch); ZK_COUNT_LAUNCH();
+  k_chunks<<<(K + 255) / 256, 256, 0, st>>>(L.counts, K, T0, L.nch); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   ZK_TRY(scan_u32(L.nch, L.choff, K, a, st));
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace too small for scans");
   k_chunk_keys<<<(K + 255) / 256, 256, 0, st>>>(L.choff, K, L.chunk_key, L.max_chunks); ZK_COUNT_LAUNCH();
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
-  unsigned qb = (L.qmax + 255) / 256;
+  unsigned qb = (L.qmax + 127) / 128;
   if (accum_stage >= 0) prof_mark(accum_stage, true, st);
-  k_accum0<F><<<qb, 256, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, bases, part); ZK_COUNT_LAUNCH();
+  k_accum0<F><<<qb, 128, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases, part); ZK_COUNT_LAUNCH();
   if (accum_stage >= 0) {
     prof_mark(accum_stage, false, st);
     if (uint32_t* hu = prof_units(accum_stage)) ZK_CUDA(cudaMemcpyAsync(hu, L.offs + K, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   }
   ZK_CUDA(cudaGetLastError());
-  // fold partials: enough levels for the largest possible chunk count
-  uint32_t levels = ceil_log2_u32((uint32_t)((S + T0 - 1) / T0 + 1));
+  // fold each bucket's partials into its first slot (enough levels for the largest
+  // possible chunk count; levels beyond the actual largest exit at once)
+  uint32_t levels = 0;
+  while ((uint64_t(1) << levels) < (S + T0 - 1) / T0 + 1) levels++;
   for (uint32_t l = 0; l < levels; l++) {
-    k_fold<F><<<qb, 256, 0, st>>>(part, L.choff, L.chunk_key, K, L.max_chunks, l); ZK_COUNT_LAUNCH();
+    k_fold<F><<<(L.qmax + 255) / 256, 256, 0, st>>>(part, L.choff, L.chunk_key, K, L.max_chunks, l); ZK_COUNT_LAUNCH();
   }
   ZK_CUDA(cudaGetLastError());
   // sum_v v B_v per (output, window) by bit decomposition
   XYZZ<F>* U = reinterpret_cast<XYZZ<F>*>(L.U);
   XYZZ<F>* D = reinterpret_cast<XYZZ<F>*>(L.D);
   k_bits_first<F><<<(L.utotal + 255) / 256, 256, 0, st>>>(part, L.counts, L.choff, L.bsegs, L.nbits, L.utotal, U); ZK_COUNT_LAUNCH();
-  for (uint32_t l = 0; (1u << l) < L.umaxlen; l++) {
-    k_tree_level<F><<<(L.utree_threads + 255) / 256, 256, 0, st>>>(U, L.utree, L.nbits, L.utree_threads, l); ZK_COUNT_LAUNCH();
-  }
+  ZK_TRY(run_tree<F>(U, h.ut, L.useg, L.ucum, st));
   k_bits_scale<F><<<(L.nbits + 63) / 64, 64, 0, st>>>(U, L.bsegs, L.nbits, D); ZK_COUNT_LAUNCH();
-  for (uint32_t l = 0; (1u << l) < L.dmaxlen; l++) {
-    k_tree_level<F><<<(L.dtree_threads + 255) / 256, 256, 0, st>>>(D, L.dtree, (uint32_t)h.dtree.size(), L.dtree_threads, l); ZK_COUNT_LAUNCH();
-  }
+  ZK_TRY(run_tree<F>(D, h.dt, L.dseg, L.dcum, st));
   k_combine_windows<F><<<((uint32_t)p.outs.size() + 63) / 64, 64, 0, st>>>(D, L.oitems, (uint32_t)p.outs.size(), results); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;

@@ -39,6 +39,7 @@ struct MsmOut {
 };
 
 struct MsmPlan {
+  uint32_t chunk = 0;  // terms per level-0 chunk (0: chosen from the slot count)
   std::vector<MsmSeg> segs;
   std::vector<MsmOut> outs;
   uint64_t slots = 0;

@@ -216,11 +216,11 @@ __device__ __forceinline__ G1A g1_affine_with(const G1J& p, const Fp& inv_zz_zzz
   return {f_mul(p.X, f_mul(inv_zz_zzz, p.ZZZ)), f_mul(p.Y, f_mul(inv_zz_zzz, p.ZZ))};
 }
 
-// Proof encoding.  Warp 0 converts A and C with one shared inversion (Montgomery's
-// trick); warp 1 converts B concurrently.
-__global__ void k_encode(const G1J* res1, const G2J* res2, uint8_t* proof) {
+// Proof encoding.  A = small[0]; C = small[1] + full[0].  Warp 0 converts A and C with
+// one shared inversion (Montgomery's trick); warp 1 converts B concurrently.
+__global__ void k_encode(const G1J* small, const G1J* full, const G2J* res2, uint8_t* proof) {
   if (threadIdx.x == 0) {
-    G1J A = ld_field(res1), C = ld_field(res1 + 1);
+    G1J A = ld_field(small), C = p_add(ld_field(small + 1), ld_field(full));
     Fp za = A.is_inf() ? Fp::one() : f_mul(A.ZZ, A.ZZZ);
     Fp zc = C.is_inf() ? Fp::one() : f_mul(C.ZZ, C.ZZZ);
     Fp inv = f_inv(f_mul(za, zc));
@@ -243,13 +243,11 @@ __global__ void k_encode(const G1J* res1, const G2J* res2, uint8_t* proof) {
 struct ProveBufs {
   Fr *ak, *bk, *yz, *S, *ev, *rs, *sw, *rw;
   int* flags;
-  G1J* res1;
+  G1J *res_small, *res_full;
   G2J* res2;
   uint8_t* proof;
-  void* ws1;
-  size_t ws1_bytes;
-  void* ws2;
-  size_t ws2_bytes;
+  void *ws_small, *ws_full, *ws2;
+  size_t ws_small_bytes, ws_full_bytes, ws2_bytes;
 };
 
 static MsmSeg seg_of(const Region& r, uint32_t first, uint32_t count, uint32_t out, int kind, const void* sc,
@@ -265,39 +263,53 @@ static MsmSeg seg_of(const Region& r, uint32_t first, uint32_t count, uint32_t o
   return s;
 }
 
-// G1 outputs: 0 = A, 1 = C.  G2 output: 0 = B.
+// Three MSM runs (see the file comment for the terms):
+//   small (G1): output 0 = A, output 1 = the small-scalar part of C (L over W and S);
+//   full  (G1): output 0 = the full-scalar part of C (H, s A_v, r B_e, s alpha, r beta,
+//               r s delta), whose buckets are uniformly filled;
+//   g2:         output 0 = B.
+// The small-scalar terms concentrate in buckets 1..128 and need long folds; running them
+// apart, on a side stream, keeps those folds off the critical path.
+struct Plans {
+  MsmPlan small, full, g2;
+};
+
 static void plans(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const int32_t* dY, const Fr* S, const Fr* h,
-                  const Fr* rs, const Fr* sw, const Fr* rw, MsmPlan* p1, MsmPlan* p2) {
+                  const Fr* rs, const Fr* sw, const Fr* rw, Plans* P) {
   const Shape& sh = pk->shape;
   const Region* g = pk->lay.g1;
   const uint32_t an = sh.a * sh.n, ab = sh.a * sh.b, nb = sh.n * sh.b;
-  p1->outs = {{ZKVC_C1, 1, 0, 0}, {ZKVC_C1, 1, 0, 0}};
-  p1->segs = {
+  P->small.outs = {{ZKVC_C1, 1, 0, 0}, {ZKVC_C1, 1, 0, 0}};
+  P->small.segs = {
       // A = [alpha]1 + sum_v w_v [A_v]1 + r [delta]1
       seg_of(g[R1_A], 0, 1, 0, SK_ONE, nullptr),
       seg_of(g[R1_A], 1, an, 0, SK_I8, dX),
       seg_of(g[R1_A], 1 + an, ab, 0, SK_I32, dY),
       seg_of(g[R1_ALPHA], 0, 1, 0, SK_ONE, nullptr),
       seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 0),
-      // C (see the file comment)
+      // C, small-scalar part: sum over the private variables of w_i [L_i]1
       seg_of(g[R1_LW], 0, nb, 1, SK_I8, dW),
       seg_of(g[R1_LS], 0, (uint32_t)(sh.n - 1), 1, SK_FR_MONT, S),
-      seg_of(g[R1_H], 0, (uint32_t)sh.N, 1, SK_FR_MONT, h, (uint32_t)sh.N - 1),
-      seg_of(g[R1_A], 0, sh.l + 1, 1, SK_FR_MONT, sw),
-      seg_of(g[R1_B], 0, nb, 1, SK_FR_MONT, rw),
-      seg_of(g[R1_ALPHA], 0, 1, 1, SK_FR_CANON, rs + 1),
-      seg_of(g[R1_BETA], 0, 1, 1, SK_FR_CANON, rs + 0),
-      seg_of(g[R1_DELTA], 0, 1, 1, SK_FR_CANON, rs + 2),
+  };
+  P->full.outs = {{ZKVC_C1, 1, 0, 0}};
+  P->full.segs = {
+      seg_of(g[R1_H], 0, (uint32_t)sh.N, 0, SK_FR_MONT, h, (uint32_t)sh.N - 1),
+      seg_of(g[R1_A], 0, sh.l + 1, 0, SK_FR_MONT, sw),
+      seg_of(g[R1_B], 0, nb, 0, SK_FR_MONT, rw),
+      seg_of(g[R1_ALPHA], 0, 1, 0, SK_FR_CANON, rs + 1),
+      seg_of(g[R1_BETA], 0, 1, 0, SK_FR_CANON, rs + 0),
+      seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 2),
   };
   const Region* g2 = pk->lay.g2;
-  p2->outs = {{ZKVC_C2, 1, 0, 0}};
-  p2->segs = {
+  P->g2.outs = {{ZKVC_C2, 1, 0, 0}};
+  P->g2.segs = {
       seg_of(g2[R2_B], 0, nb, 0, SK_I8, dW),
       seg_of(g2[R2_BETA], 0, 1, 0, SK_ONE, nullptr),
       seg_of(g2[R2_DELTA], 0, 1, 0, SK_FR_CANON, rs + 1),
   };
-  msm_plan_finalize(*p1);
-  msm_plan_finalize(*p2);
+  msm_plan_finalize(P->small);
+  msm_plan_finalize(P->full);
+  msm_plan_finalize(P->g2);
 }
 
 static size_t carve(const zkvc_pk* pk, void* base, size_t cap, ProveBufs* B, bool measuring) {
@@ -315,34 +327,39 @@ static size_t carve(const zkvc_pk* pk, void* base, size_t cap, ProveBufs* B, boo
   B->sw = a.take<Fr>(sh.l + 1);
   B->rw = a.take<Fr>(size_t(sh.n) * sh.b);
   B->flags = a.take<int>(4);
-  B->res1 = a.take<G1J>(2);
+  B->res_small = a.take<G1J>(2);
+  B->res_full = a.take<G1J>(1);
   B->res2 = a.take<G2J>(1);
   B->proof = a.take<uint8_t>(256);
-  MsmPlan p1, p2;
-  plans(pk, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &p1, &p2);
-  B->ws1_bytes = msm_workspace_bytes<Fp>(p1);
-  B->ws2_bytes = msm_workspace_bytes<Fp2>(p2);
-  B->ws1 = a.take<uint8_t>(B->ws1_bytes);
+  Plans P;
+  plans(pk, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &P);
+  B->ws_small_bytes = msm_workspace_bytes<Fp>(P.small);
+  B->ws_full_bytes = msm_workspace_bytes<Fp>(P.full);
+  B->ws2_bytes = msm_workspace_bytes<Fp2>(P.g2);
+  B->ws_small = a.take<uint8_t>(B->ws_small_bytes);
+  B->ws_full = a.take<uint8_t>(B->ws_full_bytes);
   B->ws2 = a.take<uint8_t>(B->ws2_bytes);
   return a.off;
 }
 
-// Per-thread side stream and fork/join events (created on first use on each device).
-struct SideStream {
+// Per-thread side streams and fork/join events (created on first use on each device).
+struct SideStreams {
   int dev = -1;
-  cudaStream_t st = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr};
 };
-static thread_local SideStream t_side;
+static thread_local SideStreams t_side;
 
-static int side_stream(SideStream** out) {
+static int side_streams(SideStreams** out) {
   int dev = 0;
   ZK_CUDA(cudaGetDevice(&dev));
-  if (t_side.st == nullptr || t_side.dev != dev) {
+  if (t_side.st[0] == nullptr || t_side.dev != dev) {
     t_side.dev = dev;
-    ZK_CUDA(cudaStreamCreateWithFlags(&t_side.st, cudaStreamNonBlocking));
-    ZK_CUDA(cudaEventCreateWithFlags(&t_side.fork, cudaEventDisableTiming));
-    ZK_CUDA(cudaEventCreateWithFlags(&t_side.join, cudaEventDisableTiming));
+    for (int i = 0; i < 2; i++) {
+      ZK_CUDA(cudaStreamCreateWithFlags(&t_side.st[i], cudaStreamNonBlocking));
+      ZK_CUDA(cudaEventCreateWithFlags(&t_side.fork[i], cudaEventDisableTiming));
+      ZK_CUDA(cudaEventCreateWithFlags(&t_side.join[i], cudaEventDisableTiming));
+    }
   }
   *out = &t_side;
   return ZKVC_OK;
@@ -371,17 +388,17 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   ZK_CUDA(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), st));
   ZK_CUDA(cudaMemcpyAsync(B.rs, rs_host, 64, cudaMemcpyHostToDevice, st));
   k_randomness<<<1, 1, 0, st>>>(B.rs, B.flags); ZK_COUNT_LAUNCH();
-  // G2 MSM on the side stream: it needs only W and s
-  SideStream* side = nullptr;
-  ZK_TRY(side_stream(&side));
-  MsmPlan p1, p2;
-  plans(pk, dX, dW, dY, B.S, Hev, B.rs, B.sw, B.rw, &p1, &p2);
-  ZK_CUDA(cudaEventRecord(side->fork, st));
-  ZK_CUDA(cudaStreamWaitEvent(side->st, side->fork, 0));
-  prof_mark(PS_MSM_G2, true, side->st);
-  ZK_TRY(msm_run<Fp2>(p2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st, PS_ACCUM_G2));
-  prof_mark(PS_MSM_G2, false, side->st);
-  ZK_CUDA(cudaEventRecord(side->join, side->st));
+  // G2 MSM on side stream 0: it needs only W and s
+  SideStreams* side = nullptr;
+  ZK_TRY(side_streams(&side));
+  Plans P;
+  plans(pk, dX, dW, dY, B.S, Hev, B.rs, B.sw, B.rw, &P);
+  ZK_CUDA(cudaEventRecord(side->fork[0], st));
+  ZK_CUDA(cudaStreamWaitEvent(side->st[0], side->fork[0], 0));
+  prof_mark(PS_MSM_G2, true, side->st[0]);
+  ZK_TRY(msm_run<Fp2>(P.g2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st[0], PS_ACCUM_G2));
+  prof_mark(PS_MSM_G2, false, side->st[0]);
+  ZK_CUDA(cudaEventRecord(side->join[0], side->st[0]));
   // 1. Y = X W
   dim3 mg((sh.b + 31) / 32, (sh.a + 31) / 32);
   k_matmul_i8<<<mg, dim3(32, 8), 0, st>>>(dX, dW, dY, sh.a, sh.n, sh.b); ZK_COUNT_LAUNCH();
@@ -389,7 +406,13 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
   k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz); ZK_COUNT_LAUNCH();
   k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, B.S, Aev, Bev, Cev, B.flags); ZK_COUNT_LAUNCH();
-  // 4. remaining domain evaluations
+  ZK_CUDA(cudaGetLastError());
+  // the small-scalar G1 MSM (A and the L part of C) on side stream 1: needs X, Y, W, S, r
+  ZK_CUDA(cudaEventRecord(side->fork[1], st));
+  ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->fork[1], 0));
+  ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
+  ZK_CUDA(cudaEventRecord(side->join[1], side->st[1]));
+  // 4. remaining domain evaluations and the scalars s w_v, r w_e
   size_t rest = N - sh.n;
   k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev); ZK_COUNT_LAUNCH();
   uint32_t nsc = sh.l + 1 + uint32_t(sh.n) * sh.b;
@@ -407,14 +430,15 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   k_check_h<<<1, 32, 0, st>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_NTT, false, st);
-  // 6. G1 MSM (A and C); join the G2 MSM
+  // 6. the full-scalar G1 MSM; join the side streams
   prof_mark(PS_MSM_G1, true, st);
-  ZK_TRY(msm_run<Fp>(p1, pk->g1, B.ws1, B.ws1_bytes, B.res1, st, PS_ACCUM_G1));
+  ZK_TRY(msm_run<Fp>(P.full, pk->g1, B.ws_full, B.ws_full_bytes, B.res_full, st, PS_ACCUM_G1));
   prof_mark(PS_MSM_G1, false, st);
-  ZK_CUDA(cudaStreamWaitEvent(st, side->join, 0));
+  ZK_CUDA(cudaStreamWaitEvent(st, side->join[0], 0));
+  ZK_CUDA(cudaStreamWaitEvent(st, side->join[1], 0));
   // 7. encode
   prof_mark(PS_COMBINE, true, st);
-  k_encode<<<1, 64, 0, st>>>(B.res1, B.res2, B.proof); ZK_COUNT_LAUNCH();
+  k_encode<<<1, 64, 0, st>>>(B.res_small, B.res_full, B.res2, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_COMBINE, false, st);
   int flags = 0;

@@ -294,10 +294,11 @@ __global__ void k_normalize(const XYZZ<F>* __restrict__ in, Affine<F>* out, size
 
 template <class F>
 __global__ void __launch_bounds__(256) k_fixed_base(const Fr* __restrict__ scal, size_t n, const Affine<F>* __restrict__ T,
-                                                    XYZZ<F>* out) {
+                                                    XYZZ<F>* out, int canonical = 0) {
   size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  Fr k = f_from_mont(ld_field(scal + i));
+  Fr k = ld_field(scal + i);
+  if (!canonical) k = f_from_mont(k);
   XYZZ<F> acc = XYZZ<F>::inf();
 #pragma unroll 1
   for (int w = 0; w < 32; w++) {
@@ -423,6 +424,57 @@ struct DevTemps {
     return ZKVC_OK;
   }
 };
+
+template <class F>
+__global__ void k_points_canonical(Affine<F>* p, size_t n) {
+  size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Affine<F> a = ld_field(p + i);
+  a.x = f_from_mont(a.x);
+  a.y = f_from_mont(a.y);
+  st_field(p + i, a);
+}
+
+static constexpr size_t GEN_CHUNK = size_t(1) << 20;
+
+template <class F>
+size_t generator_mul_ws(size_t n) {
+  return (n < GEN_CHUNK ? n : GEN_CHUNK) * sizeof(XYZZ<F>) + 256;
+}
+
+// out[i] = [k_i] G (canonical affine) for canonical scalars k_i: the fixed-base comb of
+// setup applied to caller data.
+template <class F>
+int generator_mul(const uint8_t* d_scalars, size_t n, uint8_t* d_out, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (n == 0) return ZKVC_OK;
+  ZK_CHECK(d_scalars && d_out && ws, ZKVC_EINVAL, "generator_mul: null pointer");
+  ZK_CHECK(ws_bytes >= generator_mul_ws<F>(n), ZKVC_EINVAL, "generator_mul: workspace too small");
+  G1A* T1 = nullptr;
+  G2A* T2 = nullptr;
+  ZK_TRY(fb_tables(&T1, &T2, st));
+  const Affine<F>* T;
+  if constexpr (sizeof(F) == sizeof(Fp))
+    T = T1;
+  else
+    T = T2;
+  const Fr* sc = reinterpret_cast<const Fr*>(d_scalars);
+  Affine<F>* out = reinterpret_cast<Affine<F>*>(d_out);
+  XYZZ<F>* tmp = reinterpret_cast<XYZZ<F>*>(ws);
+  for (size_t s = 0; s < n; s += GEN_CHUNK) {
+    size_t m = n - s < GEN_CHUNK ? n - s : GEN_CHUNK;
+    k_fixed_base<F><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(sc + s, m, T, tmp, 1); ZK_COUNT_LAUNCH();
+    ZK_CUDA(cudaGetLastError());
+    ZK_TRY(normalize<F>(tmp, out + s, m, st));
+  }
+  k_points_canonical<F><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, n); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaGetLastError());
+  return ZKVC_OK;
+}
+
+template size_t generator_mul_ws<Fp>(size_t);
+template size_t generator_mul_ws<Fp2>(size_t);
+template int generator_mul<Fp>(const uint8_t*, size_t, uint8_t*, void*, size_t, cudaStream_t);
+template int generator_mul<Fp2>(const uint8_t*, size_t, uint8_t*, void*, size_t, cudaStream_t);
 
 int setup_impl(int a, int n, int b, const uint8_t* toxic, cudaStream_t st, zkvc_pk** pk_out, zkvc_vk** vk_out) {
   Shape sh;

@@ -45,6 +45,9 @@ SIGNATURES = {
     "zkvc_msm_g1": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_msm_g2": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_msm_g1_noalloc": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_p]),
+    "zkvc_generator_mul_workspace_bytes": (_c_sz, [_c_sz, _c_int]),
+    "zkvc_g1_generator_mul": (_c_int, [_c_p, _c_sz, _c_p, _c_p, _c_sz, _c_p]),
+    "zkvc_g2_generator_mul": (_c_int, [_c_p, _c_sz, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_setup": (_c_int, [_c_int, _c_int, _c_int, _c_p, _c_p, ctypes.POINTER(_c_p), ctypes.POINTER(_c_p)]),
     "zkvc_pk_free": (None, [_c_p]),
     "zkvc_vk_free": (None, [_c_p]),
@@ -215,6 +218,29 @@ def zkvc_msm_g1(points, scalars, workspace=None):
 def zkvc_msm_g2(points, scalars, workspace=None):
     """sum_i s_i Q_i over G2: points [n, 128], scalars [n, 32]; returns 128 bytes."""
     return _msm("zkvc_msm_g2", 2, points, scalars, workspace)
+
+
+def _generator_mul(name, group, scalars):
+    torch = _torch()
+    _u8(scalars, 32)
+    n = scalars.shape[0]
+    width = 64 if group == 1 else 128
+    out = torch.empty((n, width), dtype=torch.uint8, device=scalars.device)
+    if n == 0:
+        return out
+    ws = torch.empty(lib().zkvc_generator_mul_workspace_bytes(n, group), dtype=torch.uint8, device=scalars.device)
+    check(getattr(lib(), name)(_dev_ptr(scalars), n, _dev_ptr(out), _dev_ptr(ws), ws.numel(), _stream()))
+    return out
+
+
+def zkvc_g1_generator_mul(scalars):
+    """[k_i] G1 for [n, 32] canonical scalars; returns [n, 64] canonical affine points."""
+    return _generator_mul("zkvc_g1_generator_mul", 1, scalars)
+
+
+def zkvc_g2_generator_mul(scalars):
+    """[k_i] G2 for [n, 32] canonical scalars; returns [n, 128] canonical affine points."""
+    return _generator_mul("zkvc_g2_generator_mul", 2, scalars)
 
 
 ZKVC_MSM_NOALLOC_MAX_POINTS = 4096

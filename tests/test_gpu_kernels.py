@@ -171,3 +171,13 @@ def test_msm_g2_random(nv, n):
         pts[3] = None
     got = nv.zkvc_msm_g2(_util.to_cuda(_util.g2_rows(pts)), _util.to_cuda(_util.ints_to_u8(sc)))
     assert got == bn.g2_bytes(bn.g2_msm(pts, sc))
+
+
+def test_generator_mul(nv):
+    rng = random.Random(31)
+    sc = [0, 1, 2, bn.R - 1, (bn.R - 1) // 2] + [rng.randrange(bn.R) for _ in range(200)]
+    t = _util.to_cuda(_util.ints_to_u8(sc))
+    g1 = nv.zkvc_g1_generator_mul(t).cpu().numpy()
+    assert bytes(g1.reshape(-1)) == b"".join(bn.g1_bytes(bn.g1_mul(bn.G1_GEN, k)) for k in sc)
+    g2 = nv.zkvc_g2_generator_mul(t[:40]).cpu().numpy()
+    assert bytes(g2.reshape(-1)) == b"".join(bn.g2_bytes(bn.g2_mul(bn.G2_GEN, k)) for k in sc[:40])
