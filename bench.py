@@ -202,6 +202,80 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ kernel sweep
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            m = json.load(fh)
+        return float(m["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def run_sweep(args):
+    """NTT / INTT / coset NTT at 2^16..2^24 and G1 (2^16..2^24) / G2 (2^16..2^20) MSMs on
+    uniform random Fr data, points = generator x seeded random scalars.  One JSON line."""
+    import torch
+
+    from paper_2504_12217_gb300 import native as nv
+
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    hbm, hbm_src = _peaks()
+    imad_peak = SMS * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6
+    g = torch.Generator(device="cuda").manual_seed(0x5A4B5643_00000003)
+
+    def rand_fr(n):
+        t = torch.randint(0, 256, (n, 32), dtype=torch.uint8, device="cuda", generator=g)
+        t[:, 31] &= 0x0F
+        return t
+
+    def time_it(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"ntt": [], "msm_g1": [], "msm_g2": []}
+    for logn in args.sweep_ntt:
+        n = 1 << logn
+        x = rand_fr(n)
+        passes = (logn + 9) // 10 + 1                       # DIF passes + the bit-reversal pass
+        for kind, name in ((0, "ntt"), (1, "intt"), (2, "coset_ntt")):
+            ms = time_it(lambda: nv.zkvc_ntt(x, kind), 5)
+            bytes_moved = passes * 2 * 32 * n
+            butterflies = (n // 2) * logn
+            out["ntt"].append({"log_n": logn, "kind": name, "ms": ms,
+                               "hbm_gbs": bytes_moved / ms / 1e6, "hbm_frac": bytes_moved / ms / 1e6 / hbm,
+                               "imad_frac": butterflies * MONT_IMAD / (ms / 1e3) / imad_peak})
+        del x
+        torch.cuda.empty_cache()
+    for group, sizes in ((1, args.sweep_g1), (2, args.sweep_g2)):
+        key = "msm_g1" if group == 1 else "msm_g2"
+        for logn in sizes:
+            n = 1 << logn
+            k = rand_fr(n)
+            pts = nv.zkvc_g1_generator_mul(k) if group == 1 else nv.zkvc_g2_generator_mul(k)
+            del k
+            sc = rand_fr(n)
+            ws = torch.empty(nv.zkvc_msm_workspace_bytes(n, group), dtype=torch.uint8, device="cuda")
+            fn = (lambda: nv.zkvc_msm_g1(pts, sc, ws)) if group == 1 else (lambda: nv.zkvc_msm_g2(pts, sc, ws))
+            ms = time_it(fn, 3 if logn < 22 else 1)
+            out[key].append({"log_n": logn, "ms": ms, "mpoints_per_s": n / ms / 1e3})
+            del pts, sc, ws
+            torch.cuda.empty_cache()
+    line = {"metric": "kernel sweep: NTT/INTT/coset-NTT and G1/G2 MSM over BN254", "unit": "ms",
+            "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src, "imad_peak_tops": imad_peak / 1e12,
+            "data": "synthetic (uniform Fr; points = generator x random scalars)", "sweep": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -346,7 +420,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="kernel sweep (NTT and MSM sizes) instead of proofs")
+    ap.add_argument("--sweep-ntt", type=int, nargs="*", default=[16, 18, 20, 22, 24])
+    ap.add_argument("--sweep-g1", type=int, nargs="*", default=[16, 18, 20, 22, 24])
+    ap.add_argument("--sweep-g2", type=int, nargs="*", default=[16, 18, 20])
     args = ap.parse_args()
+    if args.sweep:
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

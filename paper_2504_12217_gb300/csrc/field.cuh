@@ -275,36 +275,50 @@ __device__ __forceinline__ Field<C> f_mul(const Field<C>& a, const Field<C>& b) 
 template <class C>
 __device__ __forceinline__ Field<C> f_sqr(const Field<C>& a) { return f_mul(a, a); }
 
-// Compact Montgomery product: the same CIOS rows in a rolled loop (the multiplier's limbs
-// rotate through b[0]), called out of line.  About 100 instructions of code instead of
-// ~300 unrolled ones, for the long-latency reduction tails whose kernels run a handful of
-// point operations per launch and would otherwise stall fetching instructions.
+// Out-of-line Montgomery product with 64-bit accumulation: the same CIOS rows written
+// with 32 x 32 + 64-bit multiply-adds in plain C, which the compiler maps to wide IMADs
+// with little carry bookkeeping on the ALU pipe.  Called (not inlined) by the point
+// formulas: in the bucket-accumulation loop it gives 4.3 G mixed additions/s on GB300,
+// against 3.7 G/s for the carry-chain rows in a rolled loop and 2.9 G/s fully inlined
+// (whose ~48 KB of straight-line code stalls on instruction fetch).
 template <class C>
 __device__ __noinline__ Field<C> f_mulc(Field<C> a, Field<C> b) {
-  uint32_t t[9];
+  uint32_t t[10];
 #pragma unroll
-  for (int i = 0; i < 9; i++) t[i] = 0;
-  uint32_t m[8], bb[8];
+  for (int i = 0; i < 10; i++) t[i] = 0;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
-    m[i] = mod_limb<C>(i);
-    bb[i] = b.v[i];
-  }
-#pragma unroll 1
-  for (int i = 0; i < 8; i++) {
-    mac_row(t, a.v, bb[0]);
+    uint64_t c = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      uint64_t s = (uint64_t)a.v[j] * b.v[i] + t[j] + c;  // < 2^64
+      t[j] = (uint32_t)s;
+      c = s >> 32;
+    }
+    uint64_t s8 = (uint64_t)t[8] + c;
+    t[8] = (uint32_t)s8;
+    t[9] = (uint32_t)(s8 >> 32);
     uint32_t q = t[0] * C::INV;
-    mac_row(t, m, q);
+    c = ((uint64_t)q * mod_limb<C>(0) + t[0]) >> 32;  // low word cancels
 #pragma unroll
-    for (int j = 0; j < 8; j++) t[j] = t[j + 1];
-    t[8] = 0;
-#pragma unroll
-    for (int j = 0; j < 7; j++) bb[j] = bb[j + 1];
+    for (int j = 1; j < 8; j++) {
+      uint64_t s = (uint64_t)q * mod_limb<C>(j) + t[j] + c;
+      t[j - 1] = (uint32_t)s;
+      c = s >> 32;
+    }
+    uint64_t s7 = (uint64_t)t[8] + c;
+    t[7] = (uint32_t)s7;
+    t[8] = t[9] + (uint32_t)(s7 >> 32);
+    t[9] = 0;
   }
   Field<C> r, d;
+  uint32_t m[8];
 #pragma unroll
-  for (int i = 0; i < 8; i++) r.v[i] = t[i];
-  uint32_t br = sub8(d.v, r.v, m);
+  for (int i = 0; i < 8; i++) {
+    r.v[i] = t[i];
+    m[i] = mod_limb<C>(i);
+  }
+  uint32_t br = sub8(d.v, r.v, m);  // result < 2N < 2^255, so t[8] = 0 here
   return br ? r : d;
 }
 

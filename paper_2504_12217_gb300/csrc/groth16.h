@@ -28,6 +28,8 @@ enum G1Region : int {
   R1_LW,       // L-query, W variables                           n b     x1
   R1_LS,       // L-query, S variables (prefix sums)             n - 1   x16
   R1_H,        // H-query, bit-reversed positions                N       x16
+  R1_AY8,      // A-query, Y variables, 2^(8 w) multiples         a b     x4   (c = 8)
+  R1_DELTA8,   // [delta]1, 2^(8 w) multiples                    1       x32  (c = 8)
   R1_COUNT
 };
 

@@ -293,13 +293,17 @@ template <class F>
 __global__ void __launch_bounds__(256) k_fold(XYZZ<F>* part, const uint32_t* __restrict__ choff,
                                               const uint32_t* __restrict__ chunk_key, uint32_t K,
                                               const uint32_t* __restrict__ max_chunks, uint32_t l) {
-  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t step = 1u << l;
-  if (step >= *max_chunks || q >= choff[K]) return;
-  uint32_t k = chunk_key[q];
-  uint32_t base = choff[k], i = q - base, np = choff[k + 1] - base;
-  if ((i & (2 * step - 1)) != 0 || i + step >= np) return;
-  st_field(part + q, p_add(ld_field(part + q), ld_field(part + q + step)));
+  if (step >= *max_chunks) return;
+  const uint32_t total = choff[K];
+  // grid-stride over the chunk slots (the grid is small, so levels above the largest
+  // chunk count cost little more than the launch)
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    uint32_t k = chunk_key[q];
+    uint32_t base = choff[k], i = q - base, np = choff[k + 1] - base;
+    if ((i & (2 * step - 1)) != 0 || i + step >= np) continue;
+    st_field(part + q, p_add(ld_field(part + q), ld_field(part + q + step)));
+  }
 }
 
 template <class F>
@@ -590,7 +594,9 @@ int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes,
   uint32_t levels = 0;
   while ((uint64_t(1) << levels) < (S + T0 - 1) / T0 + 1) levels++;
   for (uint32_t l = 0; l < levels; l++) {
-    k_fold<F><<<(L.qmax + 255) / 256, 256, 0, st>>>(part, L.choff, L.chunk_key, K, L.max_chunks, l); ZK_COUNT_LAUNCH();
+    unsigned fb = (L.qmax + 255) / 256;
+    if (fb > 4 * 152) fb = 4 * 152;
+    k_fold<F><<<fb, 256, 0, st>>>(part, L.choff, L.chunk_key, K, L.max_chunks, l); ZK_COUNT_LAUNCH();
   }
   ZK_CUDA(cudaGetLastError());
   // sum_v v B_v per (output, window) by bit decomposition

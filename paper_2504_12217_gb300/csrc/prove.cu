@@ -216,11 +216,11 @@ __device__ __forceinline__ G1A g1_affine_with(const G1J& p, const Fp& inv_zz_zzz
   return {f_mul(p.X, f_mul(inv_zz_zzz, p.ZZZ)), f_mul(p.Y, f_mul(inv_zz_zzz, p.ZZ))};
 }
 
-// Proof encoding.  A = small[0]; C = small[1] + full[0].  Warp 0 converts A and C with
-// one shared inversion (Montgomery's trick); warp 1 converts B concurrently.
-__global__ void k_encode(const G1J* small, const G1J* full, const G2J* res2, uint8_t* proof) {
+// Proof encoding.  A = small[0]; C = small[1] + rest[0] + hq[0].  Warp 0 converts A and C
+// with one shared inversion (Montgomery's trick); warp 1 converts B concurrently.
+__global__ void k_encode(const G1J* small, const G1J* rest, const G1J* hq, const G2J* res2, uint8_t* proof) {
   if (threadIdx.x == 0) {
-    G1J A = ld_field(small), C = p_add(ld_field(small + 1), ld_field(full));
+    G1J A = ld_field(small), C = p_add(p_add(ld_field(small + 1), ld_field(rest)), ld_field(hq));
     Fp za = A.is_inf() ? Fp::one() : f_mul(A.ZZ, A.ZZZ);
     Fp zc = C.is_inf() ? Fp::one() : f_mul(C.ZZ, C.ZZZ);
     Fp inv = f_inv(f_mul(za, zc));
@@ -243,11 +243,11 @@ __global__ void k_encode(const G1J* small, const G1J* full, const G2J* res2, uin
 struct ProveBufs {
   Fr *ak, *bk, *yz, *S, *ev, *rs, *sw, *rw;
   int* flags;
-  G1J *res_small, *res_full;
+  G1J *res_small, *res_rest, *res_h;
   G2J* res2;
   uint8_t* proof;
-  void *ws_small, *ws_full, *ws2;
-  size_t ws_small_bytes, ws_full_bytes, ws2_bytes;
+  void *ws_small, *ws_rest, *ws_h, *ws2;
+  size_t ws_small_bytes, ws_rest_bytes, ws_h_bytes, ws2_bytes;
 };
 
 static MsmSeg seg_of(const Region& r, uint32_t first, uint32_t count, uint32_t out, int kind, const void* sc,
@@ -263,15 +263,16 @@ static MsmSeg seg_of(const Region& r, uint32_t first, uint32_t count, uint32_t o
   return s;
 }
 
-// Three MSM runs (see the file comment for the terms):
-//   small (G1): output 0 = A, output 1 = the small-scalar part of C (L over W and S);
-//   full  (G1): output 0 = the full-scalar part of C (H, s A_v, r B_e, s alpha, r beta,
-//               r s delta), whose buckets are uniformly filled;
+// Four MSM runs (see the file comment for the terms), on four streams:
+//   small (G1): output 0 = A, output 1 = the int8 part of C (L over the W variables);
+//   rest  (G1): the full-scalar part of C known right after the witness (L over S,
+//               s A_v, r B_e, s alpha, r beta, r s delta);
+//   h     (G1): the H part of C, after the NTTs;
 //   g2:         output 0 = B.
-// The small-scalar terms concentrate in buckets 1..128 and need long folds; running them
-// apart, on a side stream, keeps those folds off the critical path.
+// The small-scalar terms concentrate in buckets 1..128 and need long folds; "rest" does
+// not depend on h, so it overlaps the NTTs; only "h" follows them on the critical path.
 struct Plans {
-  MsmPlan small, full, g2;
+  MsmPlan small, rest, h, g2;
 };
 
 static void plans(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const int32_t* dY, const Fr* S, const Fr* h,
@@ -279,21 +280,24 @@ static void plans(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const i
   const Shape& sh = pk->shape;
   const Region* g = pk->lay.g1;
   const uint32_t an = sh.a * sh.n, ab = sh.a * sh.b, nb = sh.n * sh.b;
-  P->small.outs = {{ZKVC_C1, 1, 0, 0}, {ZKVC_C1, 1, 0, 0}};
+  // 8-bit digits: 128 buckets per output.  X and the constant one use window 0 of the
+  // A-query (stride 16); Y and r [delta]1 use their own 2^(8 w) regions.
+  P->small.outs = {{8, 1, 0, 0}, {8, 1, 0, 0}};
   P->small.segs = {
       // A = [alpha]1 + sum_v w_v [A_v]1 + r [delta]1
       seg_of(g[R1_A], 0, 1, 0, SK_ONE, nullptr),
       seg_of(g[R1_A], 1, an, 0, SK_I8, dX),
-      seg_of(g[R1_A], 1 + an, ab, 0, SK_I32, dY),
+      seg_of(g[R1_AY8], 0, ab, 0, SK_I32, dY),
       seg_of(g[R1_ALPHA], 0, 1, 0, SK_ONE, nullptr),
-      seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 0),
-      // C, small-scalar part: sum over the private variables of w_i [L_i]1
+      seg_of(g[R1_DELTA8], 0, 1, 0, SK_FR_CANON, rs + 0),
+      // C, int8 part: sum over the W variables of w_e [L_e]1
       seg_of(g[R1_LW], 0, nb, 1, SK_I8, dW),
-      seg_of(g[R1_LS], 0, (uint32_t)(sh.n - 1), 1, SK_FR_MONT, S),
   };
-  P->full.outs = {{ZKVC_C1, 1, 0, 0}};
-  P->full.segs = {
-      seg_of(g[R1_H], 0, (uint32_t)sh.N, 0, SK_FR_MONT, h, (uint32_t)sh.N - 1),
+  P->h.outs = {{ZKVC_C1, 1, 0, 0}};
+  P->h.segs = {seg_of(g[R1_H], 0, (uint32_t)sh.N, 0, SK_FR_MONT, h, (uint32_t)sh.N - 1)};
+  P->rest.outs = {{ZKVC_C1, 1, 0, 0}};
+  P->rest.segs = {
+      seg_of(g[R1_LS], 0, (uint32_t)(sh.n - 1), 0, SK_FR_MONT, S),
       seg_of(g[R1_A], 0, sh.l + 1, 0, SK_FR_MONT, sw),
       seg_of(g[R1_B], 0, nb, 0, SK_FR_MONT, rw),
       seg_of(g[R1_ALPHA], 0, 1, 0, SK_FR_CANON, rs + 1),
@@ -308,7 +312,8 @@ static void plans(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const i
       seg_of(g2[R2_DELTA], 0, 1, 0, SK_FR_CANON, rs + 1),
   };
   msm_plan_finalize(P->small);
-  msm_plan_finalize(P->full);
+  msm_plan_finalize(P->rest);
+  msm_plan_finalize(P->h);
   msm_plan_finalize(P->g2);
 }
 
@@ -328,25 +333,29 @@ static size_t carve(const zkvc_pk* pk, void* base, size_t cap, ProveBufs* B, boo
   B->rw = a.take<Fr>(size_t(sh.n) * sh.b);
   B->flags = a.take<int>(4);
   B->res_small = a.take<G1J>(2);
-  B->res_full = a.take<G1J>(1);
+  B->res_rest = a.take<G1J>(1);
+  B->res_h = a.take<G1J>(1);
   B->res2 = a.take<G2J>(1);
   B->proof = a.take<uint8_t>(256);
   Plans P;
   plans(pk, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &P);
   B->ws_small_bytes = msm_workspace_bytes<Fp>(P.small);
-  B->ws_full_bytes = msm_workspace_bytes<Fp>(P.full);
+  B->ws_rest_bytes = msm_workspace_bytes<Fp>(P.rest);
+  B->ws_h_bytes = msm_workspace_bytes<Fp>(P.h);
   B->ws2_bytes = msm_workspace_bytes<Fp2>(P.g2);
   B->ws_small = a.take<uint8_t>(B->ws_small_bytes);
-  B->ws_full = a.take<uint8_t>(B->ws_full_bytes);
+  B->ws_rest = a.take<uint8_t>(B->ws_rest_bytes);
+  B->ws_h = a.take<uint8_t>(B->ws_h_bytes);
   B->ws2 = a.take<uint8_t>(B->ws2_bytes);
   return a.off;
 }
 
 // Per-thread side streams and fork/join events (created on first use on each device).
+static constexpr int NSIDE = 4;
 struct SideStreams {
   int dev = -1;
-  cudaStream_t st[2] = {nullptr, nullptr};
-  cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr};
+  cudaStream_t st[NSIDE] = {};
+  cudaEvent_t fork[NSIDE] = {}, join[NSIDE] = {};
 };
 static thread_local SideStreams t_side;
 
@@ -355,8 +364,13 @@ static int side_streams(SideStreams** out) {
   ZK_CUDA(cudaGetDevice(&dev));
   if (t_side.st[0] == nullptr || t_side.dev != dev) {
     t_side.dev = dev;
-    for (int i = 0; i < 2; i++) {
-      ZK_CUDA(cudaStreamCreateWithFlags(&t_side.st[i], cudaStreamNonBlocking));
+    int lo = 0, hi = 0;
+    ZK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    for (int i = 0; i < NSIDE; i++) {
+      // Streams 0, 1 and 3 carry the latency-bound MSMs (G2; A and the int8 part of C) and
+      // the critical chain NTT -> H MSM: their blocks get precedence.  Stream 2 carries the
+      // throughput-bound "rest" MSM at the default priority and fills the gaps.
+      ZK_CUDA(cudaStreamCreateWithPriority(&t_side.st[i], cudaStreamNonBlocking, i == 2 ? lo : hi));
       ZK_CUDA(cudaEventCreateWithFlags(&t_side.fork[i], cudaEventDisableTiming));
       ZK_CUDA(cudaEventCreateWithFlags(&t_side.join[i], cudaEventDisableTiming));
     }
@@ -407,7 +421,7 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz); ZK_COUNT_LAUNCH();
   k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, B.S, Aev, Bev, Cev, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  // the small-scalar G1 MSM (A and the L part of C) on side stream 1: needs X, Y, W, S, r
+  // the small-scalar G1 MSM (A and the int8 part of C) on side stream 1: needs X, Y, W, r
   ZK_CUDA(cudaEventRecord(side->fork[1], st));
   ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->fork[1], 0));
   ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
@@ -420,25 +434,32 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
                                                       B.rw); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_WITNESS, false, st);
-  // 5. quotient
-  prof_mark(PS_NTT, true, st);
+  // the full-scalar G1 terms that need no h, on side stream 2 (overlapping the NTTs)
+  ZK_CUDA(cudaEventRecord(side->fork[2], st));
+  ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->fork[2], 0));
+  prof_mark(PS_MSM_G1, true, side->st[2]);
+  ZK_TRY(msm_run<Fp>(P.rest, pk->g1, B.ws_rest, B.ws_rest_bytes, B.res_rest, side->st[2], PS_ACCUM_G1));
+  prof_mark(PS_MSM_G1, false, side->st[2]);
+  ZK_CUDA(cudaEventRecord(side->join[2], side->st[2]));
+  // 5-6. quotient and the H part of C on side stream 3 (the critical chain)
+  ZK_CUDA(cudaEventRecord(side->fork[3], st));
+  ZK_CUDA(cudaStreamWaitEvent(side->st[3], side->fork[3], 0));
+  cudaStream_t s3 = side->st[3];
+  prof_mark(PS_NTT, true, s3);
   const NttDomain* d = pk->dom;
-  ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, st));
-  ZK_TRY(ntt_dit(Aev, 3, N, d, false, st));
-  ZK_TRY(ntt_quotient(Aev, Bev, Cev, Hev, d, st));
-  ZK_TRY(ntt_dif(Hev, 1, N, d, true, SC_NONE, SC_NGI, false, st));
-  k_check_h<<<1, 32, 0, st>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
+  ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, s3));
+  ZK_TRY(ntt_dit(Aev, 3, N, d, false, s3));
+  ZK_TRY(ntt_quotient(Aev, Bev, Cev, Hev, d, s3));
+  ZK_TRY(ntt_dif(Hev, 1, N, d, true, SC_NONE, SC_NGI, false, s3));
+  k_check_h<<<1, 32, 0, s3>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  prof_mark(PS_NTT, false, st);
-  // 6. the full-scalar G1 MSM; join the side streams
-  prof_mark(PS_MSM_G1, true, st);
-  ZK_TRY(msm_run<Fp>(P.full, pk->g1, B.ws_full, B.ws_full_bytes, B.res_full, st, PS_ACCUM_G1));
-  prof_mark(PS_MSM_G1, false, st);
-  ZK_CUDA(cudaStreamWaitEvent(st, side->join[0], 0));
-  ZK_CUDA(cudaStreamWaitEvent(st, side->join[1], 0));
+  prof_mark(PS_NTT, false, s3);
+  ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3));
+  ZK_CUDA(cudaEventRecord(side->join[3], s3));
+  for (int i = 0; i < NSIDE; i++) ZK_CUDA(cudaStreamWaitEvent(st, side->join[i], 0));
   // 7. encode
   prof_mark(PS_COMBINE, true, st);
-  k_encode<<<1, 64, 0, st>>>(B.res_small, B.res_full, B.res2, B.proof); ZK_COUNT_LAUNCH();
+  k_encode<<<1, 64, 0, st>>>(B.res_small, B.res_rest, B.res_h, B.res2, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_COMBINE, false, st);
   int flags = 0;

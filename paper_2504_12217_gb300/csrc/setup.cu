@@ -41,12 +41,13 @@ int make_shape(int a, int n, int b, Shape* s) {
 
 Layout make_layout(const Shape& s) {
   Layout L{};
-  const uint32_t nb = s.n * s.b;
-  const uint32_t cnt1[R1_COUNT] = {s.l + 1, 1, 1, 1, nb, nb, (uint32_t)(s.n - 1), (uint32_t)s.N};
-  const uint32_t win1[R1_COUNT] = {ZKVC_W1, ZKVC_W1, ZKVC_W1, ZKVC_W1, ZKVC_W1, 1, ZKVC_W1, ZKVC_W1};
+  const uint32_t nb = s.n * s.b, ab = s.a * s.b;
+  const uint32_t cnt1[R1_COUNT] = {s.l + 1, 1, 1, 1, nb, nb, (uint32_t)(s.n - 1), (uint32_t)s.N, ab, 1};
+  const uint32_t win1[R1_COUNT] = {ZKVC_W1, ZKVC_W1, ZKVC_W1, ZKVC_W1, ZKVC_W1, 1, ZKVC_W1, ZKVC_W1, 4, 32};
+  const uint32_t c1[R1_COUNT] = {ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, 8, 8};
   uint64_t off = 0;
   for (int r = 0; r < R1_COUNT; r++) {
-    L.g1[r] = {off, cnt1[r], win1[r], ZKVC_C1, r};
+    L.g1[r] = {off, cnt1[r], win1[r], c1[r], r};
     off += uint64_t(cnt1[r]) * win1[r];
   }
   L.n_g1 = off;
@@ -203,6 +204,8 @@ __global__ void k_query_scalars(RegionTab tab, int group, const SetupConsts* __r
         if (j + 1 < (uint32_t)sh.N) s = f_mul(pow_u32(sc.tau, j), f_mul(sc.tN1, sc.dinv));
         break;
       }
+      case R1_AY8: s = ld_field(L + n + 1 + an + e); break;
+      case R1_DELTA8: s = sc.delta; break;
     }
   } else if (group == GRP_G2) {
     switch (rg.kind) {
