@@ -413,6 +413,138 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched workload
+def shape_seed(base, shape):
+    a, n, b = shape
+    return base ^ (a << 40) ^ (n << 20) ^ b
+
+
+def run_batched(args):
+    """64 seeded proofs of uneven [tokens, dim] x [dim, dim | 4 dim] shapes per step, one
+    batched call (captured CUDA graph after autotuning).  One JSON line."""
+    import torch
+
+    from paper_2504_12217_gb300 import inputs
+    from paper_2504_12217_gb300 import native as nv
+
+    local = _env_int("LOCAL_RANK", 0)
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    shapes = inputs.batch_shapes(inputs.SEED_CFG[4] + rank)
+    t0 = time.perf_counter()
+    keys = {}
+    for s in dict.fromkeys(shapes):
+        keys[s] = nv.zkvc_setup(*s, inputs.to_bytes32(inputs.setup_values(shape_seed(inputs.SEED_CFG[4], s))))[0]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    sets = []
+    for v in range(2):
+        insts = [inputs.instance(inputs.SEED_CFG[4] + 1000 * (v + 1) + i, s) for i, s in enumerate(shapes)]
+        sets.append(([torch.from_numpy(t["X"]).cuda() for t in insts], [torch.from_numpy(t["W"]).cuda() for t in insts],
+                     [inputs.to_bytes32(t["rs"]) for t in insts], insts))
+    Ys = [torch.empty((s[0], s[2]), dtype=torch.int32, device="cuda") for s in shapes]
+    t0 = time.perf_counter()
+    batch = nv.Batch([keys[s] for s in shapes], flags=nv.ZKVC_BATCH_AUTOTUNE)
+    nv.zkvc_set_wait_timeout_ms(120000)
+    batch.prove(sets[0][0], sets[0][1], sets[0][2], Ys)  # autotune + capture
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    for i in range(args.warmup):
+        x = sets[i % 2]
+        batch.prove(x[0], x[1], x[2], Ys)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = nv.zkvc_kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        x = sets[i % 2]
+        flush.zero_()
+        evs[i][0].record()
+        batch.prove(x[0], x[1], x[2], Ys)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = nv.zkvc_kernel_launches() - launches0
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    count = len(shapes)
+    value = world * count * args.steps / total_s
+    terms = batch.terms()
+
+    # end to end: pinned host matrices copied in, Y and proofs read back, every step
+    Xh = [[x.cpu().pin_memory() for x in st[0]] for st in sets]
+    Wh = [[w.cpu().pin_memory() for w in st[1]] for st in sets]
+    Yh = [torch.empty(tuple(y.shape), dtype=torch.int32).pin_memory() for y in Ys]
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        x = sets[i % 2]
+        for d, h in zip(x[0], Xh[i % 2]):
+            d.copy_(h, non_blocking=True)
+        for d, h in zip(x[1], Wh[i % 2]):
+            d.copy_(h, non_blocking=True)
+        batch.prove(x[0], x[1], x[2], Ys)
+        for h, d in zip(Yh, Ys):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(s[0] * s[1] + s[1] * s[2] for s in shapes)
+    d2h = sum(256 + 4 * s[0] * s[2] for s in shapes)
+    # parity spot check of the last step against the one-proof prover (not timed)
+    x = sets[(args.steps - 1) % 2]
+    proofs, _ = batch.prove(x[0], x[1], x[2], Ys)
+    p0, _ = nv.zkvc_prove(keys[shapes[0]], x[0][0], x[1][0], x[2][0])
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    peak = SMS * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    work = (terms["small"] + terms["main"]) * G1_MADD_PRODUCTS * MONT_IMAD + terms["g2"] * G2_MADD_PRODUCTS * MONT_IMAD
+    per_step = total_s / args.steps
+    srt = sorted(step_ms)
+    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+    info = batch.info()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32 limbs (exact Fr/Fp arithmetic)", "data": "synthetic",
+        "config": {"workload": "crpc_groth16_bn254_batched_64mix", "instances": count,
+                   "distinct_shapes": len(keys), "shape_set": "a in {49,64,128,197}, n in {192,320,384,768}, b in {n,4n}",
+                   "l2": "flushed by a 256 MiB write between steps", "parallelism": f"replicas x{world}",
+                   "graph": True, "tuning": batch.get_tuning()},
+        "latency_ms": {"p50_batch": statistics.median(step_ms), "p99_batch": p99, "min": srt[0], "max": srt[-1]},
+        "e2e": {"value": world * count * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "batch_roofline": {"bound": "alu", "scope": "whole batch (all kernels, overlapped)",
+                           "achieved": work / per_step / 1e12, "peak": peak, "unit": "TIMAD/s",
+                           "frac": work / per_step / 1e12 / peak, "bucket_terms": terms},
+        "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+        "graph_kernels": info["graph_launches"], "device_bytes": info["device_bytes"],
+        "clocks": clk, "setup_s": setup_s, "autotune_and_capture_s": tune_s,
+        "spot_check_vs_one_proof_prover": proofs[0] == p0,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -424,9 +556,13 @@ def main():
     ap.add_argument("--sweep-ntt", type=int, nargs="*", default=[16, 18, 20, 22, 24])
     ap.add_argument("--sweep-g1", type=int, nargs="*", default=[16, 18, 20, 22, 24])
     ap.add_argument("--sweep-g2", type=int, nargs="*", default=[16, 18, 20])
+    ap.add_argument("--workload", choices=["plain", "batched"], default="plain",
+                    help="plain: one [49,320]x[320,512] proof per step; batched: 64 mixed shapes per step")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)
+    if args.workload == "batched" and args.impl == "ours":
+        return run_batched(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

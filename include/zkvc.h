@@ -245,6 +245,68 @@ size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk);
 int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64], int32_t* d_Y,
                void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream);
 
+/* ------------------------------------------------------------------ batched proving
+ * Many proofs of uneven shapes in one launch sequence (the paper proves the matmul
+ * layers of a network, Sec. V, each as its own CRPC circuit; batching them is this
+ * library's throughput form of Prove).  A batch is built once for an ordered list of
+ * proving keys (repeats allowed, all on the current device) and then proves one
+ * instance per key per call.  Proofs are byte-identical to zkvc_prove's for the same
+ * (pk, X, W, r, s).
+ *
+ * zkvc_batch_create allocates every device buffer the batch needs (ZKVC_ENOMEM if the
+ * device cannot hold them) plus pinned host staging, and synchronises.  Flags:
+ *   ZKVC_BATCH_AUTOTUNE  the first zkvc_batch_prove times candidate MSM chunk sizes,
+ *                        block sizes and NTT tile sizes on its own inputs and keeps the
+ *                        fastest before capturing (adds a few batch-times once);
+ *   ZKVC_BATCH_EAGER     launch the sequence every call instead of capturing it once as
+ *                        a CUDA graph and replaying it.
+ * The keys must outlive the batch.  A batch is used by one thread at a time.
+ *
+ * zkvc_batch_prove(b, d_X[i], d_W[i], rs, d_Y[i], proofs, status, stream):
+ *   d_X[i], d_W[i]  instance i's int8 matrices (device, row-major, shapes of key i);
+ *   rs              count x 64 bytes (host): r || s of each instance, canonical Fr;
+ *   d_Y[i]          instance i's a x b int32 output (device);
+ *   proofs          count x 256 bytes (host output), in key order;
+ *   status          optional count ints (host output): per-instance ZKVC_OK, ZKVC_EINVAL
+ *                   (non-canonical r or s) or ZKVC_EUNSAT.
+ * The inputs are read after the caller's earlier work on `stream`; the call returns when
+ * the proofs are on the host, waiting at most zkvc_set_wait_timeout_ms (ZKVC_ETIMEOUT
+ * then: the batch's work keeps running and the next call on the batch waits for it).
+ * Returns the first failing instance's status.
+ *
+ * zkvc_batch_get_tuning / zkvc_batch_set_tuning read or impose the launch shape as
+ * ZKVC_BATCH_TUNING_LEN integers: for the small G1, main G1 and G2 MSM runs in turn
+ * (chunk terms per thread, accumulation threads per block, fold grid blocks), then the
+ * NTT's log2 elements per block.  Setting re-captures on the next prove.
+ *
+ * zkvc_batch_terms reports the bucket terms (point additions) of the last call's three
+ * MSM runs, for throughput accounting.
+ *
+ * zkvc_prove_batch is a one-shot form (create eagerly, prove, free).
+ */
+typedef struct zkvc_batch zkvc_batch;
+#define ZKVC_BATCH_AUTOTUNE 1
+#define ZKVC_BATCH_EAGER 2
+#define ZKVC_BATCH_TUNING_LEN 10
+
+int zkvc_batch_create(const zkvc_pk* const* pks, int count, int flags, zkvc_batch** batch);
+void zkvc_batch_free(zkvc_batch* batch);
+int zkvc_batch_info(const zkvc_batch* batch, int* count, size_t* device_bytes, uint64_t* graph_launches);
+int zkvc_batch_get_tuning(const zkvc_batch* batch, int32_t* params, int n);
+/* Bucket terms (nonzero signed digits, one point addition each) of the last call's
+ * small G1, main G1 and G2 runs; synchronises the batch's stream. */
+int zkvc_batch_terms(const zkvc_batch* batch, uint64_t terms[3]);
+int zkvc_batch_set_tuning(zkvc_batch* batch, const int32_t* params, int n);
+int zkvc_batch_prove(zkvc_batch* batch, const int8_t* const* d_X, const int8_t* const* d_W, const uint8_t* rs,
+                     int32_t* const* d_Y, uint8_t* proofs, int* status, void* stream);
+int zkvc_prove_batch(const zkvc_pk* const* pks, const int8_t* const* d_X, const int8_t* const* d_W, const uint8_t* rs,
+                     int count, int32_t* const* d_Y, uint8_t* proofs, int* status, void* stream);
+
+/* Deadline of the library's host-side waits for device work (batched proving and the
+ * proof server), in milliseconds (default 60000).  A wait that runs out returns
+ * ZKVC_ETIMEOUT instead of blocking forever. */
+int zkvc_set_wait_timeout_ms(int ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,8 +1,10 @@
 // C-ABI entry points for the kernel layer: field products, NTT, variable-base MSM.
 #include <atomic>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <thread>
 
 #include "msm.h"
 #include "ntt.h"
@@ -24,6 +26,34 @@ static void clear_error() { g_err.clear(); }
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(unsigned long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+static std::atomic<int> g_wait_ms{60000};
+
+int wait_stream(cudaStream_t st, const char* what) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  const long long limit = g_wait_ms.load(std::memory_order_relaxed);
+  long long sleep_us = 0;
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) return ZKVC_OK;
+    if (e != cudaErrorNotReady) {
+      set_error("%s: %s", what, cudaGetErrorString(e));
+      return ZKVC_ECUDA;
+    }
+    long long el = std::chrono::duration_cast<std::chrono::milliseconds>(clk::now() - t0).count();
+    if (el >= limit) {
+      set_error("%s: device work not finished after %lld ms", what, el);
+      return ZKVC_ETIMEOUT;
+    }
+    // poll tightly for the first ~100 us, then back off up to 1 ms
+    if (sleep_us > 0) std::this_thread::sleep_for(std::chrono::microseconds(sleep_us));
+    sleep_us = sleep_us == 0 ? 1 : (sleep_us * 2 > 1000 ? 1000 : sleep_us * 2);
+  }
+}
 
 struct ProfSlot {
   const char* name;
@@ -186,6 +216,13 @@ const char* zkvc_last_error(void) { return g_err.c_str(); }
 int zkvc_version(void) { return 100; }
 
 uint64_t zkvc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int zkvc_set_wait_timeout_ms(int ms) {
+  clear_error();
+  ZK_CHECK(ms > 0, ZKVC_EINVAL, "wait timeout of %d ms", ms);
+  g_wait_ms.store(ms);
+  return ZKVC_OK;
+}
 
 void zkvc_profile_enable(int on) {
   for (auto& x : g_prof_slots) {

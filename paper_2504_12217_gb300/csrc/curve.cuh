@@ -171,6 +171,29 @@ __device__ __noinline__ XYZZ<F> p_mul_scalar(const XYZZ<F>& p, const uint32_t (&
   return acc;
 }
 
+// Variable-base scalar multiplication with fixed 4-bit windows: a table of the 15
+// multiples, then per window four doublings and at most one addition (254 doublings and
+// <= 64 additions for a 254-bit scalar instead of double-and-add's ~127 additions).
+template <class F>
+__device__ __noinline__ XYZZ<F> p_mul_scalar_w4(const XYZZ<F>& p, const uint32_t (&k)[8]) {
+  XYZZ<F> T[16];
+  T[0] = XYZZ<F>::inf();
+  T[1] = p;
+  for (int i = 2; i < 16; i++) T[i] = p_add(T[i - 1], p);
+  XYZZ<F> acc = XYZZ<F>::inf();
+  for (int w = 63; w >= 0; w--) {
+    if (w != 63) {
+      acc = p_dbl(acc);
+      acc = p_dbl(acc);
+      acc = p_dbl(acc);
+      acc = p_dbl(acc);
+    }
+    const uint32_t nib = (k[w >> 3] >> ((w & 7) * 4)) & 15u;
+    if (nib) acc = p_add(acc, T[nib]);
+  }
+  return acc;
+}
+
 // Curve coefficient b in Montgomery form (runtime conversion of small constants).
 __device__ __forceinline__ Fp g1_b() {
   Fp b = Fp::zero();

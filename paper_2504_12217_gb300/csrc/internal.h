@@ -13,7 +13,15 @@ void set_error(const char* fmt, ...);
 
 // Number of kernels this library has launched in the process (diagnostics).
 void count_launch();
+void count_launches(unsigned long long n);    // kernels of a replayed graph
+void uncount_launches(unsigned long long n);  // kernels recorded into a graph, not run
+unsigned long long launches_so_far();
 #define ZK_COUNT_LAUNCH() ::zkvc::count_launch()
+
+// Waits for the stream with a deadline (zkvc_set_wait_timeout_ms): ZKVC_OK when its work
+// is done, ZKVC_ETIMEOUT when the deadline passes first (the work keeps running),
+// ZKVC_ECUDA when the stream reports an error.
+int wait_stream(cudaStream_t st, const char* what);
 
 // Optional stage timers (CUDA events on the launching stream), enabled by
 // zkvc_profile_enable; collected after the synchronising end of a prove call.

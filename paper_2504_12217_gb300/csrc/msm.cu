@@ -135,9 +135,29 @@ int msm_plan_finalize(MsmPlan& p) {
     p.max_nd = std::max(p.max_nd, nd);
   }
   ZK_CHECK(slot < 0xffffffffull, ZKVC_EINVAL, "msm: too many digit slots");
-  if (p.chunk == 0) p.chunk = slot < (2u << 20) ? 16u : 32u;
+  p.chunk = p.tune.chunk ? p.tune.chunk : (slot < (2u << 20) ? 16u : 32u);
+  ZK_CHECK(p.chunk >= 1 && p.chunk <= 1024, ZKVC_EINVAL, "msm: chunk of %u terms", p.chunk);
+  ZK_CHECK(p.tune.accum_threads >= 32 && p.tune.accum_threads <= 256 && p.tune.accum_threads % 32 == 0,
+           ZKVC_EINVAL, "msm: %u accumulation threads", p.tune.accum_threads);
+  ZK_CHECK(p.tune.fold_blocks >= 1, ZKVC_EINVAL, "msm: fold grid of 0 blocks");
   p.slots = slot;
   p.points = pts;
+  // outputs with their own base arrays: every output must name one, and all must have
+  // the same power-of-two key count, so that a key's output is key >> key_shift
+  p.key_shift = -1;
+  bool any = false, all = true;
+  for (const auto& o : p.outs) {
+    if (o.bases) any = true; else all = false;
+  }
+  if (any) {
+    ZK_CHECK(all, ZKVC_EINVAL, "msm: some outputs name a base array and some do not");
+    const uint32_t nk = p.outs[0].nkeys;
+    ZK_CHECK((nk & (nk - 1)) == 0, ZKVC_EINVAL, "msm: %u keys per output is not a power of two", nk);
+    for (const auto& o : p.outs) ZK_CHECK(o.nkeys == nk, ZKVC_EINVAL, "msm: unequal key counts across outputs");
+    int sh = 0;
+    while ((1u << sh) < nk) sh++;
+    p.key_shift = sh;
+  }
   return ZKVC_OK;
 }
 
@@ -267,6 +287,7 @@ template <class F>
 __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ offs,
                                                 const uint32_t* __restrict__ choff, const uint32_t* __restrict__ chunk_key,
                                                 uint32_t K, uint32_t T0, const Affine<F>* __restrict__ bases,
+                                                const Affine<F>* const* __restrict__ obases, int key_shift,
                                                 XYZZ<F>* part) {
   uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= choff[K]) return;
@@ -274,6 +295,7 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
   uint32_t j = q - choff[k];
   uint32_t start = offs[k] + j * T0;
   uint32_t end = min(start + T0, offs[k + 1]);
+  if (key_shift >= 0) bases = obases[k >> key_shift];
   XYZZ<F> acc = XYZZ<F>::inf();
   for (uint32_t p = start; p < end; p++) {
     uint32_t v = sorted[p];
@@ -436,6 +458,7 @@ struct Layout {
   void *part, *U, *D;
   MsmSeg* segs;
   MsmOut* outs;
+  const void** obases;
   BitSeg* bsegs;
   TreeSeg *useg, *dseg;
   uint32_t *ucum, *dcum;
@@ -447,17 +470,29 @@ struct HostTables {
   std::vector<BitSeg> bsegs;
   TreePlan ut, dt;
   std::vector<OutItem> oitems;
+  std::vector<const void*> obases;
 };
+
+struct MsmExecState {
+  Layout L;
+  HostTables h;
+  Arena after_layout;  // the arena once the tables are carved: scans take from a copy
+  bool uploaded = false;
+};
+
+MsmExec::~MsmExec() { delete st; }
 
 static void tables(const MsmPlan& p, HostTables& h, Layout& L) {
   h.bsegs.clear();
   h.ut = TreePlan();
   h.dt = TreePlan();
   h.oitems.clear();
+  h.obases.clear();
   uint32_t uoff = 0, dslot = 0;
   for (const auto& o : p.outs) {
     const uint32_t nb = 1u << (o.c - 1);
     h.oitems.push_back({dslot, o.c, o.win_keys, o.c});
+    h.obases.push_back(o.bases);
     for (uint32_t w = 0; w < o.win_keys; w++) {
       h.dt.segs.push_back({dslot, o.c});
       for (uint32_t b = 0; b < o.c; b++) {
@@ -498,6 +533,7 @@ static void layout(const MsmPlan& p, Arena& a, Layout& L, HostTables& h) {
   L.D = a.take<XYZZ<F>>(L.dtotal);
   L.segs = a.take<MsmSeg>(p.segs.size());
   L.outs = a.take<MsmOut>(p.outs.size());
+  L.obases = a.take<const void*>(p.outs.size());
   L.bsegs = a.take<BitSeg>(h.bsegs.size());
   L.useg = a.take<TreeSeg>(h.ut.segs.size());
   L.ucum = a.take<uint32_t>(std::max<size_t>(1, h.ut.cum.size()));
@@ -530,22 +566,29 @@ static int run_tree(XYZZ<F>* x, const TreePlan& t, const TreeSeg* dsegs, const u
 }
 
 template <class F>
-int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results, cudaStream_t st,
-            int accum_stage) {
+int msm_prepare(const MsmPlan& p, void* ws, size_t ws_bytes, MsmExec* ex) {
   ZK_CHECK(p.keys > 0 && !p.outs.empty(), ZKVC_EINVAL, "msm: empty plan");
+  ZK_CHECK(ex, ZKVC_EINVAL, "msm: null exec");
+  delete ex->st;
+  ex->st = new MsmExecState();
+  ex->plan = p;
   Arena a;
   a.base = reinterpret_cast<uint8_t*>(ws);
   a.cap = ws_bytes;
-  Layout L;
-  HostTables h;
-  layout<F>(p, a, L, h);
+  layout<F>(ex->plan, a, ex->st->L, ex->st->h);
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace of %zu bytes is too small", ws_bytes);
-  const uint32_t K = p.keys;
-  const uint64_t S = p.slots;
-  const uint32_t T0 = p.chunk ? p.chunk : 32;
+  ex->st->after_layout = a;
+  return ZKVC_OK;
+}
 
+int msm_upload(MsmExec* ex, cudaStream_t st) {
+  ZK_CHECK(ex && ex->st, ZKVC_EINVAL, "msm: exec not prepared");
+  const MsmPlan& p = ex->plan;
+  Layout& L = ex->st->L;
+  HostTables& h = ex->st->h;
   ZK_CUDA(cudaMemcpyAsync(L.segs, p.segs.data(), p.segs.size() * sizeof(MsmSeg), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.outs, p.outs.data(), p.outs.size() * sizeof(MsmOut), cudaMemcpyHostToDevice, st));
+  ZK_CUDA(cudaMemcpyAsync(L.obases, h.obases.data(), h.obases.size() * sizeof(void*), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.bsegs, h.bsegs.data(), h.bsegs.size() * sizeof(BitSeg), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.useg, h.ut.segs.data(), h.ut.segs.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
   if (!h.ut.cum.empty())
@@ -554,6 +597,22 @@ int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes,
   if (!h.dt.cum.empty())
     ZK_CUDA(cudaMemcpyAsync(L.dcum, h.dt.cum.data(), h.dt.cum.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.oitems, h.oitems.data(), h.oitems.size() * sizeof(OutItem), cudaMemcpyHostToDevice, st));
+  ex->st->uploaded = true;
+  return ZKVC_OK;
+}
+
+template <class F>
+int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cudaStream_t st, int accum_stage) {
+  ZK_CHECK(ex && ex->st && ex->st->uploaded, ZKVC_EINVAL, "msm: exec not uploaded");
+  const MsmPlan& p = ex->plan;
+  const Layout& L = ex->st->L;
+  const HostTables& h = ex->st->h;
+  Arena a = ex->st->after_layout;
+  const uint32_t K = p.keys;
+  const uint64_t S = p.slots;
+  const uint32_t T0 = p.chunk;
+  ZK_CHECK(T0 >= 1, ZKVC_EINVAL, "msm: plan not finalized");
+  ZK_CHECK(p.key_shift >= 0 || bases, ZKVC_EINVAL, "msm: no base array");
 
   // digits -> terms
   if (p.points > 0) {
@@ -581,9 +640,11 @@ int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes,
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace too small for scans");
   k_chunk_keys<<<(K + 255) / 256, 256, 0, st>>>(L.choff, K, L.chunk_key, L.max_chunks); ZK_COUNT_LAUNCH();
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
-  unsigned qb = (L.qmax + 127) / 128;
+  const uint32_t at = p.tune.accum_threads;
+  unsigned qb = (L.qmax + at - 1) / at;
   if (accum_stage >= 0) prof_mark(accum_stage, true, st);
-  k_accum0<F><<<qb, 128, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases, part); ZK_COUNT_LAUNCH();
+  k_accum0<F><<<qb, at, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases,
+                                 reinterpret_cast<const Affine<F>* const*>(L.obases), p.key_shift, part); ZK_COUNT_LAUNCH();
   if (accum_stage >= 0) {
     prof_mark(accum_stage, false, st);
     if (uint32_t* hu = prof_units(accum_stage)) ZK_CUDA(cudaMemcpyAsync(hu, L.offs + K, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -595,7 +656,7 @@ int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes,
   while ((uint64_t(1) << levels) < (S + T0 - 1) / T0 + 1) levels++;
   for (uint32_t l = 0; l < levels; l++) {
     unsigned fb = (L.qmax + 255) / 256;
-    if (fb > 4 * 152) fb = 4 * 152;
+    if (fb > p.tune.fold_blocks) fb = p.tune.fold_blocks;
     k_fold<F><<<fb, 256, 0, st>>>(part, L.choff, L.chunk_key, K, L.max_chunks, l); ZK_COUNT_LAUNCH();
   }
   ZK_CUDA(cudaGetLastError());
@@ -611,9 +672,27 @@ int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes,
   return ZKVC_OK;
 }
 
+const uint32_t* msm_term_count(const MsmExec* ex) {
+  if (!ex || !ex->st) return nullptr;
+  return ex->st->L.offs + ex->plan.keys;
+}
+
+template <class F>
+int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results, cudaStream_t st,
+            int accum_stage) {
+  MsmExec ex;
+  ZK_TRY(msm_prepare<F>(p, ws, ws_bytes, &ex));
+  ZK_TRY(msm_upload(&ex, st));
+  return msm_launch<F>(&ex, bases, results, st, accum_stage);
+}
+
 template size_t msm_workspace_bytes<Fp>(const MsmPlan&);
 template size_t msm_workspace_bytes<Fp2>(const MsmPlan&);
 template int msm_run<Fp>(const MsmPlan&, const Affine<Fp>*, void*, size_t, XYZZ<Fp>*, cudaStream_t, int);
 template int msm_run<Fp2>(const MsmPlan&, const Affine<Fp2>*, void*, size_t, XYZZ<Fp2>*, cudaStream_t, int);
+template int msm_prepare<Fp>(const MsmPlan&, void*, size_t, MsmExec*);
+template int msm_prepare<Fp2>(const MsmPlan&, void*, size_t, MsmExec*);
+template int msm_launch<Fp>(const MsmExec*, const Affine<Fp>*, XYZZ<Fp>*, cudaStream_t, int);
+template int msm_launch<Fp2>(const MsmExec*, const Affine<Fp2>*, XYZZ<Fp2>*, cudaStream_t, int);
 
 }  // namespace zkvc

@@ -36,16 +36,28 @@ struct MsmOut {
                        // combined by Horner's rule; 1: windows use precomputed bases
   uint32_t key_off;    // planner
   uint32_t nkeys;      // planner: win_keys * 2^(c-1)
+  const void* bases;   // this output's base array (nullptr: the run's), so one run can
+                       // serve outputs of several proving keys
+};
+
+// Launch-shape knobs of a run (chosen by the batch autotuner; defaults otherwise).
+struct MsmTune {
+  uint32_t chunk = 0;          // terms per level-0 chunk (0: 16 below 2M slots, else 32)
+  uint32_t accum_threads = 128;
+  uint32_t fold_blocks = 608;  // grid cap of the fold levels (grid-stride)
 };
 
 struct MsmPlan {
-  uint32_t chunk = 0;  // terms per level-0 chunk (0: chosen from the slot count)
+  MsmTune tune;
   std::vector<MsmSeg> segs;
   std::vector<MsmOut> outs;
   uint64_t slots = 0;
   uint32_t keys = 0;
   uint32_t points = 0;
   uint32_t max_nd = 0;
+  uint32_t chunk = 0;          // planner: the level-0 chunk in use
+  int32_t key_shift = -1;      // planner: log2 of the keys per output when outputs carry
+                               // their own bases (all outputs then have equal 2^k keys)
 };
 
 // Fills the planner fields; returns ZKVC_EINVAL on an inconsistent plan.
@@ -59,6 +71,28 @@ size_t msm_workspace_bytes(const MsmPlan& p);
 template <class F>
 int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results,
             cudaStream_t st, int accum_stage = -1);
+
+// The same run split in three, for launch sequences that are built once and replayed
+// (CUDA graphs): prepare carves the workspace and builds the host tables, upload copies
+// the tables to their place in the workspace (host -> device; not under capture), and
+// launch issues only kernels, memsets and device copies (capturable).  The plan's scalar
+// and base pointers are baked into the uploaded tables.
+struct MsmExecState;
+struct MsmExec {
+  MsmPlan plan;
+  MsmExecState* st = nullptr;
+  MsmExec() = default;
+  MsmExec(const MsmExec&) = delete;
+  MsmExec& operator=(const MsmExec&) = delete;
+  ~MsmExec();
+};
+template <class F>
+int msm_prepare(const MsmPlan& p, void* ws, size_t ws_bytes, MsmExec* ex);
+int msm_upload(MsmExec* ex, cudaStream_t st);
+template <class F>
+int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cudaStream_t st, int accum_stage = -1);
+// Device address of the run's bucket-term count (valid after a launch completes).
+const uint32_t* msm_term_count(const MsmExec* ex);
 
 // The variable-base MSM behind zkvc_msm_g1 / zkvc_msm_g2: canonical points and scalars
 // in, canonical affine result out (host), using the caller's workspace.

@@ -233,10 +233,29 @@ __global__ void __launch_bounds__(256) k_ntt_pass(Fr* data, size_t bstride, cons
   }
 }
 
+static std::once_flag g_smem_once;
+
+static void ntt_smem_attrs() {
+  std::call_once(g_smem_once, [] {
+    cudaFuncSetAttribute(k_ntt_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_ntt_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+  });
+}
+
+int ntt_init() {
+  ntt_smem_attrs();
+  ZK_CUDA(cudaGetLastError());
+  return ZKVC_OK;
+}
+
 static int run_passes(bool dit, Fr* data, int batch, size_t bstride, const NttDomain* d, bool inverse,
-                      int load_scale, int store_scale, bool to_mont, cudaStream_t st) {
+                      int load_scale, int store_scale, bool to_mont, int elog, cudaStream_t st) {
+  ZK_CHECK(elog >= 8 && elog <= 11, ZKVC_EINVAL, "ntt: 2^%d elements per block outside [2^8, 2^11]", elog);
+  ZK_CHECK(batch >= 1 && batch <= 65535, ZKVC_EINVAL, "ntt: batch of %d arrays", batch);
+  ntt_smem_attrs();
   const uint32_t L = d->logN;
-  const uint32_t P = (L + 9) / 10;
+  const uint32_t kmax = (uint32_t)elog < 10 ? (uint32_t)elog : 10;
+  const uint32_t P = (L + kmax - 1) / kmax;
   const uint32_t kb = L / P, rem = L % P;
   uint32_t s0 = 0;
   const Fr* tw = inverse ? d->tw_inv : d->tw_fwd;
@@ -244,7 +263,7 @@ static int run_passes(bool dit, Fr* data, int batch, size_t bstride, const NttDo
   for (uint32_t p = 0; p < P; p++) {
     uint32_t k = kb + (p < rem ? 1 : 0);
     uint32_t groups_log = L - k;
-    uint32_t logG = 10 - k;
+    uint32_t logG = (uint32_t)elog - k;
     if (logG > groups_log) logG = groups_log;
     uint32_t E = 1u << (logG + k);
     uint32_t threads = E / 2 < 256 ? E / 2 : 256;
@@ -264,12 +283,12 @@ static int run_passes(bool dit, Fr* data, int batch, size_t bstride, const NttDo
 }
 
 int ntt_dif(Fr* data, int batch, size_t bstride, const NttDomain* d, bool inverse, int load_scale,
-            int store_scale, bool to_mont, cudaStream_t st) {
-  return run_passes(false, data, batch, bstride, d, inverse, load_scale, store_scale, to_mont, st);
+            int store_scale, bool to_mont, cudaStream_t st, int elog) {
+  return run_passes(false, data, batch, bstride, d, inverse, load_scale, store_scale, to_mont, elog, st);
 }
 
-int ntt_dit(Fr* data, int batch, size_t bstride, const NttDomain* d, bool inverse, cudaStream_t st) {
-  return run_passes(true, data, batch, bstride, d, inverse, 0, 0, false, st);
+int ntt_dit(Fr* data, int batch, size_t bstride, const NttDomain* d, bool inverse, cudaStream_t st, int elog) {
+  return run_passes(true, data, batch, bstride, d, inverse, 0, 0, false, elog, st);
 }
 
 __global__ void k_bitrev(Fr* a, uint32_t logN, int scale, int from_mont, ScaleTabs tabs) {
@@ -308,9 +327,10 @@ __global__ void k_quotient(const Fr* __restrict__ A, const Fr* __restrict__ B, c
   st_field(H + i, f_mul(v, zinv));
 }
 
-int ntt_quotient(const Fr* A, const Fr* B, const Fr* C, Fr* H, const NttDomain* d, cudaStream_t st) {
-  unsigned blocks = (unsigned)((d->N + 255) / 256);
-  k_quotient<<<blocks, 256, 0, st>>>(A, B, C, H, d->N, d->consts); ZK_COUNT_LAUNCH();
+int ntt_quotient(const Fr* A, const Fr* B, const Fr* C, Fr* H, const NttDomain* d, cudaStream_t st, size_t count) {
+  size_t n = count ? count : d->N;
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  k_quotient<<<blocks, 256, 0, st>>>(A, B, C, H, n, d->consts); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }

@@ -28,6 +28,10 @@ enum ScaleMode : int {
   SC_N = 4,     // x N^-1
 };
 
+// Sets the pass kernels' shared-memory limit (64 KB blocks); call once before capturing
+// NTT launches in a graph (the first NTT call does it otherwise).
+int ntt_init();
+
 // Cached per (device, logN); built on first use (allocates; do not call under capture).
 int ntt_domain(uint32_t logN, const NttDomain** out);
 
@@ -35,18 +39,22 @@ int ntt_domain(uint32_t logN, const NttDomain** out);
 //   load_scale  multiplies input i (natural index) before the first stage;
 //   store_scale multiplies output position p by the factor of natural index bitrev(p).
 //   to_mont     converts canonical input to Montgomery form on load.
-// batch arrays of N elements each, batch_stride elements apart.
+// batch arrays of N elements each, batch_stride elements apart.  elog = log2 of the
+// elements a block stages in shared memory (8 .. 11; passes take min(elog, 10) stages).
 int ntt_dif(Fr* data, int batch, size_t batch_stride, const NttDomain* d, bool inverse, int load_scale,
-            int store_scale, bool to_mont, cudaStream_t st);
+            int store_scale, bool to_mont, cudaStream_t st, int elog = 10);
 
 // Decimation-in-time: bit-reversed input, natural-order output, in place.
-int ntt_dit(Fr* data, int batch, size_t batch_stride, const NttDomain* d, bool inverse, cudaStream_t st);
+int ntt_dit(Fr* data, int batch, size_t batch_stride, const NttDomain* d, bool inverse, cudaStream_t st,
+            int elog = 10);
 
 // In-place bit-reversal permutation with an optional scale by natural index and an
 // optional conversion out of Montgomery form.
 int ntt_bitrev(Fr* data, const NttDomain* d, int scale, bool from_mont, cudaStream_t st);
 
-// h_ev[i] = (A[i] B[i] - C[i]) / (g^N - 1): the quotient on the coset gH.
-int ntt_quotient(const Fr* A, const Fr* B, const Fr* C, Fr* H, const NttDomain* d, cudaStream_t st);
+// h_ev[i] = (A[i] B[i] - C[i]) / (g^N - 1): the quotient on the coset gH, for i < count
+// (count = 0: N; several instances of one domain lie back to back).
+int ntt_quotient(const Fr* A, const Fr* B, const Fr* C, Fr* H, const NttDomain* d, cudaStream_t st,
+                 size_t count = 0);
 
 }  // namespace zkvc

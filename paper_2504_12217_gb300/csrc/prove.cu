@@ -26,51 +26,14 @@
 
 #include "groth16.h"
 #include "msm.h"
+#include "witness.cuh"
 
 namespace zkvc {
 
 // ------------------------------------------------------------------ witness
 __global__ void k_matmul_i8(const int8_t* __restrict__ X, const int8_t* __restrict__ W, int32_t* __restrict__ Y,
                             int a, int n, int b) {
-  __shared__ int8_t xs[32][33];
-  __shared__ int8_t ws[32][33];
-  int tj = threadIdx.x, ti = threadIdx.y;  // 32 x 8 threads, 32 x 32 output tile
-  int j = blockIdx.x * 32 + tj;
-  int i0 = blockIdx.y * 32;
-  int32_t acc[4] = {0, 0, 0, 0};
-  for (int k0 = 0; k0 < n; k0 += 32) {
-    for (int r = ti; r < 32; r += 8) {
-      int xi = i0 + r, xk = k0 + tj;
-      xs[r][tj] = (xi < a && xk < n) ? X[size_t(xi) * n + xk] : 0;
-      int wk = k0 + r, wj = blockIdx.x * 32 + tj;
-      ws[r][tj] = (wk < n && wj < b) ? W[size_t(wk) * b + wj] : 0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; kk++) {
-      int32_t w = ws[kk][tj];
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] += int32_t(xs[ti + 8 * q][kk]) * w;
-    }
-    __syncthreads();
-  }
-  for (int q = 0; q < 4; q++) {
-    int i = i0 + ti + 8 * q;
-    if (i < a && j < b) Y[size_t(i) * b + j] = acc[q];
-  }
-}
-
-// sum over the block of per-thread Fr values (blockDim.x = 256)
-__device__ Fr block_sum(Fr v, Fr* sh) {
-  st_field(sh + threadIdx.x, v);
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) st_field(sh + threadIdx.x, f_add(ld_field(sh + threadIdx.x), ld_field(sh + threadIdx.x + s)));
-    __syncthreads();
-  }
-  Fr r = ld_field(sh);
-  __syncthreads();
-  return r;
+  matmul_tile(X, W, Y, a, n, b, blockIdx.x, blockIdx.y);
 }
 
 // block k < n: a_k and b_k
@@ -78,102 +41,34 @@ __global__ void __launch_bounds__(256) k_crpc_ab(const int8_t* __restrict__ X, c
                                                  const Fr* __restrict__ zA, const Fr* __restrict__ zB, int a, int n, int b,
                                                  Fr* ak, Fr* bk) {
   __shared__ Fr sh[256];
-  int k = blockIdx.x;
-  Fr s = Fr::zero();
-  for (int i = threadIdx.x; i < a; i += blockDim.x)
-    s = f_add(s, f_mul(ld_field(zA + i), f_from_int<FrCfg>(X[size_t(i) * n + k])));
-  Fr av = block_sum(s, sh);
-  s = Fr::zero();
-  for (int j = threadIdx.x; j < b; j += blockDim.x)
-    s = f_add(s, f_mul(ld_field(zB + j), f_from_int<FrCfg>(W[size_t(k) * b + j])));
-  Fr bv = block_sum(s, sh);
-  if (threadIdx.x == 0) {
-    st_field(ak + k, av);
-    st_field(bk + k, bv);
-  }
+  crpc_ab_row(X, W, zA, zB, a, n, b, blockIdx.x, ak, bk, sh);
 }
 
 // block i < a: z^(ib) sum_j z^j y_ij
 __global__ void __launch_bounds__(256) k_crpc_y(const int32_t* __restrict__ Y, const Fr* __restrict__ zA,
                                                 const Fr* __restrict__ zB, int b, Fr* part) {
   __shared__ Fr sh[256];
-  int i = blockIdx.x;
-  Fr s = Fr::zero();
-  for (int j = threadIdx.x; j < b; j += blockDim.x)
-    s = f_add(s, f_mul(ld_field(zB + j), f_from_int<FrCfg>(Y[size_t(i) * b + j])));
-  Fr v = block_sum(s, sh);
-  if (threadIdx.x == 0) st_field(part + i, f_mul(v, ld_field(zA + i)));
+  crpc_y_row(Y, zA, zB, b, blockIdx.x, part, sh);
 }
 
-// One block of 1024 threads: c_k = a_k b_k, S_k = c_0 + ... + c_k (k <= n - 2), the
-// closing check against Y(z), and the first n domain evaluations.
+// One block of 1024 threads: products, prefix sums, closing check, first n evaluations.
 __global__ void __launch_bounds__(1024) k_psq(const Fr* __restrict__ ak, const Fr* __restrict__ bk,
                                               const Fr* __restrict__ ypart, int a, int n, Fr* S, Fr* Aev, Fr* Bev,
                                               Fr* Cev, int* flags) {
   __shared__ Fr sh[1024];
-  const int T = blockDim.x;
-  const int per = (n + T - 1) / T;
-  const int k0 = threadIdx.x * per;
-  Fr local = Fr::zero();
-  for (int k = k0; k < k0 + per && k < n; k++) {
-    Fr a_ = ld_field(ak + k), b_ = ld_field(bk + k);
-    Fr c = f_mul(a_, b_);
-    st_field(Aev + k, a_);
-    st_field(Bev + k, b_);
-    st_field(Cev + k, c);
-    local = f_add(local, c);
-  }
-  // inclusive scan of the per-thread sums (Hillis-Steele)
-  st_field(sh + threadIdx.x, local);
-  __syncthreads();
-  for (int d = 1; d < T; d <<= 1) {
-    Fr v = ld_field(sh + threadIdx.x);
-    if ((int)threadIdx.x >= d) v = f_add(v, ld_field(sh + threadIdx.x - d));
-    __syncthreads();
-    st_field(sh + threadIdx.x, v);
-    __syncthreads();
-  }
-  Fr run = threadIdx.x ? ld_field(sh + threadIdx.x - 1) : Fr::zero();
-  for (int k = k0; k < k0 + per && k < n; k++) {
-    run = f_add(run, f_mul(ld_field(ak + k), ld_field(bk + k)));
-    if (k < n - 1) st_field(S + k, run);
-  }
-  if (threadIdx.x == 0) {
-    Fr total = ld_field(sh + T - 1);  // S_(n-2) + c_(n-1)
-    Fr yz = Fr::zero();
-    for (int i = 0; i < a; i++) yz = f_add(yz, ld_field(ypart + i));
-    if (total != yz) atomicOr(flags, 1);
-  }
+  psq_chain(ak, bk, ypart, a, n, S, Aev, Bev, Cev, flags, sh);
 }
 
-// domain rows n .. N-1: A_ev[n + v] = w_v for v = 0 .. l (one, X, Y), zeros elsewhere
+// domain rows n .. N-1
 __global__ void k_domain_rest(const int8_t* __restrict__ X, const int32_t* __restrict__ Y, int n, uint32_t an,
                               uint32_t l, size_t N, Fr* Aev, Fr* Bev, Fr* Cev) {
   size_t k = n + size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= N) return;
-  size_t v = k - n;
-  Fr w = Fr::zero();
-  if (v == 0)
-    w = Fr::one();
-  else if (v <= an)
-    w = f_from_int<FrCfg>(X[v - 1]);
-  else if (v <= l)
-    w = f_from_int<FrCfg>(Y[v - 1 - an]);
-  st_field(Aev + k, w);
-  st_field(Bev + k, Fr::zero());
-  st_field(Cev + k, Fr::zero());
+  domain_rest_row(X, Y, n, an, l, k, Aev, Bev, Cev);
 }
 
 __global__ void k_check_h(const Fr* H, size_t N, int* flags) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && !ld_field(H + (N - 1)).is_zero()) atomicOr(flags, 2);
-}
-
-__device__ __forceinline__ bool canonical_fr(const Fr& x) {
-  for (int i = 7; i >= 0; i--) {
-    uint32_t m = mod_limb<FrCfg>(i);
-    if (x.v[i] != m) return x.v[i] < m;
-  }
-  return false;
 }
 
 // rs[0] = r, rs[1] = s (canonical, from the caller); rs[2] = r s (canonical)
@@ -201,41 +96,14 @@ __global__ void k_scaled_witness(const int8_t* __restrict__ X, const int32_t* __
   }
 }
 
-__device__ __forceinline__ void write_canon(uint8_t* out, const Fp& x) {
-  Fp c = f_from_mont(x);
-  for (int i = 0; i < 8; i++) {
-    out[4 * i] = (uint8_t)c.v[i];
-    out[4 * i + 1] = (uint8_t)(c.v[i] >> 8);
-    out[4 * i + 2] = (uint8_t)(c.v[i] >> 16);
-    out[4 * i + 3] = (uint8_t)(c.v[i] >> 24);
-  }
-}
-
-__device__ __forceinline__ G1A g1_affine_with(const G1J& p, const Fp& inv_zz_zzz) {
-  if (p.is_inf()) return G1A::inf();
-  return {f_mul(p.X, f_mul(inv_zz_zzz, p.ZZZ)), f_mul(p.Y, f_mul(inv_zz_zzz, p.ZZ))};
-}
-
-// Proof encoding.  A = small[0]; C = small[1] + rest[0] + hq[0].  Warp 0 converts A and C
-// with one shared inversion (Montgomery's trick); warp 1 converts B concurrently.
+// Proof encoding.  A = small[0]; C = small[1] + rest[0] + hq[0].  Thread 0 converts A and
+// C with one shared inversion; thread 32 (another warp) converts B concurrently.
 __global__ void k_encode(const G1J* small, const G1J* rest, const G1J* hq, const G2J* res2, uint8_t* proof) {
   if (threadIdx.x == 0) {
     G1J A = ld_field(small), C = p_add(p_add(ld_field(small + 1), ld_field(rest)), ld_field(hq));
-    Fp za = A.is_inf() ? Fp::one() : f_mul(A.ZZ, A.ZZZ);
-    Fp zc = C.is_inf() ? Fp::one() : f_mul(C.ZZ, C.ZZZ);
-    Fp inv = f_inv(f_mul(za, zc));
-    G1A a = g1_affine_with(A, f_mul(inv, zc));
-    G1A c = g1_affine_with(C, f_mul(inv, za));
-    write_canon(proof + 0, a.x);
-    write_canon(proof + 32, a.y);
-    write_canon(proof + 192, c.x);
-    write_canon(proof + 224, c.y);
+    encode_a_c(A, C, proof);
   } else if (threadIdx.x == 32) {
-    G2A q = p_to_affine(ld_field(res2));
-    write_canon(proof + 64, q.x.c0);
-    write_canon(proof + 96, q.x.c1);
-    write_canon(proof + 128, q.y.c0);
-    write_canon(proof + 160, q.y.c1);
+    encode_b(ld_field(res2), proof);
   }
 }
 

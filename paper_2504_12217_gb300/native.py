@@ -64,6 +64,15 @@ SIGNATURES = {
     "zkvc_vk_load": (_c_int, [ctypes.c_char_p, ctypes.POINTER(_c_p)]),
     "zkvc_prove_workspace_bytes": (_c_sz, [_c_p]),
     "zkvc_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
+    "zkvc_batch_create": (_c_int, [_c_p, _c_int, _c_int, ctypes.POINTER(_c_p)]),
+    "zkvc_batch_free": (None, [_c_p]),
+    "zkvc_batch_info": (_c_int, [_c_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_sz), ctypes.POINTER(ctypes.c_uint64)]),
+    "zkvc_batch_get_tuning": (_c_int, [_c_p, _c_p, _c_int]),
+    "zkvc_batch_terms": (_c_int, [_c_p, _c_p]),
+    "zkvc_batch_set_tuning": (_c_int, [_c_p, _c_p, _c_int]),
+    "zkvc_batch_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "zkvc_prove_batch": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_int, _c_p, _c_p, _c_p, _c_p]),
+    "zkvc_set_wait_timeout_ms": (_c_int, [_c_int]),
 }
 
 ZKVC_Q_A, ZKVC_Q_B1, ZKVC_Q_B2, ZKVC_Q_L, ZKVC_Q_H = 0, 1, 2, 3, 4
@@ -392,3 +401,105 @@ def zkvc_prove(pk, X, W, rs, Y=None, workspace=None):
     check(lib().zkvc_prove(pk.handle, _dev_ptr(X), _dev_ptr(W), rsb, _dev_ptr(Y), _dev_ptr(workspace),
                            workspace.numel(), proof, _stream()))
     return proof.raw, Y
+
+
+# ------------------------------------------------------------------ batched proving
+ZKVC_BATCH_AUTOTUNE = 1
+ZKVC_BATCH_EAGER = 2
+ZKVC_BATCH_TUNING_LEN = 10
+TUNING_NAMES = ("small_chunk", "small_accum_threads", "small_fold_blocks", "main_chunk", "main_accum_threads",
+                "main_fold_blocks", "g2_chunk", "g2_accum_threads", "g2_fold_blocks", "ntt_log_elems_per_block")
+
+
+def zkvc_set_wait_timeout_ms(ms):
+    check(lib().zkvc_set_wait_timeout_ms(int(ms)))
+
+
+def _ptr_array(ptrs):
+    arr = (_c_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+class Batch:
+    """Owns a zkvc_batch handle: one proof per listed proving key per prove() call, in one
+    captured launch sequence.  Keeps the keys alive."""
+
+    def __init__(self, pks, flags=0):
+        self.pks = list(pks)
+        h = _c_p()
+        keys = _ptr_array([pk.handle for pk in self.pks])
+        check(lib().zkvc_batch_create(keys, len(self.pks), flags, ctypes.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.zkvc_batch_free(self.handle)
+            self.handle = None
+
+    def info(self):
+        count, nbytes, launches = _c_int(), _c_sz(), ctypes.c_uint64()
+        check(lib().zkvc_batch_info(self.handle, ctypes.byref(count), ctypes.byref(nbytes), ctypes.byref(launches)))
+        return {"count": count.value, "device_bytes": nbytes.value, "graph_launches": launches.value}
+
+    def terms(self):
+        """{"small": n, "main": n, "g2": n}: bucket terms of the last call's MSM runs."""
+        arr = (ctypes.c_uint64 * 3)()
+        check(lib().zkvc_batch_terms(self.handle, arr))
+        return {"small": arr[0], "main": arr[1], "g2": arr[2]}
+
+    def get_tuning(self):
+        arr = (ctypes.c_int32 * ZKVC_BATCH_TUNING_LEN)()
+        check(lib().zkvc_batch_get_tuning(self.handle, arr, ZKVC_BATCH_TUNING_LEN))
+        return dict(zip(TUNING_NAMES, list(arr)))
+
+    def set_tuning(self, tuning):
+        vals = [tuning[k] for k in TUNING_NAMES] if isinstance(tuning, dict) else list(tuning)
+        arr = (ctypes.c_int32 * ZKVC_BATCH_TUNING_LEN)(*vals)
+        check(lib().zkvc_batch_set_tuning(self.handle, arr, ZKVC_BATCH_TUNING_LEN))
+
+    def prove(self, Xs, Ws, rs_list, Ys=None, with_status=False):
+        """Xs[i], Ws[i]: int8 CUDA tensors of key i's shape; rs_list[i]: 64 bytes.
+        Returns (list of 256-byte proofs, list of Y tensors[, per-instance status])."""
+        torch = _torch()
+        n = len(self.pks)
+        if not (len(Xs) == len(Ws) == len(rs_list) == n):
+            raise ValueError(f"expected {n} instances")
+        if Ys is None:
+            Ys = [torch.empty((pk.shape[0], pk.shape[2]), dtype=torch.int32, device=Xs[0].device) for pk in self.pks]
+        for pk, X, W, Y in zip(self.pks, Xs, Ws, Ys):
+            a, nn, b = pk.shape
+            if X.dtype != torch.int8 or tuple(X.shape) != (a, nn) or W.dtype != torch.int8 or tuple(W.shape) != (nn, b):
+                raise ValueError(f"expected X int8 [{a}, {nn}] and W int8 [{nn}, {b}]")
+            if Y.dtype != torch.int32 or tuple(Y.shape) != (a, b):
+                raise ValueError(f"expected Y int32 [{a}, {b}]")
+        if any(len(r) != 64 for r in rs_list):
+            raise ValueError("each rs must be 64 bytes")
+        xs = _ptr_array([_dev_ptr(X).value for X in Xs])
+        ws = _ptr_array([_dev_ptr(W).value for W in Ws])
+        ys = _ptr_array([_dev_ptr(Y).value for Y in Ys])
+        rsb = ctypes.create_string_buffer(b"".join(bytes(r) for r in rs_list), 64 * n)
+        proofs = ctypes.create_string_buffer(256 * n)
+        status = (_c_int * n)()
+        rc = lib().zkvc_batch_prove(self.handle, xs, ws, rsb, ys, proofs, status, _stream())
+        st = list(status)
+        if rc != ZKVC_OK and not (with_status and rc in (ZKVC_EINVAL, ZKVC_EUNSAT) and any(st)):
+            check(rc)
+        out = [proofs.raw[256 * i: 256 * (i + 1)] for i in range(n)]
+        return (out, Ys, st) if with_status else (out, Ys)
+
+
+def zkvc_prove_batch(pks, Xs, Ws, rs_list):
+    """One-shot batched prove (eager launches); returns (proofs, Ys)."""
+    torch = _torch()
+    n = len(pks)
+    Ys = [torch.empty((pk.shape[0], pk.shape[2]), dtype=torch.int32, device=Xs[0].device) for pk in pks]
+    keys = _ptr_array([pk.handle for pk in pks])
+    xs = _ptr_array([_dev_ptr(X).value for X in Xs])
+    ws = _ptr_array([_dev_ptr(W).value for W in Ws])
+    ys = _ptr_array([_dev_ptr(Y).value for Y in Ys])
+    rsb = ctypes.create_string_buffer(b"".join(bytes(r) for r in rs_list), 64 * n)
+    proofs = ctypes.create_string_buffer(256 * n)
+    check(lib().zkvc_prove_batch(keys, xs, ws, rsb, n, ys, proofs, None, _stream()))
+    return [proofs.raw[256 * i: 256 * (i + 1)] for i in range(n)], Ys
