@@ -245,6 +245,23 @@ size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk);
 int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64], int32_t* d_Y,
                void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream);
 
+/* The same proof computed two ways (identical bytes).  Groth16's C holds s A + r B1 - r s
+ * [delta]1 (Sec. II), which needs A and B1 first.
+ *   ZKVC_PROVE_FOLD   (zkvc_prove's mode) expands s A and r B1 by linearity into
+ *                     fixed-base terms sum (s w_v) [A_v]1 + sum (r w_e) [B_e]1 + ..., so
+ *                     no serial doubling chain remains: lowest latency for one proof,
+ *                     but 16 signed digits per witness entry instead of one.
+ *   ZKVC_PROVE_CHAIN  computes A and B1 with small-scalar MSMs and then s A and r B1 as
+ *                     two variable-base multiplications (254 doublings each, one thread)
+ *                     beside the H MSM: about 2.5x less MSM work per proof, so more
+ *                     proofs per second when several proofs share the GPU.
+ * Workspace sizes differ per mode. */
+#define ZKVC_PROVE_FOLD 0
+#define ZKVC_PROVE_CHAIN 1
+size_t zkvc_prove_workspace_bytes_mode(const zkvc_pk* pk, int mode);
+int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64],
+                    int32_t* d_Y, void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream);
+
 /* ------------------------------------------------------------------ batched proving
  * Many proofs of uneven shapes in one launch sequence (the paper proves the matmul
  * layers of a network, Sec. V, each as its own CRPC circuit; batching them is this
@@ -301,6 +318,45 @@ int zkvc_batch_prove(zkvc_batch* batch, const int8_t* const* d_X, const int8_t* 
                      int32_t* const* d_Y, uint8_t* proofs, int* status, void* stream);
 int zkvc_prove_batch(const zkvc_pk* const* pks, const int8_t* const* d_X, const int8_t* const* d_W, const uint8_t* rs,
                      int count, int32_t* const* d_Y, uint8_t* proofs, int* status, void* stream);
+
+/* ------------------------------------------------------------------ proof server
+ * Continuous batching of proof requests (the paper's use case, Sec. I: a client sends X
+ * and receives Y with a proof; here many clients share one GPU).  The server keeps the
+ * given proving keys resident (they must outlive it) and preallocates `mem_budget` bytes
+ * of device memory for per-request state.  `slots` worker threads, each with its own CUDA
+ * stream, take requests in arrival order: the head of the queue is admitted as soon as a
+ * worker is idle and its footprint (zkvc_server_request_bytes: prove workspace plus X, W
+ * and Y) fits in the unused budget, so requests that arrive while others run overlap
+ * with them on the device.  A request that can never fit completes with ZKVC_ENOMEM.
+ * Policy: ZKVC_SERVER_ADAPTIVE proves a request that finds the GPU idle with
+ * ZKVC_PROVE_FOLD (lowest latency) and one admitted beside others with ZKVC_PROVE_CHAIN
+ * (less work per proof); ZKVC_SERVER_FOLD / _CHAIN force one mode.  Results are the same
+ * bytes as zkvc_prove's.
+ *
+ * zkvc_server_submit copies X (a x n int8, host) and W (n x b int8, host) and rs (64
+ * bytes, host) of key `key` and returns a ticket at once.  zkvc_server_wait blocks up to
+ * timeout_ms for a ticket: ZKVC_ETIMEOUT if it is not done (the ticket stays valid),
+ * otherwise ZKVC_OK with *status = the request's status, the proof (256 bytes) and Y
+ * (a x b int32) copied out when it succeeded (either may be NULL), and times_ms = {queue,
+ * prove, total} milliseconds from submission; the ticket is then released.
+ * zkvc_server_free stops the workers after their current requests; queued requests are
+ * dropped.  Submit, wait and stats may be called from any thread.
+ */
+typedef struct zkvc_server zkvc_server;
+#define ZKVC_SERVER_ADAPTIVE 0
+#define ZKVC_SERVER_FOLD 1
+#define ZKVC_SERVER_CHAIN 2
+
+int zkvc_server_create(const zkvc_pk* const* pks, int npk, int slots, size_t mem_budget, int policy,
+                       zkvc_server** server);
+void zkvc_server_free(zkvc_server* server);
+int zkvc_server_submit(zkvc_server* server, int key, const int8_t* X, const int8_t* W, const uint8_t rs[64],
+                       uint64_t* ticket);
+int zkvc_server_wait(zkvc_server* server, uint64_t ticket, int timeout_ms, uint8_t proof[256], int32_t* Y,
+                     double times_ms[3], int* status);
+int zkvc_server_stats(zkvc_server* server, uint64_t* completed, int* in_flight, int* queued, size_t* bytes_in_use,
+                      size_t* peak_bytes, uint64_t* chain_mode);
+size_t zkvc_server_request_bytes(const zkvc_pk* pk, int mode);
 
 /* Deadline of the library's host-side waits for device work (batched proving and the
  * proof server), in milliseconds (default 60000).  A wait that runs out returns

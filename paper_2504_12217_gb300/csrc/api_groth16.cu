@@ -7,9 +7,9 @@
 
 namespace zkvc {
 int setup_impl(int a, int n, int b, const uint8_t* toxic, cudaStream_t st, zkvc_pk** pk, zkvc_vk** vk);
-size_t prove_workspace_bytes(const zkvc_pk* pk);
-int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint8_t* rs, int32_t* dY, void* ws,
-               size_t ws_bytes, uint8_t* proof, cudaStream_t st);
+size_t prove_workspace_bytes(const zkvc_pk* pk, int mode);
+int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, int32_t* dY,
+               void* ws, size_t ws_bytes, uint8_t* proof, cudaStream_t st);
 template <class F>
 int export_points(const Affine<F>* src, const std::vector<uint64_t>& idx, uint8_t* host_out, cudaStream_t st);
 
@@ -386,14 +386,27 @@ int zkvc_vk_load(const char* path, zkvc_vk** out) {
   return ZKVC_OK;
 }
 
-size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk) { return pk ? prove_workspace_bytes(pk) : 0; }
+size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk) { return pk ? prove_workspace_bytes(pk, ZKVC_PROVE_FOLD) : 0; }
+
+size_t zkvc_prove_workspace_bytes_mode(const zkvc_pk* pk, int mode) {
+  if (!pk || (mode != ZKVC_PROVE_FOLD && mode != ZKVC_PROVE_CHAIN)) return 0;
+  return prove_workspace_bytes(pk, mode);
+}
 
 int zkvc_prove(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint8_t rs[64], int32_t* dY, void* d_ws,
                size_t ws_bytes, uint8_t proof[256], void* stream) {
   set_error("%s", "");
   ZK_CHECK(pk, ZKVC_EINVAL, "prove: null key");
   ZK_TRY(device_guard(pk->device));
-  return prove_impl(pk, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
+  return prove_impl(pk, ZKVC_PROVE_FOLD, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
+}
+
+int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t rs[64], int32_t* dY,
+                    void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream) {
+  set_error("%s", "");
+  ZK_CHECK(pk, ZKVC_EINVAL, "prove: null key");
+  ZK_TRY(device_guard(pk->device));
+  return prove_impl(pk, mode, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -24,6 +24,8 @@ void set_error(const char* fmt, ...) {
 
 static void clear_error() { g_err.clear(); }
 
+const char* last_error_text() { return g_err.c_str(); }
+
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -10,6 +10,7 @@
 namespace zkvc {
 
 void set_error(const char* fmt, ...);
+const char* last_error_text();  // the calling thread's last error message
 
 // Number of kernels this library has launched in the process (diagnostics).
 void count_launch();

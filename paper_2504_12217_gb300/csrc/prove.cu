@@ -71,12 +71,26 @@ __global__ void k_check_h(const Fr* H, size_t N, int* flags) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && !ld_field(H + (N - 1)).is_zero()) atomicOr(flags, 2);
 }
 
-// rs[0] = r, rs[1] = s (canonical, from the caller); rs[2] = r s (canonical)
+// rs[0] = r, rs[1] = s (canonical, from the caller); rs[2] = r s, rs[3] = -r s (canonical)
 __global__ void k_randomness(Fr* rs, int* flags) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Fr r = ld_field(rs), s = ld_field(rs + 1);
   if (!canonical_fr(r) || !canonical_fr(s)) atomicOr(flags, 4);
-  st_field(rs + 2, f_mul(f_to_mont(r), s));  // (r R) s / R = r s, canonical
+  Fr rsv = f_mul(f_to_mont(r), s);  // (r R) s / R = r s, canonical
+  st_field(rs + 2, rsv);
+  st_field(rs + 3, f_neg(rsv));
+}
+
+// Chain mode: thread 0 computes s A, thread 1 r B1 (small-run outputs 0 and 2).
+__global__ void k_chains(const Fr* __restrict__ rs, const G1J* __restrict__ small, G1J* chain) {
+  const int t = threadIdx.x;
+  if (t >= 2) return;
+  const G1J P = ld_field(small + (t ? 2 : 0));
+  const Fr k = ld_field(rs + (t ? 0 : 1));
+  uint32_t kk[8];
+#pragma unroll
+  for (int l = 0; l < 8; l++) kk[l] = k.v[l];
+  st_field(chain + t, p_mul_scalar_w4(P, kk));
 }
 
 // sw[v] = s w_v for v = 0 .. l (one, X, Y) and rw[e] = r w_e for the W variables, in
@@ -96,22 +110,28 @@ __global__ void k_scaled_witness(const int8_t* __restrict__ X, const int32_t* __
   }
 }
 
-// Proof encoding.  A = small[0]; C = small[1] + rest[0] + hq[0].  Thread 0 converts A and
-// C with one shared inversion; thread 32 (another warp) converts B concurrently.
-__global__ void k_encode(const G1J* small, const G1J* rest, const G1J* hq, const G2J* res2, uint8_t* proof) {
+// Proof encoding.  A = small[0]; C = small[1] + x[0] + y[0] + (chain ? chain[0] + chain[1]
+// : 0), where (x, y) are the rest and H results (fold mode) or the main result and
+// infinity (chain mode).  Thread 0 converts A and C with one shared inversion; thread 32
+// (another warp) converts B concurrently.
+__global__ void k_encode(const G1J* small, const G1J* x, const G1J* y, const G1J* chain, const G2J* res2,
+                         uint8_t* proof) {
   if (threadIdx.x == 0) {
-    G1J A = ld_field(small), C = p_add(p_add(ld_field(small + 1), ld_field(rest)), ld_field(hq));
+    G1J A = ld_field(small), C = p_add(ld_field(small + 1), ld_field(x));
+    if (y) C = p_add(C, ld_field(y));
+    if (chain) C = p_add(C, p_add(ld_field(chain), ld_field(chain + 1)));
     encode_a_c(A, C, proof);
   } else if (threadIdx.x == 32) {
     encode_b(ld_field(res2), proof);
   }
 }
 
+
 // ------------------------------------------------------------------ plans and workspace
 struct ProveBufs {
   Fr *ak, *bk, *yz, *S, *ev, *rs, *sw, *rw;
   int* flags;
-  G1J *res_small, *res_rest, *res_h;
+  G1J *res_small, *res_rest, *res_h, *res_chain;
   G2J* res2;
   uint8_t* proof;
   void *ws_small, *ws_rest, *ws_h, *ws2;
@@ -131,7 +151,7 @@ static MsmSeg seg_of(const Region& r, uint32_t first, uint32_t count, uint32_t o
   return s;
 }
 
-// Four MSM runs (see the file comment for the terms), on four streams:
+// The MSM runs of one proof.  Fold mode (four runs on four streams):
 //   small (G1): output 0 = A, output 1 = the int8 part of C (L over the W variables);
 //   rest  (G1): the full-scalar part of C known right after the witness (L over S,
 //               s A_v, r B_e, s alpha, r beta, r s delta);
@@ -139,15 +159,19 @@ static MsmSeg seg_of(const Region& r, uint32_t first, uint32_t count, uint32_t o
 //   g2:         output 0 = B.
 // The small-scalar terms concentrate in buckets 1..128 and need long folds; "rest" does
 // not depend on h, so it overlaps the NTTs; only "h" follows them on the critical path.
+// Chain mode (three runs): small adds output 2 = B1 = [beta]1 + sum w_e [B_e]1 + s [delta]1,
+// "h" also takes L over S and -r s [delta]1, there is no "rest", and two variable-base
+// multiplications s A and r B1 complete C = L + H + s A + r B1 - r s delta.
 struct Plans {
   MsmPlan small, rest, h, g2;
 };
 
-static void plans(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const int32_t* dY, const Fr* S, const Fr* h,
-                  const Fr* rs, const Fr* sw, const Fr* rw, Plans* P) {
+static void plans(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const int32_t* dY, const Fr* S,
+                  const Fr* h, const Fr* rs, const Fr* sw, const Fr* rw, Plans* P) {
   const Shape& sh = pk->shape;
   const Region* g = pk->lay.g1;
   const uint32_t an = sh.a * sh.n, ab = sh.a * sh.b, nb = sh.n * sh.b;
+  const bool chain = mode == ZKVC_PROVE_CHAIN;
   // 8-bit digits: 128 buckets per output.  X and the constant one use window 0 of the
   // A-query (stride 16); Y and r [delta]1 use their own 2^(8 w) regions.
   P->small.outs = {{8, 1, 0, 0}, {8, 1, 0, 0}};
@@ -163,15 +187,25 @@ static void plans(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const i
   };
   P->h.outs = {{ZKVC_C1, 1, 0, 0}};
   P->h.segs = {seg_of(g[R1_H], 0, (uint32_t)sh.N, 0, SK_FR_MONT, h, (uint32_t)sh.N - 1)};
-  P->rest.outs = {{ZKVC_C1, 1, 0, 0}};
-  P->rest.segs = {
-      seg_of(g[R1_LS], 0, (uint32_t)(sh.n - 1), 0, SK_FR_MONT, S),
-      seg_of(g[R1_A], 0, sh.l + 1, 0, SK_FR_MONT, sw),
-      seg_of(g[R1_B], 0, nb, 0, SK_FR_MONT, rw),
-      seg_of(g[R1_ALPHA], 0, 1, 0, SK_FR_CANON, rs + 1),
-      seg_of(g[R1_BETA], 0, 1, 0, SK_FR_CANON, rs + 0),
-      seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 2),
-  };
+  if (chain) {
+    P->small.outs.push_back({8, 1, 0, 0});
+    P->small.segs.push_back(seg_of(g[R1_B], 0, nb, 2, SK_I8, dW));
+    P->small.segs.push_back(seg_of(g[R1_BETA], 0, 1, 2, SK_ONE, nullptr));
+    P->small.segs.push_back(seg_of(g[R1_DELTA8], 0, 1, 2, SK_FR_CANON, rs + 1));
+    P->h.segs.push_back(seg_of(g[R1_LS], 0, (uint32_t)(sh.n - 1), 0, SK_FR_MONT, S));
+    P->h.segs.push_back(seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 3));
+  } else {
+    P->rest.outs = {{ZKVC_C1, 1, 0, 0}};
+    P->rest.segs = {
+        seg_of(g[R1_LS], 0, (uint32_t)(sh.n - 1), 0, SK_FR_MONT, S),
+        seg_of(g[R1_A], 0, sh.l + 1, 0, SK_FR_MONT, sw),
+        seg_of(g[R1_B], 0, nb, 0, SK_FR_MONT, rw),
+        seg_of(g[R1_ALPHA], 0, 1, 0, SK_FR_CANON, rs + 1),
+        seg_of(g[R1_BETA], 0, 1, 0, SK_FR_CANON, rs + 0),
+        seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 2),
+    };
+    msm_plan_finalize(P->rest);
+  }
   const Region* g2 = pk->lay.g2;
   P->g2.outs = {{ZKVC_C2, 1, 0, 0}};
   P->g2.segs = {
@@ -180,13 +214,13 @@ static void plans(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const i
       seg_of(g2[R2_DELTA], 0, 1, 0, SK_FR_CANON, rs + 1),
   };
   msm_plan_finalize(P->small);
-  msm_plan_finalize(P->rest);
   msm_plan_finalize(P->h);
   msm_plan_finalize(P->g2);
 }
 
-static size_t carve(const zkvc_pk* pk, void* base, size_t cap, ProveBufs* B, bool measuring) {
+static size_t carve(const zkvc_pk* pk, int mode, void* base, size_t cap, ProveBufs* B, bool measuring) {
   const Shape& sh = pk->shape;
+  const bool chain = mode == ZKVC_PROVE_CHAIN;
   Arena a;
   a.base = reinterpret_cast<uint8_t*>(base);
   a.cap = cap;
@@ -197,22 +231,23 @@ static size_t carve(const zkvc_pk* pk, void* base, size_t cap, ProveBufs* B, boo
   B->S = a.take<Fr>(sh.n);
   B->ev = a.take<Fr>(4 * sh.N);
   B->rs = a.take<Fr>(4);
-  B->sw = a.take<Fr>(sh.l + 1);
-  B->rw = a.take<Fr>(size_t(sh.n) * sh.b);
+  B->sw = chain ? nullptr : a.take<Fr>(sh.l + 1);
+  B->rw = chain ? nullptr : a.take<Fr>(size_t(sh.n) * sh.b);
   B->flags = a.take<int>(4);
-  B->res_small = a.take<G1J>(2);
+  B->res_small = a.take<G1J>(3);
   B->res_rest = a.take<G1J>(1);
   B->res_h = a.take<G1J>(1);
+  B->res_chain = a.take<G1J>(2);
   B->res2 = a.take<G2J>(1);
   B->proof = a.take<uint8_t>(256);
   Plans P;
-  plans(pk, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &P);
+  plans(pk, mode, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &P);
   B->ws_small_bytes = msm_workspace_bytes<Fp>(P.small);
-  B->ws_rest_bytes = msm_workspace_bytes<Fp>(P.rest);
+  B->ws_rest_bytes = chain ? 0 : msm_workspace_bytes<Fp>(P.rest);
   B->ws_h_bytes = msm_workspace_bytes<Fp>(P.h);
   B->ws2_bytes = msm_workspace_bytes<Fp2>(P.g2);
   B->ws_small = a.take<uint8_t>(B->ws_small_bytes);
-  B->ws_rest = a.take<uint8_t>(B->ws_rest_bytes);
+  B->ws_rest = chain ? nullptr : a.take<uint8_t>(B->ws_rest_bytes);
   B->ws_h = a.take<uint8_t>(B->ws_h_bytes);
   B->ws2 = a.take<uint8_t>(B->ws2_bytes);
   return a.off;
@@ -247,19 +282,31 @@ static int side_streams(SideStreams** out) {
   return ZKVC_OK;
 }
 
-size_t prove_workspace_bytes(const zkvc_pk* pk) {
+size_t prove_workspace_bytes(const zkvc_pk* pk, int mode) {
   ProveBufs B;
-  return carve(pk, nullptr, 0, &B, true);
+  return carve(pk, mode, nullptr, 0, &B, true);
 }
 
-int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host, int32_t* dY, void* ws,
-               size_t ws_bytes, uint8_t* proof_host, cudaStream_t st) {
-  ZK_CHECK(pk && dX && dW && rs_host && dY && ws && proof_host, ZKVC_EINVAL, "prove: null argument");
-  size_t need = prove_workspace_bytes(pk);
+static int fork_to(SideStreams* side, int i, cudaStream_t st) {
+  ZK_CUDA(cudaEventRecord(side->fork[i], st));
+  ZK_CUDA(cudaStreamWaitEvent(side->st[i], side->fork[i], 0));
+  return ZKVC_OK;
+}
+
+// Enqueues one proof on st (and the calling thread's side streams, joined back into st).
+// rs_host is read before the call returns; the proof lands in proof_out and the device
+// flags in flags_out (host pointers, written when st reaches them: pinned memory lets the
+// copies run asynchronously).
+int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host,
+                  int32_t* dY, void* ws, size_t ws_bytes, uint8_t* proof_out, int* flags_out, cudaStream_t st) {
+  ZK_CHECK(pk && dX && dW && rs_host && dY && ws && proof_out && flags_out, ZKVC_EINVAL, "prove: null argument");
+  ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN, ZKVC_EINVAL, "prove: mode %d", mode);
+  size_t need = prove_workspace_bytes(pk, mode);
   ZK_CHECK(ws_bytes >= need, ZKVC_EINVAL, "prove: workspace %zu < %zu bytes", ws_bytes, need);
+  const bool chain = mode == ZKVC_PROVE_CHAIN;
   const Shape& sh = pk->shape;
   ProveBufs B;
-  carve(pk, ws, ws_bytes, &B, false);
+  carve(pk, mode, ws, ws_bytes, &B, false);
   const size_t N = sh.N;
   Fr* Aev = B.ev;
   Fr* Bev = B.ev + N;
@@ -274,9 +321,8 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   SideStreams* side = nullptr;
   ZK_TRY(side_streams(&side));
   Plans P;
-  plans(pk, dX, dW, dY, B.S, Hev, B.rs, B.sw, B.rw, &P);
-  ZK_CUDA(cudaEventRecord(side->fork[0], st));
-  ZK_CUDA(cudaStreamWaitEvent(side->st[0], side->fork[0], 0));
+  plans(pk, mode, dX, dW, dY, B.S, Hev, B.rs, B.sw, B.rw, &P);
+  ZK_TRY(fork_to(side, 0, st));
   prof_mark(PS_MSM_G2, true, side->st[0]);
   ZK_TRY(msm_run<Fp2>(P.g2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st[0], PS_ACCUM_G2));
   prof_mark(PS_MSM_G2, false, side->st[0]);
@@ -289,29 +335,35 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz); ZK_COUNT_LAUNCH();
   k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, B.S, Aev, Bev, Cev, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  // the small-scalar G1 MSM (A and the int8 part of C) on side stream 1: needs X, Y, W, r
-  ZK_CUDA(cudaEventRecord(side->fork[1], st));
-  ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->fork[1], 0));
+  // the small-scalar G1 MSM on side stream 1 (needs X, Y, W, r, s), then in chain mode
+  // the two variable-base multiplications
+  ZK_TRY(fork_to(side, 1, st));
   ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
+  if (chain) {
+    k_chains<<<1, 32, 0, side->st[1]>>>(B.rs, B.res_small, B.res_chain); ZK_COUNT_LAUNCH();
+    ZK_CUDA(cudaGetLastError());
+  }
   ZK_CUDA(cudaEventRecord(side->join[1], side->st[1]));
-  // 4. remaining domain evaluations and the scalars s w_v, r w_e
+  // 4. remaining domain evaluations (and, in fold mode, the scalars s w_v, r w_e)
   size_t rest = N - sh.n;
   k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev); ZK_COUNT_LAUNCH();
-  uint32_t nsc = sh.l + 1 + uint32_t(sh.n) * sh.b;
-  k_scaled_witness<<<(nsc + 255) / 256, 256, 0, st>>>(dX, dY, dW, B.rs, sh.a * sh.n, sh.l, uint32_t(sh.n) * sh.b, B.sw,
-                                                      B.rw); ZK_COUNT_LAUNCH();
+  if (!chain) {
+    uint32_t nsc = sh.l + 1 + uint32_t(sh.n) * sh.b;
+    k_scaled_witness<<<(nsc + 255) / 256, 256, 0, st>>>(dX, dY, dW, B.rs, sh.a * sh.n, sh.l, uint32_t(sh.n) * sh.b,
+                                                        B.sw, B.rw); ZK_COUNT_LAUNCH();
+  }
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_WITNESS, false, st);
-  // the full-scalar G1 terms that need no h, on side stream 2 (overlapping the NTTs)
-  ZK_CUDA(cudaEventRecord(side->fork[2], st));
-  ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->fork[2], 0));
-  prof_mark(PS_MSM_G1, true, side->st[2]);
-  ZK_TRY(msm_run<Fp>(P.rest, pk->g1, B.ws_rest, B.ws_rest_bytes, B.res_rest, side->st[2], PS_ACCUM_G1));
-  prof_mark(PS_MSM_G1, false, side->st[2]);
-  ZK_CUDA(cudaEventRecord(side->join[2], side->st[2]));
+  if (!chain) {
+    // the full-scalar G1 terms that need no h, on side stream 2 (overlapping the NTTs)
+    ZK_TRY(fork_to(side, 2, st));
+    prof_mark(PS_MSM_G1, true, side->st[2]);
+    ZK_TRY(msm_run<Fp>(P.rest, pk->g1, B.ws_rest, B.ws_rest_bytes, B.res_rest, side->st[2], PS_ACCUM_G1));
+    prof_mark(PS_MSM_G1, false, side->st[2]);
+    ZK_CUDA(cudaEventRecord(side->join[2], side->st[2]));
+  }
   // 5-6. quotient and the H part of C on side stream 3 (the critical chain)
-  ZK_CUDA(cudaEventRecord(side->fork[3], st));
-  ZK_CUDA(cudaStreamWaitEvent(side->st[3], side->fork[3], 0));
+  ZK_TRY(fork_to(side, 3, st));
   cudaStream_t s3 = side->st[3];
   prof_mark(PS_NTT, true, s3);
   const NttDomain* d = pk->dom;
@@ -322,23 +374,43 @@ int prove_impl(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   k_check_h<<<1, 32, 0, s3>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_NTT, false, s3);
-  ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3));
+  if (chain) prof_mark(PS_MSM_G1, true, s3);
+  ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3, chain ? PS_ACCUM_G1 : -1));
+  if (chain) prof_mark(PS_MSM_G1, false, s3);
   ZK_CUDA(cudaEventRecord(side->join[3], s3));
-  for (int i = 0; i < NSIDE; i++) ZK_CUDA(cudaStreamWaitEvent(st, side->join[i], 0));
+  for (int i = 0; i < NSIDE; i++) {
+    if (chain && i == 2) continue;
+    ZK_CUDA(cudaStreamWaitEvent(st, side->join[i], 0));
+  }
   // 7. encode
   prof_mark(PS_COMBINE, true, st);
-  k_encode<<<1, 64, 0, st>>>(B.res_small, B.res_rest, B.res_h, B.res2, B.proof); ZK_COUNT_LAUNCH();
+  if (chain)
+    k_encode<<<1, 64, 0, st>>>(B.res_small, B.res_h, nullptr, B.res_chain, B.res2, B.proof);
+  else
+    k_encode<<<1, 64, 0, st>>>(B.res_small, B.res_rest, B.res_h, nullptr, B.res2, B.proof);
+  ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_COMBINE, false, st);
-  int flags = 0;
-  ZK_CUDA(cudaMemcpyAsync(proof_host, B.proof, 256, cudaMemcpyDeviceToHost, st));
-  ZK_CUDA(cudaMemcpyAsync(&flags, B.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-  ZK_CUDA(cudaStreamSynchronize(st));
-  prof_collect();
+  ZK_CUDA(cudaMemcpyAsync(proof_out, B.proof, 256, cudaMemcpyDeviceToHost, st));
+  ZK_CUDA(cudaMemcpyAsync(flags_out, B.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  return ZKVC_OK;
+}
+
+// Status of a finished proof from its device flags.
+int prove_status(int flags) {
   ZK_CHECK(!(flags & 4), ZKVC_EINVAL, "prove: r or s is not a canonical Fr element");
   ZK_CHECK(!(flags & 1), ZKVC_EUNSAT, "prove: the PSQ chain does not close against Y(z)");
   ZK_CHECK(!(flags & 2), ZKVC_EUNSAT, "prove: the quotient has degree N - 1 (QAP not satisfied)");
   return ZKVC_OK;
+}
+
+int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host, int32_t* dY,
+               void* ws, size_t ws_bytes, uint8_t* proof_host, cudaStream_t st) {
+  int flags = 0;
+  ZK_TRY(prove_enqueue(pk, mode, dX, dW, rs_host, dY, ws, ws_bytes, proof_host, &flags, st));
+  ZK_CUDA(cudaStreamSynchronize(st));
+  prof_collect();
+  return prove_status(flags);
 }
 
 }  // namespace zkvc

@@ -64,6 +64,8 @@ SIGNATURES = {
     "zkvc_vk_load": (_c_int, [ctypes.c_char_p, ctypes.POINTER(_c_p)]),
     "zkvc_prove_workspace_bytes": (_c_sz, [_c_p]),
     "zkvc_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
+    "zkvc_prove_workspace_bytes_mode": (_c_sz, [_c_p, _c_int]),
+    "zkvc_prove_mode": (_c_int, [_c_p, _c_int, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_batch_create": (_c_int, [_c_p, _c_int, _c_int, ctypes.POINTER(_c_p)]),
     "zkvc_batch_free": (None, [_c_p]),
     "zkvc_batch_info": (_c_int, [_c_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_sz), ctypes.POINTER(ctypes.c_uint64)]),
@@ -73,6 +75,14 @@ SIGNATURES = {
     "zkvc_batch_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
     "zkvc_prove_batch": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_int, _c_p, _c_p, _c_p, _c_p]),
     "zkvc_set_wait_timeout_ms": (_c_int, [_c_int]),
+    "zkvc_server_create": (_c_int, [_c_p, _c_int, _c_int, _c_sz, _c_int, ctypes.POINTER(_c_p)]),
+    "zkvc_server_free": (None, [_c_p]),
+    "zkvc_server_submit": (_c_int, [_c_p, _c_int, _c_p, _c_p, _c_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "zkvc_server_wait": (_c_int, [_c_p, ctypes.c_uint64, _c_int, _c_p, _c_p, _c_p, ctypes.POINTER(_c_int)]),
+    "zkvc_server_stats": (_c_int, [_c_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_c_int),
+                                   ctypes.POINTER(_c_int), ctypes.POINTER(_c_sz), ctypes.POINTER(_c_sz),
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+    "zkvc_server_request_bytes": (_c_sz, [_c_p, _c_int]),
 }
 
 ZKVC_Q_A, ZKVC_Q_B1, ZKVC_Q_B2, ZKVC_Q_L, ZKVC_Q_H = 0, 1, 2, 3, 4
@@ -382,6 +392,34 @@ def zkvc_prove_workspace_bytes(pk):
     return lib().zkvc_prove_workspace_bytes(pk.handle)
 
 
+ZKVC_PROVE_FOLD = 0
+ZKVC_PROVE_CHAIN = 1
+
+
+def zkvc_prove_workspace_bytes_mode(pk, mode):
+    return lib().zkvc_prove_workspace_bytes_mode(pk.handle, mode)
+
+
+def zkvc_prove_mode(pk, mode, X, W, rs, Y=None, workspace=None):
+    """zkvc_prove with an explicit mode (ZKVC_PROVE_FOLD or ZKVC_PROVE_CHAIN)."""
+    torch = _torch()
+    a, n, b = pk.shape
+    if X.dtype != torch.int8 or tuple(X.shape) != (a, n) or W.dtype != torch.int8 or tuple(W.shape) != (n, b):
+        raise ValueError(f"expected X int8 [{a}, {n}] and W int8 [{n}, {b}]")
+    if len(rs) != 64:
+        raise ValueError("rs must be 64 bytes")
+    if Y is None:
+        Y = torch.empty((a, b), dtype=torch.int32, device=X.device)
+    need = zkvc_prove_workspace_bytes_mode(pk, mode)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=X.device)
+    proof = ctypes.create_string_buffer(256)
+    rsb = ctypes.create_string_buffer(bytes(rs), 64)
+    check(lib().zkvc_prove_mode(pk.handle, mode, _dev_ptr(X), _dev_ptr(W), rsb, _dev_ptr(Y), _dev_ptr(workspace),
+                                workspace.numel(), proof, _stream()))
+    return proof.raw, Y
+
+
 def zkvc_prove(pk, X, W, rs, Y=None, workspace=None):
     """Prove Y = X W.  X: [a, n] int8 CUDA tensor, W: [n, b] int8, rs: 64 bytes (r || s).
     Returns (proof bytes, Y as an [a, b] int32 CUDA tensor)."""
@@ -503,3 +541,71 @@ def zkvc_prove_batch(pks, Xs, Ws, rs_list):
     proofs = ctypes.create_string_buffer(256 * n)
     check(lib().zkvc_prove_batch(keys, xs, ws, rsb, n, ys, proofs, None, _stream()))
     return [proofs.raw[256 * i: 256 * (i + 1)] for i in range(n)], Ys
+
+
+# ------------------------------------------------------------------ proof server
+ZKVC_SERVER_ADAPTIVE = 0
+ZKVC_SERVER_FOLD = 1
+ZKVC_SERVER_CHAIN = 2
+
+
+def zkvc_server_request_bytes(pk, mode):
+    return lib().zkvc_server_request_bytes(pk.handle, mode)
+
+
+class Server:
+    """Owns a zkvc_server handle: continuous batching of proof requests over resident
+    keys.  submit() returns a ticket; wait() returns the result."""
+
+    def __init__(self, pks, slots=4, mem_budget=8 << 30, policy=ZKVC_SERVER_ADAPTIVE):
+        self.pks = list(pks)
+        h = _c_p()
+        keys = _ptr_array([pk.handle for pk in self.pks])
+        check(lib().zkvc_server_create(keys, len(self.pks), slots, mem_budget, policy, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.zkvc_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, key, X, W, rs):
+        """X, W: int8 numpy arrays (host) of key `key`'s shape; rs: 64 bytes."""
+        import numpy as np
+        Xn = np.ascontiguousarray(np.asarray(X, dtype=np.int8))
+        Wn = np.ascontiguousarray(np.asarray(W, dtype=np.int8))
+        if 0 <= key < len(self.pks):  # the library rejects other key indices itself
+            a, n, b = self.pks[key].shape
+            Xn, Wn = Xn.reshape(a, n), Wn.reshape(n, b)
+        if len(rs) != 64:
+            raise ValueError("rs must be 64 bytes")
+        t = ctypes.c_uint64()
+        check(lib().zkvc_server_submit(self.handle, key, Xn.ctypes.data_as(_c_p), Wn.ctypes.data_as(_c_p), bytes(rs),
+                                       ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket, key, timeout_ms=60000):
+        """(status, proof bytes or None, Y numpy int32 or None, {queue_ms, prove_ms, total_ms});
+        raises ZkvcError(ZKVC_ETIMEOUT) if the request is not done in time."""
+        import numpy as np
+        a, n, b = self.pks[key].shape if 0 <= key < len(self.pks) else (1, 1, 1)
+        proof = ctypes.create_string_buffer(256)
+        Y = np.empty((a, b), dtype=np.int32)
+        times = (ctypes.c_double * 3)()
+        status = _c_int()
+        check(lib().zkvc_server_wait(self.handle, ticket, int(timeout_ms), proof, Y.ctypes.data_as(_c_p), times,
+                                     ctypes.byref(status)))
+        t = {"queue_ms": times[0], "prove_ms": times[1], "total_ms": times[2]}
+        if status.value != ZKVC_OK:
+            return status.value, None, None, t
+        return ZKVC_OK, proof.raw, Y, t
+
+    def stats(self):
+        c, f, q, u, p, ch = ctypes.c_uint64(), _c_int(), _c_int(), _c_sz(), _c_sz(), ctypes.c_uint64()
+        check(lib().zkvc_server_stats(self.handle, ctypes.byref(c), ctypes.byref(f), ctypes.byref(q), ctypes.byref(u),
+                                      ctypes.byref(p), ctypes.byref(ch)))
+        return {"completed": c.value, "in_flight": f.value, "queued": q.value, "bytes_in_use": u.value,
+                "peak_bytes": p.value, "chain_mode": ch.value}
