@@ -51,6 +51,28 @@ def _env_int(name, default):
         return default
 
 
+# ------------------------------------------------------------------ replicas
+def rank_seed(base, rank):
+    """Seed of the instances rank `rank` proves: ranks are replicas over disjoint inputs
+    (proofs are independent, so no collective touches the data path)."""
+    return base + 7919 * rank
+
+
+def reduce_max(x, dist, device):
+    """Max over ranks of a host float (the timed region's length); identity without dist."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, world, seconds_max):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -297,7 +319,7 @@ def run_gpu(args):
             dist.barrier()
 
     a, n, b = SHAPE
-    seed = inputs.SEED_CFG[2] + rank
+    seed = rank_seed(inputs.SEED_CFG[2], rank)
     inst = inputs.instance(seed, SHAPE)
     pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(inst["toxic"]))
     Xd = torch.from_numpy(inst["X"]).cuda()
@@ -334,12 +356,8 @@ def run_gpu(args):
     prof = nv.zkvc_profile_read()
     nv.zkvc_profile_enable(False)
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    total_s = reduce_max(sum(step_ms) / 1e3, dist, "cuda")
+    value = replica_value(args.steps, world, total_s)
 
     # ---- end to end through the public API: pinned host inputs, results read back
     Xh = torch.from_numpy(inst["X"]).pin_memory()
@@ -355,12 +373,8 @@ def run_gpu(args):
         proof, _ = nv.zkvc_prove(pk, Xd, Wd, rs_list[i % total_steps], Y=Yd, workspace=ws)
         Yh.copy_(Yd, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": a * n + n * b,
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": replica_value(e2e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": a * n + n * b,
            "d2h_bytes_per_step": 256 + 4 * a * b}
 
     if rank != 0:
@@ -435,7 +449,7 @@ def run_batched(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    shapes = inputs.batch_shapes(inputs.SEED_CFG[4] + rank)
+    shapes = inputs.batch_shapes(rank_seed(inputs.SEED_CFG[4], rank))
     t0 = time.perf_counter()
     keys = {}
     for s in dict.fromkeys(shapes):
@@ -477,13 +491,9 @@ def run_batched(args):
     clk = clocks.stop()
     launches = nv.zkvc_kernel_launches() - launches0
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = reduce_max(sum(step_ms) / 1e3, dist, "cuda")
     count = len(shapes)
-    value = world * count * args.steps / total_s
+    value = replica_value(count * args.steps, world, total_s)
     terms = batch.terms()
 
     # end to end: pinned host matrices copied in, Y and proofs read back, every step
@@ -503,7 +513,7 @@ def run_batched(args):
         for h, d in zip(Yh, Ys):
             h.copy_(d, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
     h2d = sum(s[0] * s[1] + s[1] * s[2] for s in shapes)
     d2h = sum(256 + 4 * s[0] * s[2] for s in shapes)
     # parity spot check of the last step against the one-proof prover (not timed)
@@ -529,7 +539,7 @@ def run_batched(args):
                    "l2": "flushed by a 256 MiB write between steps", "parallelism": f"replicas x{world}",
                    "graph": True, "tuning": batch.get_tuning()},
         "latency_ms": {"p50_batch": statistics.median(step_ms), "p99_batch": p99, "min": srt[0], "max": srt[-1]},
-        "e2e": {"value": world * count * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": replica_value(count * e2e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "batch_roofline": {"bound": "alu", "scope": "whole batch (all kernels, overlapped)",
                            "achieved": work / per_step / 1e12, "peak": peak, "unit": "TIMAD/s",
