@@ -450,6 +450,8 @@ def run_batched(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     shapes = inputs.batch_shapes(rank_seed(inputs.SEED_CFG[4], rank))
+    if args.batch_count:  # a smaller case: the K smallest instances of the seeded mix
+        shapes = sorted(shapes, key=lambda s: s[0] * s[1] + s[0] * s[2] + s[1] * s[2])[: args.batch_count]
     t0 = time.perf_counter()
     keys = {}
     for s in dict.fromkeys(shapes):
@@ -463,7 +465,12 @@ def run_batched(args):
                      [inputs.to_bytes32(t["rs"]) for t in insts], insts))
     Ys = [torch.empty((s[0], s[2]), dtype=torch.int32, device="cuda") for s in shapes]
     t0 = time.perf_counter()
-    batch = nv.Batch([keys[s] for s in shapes], flags=nv.ZKVC_BATCH_AUTOTUNE)
+    flags = nv.ZKVC_BATCH_EAGER if args.eager else 0
+    if not args.tuning:
+        flags |= nv.ZKVC_BATCH_AUTOTUNE
+    batch = nv.Batch([keys[s] for s in shapes], flags=flags)
+    if args.tuning:
+        batch.set_tuning(args.tuning)
     nv.zkvc_set_wait_timeout_ms(120000)
     batch.prove(sets[0][0], sets[0][1], sets[0][2], Ys)  # autotune + capture
     torch.cuda.synchronize()
@@ -537,7 +544,8 @@ def run_batched(args):
         "config": {"workload": "crpc_groth16_bn254_batched_64mix", "instances": count,
                    "distinct_shapes": len(keys), "shape_set": "a in {49,64,128,197}, n in {192,320,384,768}, b in {n,4n}",
                    "l2": "flushed by a 256 MiB write between steps", "parallelism": f"replicas x{world}",
-                   "graph": True, "tuning": batch.get_tuning()},
+                   "graph": not args.eager, "tuning": batch.get_tuning(),
+                   "tuning_source": "imposed" if args.tuning else "autotuned on the first call"},
         "latency_ms": {"p50_batch": statistics.median(step_ms), "p99_batch": p99, "min": srt[0], "max": srt[-1]},
         "e2e": {"value": replica_value(count * e2e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -697,6 +705,9 @@ def main():
     ap.add_argument("--max-requests", type=int, default=1200)
     ap.add_argument("--server-slots", type=int, default=8)
     ap.add_argument("--server-budget-gib", type=int, default=48)
+    ap.add_argument("--batch-count", type=int, default=0, help="batched: only the K smallest instances")
+    ap.add_argument("--tuning", type=int, nargs=10, default=None, help="batched: impose a tuning, skip the autotuner")
+    ap.add_argument("--eager", action="store_true", help="batched: launch eagerly instead of replaying a graph")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)

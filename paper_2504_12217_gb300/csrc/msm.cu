@@ -242,20 +242,97 @@ __global__ void k_digits(const MsmSeg* __restrict__ segs, int nsegs, const MsmOu
   }
 }
 
-__global__ void k_hist(const uint32_t* keys, uint64_t n, uint32_t* counts) {
-  uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t k = keys[i];
-  if (k != KEY_NONE) atomicAdd(counts + k, 1u);
+// Counting sort by key.  A block takes a tile of HB_TILE consecutive slots and counts
+// the keys in a window of HB_BINS keys starting at the tile's smallest key in shared
+// memory, so a bucket that many terms share (small-scalar runs put thousands of terms in
+// each of 128 buckets) costs one global atomic per block instead of one per term; keys
+// outside the window fall back to global atomics.  The scatter repeats the count,
+// reserves each bin's range with one global atomic, and places the tile's terms with
+// shared-memory atomics.  (Positions inside a bucket are in no fixed order; bucket sums
+// do not depend on it.)
+constexpr int HB_THREADS = 256, HB_PER = 8, HB_TILE = HB_THREADS * HB_PER, HB_BINS = 2048;
+
+__device__ __forceinline__ uint32_t tile_min_key(const uint32_t (&k)[HB_PER], uint32_t* kmin_s) {
+  uint32_t m = KEY_NONE;
+#pragma unroll
+  for (int j = 0; j < HB_PER; j++) m = min(m, k[j]);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, d));
+  if ((threadIdx.x & 31) == 0) atomicMin(kmin_s, m);
+  __syncthreads();
+  return *kmin_s;
 }
 
-__global__ void k_scatter(const uint32_t* keys, const uint32_t* vals, uint64_t n, uint32_t* cursor, uint32_t* sorted) {
-  uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t k = keys[i];
-  if (k == KEY_NONE) return;
-  uint32_t pos = atomicAdd(cursor + k, 1u);
-  sorted[pos] = vals[i];
+__global__ void __launch_bounds__(HB_THREADS) k_hist(const uint32_t* __restrict__ keys, uint64_t n, uint32_t* counts) {
+  __shared__ uint32_t hist[HB_BINS];
+  __shared__ uint32_t kmin_s;
+  const uint64_t base = uint64_t(blockIdx.x) * HB_TILE;
+  uint32_t k[HB_PER];
+#pragma unroll
+  for (int j = 0; j < HB_PER; j++) {
+    uint64_t i = base + uint64_t(j) * HB_THREADS + threadIdx.x;
+    k[j] = i < n ? keys[i] : KEY_NONE;
+  }
+  for (int b = threadIdx.x; b < HB_BINS; b += HB_THREADS) hist[b] = 0;
+  if (threadIdx.x == 0) kmin_s = KEY_NONE;
+  __syncthreads();
+  const uint32_t k0 = tile_min_key(k, &kmin_s);
+  if (k0 == KEY_NONE) return;  // uniform: the whole tile is empty
+#pragma unroll
+  for (int j = 0; j < HB_PER; j++) {
+    if (k[j] == KEY_NONE) continue;
+    uint32_t d = k[j] - k0;
+    if (d < (uint32_t)HB_BINS)
+      atomicAdd(&hist[d], 1u);
+    else
+      atomicAdd(counts + k[j], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < HB_BINS; b += HB_THREADS) {
+    uint32_t c = hist[b];
+    if (c) atomicAdd(counts + k0 + b, c);
+  }
+}
+
+__global__ void __launch_bounds__(HB_THREADS) k_scatter(const uint32_t* __restrict__ keys,
+                                                        const uint32_t* __restrict__ vals, uint64_t n,
+                                                        uint32_t* cursor, uint32_t* sorted) {
+  __shared__ uint32_t hist[HB_BINS];
+  __shared__ uint32_t start[HB_BINS];
+  __shared__ uint32_t kmin_s;
+  const uint64_t base = uint64_t(blockIdx.x) * HB_TILE;
+  uint32_t k[HB_PER];
+#pragma unroll
+  for (int j = 0; j < HB_PER; j++) {
+    uint64_t i = base + uint64_t(j) * HB_THREADS + threadIdx.x;
+    k[j] = i < n ? keys[i] : KEY_NONE;
+  }
+  for (int b = threadIdx.x; b < HB_BINS; b += HB_THREADS) hist[b] = 0;
+  if (threadIdx.x == 0) kmin_s = KEY_NONE;
+  __syncthreads();
+  const uint32_t k0 = tile_min_key(k, &kmin_s);
+  if (k0 == KEY_NONE) return;
+#pragma unroll
+  for (int j = 0; j < HB_PER; j++) {
+    if (k[j] == KEY_NONE) continue;
+    uint32_t d = k[j] - k0;
+    if (d < (uint32_t)HB_BINS) atomicAdd(&hist[d], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < HB_BINS; b += HB_THREADS) {
+    uint32_t c = hist[b];
+    if (c) start[b] = atomicAdd(cursor + k0 + b, c);
+    hist[b] = 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < HB_PER; j++) {
+    if (k[j] == KEY_NONE) continue;
+    uint64_t i = base + uint64_t(j) * HB_THREADS + threadIdx.x;
+    uint32_t d = k[j] - k0;
+    uint32_t pos = d < (uint32_t)HB_BINS ? start[d] + atomicAdd(&hist[d], 1u) : atomicAdd(cursor + k[j], 1u);
+    sorted[pos] = vals[i];
+  }
 }
 
 __global__ void k_chunks(const uint32_t* counts, uint32_t K, uint32_t T0, uint32_t* nch) {
@@ -622,15 +699,15 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   // counting sort by bucket key
   ZK_CUDA(cudaMemsetAsync(L.counts, 0, size_t(K) * sizeof(uint32_t), st));
   ZK_CUDA(cudaMemsetAsync(L.max_chunks, 0, sizeof(uint32_t), st));
-  unsigned sb = (unsigned)((S + 255) / 256);
+  unsigned sb = (unsigned)((S + HB_TILE - 1) / HB_TILE);
   if (S > 0) {
-    k_hist<<<sb, 256, 0, st>>>(L.keys, S, L.counts); ZK_COUNT_LAUNCH();
+    k_hist<<<sb, HB_THREADS, 0, st>>>(L.keys, S, L.counts); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
   ZK_TRY(scan_u32(L.counts, L.offs, K, a, st));
   ZK_CUDA(cudaMemcpyAsync(L.cursor, L.offs, size_t(K) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
   if (S > 0) {
-    k_scatter<<<sb, 256, 0, st>>>(L.keys, L.vals, S, L.cursor, L.sorted); ZK_COUNT_LAUNCH();
+    k_scatter<<<sb, HB_THREADS, 0, st>>>(L.keys, L.vals, S, L.cursor, L.sorted); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
   // chunks of T0 terms per bucket
