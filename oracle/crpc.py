@@ -31,27 +31,50 @@ After the n CRPC rows come l + 1 input-consistency rows n + i (i = 0..l) with A 
 B = C = 0, the libsnark convention that binds the public inputs into the QAP.
 The domain size is the next power of two >= n + l + 1.
 
-Pins (tests/test_oracle_crpc.py): the worked 3x2 . 2x2 example of Sec. III-A (golden
-exponents), the identity as integer polynomials in Z, constraint satisfaction against a
-direct integer matmul, the constraint counts (n vs a b n) and the PSQ left-wire counts
-(6 vs 3 for a 3-term dot product), and the paper's two negative examples.
+The ablation circuits of Sec. V (Table II) share the variable order one | X | Y | W |
+auxiliary and differ in the auxiliary variables and rows (see CIRCUITS below); with
+public_io = "none" only the constant one is public (l = 0), so X and Y join the private
+variables and only one input-consistency row remains.
+
+Pins (tests/test_oracle_crpc.py, tests/test_oracle_circuits.py): the worked 3x2 . 2x2
+example of Sec. III-A (golden exponents), the identity as integer polynomials in Z,
+constraint satisfaction against a direct integer matmul, the constraint counts (n vs
+a b n) and the PSQ left-wire counts (6 vs 3 for a 3-term dot product), the paper's two
+negative examples, and for every circuit and public-input choice: satisfaction, a
+tampered output failing, row and variable counts, and honest Groth16 proofs verifying.
 """
 from .bn254 import R, fr_from_int
 
+# Circuit variants of the paper's ablation (Sec. V, Table II):
+#   "crpc_psq"  CRPC (Sec. III-A) with the PSQ chain (Sec. III-B)  -- the zkVC circuit
+#   "crpc"      CRPC without PSQ: product variables p_k = a_k b_k and one summing row
+#   "psq"       no CRPC, PSQ only: per output y_ij a prefix-sum chain over its n products
+#   "vanilla"   no CRPC, no PSQ: one row per product x_ik w_kj = p_ijk (a b n rows, the
+#               count Sec. III-A starts from) and one summing row per output
+# and the public-input choice: "xy" (X and Y public, the default reading) or "none" (X and
+# Y private too; only the constant one is public).
+CIRCUITS = ("crpc_psq", "crpc", "psq", "vanilla")
+PUBLIC_IO = ("xy", "none")
+
 
 class Shape:
-    def __init__(self, a, n, b):
+    def __init__(self, a, n, b, circuit="crpc_psq", public_io="xy"):
         assert a >= 1 and n >= 1 and b >= 1
+        assert circuit in CIRCUITS and public_io in PUBLIC_IO
         self.a, self.n, self.b = a, n, b
-        self.n_public = a * n + a * b                    # l
-        self.n_vars = 1 + self.n_public + n * b + (n - 1)
-        self.n_rows = n + self.n_public + 1
+        self.circuit, self.public_io = circuit, public_io
+        self.n_io = a * n + a * b                          # entries of X and Y
+        self.n_public = self.n_io if public_io == "xy" else 0   # l
+        self.n_aux = {"crpc_psq": n - 1, "crpc": n, "psq": a * b * (n - 1), "vanilla": a * b * n}[circuit]
+        self.n_vars = 1 + self.n_io + n * b + self.n_aux
+        self.n_circuit_rows = {"crpc_psq": n, "crpc": n + 1, "psq": a * b * n, "vanilla": a * b * n + a * b}[circuit]
+        self.n_rows = self.n_circuit_rows + self.n_public + 1
         N = 1
         while N < self.n_rows:
             N *= 2
         self.domain = N
 
-    # variable indices
+    # variable indices: one | X | Y | W | auxiliary
     def x(self, i, k):
         return 1 + i * self.n + k
 
@@ -59,34 +82,73 @@ class Shape:
         return 1 + self.a * self.n + i * self.b + j
 
     def w(self, k, j):
-        return 1 + self.n_public + k * self.b + j
+        return 1 + self.n_io + k * self.b + j
+
+    def aux(self, idx):
+        return 1 + self.n_io + self.n * self.b + idx
 
     def s(self, k):
-        return 1 + self.n_public + self.n * self.b + k
+        """crpc_psq: prefix sum S_k, k < n - 1."""
+        return self.aux(k)
+
+    def p(self, k):
+        """crpc: product p_k = a_k b_k, k < n."""
+        return self.aux(k)
+
+    def s3(self, i, j, k):
+        """psq: prefix sum S_ijk = sum_(k' <= k) x_ik' w_k'j, k < n - 1."""
+        return self.aux((i * self.b + j) * (self.n - 1) + k)
+
+    def p3(self, i, j, k):
+        """vanilla: product p_ijk = x_ik w_kj."""
+        return self.aux((i * self.b + j) * self.n + k)
 
     def __repr__(self):
-        return f"Shape(a={self.a}, n={self.n}, b={self.b})"
+        return f"Shape(a={self.a}, n={self.n}, b={self.b}, {self.circuit}, public {self.public_io})"
 
 
 def build_r1cs(shape, z, with_input_rows=True):
-    """Rows (A, B, C) as dicts {variable: Fr coefficient}, CRPC rows first."""
+    """Rows (A, B, C) as dicts {variable: Fr coefficient}, circuit rows first, then the
+    input-consistency rows of the public variables (z is used by the CRPC circuits)."""
     a, n, b = shape.a, shape.n, shape.b
     rows = []
-    for k in range(n):
-        A = {shape.x(i, k): pow(z, i * b, R) for i in range(a)}
-        B = {shape.w(k, j): pow(z, j, R) for j in range(b)}
-        C = {}
-        if k < n - 1:
-            C[shape.s(k)] = 1
-            if k >= 1:
-                C[shape.s(k - 1)] = R - 1
-        else:
+    if shape.circuit in ("crpc_psq", "crpc"):
+        for k in range(n):
+            A = {shape.x(i, k): pow(z, i * b, R) for i in range(a)}
+            B = {shape.w(k, j): pow(z, j, R) for j in range(b)}
+            C = {}
+            if shape.circuit == "crpc":
+                C[shape.p(k)] = 1
+            elif k < n - 1:
+                C[shape.s(k)] = 1
+                if k >= 1:
+                    C[shape.s(k - 1)] = R - 1
+            else:
+                for i in range(a):
+                    for j in range(b):
+                        C[shape.y(i, j)] = pow(z, i * b + j, R)
+                if n >= 2:
+                    C[shape.s(n - 2)] = R - 1
+            rows.append((A, B, C))
+        if shape.circuit == "crpc":   # (p_0 + ... + p_(n-1)) * 1 = Y(z)
+            C = {shape.y(i, j): pow(z, i * b + j, R) for i in range(a) for j in range(b)}
+            rows.append(({shape.p(k): 1 for k in range(n)}, {0: 1}, C))
+    else:
+        for i in range(a):
+            for j in range(b):
+                for k in range(n):
+                    A, B = {shape.x(i, k): 1}, {shape.w(k, j): 1}
+                    if shape.circuit == "vanilla":
+                        C = {shape.p3(i, j, k): 1}
+                    else:
+                        C = {shape.s3(i, j, k): 1} if k < n - 1 else {shape.y(i, j): 1}
+                        if k >= 1:
+                            C[shape.s3(i, j, k - 1)] = R - 1
+                    rows.append((A, B, C))
+        if shape.circuit == "vanilla":   # (p_ij0 + ... + p_ij(n-1)) * 1 = y_ij
             for i in range(a):
                 for j in range(b):
-                    C[shape.y(i, j)] = pow(z, i * b + j, R)
-            if n >= 2:
-                C[shape.s(n - 2)] = R - 1
-        rows.append((A, B, C))
+                    rows.append(({shape.p3(i, j, k): 1 for k in range(n)}, {0: 1}, {shape.y(i, j): 1}))
     if with_input_rows:
         for i in range(shape.n_public + 1):
             rows.append(({i: 1}, {}, {}))
@@ -127,11 +189,27 @@ def witness(shape, X, W, z, Y=None):
     for k in range(n):
         for j in range(b):
             w[shape.w(k, j)] = fr_from_int(W[k][j])
-    ak, bk = crpc_evaluations(X, W, z)
-    S = 0
-    for k in range(n - 1):                      # PSQ prefix sums (Sec. III-B)
-        S = (S + ak[k] * bk[k]) % R
-        w[shape.s(k)] = S
+    if shape.circuit in ("crpc_psq", "crpc"):
+        ak, bk = crpc_evaluations(X, W, z)
+        if shape.circuit == "crpc":
+            for k in range(n):
+                w[shape.p(k)] = ak[k] * bk[k] % R
+        else:
+            S = 0
+            for k in range(n - 1):                      # PSQ prefix sums (Sec. III-B)
+                S = (S + ak[k] * bk[k]) % R
+                w[shape.s(k)] = S
+    else:
+        for i in range(a):
+            for j in range(b):
+                acc = 0
+                for k in range(n):
+                    prod = X[i][k] * W[k][j]
+                    if shape.circuit == "vanilla":
+                        w[shape.p3(i, j, k)] = fr_from_int(prod)
+                    elif k < n - 1:
+                        acc += prod
+                        w[shape.s3(i, j, k)] = fr_from_int(acc)
     return w
 
 

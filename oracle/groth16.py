@@ -198,7 +198,10 @@ def proof_from_bytes(bs):
 
 
 def public_inputs(shape, X, Y):
-    """x_1..x_l = X row-major then Y row-major, mapped to Fr."""
+    """x_1..x_l = X row-major then Y row-major, mapped to Fr (none when X and Y are
+    private)."""
+    if shape.n_public == 0:
+        return []
     xs = [bn.fr_from_int(X[i][k]) for i in range(shape.a) for k in range(shape.n)]
     xs += [bn.fr_from_int(Y[i][j]) for i in range(shape.a) for j in range(shape.b)]
     return xs
