@@ -215,7 +215,8 @@ int zkvc_vk_import(int a, int n, int b, const uint8_t alpha1[64], const uint8_t 
  * pointers.  Runs on the host (optimal-ate pairing over BN254), no device work.
  * Returns ZKVC_OK with *ok = 1 for a valid proof and *ok = 0 otherwise -- including
  * proofs whose points are not canonical, not on the curve, or (B) not in the order-r
- * subgroup.  ZKVC_EIO for a malformed key.
+ * subgroup.  ZKVC_EIO for a malformed key.  With a key of no public inputs
+ * (ZKVC_PUBLIC_NONE) X and Y are not read and may be NULL.
  */
 int zkvc_verify(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint8_t proof[256], int* ok);
 
@@ -261,6 +262,39 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const ui
 size_t zkvc_prove_workspace_bytes_mode(const zkvc_pk* pk, int mode);
 int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64],
                     int32_t* d_Y, void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream);
+
+/* ------------------------------------------------------------------ circuit variants
+ * The paper's ablation (Sec. V, Table II) compares four R1CS encodings of the same
+ * matmul, and its verify timing suggests few public inputs.  zkvc_setup_circuit builds a
+ * key for any of them on a generic sparse-R1CS layout (variables one | X | Y | W |
+ * auxiliary, circuit rows then input-consistency rows):
+ *   ZKVC_CIRCUIT_CRPC_PSQ  CRPC (Sec. III-A) with the PSQ chain (Sec. III-B): n rows,
+ *                          auxiliary S_0..S_(n-2) -- the same circuit as zkvc_setup
+ *   ZKVC_CIRCUIT_CRPC      CRPC without PSQ: rows a_k b_k = p_k, then
+ *                          (p_0 + ... + p_(n-1)) * 1 = Y(z); auxiliary p_k
+ *   ZKVC_CIRCUIT_PSQ       PSQ without CRPC: per output y_ij the chain
+ *                          x_ik w_kj = S_ijk - S_ij(k-1), closing on y_ij (a b n rows)
+ *   ZKVC_CIRCUIT_VANILLA   x_ik w_kj = p_ijk per product (a b n rows, Sec. III-A's count)
+ *                          and (sum_k p_ijk) * 1 = y_ij per output
+ * and public_io ZKVC_PUBLIC_XY (X and Y public) or ZKVC_PUBLIC_NONE (only the constant
+ * one is public; the verifier then takes no X or Y).  toxic and the error behaviour are
+ * those of zkvc_setup (z is unused by the circuits without CRPC but still checked).
+ * zkvc_prove / zkvc_prove_mode on such a key run the generic prover (the two
+ * multiplications s A and r B1 are variable-base, as in ZKVC_PROVE_CHAIN, whichever mode
+ * is asked); zkvc_prove_workspace_bytes sizes it.  zkvc_pk_export on such a key indexes
+ * ZKVC_Q_A / B1 / B2 / L by variable (all-zero bytes where the query has no entry), H by
+ * position.  pk files, batches and the server take zkvc_setup keys only.
+ * zkvc_pk_circuit reports a key's circuit, public-input mode, rows and variables.
+ */
+#define ZKVC_CIRCUIT_CRPC_PSQ 0
+#define ZKVC_CIRCUIT_CRPC 1
+#define ZKVC_CIRCUIT_PSQ 2
+#define ZKVC_CIRCUIT_VANILLA 3
+#define ZKVC_PUBLIC_XY 0
+#define ZKVC_PUBLIC_NONE 1
+int zkvc_setup_circuit(int a, int n, int b, int circuit, int public_io, const uint8_t toxic[192], void* stream,
+                       zkvc_pk** pk, zkvc_vk** vk);
+int zkvc_pk_circuit(const zkvc_pk* pk, int* circuit, int* public_io, uint64_t* rows, uint64_t* vars);
 
 /* ------------------------------------------------------------------ batched proving
  * Many proofs of uneven shapes in one launch sequence (the paper proves the matmul

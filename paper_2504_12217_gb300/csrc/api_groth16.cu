@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "circuit.h"
 #include "groth16.h"
 
 namespace zkvc {
@@ -136,7 +137,35 @@ void zkvc_pk_free(zkvc_pk* pk) {
   cudaFree(pk->g2);
   cudaFree(pk->zA);
   cudaFree(pk->zB);
+  delete pk->gen;
   delete pk;
+}
+
+int zkvc_setup_circuit(int a, int n, int b, int circuit, int public_io, const uint8_t toxic[192], void* stream,
+                       zkvc_pk** pk, zkvc_vk** vk) {
+  set_error("%s", "");
+  ZK_CHECK(toxic && pk && vk, ZKVC_EINVAL, "setup: null argument");
+  *pk = nullptr;
+  *vk = nullptr;
+  return setup_generic(a, n, b, circuit, public_io, toxic, (cudaStream_t)stream, pk, vk);
+}
+
+int zkvc_pk_circuit(const zkvc_pk* pk, int* circuit, int* public_io, uint64_t* rows, uint64_t* vars) {
+  set_error("%s", "");
+  ZK_CHECK(pk, ZKVC_EINVAL, "pk_circuit: null key");
+  if (pk->gen) {
+    const GShape& g = pk->gen->sh;
+    if (circuit) *circuit = g.circuit;
+    if (public_io) *public_io = g.pub;
+    if (rows) *rows = g.n_rows;
+    if (vars) *vars = g.n_vars;
+  } else {
+    if (circuit) *circuit = ZKVC_CIRCUIT_CRPC_PSQ;
+    if (public_io) *public_io = ZKVC_PUBLIC_XY;
+    if (rows) *rows = pk->shape.rows;
+    if (vars) *vars = pk->shape.n_vars;
+  }
+  return ZKVC_OK;
 }
 
 void zkvc_vk_free(zkvc_vk* vk) { delete vk; }
@@ -158,6 +187,7 @@ int zkvc_pk_export(const zkvc_pk* pk, int query, size_t start, size_t count, uin
   set_error("%s", "");
   ZK_CHECK(pk && (out || count == 0), ZKVC_EINVAL, "pk_export: null argument");
   ZK_TRY(device_guard(pk->device));
+  if (pk->gen) return export_generic(pk, query, start, count, out);
   const Shape& sh = pk->shape;
   const Region* g = pk->lay.g1;
   const Region* g2 = pk->lay.g2;
@@ -250,13 +280,15 @@ int zkvc_vk_import(int a, int n, int b, const uint8_t alpha1[64], const uint8_t 
 
 int zkvc_verify(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint8_t proof[256], int* ok) {
   set_error("%s", "");
-  ZK_CHECK(vk && X && Y && proof && ok, ZKVC_EINVAL, "verify: null argument");
+  ZK_CHECK(vk && proof && ok, ZKVC_EINVAL, "verify: null argument");
+  ZK_CHECK((X && Y) || vk->ic.size() == 64, ZKVC_EINVAL, "verify: X and Y are public inputs of this key");
   return verify_impl(vk, X, Y, proof, ok);
 }
 
 int zkvc_pk_save(const zkvc_pk* pk, const char* path) {
   set_error("%s", "");
   ZK_CHECK(pk && path, ZKVC_EINVAL, "pk_save: null argument");
+  ZK_CHECK(!pk->gen, ZKVC_EINVAL, "pk_save: keys of zkvc_setup_circuit are not saved to files");
   ZK_TRY(device_guard(pk->device));
   ZK_CUDA(cudaDeviceSynchronize());
   FileGuard g;
@@ -386,11 +418,14 @@ int zkvc_vk_load(const char* path, zkvc_vk** out) {
   return ZKVC_OK;
 }
 
-size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk) { return pk ? prove_workspace_bytes(pk, ZKVC_PROVE_FOLD) : 0; }
+size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk) {
+  if (!pk) return 0;
+  return pk->gen ? prove_generic_workspace_bytes(pk) : prove_workspace_bytes(pk, ZKVC_PROVE_FOLD);
+}
 
 size_t zkvc_prove_workspace_bytes_mode(const zkvc_pk* pk, int mode) {
   if (!pk || (mode != ZKVC_PROVE_FOLD && mode != ZKVC_PROVE_CHAIN)) return 0;
-  return prove_workspace_bytes(pk, mode);
+  return pk->gen ? prove_generic_workspace_bytes(pk) : prove_workspace_bytes(pk, mode);
 }
 
 int zkvc_prove(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint8_t rs[64], int32_t* dY, void* d_ws,
@@ -398,6 +433,7 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   set_error("%s", "");
   ZK_CHECK(pk, ZKVC_EINVAL, "prove: null key");
   ZK_TRY(device_guard(pk->device));
+  if (pk->gen) return prove_generic(pk, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
   return prove_impl(pk, ZKVC_PROVE_FOLD, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
 }
 
@@ -406,6 +442,10 @@ int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t*
   set_error("%s", "");
   ZK_CHECK(pk, ZKVC_EINVAL, "prove: null key");
   ZK_TRY(device_guard(pk->device));
+  if (pk->gen) {
+    ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN, ZKVC_EINVAL, "prove: mode %d", mode);
+    return prove_generic(pk, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
+  }
   return prove_impl(pk, mode, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
 }
 

@@ -579,6 +579,7 @@ static int batch_create(const zkvc_pk* const* pks, int count, int flags, zkvc_ba
   ZK_CUDA(cudaGetDevice(&dev));
   for (int i = 0; i < count; i++) {
     ZK_CHECK(pks[i], ZKVC_EINVAL, "batch: key %d is null", i);
+    ZK_CHECK(!pks[i]->gen, ZKVC_EINVAL, "batch: key %d is a zkvc_setup_circuit key (only CRPC + PSQ keys batch)", i);
     ZK_CHECK(pks[i]->device == dev, ZKVC_EINVAL, "batch: key %d lives on device %d, current is %d", i,
              pks[i]->device, dev);
   }

@@ -70,6 +70,10 @@ Layout make_layout(const Shape& s);
 
 }  // namespace zkvc
 
+namespace zkvc {
+struct GenericKey;
+}
+
 struct zkvc_pk {
   zkvc::Shape shape;
   zkvc::Layout lay;
@@ -79,10 +83,13 @@ struct zkvc_pk {
   zkvc::Fr* zA = nullptr;    // z^(i b), i < a
   zkvc::Fr* zB = nullptr;    // z^j, j < b
   const zkvc::NttDomain* dom = nullptr;
+  zkvc::GenericKey* gen = nullptr;  // set for keys of zkvc_setup_circuit (generic R1CS layout)
 };
 
 struct zkvc_vk {
   zkvc::Shape shape;
+  int circuit = 0;    // ZKVC_CIRCUIT_*
+  int public_io = 0;  // ZKVC_PUBLIC_*: X and Y public, or no public inputs
   // canonical affine encodings (host)
   std::vector<uint8_t> alpha1, beta2, gamma2, delta2;  // 64 / 128 / 128 / 128 bytes
   std::vector<uint8_t> ic;                             // (l + 1) x 64 bytes

@@ -116,6 +116,7 @@ int msm_plan_finalize(MsmPlan& p) {
       case SK_ONE: nd = 1; break;
       case SK_I8: nd = (8 + o.c) / o.c; break;            // |v| <= 128 needs c (nd) > 8
       case SK_I32: nd = (32 + o.c - 1) / o.c; break;
+      case SK_I16: nd = o.c >= 16 ? 1 : (16 + o.c) / o.c; break;  // |v| <= 2^15 needs c (nd) > 16
       case SK_FR_MONT:
       case SK_FR_CANON: nd = (255 + o.c - 1) / o.c; break;
       default: ZK_CHECK(false, ZKVC_EINVAL, "msm: scalar kind %d", s.kind);
@@ -192,6 +193,12 @@ __global__ void k_digits(const MsmSeg* __restrict__ segs, int nsegs, const MsmOu
       case SK_ONE: m[0] = 1; break;
       case SK_I8: {
         int v = reinterpret_cast<const int8_t*>(sg.scalars)[i];
+        neg = v < 0;
+        m[0] = (uint32_t)(v < 0 ? -v : v);
+        break;
+      }
+      case SK_I16: {
+        int v = reinterpret_cast<const int16_t*>(sg.scalars)[i];
         neg = v < 0;
         m[0] = (uint32_t)(v < 0 ? -v : v);
         break;

@@ -13,6 +13,7 @@ enum ScalarKind : int32_t {
   SK_I32 = 2,       // int32 array, signed, |v| < 2^31
   SK_FR_MONT = 3,   // Fr array in Montgomery form
   SK_FR_CANON = 4,  // Fr array, canonical little-endian 8 x u32
+  SK_I16 = 5,       // int16 array, signed
 };
 
 // One run of points sharing a scalar kind and an output.

@@ -293,6 +293,7 @@ int zkvc_server_create(const zkvc_pk* const* pks, int npk, int slots, size_t mem
   ZK_CUDA(cudaGetDevice(&dev));
   for (int i = 0; i < npk; i++) {
     ZK_CHECK(pks[i], ZKVC_EINVAL, "server: key %d is null", i);
+    ZK_CHECK(!pks[i]->gen, ZKVC_EINVAL, "server: key %d is a zkvc_setup_circuit key (only CRPC + PSQ keys serve)", i);
     ZK_CHECK(pks[i]->device == dev, ZKVC_EINVAL, "server: key %d lives on device %d, current is %d", i, pks[i]->device,
              dev);
   }

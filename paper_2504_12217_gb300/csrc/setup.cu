@@ -18,6 +18,7 @@
 #include <map>
 
 #include "groth16.h"
+#include "setup_common.h"
 
 namespace zkvc {
 
@@ -63,14 +64,6 @@ Layout make_layout(const Shape& s) {
 }
 
 // ------------------------------------------------------------------ setup constants
-struct SetupConsts {
-  Fr tau, alpha, beta, gamma, delta, z;
-  Fr tN1;   // tau^N - 1 = t(tau)
-  Fr c;     // (tau^N - 1) / N
-  Fr dinv, ginv;
-  int bad;  // bit 0: non-canonical input, 1: tau^N = 1, 2: zero alpha..delta, 3: z in {0, 1}
-};
-
 __device__ __forceinline__ bool lt_modulus_fr(const Fr& x) {
   for (int i = 7; i >= 0; i--) {
     uint32_t m = mod_limb<FrCfg>(i);
@@ -109,16 +102,6 @@ __global__ void k_setup_consts(const Fr* toxic, SetupConsts* sc, uint32_t logN, 
   *sc = s;
 }
 
-__device__ __forceinline__ Fr pow_u32(Fr base, uint32_t e) {
-  Fr r = Fr::one();
-  while (e) {
-    if (e & 1u) r = f_mul(r, base);
-    base = f_sqr(base);
-    e >>= 1;
-  }
-  return r;
-}
-
 __global__ void k_zpows(const SetupConsts* sc, Fr* zA, int a, Fr* zB, int b) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a + b) return;
@@ -134,8 +117,6 @@ __device__ __forceinline__ Fr omega_pow(const Fr* tw, size_t N, size_t k) {
   size_t h = N / 2;
   return k < h ? ld_field(tw + k) : f_neg(ld_field(tw + (k - h)));
 }
-
-static constexpr int LAG_CHUNK = 32;
 
 __global__ void k_lagrange(const SetupConsts* sc, const Fr* tw, size_t N, uint32_t rows, Fr* L) {
   size_t k0 = (size_t(blockIdx.x) * blockDim.x + threadIdx.x) * LAG_CHUNK;
@@ -165,8 +146,6 @@ struct RegionTab {
   uint32_t entry_off[R1_COUNT + 1];
   int n;
 };
-
-__device__ __forceinline__ uint32_t bitrev_n(uint32_t x, uint32_t logN) { return __brev(x) >> (32 - logN); }
 
 __global__ void k_query_scalars(RegionTab tab, int group, const SetupConsts* __restrict__ scp, const Fr* __restrict__ L,
                                 const Fr* __restrict__ zA, const Fr* __restrict__ zB, Shape sh, Fr* out) {
@@ -337,7 +316,7 @@ static int build_table(Affine<F>** out, cudaStream_t st) {
   return ZKVC_OK;
 }
 
-static int fb_tables(G1A** t1, G2A** t2, cudaStream_t st) {
+int fb_tables(G1A** t1, G2A** t2, cudaStream_t st) {
   int dev = 0;
   ZK_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(g_tab_mu);
@@ -356,7 +335,7 @@ static int fb_tables(G1A** t1, G2A** t2, cudaStream_t st) {
 
 // scalars (Montgomery) -> affine bases, in chunks to bound the XYZZ temporary
 template <class F>
-static int points_from_scalars(const Fr* scal, size_t n, const Affine<F>* T, Affine<F>* out, XYZZ<F>* tmp,
+int points_from_scalars(const Fr* scal, size_t n, const Affine<F>* T, Affine<F>* out, XYZZ<F>* tmp,
                                size_t chunk, cudaStream_t st) {
   for (size_t s = 0; s < n; s += chunk) {
     size_t m = n - s < chunk ? n - s : chunk;
@@ -408,25 +387,10 @@ int export_points(const Affine<F>* src, const std::vector<uint64_t>& idx, uint8_
 }
 
 template int export_points<Fp>(const G1A*, const std::vector<uint64_t>&, uint8_t*, cudaStream_t);
+template int points_from_scalars<Fp>(const Fr*, size_t, const G1A*, G1A*, XYZZ<Fp>*, size_t, cudaStream_t);
+template int points_from_scalars<Fp2>(const Fr*, size_t, const G2A*, G2A*, XYZZ<Fp2>*, size_t, cudaStream_t);
 template int export_points<Fp2>(const G2A*, const std::vector<uint64_t>&, uint8_t*, cudaStream_t);
 
-// RAII for temporaries of one setup call
-struct DevTemps {
-  std::vector<void*> ptrs;
-  ~DevTemps() {
-    for (void* p : ptrs) cudaFree(p);
-  }
-  template <class T>
-  int alloc(T** p, size_t count) {
-    cudaError_t e = cudaMalloc(p, count * sizeof(T) + 16);
-    if (e != cudaSuccess) {
-      set_error("setup: cudaMalloc of %zu bytes: %s", count * sizeof(T), cudaGetErrorString(e));
-      return ZKVC_ENOMEM;
-    }
-    ptrs.push_back(*p);
-    return ZKVC_OK;
-  }
-};
 
 template <class F>
 __global__ void k_points_canonical(Affine<F>* p, size_t n) {

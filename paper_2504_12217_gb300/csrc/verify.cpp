@@ -620,8 +620,10 @@ int verify_impl(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint
     set_error("verify: corrupt verifying key");
     return ZKVC_EIO;
   }
-  // IC(x) = IC_0 + sum_v x_v IC_v over the public inputs X (row-major) then Y (row-major)
+  // IC(x) = IC_0 + sum_v x_v IC_v over the public inputs X (row-major) then Y (row-major);
+  // a key without public inputs (X and Y private) holds IC_0 alone
   size_t l = size_t(a) * n + size_t(a) * b;
+  if (n_ic == 1) l = 0;
   if (n_ic != l + 1) {
     set_error("verify: verifying key has %zu IC points for %zu public inputs", n_ic, l);
     return ZKVC_EIO;

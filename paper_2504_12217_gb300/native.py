@@ -65,6 +65,10 @@ SIGNATURES = {
     "zkvc_prove_workspace_bytes": (_c_sz, [_c_p]),
     "zkvc_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_prove_workspace_bytes_mode": (_c_sz, [_c_p, _c_int]),
+    "zkvc_setup_circuit": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _c_p, _c_p, ctypes.POINTER(_c_p),
+                                    ctypes.POINTER(_c_p)]),
+    "zkvc_pk_circuit": (_c_int, [_c_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_uint64),
+                                 ctypes.POINTER(ctypes.c_uint64)]),
     "zkvc_prove_mode": (_c_int, [_c_p, _c_int, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_batch_create": (_c_int, [_c_p, _c_int, _c_int, ctypes.POINTER(_c_p)]),
     "zkvc_batch_free": (None, [_c_p]),
@@ -319,6 +323,33 @@ def zkvc_setup(a, n, b, toxic):
     return ProvingKey(pk), VerifyingKey(vk, (a, n, b))
 
 
+ZKVC_CIRCUIT_CRPC_PSQ, ZKVC_CIRCUIT_CRPC, ZKVC_CIRCUIT_PSQ, ZKVC_CIRCUIT_VANILLA = 0, 1, 2, 3
+ZKVC_PUBLIC_XY, ZKVC_PUBLIC_NONE = 0, 1
+CIRCUIT_NAMES = {"crpc_psq": 0, "crpc": 1, "psq": 2, "vanilla": 3}
+PUBLIC_NAMES = {"xy": 0, "none": 1}
+
+
+def zkvc_setup_circuit(a, n, b, circuit, public_io, toxic):
+    """Gen for one of the ablation circuits (ZKVC_CIRCUIT_* or its name) with X and Y
+    public or private (ZKVC_PUBLIC_* or "xy" / "none").  Returns (ProvingKey, VerifyingKey)."""
+    circuit = CIRCUIT_NAMES.get(circuit, circuit)
+    public_io = PUBLIC_NAMES.get(public_io, public_io)
+    if len(toxic) != 192:
+        raise ValueError("toxic must be 192 bytes")
+    pk, vk = _c_p(), _c_p()
+    buf = ctypes.create_string_buffer(bytes(toxic), 192)
+    check(lib().zkvc_setup_circuit(a, n, b, circuit, public_io, buf, _stream(), ctypes.byref(pk), ctypes.byref(vk)))
+    out_vk = VerifyingKey(vk, (a, n, b))
+    out_vk.public_io = public_io
+    return ProvingKey(pk), out_vk
+
+
+def zkvc_pk_circuit(pk):
+    c, p, r, v = _c_int(), _c_int(), ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().zkvc_pk_circuit(pk.handle, ctypes.byref(c), ctypes.byref(p), ctypes.byref(r), ctypes.byref(v)))
+    return {"circuit": c.value, "public_io": p.value, "rows": r.value, "vars": v.value}
+
+
 def zkvc_pk_info(pk):
     a, n, b = _c_int(), _c_int(), _c_int()
     logd, g1, g2 = _c_u32(), _c_sz(), _c_sz()
@@ -353,14 +384,18 @@ def zkvc_vk_import(a, n, b, alpha1, beta2, gamma2, delta2, ic):
 
 
 def zkvc_verify(vk, X, Y, proof):
-    """Host-side verification; X: int8 [a, n], Y: int32 [a, b] (numpy or CPU tensors)."""
+    """Host-side verification; X: int8 [a, n], Y: int32 [a, b] (numpy or CPU tensors), or
+    None for both with a key that has no public inputs."""
     import numpy as np
     a, n, b = vk.shape
-    Xn = np.ascontiguousarray(np.asarray(X, dtype=np.int8).reshape(a, n))
-    Yn = np.ascontiguousarray(np.asarray(Y, dtype=np.int32).reshape(a, b))
     if len(proof) != 256:
         raise ValueError("proof must be 256 bytes")
     ok = _c_int(0)
+    if X is None and Y is None:
+        check(lib().zkvc_verify(vk.handle, None, None, bytes(proof), ctypes.byref(ok)))
+        return bool(ok.value)
+    Xn = np.ascontiguousarray(np.asarray(X, dtype=np.int8).reshape(a, n))
+    Yn = np.ascontiguousarray(np.asarray(Y, dtype=np.int32).reshape(a, b))
     check(lib().zkvc_verify(vk.handle, Xn.ctypes.data_as(_c_p), Yn.ctypes.data_as(_c_p), bytes(proof),
                             ctypes.byref(ok)))
     return bool(ok.value)
