@@ -325,6 +325,9 @@ def run_gpu(args):
     Xd = torch.from_numpy(inst["X"]).cuda()
     Wd = torch.from_numpy(inst["W"]).cuda()
     Yd = torch.empty((a, b), dtype=torch.int32, device="cuda")
+    # one-time latency tuning of the key's MSM chunk sizes (setup, not timed)
+    chunks = nv.zkvc_pk_autotune(pk, Xd, Wd, inputs.to_bytes32(inst["rs"])) if args.autotune else \
+        nv.zkvc_pk_get_chunks(pk)
     ws = torch.empty(nv.zkvc_prove_workspace_bytes(pk), dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     total_steps = args.warmup + args.steps
@@ -415,7 +418,9 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 limbs (exact Fr/Fp arithmetic)",
         "data": "synthetic",
         "config": {"workload": "crpc_groth16_bn254_49x320x512", "a": a, "n": n, "b": b, "log_domain": 16,
-                   "l2": "flushed by a 256 MiB write between steps", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed by a 256 MiB write between steps", "parallelism": f"replicas x{world}",
+                   "msm_chunks_small_rest_h_g2": chunks,
+                   "chunk_source": "zkvc_pk_autotune at setup" if args.autotune else "default rule"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps, "clocks": clk, "stage_ms": stages,
@@ -772,6 +777,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="plain: tune the key's MSM chunk sizes for latency at setup (zkvc_pk_autotune)")
     ap.add_argument("--sweep", action="store_true", help="kernel sweep (NTT and MSM sizes) instead of proofs")
     ap.add_argument("--sweep-ntt", type=int, nargs="*", default=[16, 18, 20, 22, 24])
     ap.add_argument("--sweep-g1", type=int, nargs="*", default=[16, 18, 20, 22, 24])

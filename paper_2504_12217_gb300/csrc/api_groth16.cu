@@ -9,6 +9,8 @@
 namespace zkvc {
 int setup_impl(int a, int n, int b, const uint8_t* toxic, cudaStream_t st, zkvc_pk** pk, zkvc_vk** vk);
 size_t prove_workspace_bytes(const zkvc_pk* pk, int mode);
+int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, cudaStream_t st,
+                   uint32_t* chosen);
 int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, int32_t* dY,
                void* ws, size_t ws_bytes, uint8_t* proof, cudaStream_t st);
 template <class F>
@@ -148,6 +150,32 @@ int zkvc_setup_circuit(int a, int n, int b, int circuit, int public_io, const ui
   *pk = nullptr;
   *vk = nullptr;
   return setup_generic(a, n, b, circuit, public_io, toxic, (cudaStream_t)stream, pk, vk);
+}
+
+int zkvc_pk_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t rs[64], void* stream,
+                     uint32_t chunks[4]) {
+  set_error("%s", "");
+  ZK_CHECK(pk && dX && dW && rs, ZKVC_EINVAL, "autotune: null argument");
+  ZK_CHECK(!pk->gen, ZKVC_EINVAL, "autotune: keys of zkvc_setup_circuit are not tuned");
+  ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN, ZKVC_EINVAL, "autotune: mode %d", mode);
+  ZK_TRY(device_guard(pk->device));
+  return prove_autotune(pk, mode, dX, dW, rs, (cudaStream_t)stream, chunks);
+}
+
+int zkvc_pk_set_chunks(zkvc_pk* pk, const uint32_t chunks[4]) {
+  set_error("%s", "");
+  ZK_CHECK(pk && chunks, ZKVC_EINVAL, "set_chunks: null argument");
+  for (int i = 0; i < 4; i++)
+    ZK_CHECK(chunks[i] <= 1024, ZKVC_EINVAL, "set_chunks: chunk %u above 1024", chunks[i]);
+  for (int i = 0; i < 4; i++) pk->prove_chunk[i] = chunks[i];
+  return ZKVC_OK;
+}
+
+int zkvc_pk_get_chunks(const zkvc_pk* pk, uint32_t chunks[4]) {
+  set_error("%s", "");
+  ZK_CHECK(pk && chunks, ZKVC_EINVAL, "get_chunks: null argument");
+  for (int i = 0; i < 4; i++) chunks[i] = pk->prove_chunk[i];
+  return ZKVC_OK;
 }
 
 int zkvc_pk_circuit(const zkvc_pk* pk, int* circuit, int* public_io, uint64_t* rows, uint64_t* vars) {

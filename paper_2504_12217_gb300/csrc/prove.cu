@@ -22,6 +22,7 @@
 //     base is a proving-key point stored with its 2^(16 w) multiples.
 //  7. Affine conversion (one inversion per point, in parallel) and the canonical
 //     256-byte encoding A || B || C.
+#include <algorithm>
 #include <cstring>
 
 #include "groth16.h"
@@ -204,7 +205,6 @@ static void plans(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
         seg_of(g[R1_BETA], 0, 1, 0, SK_FR_CANON, rs + 0),
         seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 2),
     };
-    msm_plan_finalize(P->rest);
   }
   const Region* g2 = pk->lay.g2;
   P->g2.outs = {{ZKVC_C2, 1, 0, 0}};
@@ -213,6 +213,11 @@ static void plans(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
       seg_of(g2[R2_BETA], 0, 1, 0, SK_ONE, nullptr),
       seg_of(g2[R2_DELTA], 0, 1, 0, SK_FR_CANON, rs + 1),
   };
+  P->small.tune.chunk = pk->prove_chunk[0];
+  P->rest.tune.chunk = pk->prove_chunk[1];
+  P->h.tune.chunk = pk->prove_chunk[2];
+  P->g2.tune.chunk = pk->prove_chunk[3];
+  if (!chain) msm_plan_finalize(P->rest);
   msm_plan_finalize(P->small);
   msm_plan_finalize(P->h);
   msm_plan_finalize(P->g2);
@@ -411,6 +416,80 @@ int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, 
   ZK_CUDA(cudaStreamSynchronize(st));
   prof_collect();
   return prove_status(flags);
+}
+
+// Latency tuning of the one-proof prover: coordinate descent over the level-0 chunk of
+// each MSM run (the G2 and small-scalar runs first: their bucket sums are the longest
+// dependent chains), timing whole proofs with CUDA events on st.  Proof bytes do not
+// depend on the chunks.  Allocates its own Y and workspace; the key must not be in use.
+int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, cudaStream_t st,
+                   uint32_t* chosen) {
+  static const uint32_t kCand[] = {2, 4, 8, 16, 32, 64};
+  const uint32_t saved[4] = {pk->prove_chunk[0], pk->prove_chunk[1], pk->prove_chunk[2], pk->prove_chunk[3]};
+  for (int i = 0; i < 4; i++) pk->prove_chunk[i] = 2;  // the largest workspace of all candidates
+  size_t need = prove_workspace_bytes(pk, mode);
+  for (int i = 0; i < 4; i++) pk->prove_chunk[i] = saved[i];
+  void* ws = nullptr;
+  int32_t* dY = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(ws);
+    cudaFree(dY);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&ws, need) != cudaSuccess || cudaMalloc(&dY, size_t(pk->shape.a) * pk->shape.b * 4) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    set_error("autotune: cannot allocate %zu bytes of workspace", need);
+    return ZKVC_ENOMEM;
+  }
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cleanup();
+    set_error("autotune: event creation failed");
+    return ZKVC_ECUDA;
+  }
+  uint8_t proof[256];
+  auto measure = [&](float* ms) -> int {
+    float t[5];
+    for (int rep = 0; rep < 6; rep++) {
+      ZK_CUDA(cudaEventRecord(e0, st));
+      ZK_TRY(prove_impl(pk, mode, dX, dW, rs, dY, ws, need, proof, st));
+      ZK_CUDA(cudaEventRecord(e1, st));
+      ZK_CUDA(cudaEventSynchronize(e1));
+      if (rep > 0) ZK_CUDA(cudaEventElapsedTime(&t[rep - 1], e0, e1));
+    }
+    std::sort(t, t + 5);
+    *ms = t[2];
+    return ZKVC_OK;
+  };
+  int rc = ZKVC_OK;
+  float best_ms = 0;
+  rc = measure(&best_ms);
+  const int order[4] = {3, 0, 2, 1};  // g2, small, h, rest
+  for (int oi = 0; oi < 4 && rc == ZKVC_OK; oi++) {
+    const int r = order[oi];
+    uint32_t best = pk->prove_chunk[r];
+    for (uint32_t c : kCand) {
+      if (c == best) continue;
+      pk->prove_chunk[r] = c;
+      float ms = 0;
+      if ((rc = measure(&ms)) != ZKVC_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    pk->prove_chunk[r] = best;
+  }
+  cleanup();
+  if (rc != ZKVC_OK) {
+    for (int i = 0; i < 4; i++) pk->prove_chunk[i] = saved[i];
+    return rc;
+  }
+  if (chosen)
+    for (int i = 0; i < 4; i++) chosen[i] = pk->prove_chunk[i];
+  return ZKVC_OK;
 }
 
 }  // namespace zkvc

@@ -65,6 +65,9 @@ SIGNATURES = {
     "zkvc_prove_workspace_bytes": (_c_sz, [_c_p]),
     "zkvc_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_prove_workspace_bytes_mode": (_c_sz, [_c_p, _c_int]),
+    "zkvc_pk_autotune": (_c_int, [_c_p, _c_int, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "zkvc_pk_set_chunks": (_c_int, [_c_p, _c_p]),
+    "zkvc_pk_get_chunks": (_c_int, [_c_p, _c_p]),
     "zkvc_setup_circuit": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _c_p, _c_p, ctypes.POINTER(_c_p),
                                     ctypes.POINTER(_c_p)]),
     "zkvc_pk_circuit": (_c_int, [_c_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_uint64),
@@ -429,6 +432,26 @@ def zkvc_prove_workspace_bytes(pk):
 
 ZKVC_PROVE_FOLD = 0
 ZKVC_PROVE_CHAIN = 1
+
+
+def zkvc_pk_autotune(pk, X, W, rs, mode=0):
+    """Tune the key's MSM chunk sizes for one-proof latency on these inputs; returns the
+    chosen [small, rest, h, g2] chunks."""
+    arr = (ctypes.c_uint32 * 4)()
+    rsb = ctypes.create_string_buffer(bytes(rs), 64)
+    check(lib().zkvc_pk_autotune(pk.handle, mode, _dev_ptr(X), _dev_ptr(W), rsb, _stream(), arr))
+    return list(arr)
+
+
+def zkvc_pk_set_chunks(pk, chunks):
+    arr = (ctypes.c_uint32 * 4)(*chunks)
+    check(lib().zkvc_pk_set_chunks(pk.handle, arr))
+
+
+def zkvc_pk_get_chunks(pk):
+    arr = (ctypes.c_uint32 * 4)()
+    check(lib().zkvc_pk_get_chunks(pk.handle, arr))
+    return list(arr)
 
 
 def zkvc_prove_workspace_bytes_mode(pk, mode):

@@ -182,3 +182,26 @@ def test_verifier_accepts_config2_gpu_proof(nv):
     assert nv.zkvc_verify(vk, inst["X"], Y, proof)
     bad = proof[:192] + bn.g1_bytes(bn.g1_add(bn.g1_from_bytes(proof[192:]), bn.G1_GEN))
     assert not nv.zkvc_verify(vk, inst["X"], Y, bad)
+
+
+def test_autotuned_and_imposed_chunks_prove_same_bytes(nv):
+    """Chunk sizes change only the launch shape: autotuned, imposed and default settings
+    give the same proof, in both prover modes."""
+    import torch
+    a, n, b = 5, 40, 33
+    inst = inputs.instance(555, (a, n, b))
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(inst["toxic"]))
+    Xd, Wd = torch.from_numpy(inst["X"]).cuda(), torch.from_numpy(inst["W"]).cuda()
+    rs = inputs.to_bytes32(inst["rs"])
+    p0, _ = nv.zkvc_prove(pk, Xd, Wd, rs)
+    chosen = nv.zkvc_pk_autotune(pk, Xd, Wd, rs)
+    assert all(c in (0, 2, 4, 8, 16, 32, 64) for c in chosen)
+    assert nv.zkvc_pk_get_chunks(pk) == chosen
+    assert nv.zkvc_prove(pk, Xd, Wd, rs)[0] == p0
+    for chunks in ([2, 2, 2, 2], [64, 1, 3, 7]):
+        nv.zkvc_pk_set_chunks(pk, chunks)
+        assert nv.zkvc_pk_get_chunks(pk) == chunks
+        assert nv.zkvc_prove(pk, Xd, Wd, rs)[0] == p0
+        assert nv.zkvc_prove_mode(pk, nv.ZKVC_PROVE_CHAIN, Xd, Wd, rs)[0] == p0
+    with pytest.raises(nv.ZkvcError):
+        nv.zkvc_pk_set_chunks(pk, [2048, 0, 0, 0])
