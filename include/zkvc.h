@@ -220,6 +220,26 @@ int zkvc_vk_import(int a, int n, int b, const uint8_t alpha1[64], const uint8_t 
  */
 int zkvc_verify(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint8_t proof[256], int* ok);
 
+/* Verification on the GPU, batched (Sec. II: Verify).  Proof i is checked against
+ * verifying key vks[i] (keys may repeat) with its public inputs X[i] (a x n int8) and Y[i]
+ * (a x b int32), host pointers (ignored for keys without public inputs; X and Y may then
+ * be NULL).  proofs: count x 256 bytes (host).  ok[i] (host) receives 1 for a valid proof
+ * and 0 otherwise, with the host verifier's rules: canonical coordinates, points on their
+ * curves, B in the order-r subgroup, and the pairing equation.  IC(x) of all proofs is one
+ * merged GPU MSM; each proof's four Miller loops and final exponentiation run on the GPU.
+ * Allocates temporary device memory, waits for the result (bounded by
+ * zkvc_set_wait_timeout_ms).  ZKVC_EIO for a malformed key.
+ *
+ * zkvc_pairing: e(P_i, Q_i) for n canonical G1 points (d_P, n x 64 bytes) and G2 points
+ * (d_Q, n x 128), device pointers; d_out receives n x 384 bytes, 12 canonical Fp values per
+ * pairing in the tower basis Fp12 = Fp6[w]/(w^2 - v), Fp6 = Fp2[v]/(v^3 - (9 + i)):
+ * (c0.c0, c0.c1, c0.c2, c1.c0, c1.c1, c1.c2), each Fp2 element as c0 then c1.  Exposed for
+ * verification of the pairing itself; enqueued on `stream` only.
+ */
+int zkvc_verify_batch(const zkvc_vk* const* vks, const int8_t* const* X, const int32_t* const* Y, const uint8_t* proofs,
+                      int count, int* ok, void* stream);
+int zkvc_pairing(const uint8_t* d_P, const uint8_t* d_Q, size_t n, uint8_t* d_out, void* stream);
+
 /* Key files: a versioned header (magic, version, shape, counts), the payload, and an
  * FNV-1a-64 checksum of the payload.  pk files hold the device representation of this
  * library version (Montgomery-form bases with their precomputed windows) so that a key

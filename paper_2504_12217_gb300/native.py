@@ -82,6 +82,8 @@ SIGNATURES = {
     "zkvc_batch_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
     "zkvc_prove_batch": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_int, _c_p, _c_p, _c_p, _c_p]),
     "zkvc_set_wait_timeout_ms": (_c_int, [_c_int]),
+    "zkvc_verify_batch": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_int, _c_p, _c_p]),
+    "zkvc_pairing": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_server_create": (_c_int, [_c_p, _c_int, _c_int, _c_sz, _c_int, ctypes.POINTER(_c_p)]),
     "zkvc_server_free": (None, [_c_p]),
     "zkvc_server_submit": (_c_int, [_c_p, _c_int, _c_p, _c_p, _c_p, ctypes.POINTER(ctypes.c_uint64)]),
@@ -667,3 +669,39 @@ class Server:
                                       ctypes.byref(p), ctypes.byref(ch)))
         return {"completed": c.value, "in_flight": f.value, "queued": q.value, "bytes_in_use": u.value,
                 "peak_bytes": p.value, "chain_mode": ch.value}
+
+
+# ------------------------------------------------------------------ GPU verification
+def zkvc_verify_batch(vks, Xs, Ys, proofs):
+    """Verify proofs[i] against vks[i] with public inputs Xs[i] (int8 [a, n]) and Ys[i]
+    (int32 [a, b]) on the GPU (None for keys without public inputs).  Returns a list of
+    booleans."""
+    import numpy as np
+    n = len(proofs)
+    keep = []
+    xs = (_c_p * max(1, n))()
+    ys = (_c_p * max(1, n))()
+    for i in range(n):
+        if Xs is not None and Xs[i] is not None:
+            a, nn, b = vks[i].shape
+            Xn = np.ascontiguousarray(np.asarray(Xs[i], dtype=np.int8).reshape(a, nn))
+            Yn = np.ascontiguousarray(np.asarray(Ys[i], dtype=np.int32).reshape(a, b))
+            keep += [Xn, Yn]
+            xs[i] = Xn.ctypes.data
+            ys[i] = Yn.ctypes.data
+    vka = _ptr_array([vk.handle for vk in vks]) if n else (_c_p * 1)()
+    pb = ctypes.create_string_buffer(b"".join(bytes(p) for p in proofs), max(1, 256 * n))
+    ok = (_c_int * max(1, n))()
+    check(lib().zkvc_verify_batch(vka, xs, ys, pb, n, ok, _stream()))
+    return [bool(ok[i]) for i in range(n)]
+
+
+def zkvc_pairing(P, Q):
+    """e(P_i, Q_i) on the GPU: P uint8 [n, 64], Q uint8 [n, 128] canonical CUDA tensors;
+    returns a uint8 [n, 384] CUDA tensor (tower-basis coefficients)."""
+    torch = _torch()
+    _u8(P, 64)
+    _u8(Q, 128)
+    out = torch.empty((P.shape[0], 384), dtype=torch.uint8, device=P.device)
+    check(lib().zkvc_pairing(_dev_ptr(P), _dev_ptr(Q), P.shape[0], _dev_ptr(out), _stream()))
+    return out
