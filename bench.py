@@ -458,9 +458,9 @@ def run_batched(args):
     if args.batch_count:  # a smaller case: the K smallest instances of the seeded mix
         shapes = sorted(shapes, key=lambda s: s[0] * s[1] + s[0] * s[2] + s[1] * s[2])[: args.batch_count]
     t0 = time.perf_counter()
-    keys = {}
+    keys, vkeys = {}, {}
     for s in dict.fromkeys(shapes):
-        keys[s] = nv.zkvc_setup(*s, inputs.to_bytes32(inputs.setup_values(shape_seed(inputs.SEED_CFG[4], s))))[0]
+        keys[s], vkeys[s] = nv.zkvc_setup(*s, inputs.to_bytes32(inputs.setup_values(shape_seed(inputs.SEED_CFG[4], s))))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     sets = []
@@ -532,6 +532,17 @@ def run_batched(args):
     x = sets[(args.steps - 1) % 2]
     proofs, _ = batch.prove(x[0], x[1], x[2], Ys)
     p0, _ = nv.zkvc_prove(keys[shapes[0]], x[0][0], x[1][0], x[2][0])
+    # verification of the batch's proofs: batched on the GPU, and the host verifier on a few
+    Yhost = [y.cpu().numpy() for y in Ys]
+    Xhost = [t["X"] for t in x[3]]
+    vlist = [vkeys[s] for s in shapes]
+    nv.zkvc_verify_batch(vlist[:2], Xhost[:2], Yhost[:2], proofs[:2])  # warm (Frobenius table)
+    t0 = time.perf_counter()
+    vok = nv.zkvc_verify_batch(vlist, Xhost, Yhost, proofs)
+    gpu_verify_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    host_ok = [nv.zkvc_verify(vlist[i], Xhost[i], Yhost[i], proofs[i]) for i in range(4)]
+    host_verify_s = (time.perf_counter() - t0) / 4
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -561,6 +572,9 @@ def run_batched(args):
         "graph_kernels": info["graph_launches"], "device_bytes": info["device_bytes"],
         "clocks": clk, "setup_s": setup_s, "autotune_and_capture_s": tune_s,
         "spot_check_vs_one_proof_prover": proofs[0] == p0,
+        "verify": {"gpu_batch_proofs_per_s": count / gpu_verify_s, "gpu_batch_s": gpu_verify_s,
+                   "all_valid": all(vok), "host_ms_per_proof": host_verify_s * 1e3, "host_sample_valid": all(host_ok),
+                   "note": "host wall clock; includes upload of keys, inputs and proofs"},
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
