@@ -45,7 +45,7 @@ int vk_get(const zkvc_vk* vk, int* a, int* n, int* b, const uint8_t** alpha1, co
 // u64 counts, the payload, and a trailing FNV-1a-64 checksum of the payload.
 static const char PK_MAGIC[8] = {'Z', 'K', 'V', 'C', 'P', 'K', '\0', '\1'};
 static const char VK_MAGIC[8] = {'Z', 'K', 'V', 'C', 'V', 'K', '\0', '\1'};
-static const uint32_t KEY_VERSION = 1;
+static const uint32_t KEY_VERSION = 2;  // 2: per-row Lagrange regions of the CRPC W side
 
 struct Fnv {
   uint64_t h = 1469598103934665603ull;

@@ -9,12 +9,14 @@
 //             NTTs, quotient and m coset INTTs are single batched launches;
 //   MSMs      three merged multi-instance runs, keyed (instance, bucket) with each
 //             output reading its own proving key's bases:
-//               small (G1, 8-bit digits): per instance A, the int8 part of C (L over W)
-//                 and B1 = [beta]1 + sum w_e [B_e]1 + s [delta]1;
+//               small (G1, 8-bit digits): per instance A, the L-query part over W
+//                 (sum_k b_k [alpha L_k / delta]1) and B1 = [beta]1 + sum_k b_k [L_k]1 +
+//                 s [delta]1 -- the W side through the CRPC sums over n per-row points;
 //               main  (G1, 16-bit digits over the stored 2^(16 w) multiples): L over the
 //                 prefix sums, the H query (h_j), and -r s [delta]1;
-//               g2    (8-bit digits): B = [beta]2 + sum w_e [B_e]2 + s [delta]2;
+//               g2    (8-bit digits): B = [beta]2 + sum_k b_k [L_k]2 + s [delta]2;
 //   C         = L_W + main + s A + r B1 (Groth16's C = ... + s A + r B - r s delta);
+// (The G2 run starts once the CRPC sums b_k exist.)
 //             s A and r B1 are 254-bit variable-base multiplications, one thread each,
 //             overlapping the main run.  (The one-proof prover folds them into
 //             fixed-base terms instead, which is shorter in latency but moves 16 extra
@@ -242,17 +244,18 @@ static void batch_plans(zkvc_batch* B) {
     const Region* g = pk->lay.g1;
     const Region* g2 = pk->lay.g2;
     const BInst& in = B->hinst[i];
-    const uint32_t an = sh.a * sh.n, ab = sh.a * sh.b, nb = sh.n * sh.b;
+    const uint32_t an = sh.a * sh.n, ab = sh.a * sh.b;
     const uint32_t o = 3 * i;
     for (int q = 0; q < 3; q++) B->p_small.outs.push_back({8, 1, 0, 0, pk->g1});
     auto& s = B->p_small.segs;
-    s.push_back(bseg(g[R1_A], 0, 1, o, SK_ONE, nullptr));
-    s.push_back(bseg(g[R1_A], 1, an, o, SK_I8, in.X));
+    s.push_back(bseg(g[R1_AIN], 0, 1, o, SK_ONE, nullptr));
+    s.push_back(bseg(g[R1_AIN], 1, an, o, SK_I8, in.X));
     s.push_back(bseg(g[R1_AY8], 0, ab, o, SK_I32, in.Y));
     s.push_back(bseg(g[R1_ALPHA], 0, 1, o, SK_ONE, nullptr));
     s.push_back(bseg(g[R1_DELTA8], 0, 1, o, SK_FR_CANON, in.rs + 0));
-    s.push_back(bseg(g[R1_LW], 0, nb, o + 1, SK_I8, in.W));
-    s.push_back(bseg(g[R1_B], 0, nb, o + 2, SK_I8, in.W));
+    s.push_back(bseg(g[R1_LK], 0, (uint32_t)sh.n, o, SK_FR_MONT, in.ak));
+    s.push_back(bseg(g[R1_ALK], 0, (uint32_t)sh.n, o + 1, SK_FR_MONT, in.bk));
+    s.push_back(bseg(g[R1_LK], 0, (uint32_t)sh.n, o + 2, SK_FR_MONT, in.bk));
     s.push_back(bseg(g[R1_BETA], 0, 1, o + 2, SK_ONE, nullptr));
     s.push_back(bseg(g[R1_DELTA8], 0, 1, o + 2, SK_FR_CANON, in.rs + 1));
 
@@ -264,7 +267,7 @@ static void batch_plans(zkvc_batch* B) {
 
     B->p_g2.outs.push_back({ZKVC_C2, 1, 0, 0, pk->g2});
     auto& t = B->p_g2.segs;
-    t.push_back(bseg(g2[R2_B], 0, nb, i, SK_I8, in.W));
+    t.push_back(bseg(g2[R2_LK], 0, (uint32_t)sh.n, i, SK_FR_MONT, in.bk));
     t.push_back(bseg(g2[R2_BETA], 0, 1, i, SK_ONE, nullptr));
     t.push_back(bseg(g2[R2_DELTA], 0, 1, i, SK_FR_CANON, in.rs + 1));
   }
@@ -407,14 +410,15 @@ static int enqueue(zkvc_batch* B) {
   ZK_CUDA(cudaMemcpyAsync(B->rs, B->h_rs, size_t(n) * 64, cudaMemcpyHostToDevice, st));
   k_b_randomness<<<(n + 63) / 64, 64, 0, st>>>(B->dinst, n); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  // G2 run on side stream 0 (needs W and s)
+  // witness
+  k_b_matmul<<<dim3((maxb + 31) / 32, (maxa + 31) / 32, n), dim3(32, 8), 0, st>>>(B->dinst); ZK_COUNT_LAUNCH();
+  k_b_crpc_ab<<<dim3(maxn, n), 256, 0, st>>>(B->dinst); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaGetLastError());
+  // G2 run on side stream 0 (needs b_k and s)
   ZK_CUDA(cudaEventRecord(B->fork[0], st));
   ZK_CUDA(cudaStreamWaitEvent(B->side[0], B->fork[0], 0));
   ZK_TRY(msm_launch<Fp2>(&B->x_g2, nullptr, B->res_g2, B->side[0]));
   ZK_CUDA(cudaEventRecord(B->join[0], B->side[0]));
-  // witness
-  k_b_matmul<<<dim3((maxb + 31) / 32, (maxa + 31) / 32, n), dim3(32, 8), 0, st>>>(B->dinst); ZK_COUNT_LAUNCH();
-  k_b_crpc_ab<<<dim3(maxn, n), 256, 0, st>>>(B->dinst); ZK_COUNT_LAUNCH();
   k_b_crpc_y<<<dim3(maxa, n), 256, 0, st>>>(B->dinst); ZK_COUNT_LAUNCH();
   k_b_psq<<<n, 1024, 0, st>>>(B->dinst); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());

@@ -6,10 +6,19 @@
 #include "internal.h"
 #include "ntt.h"
 
-// Window widths of the fixed-base MSMs.  The G1 MSMs use signed 16-bit digits: int8
-// and int32 scalars take one and two digits, full Fr scalars 16.  Every G1 base that a
-// full scalar can meet stores its 16 multiples 2^(16 w) P.  The G2 MSM (int8 scalars
-// plus the s [delta]2 term) uses 8-bit digits.
+// Window widths of the fixed-base MSMs.  The large G1 runs (prefix sums, the H query, the
+// s w_v terms over the public inputs) use signed 16-bit digits over bases stored with
+// their 16 multiples 2^(16 w) P; the small-scalar and n-point runs use 8-bit digits (int8
+// in one digit, int32 in four, full scalars over 32 stored multiples 2^(8 w) P), as does G2.
+//
+// CRPC structure of the W side (Sec. III-A): the QAP polynomials of W_kj are multiples of
+// row k's Lagrange basis, B_(W_kj) = z^j L_k and L_(W_kj) = alpha z^j L_k / delta, so
+//   sum_(k,j) w_kj [B_(W_kj)] = sum_k b_k [L_k(tau)],   b_k = sum_j z^j w_kj,
+// and likewise for L; the X part of the A query is z^(ib) L_k plus the input row.  The
+// prover therefore needs only the n per-row points [L_k(tau)]1,2 and [alpha L_k / delta]1
+// (the j = 0 entries of the standard queries) with the full-scalar CRPC values a_k, b_k,
+// instead of n b int8 terms per query; the proof is the same group element.  The standard
+// queries are kept with one window each for export.
 #define ZKVC_C1 16u
 #define ZKVC_W1 16u
 #define ZKVC_C2 8u
@@ -20,24 +29,28 @@ namespace zkvc {
 // Regions of the G1 base array, in order.  An entry stores nwin consecutive bases
 // 2^(c w) P (w < nwin) so that every window of one MSM shares one bucket set.
 enum G1Region : int {
-  R1_A = 0,    // A-query, variables v = 0 .. l (one, X, Y)      l + 1   x16
+  R1_A = 0,    // A-query, variables v = 0 .. l (export)          l + 1   x1
   R1_ALPHA,    // [alpha]1                                       1       x16
   R1_BETA,     // [beta]1                                        1       x16
   R1_DELTA,    // [delta]1                                       1       x16
-  R1_B,        // B-query in G1, W variables                     n b     x16
-  R1_LW,       // L-query, W variables                           n b     x1
+  R1_B,        // B-query in G1, W variables (export)            n b     x1
+  R1_LW,       // L-query, W variables (export)                  n b     x1
   R1_LS,       // L-query, S variables (prefix sums)             n - 1   x16
   R1_H,        // H-query, bit-reversed positions                N       x16
   R1_AY8,      // A-query, Y variables, 2^(8 w) multiples         a b     x4   (c = 8)
   R1_DELTA8,   // [delta]1, 2^(8 w) multiples                    1       x32  (c = 8)
+  R1_AIN,      // input rows [L_(n+v)]1, v = 0 .. l              l + 1   x16
+  R1_LK,       // [L_k]1, k < n, 2^(8 w) multiples               n       x32  (c = 8)
+  R1_ALK,      // [alpha L_k / delta]1, 2^(8 w) multiples        n       x32  (c = 8)
   R1_COUNT
 };
 
 enum G2Region : int {
-  R2_B = 0,    // B-query in G2                                  n b     x1   (c = 8)
+  R2_B = 0,    // B-query in G2 (export)                         n b     x1
   R2_BETA,     // [beta]2                                        1
   R2_DELTA,    // [delta]2                                       1       x32  (c = 8)
   R2_GAMMA,    // [gamma]2 (verifying key only)                  1
+  R2_LK,       // [L_k]2, k < n, 2^(8 w) multiples               n       x32  (c = 8)
   R2_COUNT
 };
 

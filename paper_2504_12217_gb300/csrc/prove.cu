@@ -94,20 +94,23 @@ __global__ void k_chains(const Fr* __restrict__ rs, const G1J* __restrict__ smal
   st_field(chain + t, p_mul_scalar_w4(P, kk));
 }
 
-// sw[v] = s w_v for v = 0 .. l (one, X, Y) and rw[e] = r w_e for the W variables, in
-// Montgomery form: the scalars of the C terms s sum w_v A_v and r sum w_e B_e.
-__global__ void k_scaled_witness(const int8_t* __restrict__ X, const int32_t* __restrict__ Y,
-                                 const int8_t* __restrict__ W, const Fr* __restrict__ rs, uint32_t an, uint32_t l,
-                                 uint32_t nb, Fr* sw, Fr* rw) {
+// sw[v] = s w_v for v = 0 .. l (one, X, Y), sa[k] = s a_k and rb[k] = r b_k (k < n), in
+// Montgomery form: the scalars of the C terms s sum_v w_v [L_(n+v)]1, s sum_k a_k [L_k]1
+// and r sum_k b_k [L_k]1 (s A and r B1 expanded by linearity over the CRPC rows).
+__global__ void k_scaled_witness(const int8_t* __restrict__ X, const int32_t* __restrict__ Y, const Fr* __restrict__ ak,
+                                 const Fr* __restrict__ bk, const Fr* __restrict__ rs, uint32_t an, uint32_t l, uint32_t n,
+                                 Fr* sw, Fr* sa, Fr* rb) {
   uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t <= l) {
     Fr s = f_to_mont(ld_field(rs + 1));
     Fr w = t == 0 ? Fr::one() : (t <= an ? f_from_int<FrCfg>(X[t - 1]) : f_from_int<FrCfg>(Y[t - 1 - an]));
     st_field(sw + t, f_mul(s, w));
-  } else if (t < l + 1 + nb) {
-    uint32_t e = t - l - 1;
-    Fr r = f_to_mont(ld_field(rs));
-    st_field(rw + e, f_mul(r, f_from_int<FrCfg>(W[e])));
+  } else if (t < l + 1 + n) {
+    uint32_t k = t - l - 1;
+    st_field(sa + k, f_mul(f_to_mont(ld_field(rs + 1)), ld_field(ak + k)));
+  } else if (t < l + 1 + 2 * n) {
+    uint32_t k = t - l - 1 - n;
+    st_field(rb + k, f_mul(f_to_mont(ld_field(rs)), ld_field(bk + k)));
   }
 }
 
@@ -130,7 +133,7 @@ __global__ void k_encode(const G1J* small, const G1J* x, const G1J* y, const G1J
 
 // ------------------------------------------------------------------ plans and workspace
 struct ProveBufs {
-  Fr *ak, *bk, *yz, *S, *ev, *rs, *sw, *rw;
+  Fr *ak, *bk, *yz, *S, *ev, *rs, *sw, *sa, *rb;
   int* flags;
   G1J *res_small, *res_rest, *res_h, *res_chain;
   G2J* res2;
@@ -153,54 +156,55 @@ static MsmSeg seg_of(const Region& r, uint32_t first, uint32_t count, uint32_t o
 }
 
 // The MSM runs of one proof.  Fold mode (four runs on four streams):
-//   small (G1): output 0 = A, output 1 = the int8 part of C (L over the W variables);
-//   rest  (G1): the full-scalar part of C known right after the witness (L over S,
-//               s A_v, r B_e, s alpha, r beta, r s delta);
+//   small (G1, 8-bit digits): output 0 = A = [alpha]1 + the input rows of one, X, Y +
+//               sum_k a_k [L_k]1 + r [delta]1; output 1 = the CRPC part of C:
+//               sum_k b_k [alpha L_k / delta]1 (L over W) + s sum_k a_k [L_k]1 +
+//               r sum_k b_k [L_k]1;
+//   rest  (G1, 16-bit digits): the rest of C known right after the witness: L over S,
+//               s w_v over the input rows, s alpha, r beta, r s delta;
 //   h     (G1): the H part of C, after the NTTs;
-//   g2:         output 0 = B.
-// The small-scalar terms concentrate in buckets 1..128 and need long folds; "rest" does
-// not depend on h, so it overlaps the NTTs; only "h" follows them on the critical path.
-// Chain mode (three runs): small adds output 2 = B1 = [beta]1 + sum w_e [B_e]1 + s [delta]1,
-// "h" also takes L over S and -r s [delta]1, there is no "rest", and two variable-base
-// multiplications s A and r B1 complete C = L + H + s A + r B1 - r s delta.
+//   g2:         output 0 = B = [beta]2 + sum_k b_k [L_k]2 + s [delta]2.
+// "rest" does not depend on h, so it overlaps the NTTs; only "h" follows them.
+// Chain mode (three runs): small adds output 2 = B1 = [beta]1 + sum_k b_k [L_k]1 +
+// s [delta]1 and drops the s and r terms from output 1; "h" also takes L over S and
+// -r s [delta]1; there is no "rest"; two variable-base multiplications s A and r B1
+// complete C = L + H + s A + r B1 - r s delta.
 struct Plans {
   MsmPlan small, rest, h, g2;
 };
 
-static void plans(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const int32_t* dY, const Fr* S,
-                  const Fr* h, const Fr* rs, const Fr* sw, const Fr* rw, Plans* P) {
+static void plans(const zkvc_pk* pk, int mode, const int8_t* dX, const int32_t* dY, const Fr* ak, const Fr* bk,
+                  const Fr* S, const Fr* h, const Fr* rs, const Fr* sw, const Fr* sa, const Fr* rb, Plans* P) {
   const Shape& sh = pk->shape;
   const Region* g = pk->lay.g1;
-  const uint32_t an = sh.a * sh.n, ab = sh.a * sh.b, nb = sh.n * sh.b;
+  const uint32_t an = sh.a * sh.n, ab = sh.a * sh.b, n = sh.n;
   const bool chain = mode == ZKVC_PROVE_CHAIN;
-  // 8-bit digits: 128 buckets per output.  X and the constant one use window 0 of the
-  // A-query (stride 16); Y and r [delta]1 use their own 2^(8 w) regions.
   P->small.outs = {{8, 1, 0, 0}, {8, 1, 0, 0}};
   P->small.segs = {
-      // A = [alpha]1 + sum_v w_v [A_v]1 + r [delta]1
-      seg_of(g[R1_A], 0, 1, 0, SK_ONE, nullptr),
-      seg_of(g[R1_A], 1, an, 0, SK_I8, dX),
+      seg_of(g[R1_AIN], 0, 1, 0, SK_ONE, nullptr),
+      seg_of(g[R1_AIN], 1, an, 0, SK_I8, dX),
       seg_of(g[R1_AY8], 0, ab, 0, SK_I32, dY),
       seg_of(g[R1_ALPHA], 0, 1, 0, SK_ONE, nullptr),
       seg_of(g[R1_DELTA8], 0, 1, 0, SK_FR_CANON, rs + 0),
-      // C, int8 part: sum over the W variables of w_e [L_e]1
-      seg_of(g[R1_LW], 0, nb, 1, SK_I8, dW),
+      seg_of(g[R1_LK], 0, n, 0, SK_FR_MONT, ak),
+      seg_of(g[R1_ALK], 0, n, 1, SK_FR_MONT, bk),
   };
   P->h.outs = {{ZKVC_C1, 1, 0, 0}};
   P->h.segs = {seg_of(g[R1_H], 0, (uint32_t)sh.N, 0, SK_FR_MONT, h, (uint32_t)sh.N - 1)};
   if (chain) {
     P->small.outs.push_back({8, 1, 0, 0});
-    P->small.segs.push_back(seg_of(g[R1_B], 0, nb, 2, SK_I8, dW));
+    P->small.segs.push_back(seg_of(g[R1_LK], 0, n, 2, SK_FR_MONT, bk));
     P->small.segs.push_back(seg_of(g[R1_BETA], 0, 1, 2, SK_ONE, nullptr));
     P->small.segs.push_back(seg_of(g[R1_DELTA8], 0, 1, 2, SK_FR_CANON, rs + 1));
     P->h.segs.push_back(seg_of(g[R1_LS], 0, (uint32_t)(sh.n - 1), 0, SK_FR_MONT, S));
     P->h.segs.push_back(seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 3));
   } else {
+    P->small.segs.push_back(seg_of(g[R1_LK], 0, n, 1, SK_FR_MONT, sa));
+    P->small.segs.push_back(seg_of(g[R1_LK], 0, n, 1, SK_FR_MONT, rb));
     P->rest.outs = {{ZKVC_C1, 1, 0, 0}};
     P->rest.segs = {
         seg_of(g[R1_LS], 0, (uint32_t)(sh.n - 1), 0, SK_FR_MONT, S),
-        seg_of(g[R1_A], 0, sh.l + 1, 0, SK_FR_MONT, sw),
-        seg_of(g[R1_B], 0, nb, 0, SK_FR_MONT, rw),
+        seg_of(g[R1_AIN], 0, sh.l + 1, 0, SK_FR_MONT, sw),
         seg_of(g[R1_ALPHA], 0, 1, 0, SK_FR_CANON, rs + 1),
         seg_of(g[R1_BETA], 0, 1, 0, SK_FR_CANON, rs + 0),
         seg_of(g[R1_DELTA], 0, 1, 0, SK_FR_CANON, rs + 2),
@@ -209,7 +213,7 @@ static void plans(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   const Region* g2 = pk->lay.g2;
   P->g2.outs = {{ZKVC_C2, 1, 0, 0}};
   P->g2.segs = {
-      seg_of(g2[R2_B], 0, nb, 0, SK_I8, dW),
+      seg_of(g2[R2_LK], 0, n, 0, SK_FR_MONT, bk),
       seg_of(g2[R2_BETA], 0, 1, 0, SK_ONE, nullptr),
       seg_of(g2[R2_DELTA], 0, 1, 0, SK_FR_CANON, rs + 1),
   };
@@ -237,7 +241,8 @@ static size_t carve(const zkvc_pk* pk, int mode, void* base, size_t cap, ProveBu
   B->ev = a.take<Fr>(4 * sh.N);
   B->rs = a.take<Fr>(4);
   B->sw = chain ? nullptr : a.take<Fr>(sh.l + 1);
-  B->rw = chain ? nullptr : a.take<Fr>(size_t(sh.n) * sh.b);
+  B->sa = chain ? nullptr : a.take<Fr>(sh.n);
+  B->rb = chain ? nullptr : a.take<Fr>(sh.n);
   B->flags = a.take<int>(4);
   B->res_small = a.take<G1J>(3);
   B->res_rest = a.take<G1J>(1);
@@ -246,7 +251,7 @@ static size_t carve(const zkvc_pk* pk, int mode, void* base, size_t cap, ProveBu
   B->res2 = a.take<G2J>(1);
   B->proof = a.take<uint8_t>(256);
   Plans P;
-  plans(pk, mode, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &P);
+  plans(pk, mode, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &P);
   B->ws_small_bytes = msm_workspace_bytes<Fp>(P.small);
   B->ws_rest_bytes = chain ? 0 : msm_workspace_bytes<Fp>(P.rest);
   B->ws_h_bytes = msm_workspace_bytes<Fp>(P.h);
@@ -322,26 +327,32 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   ZK_CUDA(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), st));
   ZK_CUDA(cudaMemcpyAsync(B.rs, rs_host, 64, cudaMemcpyHostToDevice, st));
   k_randomness<<<1, 1, 0, st>>>(B.rs, B.flags); ZK_COUNT_LAUNCH();
-  // G2 MSM on side stream 0: it needs only W and s
   SideStreams* side = nullptr;
   ZK_TRY(side_streams(&side));
   Plans P;
-  plans(pk, mode, dX, dW, dY, B.S, Hev, B.rs, B.sw, B.rw, &P);
+  plans(pk, mode, dX, dY, B.ak, B.bk, B.S, Hev, B.rs, B.sw, B.sa, B.rb, &P);
+  // 1. Y = X W;  2. the CRPC sums a_k, b_k
+  dim3 mg((sh.b + 31) / 32, (sh.a + 31) / 32);
+  k_matmul_i8<<<mg, dim3(32, 8), 0, st>>>(dX, dW, dY, sh.a, sh.n, sh.b); ZK_COUNT_LAUNCH();
+  k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaGetLastError());
+  // G2 MSM on side stream 0: it needs b_k and s
   ZK_TRY(fork_to(side, 0, st));
   prof_mark(PS_MSM_G2, true, side->st[0]);
   ZK_TRY(msm_run<Fp2>(P.g2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st[0], PS_ACCUM_G2));
   prof_mark(PS_MSM_G2, false, side->st[0]);
   ZK_CUDA(cudaEventRecord(side->join[0], side->st[0]));
-  // 1. Y = X W
-  dim3 mg((sh.b + 31) / 32, (sh.a + 31) / 32);
-  k_matmul_i8<<<mg, dim3(32, 8), 0, st>>>(dX, dW, dY, sh.a, sh.n, sh.b); ZK_COUNT_LAUNCH();
-  // 2-3. CRPC evaluations and PSQ prefix sums
-  k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
+  // 3. Y(z) and the PSQ prefix sums; in fold mode the scalars s w_v, s a_k, r b_k
   k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz); ZK_COUNT_LAUNCH();
   k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, B.S, Aev, Bev, Cev, B.flags); ZK_COUNT_LAUNCH();
+  if (!chain) {
+    uint32_t nsc = sh.l + 1 + 2 * uint32_t(sh.n);
+    k_scaled_witness<<<(nsc + 255) / 256, 256, 0, st>>>(dX, dY, B.ak, B.bk, B.rs, sh.a * sh.n, sh.l, sh.n, B.sw, B.sa,
+                                                        B.rb); ZK_COUNT_LAUNCH();
+  }
   ZK_CUDA(cudaGetLastError());
-  // the small-scalar G1 MSM on side stream 1 (needs X, Y, W, r, s), then in chain mode
-  // the two variable-base multiplications
+  // the small-digit G1 MSM on side stream 1, then in chain mode the two variable-base
+  // multiplications
   ZK_TRY(fork_to(side, 1, st));
   ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
   if (chain) {
@@ -349,14 +360,9 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
     ZK_CUDA(cudaGetLastError());
   }
   ZK_CUDA(cudaEventRecord(side->join[1], side->st[1]));
-  // 4. remaining domain evaluations (and, in fold mode, the scalars s w_v, r w_e)
+  // 4. remaining domain evaluations
   size_t rest = N - sh.n;
   k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev); ZK_COUNT_LAUNCH();
-  if (!chain) {
-    uint32_t nsc = sh.l + 1 + uint32_t(sh.n) * sh.b;
-    k_scaled_witness<<<(nsc + 255) / 256, 256, 0, st>>>(dX, dY, dW, B.rs, sh.a * sh.n, sh.l, uint32_t(sh.n) * sh.b,
-                                                        B.sw, B.rw); ZK_COUNT_LAUNCH();
-  }
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_WITNESS, false, st);
   if (!chain) {

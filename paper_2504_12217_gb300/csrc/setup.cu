@@ -43,17 +43,18 @@ int make_shape(int a, int n, int b, Shape* s) {
 Layout make_layout(const Shape& s) {
   Layout L{};
   const uint32_t nb = s.n * s.b, ab = s.a * s.b;
-  const uint32_t cnt1[R1_COUNT] = {s.l + 1, 1, 1, 1, nb, nb, (uint32_t)(s.n - 1), (uint32_t)s.N, ab, 1};
-  const uint32_t win1[R1_COUNT] = {ZKVC_W1, ZKVC_W1, ZKVC_W1, ZKVC_W1, ZKVC_W1, 1, ZKVC_W1, ZKVC_W1, 4, 32};
-  const uint32_t c1[R1_COUNT] = {ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, 8, 8};
+  const uint32_t n = (uint32_t)s.n;
+  const uint32_t cnt1[R1_COUNT] = {s.l + 1, 1, 1, 1, nb, nb, n - 1, (uint32_t)s.N, ab, 1, s.l + 1, n, n};
+  const uint32_t win1[R1_COUNT] = {1, ZKVC_W1, ZKVC_W1, ZKVC_W1, 1, 1, ZKVC_W1, ZKVC_W1, 4, 32, ZKVC_W1, 32, 32};
+  const uint32_t c1[R1_COUNT] = {ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, ZKVC_C1, 8, 8, ZKVC_C1, 8, 8};
   uint64_t off = 0;
   for (int r = 0; r < R1_COUNT; r++) {
     L.g1[r] = {off, cnt1[r], win1[r], c1[r], r};
     off += uint64_t(cnt1[r]) * win1[r];
   }
   L.n_g1 = off;
-  const uint32_t cnt2[R2_COUNT] = {nb, 1, 1, 1};
-  const uint32_t win2[R2_COUNT] = {1, 1, ZKVC_W2_FULL, 1};
+  const uint32_t cnt2[R2_COUNT] = {nb, 1, 1, 1, n};
+  const uint32_t win2[R2_COUNT] = {1, 1, ZKVC_W2_FULL, 1, ZKVC_W2_FULL};
   off = 0;
   for (int r = 0; r < R2_COUNT; r++) {
     L.g2[r] = {off, cnt2[r], win2[r], ZKVC_C2, r};
@@ -185,6 +186,9 @@ __global__ void k_query_scalars(RegionTab tab, int group, const SetupConsts* __r
       }
       case R1_AY8: s = ld_field(L + n + 1 + an + e); break;
       case R1_DELTA8: s = sc.delta; break;
+      case R1_AIN: s = ld_field(L + n + e); break;
+      case R1_LK: s = ld_field(L + e); break;
+      case R1_ALK: s = f_mul(f_mul(sc.alpha, sc.dinv), ld_field(L + e)); break;
     }
   } else if (group == GRP_G2) {
     switch (rg.kind) {
@@ -192,6 +196,7 @@ __global__ void k_query_scalars(RegionTab tab, int group, const SetupConsts* __r
       case R2_BETA: s = sc.beta; break;
       case R2_DELTA: s = sc.delta; break;
       case R2_GAMMA: s = sc.gamma; break;
+      case R2_LK: s = ld_field(L + e); break;
     }
   } else {  // verifying-key IC_v = (beta A_v + alpha B_v + C_v) / gamma, v = 0 .. l
     uint32_t v = e;
