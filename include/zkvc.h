@@ -57,9 +57,10 @@ uint64_t zkvc_kernel_launches(void);
 
 /* Stage timers for the prover: when enabled, zkvc_prove records CUDA events on its
  * stream around each stage and accumulates their elapsed times after its final
- * synchronisation.  Stages 0..6: witness, ntt, msm_g1, msm_g1_bucket_accum, msm_g2,
- * msm_g2_bucket_accum, combine.  The two bucket_accum stages time the bucket-accumulation
- * kernel alone and count its units (bucket terms, one mixed point addition each).
+ * synchronisation.  Stages 0..6: witness, ntt, msm_g1 (the H-query MSM),
+ * msm_g1_bucket_accum (its accumulation kernel), msm_g2, msm_g2_bucket_accum, combine.
+ * The two bucket_accum stages time the bucket-accumulation kernel alone and count its
+ * units (bucket terms, one mixed point addition each).
  * Enabling resets the counters.  A single-threaded diagnostic: not for concurrent provers.
  */
 void zkvc_profile_enable(int on);

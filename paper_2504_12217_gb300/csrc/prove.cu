@@ -368,9 +368,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   if (!chain) {
     // the full-scalar G1 terms that need no h, on side stream 2 (overlapping the NTTs)
     ZK_TRY(fork_to(side, 2, st));
-    prof_mark(PS_MSM_G1, true, side->st[2]);
-    ZK_TRY(msm_run<Fp>(P.rest, pk->g1, B.ws_rest, B.ws_rest_bytes, B.res_rest, side->st[2], PS_ACCUM_G1));
-    prof_mark(PS_MSM_G1, false, side->st[2]);
+    ZK_TRY(msm_run<Fp>(P.rest, pk->g1, B.ws_rest, B.ws_rest_bytes, B.res_rest, side->st[2]));
     ZK_CUDA(cudaEventRecord(side->join[2], side->st[2]));
   }
   // 5-6. quotient and the H part of C on side stream 3 (the critical chain)
@@ -385,9 +383,10 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   k_check_h<<<1, 32, 0, s3>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_NTT, false, s3);
-  if (chain) prof_mark(PS_MSM_G1, true, s3);
-  ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3, chain ? PS_ACCUM_G1 : -1));
-  if (chain) prof_mark(PS_MSM_G1, false, s3);
+  // the H MSM is the largest G1 run (N 16-bit digits): its stage and accumulation timers
+  prof_mark(PS_MSM_G1, true, s3);
+  ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3, PS_ACCUM_G1));
+  prof_mark(PS_MSM_G1, false, s3);
   ZK_CUDA(cudaEventRecord(side->join[3], s3));
   for (int i = 0; i < NSIDE; i++) {
     if (chain && i == 2) continue;
