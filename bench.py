@@ -809,7 +809,7 @@ def main():
     ap.add_argument("--server-slots", type=int, default=8)
     ap.add_argument("--server-budget-gib", type=int, default=48)
     ap.add_argument("--batch-count", type=int, default=0, help="batched: only the K smallest instances")
-    ap.add_argument("--tuning", type=int, nargs=10, default=None, help="batched: impose a tuning, skip the autotuner")
+    ap.add_argument("--tuning", type=int, nargs=7, default=None, help="batched: impose a tuning, skip the autotuner")
     ap.add_argument("--eager", action="store_true", help="batched: launch eagerly instead of replaying a graph")
     args = ap.parse_args()
     if args.sweep:

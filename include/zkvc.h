@@ -362,7 +362,7 @@ int zkvc_pk_circuit(const zkvc_pk* pk, int* circuit, int* public_io, uint64_t* r
  *
  * zkvc_batch_get_tuning / zkvc_batch_set_tuning read or impose the launch shape as
  * ZKVC_BATCH_TUNING_LEN integers: for the small G1, main G1 and G2 MSM runs in turn
- * (chunk terms per thread, accumulation threads per block, fold grid blocks), then the
+ * (chunk terms per thread, accumulation threads per block), then the
  * NTT's log2 elements per block.  Setting re-captures on the next prove.
  *
  * zkvc_batch_terms reports the bucket terms (point additions) of the last call's three
@@ -373,7 +373,7 @@ int zkvc_pk_circuit(const zkvc_pk* pk, int* circuit, int* public_io, uint64_t* r
 typedef struct zkvc_batch zkvc_batch;
 #define ZKVC_BATCH_AUTOTUNE 1
 #define ZKVC_BATCH_EAGER 2
-#define ZKVC_BATCH_TUNING_LEN 10
+#define ZKVC_BATCH_TUNING_LEN 7
 
 int zkvc_batch_create(const zkvc_pk* const* pks, int count, int flags, zkvc_batch** batch);
 void zkvc_batch_free(zkvc_batch* batch);

@@ -218,7 +218,6 @@ static const uint32_t kChunkG1[] = {8, 16, 32, 64};
 static const uint32_t kChunkG2[] = {8, 16, 32};
 static const uint32_t kAccumG1[] = {64, 128, 256};
 static const uint32_t kAccumG2[] = {64, 128};
-static const uint32_t kFold[] = {304, 608, 1216};
 static const int kElog[] = {9, 10, 11};
 
 static MsmSeg bseg(const Region& r, uint32_t first, uint32_t count, uint32_t out, int kind, const void* sc,
@@ -548,14 +547,6 @@ static int autotune(zkvc_batch* B) {
       ZK_TRY(trial(t, &ms));
       if (ms < best_ms) { best_ms = ms; best = t; }
     }
-    for (uint32_t f : kFold) {
-      if (f == best.fold_blocks) continue;
-      MsmTune t = best;
-      t.fold_blocks = f;
-      float ms;
-      ZK_TRY(trial(t, &ms));
-      if (ms < best_ms) { best_ms = ms; best = t; }
-    }
     *k.tune = best;
   }
   // NTT block size (the sequence transforms the evaluation buffers in place; the graph
@@ -696,11 +687,10 @@ static int device_guard_batch(int dev) {
 static void tune_to_array(const BatchTune& t, int32_t* v) {
   const MsmTune* m[3] = {&t.small, &t.main, &t.g2};
   for (int i = 0; i < 3; i++) {
-    v[3 * i] = (int32_t)m[i]->chunk;
-    v[3 * i + 1] = (int32_t)m[i]->accum_threads;
-    v[3 * i + 2] = (int32_t)m[i]->fold_blocks;
+    v[2 * i] = (int32_t)m[i]->chunk;
+    v[2 * i + 1] = (int32_t)m[i]->accum_threads;
   }
-  v[9] = t.elog;
+  v[6] = t.elog;
 }
 
 }  // namespace zkvc
@@ -746,8 +736,8 @@ int zkvc_batch_get_tuning(const zkvc_batch* b, int32_t* params, int n) {
   tune_to_array(b->tune, v);
   // chunk 0 means "automatic": report the chunk the finalized plans use
   v[0] = (int32_t)b->p_small.chunk;
-  v[3] = (int32_t)b->p_main.chunk;
-  v[6] = (int32_t)b->p_g2.chunk;
+  v[2] = (int32_t)b->p_main.chunk;
+  v[4] = (int32_t)b->p_g2.chunk;
   std::memcpy(params, v, sizeof(v));
   return ZKVC_OK;
 }
@@ -761,13 +751,12 @@ int zkvc_batch_set_tuning(zkvc_batch* b, const int32_t* params, int n) {
   MsmTune* m[3] = {&t.small, &t.main, &t.g2};
   const uint32_t min_chunk[3] = {kChunkG1[0], kChunkG1[0], kChunkG2[0]};
   for (int i = 0; i < 3; i++) {
-    ZK_CHECK(params[3 * i] >= (int32_t)min_chunk[i] && params[3 * i] <= 1024, ZKVC_EINVAL,
-             "batch tuning: chunk %d outside [%u, 1024]", params[3 * i], min_chunk[i]);
-    m[i]->chunk = (uint32_t)params[3 * i];
-    m[i]->accum_threads = (uint32_t)params[3 * i + 1];
-    m[i]->fold_blocks = (uint32_t)params[3 * i + 2];
+    ZK_CHECK(params[2 * i] >= (int32_t)min_chunk[i] && params[2 * i] <= 1024, ZKVC_EINVAL,
+             "batch tuning: chunk %d outside [%u, 1024]", params[2 * i], min_chunk[i]);
+    m[i]->chunk = (uint32_t)params[2 * i];
+    m[i]->accum_threads = (uint32_t)params[2 * i + 1];
   }
-  t.elog = params[9];
+  t.elog = params[6];
   ZK_CHECK(t.elog >= 8 && t.elog <= 11, ZKVC_EINVAL, "batch tuning: NTT block of 2^%d elements", t.elog);
   ZK_TRY(wait_stream(b->cap, "batch set tuning"));
   BatchTune old = b->tune;

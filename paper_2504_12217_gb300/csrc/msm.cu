@@ -5,20 +5,25 @@
 // selects bucket |d| and the sign negates the base's y coordinate.  Every nonzero digit
 // becomes one term (bucket key, base index | sign).  Terms are counting-sorted by key
 // (histogram, scan, atomic scatter), then each bucket's terms are summed by a
-// load-balanced segmented reduction: level 0 gives every chunk of T0 consecutive terms
-// of a bucket to one thread (mixed XYZZ + affine additions), and binary in-place folds
-// then add each bucket's partial sums, so heavily skewed buckets (int8 scalars put ~1300
-// terms in each of 128 buckets) cost only log2 of their chunk count in depth.
+// load-balanced segmented reduction: every chunk of T0 consecutive terms of a bucket goes
+// to one thread (mixed XYZZ + affine additions), and the chunk sums of a bucket are added
+// along a binary tree inside the same kernel -- of two sibling subtrees, the thread that
+// finishes second (an atomic counter per tree node tells it) adds both and climbs on, the
+// first one exits.  Heavily skewed buckets (int8 scalars put ~1300 terms in each of 128
+// buckets) so cost only log2 of their chunk count in depth, with no extra launches.
 // A window's result sum_v v B_v is evaluated as sum_b 2^b U_b with U_b the sum of the
-// buckets whose index has bit b set: wide trees for the U_b, b doublings per bit in
-// parallel, and a short tree over the bits -- log-depth instead of a running sum, since a
-// single thread's point addition is long-latency (~14 us) on the GPU.
+// buckets whose index has bit b set: one block per slice of a bit's buckets reduces it
+// in shared memory, one block per bit adds the slices and doubles b times, one block per
+// window adds the bits -- log-depth instead of a running sum, since a point addition is
+// long-latency on the GPU (about 10 us for one thread).  Where few sums remain, the
+// additions and doublings run on quads of lanes (coop.cuh).
 //
 // Fixed-base MSMs (proving-key queries) store the multiples 2^(c w) P of each base, so all
 // windows share one bucket set and no doubling chain follows; variable-base MSMs keep
 // one bucket set per window and combine windows by Horner's rule.
 #include <algorithm>
 
+#include "coop.cuh"
 #include "msm.h"
 
 namespace zkvc {
@@ -140,7 +145,6 @@ int msm_plan_finalize(MsmPlan& p) {
   ZK_CHECK(p.chunk >= 1 && p.chunk <= 1024, ZKVC_EINVAL, "msm: chunk of %u terms", p.chunk);
   ZK_CHECK(p.tune.accum_threads >= 32 && p.tune.accum_threads <= 256 && p.tune.accum_threads % 32 == 0,
            ZKVC_EINVAL, "msm: %u accumulation threads", p.tune.accum_threads);
-  ZK_CHECK(p.tune.fold_blocks >= 1, ZKVC_EINVAL, "msm: fold grid of 0 blocks");
   p.slots = slot;
   p.points = pts;
   // outputs with their own base arrays: every output must name one, and all must have
@@ -358,12 +362,28 @@ __device__ __forceinline__ uint32_t find_key(const uint32_t* off, uint32_t K, ui
 }
 
 // ------------------------------------------------------------------ bucket sums
-__global__ void k_chunk_keys(const uint32_t* __restrict__ choff, uint32_t K, uint32_t* chunk_key, uint32_t* max_chunks) {
+__global__ void k_chunk_keys(const uint32_t* __restrict__ choff, uint32_t K, uint32_t* chunk_key) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   uint32_t a = choff[k], b = choff[k + 1];
   for (uint32_t q = a; q < b; q++) chunk_key[q] = k;
-  if (b > a + 1) atomicMax(max_chunks, b - a);
+}
+
+// point loads that bypass L1: a sibling's partial sum written by another SM
+template <class F>
+__device__ __forceinline__ XYZZ<F> ld_point_cg(const XYZZ<F>* p) {
+  XYZZ<F> r;
+  uint32_t* d = reinterpret_cast<uint32_t*>(&r);
+  const uint4* s = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(XYZZ<F>) / 16); i++) {
+    uint4 q = __ldcg(s + i);
+    d[4 * i] = q.x;
+    d[4 * i + 1] = q.y;
+    d[4 * i + 2] = q.z;
+    d[4 * i + 3] = q.w;
+  }
+  return r;
 }
 
 // level 0: chunk q sums up to T0 consecutive terms of its bucket (mixed additions)
@@ -390,26 +410,62 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
   st_field(part + q, acc);
 }
 
-// binary fold of the partial sums of each bucket, in place: at level l the partial at
-// local index i (a multiple of 2^(l+1)) absorbs the one at i + 2^l.  Levels at or above
-// log2 of the largest chunk count exit at once (the count is only known on the device).
-// (A block-per-heavy-bucket variant measured slower on GB300: barrier stalls while one
-// warp finishes each block's tree.)
+// The chunk sums of each bucket are added along the binary tree over chunk positions
+// 0..np-1, in one launch: at span s the subtree at position i (a multiple of s) pairs
+// with the one at i ^ s.  Each sibling counts in at the node's counter (index: left
+// position + s - 1, distinct over all levels since it ends in exactly log2 s one-bits);
+// the first to arrive exits, the second adds both sums and climbs on.  A left subtree
+// with no right sibling climbs without waiting.  A subtree's sum sits at its left
+// position: a climber stores only sums it has changed (a chunk's own sum is there from
+// the accumulation launch).  The bucket total ends in part[choff[k]].  `arrive` holds one
+// zeroed counter per chunk.  G2 chunks get a quad of lanes each (the additions' latency
+// sets the depth of this tree; coop.cuh), G1 chunks one thread.
 template <class F>
-__global__ void __launch_bounds__(256) k_fold(XYZZ<F>* part, const uint32_t* __restrict__ choff,
-                                              const uint32_t* __restrict__ chunk_key, uint32_t K,
-                                              const uint32_t* __restrict__ max_chunks, uint32_t l) {
-  const uint32_t step = 1u << l;
-  if (step >= *max_chunks) return;
-  const uint32_t total = choff[K];
-  // grid-stride over the chunk slots (the grid is small, so levels above the largest
-  // chunk count cost little more than the launch)
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-    uint32_t k = chunk_key[q];
-    uint32_t base = choff[k], i = q - base, np = choff[k + 1] - base;
-    if ((i & (2 * step - 1)) != 0 || i + step >= np) continue;
-    st_field(part + q, p_add(ld_field(part + q), ld_field(part + q + step)));
+struct FoldLanes {
+  static constexpr int value = sizeof(F) > 32 ? 4 : 1;
+};
+
+template <class F>
+__global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ choff,
+                                                   const uint32_t* __restrict__ chunk_key, uint32_t K,
+                                                   XYZZ<F>* part, uint32_t* arrive) {
+  constexpr int QL = FoldLanes<F>::value;
+  const uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
+  if (q >= choff[K]) return;  // uniform within a quad
+  const bool lead = QL == 1 || quad_lane() == 0;
+  const uint32_t k = chunk_key[q];
+  const uint32_t base = choff[k], np = choff[k + 1] - base;
+  uint32_t pos = q - base;
+  XYZZ<F> acc;
+  bool have = false;  // acc holds this subtree's sum (else it is only in part[])
+  for (uint32_t span = 1; span < np; span <<= 1) {
+    const bool left = (pos & span) == 0;
+    const uint32_t sib = pos ^ span;
+    if (left && sib >= np) continue;
+    uint32_t first = 0;
+    if (lead) {
+      if (have) {
+        st_field(part + base + pos, acc);
+        __threadfence();
+      }
+      first = atomicAdd(arrive + base + (left ? pos : sib) + span - 1, 1u) == 0;
+      __threadfence();
+    }
+    if (QL > 1) {
+      first = __shfl_sync(quad_mask(), first, quad_base());
+      __syncwarp(quad_mask());  // orders the lead's acquire before the quad's loads
+    }
+    if (first) return;
+    if (!have) acc = ld_point_cg(part + base + pos);
+    const XYZZ<F> o = ld_point_cg(part + base + sib);
+    if (QL > 1)
+      acc = left ? p_add_quad(acc, o) : p_add_quad(o, acc);
+    else
+      acc = left ? p_add(acc, o) : p_add(o, acc);
+    have = true;
+    pos = left ? pos : sib;
   }
+  if (have && lead) st_field(part + base, acc);
 }
 
 template <class F>
@@ -419,15 +475,61 @@ __device__ __forceinline__ XYZZ<F> bucket_at(const XYZZ<F>* fin, const uint32_t*
   return ld_field(fin + choff[key]);
 }
 
+// Sum of m points get(0..m-1) by a block of BT threads (a multiple of 4), returned to
+// every thread; sh holds BT points.  Levels with more pairs than quads give a pair to a
+// thread, the others a pair to a quad (coop.cuh).  Every thread of the block must call it.
+template <class F, int BT, class Get>
+__device__ XYZZ<F> block_sum(Get get, uint32_t m, XYZZ<F>* sh) {
+  const uint32_t t = threadIdx.x, qd = t >> 2;
+  const bool lead = (t & 3) == 0;
+  uint32_t n;
+  if (m > 2 * BT) {
+    XYZZ<F> acc = XYZZ<F>::inf();
+    for (uint32_t i = t; i < m; i += BT) acc = p_add(acc, get(i));
+    st_field(sh + t, acc);
+    n = BT;
+  } else {
+    const uint32_t pairs = (m + 1) / 2;
+    if (pairs > BT / 4) {
+      if (t < pairs) {
+        XYZZ<F> a = get(2 * t);
+        if (2 * t + 1 < m) a = p_add(a, get(2 * t + 1));
+        st_field(sh + t, a);
+      }
+    } else if (qd < pairs) {
+      XYZZ<F> a = get(2 * qd);
+      if (2 * qd + 1 < m) a = p_add_quad(a, get(2 * qd + 1));
+      if (lead) st_field(sh + qd, a);
+    }
+    n = pairs;
+  }
+  __syncthreads();
+  while (n > 1) {
+    const uint32_t h = (n + 1) / 2, pairs = n - h;  // entry i < pairs absorbs entry i + h
+    if (pairs > BT / 4) {
+      if (t < pairs) st_field(sh + t, p_add(ld_field(sh + t), ld_field(sh + t + h)));
+    } else if (qd < pairs) {
+      const XYZZ<F> r = p_add_quad(ld_field(sh + qd), ld_field(sh + qd + h));
+      __syncwarp(quad_mask());  // the quad's reads of sh[qd] precede the lead's store
+      if (lead) st_field(sh + qd, r);
+    }
+    __syncthreads();
+    n = h;
+  }
+  return m ? ld_field(sh) : XYZZ<F>::inf();
+}
+
 // Window result sum_{v=1}^{NB} v B_v = sum_b 2^b U_b with U_b = sum_{v : bit b of v} B_v.
-// One BitSeg per (output, window, bit): the U_b sum starts as pairs of buckets and is
-// finished by strided tree levels; then 2^b U_b (b doublings, all bits in parallel) and a
-// tree over the bits of each (output, window).
+// One BitSeg per (output, window, bit); its cnt buckets are cut into slices, each summed
+// by one block (serial sums per thread first, then the block's tree).
 struct BitSeg {
-  uint32_t key0;  // key of bucket v = 1 of this (output, window)
-  uint32_t b, c;  // bit, window bits
-  uint32_t uoff;  // first pair in the U buffer
-  uint32_t dslot; // slot of 2^b U_b in the D buffer
+  uint32_t key0;    // key of bucket v = 1 of this (output, window)
+  uint32_t b, c;    // bit, window bits
+  uint32_t cnt;     // buckets with bit b
+  uint32_t soff;    // first slice in the slice-sum buffer
+  uint32_t nsl;     // slices
+  uint32_t dslot;   // slot of 2^b U_b in the D buffer
+  uint32_t pad;
 };
 
 __device__ __forceinline__ uint32_t nth_with_bit(uint32_t b, uint32_t c, uint32_t idx) {
@@ -435,87 +537,68 @@ __device__ __forceinline__ uint32_t nth_with_bit(uint32_t b, uint32_t c, uint32_
   return ((idx >> b) << (b + 1)) | (1u << b) | (idx & ((1u << b) - 1u));
 }
 
+// 128 (G1) or 64 (G2) threads: several blocks fit an SM beside the register-heavy point
+// formulas, so SMs stay busy while a block's tree narrows
 template <class F>
-__global__ void __launch_bounds__(256) k_bits_first(const XYZZ<F>* __restrict__ fin, const uint32_t* __restrict__ counts,
-                                                    const uint32_t* __restrict__ choff, const BitSeg* __restrict__ segs,
-                                                    uint32_t nseg, uint32_t total, XYZZ<F>* U) {
-  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
+struct SliceBT {
+  static constexpr int value = sizeof(F) > 32 ? 64 : 128;
+};
+constexpr uint32_t SLICE_WAVE = 456;  // 152 SMs x 3 resident slice blocks
+
+// block per slice: the sum of up to `slice` buckets of one bit
+template <class F>
+__global__ void __launch_bounds__(SliceBT<F>::value) k_bits_slices(const XYZZ<F>* __restrict__ fin,
+                                                                    const uint32_t* __restrict__ counts,
+                                                                    const uint32_t* __restrict__ choff,
+                                                                    const BitSeg* __restrict__ segs, uint32_t nseg,
+                                                                    uint32_t slice, XYZZ<F>* S) {
+  constexpr int BT = SliceBT<F>::value;
+  __shared__ XYZZ<F> sh[BT];
+  const uint32_t sl = blockIdx.x;
   uint32_t lo = 0, hi = nseg - 1;
   while (lo < hi) {
     uint32_t mid = (lo + hi + 1) >> 1;
-    if (segs[mid].uoff <= t) lo = mid; else hi = mid - 1;
+    if (segs[mid].soff <= sl) lo = mid; else hi = mid - 1;
   }
-  const BitSeg s = segs[lo];
-  const uint32_t j = t - s.uoff;
-  const uint32_t cnt = (s.b == s.c - 1) ? 1u : (1u << (s.c - 2));
-  XYZZ<F> acc = bucket_at(fin, counts, choff, s.key0 + nth_with_bit(s.b, s.c, 2 * j) - 1);
-  if (2 * j + 1 < cnt) acc = p_add(acc, bucket_at(fin, counts, choff, s.key0 + nth_with_bit(s.b, s.c, 2 * j + 1) - 1));
-  st_field(U + t, acc);
+  const BitSeg g = segs[lo];
+  const uint32_t first = (sl - g.soff) * slice;
+  const uint32_t m = min(slice, g.cnt - first);
+  auto get = [&](uint32_t i) { return bucket_at(fin, counts, choff, g.key0 + nth_with_bit(g.b, g.c, first + i) - 1); };
+  const XYZZ<F> r = block_sum<F, BT>(get, m, sh);
+  if (threadIdx.x == 0) st_field(S + sl, r);
 }
 
+// block per bit: U_b = the sum of the bit's slices, then 2^b U_b by b doublings (one quad)
+constexpr int BITS_BT = 64;
 template <class F>
-__global__ void __launch_bounds__(64) k_bits_scale(const XYZZ<F>* __restrict__ U, const BitSeg* __restrict__ segs,
-                                                   uint32_t nseg, XYZZ<F>* D) {
-  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nseg) return;
-  BitSeg s = segs[t];
-  XYZZ<F> x = ld_field(U + s.uoff);
-  for (uint32_t i = 0; i < s.b; i++) x = p_dbl(x);
-  st_field(D + s.dslot, x);
+__global__ void __launch_bounds__(BITS_BT) k_bits_scale(const XYZZ<F>* __restrict__ S, const BitSeg* __restrict__ segs,
+                                                         XYZZ<F>* D) {
+  __shared__ XYZZ<F> sh[BITS_BT];
+  const BitSeg g = segs[blockIdx.x];
+  auto get = [&](uint32_t i) { return ld_field(S + g.soff + i); };
+  XYZZ<F> x = block_sum<F, BITS_BT>(get, g.nsl, sh);
+  if (threadIdx.x >= 4) return;
+  for (uint32_t i = 0; i < g.b; i++) x = p_dbl_quad(x);
+  if (threadIdx.x == 0) st_field(D + g.dslot, x);
 }
 
-// In-place tree over segments: at level l, element i*2^(l+1) absorbs element
-// i*2^(l+1) + 2^l of the same segment.  Threads map only to pairs that exist at this
-// level (cum[s] counts the pairs of the segments before s), so no lane is idle.
+// block per (output, window): the window's c terms 2^b U_b, summed into the first slot
 struct TreeSeg {
   uint32_t off;  // first element
   uint32_t len;  // elements
 };
 
 template <class F>
-__global__ void __launch_bounds__(256) k_tree_level(XYZZ<F>* x, const TreeSeg* __restrict__ segs,
-                                                    const uint32_t* __restrict__ cum, uint32_t nseg, uint32_t total,
-                                                    uint32_t l) {
-  uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  uint32_t lo = 0, hi = nseg - 1;
-  while (lo < hi) {
-    uint32_t mid = (lo + hi + 1) >> 1;
-    if (cum[mid] <= t) lo = mid; else hi = mid - 1;
-  }
-  TreeSeg s = segs[lo];
-  uint32_t i = t - cum[lo];
-  uint64_t a = s.off + (uint64_t(i) << (l + 1)), b = a + (1ull << l);
-  st_field(x + a, p_add(ld_field(x + a), ld_field(x + b)));
+__global__ void __launch_bounds__(BITS_BT) k_bits_window(XYZZ<F>* D, const TreeSeg* __restrict__ segs) {
+  __shared__ XYZZ<F> sh[BITS_BT];
+  const TreeSeg g = segs[blockIdx.x];
+  auto get = [&](uint32_t i) { return ld_field(D + g.off + i); };
+  const XYZZ<F> r = block_sum<F, BITS_BT>(get, g.len, sh);
+  if (threadIdx.x == 0) st_field(D + g.off, r);
 }
 
-// host-side per-level pair counts of a tree over segments
-struct TreePlan {
-  std::vector<TreeSeg> segs;
-  std::vector<uint32_t> cum;     // levels x nseg
-  std::vector<uint32_t> totals;  // per level
-  uint32_t levels = 0;
-  void finish() {
-    uint32_t maxlen = 1;
-    for (auto& s : segs) maxlen = std::max(maxlen, s.len);
-    levels = 0;
-    while ((1u << levels) < maxlen) levels++;
-    cum.assign(size_t(levels) * segs.size(), 0);
-    totals.assign(levels, 0);
-    for (uint32_t l = 0; l < levels; l++) {
-      uint32_t acc = 0, step = 1u << l;
-      for (size_t s = 0; s < segs.size(); s++) {
-        cum[size_t(l) * segs.size() + s] = acc;
-        uint32_t len = segs[s].len;
-        acc += len > step ? (len - step + 2 * step - 1) / (2 * step) : 0;
-      }
-      totals[l] = acc;
-    }
-  }
-};
-
-// results[o] = sum_w 2^(c w) W[o][w] by Horner's rule (windows of variable-base outputs).
+// results[o] = sum_w 2^(c w) W[o][w] by Horner's rule (windows of variable-base outputs),
+// one quad per output.
 struct OutItem {
   uint32_t first;     // index of window 0's result in D
   uint32_t stride;    // distance between windows' results
@@ -525,34 +608,33 @@ struct OutItem {
 
 template <class F>
 __global__ void k_combine_windows(const XYZZ<F>* D, const OutItem* outs, uint32_t nouts, XYZZ<F>* results) {
-  uint32_t o = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
   if (o >= nouts) return;
   OutItem it = outs[o];
   XYZZ<F> acc = ld_field(D + it.first + (it.nwin - 1) * it.stride);
   for (int w = (int)it.nwin - 2; w >= 0; w--) {
-    for (uint32_t i = 0; i < it.c; i++) acc = p_dbl(acc);
-    acc = p_add(acc, ld_field(D + it.first + uint32_t(w) * it.stride));
+    for (uint32_t i = 0; i < it.c; i++) acc = p_dbl_quad(acc);
+    acc = p_add_quad(acc, ld_field(D + it.first + uint32_t(w) * it.stride));
   }
-  st_field(results + o, acc);
+  if (quad_lane() == 0) st_field(results + o, acc);
 }
 
 // ------------------------------------------------------------------ driver
 struct Layout {
-  uint32_t *keys, *vals, *sorted, *counts, *offs, *cursor, *nch, *choff, *chunk_key, *max_chunks;
-  void *part, *U, *D;
+  uint32_t *keys, *vals, *sorted, *counts, *offs, *cursor, *nch, *choff, *chunk_key, *arrive;
+  void *part, *S, *D;
   MsmSeg* segs;
   MsmOut* outs;
   const void** obases;
   BitSeg* bsegs;
-  TreeSeg *useg, *dseg;
-  uint32_t *ucum, *dcum;
+  TreeSeg* dseg;
   OutItem* oitems;
-  uint32_t qmax, nbits, utotal, dtotal;
+  uint32_t qmax, nbits, nslices, dtotal, slice;
 };
 
 struct HostTables {
   std::vector<BitSeg> bsegs;
-  TreePlan ut, dt;
+  std::vector<TreeSeg> dsegs;
   std::vector<OutItem> oitems;
   std::vector<const void*> obases;
 };
@@ -566,33 +648,38 @@ struct MsmExecState {
 
 MsmExec::~MsmExec() { delete st; }
 
-static void tables(const MsmPlan& p, HostTables& h, Layout& L) {
+// Slices of bt * r buckets, r >= 2 chosen so that the slice kernel fills about one wave
+// of `wave` blocks (a lone wave's blocks each run their tree once; more buckets per
+// slice are serial sums, which the SMs run at full rate).
+static void tables(const MsmPlan& p, uint32_t bt, uint32_t wave, HostTables& h, Layout& L) {
+  uint64_t total = 0;
+  for (const auto& o : p.outs) total += uint64_t(o.win_keys) * ((o.c - 1) * (1ull << (o.c - 2)) + 1);
+  uint64_t r = (total + uint64_t(bt) * wave - 1) / (uint64_t(bt) * wave);
+  r = std::min<uint64_t>(std::max<uint64_t>(r, 2), 64);
+  const uint32_t slice = (uint32_t)(bt * r);
+  L.slice = slice;
   h.bsegs.clear();
-  h.ut = TreePlan();
-  h.dt = TreePlan();
+  h.dsegs.clear();
   h.oitems.clear();
   h.obases.clear();
-  uint32_t uoff = 0, dslot = 0;
+  uint32_t soff = 0, dslot = 0;
   for (const auto& o : p.outs) {
     const uint32_t nb = 1u << (o.c - 1);
     h.oitems.push_back({dslot, o.c, o.win_keys, o.c});
     h.obases.push_back(o.bases);
     for (uint32_t w = 0; w < o.win_keys; w++) {
-      h.dt.segs.push_back({dslot, o.c});
+      h.dsegs.push_back({dslot, o.c});
       for (uint32_t b = 0; b < o.c; b++) {
-        uint32_t cnt = (b == o.c - 1) ? 1u : (1u << (o.c - 2));
-        uint32_t pairs = (cnt + 1) / 2;
-        h.bsegs.push_back({o.key_off + w * nb, b, o.c, uoff, dslot + b});
-        h.ut.segs.push_back({uoff, pairs});
-        uoff += pairs;
+        const uint32_t cnt = (b == o.c - 1) ? 1u : (1u << (o.c - 2));
+        const uint32_t nsl = (cnt + slice - 1) / slice;
+        h.bsegs.push_back({o.key_off + w * nb, b, o.c, cnt, soff, nsl, dslot + b, 0});
+        soff += nsl;
       }
       dslot += o.c;
     }
   }
-  h.ut.finish();
-  h.dt.finish();
   L.nbits = (uint32_t)h.bsegs.size();
-  L.utotal = uoff;
+  L.nslices = soff;
   L.dtotal = dslot;
 }
 
@@ -610,19 +697,16 @@ static void layout(const MsmPlan& p, Arena& a, Layout& L, HostTables& h) {
   L.choff = a.take<uint32_t>(K + 1);
   L.qmax = (uint32_t)(S / T0 + K + 1);
   L.chunk_key = a.take<uint32_t>(L.qmax);
-  L.max_chunks = a.take<uint32_t>(1);
+  L.arrive = a.take<uint32_t>(L.qmax);
   L.part = a.take<XYZZ<F>>(L.qmax);
-  tables(p, h, L);
-  L.U = a.take<XYZZ<F>>(L.utotal);
+  tables(p, SliceBT<F>::value, SLICE_WAVE, h, L);
+  L.S = a.take<XYZZ<F>>(L.nslices);
   L.D = a.take<XYZZ<F>>(L.dtotal);
   L.segs = a.take<MsmSeg>(p.segs.size());
   L.outs = a.take<MsmOut>(p.outs.size());
   L.obases = a.take<const void*>(p.outs.size());
   L.bsegs = a.take<BitSeg>(h.bsegs.size());
-  L.useg = a.take<TreeSeg>(h.ut.segs.size());
-  L.ucum = a.take<uint32_t>(std::max<size_t>(1, h.ut.cum.size()));
-  L.dseg = a.take<TreeSeg>(h.dt.segs.size());
-  L.dcum = a.take<uint32_t>(std::max<size_t>(1, h.dt.cum.size()));
+  L.dseg = a.take<TreeSeg>(h.dsegs.size());
   L.oitems = a.take<OutItem>(h.oitems.size());
 }
 
@@ -635,18 +719,6 @@ size_t msm_workspace_bytes(const MsmPlan& p) {
   layout<F>(p, a, L, h);
   a.off += scan_u32_temp_bytes(p.keys) + scan_u32_temp_bytes(p.keys) + 256;
   return a.off;
-}
-
-template <class F>
-static int run_tree(XYZZ<F>* x, const TreePlan& t, const TreeSeg* dsegs, const uint32_t* dcum, cudaStream_t st) {
-  const uint32_t nseg = (uint32_t)t.segs.size();
-  for (uint32_t l = 0; l < t.levels; l++) {
-    uint32_t total = t.totals[l];
-    if (total == 0) continue;
-    k_tree_level<F><<<(total + 255) / 256, 256, 0, st>>>(x, dsegs, dcum + size_t(l) * nseg, nseg, total, l); ZK_COUNT_LAUNCH();
-  }
-  ZK_CUDA(cudaGetLastError());
-  return ZKVC_OK;
 }
 
 template <class F>
@@ -674,12 +746,7 @@ int msm_upload(MsmExec* ex, cudaStream_t st) {
   ZK_CUDA(cudaMemcpyAsync(L.outs, p.outs.data(), p.outs.size() * sizeof(MsmOut), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.obases, h.obases.data(), h.obases.size() * sizeof(void*), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.bsegs, h.bsegs.data(), h.bsegs.size() * sizeof(BitSeg), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.useg, h.ut.segs.data(), h.ut.segs.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
-  if (!h.ut.cum.empty())
-    ZK_CUDA(cudaMemcpyAsync(L.ucum, h.ut.cum.data(), h.ut.cum.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.dseg, h.dt.segs.data(), h.dt.segs.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
-  if (!h.dt.cum.empty())
-    ZK_CUDA(cudaMemcpyAsync(L.dcum, h.dt.cum.data(), h.dt.cum.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  ZK_CUDA(cudaMemcpyAsync(L.dseg, h.dsegs.data(), h.dsegs.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
   ZK_CUDA(cudaMemcpyAsync(L.oitems, h.oitems.data(), h.oitems.size() * sizeof(OutItem), cudaMemcpyHostToDevice, st));
   ex->st->uploaded = true;
   return ZKVC_OK;
@@ -705,7 +772,6 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   }
   // counting sort by bucket key
   ZK_CUDA(cudaMemsetAsync(L.counts, 0, size_t(K) * sizeof(uint32_t), st));
-  ZK_CUDA(cudaMemsetAsync(L.max_chunks, 0, sizeof(uint32_t), st));
   unsigned sb = (unsigned)((S + HB_TILE - 1) / HB_TILE);
   if (S > 0) {
     k_hist<<<sb, HB_THREADS, 0, st>>>(L.keys, S, L.counts); ZK_COUNT_LAUNCH();
@@ -722,7 +788,8 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   ZK_CUDA(cudaGetLastError());
   ZK_TRY(scan_u32(L.nch, L.choff, K, a, st));
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace too small for scans");
-  k_chunk_keys<<<(K + 255) / 256, 256, 0, st>>>(L.choff, K, L.chunk_key, L.max_chunks); ZK_COUNT_LAUNCH();
+  k_chunk_keys<<<(K + 255) / 256, 256, 0, st>>>(L.choff, K, L.chunk_key); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaMemsetAsync(L.arrive, 0, size_t(L.qmax) * sizeof(uint32_t), st));
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
   const uint32_t at = p.tune.accum_threads;
   unsigned qb = (L.qmax + at - 1) / at;
@@ -734,24 +801,17 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
     if (uint32_t* hu = prof_units(accum_stage)) ZK_CUDA(cudaMemcpyAsync(hu, L.offs + K, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   }
   ZK_CUDA(cudaGetLastError());
-  // fold each bucket's partials into its first slot (enough levels for the largest
-  // possible chunk count; levels beyond the actual largest exit at once)
-  uint32_t levels = 0;
-  while ((uint64_t(1) << levels) < (S + T0 - 1) / T0 + 1) levels++;
-  for (uint32_t l = 0; l < levels; l++) {
-    unsigned fb = (L.qmax + 255) / 256;
-    if (fb > p.tune.fold_blocks) fb = p.tune.fold_blocks;
-    k_fold<F><<<fb, 256, 0, st>>>(part, L.choff, L.chunk_key, K, L.max_chunks, l); ZK_COUNT_LAUNCH();
-  }
-  ZK_CUDA(cudaGetLastError());
+  k_fold_tree<F><<<(unsigned)((uint64_t(L.qmax) * FoldLanes<F>::value + 127) / 128), 128, 0, st>>>(L.choff, L.chunk_key, K, part,
+                                                                                                L.arrive); ZK_COUNT_LAUNCH();
   // sum_v v B_v per (output, window) by bit decomposition
-  XYZZ<F>* U = reinterpret_cast<XYZZ<F>*>(L.U);
+  XYZZ<F>* Sl = reinterpret_cast<XYZZ<F>*>(L.S);
   XYZZ<F>* D = reinterpret_cast<XYZZ<F>*>(L.D);
-  k_bits_first<F><<<(L.utotal + 255) / 256, 256, 0, st>>>(part, L.counts, L.choff, L.bsegs, L.nbits, L.utotal, U); ZK_COUNT_LAUNCH();
-  ZK_TRY(run_tree<F>(U, h.ut, L.useg, L.ucum, st));
-  k_bits_scale<F><<<(L.nbits + 63) / 64, 64, 0, st>>>(U, L.bsegs, L.nbits, D); ZK_COUNT_LAUNCH();
-  ZK_TRY(run_tree<F>(D, h.dt, L.dseg, L.dcum, st));
-  k_combine_windows<F><<<((uint32_t)p.outs.size() + 63) / 64, 64, 0, st>>>(D, L.oitems, (uint32_t)p.outs.size(), results); ZK_COUNT_LAUNCH();
+  k_bits_slices<F><<<L.nslices, SliceBT<F>::value, 0, st>>>(part, L.counts, L.choff, L.bsegs, L.nbits, L.slice, Sl);
+  ZK_COUNT_LAUNCH();
+  k_bits_scale<F><<<L.nbits, BITS_BT, 0, st>>>(Sl, L.bsegs, D); ZK_COUNT_LAUNCH();
+  k_bits_window<F><<<(unsigned)h.dsegs.size(), BITS_BT, 0, st>>>(D, L.dseg); ZK_COUNT_LAUNCH();
+  const uint32_t nouts = (uint32_t)p.outs.size();
+  k_combine_windows<F><<<(4 * nouts + 63) / 64, 64, 0, st>>>(D, L.oitems, nouts, results); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }

@@ -45,7 +45,6 @@ struct MsmOut {
 struct MsmTune {
   uint32_t chunk = 0;          // terms per level-0 chunk (0: 16 below 2M slots, else 32)
   uint32_t accum_threads = 128;
-  uint32_t fold_blocks = 608;  // grid cap of the fold levels (grid-stride)
 };
 
 struct MsmPlan {

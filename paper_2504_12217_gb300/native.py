@@ -504,9 +504,9 @@ def zkvc_prove(pk, X, W, rs, Y=None, workspace=None):
 # ------------------------------------------------------------------ batched proving
 ZKVC_BATCH_AUTOTUNE = 1
 ZKVC_BATCH_EAGER = 2
-ZKVC_BATCH_TUNING_LEN = 10
-TUNING_NAMES = ("small_chunk", "small_accum_threads", "small_fold_blocks", "main_chunk", "main_accum_threads",
-                "main_fold_blocks", "g2_chunk", "g2_accum_threads", "g2_fold_blocks", "ntt_log_elems_per_block")
+ZKVC_BATCH_TUNING_LEN = 7
+TUNING_NAMES = ("small_chunk", "small_accum_threads", "main_chunk", "main_accum_threads",
+                "g2_chunk", "g2_accum_threads", "ntt_log_elems_per_block")
 
 
 def zkvc_set_wait_timeout_ms(ms):

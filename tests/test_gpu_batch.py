@@ -98,13 +98,13 @@ def test_batch_set_tuning_and_one_shot(nv, small_keys):
     rs = [inputs.to_bytes32(r) for _, _, r in insts]
     expect = [p for p, _ in _oracle_proofs(small_keys, SMALL, insts)]
     batch = nv.Batch(pks)
-    for tuning in ([64, 64, 304, 8, 256, 1216, 32, 64, 304, 11], [8, 256, 1216, 64, 64, 304, 8, 128, 608, 9]):
+    for tuning in ([64, 64, 8, 256, 32, 64, 11], [8, 256, 64, 64, 8, 128, 9]):
         batch.set_tuning(tuning)
         assert list(batch.get_tuning().values()) == tuning
         proofs, _ = batch.prove(Xs, Ws, rs)
         assert proofs == expect
     with pytest.raises(nv.ZkvcError):
-        batch.set_tuning([4, 128, 608, 16, 128, 608, 8, 128, 608, 10])  # chunk below the sized minimum
+        batch.set_tuning([4, 128, 16, 128, 8, 128, 10])  # chunk below the sized minimum
     proofs, _ = nv.zkvc_prove_batch(pks, Xs, Ws, rs)
     assert proofs == expect
 
