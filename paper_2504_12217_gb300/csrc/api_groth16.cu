@@ -153,28 +153,30 @@ int zkvc_setup_circuit(int a, int n, int b, int circuit, int public_io, const ui
 }
 
 int zkvc_pk_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t rs[64], void* stream,
-                     uint32_t chunks[4]) {
+                     uint32_t tuning[ZKVC_PK_TUNING_LEN]) {
   set_error("%s", "");
   ZK_CHECK(pk && dX && dW && rs, ZKVC_EINVAL, "autotune: null argument");
   ZK_CHECK(!pk->gen, ZKVC_EINVAL, "autotune: keys of zkvc_setup_circuit are not tuned");
   ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN, ZKVC_EINVAL, "autotune: mode %d", mode);
   ZK_TRY(device_guard(pk->device));
-  return prove_autotune(pk, mode, dX, dW, rs, (cudaStream_t)stream, chunks);
+  return prove_autotune(pk, mode, dX, dW, rs, (cudaStream_t)stream, tuning);
 }
 
-int zkvc_pk_set_chunks(zkvc_pk* pk, const uint32_t chunks[4]) {
+int zkvc_pk_set_tuning(zkvc_pk* pk, const uint32_t tuning[ZKVC_PK_TUNING_LEN]) {
   set_error("%s", "");
-  ZK_CHECK(pk && chunks, ZKVC_EINVAL, "set_chunks: null argument");
+  ZK_CHECK(pk && tuning, ZKVC_EINVAL, "set_tuning: null argument");
   for (int i = 0; i < 4; i++)
-    ZK_CHECK(chunks[i] <= 1024, ZKVC_EINVAL, "set_chunks: chunk %u above 1024", chunks[i]);
-  for (int i = 0; i < 4; i++) pk->prove_chunk[i] = chunks[i];
+    ZK_CHECK(tuning[i] <= 1024, ZKVC_EINVAL, "set_tuning: chunk %u above 1024", tuning[i]);
+  ZK_CHECK(tuning[4] == 0 || (tuning[4] >= 8 && tuning[4] <= 11), ZKVC_EINVAL,
+           "set_tuning: 2^%u NTT elements per block outside [2^8, 2^11]", tuning[4]);
+  for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = tuning[i];
   return ZKVC_OK;
 }
 
-int zkvc_pk_get_chunks(const zkvc_pk* pk, uint32_t chunks[4]) {
+int zkvc_pk_get_tuning(const zkvc_pk* pk, uint32_t tuning[ZKVC_PK_TUNING_LEN]) {
   set_error("%s", "");
-  ZK_CHECK(pk && chunks, ZKVC_EINVAL, "get_chunks: null argument");
-  for (int i = 0; i < 4; i++) chunks[i] = pk->prove_chunk[i];
+  ZK_CHECK(pk && tuning, ZKVC_EINVAL, "get_tuning: null argument");
+  for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) tuning[i] = pk->prove_tune[i];
   return ZKVC_OK;
 }
 

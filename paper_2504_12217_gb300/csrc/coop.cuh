@@ -95,6 +95,34 @@ __device__ __forceinline__ XYZZ<F> p_add_quad_body(const XYZZ<F>& p, const XYZZ<
   return {X3, Y3, ZZ3, ZZZ3};
 }
 
+// madd-2008-s (XYZZ + affine) in four product rounds:
+//   (U2 = X2 ZZ1, S2 = Y2 ZZZ1)  ->  (PP = P^2, R^2)  ->  (PPP = P PP, Q = X1 PP, ZZ3 = ZZ1 PP)
+//   ->  (R (Q - X3), Y1 PPP, ZZZ3 = ZZZ1 PPP)
+template <class F>
+__device__ __forceinline__ XYZZ<F> p_add_affine_quad_body(const XYZZ<F>& p, const Affine<F>& q) {
+  if (q.is_inf()) return p;
+  if (p.is_inf()) return XYZZ<F>::from_affine(q);
+  F m = f_mulx(quad_pick(q.x, q.y, q.x, q.y), quad_pick(p.ZZ, p.ZZZ, p.ZZ, p.ZZZ));
+  const F P = f_sub(quad_bcast(m, 0), p.X), R = f_sub(quad_bcast(m, 1), p.Y);
+  if (P.is_zero()) {
+    if (R.is_zero()) return p_dbl_affine(q);  // rare: every lane doubles alone
+    return XYZZ<F>::inf();
+  }
+  m = f_mulx(quad_pick(P, R, P, R), quad_pick(P, R, P, R));
+  const F PP = quad_bcast(m, 0), RR = quad_bcast(m, 1);
+  m = f_mulx(quad_pick(P, p.X, p.ZZ, P), PP);
+  const F PPP = quad_bcast(m, 0), Q = quad_bcast(m, 1), ZZ3 = quad_bcast(m, 2);
+  const F X3 = f_sub(f_sub(RR, PPP), f_dbl(Q));
+  const F QX = f_sub(Q, X3);
+  m = f_mulx(quad_pick(R, p.Y, p.ZZZ, R), quad_pick(QX, PPP, PPP, QX));
+  const F Y3 = f_sub(quad_bcast(m, 0), quad_bcast(m, 1));
+  const F ZZZ3 = quad_bcast(m, 2);
+  return {X3, Y3, ZZ3, ZZZ3};
+}
+
+static __device__ __noinline__ G2J p_add_affine_quad_g2(G2J p, G2A q) { return p_add_affine_quad_body(p, q); }
+__device__ __forceinline__ G2J p_add_affine_quad(const G2J& p, const G2A& q) { return p_add_affine_quad_g2(p, q); }
+
 static __device__ __noinline__ G1J p_dbl_quad_g1(G1J p) { return p_dbl_quad_body(p); }
 static __device__ __noinline__ G2J p_dbl_quad_g2(G2J p) { return p_dbl_quad_body(p); }
 static __device__ __noinline__ G1J p_add_quad_g1(G1J p, G1J q) { return p_add_quad_body(p, q); }

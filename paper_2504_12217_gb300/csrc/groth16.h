@@ -97,9 +97,10 @@ struct zkvc_pk {
   zkvc::Fr* zB = nullptr;    // z^j, j < b
   const zkvc::NttDomain* dom = nullptr;
   zkvc::GenericKey* gen = nullptr;  // set for keys of zkvc_setup_circuit (generic R1CS layout)
-  // terms per level-0 chunk of the one-proof prover's MSM runs (small, rest, h, g2;
-  // 0 = the default rule), chosen by zkvc_pk_autotune
-  uint32_t prove_chunk[4] = {0, 0, 0, 0};
+  // launch shape of the one-proof prover, chosen by zkvc_pk_autotune: terms per level-0
+  // chunk of the MSM runs (small, rest, h, g2; 0 = the default rule), then log2 of the
+  // NTT elements per block (0 = 10)
+  uint32_t prove_tune[5] = {0, 0, 0, 0, 0};
 };
 
 struct zkvc_vk {

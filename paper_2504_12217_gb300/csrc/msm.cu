@@ -369,6 +369,14 @@ __global__ void k_chunk_keys(const uint32_t* __restrict__ choff, uint32_t K, uin
   for (uint32_t q = a; q < b; q++) chunk_key[q] = k;
 }
 
+// fetch-and-add with release (this thread's earlier stores) and acquire (its later
+// loads) semantics at GPU scope
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // point loads that bypass L1: a sibling's partial sum written by another SM
 template <class F>
 __device__ __forceinline__ XYZZ<F> ld_point_cg(const XYZZ<F>* p) {
@@ -386,6 +394,18 @@ __device__ __forceinline__ XYZZ<F> ld_point_cg(const XYZZ<F>* p) {
   return r;
 }
 
+// Lanes per chunk: G2 point formulas are long enough that a quad of lanes per chunk
+// (coop.cuh) pays in the latency-bound G2 runs of a proof; G1 chunks get one thread.
+template <class F>
+struct ChunkLanes {
+  static constexpr int value = sizeof(F) > 32 ? 4 : 1;
+};
+
+__device__ __forceinline__ XYZZ<Fp> madd_lanes(const XYZZ<Fp>& p, const Affine<Fp>& q) { return p_add_affine(p, q); }
+__device__ __forceinline__ XYZZ<Fp2> madd_lanes(const XYZZ<Fp2>& p, const Affine<Fp2>& q) {
+  return p_add_affine_quad(p, q);
+}
+
 // level 0: chunk q sums up to T0 consecutive terms of its bucket (mixed additions)
 template <class F>
 __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ offs,
@@ -393,8 +413,9 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
                                                 uint32_t K, uint32_t T0, const Affine<F>* __restrict__ bases,
                                                 const Affine<F>* const* __restrict__ obases, int key_shift,
                                                 XYZZ<F>* part) {
-  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= choff[K]) return;
+  constexpr int QL = ChunkLanes<F>::value;
+  uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
+  if (q >= choff[K]) return;  // uniform within a quad
   uint32_t k = chunk_key[q];
   uint32_t j = q - choff[k];
   uint32_t start = offs[k] + j * T0;
@@ -405,9 +426,9 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
     uint32_t v = sorted[p];
     Affine<F> P = ld_field(bases + (v & 0x7fffffffu));
     if (v >> 31) P.y = f_neg(P.y);
-    acc = p_add_affine(acc, P);
+    acc = madd_lanes(acc, P);
   }
-  st_field(part + q, acc);
+  if (QL == 1 || quad_lane() == 0) st_field(part + q, acc);
 }
 
 // The chunk sums of each bucket are added along the binary tree over chunk positions
@@ -418,18 +439,13 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
 // with no right sibling climbs without waiting.  A subtree's sum sits at its left
 // position: a climber stores only sums it has changed (a chunk's own sum is there from
 // the accumulation launch).  The bucket total ends in part[choff[k]].  `arrive` holds one
-// zeroed counter per chunk.  G2 chunks get a quad of lanes each (the additions' latency
-// sets the depth of this tree; coop.cuh), G1 chunks one thread.
-template <class F>
-struct FoldLanes {
-  static constexpr int value = sizeof(F) > 32 ? 4 : 1;
-};
-
+// zeroed counter per chunk.  The counter's fetch-and-add releases the climber's store
+// and acquires its sibling's.  G2 chunks get a quad of lanes each, G1 chunks one thread.
 template <class F>
 __global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ choff,
                                                    const uint32_t* __restrict__ chunk_key, uint32_t K,
                                                    XYZZ<F>* part, uint32_t* arrive) {
-  constexpr int QL = FoldLanes<F>::value;
+  constexpr int QL = ChunkLanes<F>::value;
   const uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
   if (q >= choff[K]) return;  // uniform within a quad
   const bool lead = QL == 1 || quad_lane() == 0;
@@ -444,12 +460,8 @@ __global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ 
     if (left && sib >= np) continue;
     uint32_t first = 0;
     if (lead) {
-      if (have) {
-        st_field(part + base + pos, acc);
-        __threadfence();
-      }
-      first = atomicAdd(arrive + base + (left ? pos : sib) + span - 1, 1u) == 0;
-      __threadfence();
+      if (have) st_field(part + base + pos, acc);
+      first = atom_add_acq_rel(arrive + base + (left ? pos : sib) + span - 1, 1u) == 0;
     }
     if (QL > 1) {
       first = __shfl_sync(quad_mask(), first, quad_base());
@@ -476,42 +488,56 @@ __device__ __forceinline__ XYZZ<F> bucket_at(const XYZZ<F>* fin, const uint32_t*
 }
 
 // Sum of m points get(0..m-1) by a block of BT threads (a multiple of 4), returned to
-// every thread; sh holds BT points.  Levels with more pairs than quads give a pair to a
-// thread, the others a pair to a quad (coop.cuh).  Every thread of the block must call it.
+// every thread; sh holds BT points.  G1 levels with more pairs than quads give a pair to
+// a thread, the others a pair (or several in turn) to a quad (coop.cuh); G2 levels always
+// use quads.  Every thread of the block must call it.
 template <class F, int BT, class Get>
 __device__ XYZZ<F> block_sum(Get get, uint32_t m, XYZZ<F>* sh) {
+  constexpr bool all_quads = sizeof(F) > 32;
+  constexpr uint32_t NQ = BT / 4;
   const uint32_t t = threadIdx.x, qd = t >> 2;
   const bool lead = (t & 3) == 0;
   uint32_t n;
   if (m > 2 * BT) {
-    XYZZ<F> acc = XYZZ<F>::inf();
-    for (uint32_t i = t; i < m; i += BT) acc = p_add(acc, get(i));
-    st_field(sh + t, acc);
-    n = BT;
+    if (all_quads) {
+      XYZZ<F> acc = XYZZ<F>::inf();
+      for (uint32_t i = qd; i < m; i += NQ) acc = p_add_quad(acc, get(i));
+      if (lead) st_field(sh + qd, acc);
+      n = NQ;
+    } else {
+      XYZZ<F> acc = XYZZ<F>::inf();
+      for (uint32_t i = t; i < m; i += BT) acc = p_add(acc, get(i));
+      st_field(sh + t, acc);
+      n = BT;
+    }
   } else {
     const uint32_t pairs = (m + 1) / 2;
-    if (pairs > BT / 4) {
+    if (!all_quads && pairs > NQ) {
       if (t < pairs) {
         XYZZ<F> a = get(2 * t);
         if (2 * t + 1 < m) a = p_add(a, get(2 * t + 1));
         st_field(sh + t, a);
       }
-    } else if (qd < pairs) {
-      XYZZ<F> a = get(2 * qd);
-      if (2 * qd + 1 < m) a = p_add_quad(a, get(2 * qd + 1));
-      if (lead) st_field(sh + qd, a);
+    } else {
+      for (uint32_t pr = qd; pr < pairs; pr += NQ) {
+        XYZZ<F> a = get(2 * pr);
+        if (2 * pr + 1 < m) a = p_add_quad(a, get(2 * pr + 1));
+        if (lead) st_field(sh + pr, a);
+      }
     }
     n = pairs;
   }
   __syncthreads();
   while (n > 1) {
     const uint32_t h = (n + 1) / 2, pairs = n - h;  // entry i < pairs absorbs entry i + h
-    if (pairs > BT / 4) {
+    if (!all_quads && pairs > NQ) {
       if (t < pairs) st_field(sh + t, p_add(ld_field(sh + t), ld_field(sh + t + h)));
-    } else if (qd < pairs) {
-      const XYZZ<F> r = p_add_quad(ld_field(sh + qd), ld_field(sh + qd + h));
-      __syncwarp(quad_mask());  // the quad's reads of sh[qd] precede the lead's store
-      if (lead) st_field(sh + qd, r);
+    } else {
+      for (uint32_t pr = qd; pr < pairs; pr += NQ) {
+        const XYZZ<F> r = p_add_quad(ld_field(sh + pr), ld_field(sh + pr + h));
+        __syncwarp(quad_mask());  // the quad's reads of sh[pr] precede the lead's store
+        if (lead) st_field(sh + pr, r);
+      }
     }
     __syncthreads();
     n = h;
@@ -792,7 +818,7 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   ZK_CUDA(cudaMemsetAsync(L.arrive, 0, size_t(L.qmax) * sizeof(uint32_t), st));
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
   const uint32_t at = p.tune.accum_threads;
-  unsigned qb = (L.qmax + at - 1) / at;
+  unsigned qb = (unsigned)((uint64_t(L.qmax) * ChunkLanes<F>::value + at - 1) / at);
   if (accum_stage >= 0) prof_mark(accum_stage, true, st);
   k_accum0<F><<<qb, at, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases,
                                  reinterpret_cast<const Affine<F>* const*>(L.obases), p.key_shift, part); ZK_COUNT_LAUNCH();
@@ -801,8 +827,9 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
     if (uint32_t* hu = prof_units(accum_stage)) ZK_CUDA(cudaMemcpyAsync(hu, L.offs + K, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   }
   ZK_CUDA(cudaGetLastError());
-  k_fold_tree<F><<<(unsigned)((uint64_t(L.qmax) * FoldLanes<F>::value + 127) / 128), 128, 0, st>>>(L.choff, L.chunk_key, K, part,
-                                                                                                L.arrive); ZK_COUNT_LAUNCH();
+  k_fold_tree<F><<<(unsigned)((uint64_t(L.qmax) * ChunkLanes<F>::value + 127) / 128), 128, 0, st>>>(L.choff, L.chunk_key, K,
+                                                                                                 part, L.arrive);
+  ZK_COUNT_LAUNCH();
   // sum_v v B_v per (output, window) by bit decomposition
   XYZZ<F>* Sl = reinterpret_cast<XYZZ<F>*>(L.S);
   XYZZ<F>* D = reinterpret_cast<XYZZ<F>*>(L.D);

@@ -217,10 +217,10 @@ static void plans(const zkvc_pk* pk, int mode, const int8_t* dX, const int32_t* 
       seg_of(g2[R2_BETA], 0, 1, 0, SK_ONE, nullptr),
       seg_of(g2[R2_DELTA], 0, 1, 0, SK_FR_CANON, rs + 1),
   };
-  P->small.tune.chunk = pk->prove_chunk[0];
-  P->rest.tune.chunk = pk->prove_chunk[1];
-  P->h.tune.chunk = pk->prove_chunk[2];
-  P->g2.tune.chunk = pk->prove_chunk[3];
+  P->small.tune.chunk = pk->prove_tune[0];
+  P->rest.tune.chunk = pk->prove_tune[1];
+  P->h.tune.chunk = pk->prove_tune[2];
+  P->g2.tune.chunk = pk->prove_tune[3];
   if (!chain) msm_plan_finalize(P->rest);
   msm_plan_finalize(P->small);
   msm_plan_finalize(P->h);
@@ -376,10 +376,11 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   cudaStream_t s3 = side->st[3];
   prof_mark(PS_NTT, true, s3);
   const NttDomain* d = pk->dom;
-  ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, s3));
-  ZK_TRY(ntt_dit(Aev, 3, N, d, false, s3));
+  const int elog = pk->prove_tune[4] ? (int)pk->prove_tune[4] : 10;
+  ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, s3, elog));
+  ZK_TRY(ntt_dit(Aev, 3, N, d, false, s3, elog));
   ZK_TRY(ntt_quotient(Aev, Bev, Cev, Hev, d, s3));
-  ZK_TRY(ntt_dif(Hev, 1, N, d, true, SC_NONE, SC_NGI, false, s3));
+  ZK_TRY(ntt_dif(Hev, 1, N, d, true, SC_NONE, SC_NGI, false, s3, elog));
   k_check_h<<<1, 32, 0, s3>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_NTT, false, s3);
@@ -430,10 +431,12 @@ int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, 
 int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, cudaStream_t st,
                    uint32_t* chosen) {
   static const uint32_t kCand[] = {2, 4, 8, 16, 32, 64};
-  const uint32_t saved[4] = {pk->prove_chunk[0], pk->prove_chunk[1], pk->prove_chunk[2], pk->prove_chunk[3]};
-  for (int i = 0; i < 4; i++) pk->prove_chunk[i] = 2;  // the largest workspace of all candidates
+  static const uint32_t kElog[] = {8, 9, 10, 11};
+  uint32_t saved[5];
+  for (int i = 0; i < 5; i++) saved[i] = pk->prove_tune[i];
+  for (int i = 0; i < 4; i++) pk->prove_tune[i] = 2;  // the largest workspace of all candidates
   size_t need = prove_workspace_bytes(pk, mode);
-  for (int i = 0; i < 4; i++) pk->prove_chunk[i] = saved[i];
+  for (int i = 0; i < 4; i++) pk->prove_tune[i] = saved[i];
   void* ws = nullptr;
   int32_t* dY = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -472,12 +475,15 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
   float best_ms = 0;
   rc = measure(&best_ms);
   const int order[4] = {3, 0, 2, 1};  // g2, small, h, rest
-  for (int oi = 0; oi < 4 && rc == ZKVC_OK; oi++) {
-    const int r = order[oi];
-    uint32_t best = pk->prove_chunk[r];
-    for (uint32_t c : kCand) {
-      if (c == best) continue;
-      pk->prove_chunk[r] = c;
+  for (int oi = 0; oi < 5 && rc == ZKVC_OK; oi++) {
+    const int r = oi < 4 ? order[oi] : 4;  // then the NTT block
+    const uint32_t* cand = r < 4 ? kCand : kElog;
+    const int ncand = r < 4 ? 6 : 4;
+    uint32_t best = pk->prove_tune[r];
+    for (int ci = 0; ci < ncand; ci++) {
+      const uint32_t c = cand[ci];
+      if (c == best || (r == 4 && best == 0 && c == 10)) continue;
+      pk->prove_tune[r] = c;
       float ms = 0;
       if ((rc = measure(&ms)) != ZKVC_OK) break;
       if (ms < best_ms) {
@@ -485,15 +491,15 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
         best = c;
       }
     }
-    pk->prove_chunk[r] = best;
+    pk->prove_tune[r] = best;
   }
   cleanup();
   if (rc != ZKVC_OK) {
-    for (int i = 0; i < 4; i++) pk->prove_chunk[i] = saved[i];
+    for (int i = 0; i < 5; i++) pk->prove_tune[i] = saved[i];
     return rc;
   }
   if (chosen)
-    for (int i = 0; i < 4; i++) chosen[i] = pk->prove_chunk[i];
+    for (int i = 0; i < 5; i++) chosen[i] = pk->prove_tune[i];
   return ZKVC_OK;
 }
 

@@ -66,8 +66,8 @@ SIGNATURES = {
     "zkvc_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_prove_workspace_bytes_mode": (_c_sz, [_c_p, _c_int]),
     "zkvc_pk_autotune": (_c_int, [_c_p, _c_int, _c_p, _c_p, _c_p, _c_p, _c_p]),
-    "zkvc_pk_set_chunks": (_c_int, [_c_p, _c_p]),
-    "zkvc_pk_get_chunks": (_c_int, [_c_p, _c_p]),
+    "zkvc_pk_set_tuning": (_c_int, [_c_p, _c_p]),
+    "zkvc_pk_get_tuning": (_c_int, [_c_p, _c_p]),
     "zkvc_setup_circuit": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _c_p, _c_p, ctypes.POINTER(_c_p),
                                     ctypes.POINTER(_c_p)]),
     "zkvc_pk_circuit": (_c_int, [_c_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_uint64),
@@ -436,23 +436,26 @@ ZKVC_PROVE_FOLD = 0
 ZKVC_PROVE_CHAIN = 1
 
 
+ZKVC_PK_TUNING_LEN = 5
+
+
 def zkvc_pk_autotune(pk, X, W, rs, mode=0):
-    """Tune the key's MSM chunk sizes for one-proof latency on these inputs; returns the
-    chosen [small, rest, h, g2] chunks."""
-    arr = (ctypes.c_uint32 * 4)()
+    """Tune the key's launch shape for one-proof latency on these inputs; returns the
+    chosen [small, rest, h, g2 chunk terms, NTT log2 elements per block]."""
+    arr = (ctypes.c_uint32 * ZKVC_PK_TUNING_LEN)()
     rsb = ctypes.create_string_buffer(bytes(rs), 64)
     check(lib().zkvc_pk_autotune(pk.handle, mode, _dev_ptr(X), _dev_ptr(W), rsb, _stream(), arr))
     return list(arr)
 
 
-def zkvc_pk_set_chunks(pk, chunks):
-    arr = (ctypes.c_uint32 * 4)(*chunks)
-    check(lib().zkvc_pk_set_chunks(pk.handle, arr))
+def zkvc_pk_set_tuning(pk, tuning):
+    arr = (ctypes.c_uint32 * ZKVC_PK_TUNING_LEN)(*tuning)
+    check(lib().zkvc_pk_set_tuning(pk.handle, arr))
 
 
-def zkvc_pk_get_chunks(pk):
-    arr = (ctypes.c_uint32 * 4)()
-    check(lib().zkvc_pk_get_chunks(pk.handle, arr))
+def zkvc_pk_get_tuning(pk):
+    arr = (ctypes.c_uint32 * ZKVC_PK_TUNING_LEN)()
+    check(lib().zkvc_pk_get_tuning(pk.handle, arr))
     return list(arr)
 
 

@@ -184,9 +184,9 @@ def test_verifier_accepts_config2_gpu_proof(nv):
     assert not nv.zkvc_verify(vk, inst["X"], Y, bad)
 
 
-def test_autotuned_and_imposed_chunks_prove_same_bytes(nv):
-    """Chunk sizes change only the launch shape: autotuned, imposed and default settings
-    give the same proof, in both prover modes."""
+def test_autotuned_and_imposed_tuning_prove_same_bytes(nv):
+    """Chunk sizes and NTT blocks change only the launch shape: autotuned, imposed and
+    default settings give the same proof, in both prover modes."""
     import torch
     a, n, b = 5, 40, 33
     inst = inputs.instance(555, (a, n, b))
@@ -195,13 +195,14 @@ def test_autotuned_and_imposed_chunks_prove_same_bytes(nv):
     rs = inputs.to_bytes32(inst["rs"])
     p0, _ = nv.zkvc_prove(pk, Xd, Wd, rs)
     chosen = nv.zkvc_pk_autotune(pk, Xd, Wd, rs)
-    assert all(c in (0, 2, 4, 8, 16, 32, 64) for c in chosen)
-    assert nv.zkvc_pk_get_chunks(pk) == chosen
+    assert all(c in (0, 2, 4, 8, 16, 32, 64) for c in chosen[:4]) and chosen[4] in (0, 8, 9, 11)
+    assert nv.zkvc_pk_get_tuning(pk) == chosen
     assert nv.zkvc_prove(pk, Xd, Wd, rs)[0] == p0
-    for chunks in ([2, 2, 2, 2], [64, 1, 3, 7]):
-        nv.zkvc_pk_set_chunks(pk, chunks)
-        assert nv.zkvc_pk_get_chunks(pk) == chunks
+    for tuning in ([2, 2, 2, 2, 8], [64, 1, 3, 7, 11], [0, 0, 0, 0, 9]):
+        nv.zkvc_pk_set_tuning(pk, tuning)
+        assert nv.zkvc_pk_get_tuning(pk) == tuning
         assert nv.zkvc_prove(pk, Xd, Wd, rs)[0] == p0
         assert nv.zkvc_prove_mode(pk, nv.ZKVC_PROVE_CHAIN, Xd, Wd, rs)[0] == p0
-    with pytest.raises(nv.ZkvcError):
-        nv.zkvc_pk_set_chunks(pk, [2048, 0, 0, 0])
+    for bad in ([2048, 0, 0, 0, 0], [0, 0, 0, 0, 7], [0, 0, 0, 0, 12]):
+        with pytest.raises(nv.ZkvcError):
+            nv.zkvc_pk_set_tuning(pk, bad)
