@@ -77,6 +77,17 @@ int zkvc_fr_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n
 int zkvc_fp_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream);
 int zkvc_fp2_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream);
 
+/* ------------------------------------------------------------------ witness matmul
+ * Y = X W for int8 X (a x n, row-major) and W (n x b, row-major) into int32 Y (a x b,
+ * row-major), exactly -- the matrix product whose correctness zkVC proves (Sec. II) and
+ * the first step of the prover's witness.  It runs on the tensor cores (tcgen05, bf16
+ * operands, fp32 accumulation in passes of 256 products, each pass exact) and returns
+ * when Y is written (synchronises `stream`).  All pointers are device memory owned by
+ * the caller.  ZKVC_EINVAL for a null pointer or a shape below 1; ZKVC_ETIMEOUT if a
+ * tensor-core wait ran out (Y is then not written).
+ */
+int zkvc_matmul_i8(const int8_t* d_X, const int8_t* d_W, int32_t* d_Y, int a, int n, int b, void* stream);
+
 /* ------------------------------------------------------------------ NTT over Fr
  * In-place transform of N = 2^log_n canonical Fr elements in natural order
  * (1 <= log_n <= 28), over the domain H = <omega_N>, omega_N = 5^((r-1)/2^28)^(2^28/N),

@@ -292,6 +292,27 @@ int zkvc_ntt(uint8_t* d_data, uint32_t log_n, int kind, void* stream) {
   return ZKVC_OK;
 }
 
+int zkvc_matmul_i8(const int8_t* d_X, const int8_t* d_W, int32_t* d_Y, int a, int n, int b, void* stream) {
+  clear_error();
+  ZK_CHECK(d_X && d_W && d_Y, ZKVC_EINVAL, "matmul: null pointer");
+  static thread_local int* t_flag = nullptr;
+  static thread_local int t_dev = -1;
+  int dev = 0;
+  ZK_CUDA(cudaGetDevice(&dev));
+  if (!t_flag || t_dev != dev) {
+    ZK_CUDA(cudaMalloc(&t_flag, sizeof(int)));
+    t_dev = dev;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ZK_CUDA(cudaMemsetAsync(t_flag, 0, sizeof(int), st));
+  ZK_TRY(matmul_i8(d_X, d_W, d_Y, a, n, b, t_flag, st));
+  int h = 0;
+  ZK_CUDA(cudaMemcpyAsync(&h, t_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ZK_TRY(wait_stream(st, "matmul"));
+  ZK_CHECK(!(h & 8), ZKVC_ETIMEOUT, "matmul: a tensor-core wait timed out");
+  return ZKVC_OK;
+}
+
 size_t zkvc_msm_workspace_bytes(size_t n, int group) {
   if (n == 0) return 0;
   return group == 2 ? msm_api_ws<Fp2>(n) : msm_api_ws<Fp>(n);

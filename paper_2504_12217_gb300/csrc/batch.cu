@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "groth16.h"
+#include "matmul_tc.cuh"
 #include "msm.h"
 #include "witness.cuh"
 
@@ -65,11 +66,13 @@ __global__ void k_b_randomness(const BInst* __restrict__ I, int count) {
   st_field(in.nrs, f_neg(f_mul(f_to_mont(r), s)));  // (r R) s / R = r s, negated mod r
 }
 
-__global__ void k_b_matmul(const BInst* __restrict__ I) {
+// the witness matmul of every instance on the tensor cores (matmul_tc.cuh)
+__global__ void __launch_bounds__(MM_THREADS) k_b_matmul(const BInst* __restrict__ I) {
+  __shared__ MatmulSmem sm;
   const BInst& in = I[blockIdx.z];
   const int a = in.a, b = in.b;
-  if ((int)blockIdx.x * 32 >= b || (int)blockIdx.y * 32 >= a) return;  // uniform per block
-  matmul_tile(in.X, in.W, in.Y, a, in.n, b, blockIdx.x, blockIdx.y);
+  if ((int)blockIdx.x * MM_M >= b || (int)blockIdx.y * MM_N >= a) return;  // uniform per block
+  matmul_tc_tile(in.X, in.W, in.Y, a, in.n, b, blockIdx.x * MM_M, blockIdx.y * MM_N, sm, in.flags);
 }
 
 __global__ void __launch_bounds__(256) k_b_crpc_ab(const BInst* __restrict__ I) {
@@ -410,7 +413,8 @@ static int enqueue(zkvc_batch* B) {
   k_b_randomness<<<(n + 63) / 64, 64, 0, st>>>(B->dinst, n); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   // witness
-  k_b_matmul<<<dim3((maxb + 31) / 32, (maxa + 31) / 32, n), dim3(32, 8), 0, st>>>(B->dinst); ZK_COUNT_LAUNCH();
+  k_b_matmul<<<dim3((maxb + MM_M - 1) / MM_M, (maxa + MM_N - 1) / MM_N, n), MM_THREADS, 0, st>>>(B->dinst);
+  ZK_COUNT_LAUNCH();
   k_b_crpc_ab<<<dim3(maxn, n), 256, 0, st>>>(B->dinst); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   // G2 run on side stream 0 (needs b_k and s)
@@ -663,7 +667,7 @@ static int batch_prove(zkvc_batch* B, const int8_t* const* dX, const int8_t* con
   int first_bad = -1, first_flag = 0;
   for (int i = 0; i < n; i++) {
     int f = B->h_flags[i];
-    int code = (f & 4) ? ZKVC_EINVAL : (f & 3) ? ZKVC_EUNSAT : ZKVC_OK;
+    int code = (f & 4) ? ZKVC_EINVAL : (f & 8) ? ZKVC_ETIMEOUT : (f & 3) ? ZKVC_EUNSAT : ZKVC_OK;
     if (status) status[i] = code;
     if (code != ZKVC_OK && first_bad < 0) {
       first_bad = i;
@@ -671,6 +675,8 @@ static int batch_prove(zkvc_batch* B, const int8_t* const* dX, const int8_t* con
     }
   }
   ZK_CHECK(first_bad < 0 || !(first_flag & 4), ZKVC_EINVAL, "batch prove: instance %d: r or s is not a canonical Fr element",
+           first_bad);
+  ZK_CHECK(first_bad < 0 || !(first_flag & 8), ZKVC_ETIMEOUT, "batch prove: instance %d: a tensor-core wait timed out",
            first_bad);
   ZK_CHECK(first_bad < 0, ZKVC_EUNSAT, "batch prove: instance %d does not satisfy its constraints (flags %d)", first_bad,
            first_flag);

@@ -31,7 +31,6 @@
 namespace zkvc {
 
 // kernels of the specialised prover reused here (defined in prove.cu)
-__global__ void k_matmul_i8(const int8_t* X, const int8_t* W, int32_t* Y, int a, int n, int b);
 __global__ void k_crpc_ab(const int8_t* X, const int8_t* W, const Fr* zA, const Fr* zB, int a, int n, int b, Fr* ak,
                           Fr* bk);
 __global__ void k_crpc_y(const int32_t* Y, const Fr* zA, const Fr* zB, int b, Fr* part);
@@ -835,8 +834,7 @@ int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const u
   ZK_CUDA(cudaMemcpyAsync(B.rs, rs_host, 64, cudaMemcpyHostToDevice, st));
   k_randomness<<<1, 1, 0, st>>>(B.rs, B.flags); ZK_COUNT_LAUNCH();
   // witness: Y, then the auxiliary variables
-  dim3 mg((sh.b + 31) / 32, (sh.a + 31) / 32);
-  k_matmul_i8<<<mg, dim3(32, 8), 0, st>>>(dX, dW, dY, sh.a, sh.n, sh.b); ZK_COUNT_LAUNCH();
+  ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
   switch (sh.circuit) {
     case ZKVC_CIRCUIT_CRPC_PSQ:
     case ZKVC_CIRCUIT_CRPC:

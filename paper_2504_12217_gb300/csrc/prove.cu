@@ -32,11 +32,6 @@
 namespace zkvc {
 
 // ------------------------------------------------------------------ witness
-__global__ void k_matmul_i8(const int8_t* __restrict__ X, const int8_t* __restrict__ W, int32_t* __restrict__ Y,
-                            int a, int n, int b) {
-  matmul_tile(X, W, Y, a, n, b, blockIdx.x, blockIdx.y);
-}
-
 // block k < n: a_k and b_k
 __global__ void __launch_bounds__(256) k_crpc_ab(const int8_t* __restrict__ X, const int8_t* __restrict__ W,
                                                  const Fr* __restrict__ zA, const Fr* __restrict__ zB, int a, int n, int b,
@@ -331,9 +326,8 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   ZK_TRY(side_streams(&side));
   Plans P;
   plans(pk, mode, dX, dY, B.ak, B.bk, B.S, Hev, B.rs, B.sw, B.sa, B.rb, &P);
-  // 1. Y = X W;  2. the CRPC sums a_k, b_k
-  dim3 mg((sh.b + 31) / 32, (sh.a + 31) / 32);
-  k_matmul_i8<<<mg, dim3(32, 8), 0, st>>>(dX, dW, dY, sh.a, sh.n, sh.b); ZK_COUNT_LAUNCH();
+  // 1. Y = X W (tensor cores);  2. the CRPC sums a_k, b_k
+  ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
   k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   // G2 MSM on side stream 0: it needs b_k and s
@@ -410,6 +404,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
 // Status of a finished proof from its device flags.
 int prove_status(int flags) {
   ZK_CHECK(!(flags & 4), ZKVC_EINVAL, "prove: r or s is not a canonical Fr element");
+  ZK_CHECK(!(flags & 8), ZKVC_ETIMEOUT, "prove: a tensor-core wait of the witness matmul timed out");
   ZK_CHECK(!(flags & 1), ZKVC_EUNSAT, "prove: the PSQ chain does not close against Y(z)");
   ZK_CHECK(!(flags & 2), ZKVC_EUNSAT, "prove: the quotient has degree N - 1 (QAP not satisfied)");
   return ZKVC_OK;

@@ -10,37 +10,6 @@
 
 namespace zkvc {
 
-// One 32 x 32 output tile of Y = X W (int8 x int8 -> int32 exactly), 32 x 8 threads.
-__device__ __forceinline__ void matmul_tile(const int8_t* __restrict__ X, const int8_t* __restrict__ W,
-                                            int32_t* __restrict__ Y, int a, int n, int b, int tile_j, int tile_i) {
-  __shared__ int8_t xs[32][33];
-  __shared__ int8_t ws[32][33];
-  int tj = threadIdx.x, ti = threadIdx.y;
-  int j = tile_j * 32 + tj;
-  int i0 = tile_i * 32;
-  int32_t acc[4] = {0, 0, 0, 0};
-  for (int k0 = 0; k0 < n; k0 += 32) {
-    for (int r = ti; r < 32; r += 8) {
-      int xi = i0 + r, xk = k0 + tj;
-      xs[r][tj] = (xi < a && xk < n) ? X[size_t(xi) * n + xk] : 0;
-      int wk = k0 + r, wj = tile_j * 32 + tj;
-      ws[r][tj] = (wk < n && wj < b) ? W[size_t(wk) * b + wj] : 0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; kk++) {
-      int32_t w = ws[kk][tj];
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[q] += int32_t(xs[ti + 8 * q][kk]) * w;
-    }
-    __syncthreads();
-  }
-  for (int q = 0; q < 4; q++) {
-    int i = i0 + ti + 8 * q;
-    if (i < a && j < b) Y[size_t(i) * b + j] = acc[q];
-  }
-}
-
 // Sum over the block of per-thread Fr values (blockDim.x = 256, sh of 256 entries).
 __device__ __forceinline__ Fr block_sum(Fr v, Fr* sh) {
   st_field(sh + threadIdx.x, v);

@@ -41,6 +41,7 @@ SIGNATURES = {
     "zkvc_fp_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_fp2_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_ntt": (_c_int, [_c_p, _c_u32, _c_int, _c_p]),
+    "zkvc_matmul_i8": (_c_int, [_c_p, _c_p, _c_p, _c_int, _c_int, _c_int, _c_p]),
     "zkvc_msm_workspace_bytes": (_c_sz, [_c_sz, _c_int]),
     "zkvc_msm_g1": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_msm_g2": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_sz, _c_p, _c_p]),
@@ -204,6 +205,23 @@ def _field_mul(name, a, b, out, width):
         out = _torch().empty_like(a)
     check(getattr(lib(), name)(_dev_ptr(a), _dev_ptr(b), _dev_ptr(out), a.shape[0], _stream()))
     return out
+
+
+def zkvc_matmul_i8(X, W):
+    """Y = X W for int8 CUDA tensors X [a, n] and W [n, b] (contiguous), exactly, on the
+    tensor cores; returns int32 Y [a, b] (a CUDA tensor)."""
+    import torch
+    if X.dtype != torch.int8 or W.dtype != torch.int8 or X.dim() != 2 or W.dim() != 2:
+        raise ValueError("X and W must be 2-D int8 tensors")
+    if not (X.is_cuda and W.is_cuda and X.is_contiguous() and W.is_contiguous()):
+        raise ValueError("X and W must be contiguous CUDA tensors")
+    a, n = X.shape
+    n2, b = W.shape
+    if n != n2:
+        raise ValueError("inner dimensions differ")
+    Y = torch.empty((a, b), dtype=torch.int32, device=X.device)
+    check(lib().zkvc_matmul_i8(_dev_ptr(X), _dev_ptr(W), _dev_ptr(Y), a, n, b, _stream()))
+    return Y
 
 
 def zkvc_ntt(data, kind):
