@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "coop.cuh"
 #include "groth16.h"
 #include "msm.h"
 #include "witness.cuh"
@@ -113,16 +114,31 @@ __global__ void k_scaled_witness(const int8_t* __restrict__ X, const int32_t* __
 // : 0), where (x, y) are the rest and H results (fold mode) or the main result and
 // infinity (chain mode).  Thread 0 converts A and C with one shared inversion; thread 32
 // (another warp) converts B concurrently.
-__global__ void k_encode(const G1J* small, const G1J* x, const G1J* y, const G1J* chain, const G2J* res2,
-                         uint8_t* proof) {
-  if (threadIdx.x == 0) {
-    G1J A = ld_field(small), C = p_add(ld_field(small + 1), ld_field(x));
-    if (y) C = p_add(C, ld_field(y));
-    if (chain) C = p_add(C, p_add(ld_field(chain), ld_field(chain + 1)));
-    encode_a_c(A, C, proof);
-  } else if (threadIdx.x == 32) {
-    encode_b(ld_field(res2), proof);
-  }
+// The proof is encoded piecewise as its parts become ready, so that only C's last
+// addition and inversion follow the H MSM: B on the G2 stream, A (and the part of C
+// without the H and rest terms) on the small-digit stream, the rest term on its own
+// stream, and C on the main stream after the joins.
+__global__ void k_encode_a(const G1J* small, const G1J* chain, G1J* cpart, uint8_t* proof) {
+  if (threadIdx.x != 0) return;
+  G1J c = ld_field(small + 1);
+  if (chain) c = p_add(c, p_add(ld_field(chain), ld_field(chain + 1)));
+  st_field(cpart, c);
+  encode_g1(ld_field(small), proof);
+}
+
+__global__ void k_encode_b(const G2J* res2, uint8_t* proof) {
+  if (threadIdx.x == 0) encode_b(ld_field(res2), proof);
+}
+
+__global__ void k_add_into(G1J* acc, const G1J* x) {
+  const G1J r = p_add_quad(ld_field(acc), ld_field(x));
+  if (threadIdx.x == 0) st_field(acc, r);
+}
+
+// C = cpart + H (one quad), then its encoding (bytes 192..255)
+__global__ void k_encode_c(const G1J* cpart, const G1J* h, uint8_t* proof) {
+  const G1J C = p_add_quad(ld_field(cpart), ld_field(h));
+  if (threadIdx.x == 0) encode_g1(C, proof + 192);
 }
 
 
@@ -130,7 +146,7 @@ __global__ void k_encode(const G1J* small, const G1J* x, const G1J* y, const G1J
 struct ProveBufs {
   Fr *ak, *bk, *yz, *S, *ev, *rs, *sw, *sa, *rb;
   int* flags;
-  G1J *res_small, *res_rest, *res_h, *res_chain;
+  G1J *res_small, *res_rest, *res_h, *res_chain, *cpart;
   G2J* res2;
   uint8_t* proof;
   void *ws_small, *ws_rest, *ws_h, *ws2;
@@ -243,6 +259,7 @@ static size_t carve(const zkvc_pk* pk, int mode, void* base, size_t cap, ProveBu
   B->res_rest = a.take<G1J>(1);
   B->res_h = a.take<G1J>(1);
   B->res_chain = a.take<G1J>(2);
+  B->cpart = a.take<G1J>(1);
   B->res2 = a.take<G2J>(1);
   B->proof = a.take<uint8_t>(256);
   Plans P;
@@ -275,10 +292,11 @@ static int side_streams(SideStreams** out) {
     int lo = 0, hi = 0;
     ZK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     for (int i = 0; i < NSIDE; i++) {
-      // Streams 0, 1 and 3 carry the latency-bound MSMs (G2; A and the int8 part of C) and
-      // the critical chain NTT -> H MSM: their blocks get precedence.  Stream 2 carries the
+      // Stream 3 carries the critical chain NTT -> H MSM: its blocks go first.  Streams 0
+      // and 1 (the latency-bound G2 and small-digit MSMs) come next; stream 2 carries the
       // throughput-bound "rest" MSM at the default priority and fills the gaps.
-      ZK_CUDA(cudaStreamCreateWithPriority(&t_side.st[i], cudaStreamNonBlocking, i == 2 ? lo : hi));
+      const int next = hi < lo ? hi + 1 : hi;
+      ZK_CUDA(cudaStreamCreateWithPriority(&t_side.st[i], cudaStreamNonBlocking, i == 3 ? hi : i == 2 ? lo : next));
       ZK_CUDA(cudaEventCreateWithFlags(&t_side.fork[i], cudaEventDisableTiming));
       ZK_CUDA(cudaEventCreateWithFlags(&t_side.join[i], cudaEventDisableTiming));
     }
@@ -335,6 +353,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   prof_mark(PS_MSM_G2, true, side->st[0]);
   ZK_TRY(msm_run<Fp2>(P.g2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st[0], PS_ACCUM_G2));
   prof_mark(PS_MSM_G2, false, side->st[0]);
+  k_encode_b<<<1, 32, 0, side->st[0]>>>(B.res2, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaEventRecord(side->join[0], side->st[0]));
   // 3. Y(z) and the PSQ prefix sums; in fold mode the scalars s w_v, s a_k, r b_k
   k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz); ZK_COUNT_LAUNCH();
@@ -353,6 +372,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
     k_chains<<<1, 32, 0, side->st[1]>>>(B.rs, B.res_small, B.res_chain); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
+  k_encode_a<<<1, 32, 0, side->st[1]>>>(B.res_small, chain ? B.res_chain : nullptr, B.cpart, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaEventRecord(side->join[1], side->st[1]));
   // 4. remaining domain evaluations
   size_t rest = N - sh.n;
@@ -363,6 +383,8 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
     // the full-scalar G1 terms that need no h, on side stream 2 (overlapping the NTTs)
     ZK_TRY(fork_to(side, 2, st));
     ZK_TRY(msm_run<Fp>(P.rest, pk->g1, B.ws_rest, B.ws_rest_bytes, B.res_rest, side->st[2]));
+    ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->join[1], 0));
+    k_add_into<<<1, 4, 0, side->st[2]>>>(B.cpart, B.res_rest); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaEventRecord(side->join[2], side->st[2]));
   }
   // 5-6. quotient and the H part of C on side stream 3 (the critical chain)
@@ -389,11 +411,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   }
   // 7. encode
   prof_mark(PS_COMBINE, true, st);
-  if (chain)
-    k_encode<<<1, 64, 0, st>>>(B.res_small, B.res_h, nullptr, B.res_chain, B.res2, B.proof);
-  else
-    k_encode<<<1, 64, 0, st>>>(B.res_small, B.res_rest, B.res_h, nullptr, B.res2, B.proof);
-  ZK_COUNT_LAUNCH();
+  k_encode_c<<<1, 4, 0, st>>>(B.cpart, B.res_h, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_COMBINE, false, st);
   ZK_CUDA(cudaMemcpyAsync(proof_out, B.proof, 256, cudaMemcpyDeviceToHost, st));

@@ -132,6 +132,14 @@ __device__ __forceinline__ G1A g1_affine_with(const G1J& p, const Fp& inv_zz_zzz
   return {f_mul(p.X, f_mul(inv_zz_zzz, p.ZZZ)), f_mul(p.Y, f_mul(inv_zz_zzz, p.ZZ))};
 }
 
+// Canonical affine encoding of one G1 point (64 bytes: x, y; infinity as zeros); one thread.
+__device__ __forceinline__ void encode_g1(const G1J& P, uint8_t* out) {
+  const Fp inv = P.is_inf() ? Fp::one() : f_inv(f_mul(P.ZZ, P.ZZZ));
+  const G1A q = g1_affine_with(P, inv);
+  write_canon(out, q.x);
+  write_canon(out + 32, q.y);
+}
+
 // Canonical encodings of A (bytes 0..63) and C (192..255) with one shared inversion
 // (Montgomery's trick); one thread.
 __device__ __forceinline__ void encode_a_c(const G1J& A, const G1J& C, uint8_t* proof) {
