@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "groth16.h"
@@ -68,11 +69,19 @@ __global__ void k_b_randomness(const BInst* __restrict__ I, int count) {
 
 // the witness matmul of every instance on the tensor cores (matmul_tc.cuh)
 __global__ void __launch_bounds__(MM_THREADS) k_b_matmul(const BInst* __restrict__ I) {
-  __shared__ MatmulSmem sm;
+  extern __shared__ __align__(128) uint8_t mm_dyn[];
+  MatmulSmem& sm = *reinterpret_cast<MatmulSmem*>(mm_dyn);
   const BInst& in = I[blockIdx.z];
   const int a = in.a, b = in.b;
   if ((int)blockIdx.x * MM_M >= b || (int)blockIdx.y * MM_N >= a) return;  // uniform per block
-  matmul_tc_tile(in.X, in.W, in.Y, a, in.n, b, blockIdx.x * MM_M, blockIdx.y * MM_N, sm, in.flags);
+  matmul_tc_tile(in.X, in.W, in.Y, a, in.n, b, blockIdx.x * MM_M, blockIdx.y * MM_N, 0, in.n, false, sm, in.flags);
+}
+
+static std::once_flag g_bmm_once;
+static void b_matmul_init() {
+  std::call_once(g_bmm_once, [] {
+    cudaFuncSetAttribute(k_b_matmul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MatmulSmem));
+  });
 }
 
 __global__ void __launch_bounds__(256) k_b_crpc_ab(const BInst* __restrict__ I) {
@@ -413,7 +422,9 @@ static int enqueue(zkvc_batch* B) {
   k_b_randomness<<<(n + 63) / 64, 64, 0, st>>>(B->dinst, n); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   // witness
-  k_b_matmul<<<dim3((maxb + MM_M - 1) / MM_M, (maxa + MM_N - 1) / MM_N, n), MM_THREADS, 0, st>>>(B->dinst);
+  b_matmul_init();
+  k_b_matmul<<<dim3((maxb + MM_M - 1) / MM_M, (maxa + MM_N - 1) / MM_N, n), MM_THREADS, sizeof(MatmulSmem), st>>>(
+      B->dinst);
   ZK_COUNT_LAUNCH();
   k_b_crpc_ab<<<dim3(maxn, n), 256, 0, st>>>(B->dinst); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
@@ -572,6 +583,7 @@ static int autotune(zkvc_batch* B) {
 
 static int batch_create(const zkvc_pk* const* pks, int count, int flags, zkvc_batch** out) {
   ZK_CHECK(pks && out, ZKVC_EINVAL, "batch: null argument");
+  b_matmul_init();  // before any capture
   ZK_CHECK(count >= 1 && count <= 4096, ZKVC_EINVAL, "batch: %d instances outside [1, 4096]", count);
   ZK_CHECK((flags & ~(ZKVC_BATCH_AUTOTUNE | ZKVC_BATCH_EAGER)) == 0, ZKVC_EINVAL, "batch: unknown flags 0x%x", flags);
   int dev = 0;
