@@ -169,6 +169,7 @@ int zkvc_pk_set_tuning(zkvc_pk* pk, const uint32_t tuning[ZKVC_PK_TUNING_LEN]) {
     ZK_CHECK(tuning[i] <= 1024, ZKVC_EINVAL, "set_tuning: chunk %u above 1024", tuning[i]);
   ZK_CHECK(tuning[4] == 0 || (tuning[4] >= 8 && tuning[4] <= 11), ZKVC_EINVAL,
            "set_tuning: 2^%u NTT elements per block outside [2^8, 2^11]", tuning[4]);
+  ZK_CHECK(tuning[5] <= 2, ZKVC_EINVAL, "set_tuning: rest-MSM start %u outside 0..2", tuning[5]);
   for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = tuning[i];
   return ZKVC_OK;
 }

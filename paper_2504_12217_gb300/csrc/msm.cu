@@ -779,7 +779,8 @@ int msm_upload(MsmExec* ex, cudaStream_t st) {
 }
 
 template <class F>
-int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cudaStream_t st, int accum_stage) {
+int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cudaStream_t st, int accum_stage,
+               cudaEvent_t after_accum) {
   ZK_CHECK(ex && ex->st && ex->st->uploaded, ZKVC_EINVAL, "msm: exec not uploaded");
   const MsmPlan& p = ex->plan;
   const Layout& L = ex->st->L;
@@ -827,6 +828,7 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
     if (uint32_t* hu = prof_units(accum_stage)) ZK_CUDA(cudaMemcpyAsync(hu, L.offs + K, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   }
   ZK_CUDA(cudaGetLastError());
+  if (after_accum) ZK_CUDA(cudaEventRecord(after_accum, st));
   k_fold_tree<F><<<(unsigned)((uint64_t(L.qmax) * ChunkLanes<F>::value + 127) / 128), 128, 0, st>>>(L.choff, L.chunk_key, K,
                                                                                                  part, L.arrive);
   ZK_COUNT_LAUNCH();
@@ -850,20 +852,20 @@ const uint32_t* msm_term_count(const MsmExec* ex) {
 
 template <class F>
 int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results, cudaStream_t st,
-            int accum_stage) {
+            int accum_stage, cudaEvent_t after_accum) {
   MsmExec ex;
   ZK_TRY(msm_prepare<F>(p, ws, ws_bytes, &ex));
   ZK_TRY(msm_upload(&ex, st));
-  return msm_launch<F>(&ex, bases, results, st, accum_stage);
+  return msm_launch<F>(&ex, bases, results, st, accum_stage, after_accum);
 }
 
 template size_t msm_workspace_bytes<Fp>(const MsmPlan&);
 template size_t msm_workspace_bytes<Fp2>(const MsmPlan&);
-template int msm_run<Fp>(const MsmPlan&, const Affine<Fp>*, void*, size_t, XYZZ<Fp>*, cudaStream_t, int);
-template int msm_run<Fp2>(const MsmPlan&, const Affine<Fp2>*, void*, size_t, XYZZ<Fp2>*, cudaStream_t, int);
+template int msm_run<Fp>(const MsmPlan&, const Affine<Fp>*, void*, size_t, XYZZ<Fp>*, cudaStream_t, int, cudaEvent_t);
+template int msm_run<Fp2>(const MsmPlan&, const Affine<Fp2>*, void*, size_t, XYZZ<Fp2>*, cudaStream_t, int, cudaEvent_t);
 template int msm_prepare<Fp>(const MsmPlan&, void*, size_t, MsmExec*);
 template int msm_prepare<Fp2>(const MsmPlan&, void*, size_t, MsmExec*);
-template int msm_launch<Fp>(const MsmExec*, const Affine<Fp>*, XYZZ<Fp>*, cudaStream_t, int);
-template int msm_launch<Fp2>(const MsmExec*, const Affine<Fp2>*, XYZZ<Fp2>*, cudaStream_t, int);
+template int msm_launch<Fp>(const MsmExec*, const Affine<Fp>*, XYZZ<Fp>*, cudaStream_t, int, cudaEvent_t);
+template int msm_launch<Fp2>(const MsmExec*, const Affine<Fp2>*, XYZZ<Fp2>*, cudaStream_t, int, cudaEvent_t);
 
 }  // namespace zkvc

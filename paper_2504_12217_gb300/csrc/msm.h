@@ -67,10 +67,12 @@ int msm_plan_finalize(MsmPlan& p);
 template <class F>
 size_t msm_workspace_bytes(const MsmPlan& p);
 
-// Runs every output of the plan; results[o] receives output o (XYZZ, device).
+// Runs every output of the plan; results[o] receives output o (XYZZ, device).  If
+// after_accum is given it is recorded on `st` once the bucket accumulation is enqueued
+// (other streams may wait for the end of the run's throughput-bound part).
 template <class F>
 int msm_run(const MsmPlan& p, const Affine<F>* bases, void* ws, size_t ws_bytes, XYZZ<F>* results,
-            cudaStream_t st, int accum_stage = -1);
+            cudaStream_t st, int accum_stage = -1, cudaEvent_t after_accum = nullptr);
 
 // The same run split in three, for launch sequences that are built once and replayed
 // (CUDA graphs): prepare carves the workspace and builds the host tables, upload copies
@@ -90,7 +92,8 @@ template <class F>
 int msm_prepare(const MsmPlan& p, void* ws, size_t ws_bytes, MsmExec* ex);
 int msm_upload(MsmExec* ex, cudaStream_t st);
 template <class F>
-int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cudaStream_t st, int accum_stage = -1);
+int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cudaStream_t st, int accum_stage = -1,
+               cudaEvent_t after_accum = nullptr);
 // Device address of the run's bucket-term count (valid after a launch completes).
 const uint32_t* msm_term_count(const MsmExec* ex);
 

@@ -281,6 +281,7 @@ struct SideStreams {
   int dev = -1;
   cudaStream_t st[NSIDE] = {};
   cudaEvent_t fork[NSIDE] = {}, join[NSIDE] = {};
+  cudaEvent_t ntt_done = nullptr, h_accum = nullptr;  // points where the rest MSM may start
 };
 static thread_local SideStreams t_side;
 
@@ -300,6 +301,8 @@ static int side_streams(SideStreams** out) {
       ZK_CUDA(cudaEventCreateWithFlags(&t_side.fork[i], cudaEventDisableTiming));
       ZK_CUDA(cudaEventCreateWithFlags(&t_side.join[i], cudaEventDisableTiming));
     }
+    ZK_CUDA(cudaEventCreateWithFlags(&t_side.ntt_done, cudaEventDisableTiming));
+    ZK_CUDA(cudaEventCreateWithFlags(&t_side.h_accum, cudaEventDisableTiming));
   }
   *out = &t_side;
   return ZKVC_OK;
@@ -379,14 +382,6 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_WITNESS, false, st);
-  if (!chain) {
-    // the full-scalar G1 terms that need no h, on side stream 2 (overlapping the NTTs)
-    ZK_TRY(fork_to(side, 2, st));
-    ZK_TRY(msm_run<Fp>(P.rest, pk->g1, B.ws_rest, B.ws_rest_bytes, B.res_rest, side->st[2]));
-    ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->join[1], 0));
-    k_add_into<<<1, 4, 0, side->st[2]>>>(B.cpart, B.res_rest); ZK_COUNT_LAUNCH();
-    ZK_CUDA(cudaEventRecord(side->join[2], side->st[2]));
-  }
   // 5-6. quotient and the H part of C on side stream 3 (the critical chain)
   ZK_TRY(fork_to(side, 3, st));
   cudaStream_t s3 = side->st[3];
@@ -400,11 +395,24 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   k_check_h<<<1, 32, 0, s3>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_NTT, false, s3);
+  ZK_CUDA(cudaEventRecord(side->ntt_done, s3));
   // the H MSM is the largest G1 run (N 16-bit digits): its stage and accumulation timers
   prof_mark(PS_MSM_G1, true, s3);
-  ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3, PS_ACCUM_G1));
+  ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3, PS_ACCUM_G1, side->h_accum));
   prof_mark(PS_MSM_G1, false, s3);
   ZK_CUDA(cudaEventRecord(side->join[3], s3));
+  if (!chain) {
+    // the full-scalar G1 terms that need no h, on side stream 2, then their term of C.
+    // It starts at once, after the NTTs or after the H accumulation (a tuned choice: its
+    // accumulation competes with the critical chain's for the SMs)
+    ZK_TRY(fork_to(side, 2, st));
+    if (pk->prove_tune[5] == 1) ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->ntt_done, 0));
+    if (pk->prove_tune[5] == 2) ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->h_accum, 0));
+    ZK_TRY(msm_run<Fp>(P.rest, pk->g1, B.ws_rest, B.ws_rest_bytes, B.res_rest, side->st[2]));
+    ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->join[1], 0));
+    k_add_into<<<1, 4, 0, side->st[2]>>>(B.cpart, B.res_rest); ZK_COUNT_LAUNCH();
+    ZK_CUDA(cudaEventRecord(side->join[2], side->st[2]));
+  }
   for (int i = 0; i < NSIDE; i++) {
     if (chain && i == 2) continue;
     ZK_CUDA(cudaStreamWaitEvent(st, side->join[i], 0));
@@ -445,8 +453,9 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
                    uint32_t* chosen) {
   static const uint32_t kCand[] = {2, 4, 8, 16, 32, 64};
   static const uint32_t kElog[] = {8, 9, 10, 11};
-  uint32_t saved[5];
-  for (int i = 0; i < 5; i++) saved[i] = pk->prove_tune[i];
+  static const uint32_t kRest[] = {0, 1, 2};
+  uint32_t saved[ZKVC_PK_TUNING_LEN];
+  for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) saved[i] = pk->prove_tune[i];
   for (int i = 0; i < 4; i++) pk->prove_tune[i] = 2;  // the largest workspace of all candidates
   size_t need = prove_workspace_bytes(pk, mode);
   for (int i = 0; i < 4; i++) pk->prove_tune[i] = saved[i];
@@ -488,10 +497,11 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
   float best_ms = 0;
   rc = measure(&best_ms);
   const int order[4] = {3, 0, 2, 1};  // g2, small, h, rest
-  for (int oi = 0; oi < 5 && rc == ZKVC_OK; oi++) {
-    const int r = oi < 4 ? order[oi] : 4;  // then the NTT block
-    const uint32_t* cand = r < 4 ? kCand : kElog;
-    const int ncand = r < 4 ? 6 : 4;
+  for (int oi = 0; oi < 6 && rc == ZKVC_OK; oi++) {
+    const int r = oi < 4 ? order[oi] : oi;  // then the NTT block, then the rest MSM's start
+    if (r == 5 && mode != ZKVC_PROVE_FOLD) break;  // no rest MSM in chain mode
+    const uint32_t* cand = r < 4 ? kCand : r == 4 ? kElog : kRest;
+    const int ncand = r < 4 ? 6 : r == 4 ? 4 : 3;
     uint32_t best = pk->prove_tune[r];
     for (int ci = 0; ci < ncand; ci++) {
       const uint32_t c = cand[ci];
@@ -508,11 +518,11 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
   }
   cleanup();
   if (rc != ZKVC_OK) {
-    for (int i = 0; i < 5; i++) pk->prove_tune[i] = saved[i];
+    for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = saved[i];
     return rc;
   }
   if (chosen)
-    for (int i = 0; i < 5; i++) chosen[i] = pk->prove_tune[i];
+    for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) chosen[i] = pk->prove_tune[i];
   return ZKVC_OK;
 }
 
