@@ -351,13 +351,10 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
   k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  // G2 MSM on side stream 0: it needs b_k and s
-  ZK_TRY(fork_to(side, 0, st));
-  prof_mark(PS_MSM_G2, true, side->st[0]);
-  ZK_TRY(msm_run<Fp2>(P.g2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st[0], PS_ACCUM_G2));
-  prof_mark(PS_MSM_G2, false, side->st[0]);
-  k_encode_b<<<1, 32, 0, side->st[0]>>>(B.res2, B.proof); ZK_COUNT_LAUNCH();
-  ZK_CUDA(cudaEventRecord(side->join[0], side->st[0]));
+  // The side streams may start at these points of the main stream (the events are
+  // recorded now); their work is enqueued after the critical NTT -> H chain's, so that
+  // the host reaches that chain's launches as early as possible.
+  ZK_CUDA(cudaEventRecord(side->fork[0], st));  // G2 MSM: needs b_k and s
   // 3. Y(z) and the PSQ prefix sums; in fold mode the scalars s w_v, s a_k, r b_k
   k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz); ZK_COUNT_LAUNCH();
   k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, B.S, Aev, Bev, Cev, B.flags); ZK_COUNT_LAUNCH();
@@ -367,21 +364,13 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
                                                         B.rb); ZK_COUNT_LAUNCH();
   }
   ZK_CUDA(cudaGetLastError());
-  // the small-digit G1 MSM on side stream 1, then in chain mode the two variable-base
-  // multiplications
-  ZK_TRY(fork_to(side, 1, st));
-  ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
-  if (chain) {
-    k_chains<<<1, 32, 0, side->st[1]>>>(B.rs, B.res_small, B.res_chain); ZK_COUNT_LAUNCH();
-    ZK_CUDA(cudaGetLastError());
-  }
-  k_encode_a<<<1, 32, 0, side->st[1]>>>(B.res_small, chain ? B.res_chain : nullptr, B.cpart, B.proof); ZK_COUNT_LAUNCH();
-  ZK_CUDA(cudaEventRecord(side->join[1], side->st[1]));
+  ZK_CUDA(cudaEventRecord(side->fork[1], st));  // small-digit G1 MSM
   // 4. remaining domain evaluations
   size_t rest = N - sh.n;
   k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_WITNESS, false, st);
+  ZK_CUDA(cudaEventRecord(side->fork[2], st));  // rest MSM
   // 5-6. quotient and the H part of C on side stream 3 (the critical chain)
   ZK_TRY(fork_to(side, 3, st));
   cudaStream_t s3 = side->st[3];
@@ -401,11 +390,28 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3, PS_ACCUM_G1, side->h_accum));
   prof_mark(PS_MSM_G1, false, s3);
   ZK_CUDA(cudaEventRecord(side->join[3], s3));
+  // the G2 MSM on side stream 0, then the encoding of B
+  ZK_CUDA(cudaStreamWaitEvent(side->st[0], side->fork[0], 0));
+  prof_mark(PS_MSM_G2, true, side->st[0]);
+  ZK_TRY(msm_run<Fp2>(P.g2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st[0], PS_ACCUM_G2));
+  prof_mark(PS_MSM_G2, false, side->st[0]);
+  k_encode_b<<<1, 32, 0, side->st[0]>>>(B.res2, B.proof); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaEventRecord(side->join[0], side->st[0]));
+  // the small-digit G1 MSM on side stream 1, then in chain mode the two variable-base
+  // multiplications, then the encoding of A and the H-free part of C
+  ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->fork[1], 0));
+  ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
+  if (chain) {
+    k_chains<<<1, 32, 0, side->st[1]>>>(B.rs, B.res_small, B.res_chain); ZK_COUNT_LAUNCH();
+    ZK_CUDA(cudaGetLastError());
+  }
+  k_encode_a<<<1, 32, 0, side->st[1]>>>(B.res_small, chain ? B.res_chain : nullptr, B.cpart, B.proof); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaEventRecord(side->join[1], side->st[1]));
   if (!chain) {
     // the full-scalar G1 terms that need no h, on side stream 2, then their term of C.
     // It starts at once, after the NTTs or after the H accumulation (a tuned choice: its
     // accumulation competes with the critical chain's for the SMs)
-    ZK_TRY(fork_to(side, 2, st));
+    ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->fork[2], 0));
     if (pk->prove_tune[5] == 1) ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->ntt_done, 0));
     if (pk->prove_tune[5] == 2) ZK_CUDA(cudaStreamWaitEvent(side->st[2], side->h_accum, 0));
     ZK_TRY(msm_run<Fp>(P.rest, pk->g1, B.ws_rest, B.ws_rest_bytes, B.res_rest, side->st[2]));
