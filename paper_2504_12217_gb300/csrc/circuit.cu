@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "circuit.h"
+#include "glv.h"
 #include "msm.h"
 #include "setup_common.h"
 #include "witness.cuh"
@@ -38,7 +39,7 @@ __global__ void k_psq(const Fr* ak, const Fr* bk, const Fr* ypart, int a, int n,
                       int* flags);
 __global__ void k_randomness(Fr* rs, int* flags);
 __global__ void k_check_h(const Fr* H, size_t N, int* flags);
-__global__ void k_chains(const Fr* rs, const G1J* small, G1J* chain);
+__global__ void k_chains(const GlvScalar* gs, const G1J* small, G1J* chain);
 
 static constexpr uint32_t COEF_ONE = 0, COEF_NEG = 1, COEF_Z0 = 2;
 static constexpr uint32_t LONG_ROW = 64;
@@ -707,6 +708,7 @@ struct GenBufs {
   void* aux;
   int* flags;
   G1J *pre, *hres, *chain;
+  GlvScalar* glv;
   G2J* g2res;
   uint8_t* proof;
   void *ws_pre, *ws_h, *ws_g2;
@@ -781,6 +783,7 @@ static size_t gen_carve(const zkvc_pk* pk, void* base, size_t cap, GenBufs* B, b
   B->pre = a.take<G1J>(3);
   B->hres = a.take<G1J>(1);
   B->chain = a.take<G1J>(2);
+  B->glv = a.take<GlvScalar>(2);
   B->g2res = a.take<G2J>(1);
   B->proof = a.take<uint8_t>(256);
   GenPlans P;
@@ -832,6 +835,11 @@ int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const u
 
   ZK_CUDA(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), st));
   ZK_CUDA(cudaMemcpyAsync(B.rs, rs_host, 64, cudaMemcpyHostToDevice, st));
+  {
+    // s and r split by the GLV endomorphism for s A and r B1
+    const GlvScalar g[2] = {glv_split(rs_host + 32), glv_split(rs_host)};
+    ZK_CUDA(cudaMemcpyAsync(B.glv, g, sizeof(g), cudaMemcpyHostToDevice, st));
+  }
   k_randomness<<<1, 1, 0, st>>>(B.rs, B.flags); ZK_COUNT_LAUNCH();
   // witness: Y, then the auxiliary variables
   ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
@@ -885,7 +893,7 @@ int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const u
   ZK_CUDA(cudaGetLastError());
   // A, the private part of C and B1 (all witness scalars known now)
   ZK_TRY(msm_run<Fp>(P.pre, pk->g1, B.ws_pre, B.ws_pre_bytes, B.pre, st));
-  k_chains<<<1, 32, 0, st>>>(B.rs, B.pre, B.chain); ZK_COUNT_LAUNCH();
+  k_chains<<<1, 32, 0, st>>>(B.glv, B.pre, B.chain); ZK_COUNT_LAUNCH();
   // quotient and H
   const NttDomain* d = pk->dom;
   ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, st));

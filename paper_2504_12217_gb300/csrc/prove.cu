@@ -26,6 +26,7 @@
 #include <cstring>
 
 #include "coop.cuh"
+#include "glv.h"
 #include "groth16.h"
 #include "msm.h"
 #include "witness.cuh"
@@ -78,16 +79,30 @@ __global__ void k_randomness(Fr* rs, int* flags) {
   st_field(rs + 3, f_neg(rsv));
 }
 
-// Chain mode: thread 0 computes s A, thread 1 r B1 (small-run outputs 0 and 2).
-__global__ void k_chains(const Fr* __restrict__ rs, const G1J* __restrict__ small, G1J* chain) {
-  const int t = threadIdx.x;
-  if (t >= 2) return;
-  const G1J P = ld_field(small + (t ? 2 : 0));
-  const Fr k = ld_field(rs + (t ? 0 : 1));
-  uint32_t kk[8];
+// Chain mode: s A and r B1 (small-run outputs 0 and 2) with the scalars split by the GLV
+// endomorphism on the host (gs[0] = s, gs[1] = r): four quads compute s1 A, s2 phi(A),
+// r1 B1 and r2 phi(B1) side by side (phi(x, y) = (beta x, y)), then two quads add the
+// pairs.  One block of 32 threads.
+__global__ void k_chains(const GlvScalar* __restrict__ gs, const G1J* __restrict__ small, G1J* chain) {
+  __shared__ G1J T[4][16];
+  __shared__ G1J part[4];
+  const int q = threadIdx.x >> 2;
+  if (q < 4) {
+    G1J P = ld_field(small + (q < 2 ? 0 : 2));
+    if (q & 1) {
+      Fp beta;
 #pragma unroll
-  for (int l = 0; l < 8; l++) kk[l] = k.v[l];
-  st_field(chain + t, p_mul_scalar_w4(P, kk));
+      for (int i = 0; i < 8; i++) beta.v[i] = glv_beta_limb(i);
+      P.X = f_mul(P.X, f_to_mont(beta));
+    }
+    const G1J R = p_mul_half_quad(P, gs[q >> 1].h[q & 1], T[q]);
+    if (quad_lane() == 0) st_field(part + q, R);
+  }
+  __syncthreads();
+  if (q == 0 || q == 2) {
+    const G1J S = p_add_quad(ld_field(part + q), ld_field(part + q + 1));
+    if (quad_lane() == 0) st_field(chain + (q >> 1), S);
+  }
 }
 
 // sw[v] = s w_v for v = 0 .. l (one, X, Y), sa[k] = s a_k and rb[k] = r b_k (k < n), in
@@ -147,6 +162,7 @@ struct ProveBufs {
   Fr *ak, *bk, *yz, *S, *ev, *rs, *sw, *sa, *rb;
   int* flags;
   G1J *res_small, *res_rest, *res_h, *res_chain, *cpart;
+  GlvScalar* glv;
   G2J* res2;
   uint8_t* proof;
   void *ws_small, *ws_rest, *ws_h, *ws2;
@@ -260,6 +276,7 @@ static size_t carve(const zkvc_pk* pk, int mode, void* base, size_t cap, ProveBu
   B->res_h = a.take<G1J>(1);
   B->res_chain = a.take<G1J>(2);
   B->cpart = a.take<G1J>(1);
+  B->glv = a.take<GlvScalar>(2);
   B->res2 = a.take<G2J>(1);
   B->proof = a.take<uint8_t>(256);
   Plans P;
@@ -342,6 +359,11 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   prof_mark(PS_WITNESS, true, st);
   ZK_CUDA(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), st));
   ZK_CUDA(cudaMemcpyAsync(B.rs, rs_host, 64, cudaMemcpyHostToDevice, st));
+  if (chain) {
+    // s and r split by the GLV endomorphism for the two scalar multiplications
+    const GlvScalar g[2] = {glv_split(rs_host + 32), glv_split(rs_host)};
+    ZK_CUDA(cudaMemcpyAsync(B.glv, g, sizeof(g), cudaMemcpyHostToDevice, st));
+  }
   k_randomness<<<1, 1, 0, st>>>(B.rs, B.flags); ZK_COUNT_LAUNCH();
   SideStreams* side = nullptr;
   ZK_TRY(side_streams(&side));
@@ -402,7 +424,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->fork[1], 0));
   ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
   if (chain) {
-    k_chains<<<1, 32, 0, side->st[1]>>>(B.rs, B.res_small, B.res_chain); ZK_COUNT_LAUNCH();
+    k_chains<<<1, 32, 0, side->st[1]>>>(B.glv, B.res_small, B.res_chain); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
   k_encode_a<<<1, 32, 0, side->st[1]>>>(B.res_small, chain ? B.res_chain : nullptr, B.cpart, B.proof); ZK_COUNT_LAUNCH();
