@@ -327,7 +327,8 @@ def run_gpu(args):
     Wd = torch.from_numpy(inst["W"]).cuda()
     Yd = torch.empty((a, b), dtype=torch.int32, device="cuda")
     # one-time latency tuning of the key's launch shape (setup, not timed)
-    tuning = nv.zkvc_pk_autotune(pk, Xd, Wd, inputs.to_bytes32(inst["rs"])) if not args.no_autotune else \
+    tuning = nv.zkvc_pk_autotune(pk, Xd, Wd, inputs.to_bytes32(inst["rs"]), mode=nv.ZKVC_PROVE_AUTO) \
+        if not args.no_autotune else \
         nv.zkvc_pk_get_tuning(pk)
     ws = torch.empty(nv.zkvc_prove_workspace_bytes(pk), dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -424,6 +425,7 @@ def run_gpu(args):
                    "l2": "flushed by a 256 MiB write between steps", "parallelism": f"replicas x{world}",
                    "msm_chunks_small_rest_h_g2": tuning[:4], "ntt_log_elems_per_block": tuning[4] or 10,
                    "rest_msm_start": ("at once", "after the NTTs", "after the H accumulation")[tuning[5]],
+                   "prover_mode": ("fold", "chain")[tuning[6]],
                    "chunk_source": "default rule" if args.no_autotune else "zkvc_pk_autotune at setup"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,

@@ -280,29 +280,35 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const ui
 
 /* The same proof computed two ways (identical bytes).  Groth16's C holds s A + r B1 - r s
  * [delta]1 (Sec. II), which needs A and B1 first.
- *   ZKVC_PROVE_FOLD   (zkvc_prove's mode) expands s A and r B1 by linearity into
+ *   ZKVC_PROVE_FOLD   (zkvc_prove's mode unless tuning chose chain) expands s A and r B1 by linearity into
  *                     fixed-base terms sum (s w_v) [A_v]1 + sum (r w_e) [B_e]1 + ..., so
  *                     no serial doubling chain remains: lowest latency for one proof,
  *                     but 16 signed digits per witness entry instead of one.
  *   ZKVC_PROVE_CHAIN  computes A and B1 with small-scalar MSMs and then s A and r B1 as
- *                     two variable-base multiplications (254 doublings each, one thread)
- *                     beside the H MSM: about 2.5x less MSM work per proof, so more
- *                     proofs per second when several proofs share the GPU.
- * Workspace sizes differ per mode. */
+ *                     two variable-base multiplications beside the H MSM (the scalars
+ *                     split by the GLV endomorphism, four 127-bit halves on four lane
+ *                     quads): about 2.5x less MSM work per proof, so more proofs per
+ *                     second when several proofs share the GPU.
+ * Workspace sizes differ per mode.  zkvc_prove uses the key's mode (tuning value 6),
+ * ZKVC_PROVE_FOLD unless zkvc_pk_autotune or zkvc_pk_set_tuning chose chain, and
+ * zkvc_prove_workspace_bytes follows it. */
 /* Latency tuning of the one-proof prover for a key: zkvc_pk_autotune times whole proofs
  * of the given inputs (device X, W; host rs) in `mode` while it varies the launch shape
  * -- ZKVC_PK_TUNING_LEN values: the terms per level-0 chunk of each MSM run (small-scalar
  * G1, rest G1, H, G2; 0 = the default rule: 16 terms below 2 M bucket terms per run, else
  * 32), log2 of the NTT elements per block (8..11; 0 = 10), and when the fold mode's
  * full-scalar "rest" MSM starts (0 at once, 1 after the NTTs, 2 after the H MSM's bucket
- * accumulation) -- keeps the fastest in the key and writes it to tuning (may be NULL).  It allocates and frees its own
- * workspace and synchronises `stream`; the key must not be proving meanwhile.
+ * accumulation), and the mode zkvc_prove uses (ZKVC_PROVE_FOLD or ZKVC_PROVE_CHAIN) --
+ * keeps the fastest in the key and writes it to tuning (may be NULL).  `mode` is the
+ * mode to tune, or ZKVC_PROVE_AUTO to tune both and keep the faster.  It allocates and
+ * frees its own workspace and synchronises `stream`; the key must not be proving
+ * meanwhile.
  * Afterwards zkvc_prove_workspace_bytes reflects the chosen chunks (smaller chunks need
  * more workspace).  zkvc_pk_set_tuning / zkvc_pk_get_tuning impose or read the setting
- * (ZKVC_EINVAL for a chunk above 1024, an NTT block outside 2^8..2^11 or a start above
- * 2).  Proof bytes
+ * (ZKVC_EINVAL for a chunk above 1024, an NTT block outside 2^8..2^11, a start above 2
+ * or a mode other than fold or chain).  Proof bytes
  * never depend on it.  Keys of zkvc_setup only. */
-#define ZKVC_PK_TUNING_LEN 6
+#define ZKVC_PK_TUNING_LEN 7
 int zkvc_pk_autotune(zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64], void* stream,
                      uint32_t tuning[ZKVC_PK_TUNING_LEN]);
 int zkvc_pk_set_tuning(zkvc_pk* pk, const uint32_t tuning[ZKVC_PK_TUNING_LEN]);
@@ -310,6 +316,7 @@ int zkvc_pk_get_tuning(const zkvc_pk* pk, uint32_t tuning[ZKVC_PK_TUNING_LEN]);
 
 #define ZKVC_PROVE_FOLD 0
 #define ZKVC_PROVE_CHAIN 1
+#define ZKVC_PROVE_AUTO 2 /* zkvc_pk_autotune only: tune both modes, keep the faster */
 size_t zkvc_prove_workspace_bytes_mode(const zkvc_pk* pk, int mode);
 int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64],
                     int32_t* d_Y, void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream);

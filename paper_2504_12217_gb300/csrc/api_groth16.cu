@@ -157,7 +157,8 @@ int zkvc_pk_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, 
   set_error("%s", "");
   ZK_CHECK(pk && dX && dW && rs, ZKVC_EINVAL, "autotune: null argument");
   ZK_CHECK(!pk->gen, ZKVC_EINVAL, "autotune: keys of zkvc_setup_circuit are not tuned");
-  ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN, ZKVC_EINVAL, "autotune: mode %d", mode);
+  ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN || mode == ZKVC_PROVE_AUTO, ZKVC_EINVAL,
+           "autotune: mode %d", mode);
   ZK_TRY(device_guard(pk->device));
   return prove_autotune(pk, mode, dX, dW, rs, (cudaStream_t)stream, tuning);
 }
@@ -170,6 +171,7 @@ int zkvc_pk_set_tuning(zkvc_pk* pk, const uint32_t tuning[ZKVC_PK_TUNING_LEN]) {
   ZK_CHECK(tuning[4] == 0 || (tuning[4] >= 8 && tuning[4] <= 11), ZKVC_EINVAL,
            "set_tuning: 2^%u NTT elements per block outside [2^8, 2^11]", tuning[4]);
   ZK_CHECK(tuning[5] <= 2, ZKVC_EINVAL, "set_tuning: rest-MSM start %u outside 0..2", tuning[5]);
+  ZK_CHECK(tuning[6] <= 1, ZKVC_EINVAL, "set_tuning: prover mode %u is neither fold (0) nor chain (1)", tuning[6]);
   for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = tuning[i];
   return ZKVC_OK;
 }
@@ -451,7 +453,7 @@ int zkvc_vk_load(const char* path, zkvc_vk** out) {
 
 size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk) {
   if (!pk) return 0;
-  return pk->gen ? prove_generic_workspace_bytes(pk) : prove_workspace_bytes(pk, ZKVC_PROVE_FOLD);
+  return pk->gen ? prove_generic_workspace_bytes(pk) : prove_workspace_bytes(pk, (int)pk->prove_tune[6]);
 }
 
 size_t zkvc_prove_workspace_bytes_mode(const zkvc_pk* pk, int mode) {
@@ -465,7 +467,7 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   ZK_CHECK(pk, ZKVC_EINVAL, "prove: null key");
   ZK_TRY(device_guard(pk->device));
   if (pk->gen) return prove_generic(pk, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
-  return prove_impl(pk, ZKVC_PROVE_FOLD, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
+  return prove_impl(pk, (int)pk->prove_tune[6], dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
 }
 
 int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t rs[64], int32_t* dY,

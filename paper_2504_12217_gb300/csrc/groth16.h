@@ -100,8 +100,8 @@ struct zkvc_pk {
   // launch shape of the one-proof prover, chosen by zkvc_pk_autotune: terms per level-0
   // chunk of the MSM runs (small, rest, h, g2; 0 = the default rule), log2 of the NTT
   // elements per block (0 = 10), when the rest MSM starts (0 at once, 1 after the NTTs,
-  // 2 after the H accumulation)
-  uint32_t prove_tune[ZKVC_PK_TUNING_LEN] = {0, 0, 0, 0, 0, 0};
+  // 2 after the H accumulation), and zkvc_prove's mode (ZKVC_PROVE_FOLD or _CHAIN)
+  uint32_t prove_tune[ZKVC_PK_TUNING_LEN] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 struct zkvc_vk {

@@ -475,8 +475,10 @@ int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, 
 
 // Latency tuning of the one-proof prover: coordinate descent over the level-0 chunk of
 // each MSM run (the G2 and small-scalar runs first: their bucket sums are the longest
-// dependent chains), timing whole proofs with CUDA events on st.  Proof bytes do not
-// depend on the chunks.  Allocates its own Y and workspace; the key must not be in use.
+// dependent chains), the NTT block and, in fold mode, the start of the rest MSM, timing
+// whole proofs with CUDA events on st.  With ZKVC_PROVE_AUTO both modes are tuned and the
+// faster one is kept as the key's mode for zkvc_prove.  Proof bytes do not depend on any
+// of it.  Allocates its own Y and workspace; the key must not be in use.
 int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, cudaStream_t st,
                    uint32_t* chosen) {
   static const uint32_t kCand[] = {2, 4, 8, 16, 32, 64};
@@ -485,7 +487,7 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
   uint32_t saved[ZKVC_PK_TUNING_LEN];
   for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) saved[i] = pk->prove_tune[i];
   for (int i = 0; i < 4; i++) pk->prove_tune[i] = 2;  // the largest workspace of all candidates
-  size_t need = prove_workspace_bytes(pk, mode);
+  size_t need = std::max(prove_workspace_bytes(pk, ZKVC_PROVE_FOLD), prove_workspace_bytes(pk, ZKVC_PROVE_CHAIN));
   for (int i = 0; i < 4; i++) pk->prove_tune[i] = saved[i];
   void* ws = nullptr;
   int32_t* dY = nullptr;
@@ -508,11 +510,11 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
     return ZKVC_ECUDA;
   }
   uint8_t proof[256];
-  auto measure = [&](float* ms) -> int {
+  auto measure = [&](int m, float* ms) -> int {
     float t[5];
     for (int rep = 0; rep < 6; rep++) {
       ZK_CUDA(cudaEventRecord(e0, st));
-      ZK_TRY(prove_impl(pk, mode, dX, dW, rs, dY, ws, need, proof, st));
+      ZK_TRY(prove_impl(pk, m, dX, dW, rs, dY, ws, need, proof, st));
       ZK_CUDA(cudaEventRecord(e1, st));
       ZK_CUDA(cudaEventSynchronize(e1));
       if (rep > 0) ZK_CUDA(cudaEventElapsedTime(&t[rep - 1], e0, e1));
@@ -521,28 +523,50 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
     *ms = t[2];
     return ZKVC_OK;
   };
-  int rc = ZKVC_OK;
-  float best_ms = 0;
-  rc = measure(&best_ms);
-  const int order[4] = {3, 0, 2, 1};  // g2, small, h, rest
-  for (int oi = 0; oi < 6 && rc == ZKVC_OK; oi++) {
-    const int r = oi < 4 ? order[oi] : oi;  // then the NTT block, then the rest MSM's start
-    if (r == 5 && mode != ZKVC_PROVE_FOLD) break;  // no rest MSM in chain mode
-    const uint32_t* cand = r < 4 ? kCand : r == 4 ? kElog : kRest;
-    const int ncand = r < 4 ? 6 : r == 4 ? 4 : 3;
-    uint32_t best = pk->prove_tune[r];
-    for (int ci = 0; ci < ncand; ci++) {
-      const uint32_t c = cand[ci];
-      if (c == best || (r == 4 && best == 0 && c == 10)) continue;
-      pk->prove_tune[r] = c;
-      float ms = 0;
-      if ((rc = measure(&ms)) != ZKVC_OK) break;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = c;
+  // coordinate descent for one mode from the key's current setting
+  auto tune = [&](int m, float* best_ms) -> int {
+    ZK_TRY(measure(m, best_ms));
+    const int order[4] = {3, 0, 2, 1};  // g2, small, h, rest
+    for (int oi = 0; oi < 6; oi++) {
+      const int r = oi < 4 ? order[oi] : oi;  // then the NTT block, then the rest MSM's start
+      if (r == 5 && m != ZKVC_PROVE_FOLD) break;  // no rest MSM in chain mode
+      const uint32_t* cand = r < 4 ? kCand : r == 4 ? kElog : kRest;
+      const int ncand = r < 4 ? 6 : r == 4 ? 4 : 3;
+      uint32_t best = pk->prove_tune[r];
+      for (int ci = 0; ci < ncand; ci++) {
+        const uint32_t c = cand[ci];
+        if (c == best || (r == 4 && best == 0 && c == 10)) continue;
+        pk->prove_tune[r] = c;
+        float ms = 0;
+        ZK_TRY(measure(m, &ms));
+        if (ms < *best_ms) {
+          *best_ms = ms;
+          best = c;
+        }
       }
+      pk->prove_tune[r] = best;
     }
-    pk->prove_tune[r] = best;
+    return ZKVC_OK;
+  };
+  int rc = ZKVC_OK;
+  if (mode == ZKVC_PROVE_AUTO) {
+    float fold_ms = 0, chain_ms = 0;
+    uint32_t fold_tune[ZKVC_PK_TUNING_LEN];
+    rc = tune(ZKVC_PROVE_FOLD, &fold_ms);
+    for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) fold_tune[i] = pk->prove_tune[i];
+    if (rc == ZKVC_OK) {
+      for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = saved[i];
+      rc = tune(ZKVC_PROVE_CHAIN, &chain_ms);
+    }
+    if (rc == ZKVC_OK) {
+      if (fold_ms <= chain_ms)
+        for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = fold_tune[i];
+      pk->prove_tune[6] = fold_ms <= chain_ms ? ZKVC_PROVE_FOLD : ZKVC_PROVE_CHAIN;
+    }
+  } else {
+    float ms = 0;
+    rc = tune(mode, &ms);
+    if (rc == ZKVC_OK) pk->prove_tune[6] = (uint32_t)mode;
   }
   cleanup();
   if (rc != ZKVC_OK) {

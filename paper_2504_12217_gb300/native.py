@@ -452,14 +452,16 @@ def zkvc_prove_workspace_bytes(pk):
 
 ZKVC_PROVE_FOLD = 0
 ZKVC_PROVE_CHAIN = 1
+ZKVC_PROVE_AUTO = 2
 
 
-ZKVC_PK_TUNING_LEN = 6
+ZKVC_PK_TUNING_LEN = 7
 
 
 def zkvc_pk_autotune(pk, X, W, rs, mode=0):
     """Tune the key's launch shape for one-proof latency on these inputs; returns the
-    chosen [small, rest, h, g2 chunk terms, NTT log2 elements per block, rest-MSM start]."""
+    chosen [small, rest, h, g2 chunk terms, NTT log2 elements per block, rest-MSM start,
+    prover mode].  mode: ZKVC_PROVE_FOLD, ZKVC_PROVE_CHAIN or ZKVC_PROVE_AUTO (both)."""
     arr = (ctypes.c_uint32 * ZKVC_PK_TUNING_LEN)()
     rsb = ctypes.create_string_buffer(bytes(rs), 64)
     check(lib().zkvc_pk_autotune(pk.handle, mode, _dev_ptr(X), _dev_ptr(W), rsb, _stream(), arr))
