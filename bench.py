@@ -424,8 +424,9 @@ def run_gpu(args):
         "config": {"workload": "crpc_groth16_bn254_49x320x512", "a": a, "n": n, "b": b, "log_domain": 16,
                    "l2": "flushed by a 256 MiB write between steps", "parallelism": f"replicas x{world}",
                    "msm_chunks_small_rest_h_g2": tuning[:4], "ntt_log_elems_per_block": tuning[4] or 10,
-                   "rest_msm_start": ("at once", "after the NTTs", "after the H accumulation")[tuning[5]],
+                   "side_msm_start": ("at once", "after the NTTs", "after the H accumulation")[tuning[5]],
                    "prover_mode": ("fold", "chain")[tuning[6]],
+                   "g2_msm_start": ("at once", "after the NTTs")[tuning[7]],
                    "chunk_source": "default rule" if args.no_autotune else "zkvc_pk_autotune at setup"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,

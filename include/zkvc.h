@@ -296,19 +296,20 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const ui
  * of the given inputs (device X, W; host rs) in `mode` while it varies the launch shape
  * -- ZKVC_PK_TUNING_LEN values: the terms per level-0 chunk of each MSM run (small-scalar
  * G1, rest G1, H, G2; 0 = the default rule: 16 terms below 2 M bucket terms per run, else
- * 32), log2 of the NTT elements per block (8..11; 0 = 10), and when the fold mode's
- * full-scalar "rest" MSM starts (0 at once, 1 after the NTTs, 2 after the H MSM's bucket
- * accumulation), and the mode zkvc_prove uses (ZKVC_PROVE_FOLD or ZKVC_PROVE_CHAIN) --
+ * 32), log2 of the NTT elements per block (8..11; 0 = 10), when the side MSM starts (the
+ * full-scalar "rest" MSM in fold mode, the small-digit MSM in chain mode: 0 at once, 1
+ * after the NTTs, 2 after the H MSM's bucket accumulation), the mode zkvc_prove uses
+ * (ZKVC_PROVE_FOLD or ZKVC_PROVE_CHAIN), and when the G2 MSM starts (0, 1) --
  * keeps the fastest in the key and writes it to tuning (may be NULL).  `mode` is the
  * mode to tune, or ZKVC_PROVE_AUTO to tune both and keep the faster.  It allocates and
  * frees its own workspace and synchronises `stream`; the key must not be proving
  * meanwhile.
  * Afterwards zkvc_prove_workspace_bytes reflects the chosen chunks (smaller chunks need
  * more workspace).  zkvc_pk_set_tuning / zkvc_pk_get_tuning impose or read the setting
- * (ZKVC_EINVAL for a chunk above 1024, an NTT block outside 2^8..2^11, a start above 2
- * or a mode other than fold or chain).  Proof bytes
+ * (ZKVC_EINVAL for a chunk above 1024, an NTT block outside 2^8..2^11, a start outside
+ * its range or a mode other than fold or chain).  Proof bytes
  * never depend on it.  Keys of zkvc_setup only. */
-#define ZKVC_PK_TUNING_LEN 7
+#define ZKVC_PK_TUNING_LEN 8
 int zkvc_pk_autotune(zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64], void* stream,
                      uint32_t tuning[ZKVC_PK_TUNING_LEN]);
 int zkvc_pk_set_tuning(zkvc_pk* pk, const uint32_t tuning[ZKVC_PK_TUNING_LEN]);

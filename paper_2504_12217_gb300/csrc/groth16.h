@@ -99,9 +99,11 @@ struct zkvc_pk {
   zkvc::GenericKey* gen = nullptr;  // set for keys of zkvc_setup_circuit (generic R1CS layout)
   // launch shape of the one-proof prover, chosen by zkvc_pk_autotune: terms per level-0
   // chunk of the MSM runs (small, rest, h, g2; 0 = the default rule), log2 of the NTT
-  // elements per block (0 = 10), when the rest MSM starts (0 at once, 1 after the NTTs,
-  // 2 after the H accumulation), and zkvc_prove's mode (ZKVC_PROVE_FOLD or _CHAIN)
-  uint32_t prove_tune[ZKVC_PK_TUNING_LEN] = {0, 0, 0, 0, 0, 0, 0};
+  // elements per block (0 = 10), when the side MSM starts (the rest MSM in fold mode, the
+  // small-digit MSM in chain mode: 0 at once, 1 after the NTTs, 2 after the H
+  // accumulation), zkvc_prove's mode (ZKVC_PROVE_FOLD or _CHAIN), when the G2 MSM starts
+  // (0 at once, 1 after the NTTs)
+  uint32_t prove_tune[ZKVC_PK_TUNING_LEN] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 struct zkvc_vk {

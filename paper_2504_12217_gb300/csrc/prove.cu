@@ -412,16 +412,22 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3, PS_ACCUM_G1, side->h_accum));
   prof_mark(PS_MSM_G1, false, s3);
   ZK_CUDA(cudaEventRecord(side->join[3], s3));
-  // the G2 MSM on side stream 0, then the encoding of B
+  // the G2 MSM on side stream 0 (at once or after the NTTs, a tuned choice), then the
+  // encoding of B
   ZK_CUDA(cudaStreamWaitEvent(side->st[0], side->fork[0], 0));
+  if (pk->prove_tune[7] == 1) ZK_CUDA(cudaStreamWaitEvent(side->st[0], side->ntt_done, 0));
   prof_mark(PS_MSM_G2, true, side->st[0]);
   ZK_TRY(msm_run<Fp2>(P.g2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st[0], PS_ACCUM_G2));
   prof_mark(PS_MSM_G2, false, side->st[0]);
   k_encode_b<<<1, 32, 0, side->st[0]>>>(B.res2, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaEventRecord(side->join[0], side->st[0]));
   // the small-digit G1 MSM on side stream 1, then in chain mode the two variable-base
-  // multiplications, then the encoding of A and the H-free part of C
+  // multiplications, then the encoding of A and the H-free part of C.  In chain mode it
+  // is the side MSM whose start is tuned (at once, after the NTTs, after the H
+  // accumulation); in fold mode the rest MSM is.
   ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->fork[1], 0));
+  if (chain && pk->prove_tune[5] == 1) ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->ntt_done, 0));
+  if (chain && pk->prove_tune[5] == 2) ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->h_accum, 0));
   ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
   if (chain) {
     k_chains<<<1, 32, 0, side->st[1]>>>(B.glv, B.res_small, B.res_chain); ZK_COUNT_LAUNCH();
@@ -484,6 +490,7 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
   static const uint32_t kCand[] = {2, 4, 8, 16, 32, 64};
   static const uint32_t kElog[] = {8, 9, 10, 11};
   static const uint32_t kRest[] = {0, 1, 2};
+  static const uint32_t kG2[] = {0, 1};
   uint32_t saved[ZKVC_PK_TUNING_LEN];
   for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) saved[i] = pk->prove_tune[i];
   for (int i = 0; i < 4; i++) pk->prove_tune[i] = 2;  // the largest workspace of all candidates
@@ -510,28 +517,31 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
     return ZKVC_ECUDA;
   }
   uint8_t proof[256];
+  // median of nine timed proofs after one untimed
   auto measure = [&](int m, float* ms) -> int {
-    float t[5];
-    for (int rep = 0; rep < 6; rep++) {
+    float t[9];
+    for (int rep = 0; rep < 10; rep++) {
       ZK_CUDA(cudaEventRecord(e0, st));
       ZK_TRY(prove_impl(pk, m, dX, dW, rs, dY, ws, need, proof, st));
       ZK_CUDA(cudaEventRecord(e1, st));
       ZK_CUDA(cudaEventSynchronize(e1));
       if (rep > 0) ZK_CUDA(cudaEventElapsedTime(&t[rep - 1], e0, e1));
     }
-    std::sort(t, t + 5);
-    *ms = t[2];
+    std::sort(t, t + 9);
+    *ms = t[4];
     return ZKVC_OK;
   };
-  // coordinate descent for one mode from the key's current setting
+  // coordinate descent for one mode from the key's current setting: two sweeps, the
+  // incumbent re-timed at the start of each (timings on a shared GPU drift)
   auto tune = [&](int m, float* best_ms) -> int {
-    ZK_TRY(measure(m, best_ms));
     const int order[4] = {3, 0, 2, 1};  // g2, small, h, rest
-    for (int oi = 0; oi < 6; oi++) {
-      const int r = oi < 4 ? order[oi] : oi;  // then the NTT block, then the rest MSM's start
-      if (r == 5 && m != ZKVC_PROVE_FOLD) break;  // no rest MSM in chain mode
-      const uint32_t* cand = r < 4 ? kCand : r == 4 ? kElog : kRest;
-      const int ncand = r < 4 ? 6 : r == 4 ? 4 : 3;
+    for (int sweep = 0; sweep < 2; sweep++) {
+    ZK_TRY(measure(m, best_ms));
+    for (int oi = 0; oi < 7; oi++) {
+      // then the NTT block, the side MSM's start, the G2 MSM's start (index 6 is the mode)
+      const int r = oi < 4 ? order[oi] : oi == 6 ? 7 : oi;
+      const uint32_t* cand = r < 4 ? kCand : r == 4 ? kElog : r == 5 ? kRest : kG2;
+      const int ncand = r < 4 ? 6 : r == 4 ? 4 : r == 5 ? 3 : 2;
       uint32_t best = pk->prove_tune[r];
       for (int ci = 0; ci < ncand; ci++) {
         const uint32_t c = cand[ci];
@@ -545,6 +555,7 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
         }
       }
       pk->prove_tune[r] = best;
+    }
     }
     return ZKVC_OK;
   };
