@@ -327,9 +327,13 @@ def run_gpu(args):
     Wd = torch.from_numpy(inst["W"]).cuda()
     Yd = torch.empty((a, b), dtype=torch.int32, device="cuda")
     # one-time latency tuning of the key's launch shape (setup, not timed)
-    tuning = nv.zkvc_pk_autotune(pk, Xd, Wd, inputs.to_bytes32(inst["rs"]), mode=nv.ZKVC_PROVE_AUTO) \
-        if not args.no_autotune else \
-        nv.zkvc_pk_get_tuning(pk)
+    if args.key_tuning:
+        nv.zkvc_pk_set_tuning(pk, args.key_tuning)
+        tuning = nv.zkvc_pk_get_tuning(pk)
+    elif args.no_autotune:
+        tuning = nv.zkvc_pk_get_tuning(pk)
+    else:
+        tuning = nv.zkvc_pk_autotune(pk, Xd, Wd, inputs.to_bytes32(inst["rs"]), mode=nv.ZKVC_PROVE_AUTO)
     ws = torch.empty(nv.zkvc_prove_workspace_bytes(pk), dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     total_steps = args.warmup + args.steps
@@ -427,7 +431,8 @@ def run_gpu(args):
                    "side_msm_start": ("at once", "after the NTTs", "after the H accumulation")[tuning[5]],
                    "prover_mode": ("fold", "chain")[tuning[6]],
                    "g2_msm_start": ("at once", "after the NTTs")[tuning[7]],
-                   "chunk_source": "default rule" if args.no_autotune else "zkvc_pk_autotune at setup"},
+                   "chunk_source": "imposed (--key-tuning)" if args.key_tuning else
+                   "default rule" if args.no_autotune else "zkvc_pk_autotune at setup"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps, "clocks": clk, "stage_ms": stages,
@@ -813,6 +818,8 @@ def main():
     ap.add_argument("--server-slots", type=int, default=8)
     ap.add_argument("--server-budget-gib", type=int, default=48)
     ap.add_argument("--batch-count", type=int, default=0, help="batched: only the K smallest instances")
+    ap.add_argument("--key-tuning", type=int, nargs=8, default=None,
+                    help="plain: impose the key's launch shape (zkvc_pk_set_tuning), skip the autotuner")
     ap.add_argument("--tuning", type=int, nargs=7, default=None, help="batched: impose a tuning, skip the autotuner")
     ap.add_argument("--eager", action="store_true", help="batched: launch eagerly instead of replaying a graph")
     args = ap.parse_args()
