@@ -431,6 +431,7 @@ def run_gpu(args):
                    "side_msm_start": ("at once", "after the NTTs", "after the H accumulation")[tuning[5]],
                    "prover_mode": ("fold", "chain")[tuning[6]],
                    "g2_msm_start": ("at once", "after the NTTs")[tuning[7]],
+                   "quad_lanes_h_small": tuning[8:10],
                    "chunk_source": "imposed (--key-tuning)" if args.key_tuning else
                    "default rule" if args.no_autotune else "zkvc_pk_autotune at setup"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
@@ -818,7 +819,7 @@ def main():
     ap.add_argument("--server-slots", type=int, default=8)
     ap.add_argument("--server-budget-gib", type=int, default=48)
     ap.add_argument("--batch-count", type=int, default=0, help="batched: only the K smallest instances")
-    ap.add_argument("--key-tuning", type=int, nargs=8, default=None,
+    ap.add_argument("--key-tuning", type=int, nargs=10, default=None,
                     help="plain: impose the key's launch shape (zkvc_pk_set_tuning), skip the autotuner")
     ap.add_argument("--tuning", type=int, nargs=7, default=None, help="batched: impose a tuning, skip the autotuner")
     ap.add_argument("--eager", action="store_true", help="batched: launch eagerly instead of replaying a graph")

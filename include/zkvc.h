@@ -299,7 +299,8 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const ui
  * 32), log2 of the NTT elements per block (8..11; 0 = 10), when the side MSM starts (the
  * full-scalar "rest" MSM in fold mode, the small-digit MSM in chain mode: 0 at once, 1
  * after the NTTs, 2 after the H MSM's bucket accumulation), the mode zkvc_prove uses
- * (ZKVC_PROVE_FOLD or ZKVC_PROVE_CHAIN), and when the G2 MSM starts (0, 1) --
+ * (ZKVC_PROVE_FOLD or ZKVC_PROVE_CHAIN), when the G2 MSM starts (0, 1), and whether the H
+ * and the small-digit runs accumulate on quads of lanes (0, 1) --
  * keeps the fastest in the key and writes it to tuning (may be NULL).  `mode` is the
  * mode to tune, or ZKVC_PROVE_AUTO to tune both and keep the faster.  It allocates and
  * frees its own workspace and synchronises `stream`; the key must not be proving
@@ -309,7 +310,7 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const ui
  * (ZKVC_EINVAL for a chunk above 1024, an NTT block outside 2^8..2^11, a start outside
  * its range or a mode other than fold or chain).  Proof bytes
  * never depend on it.  Keys of zkvc_setup only. */
-#define ZKVC_PK_TUNING_LEN 8
+#define ZKVC_PK_TUNING_LEN 10
 int zkvc_pk_autotune(zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64], void* stream,
                      uint32_t tuning[ZKVC_PK_TUNING_LEN]);
 int zkvc_pk_set_tuning(zkvc_pk* pk, const uint32_t tuning[ZKVC_PK_TUNING_LEN]);

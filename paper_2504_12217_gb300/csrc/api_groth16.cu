@@ -173,6 +173,8 @@ int zkvc_pk_set_tuning(zkvc_pk* pk, const uint32_t tuning[ZKVC_PK_TUNING_LEN]) {
   ZK_CHECK(tuning[5] <= 2, ZKVC_EINVAL, "set_tuning: rest-MSM start %u outside 0..2", tuning[5]);
   ZK_CHECK(tuning[6] <= 1, ZKVC_EINVAL, "set_tuning: prover mode %u is neither fold (0) nor chain (1)", tuning[6]);
   ZK_CHECK(tuning[7] <= 1, ZKVC_EINVAL, "set_tuning: G2 start %u outside 0..1", tuning[7]);
+  ZK_CHECK(tuning[8] <= 1 && tuning[9] <= 1, ZKVC_EINVAL, "set_tuning: quad flags %u, %u outside 0..1", tuning[8],
+           tuning[9]);
   for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = tuning[i];
   return ZKVC_OK;
 }

@@ -39,7 +39,7 @@ __global__ void k_psq(const Fr* ak, const Fr* bk, const Fr* ypart, int a, int n,
                       int* flags);
 __global__ void k_randomness(Fr* rs, int* flags);
 __global__ void k_check_h(const Fr* H, size_t N, int* flags);
-__global__ void k_chains(const GlvScalar* gs, const G1J* small, G1J* chain);
+__global__ void k_chains(const GlvScalar* gs, const G1J* small, G1J* chain, G1J* cpart, uint8_t* proof);
 
 static constexpr uint32_t COEF_ONE = 0, COEF_NEG = 1, COEF_Z0 = 2;
 static constexpr uint32_t LONG_ROW = 64;
@@ -893,7 +893,7 @@ int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const u
   ZK_CUDA(cudaGetLastError());
   // A, the private part of C and B1 (all witness scalars known now)
   ZK_TRY(msm_run<Fp>(P.pre, pk->g1, B.ws_pre, B.ws_pre_bytes, B.pre, st));
-  k_chains<<<1, 32, 0, st>>>(B.glv, B.pre, B.chain); ZK_COUNT_LAUNCH();
+  k_chains<<<1, 64, 0, st>>>(B.glv, B.pre, B.chain, nullptr, nullptr); ZK_COUNT_LAUNCH();
   // quotient and H
   const NttDomain* d = pk->dom;
   ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, st));

@@ -125,7 +125,9 @@ __device__ __forceinline__ XYZZ<F> p_add_affine_quad_body(const XYZZ<F>& p, cons
   return {X3, Y3, ZZ3, ZZZ3};
 }
 
+static __device__ __noinline__ G1J p_add_affine_quad_g1(G1J p, G1A q) { return p_add_affine_quad_body(p, q); }
 static __device__ __noinline__ G2J p_add_affine_quad_g2(G2J p, G2A q) { return p_add_affine_quad_body(p, q); }
+__device__ __forceinline__ G1J p_add_affine_quad(const G1J& p, const G1A& q) { return p_add_affine_quad_g1(p, q); }
 __device__ __forceinline__ G2J p_add_affine_quad(const G2J& p, const G2A& q) { return p_add_affine_quad_g2(p, q); }
 
 static __device__ __noinline__ G1J p_dbl_quad_g1(G1J p) { return p_dbl_quad_body(p); }

@@ -102,8 +102,8 @@ struct zkvc_pk {
   // elements per block (0 = 10), when the side MSM starts (the rest MSM in fold mode, the
   // small-digit MSM in chain mode: 0 at once, 1 after the NTTs, 2 after the H
   // accumulation), zkvc_prove's mode (ZKVC_PROVE_FOLD or _CHAIN), when the G2 MSM starts
-  // (0 at once, 1 after the NTTs)
-  uint32_t prove_tune[ZKVC_PK_TUNING_LEN] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // (0 at once, 1 after the NTTs), quad-lane chunks in the H and small-digit runs (0, 1)
+  uint32_t prove_tune[ZKVC_PK_TUNING_LEN] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 struct zkvc_vk {

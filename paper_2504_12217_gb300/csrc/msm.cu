@@ -145,6 +145,7 @@ int msm_plan_finalize(MsmPlan& p) {
   ZK_CHECK(p.chunk >= 1 && p.chunk <= 1024, ZKVC_EINVAL, "msm: chunk of %u terms", p.chunk);
   ZK_CHECK(p.tune.accum_threads >= 32 && p.tune.accum_threads <= 256 && p.tune.accum_threads % 32 == 0,
            ZKVC_EINVAL, "msm: %u accumulation threads", p.tune.accum_threads);
+  ZK_CHECK(p.tune.lanes == 1 || p.tune.lanes == 4, ZKVC_EINVAL, "msm: %u lanes per chunk", p.tune.lanes);
   p.slots = slot;
   p.points = pts;
   // outputs with their own base arrays: every output must name one, and all must have
@@ -394,26 +395,24 @@ __device__ __forceinline__ XYZZ<F> ld_point_cg(const XYZZ<F>* p) {
   return r;
 }
 
-// Lanes per chunk: G2 point formulas are long enough that a quad of lanes per chunk
-// (coop.cuh) pays in the latency-bound G2 runs of a proof; G1 chunks get one thread.
-template <class F>
-struct ChunkLanes {
-  static constexpr int value = sizeof(F) > 32 ? 4 : 1;
-};
-
-__device__ __forceinline__ XYZZ<Fp> madd_lanes(const XYZZ<Fp>& p, const Affine<Fp>& q) { return p_add_affine(p, q); }
-__device__ __forceinline__ XYZZ<Fp2> madd_lanes(const XYZZ<Fp2>& p, const Affine<Fp2>& q) {
-  return p_add_affine_quad(p, q);
+// Lanes per chunk (QL): one thread, or a quad of lanes (coop.cuh) whose point operations
+// have a third of a thread's latency for four times the lanes.  G2 chunks always take a
+// quad (the G2 runs of a proof are latency-bound); a G1 run takes what its tuning says
+// (MsmTune::lanes: quads pay where the run is latency-bound, one thread where it fills
+// the GPU).
+template <int QL, class F>
+__device__ __forceinline__ XYZZ<F> madd_lanes(const XYZZ<F>& p, const Affine<F>& q) {
+  if constexpr (QL == 1) return p_add_affine(p, q);
+  else return p_add_affine_quad(p, q);
 }
 
 // level 0: chunk q sums up to T0 consecutive terms of its bucket (mixed additions)
-template <class F>
+template <class F, int QL>
 __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ offs,
                                                 const uint32_t* __restrict__ choff, const uint32_t* __restrict__ chunk_key,
                                                 uint32_t K, uint32_t T0, const Affine<F>* __restrict__ bases,
                                                 const Affine<F>* const* __restrict__ obases, int key_shift,
                                                 XYZZ<F>* part) {
-  constexpr int QL = ChunkLanes<F>::value;
   uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
   if (q >= choff[K]) return;  // uniform within a quad
   uint32_t k = chunk_key[q];
@@ -426,7 +425,7 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
     uint32_t v = sorted[p];
     Affine<F> P = ld_field(bases + (v & 0x7fffffffu));
     if (v >> 31) P.y = f_neg(P.y);
-    acc = madd_lanes(acc, P);
+    acc = madd_lanes<QL>(acc, P);
   }
   if (QL == 1 || quad_lane() == 0) st_field(part + q, acc);
 }
@@ -440,12 +439,11 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
 // position: a climber stores only sums it has changed (a chunk's own sum is there from
 // the accumulation launch).  The bucket total ends in part[choff[k]].  `arrive` holds one
 // zeroed counter per chunk.  The counter's fetch-and-add releases the climber's store
-// and acquires its sibling's.  G2 chunks get a quad of lanes each, G1 chunks one thread.
-template <class F>
+// and acquires its sibling's.  QL lanes per chunk as in the accumulation.
+template <class F, int QL>
 __global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ choff,
                                                    const uint32_t* __restrict__ chunk_key, uint32_t K,
                                                    XYZZ<F>* part, uint32_t* arrive) {
-  constexpr int QL = ChunkLanes<F>::value;
   const uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
   if (q >= choff[K]) return;  // uniform within a quad
   const bool lead = QL == 1 || quad_lane() == 0;
@@ -819,18 +817,26 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   ZK_CUDA(cudaMemsetAsync(L.arrive, 0, size_t(L.qmax) * sizeof(uint32_t), st));
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
   const uint32_t at = p.tune.accum_threads;
-  unsigned qb = (unsigned)((uint64_t(L.qmax) * ChunkLanes<F>::value + at - 1) / at);
+  const int lanes = sizeof(F) > 32 ? 4 : (p.tune.lanes == 4 ? 4 : 1);
+  unsigned qb = (unsigned)((uint64_t(L.qmax) * lanes + at - 1) / at);
+  unsigned fb = (unsigned)((uint64_t(L.qmax) * lanes + 127) / 128);
   if (accum_stage >= 0) prof_mark(accum_stage, true, st);
-  k_accum0<F><<<qb, at, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases,
-                                 reinterpret_cast<const Affine<F>* const*>(L.obases), p.key_shift, part); ZK_COUNT_LAUNCH();
+  const auto* ob = reinterpret_cast<const Affine<F>* const*>(L.obases);
+  if (lanes == 4)
+    k_accum0<F, 4><<<qb, at, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases, ob, p.key_shift, part);
+  else if constexpr (sizeof(F) <= 32)
+    k_accum0<F, 1><<<qb, at, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases, ob, p.key_shift, part);
+  ZK_COUNT_LAUNCH();
   if (accum_stage >= 0) {
     prof_mark(accum_stage, false, st);
     if (uint32_t* hu = prof_units(accum_stage)) ZK_CUDA(cudaMemcpyAsync(hu, L.offs + K, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   }
   ZK_CUDA(cudaGetLastError());
   if (after_accum) ZK_CUDA(cudaEventRecord(after_accum, st));
-  k_fold_tree<F><<<(unsigned)((uint64_t(L.qmax) * ChunkLanes<F>::value + 127) / 128), 128, 0, st>>>(L.choff, L.chunk_key, K,
-                                                                                                 part, L.arrive);
+  if (lanes == 4)
+    k_fold_tree<F, 4><<<fb, 128, 0, st>>>(L.choff, L.chunk_key, K, part, L.arrive);
+  else if constexpr (sizeof(F) <= 32)
+    k_fold_tree<F, 1><<<fb, 128, 0, st>>>(L.choff, L.chunk_key, K, part, L.arrive);
   ZK_COUNT_LAUNCH();
   // sum_v v B_v per (output, window) by bit decomposition
   XYZZ<F>* Sl = reinterpret_cast<XYZZ<F>*>(L.S);

@@ -45,6 +45,7 @@ struct MsmOut {
 struct MsmTune {
   uint32_t chunk = 0;          // terms per level-0 chunk (0: 16 below 2M slots, else 32)
   uint32_t accum_threads = 128;
+  uint32_t lanes = 1;          // G1 lanes per chunk: 1 or 4 (a quad); G2 always uses 4
 };
 
 struct MsmPlan {

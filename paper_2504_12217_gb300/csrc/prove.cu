@@ -82,11 +82,16 @@ __global__ void k_randomness(Fr* rs, int* flags) {
 // Chain mode: s A and r B1 (small-run outputs 0 and 2) with the scalars split by the GLV
 // endomorphism on the host (gs[0] = s, gs[1] = r): four quads compute s1 A, s2 phi(A),
 // r1 B1 and r2 phi(B1) side by side (phi(x, y) = (beta x, y)), then two quads add the
-// pairs.  One block of 32 threads.
-__global__ void k_chains(const GlvScalar* __restrict__ gs, const G1J* __restrict__ small, G1J* chain) {
+// pairs.  Meanwhile the second warp encodes A (bytes 0..63 of the proof: its inversion
+// overlaps the chains).  Then the H-free part of C, small[1] + s A + r B1, goes to cpart.
+// (proof and cpart may be null: the generic engine encodes A and C itself.)  One block
+// of 64 threads.
+__global__ void k_chains(const GlvScalar* __restrict__ gs, const G1J* __restrict__ small, G1J* chain, G1J* cpart,
+                         uint8_t* proof) {
   __shared__ G1J T[4][16];
   __shared__ G1J part[4];
   const int q = threadIdx.x >> 2;
+  if (threadIdx.x == 32 && proof) encode_g1(ld_field(small), proof);
   if (q < 4) {
     G1J P = ld_field(small + (q < 2 ? 0 : 2));
     if (q & 1) {
@@ -101,7 +106,18 @@ __global__ void k_chains(const GlvScalar* __restrict__ gs, const G1J* __restrict
   __syncthreads();
   if (q == 0 || q == 2) {
     const G1J S = p_add_quad(ld_field(part + q), ld_field(part + q + 1));
-    if (quad_lane() == 0) st_field(chain + (q >> 1), S);
+    if (quad_lane() == 0) st_field(part + q, S);
+  }
+  __syncthreads();
+  if (q == 0) {
+    if (quad_lane() == 0) {
+      st_field(chain, ld_field(part));
+      st_field(chain + 1, ld_field(part + 2));
+    }
+    if (cpart) {
+      const G1J c = p_add_quad(ld_field(small + 1), p_add_quad(ld_field(part), ld_field(part + 2)));
+      if (quad_lane() == 0) st_field(cpart, c);
+    }
   }
 }
 
@@ -248,6 +264,8 @@ static void plans(const zkvc_pk* pk, int mode, const int8_t* dX, const int32_t* 
   P->rest.tune.chunk = pk->prove_tune[1];
   P->h.tune.chunk = pk->prove_tune[2];
   P->g2.tune.chunk = pk->prove_tune[3];
+  P->h.tune.lanes = pk->prove_tune[8] ? 4 : 1;
+  P->small.tune.lanes = pk->prove_tune[9] ? 4 : 1;
   if (!chain) msm_plan_finalize(P->rest);
   msm_plan_finalize(P->small);
   msm_plan_finalize(P->h);
@@ -430,10 +448,11 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   if (chain && pk->prove_tune[5] == 2) ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->h_accum, 0));
   ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
   if (chain) {
-    k_chains<<<1, 32, 0, side->st[1]>>>(B.glv, B.res_small, B.res_chain); ZK_COUNT_LAUNCH();
+    k_chains<<<1, 64, 0, side->st[1]>>>(B.glv, B.res_small, B.res_chain, B.cpart, B.proof); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
+  } else {
+    k_encode_a<<<1, 32, 0, side->st[1]>>>(B.res_small, nullptr, B.cpart, B.proof); ZK_COUNT_LAUNCH();
   }
-  k_encode_a<<<1, 32, 0, side->st[1]>>>(B.res_small, chain ? B.res_chain : nullptr, B.cpart, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaEventRecord(side->join[1], side->st[1]));
   if (!chain) {
     // the full-scalar G1 terms that need no h, on side stream 2, then their term of C.
@@ -490,7 +509,7 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
   static const uint32_t kCand[] = {2, 4, 8, 16, 32, 64};
   static const uint32_t kElog[] = {8, 9, 10, 11};
   static const uint32_t kRest[] = {0, 1, 2};
-  static const uint32_t kG2[] = {0, 1};
+  static const uint32_t kBin[] = {0, 1};
   uint32_t saved[ZKVC_PK_TUNING_LEN];
   for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) saved[i] = pk->prove_tune[i];
   for (int i = 0; i < 4; i++) pk->prove_tune[i] = 2;  // the largest workspace of all candidates
@@ -537,10 +556,11 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
     const int order[4] = {3, 0, 2, 1};  // g2, small, h, rest
     for (int sweep = 0; sweep < 2; sweep++) {
     ZK_TRY(measure(m, best_ms));
-    for (int oi = 0; oi < 7; oi++) {
-      // then the NTT block, the side MSM's start, the G2 MSM's start (index 6 is the mode)
-      const int r = oi < 4 ? order[oi] : oi == 6 ? 7 : oi;
-      const uint32_t* cand = r < 4 ? kCand : r == 4 ? kElog : r == 5 ? kRest : kG2;
+    for (int oi = 0; oi < 9; oi++) {
+      // then the NTT block, the side MSM's start, the G2 MSM's start, quads for the H and
+      // small-digit accumulations (index 6 is the mode)
+      const int r = oi < 4 ? order[oi] : oi < 6 ? oi : oi + 1;
+      const uint32_t* cand = r < 4 ? kCand : r == 4 ? kElog : r == 5 ? kRest : kBin;
       const int ncand = r < 4 ? 6 : r == 4 ? 4 : r == 5 ? 3 : 2;
       uint32_t best = pk->prove_tune[r];
       for (int ci = 0; ci < ncand; ci++) {
@@ -549,7 +569,7 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
         pk->prove_tune[r] = c;
         float ms = 0;
         ZK_TRY(measure(m, &ms));
-        if (ms < *best_ms) {
+        if (ms < 0.99f * *best_ms) {  // a gain within timing noise does not move the setting
           *best_ms = ms;
           best = c;
         }

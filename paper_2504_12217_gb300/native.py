@@ -455,13 +455,13 @@ ZKVC_PROVE_CHAIN = 1
 ZKVC_PROVE_AUTO = 2
 
 
-ZKVC_PK_TUNING_LEN = 8
+ZKVC_PK_TUNING_LEN = 10
 
 
 def zkvc_pk_autotune(pk, X, W, rs, mode=0):
     """Tune the key's launch shape for one-proof latency on these inputs; returns the
     chosen [small, rest, h, g2 chunk terms, NTT log2 elements per block, side-MSM start,
-    prover mode, G2-MSM start].  mode: ZKVC_PROVE_FOLD, ZKVC_PROVE_CHAIN or ZKVC_PROVE_AUTO (both)."""
+    prover mode, G2-MSM start, H-run quads, small-run quads].  mode: ZKVC_PROVE_FOLD, ZKVC_PROVE_CHAIN or ZKVC_PROVE_AUTO (both)."""
     arr = (ctypes.c_uint32 * ZKVC_PK_TUNING_LEN)()
     rsb = ctypes.create_string_buffer(bytes(rs), 64)
     check(lib().zkvc_pk_autotune(pk.handle, mode, _dev_ptr(X), _dev_ptr(W), rsb, _stream(), arr))
