@@ -91,7 +91,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -402,8 +402,12 @@ def run_gpu(args):
         ("k_accum0<G2>", w2, g2["ms"], g2["calls"])
     peak = SMS * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     achieved = (work / calls) / (ms / calls / 1e3) / 1e12 if ms > 0 else 0.0
+    # DRAM bytes (read + write) of one H-query accumulation launch, from one ncu capture per
+    # chunk setting of this workload (dram__bytes_read.sum + dram__bytes_write.sum)
+    h_traffic = {0: 75253248, 16: 75253248, 32: 74893568, 64: 74598400}
+    traffic = h_traffic.get(tuning[2]) if dom.startswith("k_accum0<G1>") else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (nominal unit count and max clock)",
                 "algorithmic_imad_per_launch": work / max(calls, 1),
                 "launch_ms": ms / max(calls, 1)}
@@ -800,7 +804,7 @@ def run_ablation(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
