@@ -295,8 +295,8 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const ui
 /* Latency tuning of the one-proof prover for a key: zkvc_pk_autotune times whole proofs
  * of the given inputs (device X, W; host rs) in `mode` while it varies the launch shape
  * -- ZKVC_PK_TUNING_LEN values: the terms per level-0 chunk of each MSM run (small-scalar
- * G1, rest G1, H, G2; 0 = the default rule: 16 terms below 2 M bucket terms per run, else
- * 32), log2 of the NTT elements per block (8..11; 0 = 10), when the side MSM starts (the
+ * G1, rest G1, H, G2; 0 = the default rule: about two chunks per bucket, at least 16 terms
+ * and about 40 k chunks), log2 of the NTT elements per block (8..11; 0 = 10), when the side MSM starts (the
  * full-scalar "rest" MSM in fold mode, the small-digit MSM in chain mode: 0 at once, 1
  * after the NTTs, 2 after the H MSM's bucket accumulation), the mode zkvc_prove uses
  * (ZKVC_PROVE_FOLD or ZKVC_PROVE_CHAIN), when the G2 MSM starts (0, 1), and whether the H

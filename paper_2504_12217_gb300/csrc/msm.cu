@@ -141,13 +141,26 @@ int msm_plan_finalize(MsmPlan& p) {
     p.max_nd = std::max(p.max_nd, nd);
   }
   ZK_CHECK(slot < 0xffffffffull, ZKVC_EINVAL, "msm: too many digit slots");
-  p.chunk = p.tune.chunk ? p.tune.chunk : (slot < (2u << 20) ? 16u : 32u);
+  // default chunk: about two chunks per bucket (serial sums keep every lane busy, while
+  // the fold tree loses half its lanes per level), but at least ~40 k chunks so that the
+  // accumulation fills the GPU, and 16 at the least
+  if (p.tune.chunk) {
+    p.chunk = p.tune.chunk;
+  } else {
+    const uint64_t per_bucket = slot / (2ull * std::max<uint32_t>(key, 1u));
+    const uint64_t fill = slot / 40960ull;
+    p.chunk = (uint32_t)std::max<uint64_t>(16, std::min<uint64_t>(std::min(per_bucket, fill), 1024));
+  }
   ZK_CHECK(p.chunk >= 1 && p.chunk <= 1024, ZKVC_EINVAL, "msm: chunk of %u terms", p.chunk);
   ZK_CHECK(p.tune.accum_threads >= 32 && p.tune.accum_threads <= 256 && p.tune.accum_threads % 32 == 0,
            ZKVC_EINVAL, "msm: %u accumulation threads", p.tune.accum_threads);
-  ZK_CHECK(p.tune.lanes == 1 || p.tune.lanes == 4, ZKVC_EINVAL, "msm: %u lanes per chunk", p.tune.lanes);
+  ZK_CHECK(p.tune.lanes == 0 || p.tune.lanes == 1 || p.tune.lanes == 4, ZKVC_EINVAL, "msm: %u lanes per chunk",
+           p.tune.lanes);
   p.slots = slot;
   p.points = pts;
+  // lanes per chunk: quads where the run has too few chunks to fill the GPU (their point
+  // operations have a third of a thread's latency), one thread where it is throughput-bound
+  p.lanes = p.tune.lanes ? p.tune.lanes : (slot / p.chunk < 40960 ? 4u : 1u);
   // outputs with their own base arrays: every output must name one, and all must have
   // the same power-of-two key count, so that a key's output is key >> key_shift
   p.key_shift = -1;
@@ -817,14 +830,14 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   ZK_CUDA(cudaMemsetAsync(L.arrive, 0, size_t(L.qmax) * sizeof(uint32_t), st));
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
   const uint32_t at = p.tune.accum_threads;
-  const int lanes = sizeof(F) > 32 ? 4 : (p.tune.lanes == 4 ? 4 : 1);
+  const int lanes = p.lanes == 4 ? 4 : 1;
   unsigned qb = (unsigned)((uint64_t(L.qmax) * lanes + at - 1) / at);
   unsigned fb = (unsigned)((uint64_t(L.qmax) * lanes + 127) / 128);
   if (accum_stage >= 0) prof_mark(accum_stage, true, st);
   const auto* ob = reinterpret_cast<const Affine<F>* const*>(L.obases);
   if (lanes == 4)
     k_accum0<F, 4><<<qb, at, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases, ob, p.key_shift, part);
-  else if constexpr (sizeof(F) <= 32)
+  else
     k_accum0<F, 1><<<qb, at, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases, ob, p.key_shift, part);
   ZK_COUNT_LAUNCH();
   if (accum_stage >= 0) {
@@ -835,7 +848,7 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   if (after_accum) ZK_CUDA(cudaEventRecord(after_accum, st));
   if (lanes == 4)
     k_fold_tree<F, 4><<<fb, 128, 0, st>>>(L.choff, L.chunk_key, K, part, L.arrive);
-  else if constexpr (sizeof(F) <= 32)
+  else
     k_fold_tree<F, 1><<<fb, 128, 0, st>>>(L.choff, L.chunk_key, K, part, L.arrive);
   ZK_COUNT_LAUNCH();
   // sum_v v B_v per (output, window) by bit decomposition

@@ -43,9 +43,9 @@ struct MsmOut {
 
 // Launch-shape knobs of a run (chosen by the batch autotuner; defaults otherwise).
 struct MsmTune {
-  uint32_t chunk = 0;          // terms per level-0 chunk (0: 16 below 2M slots, else 32)
+  uint32_t chunk = 0;          // terms per level-0 chunk (0: the default rule of msm_plan_finalize)
   uint32_t accum_threads = 128;
-  uint32_t lanes = 1;          // G1 lanes per chunk: 1 or 4 (a quad); G2 always uses 4
+  uint32_t lanes = 0;          // lanes per chunk: 1, 4 (a quad), 0 = by the run's size
 };
 
 struct MsmPlan {
@@ -57,6 +57,7 @@ struct MsmPlan {
   uint32_t points = 0;
   uint32_t max_nd = 0;
   uint32_t chunk = 0;          // planner: the level-0 chunk in use
+  uint32_t lanes = 1;          // planner: lanes per chunk in use
   int32_t key_shift = -1;      // planner: log2 of the keys per output when outputs carry
                                // their own bases (all outputs then have equal 2^k keys)
 };

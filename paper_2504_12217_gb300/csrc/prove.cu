@@ -266,6 +266,8 @@ static void plans(const zkvc_pk* pk, int mode, const int8_t* dX, const int32_t* 
   P->g2.tune.chunk = pk->prove_tune[3];
   P->h.tune.lanes = pk->prove_tune[8] ? 4 : 1;
   P->small.tune.lanes = pk->prove_tune[9] ? 4 : 1;
+  P->rest.tune.lanes = 1;
+  P->g2.tune.lanes = 4;  // a proof's G2 run is latency-bound
   if (!chain) msm_plan_finalize(P->rest);
   msm_plan_finalize(P->small);
   msm_plan_finalize(P->h);
