@@ -7,7 +7,7 @@
 // formulas have independent products: add-2008-s has four rounds of at most four
 // independent products, dbl-2008-s-1 three.  So four lanes hold the same operands, each
 // computes one product of a round, and the products are broadcast with warp shuffles
-// before the next round; all four lanes end with the same result.
+// before the products that depend on them; all four lanes end with the same result.
 //
 // Every lane of a quad must call these functions with the same operands (the branches on
 // infinity and on equal x are then uniform within the quad).  The shuffles name only the
