@@ -1,8 +1,8 @@
 // Point additions and doublings spread over a quad of four lanes.
 //
 // One thread doing an XYZZ addition runs its 14 Montgomery products back to back, and a
-// product's dependent carry chain is long: a lone thread needs about 10 us per G1
-// addition.  Where few sums remain (the upper levels of the bucket-sum trees, the 2^b
+// product costs a lone thread about 1,300 cycles (the multiply issue rate of one warp):
+// a lone thread needs about 9 us per G1 addition.  Where few sums remain (the upper levels of the bucket-sum trees, the 2^b
 // scalings, the window combination) that latency, not throughput, sets the time.  The
 // formulas have independent products: add-2008-s has four rounds of at most four
 // independent products, dbl-2008-s-1 three.  So four lanes hold the same operands, each
