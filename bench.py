@@ -635,7 +635,9 @@ def run_served(args):
     rng = random.Random(inputs.SEED_CFG[5] + rank)
     rates = args.rates
     budget = args.server_budget_gib << 30
-    srv = nv.Server(pks, slots=args.server_slots, mem_budget=budget, policy=nv.ZKVC_SERVER_ADAPTIVE)
+    policy = {"adaptive": nv.ZKVC_SERVER_ADAPTIVE, "fold": nv.ZKVC_SERVER_FOLD, "chain": nv.ZKVC_SERVER_CHAIN}[
+        args.server_policy]
+    srv = nv.Server(pks, slots=args.server_slots, mem_budget=budget, policy=policy)
     nv.zkvc_set_wait_timeout_ms(600000)
     # warm up every shape once (domain tables, side streams, caches)
     for k in range(len(shapes)):
@@ -710,7 +712,8 @@ def run_served(args):
         "dtype": "u32 limbs (exact Fr/Fp arithmetic)", "data": "synthetic",
         "config": {"workload": "crpc_groth16_bn254_served_poisson", "shapes": len(shapes),
                    "rates_rps": rates, "slots": args.server_slots, "mem_budget_bytes": budget,
-                   "policy": "adaptive (fold when idle, chain when shared)",
+                   "policy": {"adaptive": "adaptive (fold when idle, chain when shared)", "fold": "fold",
+                              "chain": "chain"}[args.server_policy],
                    "latency": "host wall clock from submit to result (includes H2D of X, W and D2H of Y, proof)"},
         "served": per_rate,
         "plain_one_proof_path": {"proofs_per_s": 1e3 / statistics.mean(plain_ms), "p50_ms": statistics.median(ps),
@@ -822,6 +825,8 @@ def main():
     ap.add_argument("--max-requests", type=int, default=1200)
     ap.add_argument("--server-slots", type=int, default=8)
     ap.add_argument("--server-budget-gib", type=int, default=48)
+    ap.add_argument("--server-policy", choices=["adaptive", "fold", "chain"], default="chain",
+                    help="served: prover mode per request")
     ap.add_argument("--batch-count", type=int, default=0, help="batched: only the K smallest instances")
     ap.add_argument("--key-tuning", type=int, nargs=10, default=None,
                     help="plain: impose the key's launch shape (zkvc_pk_set_tuning), skip the autotuner")
