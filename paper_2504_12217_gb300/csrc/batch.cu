@@ -396,11 +396,7 @@ static int run_ntts(zkvc_batch* B, cudaStream_t st) {
   for (const NttGroup& gr : B->groups) {
     const size_t N = gr.N;
     const int m = gr.m;
-    ZK_TRY(ntt_dif(gr.ev, 3 * m, N, gr.d, true, SC_NONE, SC_NG, false, st, B->tune.elog));
-    ZK_TRY(ntt_dit(gr.ev, 3 * m, N, gr.d, false, st, B->tune.elog));
-    ZK_TRY(ntt_quotient(gr.ev, gr.ev + size_t(m) * N, gr.ev + size_t(2 * m) * N, gr.ev + size_t(3 * m) * N, gr.d, st,
-                        size_t(m) * N));
-    ZK_TRY(ntt_dif(gr.ev + size_t(3 * m) * N, m, N, gr.d, true, SC_NONE, SC_NGI, false, st, B->tune.elog));
+    ZK_TRY(ntt_quotient_chain(gr.ev, m, N, gr.d, st, B->tune.elog));
   }
   return ZKVC_OK;
 }

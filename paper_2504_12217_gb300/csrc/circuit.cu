@@ -896,10 +896,7 @@ int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const u
   k_chains<<<1, 64, 0, st>>>(B.glv, B.pre, B.chain, nullptr, nullptr); ZK_COUNT_LAUNCH();
   // quotient and H
   const NttDomain* d = pk->dom;
-  ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, st));
-  ZK_TRY(ntt_dit(Aev, 3, N, d, false, st));
-  ZK_TRY(ntt_quotient(Aev, Bev, Cev, Hev, d, st));
-  ZK_TRY(ntt_dif(Hev, 1, N, d, true, SC_NONE, SC_NGI, false, st));
+  ZK_TRY(ntt_quotient_chain(Aev, 1, N, d, st));
   k_check_h<<<1, 32, 0, st>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
   ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.hres, st));
   ZK_CUDA(cudaStreamWaitEvent(st, t_gen.join, 0));

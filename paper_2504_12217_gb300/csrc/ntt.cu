@@ -13,9 +13,11 @@
 // the coset shift g^i and 1/N are applied at the bit-reversed store of the inverse
 // transforms.  Twiddles are read from a table omega^e (e < N/2), L2-resident for the
 // proof domains.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 #include "ntt.h"
 
@@ -154,53 +156,84 @@ static ScaleTabs tabs_of(const NttDomain* d) {
   return {d->g_lo, d->gi_lo, d->g_hi, d->g_hi_n, d->gi_hi_n, d->consts};
 }
 
-// One pass of k stages over G groups per block; see the file comment.
-template <bool DIT>
-__global__ void __launch_bounds__(256) k_ntt_pass(Fr* data, size_t bstride, const Fr* __restrict__ tw,
-                                                  uint32_t logN, uint32_t s0, uint32_t k, uint32_t logG,
-                                                  int load_scale, int store_scale, int to_mont, ScaleTabs tabs) {
-  extern __shared__ uint32_t sm[];
-  const uint32_t G = 1u << logG;
-  const uint32_t E = G << k;
-  Fr* arr = data + size_t(blockIdx.y) * bstride;
-  const uint32_t L = logN;
-  const uint32_t sbits = DIT ? s0 : (L - s0 - k);
-  const size_t smask = (size_t(1) << sbits) - 1;
-  const size_t gid0 = size_t(blockIdx.x) << logG;
+// One pass: k consecutive radix-2 stages from stage s0, over G = 2^logG groups of 2^k
+// elements per block (E = G 2^k elements, staged limb-major in shared memory).
+struct PassGeo {
+  uint32_t L, s0, k, logG;
+};
 
+// global index of the block's e-th staged element
+template <bool DIT>
+__device__ __forceinline__ size_t pass_index(const PassGeo& g, size_t gid0, uint32_t e) {
+  const uint32_t G = 1u << g.logG;
+  const uint32_t gg = e & (G - 1), j = e >> g.logG;
+  const size_t gid = gid0 + gg;
+  const uint32_t sbits = DIT ? g.s0 : (g.L - g.s0 - g.k);
+  const size_t lo = gid & ((size_t(1) << sbits) - 1), hi = gid >> sbits;
+  const size_t base = DIT ? ((hi << (g.s0 + g.k)) | lo) : ((hi << (g.L - g.s0)) | lo);
+  return base + (size_t(j) << sbits);
+}
+
+__device__ __forceinline__ Fr sm_get(const uint32_t* sm, uint32_t E, uint32_t e) {
+  Fr x;
+#pragma unroll
+  for (int l = 0; l < 8; l++) x.v[l] = sm[l * E + e];
+  return x;
+}
+__device__ __forceinline__ void sm_put(uint32_t* sm, uint32_t E, uint32_t e, const Fr& x) {
+#pragma unroll
+  for (int l = 0; l < 8; l++) sm[l * E + e] = x.v[l];
+}
+
+template <bool DIT>
+__device__ __forceinline__ void pass_load(const Fr* arr, const PassGeo& g, size_t gid0, uint32_t* sm, int load_scale,
+                                          int to_mont, const ScaleTabs& tabs) {
+  const uint32_t E = 1u << (g.logG + g.k);
   for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
-    uint32_t g = e & (G - 1), j = e >> logG;
-    size_t gid = gid0 + g;
-    size_t lo = gid & smask, hi = gid >> sbits;
-    size_t base = DIT ? ((hi << (s0 + k)) | lo) : ((hi << (L - s0)) | lo);
-    size_t idx = base + (size_t(j) << sbits);
+    const size_t idx = pass_index<DIT>(g, gid0, e);
     Fr x = ld_field(arr + idx);
     if (to_mont) x = f_to_mont(x);
     if (load_scale) x = f_mul(x, scale_factor(tabs, load_scale, (uint32_t)idx));
-#pragma unroll
-    for (int l = 0; l < 8; l++) sm[l * E + e] = x.v[l];
+    sm_put(sm, E, e, x);
   }
-  __syncthreads();
+}
 
+template <bool DIT>
+__device__ __forceinline__ void pass_store(Fr* arr, const PassGeo& g, size_t gid0, const uint32_t* sm, int store_scale,
+                                           const ScaleTabs& tabs) {
+  const uint32_t E = 1u << (g.logG + g.k);
+  for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
+    const size_t idx = pass_index<DIT>(g, gid0, e);
+    Fr x = sm_get(sm, E, e);
+    if (store_scale) x = f_mul(x, scale_factor(tabs, store_scale, brev_bits((uint32_t)idx, g.L)));
+    st_field(arr + idx, x);
+  }
+}
+
+// The pass's k stages on NPOLY staged arrays (8 E words apart); barriers between stages
+// (the first one orders the loads before it).
+template <bool DIT, int NPOLY>
+__device__ __forceinline__ void pass_stages(uint32_t* sm, const PassGeo& g, size_t gid0, const Fr* tw) {
+  const uint32_t G = 1u << g.logG, E = G << g.k, L = g.L, logG = g.logG;
+  const uint32_t sbits = DIT ? g.s0 : (L - g.s0 - g.k);
+  const size_t smask = (size_t(1) << sbits) - 1;
   const uint32_t nbf = E >> 1;
-  for (uint32_t t = 0; t < k; t++) {
-    const uint32_t s = s0 + t;
-    const uint32_t logh = DIT ? t : (k - 1 - t);
+  __syncthreads();
+  for (uint32_t t = 0; t < g.k; t++) {
+    const uint32_t s = g.s0 + t;
+    const uint32_t logh = DIT ? t : (g.k - 1 - t);
     const uint32_t h = 1u << logh;
-    for (uint32_t bf = threadIdx.x; bf < nbf; bf += blockDim.x) {
-      uint32_t g = bf & (G - 1), q = bf >> logG;
-      uint32_t qh = q & (h - 1);
-      uint32_t ju = ((q >> logh) << (logh + 1)) + qh;
-      uint32_t pu = (ju << logG) + g, pv = ((ju + h) << logG) + g;
-      size_t lo = (gid0 + g) & smask;
-      size_t etw = DIT ? ((((size_t)qh << s0) + lo) << (L - 1 - s)) : ((((size_t)qh << sbits) + lo) << s);
-      Fr w = ld_field(tw + etw);
-      Fr u, v;
-#pragma unroll
-      for (int l = 0; l < 8; l++) {
-        u.v[l] = sm[l * E + pu];
-        v.v[l] = sm[l * E + pv];
-      }
+    for (uint32_t bfa = threadIdx.x; bfa < nbf * (uint32_t)NPOLY; bfa += blockDim.x) {
+      const uint32_t poly = NPOLY == 1 ? 0u : bfa / nbf, bf = bfa - poly * nbf;
+      uint32_t* smp = sm + size_t(poly) * 8 * E;
+      const uint32_t gg = bf & (G - 1), q = bf >> logG;
+      const uint32_t qh = q & (h - 1);
+      const uint32_t ju = ((q >> logh) << (logh + 1)) + qh;
+      const uint32_t pu = (ju << logG) + gg, pv = ((ju + h) << logG) + gg;
+      const size_t lo = (gid0 + gg) & smask;
+      const size_t etw = DIT ? ((((size_t)qh << g.s0) + lo) << (L - 1 - s)) : ((((size_t)qh << sbits) + lo) << s);
+      const Fr w = ld_field(tw + etw);
+      Fr u = sm_get(smp, E, pu), v = sm_get(smp, E, pv);
       Fr a, b;
       if (DIT) {
         v = f_mul(v, w);
@@ -210,27 +243,73 @@ __global__ void __launch_bounds__(256) k_ntt_pass(Fr* data, size_t bstride, cons
         a = f_add(u, v);
         b = f_mul(f_sub(u, v), w);
       }
-#pragma unroll
-      for (int l = 0; l < 8; l++) {
-        sm[l * E + pu] = a.v[l];
-        sm[l * E + pv] = b.v[l];
-      }
+      sm_put(smp, E, pu, a);
+      sm_put(smp, E, pv, b);
     }
     __syncthreads();
   }
+}
 
+// One pass of k stages over G groups per block; see the file comment.
+template <bool DIT>
+__global__ void __launch_bounds__(256) k_ntt_pass(Fr* data, size_t bstride, const Fr* __restrict__ tw,
+                                                  uint32_t logN, uint32_t s0, uint32_t k, uint32_t logG,
+                                                  int load_scale, int store_scale, int to_mont, ScaleTabs tabs) {
+  extern __shared__ uint32_t sm[];
+  const PassGeo g{logN, s0, k, logG};
+  Fr* arr = data + size_t(blockIdx.y) * bstride;
+  const size_t gid0 = size_t(blockIdx.x) << logG;
+  pass_load<DIT>(arr, g, gid0, sm, load_scale, to_mont, tabs);
+  pass_stages<DIT, 1>(sm, g, gid0, tw);
+  pass_store<DIT>(arr, g, gid0, sm, store_scale, tabs);
+}
+
+// The turn of an inverse DIF transform into a forward DIT transform, in one pass: the
+// DIF's last pass (its k stages end at stage L - 1, groups of 2^k consecutive elements),
+// the inverse's scaling by the factor of each element's natural index, and the DIT's
+// first pass over the same groups.  Saves a global round trip and a launch.
+__global__ void __launch_bounds__(256) k_ntt_turn(Fr* data, size_t bstride, const Fr* __restrict__ tw_inv,
+                                                  const Fr* __restrict__ tw_fwd, uint32_t L, uint32_t k,
+                                                  uint32_t logG, int mid_scale, ScaleTabs tabs) {
+  extern __shared__ uint32_t sm[];
+  const PassGeo gdif{L, L - k, k, logG}, gdit{L, 0, k, logG};
+  Fr* arr = data + size_t(blockIdx.y) * bstride;
+  const size_t gid0 = size_t(blockIdx.x) << logG;
+  const uint32_t E = 1u << (logG + k);
+  pass_load<false>(arr, gdif, gid0, sm, SC_NONE, 0, tabs);
+  pass_stages<false, 1>(sm, gdif, gid0, tw_inv);
   for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
-    uint32_t g = e & (G - 1), j = e >> logG;
-    size_t gid = gid0 + g;
-    size_t lo = gid & smask, hi = gid >> sbits;
-    size_t base = DIT ? ((hi << (s0 + k)) | lo) : ((hi << (L - s0)) | lo);
-    size_t idx = base + (size_t(j) << sbits);
-    Fr x;
-#pragma unroll
-    for (int l = 0; l < 8; l++) x.v[l] = sm[l * E + e];
-    if (store_scale) x = f_mul(x, scale_factor(tabs, store_scale, brev_bits((uint32_t)idx, L)));
-    st_field(arr + idx, x);
+    const size_t idx = pass_index<false>(gdif, gid0, e);
+    sm_put(sm, E, e, f_mul(sm_get(sm, E, e), scale_factor(tabs, mid_scale, brev_bits((uint32_t)idx, L))));
   }
+  pass_stages<true, 1>(sm, gdit, gid0, tw_fwd);
+  pass_store<true>(arr, gdit, gid0, sm, SC_NONE, tabs);
+}
+
+// The quotient turn, one instance per blockIdx.y (arrays A_i, B_i, C_i, H_i of N
+// elements at i, m + i, 2m + i, 3m + i): the last DIT pass of A, B and C (strided groups),
+// h_ev = (A B - C) / (g^N - 1) on the staged elements, and the first DIF pass of the
+// inverse transform of h over the same groups; only H is written.  Small grids get up
+// to three times the threads of a single-array pass (the three forward passes side by
+// side), large ones one array's worth.
+__global__ void __launch_bounds__(768) k_ntt_quotient_turn(Fr* ev, uint32_t m, size_t N, const Fr* __restrict__ tw_fwd,
+                                                           const Fr* __restrict__ tw_inv, uint32_t L, uint32_t k,
+                                                           uint32_t logG, ScaleTabs tabs) {
+  extern __shared__ uint32_t sm[];
+  const PassGeo gdit{L, L - k, k, logG}, gdif{L, 0, k, logG};
+  const size_t gid0 = size_t(blockIdx.x) << logG;
+  const uint32_t E = 1u << (logG + k);
+  const size_t i = blockIdx.y;
+  for (int p = 0; p < 3; p++)
+    pass_load<true>(ev + (size_t(p) * m + i) * N, gdit, gid0, sm + size_t(p) * 8 * E, SC_NONE, 0, tabs);
+  pass_stages<true, 3>(sm, gdit, gid0, tw_fwd);
+  const Fr zinv = ld_field(tabs.consts + 1);
+  for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
+    const Fr a = sm_get(sm, E, e), b = sm_get(sm + 8 * E, E, e), c = sm_get(sm + 16 * E, E, e);
+    sm_put(sm, E, e, f_mul(f_sub(f_mul(a, b), c), zinv));
+  }
+  pass_stages<false, 1>(sm, gdif, gid0, tw_inv);
+  pass_store<false>(ev + (size_t(3) * m + i) * N, gdif, gid0, sm, SC_NONE, tabs);
 }
 
 static std::once_flag g_smem_once;
@@ -239,6 +318,8 @@ static void ntt_smem_attrs() {
   std::call_once(g_smem_once, [] {
     cudaFuncSetAttribute(k_ntt_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
     cudaFuncSetAttribute(k_ntt_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_ntt_turn, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_ntt_quotient_turn, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 << 10);
   });
 }
 
@@ -248,36 +329,122 @@ int ntt_init() {
   return ZKVC_OK;
 }
 
+// Stage split of an N = 2^L transform into passes of at most min(elog, 10) stages, the
+// first passes one stage longer.
+static std::vector<uint32_t> pass_split(uint32_t L, int elog) {
+  const uint32_t kmax = (uint32_t)elog < 10 ? (uint32_t)elog : 10;
+  const uint32_t P = (L + kmax - 1) / kmax;
+  const uint32_t kb = L / P, rem = L % P;
+  std::vector<uint32_t> ks(P);
+  for (uint32_t p = 0; p < P; p++) ks[p] = kb + (p < rem ? 1 : 0);
+  return ks;
+}
+
+// groups per block (log2) and the block shape of a pass of k stages
+struct PassShape {
+  uint32_t logG, E, threads;
+  dim3 grid;
+};
+static PassShape pass_shape(uint32_t L, uint32_t k, int elog, int batch) {
+  PassShape sh;
+  const uint32_t groups_log = L - k;
+  sh.logG = (uint32_t)elog - k;
+  if (sh.logG > groups_log) sh.logG = groups_log;
+  sh.E = 1u << (sh.logG + k);
+  sh.threads = sh.E / 2 < 256 ? sh.E / 2 : 256;
+  sh.grid = dim3((unsigned)(size_t(1) << (groups_log - sh.logG)), (unsigned)batch);
+  return sh;
+}
+
+static int launch_pass(bool dit, Fr* data, int batch, size_t bstride, const NttDomain* d, const Fr* tw, uint32_t s0,
+                       uint32_t k, int elog, int ls, int ss, int tm, cudaStream_t st) {
+  const uint32_t L = d->logN;
+  const PassShape sh = pass_shape(L, k, elog, batch);
+  const size_t smem = size_t(sh.E) * 32;
+  const ScaleTabs tabs = tabs_of(d);
+  if (dit)
+    k_ntt_pass<true><<<sh.grid, sh.threads, smem, st>>>(data, bstride, tw, L, s0, k, sh.logG, ls, ss, tm, tabs);
+  else
+    k_ntt_pass<false><<<sh.grid, sh.threads, smem, st>>>(data, bstride, tw, L, s0, k, sh.logG, ls, ss, tm, tabs);
+  ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaGetLastError());
+  return ZKVC_OK;
+}
+
 static int run_passes(bool dit, Fr* data, int batch, size_t bstride, const NttDomain* d, bool inverse,
                       int load_scale, int store_scale, bool to_mont, int elog, cudaStream_t st) {
   ZK_CHECK(elog >= 8 && elog <= 11, ZKVC_EINVAL, "ntt: 2^%d elements per block outside [2^8, 2^11]", elog);
   ZK_CHECK(batch >= 1 && batch <= 65535, ZKVC_EINVAL, "ntt: batch of %d arrays", batch);
   ntt_smem_attrs();
-  const uint32_t L = d->logN;
-  const uint32_t kmax = (uint32_t)elog < 10 ? (uint32_t)elog : 10;
-  const uint32_t P = (L + kmax - 1) / kmax;
-  const uint32_t kb = L / P, rem = L % P;
-  uint32_t s0 = 0;
+  const std::vector<uint32_t> ks = pass_split(d->logN, elog);
+  const uint32_t P = (uint32_t)ks.size();
   const Fr* tw = inverse ? d->tw_inv : d->tw_fwd;
-  ScaleTabs tabs = tabs_of(d);
+  uint32_t s0 = 0;
   for (uint32_t p = 0; p < P; p++) {
-    uint32_t k = kb + (p < rem ? 1 : 0);
-    uint32_t groups_log = L - k;
-    uint32_t logG = (uint32_t)elog - k;
-    if (logG > groups_log) logG = groups_log;
-    uint32_t E = 1u << (logG + k);
-    uint32_t threads = E / 2 < 256 ? E / 2 : 256;
-    dim3 grid((unsigned)(size_t(1) << (groups_log - logG)), (unsigned)batch);
-    size_t smem = size_t(E) * 32;
-    bool first = p == 0, last = p + 1 == P;
-    int ls = first ? load_scale : 0, ss = last ? store_scale : 0, tm = (first && to_mont) ? 1 : 0;
-    if (dit)
-      k_ntt_pass<true><<<grid, threads, smem, st>>>(data, bstride, tw, L, s0, k, logG, ls, ss, tm, tabs);
-    else
-      k_ntt_pass<false><<<grid, threads, smem, st>>>(data, bstride, tw, L, s0, k, logG, ls, ss, tm, tabs);
+    const bool first = p == 0, last = p + 1 == P;
+    ZK_TRY(launch_pass(dit, data, batch, bstride, d, tw, s0, ks[p], elog, first ? load_scale : 0,
+                       last ? store_scale : 0, (first && to_mont) ? 1 : 0, st));
+    s0 += ks[p];
+  }
+  return ZKVC_OK;
+}
+
+int ntt_quotient_chain(Fr* ev, int m, size_t N, const NttDomain* d, cudaStream_t st, int elog) {
+  ZK_CHECK(elog >= 8 && elog <= 11, ZKVC_EINVAL, "ntt: 2^%d elements per block outside [2^8, 2^11]", elog);
+  ZK_CHECK(m >= 1 && 3 * m <= 65535, ZKVC_EINVAL, "ntt: %d instances", m);
+  ZK_CHECK(N == d->N, ZKVC_EINVAL, "ntt: array stride %zu is not N", N);
+  ntt_smem_attrs();
+  const uint32_t L = d->logN;
+  const std::vector<uint32_t> ks = pass_split(L, elog);
+  const uint32_t P = (uint32_t)ks.size();
+  Fr* H = ev + size_t(3) * m * N;
+  if (P < 2 || L < 2) {  // one pass: no turn to fuse
+    ZK_TRY(run_passes(false, ev, 3 * m, N, d, true, SC_NONE, SC_NG, false, elog, st));
+    ZK_TRY(run_passes(true, ev, 3 * m, N, d, false, SC_NONE, SC_NONE, false, elog, st));
+    ZK_TRY(ntt_quotient(ev, ev + size_t(m) * N, ev + size_t(2) * m * N, H, d, st, size_t(m) * N));
+    return run_passes(false, H, m, N, d, true, SC_NONE, SC_NGI, false, elog, st);
+  }
+  const ScaleTabs tabs = tabs_of(d);
+  // inverse DIF transforms of A, B, C up to their last pass
+  uint32_t s0 = 0;
+  for (uint32_t p = 0; p + 1 < P; p++) {
+    ZK_TRY(launch_pass(false, ev, 3 * m, N, d, d->tw_inv, s0, ks[p], elog, 0, 0, 0, st));
+    s0 += ks[p];
+  }
+  // turn: the inverse's last pass, x N^-1 g^i, the forward DIT's first pass
+  {
+    const uint32_t k = ks[P - 1];
+    const PassShape sh = pass_shape(L, k, elog, 3 * m);
+    k_ntt_turn<<<sh.grid, sh.threads, size_t(sh.E) * 32, st>>>(ev, N, d->tw_inv, d->tw_fwd, L, k, sh.logG, SC_NG, tabs);
     ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
-    s0 += k;
+  }
+  // the forward DIT's middle passes: the mirror of the DIF split (its pass q covers the
+  // groups of the DIF's pass P - 1 - q)
+  uint32_t s0d = ks[P - 1];
+  for (uint32_t q = 1; q + 1 < P; q++) {
+    ZK_TRY(launch_pass(true, ev, 3 * m, N, d, d->tw_fwd, s0d, ks[P - 1 - q], elog, 0, 0, 0, st));
+    s0d += ks[P - 1 - q];
+  }
+  // quotient turn: the forward's last pass of A, B, C, the quotient, the first inverse
+  // DIF pass of h
+  {
+    const uint32_t k = ks[0];
+    const PassShape sh = pass_shape(L, k, elog, m);
+    // three times the threads where the grid is too small to fill the GPU (latency-bound),
+    // one array's worth where it is large (more blocks per SM)
+    const uint64_t blocks = uint64_t(sh.grid.x) * sh.grid.y;
+    const uint32_t threads = blocks < 2 * 152 ? std::min<uint32_t>(3 * sh.threads, 768) : sh.threads;
+    k_ntt_quotient_turn<<<sh.grid, threads, size_t(3) * sh.E * 32, st>>>(ev, (uint32_t)m, N, d->tw_fwd, d->tw_inv, L,
+                                                                         k, sh.logG, tabs);
+    ZK_COUNT_LAUNCH();
+    ZK_CUDA(cudaGetLastError());
+  }
+  // the rest of h's inverse DIF transform, x N^-1 g^-i at the last store
+  s0 = ks[0];
+  for (uint32_t p = 1; p < P; p++) {
+    ZK_TRY(launch_pass(false, H, m, N, d, d->tw_inv, s0, ks[p], elog, 0, p + 1 == P ? SC_NGI : 0, 0, st));
+    s0 += ks[p];
   }
   return ZKVC_OK;
 }

@@ -52,6 +52,13 @@ int ntt_dit(Fr* data, int batch, size_t batch_stride, const NttDomain* d, bool i
 // optional conversion out of Montgomery form.
 int ntt_bitrev(Fr* data, const NttDomain* d, int scale, bool from_mont, cudaStream_t st);
 
+// The prover's quotient chain for m instances of one domain: ev holds the arrays A_0 ..
+// A_(m-1), B_0 .., C_0 .., H_0 .. (N_stride elements apart) with A, B, C the evaluations
+// on H (natural order); on return H_i holds the coefficients of h_i = (A_i B_i - C_i) / t
+// (bit-reversed order), computed as INTT, coset NTT, pointwise quotient, coset INTT with
+// the turns between transforms fused into single passes.  A, B, C are overwritten.
+int ntt_quotient_chain(Fr* ev, int m, size_t N_stride, const NttDomain* d, cudaStream_t st, int elog = 10);
+
 // h_ev[i] = (A[i] B[i] - C[i]) / (g^N - 1): the quotient on the coset gH, for i < count
 // (count = 0: N; several instances of one domain lie back to back).
 int ntt_quotient(const Fr* A, const Fr* B, const Fr* C, Fr* H, const NttDomain* d, cudaStream_t st,

@@ -419,10 +419,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   prof_mark(PS_NTT, true, s3);
   const NttDomain* d = pk->dom;
   const int elog = pk->prove_tune[4] ? (int)pk->prove_tune[4] : 10;
-  ZK_TRY(ntt_dif(Aev, 3, N, d, true, SC_NONE, SC_NG, false, s3, elog));
-  ZK_TRY(ntt_dit(Aev, 3, N, d, false, s3, elog));
-  ZK_TRY(ntt_quotient(Aev, Bev, Cev, Hev, d, s3));
-  ZK_TRY(ntt_dif(Hev, 1, N, d, true, SC_NONE, SC_NGI, false, s3, elog));
+  ZK_TRY(ntt_quotient_chain(Aev, 1, N, d, s3, elog));
   k_check_h<<<1, 32, 0, s3>>>(Hev, N, B.flags); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_NTT, false, s3);
