@@ -831,8 +831,11 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
   const uint32_t at = p.tune.accum_threads;
   const int lanes = p.lanes == 4 ? 4 : 1;
+  // the fold is latency-bound unless the run is large: quads there whatever the
+  // accumulation uses
+  const int flanes = (lanes == 4 || S / T0 < 40960) ? 4 : 1;
   unsigned qb = (unsigned)((uint64_t(L.qmax) * lanes + at - 1) / at);
-  unsigned fb = (unsigned)((uint64_t(L.qmax) * lanes + 127) / 128);
+  unsigned fb = (unsigned)((uint64_t(L.qmax) * flanes + 127) / 128);
   if (accum_stage >= 0) prof_mark(accum_stage, true, st);
   const auto* ob = reinterpret_cast<const Affine<F>* const*>(L.obases);
   if (lanes == 4)
@@ -846,7 +849,7 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   }
   ZK_CUDA(cudaGetLastError());
   if (after_accum) ZK_CUDA(cudaEventRecord(after_accum, st));
-  if (lanes == 4)
+  if (flanes == 4)
     k_fold_tree<F, 4><<<fb, 128, 0, st>>>(L.choff, L.chunk_key, K, part, L.arrive);
   else
     k_fold_tree<F, 1><<<fb, 128, 0, st>>>(L.choff, L.chunk_key, K, part, L.arrive);
