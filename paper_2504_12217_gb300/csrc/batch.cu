@@ -226,7 +226,7 @@ zkvc_batch::~zkvc_batch() {
 namespace zkvc {
 
 // The candidates the autotuner tries; workspaces are sized for the smallest chunk.
-static const uint32_t kChunkG1[] = {8, 16, 32, 64};
+static const uint32_t kChunkG1[] = {8, 16, 32, 64, 128, 256};
 static const uint32_t kChunkG2[] = {8, 16, 32};
 static const uint32_t kAccumG1[] = {64, 128, 256};
 static const uint32_t kAccumG2[] = {64, 128};
@@ -540,7 +540,8 @@ static int autotune(zkvc_batch* B) {
     MsmTune best = *k.tune;
     float best_ms = 1e30f;
     const uint32_t* chunks = k.g2 ? kChunkG2 : kChunkG1;
-    const int nchunks = k.g2 ? 3 : 4;
+    const int nchunks = k.g2 ? (int)(sizeof(kChunkG2) / sizeof(kChunkG2[0]))
+                             : (int)(sizeof(kChunkG1) / sizeof(kChunkG1[0]));
     for (int c = 0; c < nchunks; c++) {
       MsmTune t = best;
       t.chunk = chunks[c];

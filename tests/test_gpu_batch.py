@@ -84,7 +84,7 @@ def test_batch_small_shapes(nv, small_keys, flags):
         assert p0 == proofs[4]
     if flags == 1:
         t = batch.get_tuning()
-        assert t["main_chunk"] in (8, 16, 32, 64) and t["ntt_log_elems_per_block"] in (9, 10, 11)
+        assert t["main_chunk"] in (8, 16, 32, 64, 128, 256) and t["ntt_log_elems_per_block"] in (9, 10, 11)
     info = batch.info()
     assert info["count"] == len(SMALL) and info["device_bytes"] > 0
     assert (info["graph_launches"] > 0) == (flags != 2)
