@@ -893,7 +893,7 @@ int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const u
   ZK_CUDA(cudaGetLastError());
   // A, the private part of C and B1 (all witness scalars known now)
   ZK_TRY(msm_run<Fp>(P.pre, pk->g1, B.ws_pre, B.ws_pre_bytes, B.pre, st));
-  k_chains<<<1, 64, 0, st>>>(B.glv, B.pre, B.chain, nullptr, nullptr); ZK_COUNT_LAUNCH();
+  k_chains<<<1, 160, 0, st>>>(B.glv, B.pre, B.chain, nullptr, nullptr); ZK_COUNT_LAUNCH();
   // quotient and H
   const NttDomain* d = pk->dom;
   ZK_TRY(ntt_quotient_chain(Aev, 1, N, d, st));

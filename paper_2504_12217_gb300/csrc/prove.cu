@@ -26,6 +26,7 @@
 #include <cstring>
 
 #include "coop.cuh"
+#include "sliced.cuh"
 #include "glv.h"
 #include "groth16.h"
 #include "msm.h"
@@ -80,44 +81,41 @@ __global__ void k_randomness(Fr* rs, int* flags) {
 }
 
 // Chain mode: s A and r B1 (small-run outputs 0 and 2) with the scalars split by the GLV
-// endomorphism on the host (gs[0] = s, gs[1] = r): four quads compute s1 A, s2 phi(A),
-// r1 B1 and r2 phi(B1) side by side (phi(x, y) = (beta x, y)), then two quads add the
-// pairs.  Meanwhile the second warp encodes A (bytes 0..63 of the proof: its inversion
+// endomorphism on the host (gs[0] = s, gs[1] = r): four warps compute s1 A, s2 phi(A),
+// r1 B1 and r2 phi(B1) side by side (phi(x, y) = (beta x, y)) in limb-sliced arithmetic
+// (sliced.cuh: eight lanes per product, four products per warp), then two warps add the
+// pairs.  Meanwhile the fifth warp encodes A (bytes 0..63 of the proof: its inversion
 // overlaps the chains).  Then the H-free part of C, small[1] + s A + r B1, goes to cpart.
 // (proof and cpart may be null: the generic engine encodes A and C itself.)  One block
-// of 64 threads.
-__global__ void k_chains(const GlvScalar* __restrict__ gs, const G1J* __restrict__ small, G1J* chain, G1J* cpart,
-                         uint8_t* proof) {
+// of 160 threads.
+__global__ void __launch_bounds__(160) k_chains(const GlvScalar* __restrict__ gs, const G1J* __restrict__ small,
+                                                G1J* chain, G1J* cpart, uint8_t* proof) {
   __shared__ G1J T[4][16];
   __shared__ G1J part[4];
-  const int q = threadIdx.x >> 2;
-  if (threadIdx.x == 32 && proof) encode_g1(ld_field(small), proof);
-  if (q < 4) {
-    G1J P = ld_field(small + (q < 2 ? 0 : 2));
-    if (q & 1) {
-      Fp beta;
+  const int w = threadIdx.x >> 5;
+  if (threadIdx.x == 128 && proof) encode_g1(ld_field(small), proof);
+  if (w < 4) {
+    SlG1 P = sl_ld(small + (w < 2 ? 0 : 2));
+    if (w & 1) {  // beta in Montgomery form: beta R^2 R^-1
+      const int j = sl_limb();
+      uint32_t beta = 0, r2 = 0;
 #pragma unroll
-      for (int i = 0; i < 8; i++) beta.v[i] = glv_beta_limb(i);
-      P.X = f_mul(P.X, f_to_mont(beta));
+      for (int i = 0; i < 8; i++) {
+        beta |= glv_beta_limb(i) & (0u - uint32_t(j == i));
+        r2 |= r2_limb<FpCfg>(i) & (0u - uint32_t(j == i));
+      }
+      P.X = sl_mul(P.X, sl_mul(beta, r2));
     }
-    const G1J R = p_mul_half_quad(P, gs[q >> 1].h[q & 1], T[q]);
-    if (quad_lane() == 0) st_field(part + q, R);
+    sl_st(part + w, sl_mul_half(P, gs[w >> 1].h[w & 1], T[w]));
   }
   __syncthreads();
-  if (q == 0 || q == 2) {
-    const G1J S = p_add_quad(ld_field(part + q), ld_field(part + q + 1));
-    if (quad_lane() == 0) st_field(part + q, S);
-  }
+  if (w == 0 || w == 2) sl_st(part + w, sl_padd(sl_ld(part + w), sl_ld(part + w + 1)));
   __syncthreads();
-  if (q == 0) {
-    if (quad_lane() == 0) {
-      st_field(chain, ld_field(part));
-      st_field(chain + 1, ld_field(part + 2));
-    }
-    if (cpart) {
-      const G1J c = p_add_quad(ld_field(small + 1), p_add_quad(ld_field(part), ld_field(part + 2)));
-      if (quad_lane() == 0) st_field(cpart, c);
-    }
+  if (w == 0) {
+    const SlG1 sA = sl_ld(part), rB = sl_ld(part + 2);
+    sl_st(chain, sA);
+    sl_st(chain + 1, rB);
+    if (cpart) sl_st(cpart, sl_padd(sl_ld(small + 1), sl_padd(sA, rB)));
   }
 }
 
@@ -447,7 +445,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   if (chain && pk->prove_tune[5] == 2) ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->h_accum, 0));
   ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
   if (chain) {
-    k_chains<<<1, 64, 0, side->st[1]>>>(B.glv, B.res_small, B.res_chain, B.cpart, B.proof); ZK_COUNT_LAUNCH();
+    k_chains<<<1, 160, 0, side->st[1]>>>(B.glv, B.res_small, B.res_chain, B.cpart, B.proof); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   } else {
     k_encode_a<<<1, 32, 0, side->st[1]>>>(B.res_small, nullptr, B.cpart, B.proof); ZK_COUNT_LAUNCH();
