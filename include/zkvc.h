@@ -77,6 +77,15 @@ int zkvc_fr_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n
 int zkvc_fp_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream);
 int zkvc_fp2_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n, void* stream);
 
+/* Elementwise inverses d_out[i] = d_a[i]^-1 mod r (fr) or mod p (fp), 0 -> 0, for n
+ * canonical 32-byte little-endian elements in device memory; d_out may alias d_a.  The
+ * inversion of the prover's affine conversions (the Groth16 proof encodes A, B and C in
+ * affine coordinates, Sec. II): a binary GCD that takes 31 steps at a time on 64-bit
+ * approximations of the operands.  Returns ZKVC_EINVAL on a null pointer with n > 0.
+ */
+int zkvc_fr_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream);
+int zkvc_fp_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream);
+
 /* ------------------------------------------------------------------ witness matmul
  * Y = X W for int8 X (a x n, row-major) and W (n x b, row-major) into int32 Y (a x b,
  * row-major), exactly -- the matrix product whose correctness zkVC proves (Sec. II) and

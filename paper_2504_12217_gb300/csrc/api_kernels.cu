@@ -109,6 +109,14 @@ __global__ void k_field_mul(const Field<C>* a, const Field<C>* b, Field<C>* out,
   st_field(out + i, f_mul(f_to_mont(ld_field(a + i)), ld_field(b + i)));
 }
 
+// a^-1 (0 -> 0): Montgomery form in, inversion (binary GCD), canonical out
+template <class C>
+__global__ void k_field_inv(const Field<C>* a, Field<C>* out, size_t n) {
+  size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  st_field(out + i, f_from_mont(f_inv(f_to_mont(ld_field(a + i)))));
+}
+
 __global__ void k_fp2_mul(const Fp2* a, const Fp2* b, Fp2* out, size_t n) {
   size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -262,6 +270,26 @@ int zkvc_fp_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t n
   ZK_CHECK(d_a && d_b && d_out, ZKVC_EINVAL, "fp_mul: null pointer");
   k_field_mul<FpCfg><<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
       (const Fp*)d_a, (const Fp*)d_b, (Fp*)d_out, n); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaGetLastError());
+  return ZKVC_OK;
+}
+
+int zkvc_fr_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream) {
+  clear_error();
+  if (n == 0) return ZKVC_OK;
+  ZK_CHECK(d_a && d_out, ZKVC_EINVAL, "fr_inv: null pointer");
+  k_field_inv<FrCfg><<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>((const Fr*)d_a, (Fr*)d_out, n);
+  ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaGetLastError());
+  return ZKVC_OK;
+}
+
+int zkvc_fp_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream) {
+  clear_error();
+  if (n == 0) return ZKVC_OK;
+  ZK_CHECK(d_a && d_out, ZKVC_EINVAL, "fp_inv: null pointer");
+  k_field_inv<FpCfg><<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>((const Fp*)d_a, (Fp*)d_out, n);
+  ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }

@@ -40,6 +40,8 @@ SIGNATURES = {
     "zkvc_fr_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_fp_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_fp2_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
+    "zkvc_fr_inv": (_c_int, [_c_p, _c_p, _c_sz, _c_p]),
+    "zkvc_fp_inv": (_c_int, [_c_p, _c_p, _c_sz, _c_p]),
     "zkvc_ntt": (_c_int, [_c_p, _c_u32, _c_int, _c_p]),
     "zkvc_matmul_i8": (_c_int, [_c_p, _c_p, _c_p, _c_int, _c_int, _c_int, _c_p]),
     "zkvc_msm_workspace_bytes": (_c_sz, [_c_sz, _c_int]),
@@ -196,6 +198,24 @@ def zkvc_fp_mul(a, b, out=None):
 
 def zkvc_fp2_mul(a, b, out=None):
     return _field_mul("zkvc_fp2_mul", a, b, out, 64)
+
+
+def zkvc_fr_inv(a, out=None):
+    """Elementwise a^-1 mod r (0 -> 0) of a [n, 32] canonical uint8 CUDA tensor."""
+    return _field_inv("zkvc_fr_inv", a, out)
+
+
+def zkvc_fp_inv(a, out=None):
+    """Elementwise a^-1 mod p (0 -> 0) of a [n, 32] canonical uint8 CUDA tensor."""
+    return _field_inv("zkvc_fp_inv", a, out)
+
+
+def _field_inv(name, a, out):
+    _u8(a, 32)
+    if out is None:
+        out = _torch().empty_like(a)
+    check(getattr(lib(), name)(_dev_ptr(a), _dev_ptr(out), a.shape[0], _stream()))
+    return out
 
 
 def _field_mul(name, a, b, out, width):

@@ -38,6 +38,27 @@ def test_prime_field_mul(nv, name, mod):
     assert got == [x * y % mod for x, y in zip(a, b)]
 
 
+@pytest.mark.parametrize("name,mod", [("fr", R), ("fp", P)])
+def test_prime_field_inv(nv, name, mod):
+    """a^-1 against its definition (a a^-1 = 1; 0 -> 0).  The device inverts the integer
+    y = a 2^256 mod m (the Montgomery form of a), so the inputs include a = y 2^-256 for
+    the y that stress the binary GCD: tiny and all-ones values, powers of two, m - 1, and
+    ratios of consecutive Fibonacci numbers (the most subtraction steps)."""
+    rng = random.Random(12)
+    rinv = pow(1 << 256, -1, mod)
+    fib = [1, 2]
+    while fib[-1] < mod:
+        fib.append(fib[-1] + fib[-2])
+    ys = [1, 2, 3, mod - 1, mod - 2, (mod - 1) // 2, (mod + 1) // 2, (1 << 253) - 1, 1 << 253, (1 << 64) - 1,
+          1 << 64, (1 << 31) - 1, 1 << 31] + [f for f in fib[-8:] if f < mod] + [1 << k for k in range(0, 254, 7)]
+    ys += [rng.randrange(1, 1 << rng.randrange(1, 254)) for _ in range(1000)]
+    a = [0] + _edge(mod) + [y * rinv % mod for y in ys] + [rng.randrange(mod) for _ in range(3000)]
+    out = getattr(nv, f"zkvc_{name}_inv")(_util.to_cuda(_util.ints_to_u8(a)))
+    got = _util.u8_to_ints(out.cpu().numpy())
+    for x, g in zip(a, got):
+        assert g == (pow(x, -1, mod) if x else 0), x
+
+
 def test_fp2_mul(nv):
     rng = random.Random(12)
     n = 2000
