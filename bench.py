@@ -343,8 +343,7 @@ def run_gpu(args):
         nv.zkvc_prove(pk, Xd, Wd, rs_list[i], Y=Yd, workspace=ws)
     torch.cuda.synchronize()
 
-    # ---- device-timed steps, inputs resident
-    nv.zkvc_profile_enable(True)
+    # ---- device-timed steps, inputs resident (zkvc_prove replays its captured graph)
     launches0 = nv.zkvc_kernel_launches()
     clocks = ClockSampler(local)
     clocks.start()
@@ -362,8 +361,6 @@ def run_gpu(args):
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     launches = nv.zkvc_kernel_launches() - launches0
-    prof = nv.zkvc_profile_read()
-    nv.zkvc_profile_enable(False)
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     total_s = reduce_max(sum(step_ms) / 1e3, dist, "cuda")
     value = replica_value(args.steps, world, total_s)
@@ -385,6 +382,17 @@ def run_gpu(args):
     e2e_s = reduce_max(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": replica_value(e2e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": a * n + n * b,
            "d2h_bytes_per_step": 256 + 4 * a * b}
+
+    # ---- stage timers (events on the prover's streams; zkvc_prove enqueues directly while
+    # they are on): the accumulation kernels' live durations for the roofline and the
+    # proof's timeline across its streams
+    nv.zkvc_profile_enable(True)
+    for i in range(min(args.steps, 50)):
+        flush.zero_()
+        nv.zkvc_prove(pk, Xd, Wd, rs_list[args.warmup + i], Y=Yd, workspace=ws)
+    torch.cuda.synchronize()
+    prof = nv.zkvc_profile_read()
+    nv.zkvc_profile_enable(False)
 
     if rank != 0:
         if dist is not None:
@@ -412,6 +420,7 @@ def run_gpu(args):
                 "algorithmic_imad_per_launch": work / max(calls, 1),
                 "launch_ms": ms / max(calls, 1)}
     stages = {k: round(v["ms"] / max(v["calls"], 1), 4) for k, v in prof.items()}
+    spans = {k: [round(v["start_ms"], 4), round(v["end_ms"], 4)] for k, v in prof.items() if v["calls"]}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -441,6 +450,7 @@ def run_gpu(args):
         "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps, "clocks": clk, "stage_ms": stages,
+        "stage_span_ms": spans,
         "wall_s_timed_region": wall,
     }
     print(json.dumps(line), flush=True)

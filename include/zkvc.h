@@ -55,16 +55,22 @@ int zkvc_version(void);
  * all threads); a diagnostic for launch-count accounting. */
 uint64_t zkvc_kernel_launches(void);
 
-/* Stage timers for the prover: when enabled, zkvc_prove records CUDA events on its
- * stream around each stage and accumulates their elapsed times after its final
- * synchronisation.  Stages 0..6: witness, ntt, msm_g1 (the H-query MSM),
- * msm_g1_bucket_accum (its accumulation kernel), msm_g2, msm_g2_bucket_accum, combine.
- * The two bucket_accum stages time the bucket-accumulation kernel alone and count its
- * units (bucket terms, one mixed point addition each).
- * Enabling resets the counters.  A single-threaded diagnostic: not for concurrent provers.
+/* Stage timers for the prover: when enabled, zkvc_prove records CUDA events on the
+ * streams of its stages and accumulates their elapsed times after its final
+ * synchronisation.  Stages 0..7: witness, ntt, msm_g1 (the H-query MSM),
+ * msm_g1_bucket_accum (its accumulation kernel), msm_g2 (with the encoding of B),
+ * msm_g2_bucket_accum, combine (the encoding of C after the joins), msm_g1_small (the
+ * small-digit G1 run with what follows it on its stream: the chain-mode scalar
+ * multiplications or the encoding of A).  The two bucket_accum stages time the
+ * bucket-accumulation kernel alone and count its units (bucket terms, one mixed point
+ * addition each).  zkvc_profile_span gives a stage's mean begin and end offsets (ms) from
+ * the begin of the witness stage of the same proof: the proof's timeline across its
+ * streams.  Enabling resets the counters.  A single-threaded diagnostic: not for
+ * concurrent provers.  Out-of-range stages return ZKVC_EINVAL.
  */
 void zkvc_profile_enable(int on);
 int zkvc_profile_read(int stage, const char** name, double* ms, uint64_t* calls, uint64_t* units);
+int zkvc_profile_span(int stage, double* start_ms, double* end_ms);
 
 /* ------------------------------------------------------------------ field kernels
  * Elementwise products of n canonical elements: d_out[i] = d_a[i] * d_b[i] mod the
@@ -282,6 +288,11 @@ int zkvc_vk_load(const char* path, zkvc_vk** vk);
  * Synchronises `stream`.  ZKVC_EUNSAT if the device-side checks find the witness does
  * not satisfy the constraints (the PSQ chain must close against Y(z) and h must have
  * degree < N - 1).  The proof is a deterministic function of (pk, X, W, r, s).
+ * When a key is proven twice in a row with the same d_X, d_W, d_Y, d_ws, mode and
+ * tuning, the second call captures the proof's launch sequence as a CUDA graph (kept with
+ * the key, freed by zkvc_pk_free) and later calls with those buffers replay it; other
+ * calls, and every call while the stage timers are on, enqueue directly.  The bytes are
+ * the same either way.
  */
 size_t zkvc_prove_workspace_bytes(const zkvc_pk* pk);
 int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64], int32_t* d_Y,

@@ -13,6 +13,8 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
                    uint32_t* chosen);
 int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, int32_t* dY,
                void* ws, size_t ws_bytes, uint8_t* proof, cudaStream_t st);
+int prove_graph(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, int32_t* dY,
+                void* ws, size_t ws_bytes, uint8_t* proof, cudaStream_t st);
 template <class F>
 int export_points(const Affine<F>* src, const std::vector<uint64_t>& idx, uint8_t* host_out, cudaStream_t st);
 
@@ -139,6 +141,7 @@ void zkvc_pk_free(zkvc_pk* pk) {
   cudaFree(pk->g2);
   cudaFree(pk->zA);
   cudaFree(pk->zB);
+  zkvc::prove_graph_free(pk->graph);
   delete pk->gen;
   delete pk;
 }
@@ -470,7 +473,7 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   ZK_CHECK(pk, ZKVC_EINVAL, "prove: null key");
   ZK_TRY(device_guard(pk->device));
   if (pk->gen) return prove_generic(pk, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
-  return prove_impl(pk, (int)pk->prove_tune[6], dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
+  return prove_graph(pk, (int)pk->prove_tune[6], dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
 }
 
 int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t rs[64], int32_t* dY,
@@ -482,7 +485,7 @@ int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t*
     ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN, ZKVC_EINVAL, "prove: mode %d", mode);
     return prove_generic(pk, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
   }
-  return prove_impl(pk, mode, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
+  return prove_graph(pk, mode, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -63,10 +63,12 @@ struct ProfSlot {
   uint32_t* host_units = nullptr;
   bool pending = false;
   double ms = 0;
+  double start_ms = 0, end_ms = 0;  // offsets of the begin and end events from the witness begin
   unsigned long long calls = 0, units = 0;
 };
 static ProfSlot g_prof_slots[PS_COUNT] = {{"witness"},   {"ntt"},    {"msm_g1"},  {"msm_g1_bucket_accum"},
-                                          {"msm_g2"},    {"msm_g2_bucket_accum"}, {"combine"}};
+                                          {"msm_g2"},    {"msm_g2_bucket_accum"}, {"combine"},
+                                          {"msm_g1_small"}};
 static std::atomic<bool> g_prof{false};
 
 void prof_mark(int stage, bool begin, cudaStream_t st) {
@@ -82,6 +84,8 @@ void prof_mark(int stage, bool begin, cudaStream_t st) {
   if (!begin) x.pending = true;
 }
 
+bool prof_enabled() { return g_prof.load(std::memory_order_relaxed); }
+
 uint32_t* prof_units(int stage) {
   if (!g_prof.load(std::memory_order_relaxed)) return nullptr;
   return g_prof_slots[stage].host_units;
@@ -89,10 +93,14 @@ uint32_t* prof_units(int stage) {
 
 void prof_collect() {
   if (!g_prof.load(std::memory_order_relaxed)) return;
+  const ProfSlot& ref = g_prof_slots[PS_WITNESS];
+  const bool spans = ref.pending;
   for (auto& x : g_prof_slots) {
     if (!x.pending) continue;
     float ms = 0;
     if (cudaEventElapsedTime(&ms, x.b, x.e) == cudaSuccess) x.ms += ms;
+    if (spans && cudaEventElapsedTime(&ms, ref.b, x.b) == cudaSuccess) x.start_ms += ms;
+    if (spans && cudaEventElapsedTime(&ms, ref.b, x.e) == cudaSuccess) x.end_ms += ms;
     x.calls++;
     x.units += *x.host_units;
     *x.host_units = 0;
@@ -236,7 +244,7 @@ int zkvc_set_wait_timeout_ms(int ms) {
 
 void zkvc_profile_enable(int on) {
   for (auto& x : g_prof_slots) {
-    x.ms = 0;
+    x.ms = x.start_ms = x.end_ms = 0;
     x.calls = x.units = 0;
     x.pending = false;
   }
@@ -251,6 +259,16 @@ int zkvc_profile_read(int stage, const char** name, double* ms, uint64_t* calls,
   if (ms) *ms = x.ms;
   if (calls) *calls = x.calls;
   if (units) *units = x.units;
+  return ZKVC_OK;
+}
+
+int zkvc_profile_span(int stage, double* start_ms, double* end_ms) {
+  clear_error();
+  ZK_CHECK(stage >= 0 && stage < PS_COUNT, ZKVC_EINVAL, "profile: stage %d outside [0, %d)", stage, (int)PS_COUNT);
+  const ProfSlot& x = g_prof_slots[stage];
+  const double n = x.calls ? (double)x.calls : 1.0;
+  if (start_ms) *start_ms = x.start_ms / n;
+  if (end_ms) *end_ms = x.end_ms / n;
   return ZKVC_OK;
 }
 

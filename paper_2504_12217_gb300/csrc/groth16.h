@@ -85,6 +85,8 @@ Layout make_layout(const Shape& s);
 
 namespace zkvc {
 struct GenericKey;
+struct ProveGraph;
+void prove_graph_free(ProveGraph* g);
 }
 
 struct zkvc_pk {
@@ -104,6 +106,8 @@ struct zkvc_pk {
   // accumulation), zkvc_prove's mode (ZKVC_PROVE_FOLD or _CHAIN), when the G2 MSM starts
   // (0 at once, 1 after the NTTs), quad-lane chunks in the H and small-digit runs (0, 1)
   uint32_t prove_tune[ZKVC_PK_TUNING_LEN] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // captured one-proof graph of zkvc_prove (prove.cu), created on first use
+  mutable zkvc::ProveGraph* graph = nullptr;
 };
 
 struct zkvc_vk {

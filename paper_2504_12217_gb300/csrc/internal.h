@@ -38,11 +38,13 @@ enum ProfStage : int {
   PS_MSM_G2,
   PS_ACCUM_G2,   // the G2 bucket-accumulation kernel alone; units = bucket terms
   PS_COMBINE,
+  PS_MSM_SMALL,  // the small-digit G1 run and what follows it on its stream
   PS_COUNT
 };
 void prof_mark(int stage, bool begin, cudaStream_t st);
 uint32_t* prof_units(int stage);  // pinned host slot for the stage's unit count, or null
 void prof_collect();
+bool prof_enabled();
 
 #define ZK_CUDA(call)                                                                       \
   do {                                                                                      \

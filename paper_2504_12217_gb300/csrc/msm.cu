@@ -22,6 +22,8 @@
 // windows share one bucket set and no doubling chain follows; variable-base MSMs keep
 // one bucket set per window and combine windows by Horner's rule.
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "coop.cuh"
 #include "msm.h"
@@ -774,17 +776,55 @@ int msm_prepare(const MsmPlan& p, void* ws, size_t ws_bytes, MsmExec* ex) {
   return ZKVC_OK;
 }
 
+// Pinned host memory that this thread's uploads take their table images from while a
+// launch sequence that includes the uploads is being captured (the copy nodes then read
+// it on every replay, so it must outlive the graph and keep its contents).
+static thread_local uint8_t* t_stage = nullptr;
+static thread_local size_t t_stage_cap = 0, t_stage_off = 0;
+
+void msm_table_stage(uint8_t* host, size_t cap) {
+  t_stage = host;
+  t_stage_cap = host ? cap : 0;
+  t_stage_off = 0;
+}
+
+// The tables are carved one after another (segs, outs, obases, bsegs, dseg, oitems), so
+// one image of their span, with each table at its device offset, goes up in one copy.
 int msm_upload(MsmExec* ex, cudaStream_t st) {
   ZK_CHECK(ex && ex->st, ZKVC_EINVAL, "msm: exec not prepared");
   const MsmPlan& p = ex->plan;
   Layout& L = ex->st->L;
   HostTables& h = ex->st->h;
-  ZK_CUDA(cudaMemcpyAsync(L.segs, p.segs.data(), p.segs.size() * sizeof(MsmSeg), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.outs, p.outs.data(), p.outs.size() * sizeof(MsmOut), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.obases, h.obases.data(), h.obases.size() * sizeof(void*), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.bsegs, h.bsegs.data(), h.bsegs.size() * sizeof(BitSeg), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.dseg, h.dsegs.data(), h.dsegs.size() * sizeof(TreeSeg), cudaMemcpyHostToDevice, st));
-  ZK_CUDA(cudaMemcpyAsync(L.oitems, h.oitems.data(), h.oitems.size() * sizeof(OutItem), cudaMemcpyHostToDevice, st));
+  uint8_t* const dev0 = reinterpret_cast<uint8_t*>(L.segs);
+  uint8_t* const dev1 = reinterpret_cast<uint8_t*>(L.oitems) + h.oitems.size() * sizeof(OutItem);
+  ZK_CHECK(dev0 && dev1 > dev0, ZKVC_EINVAL, "msm: tables not carved");
+  const size_t span = size_t(dev1 - dev0);
+  std::vector<uint8_t> tmp;
+  uint8_t* img = nullptr;
+  if (t_stage) {
+    ZK_CHECK(t_stage_off + span <= t_stage_cap, ZKVC_ENOMEM, "msm: %zu bytes of table staging are not enough",
+             t_stage_cap);
+    img = t_stage + t_stage_off;
+    t_stage_off += (span + 255) & ~size_t(255);
+  } else {
+    tmp.resize(span);
+    img = tmp.data();
+  }
+  auto put = [&](const void* dev, const void* src, size_t bytes) -> bool {
+    const uint8_t* d = reinterpret_cast<const uint8_t*>(dev);
+    if (bytes == 0) return true;
+    if (d < dev0 || d + bytes > dev1) return false;
+    std::memcpy(img + (d - dev0), src, bytes);
+    return true;
+  };
+  const bool ok = put(L.segs, p.segs.data(), p.segs.size() * sizeof(MsmSeg)) &&
+                  put(L.outs, p.outs.data(), p.outs.size() * sizeof(MsmOut)) &&
+                  put(L.obases, h.obases.data(), h.obases.size() * sizeof(void*)) &&
+                  put(L.bsegs, h.bsegs.data(), h.bsegs.size() * sizeof(BitSeg)) &&
+                  put(L.dseg, h.dsegs.data(), h.dsegs.size() * sizeof(TreeSeg)) &&
+                  put(L.oitems, h.oitems.data(), h.oitems.size() * sizeof(OutItem));
+  ZK_CHECK(ok, ZKVC_EINVAL, "msm: tables outside their span");
+  ZK_CUDA(cudaMemcpyAsync(dev0, img, span, cudaMemcpyHostToDevice, st));
   ex->st->uploaded = true;
   return ZKVC_OK;
 }

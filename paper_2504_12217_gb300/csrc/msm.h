@@ -93,6 +93,10 @@ struct MsmExec {
 template <class F>
 int msm_prepare(const MsmPlan& p, void* ws, size_t ws_bytes, MsmExec* ex);
 int msm_upload(MsmExec* ex, cudaStream_t st);
+// While set (this thread), msm_upload writes its table images into the pinned host
+// buffer [host, host + cap) instead of temporary memory: for uploads captured into a
+// graph, whose copy nodes read the images again on every replay.  nullptr unsets it.
+void msm_table_stage(uint8_t* host, size_t cap);
 template <class F>
 int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cudaStream_t st, int accum_stage = -1,
                cudaEvent_t after_accum = nullptr);

@@ -23,6 +23,8 @@
 //  7. Affine conversion (one inversion per point, in parallel) and the canonical
 //     256-byte encoding A || B || C.
 #include <algorithm>
+#include <mutex>
+#include <new>
 #include <cstring>
 
 #include "coop.cuh"
@@ -357,9 +359,12 @@ static int fork_to(SideStreams* side, int i, cudaStream_t st) {
 // Enqueues one proof on st (and the calling thread's side streams, joined back into st).
 // rs_host is read before the call returns; the proof lands in proof_out and the device
 // flags in flags_out (host pointers, written when st reaches them: pinned memory lets the
-// copies run asynchronously).
-int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host,
-                  int32_t* dY, void* ws, size_t ws_bytes, uint8_t* proof_out, int* flags_out, cudaStream_t st) {
+// copies run asynchronously).  glv_host, when given (pinned, chain mode), supplies the
+// GLV halves of s and r as a copy source instead of a split made now: a captured graph
+// then reads whatever the host wrote there before each replay.
+static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host,
+                              const GlvScalar* glv_host, int32_t* dY, void* ws, size_t ws_bytes, uint8_t* proof_out,
+                              int* flags_out, cudaStream_t st) {
   ZK_CHECK(pk && dX && dW && rs_host && dY && ws && proof_out && flags_out, ZKVC_EINVAL, "prove: null argument");
   ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN, ZKVC_EINVAL, "prove: mode %d", mode);
   size_t need = prove_workspace_bytes(pk, mode);
@@ -377,7 +382,9 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   prof_mark(PS_WITNESS, true, st);
   ZK_CUDA(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), st));
   ZK_CUDA(cudaMemcpyAsync(B.rs, rs_host, 64, cudaMemcpyHostToDevice, st));
-  if (chain) {
+  if (chain && glv_host) {
+    ZK_CUDA(cudaMemcpyAsync(B.glv, glv_host, 2 * sizeof(GlvScalar), cudaMemcpyHostToDevice, st));
+  } else if (chain) {
     // s and r split by the GLV endomorphism for the two scalar multiplications
     const GlvScalar g[2] = {glv_split(rs_host + 32), glv_split(rs_host)};
     ZK_CUDA(cudaMemcpyAsync(B.glv, g, sizeof(g), cudaMemcpyHostToDevice, st));
@@ -433,8 +440,8 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   if (pk->prove_tune[7] == 1) ZK_CUDA(cudaStreamWaitEvent(side->st[0], side->ntt_done, 0));
   prof_mark(PS_MSM_G2, true, side->st[0]);
   ZK_TRY(msm_run<Fp2>(P.g2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st[0], PS_ACCUM_G2));
-  prof_mark(PS_MSM_G2, false, side->st[0]);
   k_encode_b<<<1, 32, 0, side->st[0]>>>(B.res2, B.proof); ZK_COUNT_LAUNCH();
+  prof_mark(PS_MSM_G2, false, side->st[0]);
   ZK_CUDA(cudaEventRecord(side->join[0], side->st[0]));
   // the small-digit G1 MSM on side stream 1, then in chain mode the two variable-base
   // multiplications, then the encoding of A and the H-free part of C.  In chain mode it
@@ -443,6 +450,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->fork[1], 0));
   if (chain && pk->prove_tune[5] == 1) ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->ntt_done, 0));
   if (chain && pk->prove_tune[5] == 2) ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->h_accum, 0));
+  prof_mark(PS_MSM_SMALL, true, side->st[1]);
   ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
   if (chain) {
     k_chains<<<1, 160, 0, side->st[1]>>>(B.glv, B.res_small, B.res_chain, B.cpart, B.proof); ZK_COUNT_LAUNCH();
@@ -450,6 +458,7 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   } else {
     k_encode_a<<<1, 32, 0, side->st[1]>>>(B.res_small, nullptr, B.cpart, B.proof); ZK_COUNT_LAUNCH();
   }
+  prof_mark(PS_MSM_SMALL, false, side->st[1]);
   ZK_CUDA(cudaEventRecord(side->join[1], side->st[1]));
   if (!chain) {
     // the full-scalar G1 terms that need no h, on side stream 2, then their term of C.
@@ -477,6 +486,11 @@ int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* d
   return ZKVC_OK;
 }
 
+int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host,
+                  int32_t* dY, void* ws, size_t ws_bytes, uint8_t* proof_out, int* flags_out, cudaStream_t st) {
+  return prove_enqueue_impl(pk, mode, dX, dW, rs_host, nullptr, dY, ws, ws_bytes, proof_out, flags_out, st);
+}
+
 // Status of a finished proof from its device flags.
 int prove_status(int flags) {
   ZK_CHECK(!(flags & 4), ZKVC_EINVAL, "prove: r or s is not a canonical Fr element");
@@ -495,7 +509,180 @@ int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, 
   return prove_status(flags);
 }
 
-// Latency tuning of the one-proof prover: coordinate descent over the level-0 chunk of
+// ------------------------------------------------------------------ one-proof graph
+// zkvc_prove and zkvc_prove_mode replay a CUDA graph of the whole proof (its kernels,
+// memsets, copies and the fork/join events of its five streams) once a key is proven
+// with the same buffers, mode and tuning on two calls in a row: the first of the two
+// runs directly and records the buffers, the second captures the enqueue on a capture
+// stream and instantiates it with the streams' priorities kept per node.  The graph reads
+// r, s and their GLV halves from pinned host memory that the host fills before each
+// replay and writes the proof and the device flags to pinned memory.  A change of
+// buffers, mode or tuning re-arms the capture; profiling, or another thread proving with
+// the same key at the same time, takes the direct path.
+struct ProveGraphKey {
+  const void* ws;
+  size_t ws_bytes;
+  const int8_t* dX;
+  const int8_t* dW;
+  int32_t* dY;
+  int mode, dev;
+  uint32_t tune[ZKVC_PK_TUNING_LEN];
+};
+
+struct ProveGraph {
+  std::mutex mu;
+  ProveGraphKey key, cand, bad;  // captured; seen on the last call; failed to capture
+  bool has_key = false, has_cand = false, has_bad = false;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  unsigned long long launches = 0;  // kernels per replay
+  uint8_t* host = nullptr;          // pinned: rs (64 B) | GLV halves | proof (256 B) | flags
+  uint8_t* tables = nullptr;        // pinned: the MSM runs' table images (msm_table_stage)
+  static constexpr size_t GLV = 64, PROOF = 256, FLAGS = 512, BYTES = 1024, TABLE_BYTES = 256 << 10;
+};
+static_assert(ProveGraph::GLV + 2 * sizeof(GlvScalar) <= ProveGraph::PROOF, "staging layout");
+
+static ProveGraphKey graph_key(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, int32_t* dY,
+                               const void* ws, size_t ws_bytes, int dev) {
+  ProveGraphKey k;
+  std::memset(&k, 0, sizeof k);  // padding included: keys compare bytewise
+  k.ws = ws;
+  k.ws_bytes = ws_bytes;
+  k.dX = dX;
+  k.dW = dW;
+  k.dY = dY;
+  k.mode = mode;
+  k.dev = dev;
+  std::memcpy(k.tune, pk->prove_tune, sizeof k.tune);
+  return k;
+}
+
+static bool same_key(const ProveGraphKey& a, const ProveGraphKey& b) { return std::memcmp(&a, &b, sizeof a) == 0; }
+
+static std::mutex g_graph_create;
+
+static ProveGraph* graph_of(const zkvc_pk* pk) {
+  std::lock_guard<std::mutex> lock(g_graph_create);
+  if (!pk->graph) {
+    ProveGraph* g = new (std::nothrow) ProveGraph;
+    if (!g) return nullptr;
+    if (cudaMallocHost(&g->host, ProveGraph::BYTES) != cudaSuccess ||
+        cudaMallocHost(&g->tables, ProveGraph::TABLE_BYTES) != cudaSuccess) {
+      cudaGetLastError();
+      if (g->host) cudaFreeHost(g->host);
+      delete g;
+      return nullptr;
+    }
+    pk->graph = g;
+  }
+  return pk->graph;
+}
+
+// Forgets the captured graph and the candidate buffers (the autotuner's, freed after it).
+static void prove_graph_reset(const zkvc_pk* pk) {
+  ProveGraph* g = pk->graph;
+  if (!g) return;
+  std::lock_guard<std::mutex> lock(g->mu);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  g->exec = nullptr;
+  g->has_key = g->has_cand = g->has_bad = false;
+}
+
+void prove_graph_free(ProveGraph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  if (g->host) cudaFreeHost(g->host);
+  if (g->tables) cudaFreeHost(g->tables);
+  delete g;
+}
+
+static int capture_proof(ProveGraph* g, const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW,
+                         int32_t* dY, void* ws, size_t ws_bytes) {
+  if (g->exec) {
+    ZK_CUDA(cudaGraphExecDestroy(g->exec));
+    g->exec = nullptr;
+    g->has_key = false;
+  }
+  if (!g->cap) ZK_CUDA(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
+  const unsigned long long before = launches_so_far();
+  ZK_CUDA(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+  // every host source of the captured copies is pinned memory of this cache: r and s,
+  // their GLV halves, and the MSM tables (constant for the key: their pointers are the
+  // key's buffers)
+  msm_table_stage(g->tables, ProveGraph::TABLE_BYTES);
+  int rc = prove_enqueue_impl(pk, mode, dX, dW, g->host, reinterpret_cast<const GlvScalar*>(g->host + ProveGraph::GLV),
+                              dY, ws, ws_bytes, g->host + ProveGraph::PROOF,
+                              reinterpret_cast<int*>(g->host + ProveGraph::FLAGS), g->cap);
+  msm_table_stage(nullptr, 0);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
+  // the kernels counted while capturing run on every replay, not now
+  const unsigned long long n = launches_so_far() - before;
+  uncount_launches(n);
+  if (rc != ZKVC_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    ZK_TRY(rc);
+    ZK_CUDA(e);
+  }
+  const cudaError_t ie = cudaGraphInstantiateWithFlags(&g->exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) g->exec = nullptr;
+  ZK_CUDA(ie);
+  g->launches = n;
+  return ZKVC_OK;
+}
+
+int prove_graph(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, int32_t* dY,
+                void* ws, size_t ws_bytes, uint8_t* proof, cudaStream_t st) {
+  ProveGraph* g = prof_enabled() ? nullptr : graph_of(pk);
+  if (!g) return prove_impl(pk, mode, dX, dW, rs, dY, ws, ws_bytes, proof, st);
+  std::unique_lock<std::mutex> lock(g->mu, std::try_to_lock);
+  if (!lock.owns_lock()) return prove_impl(pk, mode, dX, dW, rs, dY, ws, ws_bytes, proof, st);
+  ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN, ZKVC_EINVAL, "prove: mode %d", mode);
+  int dev = 0;
+  ZK_CUDA(cudaGetDevice(&dev));
+  const ProveGraphKey k = graph_key(pk, mode, dX, dW, dY, ws, ws_bytes, dev);
+  if (!(g->exec && g->has_key && same_key(g->key, k))) {
+    if (g->has_bad && same_key(g->bad, k)) return prove_impl(pk, mode, dX, dW, rs, dY, ws, ws_bytes, proof, st);
+    if (!(g->has_cand && same_key(g->cand, k))) {
+      // a direct proof; its buffers become the candidate if it went through (so that a
+      // capture only ever repeats a sequence that has just run)
+      const int rc = prove_impl(pk, mode, dX, dW, rs, dY, ws, ws_bytes, proof, st);
+      g->cand = k;
+      g->has_cand = rc == ZKVC_OK || rc == ZKVC_EUNSAT;
+      return rc;
+    }
+    if (capture_proof(g, pk, mode, dX, dW, dY, ws, ws_bytes) != ZKVC_OK) {
+      // not capturable here (the direct path reports any real error): stay direct for
+      // these buffers until another key comes along
+      cudaGetLastError();
+      set_error("%s", "");
+      g->bad = k;
+      g->has_bad = true;
+      return prove_impl(pk, mode, dX, dW, rs, dY, ws, ws_bytes, proof, st);
+    }
+    g->key = k;
+    g->has_key = true;
+  }
+  std::memcpy(g->host, rs, 64);
+  if (mode == ZKVC_PROVE_CHAIN) {
+    GlvScalar* h = reinterpret_cast<GlvScalar*>(g->host + ProveGraph::GLV);
+    h[0] = glv_split(rs + 32);
+    h[1] = glv_split(rs);
+  }
+  ZK_CUDA(cudaGraphLaunch(g->exec, st));
+  count_launches(g->launches);
+  ZK_CUDA(cudaStreamSynchronize(st));
+  std::memcpy(proof, g->host + ProveGraph::PROOF, 256);
+  int flags = 0;
+  std::memcpy(&flags, g->host + ProveGraph::FLAGS, sizeof flags);
+  return prove_status(flags);
+}
+
+// Latency tuning of the one-proof prover (timing replays of the captured proof, as
+// zkvc_prove runs it): coordinate descent over the level-0 chunk of
 // each MSM run (the G2 and small-scalar runs first: their bucket sums are the longest
 // dependent chains), the NTT block and, in fold mode, the start of the rest MSM, timing
 // whole proofs with CUDA events on st.  With ZKVC_PROVE_AUTO both modes are tuned and the
@@ -533,15 +720,16 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
     return ZKVC_ECUDA;
   }
   uint8_t proof[256];
-  // median of nine timed proofs after one untimed
+  // median of nine timed proofs after two untimed, as zkvc_prove runs them: the first
+  // direct, the second captured, the timed ones replays of the captured graph
   auto measure = [&](int m, float* ms) -> int {
     float t[9];
-    for (int rep = 0; rep < 10; rep++) {
+    for (int rep = 0; rep < 11; rep++) {
       ZK_CUDA(cudaEventRecord(e0, st));
-      ZK_TRY(prove_impl(pk, m, dX, dW, rs, dY, ws, need, proof, st));
+      ZK_TRY(prove_graph(pk, m, dX, dW, rs, dY, ws, need, proof, st));
       ZK_CUDA(cudaEventRecord(e1, st));
       ZK_CUDA(cudaEventSynchronize(e1));
-      if (rep > 0) ZK_CUDA(cudaEventElapsedTime(&t[rep - 1], e0, e1));
+      if (rep > 1) ZK_CUDA(cudaEventElapsedTime(&t[rep - 2], e0, e1));
     }
     std::sort(t, t + 9);
     *ms = t[4];
@@ -596,6 +784,7 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
     rc = tune(mode, &ms);
     if (rc == ZKVC_OK) pk->prove_tune[6] = (uint32_t)mode;
   }
+  prove_graph_reset(pk);
   cleanup();
   if (rc != ZKVC_OK) {
     for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = saved[i];

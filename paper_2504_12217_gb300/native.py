@@ -35,6 +35,7 @@ SIGNATURES = {
     "zkvc_version": (_c_int, []),
     "zkvc_kernel_launches": (ctypes.c_uint64, []),
     "zkvc_profile_enable": (None, [_c_int]),
+    "zkvc_profile_span": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "zkvc_profile_read": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "zkvc_fr_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
@@ -173,7 +174,8 @@ def zkvc_profile_enable(on):
 
 
 def zkvc_profile_read():
-    """{stage name: {"ms": total ms, "calls": n, "units": accumulated units}}"""
+    """{stage name: {"ms": total ms, "calls": n, "units": accumulated units, "start_ms": mean
+    begin offset, "end_ms": mean end offset (both from the witness stage's begin)}}"""
     out = {}
     stage = 0
     while True:
@@ -183,7 +185,10 @@ def zkvc_profile_read():
                                      ctypes.byref(units))
         if rc != ZKVC_OK:
             return out
-        out[name.value.decode()] = {"ms": ms.value, "calls": calls.value, "units": units.value}
+        t0, t1 = ctypes.c_double(), ctypes.c_double()
+        check(lib().zkvc_profile_span(stage, ctypes.byref(t0), ctypes.byref(t1)))
+        out[name.value.decode()] = {"ms": ms.value, "calls": calls.value, "units": units.value,
+                                    "start_ms": t0.value, "end_ms": t1.value}
         stage += 1
 
 

@@ -209,3 +209,80 @@ def test_autotuned_and_imposed_tuning_prove_same_bytes(nv):
                 [0, 0, 0, 0, 0, 0, 0, 0, 2, 0]):
         with pytest.raises(nv.ZkvcError):
             nv.zkvc_pk_set_tuning(pk, bad)
+
+
+@pytest.mark.parametrize("mode", ["fold", "chain"])
+def test_stage_timeline_follows_the_stream_joins(nv, mode):
+    """The stage spans of a proof respect the prover's dependencies: the NTTs follow the
+    witness, the H-query MSM follows the NTTs, and the encoding of C follows every side
+    stream (H, G2 with B's encoding, the small-digit run with what follows it)."""
+    import torch
+    a, n, b = 5, 7, 3
+    inst = inputs.instance(31, (a, n, b))
+    pk, _ = nv.zkvc_setup(a, n, b, inputs.to_bytes32(inst["toxic"]))
+    m = {"fold": nv.ZKVC_PROVE_FOLD, "chain": nv.ZKVC_PROVE_CHAIN}[mode]
+    Xd, Wd = torch.from_numpy(inst["X"]).cuda(), torch.from_numpy(inst["W"]).cuda()
+    rs = inputs.to_bytes32(inst["rs"])
+    ref = nv.zkvc_prove_mode(pk, m, Xd, Wd, rs)[0]
+    nv.zkvc_profile_enable(True)
+    try:
+        for _ in range(3):
+            assert nv.zkvc_prove_mode(pk, m, Xd, Wd, rs)[0] == ref
+        prof = nv.zkvc_profile_read()
+    finally:
+        nv.zkvc_profile_enable(False)
+    span = {k: (v["start_ms"], v["end_ms"]) for k, v in prof.items() if v["calls"]}
+    for k in ("witness", "ntt", "msm_g1", "msm_g2", "msm_g1_small", "combine"):
+        assert prof[k]["calls"] == 3, k
+        assert 0.0 <= span[k][0] <= span[k][1], k
+    eps = 1e-3
+    assert span["witness"][0] == 0.0
+    assert span["ntt"][0] >= span["witness"][1] - eps
+    assert span["msm_g1"][0] >= span["ntt"][1] - eps
+    for k in ("msm_g1", "msm_g2", "msm_g1_small"):
+        assert span["combine"][0] >= span[k][1] - eps, k
+
+
+def test_graph_replays_match_direct_proofs(nv):
+    """zkvc_prove captures the proof as a CUDA graph once the same buffers come back and
+    replays it afterwards: every replayed proof (new r, s each time, both modes, a change
+    of tuning in between) equals the proof of a direct enqueue with fresh buffers, and a
+    replay runs as many kernels as a direct proof."""
+    import torch
+    a, n, b = 5, 7, 3
+    inst = inputs.instance(37, (a, n, b))
+    pk, vk = nv.zkvc_setup(a, n, b, inputs.to_bytes32(inst["toxic"]))
+    rng = random.Random(38)
+    rss = [inputs.to_bytes32((rng.randrange(1, bn.R), rng.randrange(1, bn.R))) for _ in range(10)]
+
+    def direct(mode, rs):  # fresh buffers every call: never the captured ones
+        Xd, Wd = torch.from_numpy(inst["X"]).cuda(), torch.from_numpy(inst["W"]).cuda()
+        return nv.zkvc_prove_mode(pk, mode, Xd, Wd, rs)[0]
+
+    Xd, Wd = torch.from_numpy(inst["X"]).cuda(), torch.from_numpy(inst["W"]).cuda()
+    Yd = torch.empty((a, b), dtype=torch.int32, device="cuda")
+    for mode in (nv.ZKVC_PROVE_CHAIN, nv.ZKVC_PROVE_FOLD):
+        ws = torch.empty(nv.zkvc_prove_workspace_bytes_mode(pk, mode), dtype=torch.uint8, device="cuda")
+        l0 = nv.zkvc_kernel_launches()
+        ref0 = direct(mode, rss[0])
+        per_direct = nv.zkvc_kernel_launches() - l0
+        for i, rs in enumerate(rss):
+            proof = nv.zkvc_prove_mode(pk, mode, Xd, Wd, rs, Y=Yd, workspace=ws)[0]
+            assert proof == (ref0 if i == 0 else direct(mode, rs)), (mode, i)
+            assert np.array_equal(Yd.cpu().numpy(), inst["X"].astype(np.int64) @ inst["W"].astype(np.int64))
+        l1 = nv.zkvc_kernel_launches()
+        nv.zkvc_prove_mode(pk, mode, Xd, Wd, rss[3], Y=Yd, workspace=ws)
+        assert nv.zkvc_kernel_launches() - l1 == per_direct
+    # a new tuning re-arms the capture; proofs stay the same
+    t = nv.zkvc_pk_get_tuning(pk)
+    t2 = list(t)
+    t2[2] = 16 if t[2] != 16 else 32
+    nv.zkvc_pk_set_tuning(pk, t2)
+    ws = torch.empty(nv.zkvc_prove_workspace_bytes(pk), dtype=torch.uint8, device="cuda")
+    mode = t2[6]
+    for rs in rss[:4]:
+        assert nv.zkvc_prove(pk, Xd, Wd, rs, Y=Yd, workspace=ws)[0] == direct(mode, rs)
+    X, W = _mats(inst["X"], inst["W"])
+    Y = (inst["X"].astype(np.int64) @ inst["W"].astype(np.int64)).tolist()
+    assert nv.zkvc_verify(vk, inst["X"], np.array(Y, dtype=np.int32), nv.zkvc_prove(pk, Xd, Wd, rss[5], Y=Yd,
+                                                                                     workspace=ws)[0])
