@@ -166,10 +166,41 @@ __global__ void k_add_into(G1J* acc, const G1J* x) {
   if (threadIdx.x == 0) st_field(acc, r);
 }
 
-// C = cpart + H (one quad), then its encoding (bytes 192..255)
-__global__ void k_encode_c(const G1J* cpart, const G1J* h, uint8_t* proof) {
-  const G1J C = p_add_quad(ld_field(cpart), ld_field(h));
-  if (threadIdx.x == 0) encode_g1(C, proof + 192);
+// C = cpart + H, then its canonical affine encoding (bytes 192..255), on one warp in
+// limb-sliced arithmetic: the addition, ZZ ZZZ and the products of the affine conversion
+// (x = X ZZZ / (ZZ ZZZ), y = Y ZZ / (ZZ ZZZ), then out of Montgomery form) run sliced,
+// the inversion in lane 0.
+__global__ void __launch_bounds__(32) k_encode_c(const G1J* cpart, const G1J* h, uint8_t* proof) {
+  __shared__ uint32_t zs[8], inv[8];
+  const SlG1 C = sl_padd(sl_ld(cpart), sl_ld(h));
+  const int j = sl_limb(), grp = sl_group();
+  uint8_t* out = proof + 192;
+  if (sl_is_zero(C.ZZ)) {  // infinity encodes as zeros
+    for (int i = threadIdx.x; i < 64; i += 32) out[i] = 0;
+    return;
+  }
+  const uint32_t z = sl_mul(C.ZZ, C.ZZZ);
+  if (grp == 0) zs[j] = z;
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    Fp zf;
+#pragma unroll
+    for (int i = 0; i < 8; i++) zf.v[i] = zs[i];
+    const Fp iv = f_inv(zf);
+#pragma unroll
+    for (int i = 0; i < 8; i++) inv[i] = iv.v[i];
+  }
+  __syncwarp();
+  const uint32_t m = sl_mul(inv[j], sl_pick(C.ZZZ, C.ZZ, C.ZZZ, C.ZZ));
+  const uint32_t a = sl_mul(sl_pick(C.X, C.Y, C.X, C.Y), m);  // group 0: x, group 1: y (Montgomery)
+  const uint32_t c = sl_mul(a, j == 0 ? 1u : 0u);             // times R^-1: canonical
+  if (grp < 2) {
+    uint8_t* o = out + 32 * grp + 4 * j;
+    o[0] = (uint8_t)c;
+    o[1] = (uint8_t)(c >> 8);
+    o[2] = (uint8_t)(c >> 16);
+    o[3] = (uint8_t)(c >> 24);
+  }
 }
 
 
@@ -478,7 +509,7 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
   }
   // 7. encode
   prof_mark(PS_COMBINE, true, st);
-  k_encode_c<<<1, 4, 0, st>>>(B.cpart, B.res_h, B.proof); ZK_COUNT_LAUNCH();
+  k_encode_c<<<1, 32, 0, st>>>(B.cpart, B.res_h, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   prof_mark(PS_COMBINE, false, st);
   ZK_CUDA(cudaMemcpyAsync(proof_out, B.proof, 256, cudaMemcpyDeviceToHost, st));
