@@ -27,6 +27,7 @@
 
 #include "coop.cuh"
 #include "msm.h"
+#include "sliced.cuh"
 
 namespace zkvc {
 
@@ -607,7 +608,9 @@ __global__ void __launch_bounds__(SliceBT<F>::value) k_bits_slices(const XYZZ<F>
   if (threadIdx.x == 0) st_field(S + sl, r);
 }
 
-// block per bit: U_b = the sum of the bit's slices, then 2^b U_b by b doublings (one quad)
+// block per bit: U_b = the sum of the bit's slices, then 2^b U_b by b doublings (G1: one
+// warp in limb-sliced arithmetic, about two thirds of a quad doubling's latency; G2: one
+// quad)
 constexpr int BITS_BT = 64;
 template <class F>
 __global__ void __launch_bounds__(BITS_BT) k_bits_scale(const XYZZ<F>* __restrict__ S, const BitSeg* __restrict__ segs,
@@ -616,9 +619,19 @@ __global__ void __launch_bounds__(BITS_BT) k_bits_scale(const XYZZ<F>* __restric
   const BitSeg g = segs[blockIdx.x];
   auto get = [&](uint32_t i) { return ld_field(S + g.soff + i); };
   XYZZ<F> x = block_sum<F, BITS_BT>(get, g.nsl, sh);
-  if (threadIdx.x >= 4) return;
-  for (uint32_t i = 0; i < g.b; i++) x = p_dbl_quad(x);
-  if (threadIdx.x == 0) st_field(D + g.dslot, x);
+  if constexpr (sizeof(F) == sizeof(Fp)) {
+    __shared__ G1J xs;
+    if (threadIdx.x == 0) st_field(&xs, x);
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    SlG1 y = sl_ld(&xs);
+    for (uint32_t i = 0; i < g.b; i++) y = sl_pdbl(y);
+    sl_st(D + g.dslot, y);
+  } else {
+    if (threadIdx.x >= 4) return;
+    for (uint32_t i = 0; i < g.b; i++) x = p_dbl_quad(x);
+    if (threadIdx.x == 0) st_field(D + g.dslot, x);
+  }
 }
 
 // block per (output, window): the window's c terms 2^b U_b, summed into the first slot

@@ -173,31 +173,42 @@ __device__ __forceinline__ uint32_t sl_from(uint32_t m, int k) {
   return __shfl_sync(SL_FULL, m, 8 * k + sl_limb());
 }
 
-// dbl-2008-s-1 in three product rounds (as p_dbl_quad_body in coop.cuh)
+// dbl-2008-s-1 (U = 2Y, V = U^2, W = U V, S = X V, M = 3 X^2, X3 = M^2 - 2S,
+// Y3 = M (S - X3) - W Y, ZZ3 = V ZZ, ZZZ3 = W ZZZ) in three product rounds with four
+// levels of additions and subtractions (an addition costs two ballot round trips here):
+// 2X and 3X come first, so that M = X (3X), 2S = (2X) V and 3S = (3X) V are products, and
+// X3 = M^2 - 2S and S - X3 = 3S - M^2 are one level.
+//   (V = U^2, M = X 3X)  ->  (W = U V, M^2, 2S, 3S)  ->  (M (S - X3), W Y, W ZZZ, V ZZ)
 static __device__ __noinline__ SlG1 sl_pdbl(SlG1 p) {
   const bool inf = sl_is_zero(p.ZZ), y0 = sl_is_zero(p.Y);
   if (inf || y0) return sl_inf();
-  const uint32_t U = sl_add(p.Y, p.Y);
-  uint32_t m = sl_mul(sl_pick(U, p.X, U, p.X), sl_pick(U, p.X, U, p.X));
-  const uint32_t V = sl_from(m, 0), X2 = sl_from(m, 1);
-  const uint32_t M = sl_add(sl_add(X2, X2), X2);
-  m = sl_mul(sl_pick(U, p.X, M, V), sl_pick(V, V, M, p.ZZ));
-  const uint32_t W = sl_from(m, 0), S = sl_from(m, 1), MM = sl_from(m, 2), ZZ3 = sl_from(m, 3);
-  const uint32_t X3 = sl_sub(MM, sl_add(S, S));
-  const uint32_t SX = sl_sub(S, X3);
-  m = sl_mul(sl_pick(M, W, W, M), sl_pick(SX, p.Y, p.ZZZ, SX));
+  const uint32_t U = sl_add(p.Y, p.Y), X2 = sl_add(p.X, p.X);
+  const uint32_t X3x = sl_add(X2, p.X);
+  uint32_t m = sl_mul(sl_pick(U, p.X, U, p.X), sl_pick(U, X3x, U, X3x));
+  const uint32_t V = sl_from(m, 0), M = sl_from(m, 1);
+  m = sl_mul(sl_pick(U, M, X2, X3x), sl_pick(V, M, V, V));
+  const uint32_t W = sl_from(m, 0), MM = sl_from(m, 1), S2 = sl_from(m, 2), S3 = sl_from(m, 3);
+  const uint32_t X3 = sl_sub(MM, S2), SX = sl_sub(S3, MM);
+  m = sl_mul(sl_pick(M, W, W, V), sl_pick(SX, p.Y, p.ZZZ, p.ZZ));
   const uint32_t Y3 = sl_sub(sl_from(m, 0), sl_from(m, 1));
-  return {X3, Y3, ZZ3, sl_from(m, 2)};
+  return {X3, Y3, sl_from(m, 3), sl_from(m, 2)};
 }
 
-// add-2008-s in four product rounds (as p_add_quad_body in coop.cuh)
+// add-2008-s (U1 = X1 ZZ2, U2 = X2 ZZ1, S1 = Y1 ZZZ2, S2 = Y2 ZZZ1, P = U2 - U1,
+// R = S2 - S1, PP = P^2, PPP = P PP, Q = U1 PP, X3 = R^2 - PPP - 2Q, Y3 = R (Q - X3) -
+// S1 PPP, ZZ3 = ZZ1 ZZ2 PP, ZZZ3 = ZZZ1 ZZZ2 PPP) in four product rounds with four
+// levels of additions and subtractions: the third round's free product gives 2Q =
+// (2 U1) PP, so that X3 = (R^2 - PPP) - 2Q and Q - X3 = 3Q - (R^2 - PPP) are one level
+// after R^2 - PPP and 3Q.
+//   (U1, U2, S1, S2)  ->  (P^2, R^2, ZZ1 ZZ2, ZZZ1 ZZZ2)  ->  (PPP, Q, ZZ3, 2Q)
+//   ->  (R (Q - X3), S1 PPP, ZZZ3)
 static __device__ __noinline__ SlG1 sl_padd(SlG1 p, SlG1 q) {
   const bool qi = sl_is_zero(q.ZZ), pi = sl_is_zero(p.ZZ);
   if (qi) return p;
   if (pi) return q;
   uint32_t m = sl_mul(sl_pick(p.X, q.X, p.Y, q.Y), sl_pick(q.ZZ, p.ZZ, q.ZZZ, p.ZZZ));
   const uint32_t U1 = sl_from(m, 0), U2 = sl_from(m, 1), S1 = sl_from(m, 2), S2 = sl_from(m, 3);
-  const uint32_t P = sl_sub(U2, U1), R = sl_sub(S2, S1);
+  const uint32_t P = sl_sub(U2, U1), R = sl_sub(S2, S1), U1x2 = sl_add(U1, U1);
   const bool p0 = sl_is_zero(P), r0 = sl_is_zero(R);
   if (p0) {
     if (r0) return sl_pdbl(p);
@@ -205,10 +216,10 @@ static __device__ __noinline__ SlG1 sl_padd(SlG1 p, SlG1 q) {
   }
   m = sl_mul(sl_pick(P, R, p.ZZ, p.ZZZ), sl_pick(P, R, q.ZZ, q.ZZZ));
   const uint32_t PP = sl_from(m, 0), RR = sl_from(m, 1), Z2 = sl_from(m, 2), Z3 = sl_from(m, 3);
-  m = sl_mul(sl_pick(P, U1, Z2, P), PP);
-  const uint32_t PPP = sl_from(m, 0), Q = sl_from(m, 1), ZZ3 = sl_from(m, 2);
-  const uint32_t X3 = sl_sub(sl_sub(RR, PPP), sl_add(Q, Q));
-  const uint32_t QX = sl_sub(Q, X3);
+  m = sl_mul(sl_pick(P, U1, Z2, U1x2), PP);
+  const uint32_t PPP = sl_from(m, 0), Q = sl_from(m, 1), ZZ3 = sl_from(m, 2), Q2 = sl_from(m, 3);
+  const uint32_t A = sl_sub(RR, PPP), Q3 = sl_add(Q, Q2);
+  const uint32_t X3 = sl_sub(A, Q2), QX = sl_sub(Q3, A);
   m = sl_mul(sl_pick(R, S1, Z3, R), sl_pick(QX, PPP, PPP, QX));
   const uint32_t Y3 = sl_sub(sl_from(m, 0), sl_from(m, 1));
   return {X3, Y3, ZZ3, sl_from(m, 2)};
