@@ -90,6 +90,15 @@ int zkvc_fp2_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t 
  * approximations of the operands.  Returns ZKVC_EINVAL on a null pointer with n > 0.
  */
 int zkvc_fr_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream);
+
+/* The host-side GLV split of the chain-mode scalar multiplications (G1 of BN254 has the
+ * endomorphism phi(x, y) = (beta x, y) = lambda (x, y)): k (32 bytes little-endian,
+ * k < r) = k1 + k2 lambda (mod r) with |k1|, |k2| < 2^127, by rounding against a short
+ * basis of the lattice {(x, y) : x + y lambda = 0 mod r} (Gallant, Lambert, Vanstone).
+ * out: |k1| (16 bytes little-endian), sign of k1 (1 byte: 1 = negative), then |k2| and
+ * its sign (34 bytes).  Host only; ZKVC_EINVAL on a null pointer.
+ */
+int zkvc_glv_split(const uint8_t k[32], uint8_t out[34]);
 int zkvc_fp_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream);
 
 /* ------------------------------------------------------------------ witness matmul

@@ -6,6 +6,7 @@
 #include <string>
 #include <thread>
 
+#include "glv.h"
 #include "msm.h"
 #include "ntt.h"
 
@@ -232,6 +233,18 @@ extern "C" {
 const char* zkvc_last_error(void) { return g_err.c_str(); }
 
 int zkvc_version(void) { return 100; }
+
+int zkvc_glv_split(const uint8_t k[32], uint8_t out[34]) {
+  clear_error();
+  ZK_CHECK(k && out, ZKVC_EINVAL, "glv_split: null pointer");
+  const GlvScalar g = glv_split(k);
+  for (int h = 0; h < 2; h++) {
+    for (int i = 0; i < 4; i++)
+      for (int b = 0; b < 4; b++) out[17 * h + 4 * i + b] = (uint8_t)(g.h[h].mag[i] >> (8 * b));
+    out[17 * h + 16] = (uint8_t)g.h[h].neg;
+  }
+  return ZKVC_OK;
+}
 
 uint64_t zkvc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -42,6 +42,7 @@ SIGNATURES = {
     "zkvc_fp_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_fp2_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_fr_inv": (_c_int, [_c_p, _c_p, _c_sz, _c_p]),
+    "zkvc_glv_split": (_c_int, [_c_p, _c_p]),
     "zkvc_fp_inv": (_c_int, [_c_p, _c_p, _c_sz, _c_p]),
     "zkvc_ntt": (_c_int, [_c_p, _c_u32, _c_int, _c_p]),
     "zkvc_matmul_i8": (_c_int, [_c_p, _c_p, _c_p, _c_int, _c_int, _c_int, _c_p]),
@@ -203,6 +204,19 @@ def zkvc_fp_mul(a, b, out=None):
 
 def zkvc_fp2_mul(a, b, out=None):
     return _field_mul("zkvc_fp2_mul", a, b, out, 64)
+
+
+def zkvc_glv_split(k):
+    """(k1, k2) as signed Python ints with k = k1 + k2 lambda (mod r), for 0 <= k < r."""
+    kb = ctypes.create_string_buffer(int(k).to_bytes(32, "little"), 32)
+    out = ctypes.create_string_buffer(34)
+    check(lib().zkvc_glv_split(kb, out))
+    raw = out.raw
+    halves = []
+    for h in range(2):
+        mag = int.from_bytes(raw[17 * h:17 * h + 16], "little")
+        halves.append(-mag if raw[17 * h + 16] else mag)
+    return tuple(halves)
 
 
 def zkvc_fr_inv(a, out=None):
