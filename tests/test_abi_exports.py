@@ -29,6 +29,13 @@ def test_argument_errors_need_no_gpu():
     assert b"null" in lib.zkvc_last_error()
     assert lib.zkvc_ntt(ctypes.c_void_p(16), 4, 9, None) == nv.ZKVC_EINVAL
     assert lib.zkvc_fr_mul(None, None, None, 4, None) == nv.ZKVC_EINVAL
+    assert lib.zkvc_fr_inv(None, None, 4, None) == nv.ZKVC_EINVAL
+    assert lib.zkvc_fp_inv(None, None, 4, None) == nv.ZKVC_EINVAL
+    assert lib.zkvc_fp_inv(None, None, 0, None) == nv.ZKVC_OK  # n = 0: nothing to do
+    t0, t1 = ctypes.c_double(), ctypes.c_double()
+    assert lib.zkvc_profile_span(-1, ctypes.byref(t0), ctypes.byref(t1)) == nv.ZKVC_EINVAL
+    assert lib.zkvc_profile_span(1 << 20, None, None) == nv.ZKVC_EINVAL
+    assert lib.zkvc_profile_span(0, ctypes.byref(t0), ctypes.byref(t1)) == nv.ZKVC_OK
     out = (ctypes.c_uint8 * 64)()
     assert lib.zkvc_msm_g1(None, None, 0, None, 0, out, None) == nv.ZKVC_OK   # n = 0: infinity
     assert bytes(out) == bytes(64)
