@@ -545,11 +545,13 @@ int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, 
 // memsets, copies and the fork/join events of its five streams) once a key is proven
 // with the same buffers, mode and tuning on two calls in a row: the first of the two
 // runs directly and records the buffers, the second captures the enqueue on a capture
-// stream and instantiates it with the streams' priorities kept per node.  The graph reads
-// r, s and their GLV halves from pinned host memory that the host fills before each
-// replay and writes the proof and the device flags to pinned memory.  A change of
-// buffers, mode or tuning re-arms the capture; profiling, or another thread proving with
-// the same key at the same time, takes the direct path.
+// stream and instantiates it with the streams' priorities kept per node.  A captured copy
+// reads its host source again on every replay, so every host source is pinned memory of
+// this cache: r, s and their GLV halves (filled by the host before each replay) and the
+// MSM runs' table images (constant for the buffers: the tables hold their pointers); the
+// proof and the device flags land in pinned memory too.  A change of buffers, mode or
+// tuning re-arms the capture; profiling, or another thread proving with the same key at
+// the same time, takes the direct path.
 struct ProveGraphKey {
   const void* ws;
   size_t ws_bytes;
