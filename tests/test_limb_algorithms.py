@@ -133,3 +133,46 @@ def test_carry_lookahead_identity():
         S = (G | P) + G
         assert [((S ^ P) >> j) & 1 for j in range(8)] == ripple
         assert (S >> 8) & 1 == carry
+
+
+def test_sliced_point_formula_arrangements():
+    """The XYZZ doubling and addition exactly as sliced.cuh arranges them (2X and 3X
+    first, so that M = X 3X, 2S = 2X V and 3S = 3X V are products, X3 = M^2 - 2S and
+    S - X3 = 3S - M^2; the addition's 2Q = 2U1 PP, X3 = (R^2 - PPP) - 2Q and
+    Q - X3 = 3Q - (R^2 - PPP)) give the oracle's affine doubling and addition on random
+    points in random XYZZ representations."""
+    P = bn.P
+
+    def dbl(X, Y, ZZ, ZZZ):
+        U, X2 = 2 * Y % P, 2 * X % P
+        X3x = (X2 + X) % P
+        V, M = U * U % P, X * X3x % P
+        W, MM, S2, S3 = U * V % P, M * M % P, X2 * V % P, X3x * V % P
+        X3, SX = (MM - S2) % P, (S3 - MM) % P
+        return X3, (M * SX - W * Y) % P, V * ZZ % P, W * ZZZ % P
+
+    def add(p, q):
+        X1, Y1, ZZ1, ZZZ1 = p
+        X2, Y2, ZZ2, ZZZ2 = q
+        U1, U2, S1, S2 = X1 * ZZ2 % P, X2 * ZZ1 % P, Y1 * ZZZ2 % P, Y2 * ZZZ1 % P
+        Pd, R, U1x2 = (U2 - U1) % P, (S2 - S1) % P, 2 * U1 % P
+        PP, RR, Z2, Z3 = Pd * Pd % P, R * R % P, ZZ1 * ZZ2 % P, ZZZ1 * ZZZ2 % P
+        PPP, Q, ZZ3, Q2 = Pd * PP % P, U1 * PP % P, Z2 * PP % P, U1x2 * PP % P
+        A, Q3 = (RR - PPP) % P, (Q + Q2) % P
+        X3, QX = (A - Q2) % P, (Q3 - A) % P
+        return X3, (R * QX - S1 * PPP) % P, ZZ3, Z3 * PPP % P
+
+    def affine(pt):
+        X, Y, ZZ, ZZZ = pt
+        return X * pow(ZZ, -1, P) % P, Y * pow(ZZZ, -1, P) % P
+
+    def xyzz(A, z):
+        return A[0] * z * z % P, A[1] * z * z * z % P, z * z % P, z * z * z % P
+
+    rng = random.Random(53)
+    for _ in range(60):
+        A = bn.g1_mul(bn.G1_GEN, rng.randrange(1, bn.R))
+        B = bn.g1_mul(bn.G1_GEN, rng.randrange(1, bn.R))
+        a, b = xyzz(A, rng.randrange(1, P)), xyzz(B, rng.randrange(1, P))
+        assert affine(dbl(*a)) == bn.g1_add(A, A)
+        assert affine(add(a, b)) == bn.g1_add(A, B)
