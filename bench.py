@@ -14,8 +14,13 @@ and PSQ evaluation, the NTT chain to h(x), every MSM, and the proof encoding.
               algorithmic work), timed live with CUDA events on its stream; its algorithmic
               work is one mixed point addition per bucket term (10 Montgomery products of
               264 32-bit IMADs in G1).
-* ``cpu_baseline`` the oracle (tests' reference implementation) on a bounded sample of
-              the same workload, extrapolated to one proof.
+* ``ntt_roofline`` the prover's NTT chain live at 2^16 points and one 2^24-point
+              transform: fractions of the measured integer peak and of HBM bandwidth.
+* ``batched`` / ``served`` the 64-proof batched workload (one captured graph per 64
+              proofs) and Poisson-served requests over 32 shapes, each beside the plain
+              one-proof path on the same instances.
+* ``cpu_baseline`` the oracle (tests' reference implementation) proving one whole
+              instance on all host cores, measured.
 
 With ``--gpus N`` under torchrun every rank proves its own instances (replicas: proofs
 are independent, no collective on the data path); value = all proofs / max rank time.
@@ -37,9 +42,7 @@ if ROOT not in sys.path:
 METRIC = "CRPC-matmul Groth16 proofs/s + p50/p99 latency; MSM/NTT % of roofline"
 UNIT = "proofs/s"
 SHAPE = (49, 320, 512)
-SMS = 152
-IMAD_PER_CLK_SM = 64          # 32-bit integer multiply-add issue rate per SM per clock
-SM_MAX_MHZ = 2070.0
+IMAD_PER_CLK_SM = 64          # nominal 32-bit integer multiply-add rate per SM per clock (context)
 MONT_IMAD = 4 * 8 * 8 + 8     # CIOS product on 8 x 32-bit limbs
 G1_MADD_PRODUCTS = 10         # madd-2008-s: 8M + 2S
 G2_MADD_PRODUCTS = 30         # the same over Fp2, 3 Fp products per Fp2 product
@@ -123,72 +126,149 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle baseline
-def oracle_sample(seed, frac=1.0):
-    """Time the oracle on a bounded sample of one proof and extrapolate to the whole proof.
+# The oracle (the tests' plain reference implementation) proving one [49,320]x[320,512]
+# instance on the host cores: the steps of oracle.groth16.prove -- witness, domain
+# evaluations, the quotient through the textbook NTTs, every naive MSM -- with the
+# independent transforms and the MSMs' point ranges spread over a spawn pool of worker
+# processes (one per core).  Proving-key points stand in as arithmetic progressions
+# [c + i d]G of the right counts (the oracle's own setup at this size would take about
+# 40 core-minutes, and an MSM's cost does not depend on which points it sums).
 
-    Sample: matmul on 2 of the 49 rows; CRPC evaluations in full; one textbook NTT of
-    2^14 points scaled to the seven 2^16-point transforms by N log N; naive scalar
-    multiplications on 64 points of each scalar type (int8 X/W, int32 Y, full Fr S/h, G2
-    int8) scaled by the term counts of each query.  Returns (seconds per proof, details).
-    """
-    import random
-
+def _oracle_points(job):
+    """Stand-in key points: [c + i d] G for i < count, by repeated affine addition."""
     from oracle import bn254 as bn
-    from oracle import crpc
-    from oracle import ntt as ont
-    from paper_2504_12217_gb300 import inputs
+    group, c, d, count = job
+    mul, add, gen = (bn.g1_mul, bn.g1_add, bn.G1_GEN) if group == 1 else (bn.g2_mul, bn.g2_add, bn.G2_GEN)
+    P, D = mul(gen, c), mul(gen, d)
+    out = []
+    for _ in range(count):
+        out.append(P)
+        P = add(P, D)
+    return out
 
-    a, n, b = SHAPE
-    inst = inputs.instance(seed, SHAPE)
-    X = inst["X"].astype(int).tolist()
-    W = inst["W"].astype(int).tolist()
-    z = inst["toxic"][5]
-    rng = random.Random(seed)
-    parts = {}
-    m = max(8, int(64 * frac))
 
-    t = time.perf_counter()
-    rows = 2
-    crpc.matmul_int(X[:rows], W)
-    parts["matmul"] = (time.perf_counter() - t) * a / rows
+def _oracle_task(job):
+    """One unit of the oracle's prove: a transform of oracle.ntt, or a naive MSM slice."""
+    from oracle import bn254 as bn
+    from oracle import ntt as nt
+    kind = job[0]
+    if kind == "ntt":
+        return getattr(nt, job[1])(job[2])
+    pts, sc = job[1], job[2]
+    return bn.g1_msm(pts, sc) if kind == "g1" else bn.g2_msm(pts, sc)
 
-    t = time.perf_counter()
-    crpc.crpc_evaluations(X, W, z)
-    parts["crpc_eval"] = time.perf_counter() - t
 
-    N = 1 << 16
-    ns = 1 << 14
-    vec = [rng.randrange(bn.R) for _ in range(ns)]
-    t = time.perf_counter()
-    ont.ntt(vec)
-    parts["ntt"] = (time.perf_counter() - t) * 7 * (N * 16) / (ns * 14)
+class OracleProver:
+    """Key stand-ins and the pool, made once (not timed); prove() times one proof."""
 
-    P1 = bn.g1_mul(bn.G1_GEN, rng.randrange(1, bn.R))
-    P2 = bn.g2_mul(bn.G2_GEN, rng.randrange(1, bn.R))
+    def __init__(self, seed, cores=None):
+        import multiprocessing as mp
+        import random
 
-    def per_op(fn, scalars):
+        from oracle import crpc
+        from paper_2504_12217_gb300 import inputs
+        a, n, b = SHAPE
+        self.inst = inputs.instance(seed, SHAPE)
+        self.z = self.inst["toxic"][5]
+        self.shape = crpc.Shape(a, n, b)
+        self.rows = crpc.build_r1cs(self.shape, self.z)
+        sA, sB = set(), set()
+        for A, B, _ in self.rows:
+            sA.update(A)
+            sB.update(B)
+        self.A_vars, self.B_vars = sorted(sA), sorted(sB)
+        self.L_vars = list(range(self.shape.n_public + 1, self.shape.n_vars))
+        self.N = self.shape.domain
+        self.cores = cores or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        rng = random.Random(seed)
+        counts = {"A": len(self.A_vars), "B1": len(self.B_vars), "L": len(self.L_vars), "H": self.N - 1}
+        self.pts = {}
+        for name, cnt in list(counts.items()) + [("B2", len(self.B_vars))]:
+            group = 2 if name == "B2" else 1
+            step = max(1, cnt // (4 * self.cores) + 1)
+            jobs = [(group, rng.randrange(1, 1 << 250), rng.randrange(1, 1 << 250), min(step, cnt - o))
+                    for o in range(0, cnt, step)]
+            self.pts[name] = [p for part in self.pool.map(_oracle_points, jobs) for p in part]
+        self.consts = _oracle_points((1, rng.randrange(1, 1 << 250), 1, 4)) + _oracle_points(
+            (2, rng.randrange(1, 1 << 250), 1, 2))
+
+    def close(self):
+        self.pool.terminate()
+
+    def prove(self, r, s, frac=1.0):
+        """Seconds of one proof; frac < 1 runs each MSM on that share of its terms and
+        scales its part by the term counts (the witness and quotient always run whole)."""
+        from oracle import bn254 as bn
+        from oracle import crpc
+        from oracle import groth16 as og
+        X = self.inst["X"].astype(int).tolist()
+        W = self.inst["W"].astype(int).tolist()
+        N = self.N
+        parts = {}
         t0 = time.perf_counter()
-        for s in scalars:
-            fn(s)
-        return (time.perf_counter() - t0) / len(scalars)
+        Y = crpc.matmul_int(X, W)
+        w = crpc.witness(self.shape, X, W, self.z, Y)
+        Aev, Bev, Cev = og.domain_evaluations(self.rows, w, N)
+        parts["witness"] = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        a, b, c = self.pool.map(_oracle_task, [("ntt", "intt", v) for v in (Aev, Bev, Cev)])
+        ae, be, ce = self.pool.map(_oracle_task, [("ntt", "coset_ntt", v) for v in (a, b, c)])
+        zinv = pow((pow(bn.FR_GEN, N, bn.R) - 1) % bn.R, -1, bn.R)
+        hev = [((x * y - zz) * zinv) % bn.R for x, y, zz in zip(ae, be, ce)]
+        h = self.pool.apply(_oracle_task, (("ntt", "coset_intt", hev),))
+        parts["quotient"] = time.perf_counter() - t1
+        t2 = time.perf_counter()
+        msms = [("g1", "A", [w[i] for i in self.A_vars]), ("g1", "B1", [w[i] for i in self.B_vars]),
+                ("g2", "B2", [w[i] for i in self.B_vars]), ("g1", "L", [w[i] for i in self.L_vars]),
+                ("g1", "H", h[:N - 1])]
+        jobs, owner, scale = [], [], {}
+        for kind, name, sc in msms:
+            pts = self.pts[name]
+            take = max(1, int(len(sc) * frac))
+            scale[name] = len(sc) / take
+            step = max(1, take // (4 * self.cores) + 1)
+            for o in range(0, take, step):
+                jobs.append((kind, pts[o:o + step], sc[o:o + step]))
+                owner.append(name)
+        order = sorted(range(len(jobs)), key=lambda j: owner[j] != "H")
+        res = self.pool.map(_oracle_task, [jobs[j] for j in order], chunksize=1)
+        sums = {}
+        for j, v in zip(order, res):
+            nm = owner[j]
+            sums[nm] = (bn.g2_add if nm == "B2" else bn.g1_add)(sums.get(nm), v)
+        al, be1, de1, _, be2, de2 = self.consts
+        A = bn.g1_add(bn.g1_add(al, sums["A"]), bn.g1_mul(de1, r))
+        B1 = bn.g1_add(bn.g1_add(be1, sums["B1"]), bn.g1_mul(de1, s))
+        bn.g2_add(bn.g2_add(be2, sums["B2"]), bn.g2_mul(de2, s))
+        C = bn.g1_add(sums["L"], sums["H"])
+        C = bn.g1_add(C, bn.g1_mul(A, s))
+        C = bn.g1_add(C, bn.g1_mul(B1, r))
+        bn.g1_add(C, bn.g1_neg(bn.g1_mul(de1, r * s % bn.R)))
+        msm_s = time.perf_counter() - t2
+        parts["msm"] = msm_s * (max(scale.values()) if frac < 1.0 else 1.0)
+        total = parts["witness"] + parts["quotient"] + parts["msm"]
+        return total, parts
 
-    i8 = [bn.fr_from_int(rng.randint(-128, 127)) for _ in range(m)]
-    i32 = [bn.fr_from_int(rng.randint(-(1 << 22), 1 << 22)) for _ in range(m)]
-    full = [rng.randrange(bn.R) for _ in range(m)]
-    c_i8 = per_op(lambda s: bn.g1_mul(P1, s), i8)
-    c_i32 = per_op(lambda s: bn.g1_mul(P1, s), i32)
-    c_full = per_op(lambda s: bn.g1_mul(P1, s), full)
-    c_g2_i8 = per_op(lambda s: bn.g2_mul(P2, s), i8)
-    c_g2_full = per_op(lambda s: bn.g2_mul(P2, s), full[: max(4, m // 8)])
-    an, ab, nb = a * n, a * b, n * b
-    parts["msm_A"] = c_i8 * an + c_i32 * ab + c_full
-    parts["msm_B1"] = c_i8 * nb + c_full
-    parts["msm_B2"] = c_g2_i8 * nb + c_g2_full
-    parts["msm_L"] = c_i8 * nb + c_full * (n - 1)
-    parts["msm_H"] = c_full * (N - 1)
-    parts["randomisation"] = c_full * 4
-    total = sum(parts.values())
-    return total, parts
+
+def cpu_baseline(args):
+    """One whole oracle proof of the benchmark's instance on all host cores (measured)."""
+    from paper_2504_12217_gb300 import inputs
+    seed = inputs.SEED_CFG[2]
+    t0 = time.perf_counter()
+    op = OracleProver(seed)
+    prep = time.perf_counter() - t0
+    try:
+        r, s = inputs.prover_values(seed)
+        sec, parts = op.prove(r, s)
+    finally:
+        op.close()
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": op.cores, "kind": "oracle",
+            "sample": "one whole [49,320]x[320,512] proof with the oracle's prove steps (witness, domain "
+                      "evaluations, textbook-NTT quotient, every naive MSM), transforms and MSM point ranges "
+                      "over a spawn pool of all host cores; key points are stand-in arithmetic progressions "
+                      "of the right counts (built before timing)",
+            "seconds_per_proof": sec, "parts_s": parts, "key_standins_s": prep}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -198,27 +278,36 @@ def run_reference(args):
         return 0
     from paper_2504_12217_gb300 import inputs
     seed = inputs.SEED_CFG[2]
-    for _ in range(args.warmup):
-        oracle_sample(seed, frac=0.25)
-    times = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sec, _ = oracle_sample(seed, frac=0.25)
-        times.append(sec)
-    wall = time.perf_counter() - t0
+    frac = 1.0 / 16
+    op = OracleProver(seed)
+    try:
+        total = args.warmup + args.steps
+        rs = [inputs.prover_values(seed * 1000 + i) for i in range(total)]
+        for i in range(args.warmup):
+            op.prove(*rs[i], frac=frac)
+        times = []
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            sec, _ = op.prove(*rs[args.warmup + i], frac=frac)
+            times.append(sec)
+        wall = time.perf_counter() - t0
+    finally:
+        op.close()
     per_proof = statistics.median(times)
     value = 1.0 / per_proof
-    sample = ("per step: matmul on 2 of 49 rows, full CRPC evaluations, one 2^14-point textbook NTT "
-              "scaled to seven 2^16 transforms, 16 naive scalar multiplications per scalar type scaled "
-              "by each query's term count; extrapolated to one [49,320]x[320,512] proof")
+    sample = ("per step: the oracle's prove steps for the [49,320]x[320,512] instance on a spawn pool of all host "
+              "cores -- witness, domain evaluations and the textbook-NTT quotient whole, each naive MSM on 1/16 "
+              "of its terms with its time scaled by 16; key points are stand-in arithmetic progressions")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_proof * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "python-int (exact)", "data": "synthetic",
         "config": {"workload": "crpc_groth16_bn254_49x320x512", "a": SHAPE[0], "n": SHAPE[1], "b": SHAPE[2],
                    "log_domain": 16},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                         "wall_s": wall},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": op.cores, "kind": "oracle", "sample": sample,
+                         "extrapolated": True, "wall_s": wall,
+                         "note": "ms_per_step is the extrapolated time of one whole proof; the timed steps "
+                                 "themselves ran the sample above"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -236,6 +325,78 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def nominal_imad_peak(sms, mhz):
+    """The unit-count figure the measured peak stands beside: SMs x 64 IMAD/clk x clock."""
+    return sms * IMAD_PER_CLK_SM * mhz * 1e6
+
+
+def measure_imad_peak(nv, local):
+    """The integer-pipe peak measured on this GPU (zkvc_imad_rate): the faster of the two
+    microbenchmark forms, with the SM clock sampled while it runs."""
+    clocks = ClockSampler(local)
+    clocks.start()
+    forms = {"independent_mad_lo": nv.zkvc_imad_rate(0, 1 << 18), "cios_carry_row": nv.zkvc_imad_rate(1, 1 << 18)}
+    clk = clocks.stop()
+    best = max(forms.values(), key=lambda f: f["imad_per_s"])
+    return {"imad_per_s": best["imad_per_s"], "sms": best["sms"], "forms": forms, "clocks": clk}
+
+
+def ntt_passes(log_n):
+    """HBM passes of one transform as the method counts them: one below 2^20 points
+    (the transform fits on chip per block of stages), two from 2^20 up."""
+    return 1 if log_n < 20 else 2
+
+
+def ntt_work(log_n, transforms=1):
+    """(IMADs, bytes) of `transforms` radix-2 NTTs of 2^log_n points: (N/2) log N
+    butterflies of one Montgomery product each, and 64 B per point per HBM pass."""
+    n = 1 << log_n
+    return transforms * (n // 2) * log_n * MONT_IMAD, transforms * ntt_passes(log_n) * 64 * n
+
+
+def ntt_roofline(nv, prof, log_n_proof, imad_peak, hbm_peak, hbm_src):
+    """NTT fractions of the integer and HBM peaks: the quotient chain live in the proof
+    (seven transforms of 2^16 points and the pointwise quotient), and one timed 2^24
+    forward transform on uniform Fr data."""
+    import torch
+    out = {"bytes_rule": "64 B per point per HBM pass; 1 pass below 2^20 points, 2 from 2^20",
+           "imad_rule": "(N/2) log2 N butterflies x 264 IMAD per transform (scalings and the quotient's "
+                        "products not counted)"}
+    st = prof.get("ntt", {"ms": 0, "calls": 0})
+    if st["calls"]:
+        ms = st["ms"] / st["calls"]
+        imad, nbytes = ntt_work(log_n_proof, 7)
+        out["in_proof"] = {"log_n": log_n_proof, "transforms": 7, "ms": ms,
+                           "imad_frac": imad / (ms / 1e3) / imad_peak, "hbm_gbs": nbytes / ms / 1e6,
+                           "hbm_frac": nbytes / ms / 1e6 / hbm_peak,
+                           "note": "the prover's quotient chain (3 INTT, 3 coset NTT, quotient, coset INTT) on "
+                                   "its stream, stage timers"}
+    log_n = 24
+    n = 1 << log_n
+    g = torch.Generator(device="cuda").manual_seed(0x5A4B5643_00000003)
+    x = torch.randint(0, 256, (n, 32), dtype=torch.uint8, device="cuda", generator=g)
+    x[:, 31] &= 0x0F
+    nv.zkvc_ntt(x, 0)
+    torch.cuda.synchronize()
+    reps = 5
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for e0, e1 in evs:  # 512 MiB of points: larger than L2 on its own
+        e0.record()
+        nv.zkvc_ntt(x, 0)
+        e1.record()
+    torch.cuda.synchronize()
+    ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in evs)
+    imad, nbytes = ntt_work(log_n)
+    out["full_2e24"] = {"log_n": log_n, "kind": "forward", "ms": ms, "imad_frac": imad / (ms / 1e3) / imad_peak,
+                        "hbm_gbs": nbytes / ms / 1e6, "hbm_frac": nbytes / ms / 1e6 / hbm_peak}
+    out["hbm_peak_gbs"] = hbm_peak
+    out["hbm_peak_source"] = hbm_src
+    out["imad_peak_tops"] = imad_peak / 1e12
+    del x
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_sweep(args):
     """NTT / INTT / coset NTT at 2^16..2^24 and G1 (2^16..2^24) / G2 (2^16..2^20) MSMs on
     uniform random Fr data, points = generator x seeded random scalars.  One JSON line."""
@@ -245,7 +406,8 @@ def run_sweep(args):
 
     torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
     hbm, hbm_src = _peaks()
-    imad_peak = SMS * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6
+    imad = measure_imad_peak(nv, _env_int("LOCAL_RANK", 0))
+    imad_peak = imad["imad_per_s"]
     g = torch.Generator(device="cuda").manual_seed(0x5A4B5643_00000003)
 
     def rand_fr(n):
@@ -268,14 +430,12 @@ def run_sweep(args):
     for logn in args.sweep_ntt:
         n = 1 << logn
         x = rand_fr(n)
-        passes = (logn + 9) // 10 + 1                       # DIF passes + the bit-reversal pass
         for kind, name in ((0, "ntt"), (1, "intt"), (2, "coset_ntt")):
             ms = time_it(lambda: nv.zkvc_ntt(x, kind), 5)
-            bytes_moved = passes * 2 * 32 * n
-            butterflies = (n // 2) * logn
+            work, bytes_moved = ntt_work(logn)
             out["ntt"].append({"log_n": logn, "kind": name, "ms": ms,
                                "hbm_gbs": bytes_moved / ms / 1e6, "hbm_frac": bytes_moved / ms / 1e6 / hbm,
-                               "imad_frac": butterflies * MONT_IMAD / (ms / 1e3) / imad_peak})
+                               "imad_frac": work / (ms / 1e3) / imad_peak})
         del x
         torch.cuda.empty_cache()
     for group, sizes in ((1, args.sweep_g1), (2, args.sweep_g2)):
@@ -294,12 +454,19 @@ def run_sweep(args):
             torch.cuda.empty_cache()
     line = {"metric": "kernel sweep: NTT/INTT/coset-NTT and G1/G2 MSM over BN254", "unit": "ms",
             "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src, "imad_peak_tops": imad_peak / 1e12,
+            "imad_peak_source": "measured (zkvc_imad_rate)", "imad_microbenchmark": imad,
+            "ntt_bytes_rule": "64 B per point per HBM pass; 1 pass below 2^20 points, 2 from 2^20",
             "data": "synthetic (uniform Fr; points = generator x random scalars)", "sweep": out}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------ GPU arm
+def p99_of(xs):
+    srt = sorted(xs)
+    return srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+
+
 def run_gpu(args):
     import torch
 
@@ -393,6 +560,20 @@ def run_gpu(args):
     torch.cuda.synchronize()
     prof = nv.zkvc_profile_read()
     nv.zkvc_profile_enable(False)
+    del flush
+    torch.cuda.empty_cache()
+
+    # ---- the integer-pipe peak of this GPU (microbenchmark, outside the timed region)
+    imad = measure_imad_peak(nv, local)
+    peak = imad["imad_per_s"] / 1e12
+    hbm, hbm_src = _peaks()
+
+    # ---- the batched and served forms beside the plain one-proof path (1 GPU, rank 0)
+    batched = served = None
+    if world == 1 and not args.no_batched:
+        batched = batched_section(nv, args, local)
+    if world == 1 and not args.no_served:
+        served = served_section(nv, args, local)
 
     if rank != 0:
         if dist is not None:
@@ -408,31 +589,23 @@ def run_gpu(args):
     # run in G1 (its time share also leads the launch list)
     dom, work, ms, calls = ("k_accum0<G1> (H query)", w1, g1["ms"], g1["calls"]) if w1 >= w2 else \
         ("k_accum0<G2>", w2, g2["ms"], g2["calls"])
-    peak = SMS * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     achieved = (work / calls) / (ms / calls / 1e3) / 1e12 if ms > 0 else 0.0
-    # DRAM bytes (read + write) of one H-query accumulation launch, from one ncu capture per
-    # chunk setting of this workload (dram__bytes_read.sum + dram__bytes_write.sum)
-    h_traffic = {0: 75253248, 16: 75253248, 32: 74893568, 64: 74598400}
-    traffic = h_traffic.get(tuning[2]) if dom.startswith("k_accum0<G1>") else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-                "peak_source": "152 SMs x 64 IMAD/clk x 2070 MHz (nominal unit count and max clock)",
+                "frac": achieved / peak, "traffic": H_ACCUM_TRAFFIC.get(tuning[2]) if dom.startswith("k_accum0<G1>")
+                else None, "traffic_unit": "bytes per launch",
+                "peak_source": "measured on this GPU by zkvc_imad_rate (of measured), the faster of two forms",
+                "peak_nominal": nominal_imad_peak(imad["sms"], 2070.0) / 1e12,
                 "algorithmic_imad_per_launch": work / max(calls, 1),
                 "launch_ms": ms / max(calls, 1)}
     stages = {k: round(v["ms"] / max(v["calls"], 1), 4) for k, v in prof.items()}
     spans = {k: [round(v["start_ms"], 4), round(v["end_ms"], 4)] for k, v in prof.items() if v["calls"]}
+    nttr = ntt_roofline(nv, prof, 16, imad["imad_per_s"], hbm, hbm_src)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        secs = [oracle_sample(inputs.SEED_CFG[2])[0] for _ in range(2)]
-        per = statistics.median(secs)
-        cpu = {"value": 1.0 / per, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "matmul on 2 of 49 rows, full CRPC evaluations, one 2^14-point textbook NTT scaled "
-                         "to seven 2^16 transforms, 64 naive scalar multiplications per scalar type scaled by "
-                         "each query's term count; extrapolated to one [49,320]x[320,512] proof"}
+        cpu = cpu_baseline(args)
 
     srt = sorted(step_ms)
-    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
@@ -447,8 +620,9 @@ def run_gpu(args):
                    "quad_lanes_h_small": tuning[8:10],
                    "chunk_source": "imposed (--key-tuning)" if args.key_tuning else
                    "default rule" if args.no_autotune else "zkvc_pk_autotune at setup"},
-        "latency_ms": {"p50": statistics.median(step_ms), "p99": p99, "min": srt[0], "max": srt[-1]},
-        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches,
+        "latency_ms": {"p50": statistics.median(step_ms), "p99": p99_of(step_ms), "min": srt[0], "max": srt[-1]},
+        "e2e": e2e, "roofline": roofline, "ntt_roofline": nttr, "imad_peak": imad,
+        "batched": batched, "served": served, "cpu_baseline": cpu, "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps, "clocks": clk, "stage_ms": stages,
         "stage_span_ms": spans,
         "wall_s_timed_region": wall,
@@ -459,10 +633,128 @@ def run_gpu(args):
     return 0
 
 
+# DRAM bytes (read + write) of one H-query accumulation launch of the [49,320]x[320,512]
+# proof, from one ncu capture per chunk setting (dram__bytes_read.sum +
+# dram__bytes_write.sum); keyed by the H run's chunk tuning
+H_ACCUM_TRAFFIC = {0: 75253248, 16: 75253248, 32: 74893568, 64: 74598400}
+
+
 # ------------------------------------------------------------------ batched workload
 def shape_seed(base, shape):
     a, n, b = shape
     return base ^ (a << 40) ^ (n << 20) ^ b
+
+
+def batched_setup(nv, inputs, shapes):
+    """One proving key per distinct shape of the mix (setup seeds by shape)."""
+    keys, vkeys = {}, {}
+    for s in dict.fromkeys(shapes):
+        keys[s], vkeys[s] = nv.zkvc_setup(*s, inputs.to_bytes32(inputs.setup_values(shape_seed(inputs.SEED_CFG[4], s))))
+    return keys, vkeys
+
+
+def batched_core(nv, shapes, keys, steps, warmup, local, tuning=None, eager=False, autotune=True):
+    """Times `steps` calls of one batched prove over `shapes` (one instance each) after
+    autotuning and capture: device time per call with CUDA events, L2 flushed between
+    calls.  Returns a dict of measurements plus the objects the callers reuse."""
+    import torch
+
+    from paper_2504_12217_gb300 import inputs
+    sets = []
+    for v in range(2):
+        insts = [inputs.instance(inputs.SEED_CFG[4] + 1000 * (v + 1) + i, s) for i, s in enumerate(shapes)]
+        sets.append(([torch.from_numpy(t["X"]).cuda() for t in insts], [torch.from_numpy(t["W"]).cuda() for t in insts],
+                     [inputs.to_bytes32(t["rs"]) for t in insts], insts))
+    Ys = [torch.empty((s[0], s[2]), dtype=torch.int32, device="cuda") for s in shapes]
+    t0 = time.perf_counter()
+    flags = nv.ZKVC_BATCH_EAGER if eager else 0
+    if autotune and not tuning:
+        flags |= nv.ZKVC_BATCH_AUTOTUNE
+    batch = nv.Batch([keys[s] for s in shapes], flags=flags)
+    if tuning:
+        batch.set_tuning(tuning)
+    nv.zkvc_set_wait_timeout_ms(120000)
+    batch.prove(sets[0][0], sets[0][1], sets[0][2], Ys)  # autotune + capture
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    for i in range(warmup):
+        x = sets[i % 2]
+        batch.prove(x[0], x[1], x[2], Ys)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = nv.zkvc_kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        x = sets[i % 2]
+        flush.zero_()
+        evs[i][0].record()
+        batch.prove(x[0], x[1], x[2], Ys)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = nv.zkvc_kernel_launches() - launches0
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    return {"step_ms": step_ms, "tune_s": tune_s, "clocks": clk, "launches": launches, "batch": batch, "sets": sets,
+            "Ys": Ys, "terms": batch.terms(), "info": batch.info()}
+
+
+def plain_on_mix(nv, pks, instances, samples, rng):
+    """The plain one-proof path on a request mix: zkvc_prove one instance at a time
+    (inputs on the device, one warm call before each timed one), CUDA events."""
+    import torch
+    wss = {}
+    out = []
+    for _ in range(samples):
+        k, Xd, Wd, rs = instances[rng.randrange(len(instances))]
+        if k not in wss:
+            wss[k] = torch.empty(nv.zkvc_prove_workspace_bytes(pks[k]), dtype=torch.uint8, device="cuda")
+        nv.zkvc_prove(pks[k], Xd, Wd, rs, workspace=wss[k])  # warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        nv.zkvc_prove(pks[k], Xd, Wd, rs, workspace=wss[k])
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    del wss
+    torch.cuda.empty_cache()
+    return {"proofs_per_s": 1e3 / statistics.mean(out), "p50_ms": statistics.median(out), "p99_ms": p99_of(out),
+            "samples": len(out)}
+
+
+def batched_section(nv, args, local):
+    """The 64-proof batched workload inside the default bench line: proofs/s per graph
+    replay, batch latency, and the plain one-proof path on the same 64 instances."""
+    import random
+
+    import torch
+
+    from paper_2504_12217_gb300 import inputs
+    shapes = inputs.batch_shapes()
+    t0 = time.perf_counter()
+    keys, _ = batched_setup(nv, inputs, shapes)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    steps = max(3, min(args.steps, 10))
+    r = batched_core(nv, shapes, keys, steps, 2, local)
+    step_ms = r["step_ms"]
+    per = statistics.mean(step_ms)
+    x = r["sets"][0]
+    inst = [(i, x[0][i], x[1][i], x[2][i]) for i in range(len(shapes))]
+    plain = plain_on_mix(nv, [keys[s] for s in shapes], inst, 64, random.Random(4))
+    work = (r["terms"]["small"] + r["terms"]["main"]) * G1_MADD_PRODUCTS * MONT_IMAD + \
+        r["terms"]["g2"] * G2_MADD_PRODUCTS * MONT_IMAD
+    out = {"workload": "crpc_groth16_bn254_batched_64mix", "instances": len(shapes), "distinct_shapes": len(keys),
+           "proofs_per_s": len(shapes) / (per / 1e3), "ms_per_batch_p50": statistics.median(step_ms),
+           "ms_per_batch_p99": p99_of(step_ms), "steps": steps, "graph_kernels": r["info"]["graph_launches"],
+           "gpu_launches": r["launches"], "tuning": r["batch"].get_tuning(), "tuning_source": "autotuned on the first call",
+           "setup_s": setup_s, "autotune_and_capture_s": r["tune_s"], "whole_batch_imad_per_s": work / (per / 1e3),
+           "plain_one_proof_path_same_64": plain, "clocks": r["clocks"],
+           "l2": "flushed by a 256 MiB write between steps"}
+    del r, keys
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(args):
@@ -485,55 +777,19 @@ def run_batched(args):
     if args.batch_count:  # a smaller case: the K smallest instances of the seeded mix
         shapes = sorted(shapes, key=lambda s: s[0] * s[1] + s[0] * s[2] + s[1] * s[2])[: args.batch_count]
     t0 = time.perf_counter()
-    keys, vkeys = {}, {}
-    for s in dict.fromkeys(shapes):
-        keys[s], vkeys[s] = nv.zkvc_setup(*s, inputs.to_bytes32(inputs.setup_values(shape_seed(inputs.SEED_CFG[4], s))))
+    keys, vkeys = batched_setup(nv, inputs, shapes)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    sets = []
-    for v in range(2):
-        insts = [inputs.instance(inputs.SEED_CFG[4] + 1000 * (v + 1) + i, s) for i, s in enumerate(shapes)]
-        sets.append(([torch.from_numpy(t["X"]).cuda() for t in insts], [torch.from_numpy(t["W"]).cuda() for t in insts],
-                     [inputs.to_bytes32(t["rs"]) for t in insts], insts))
-    Ys = [torch.empty((s[0], s[2]), dtype=torch.int32, device="cuda") for s in shapes]
-    t0 = time.perf_counter()
-    flags = nv.ZKVC_BATCH_EAGER if args.eager else 0
-    if not args.tuning:
-        flags |= nv.ZKVC_BATCH_AUTOTUNE
-    batch = nv.Batch([keys[s] for s in shapes], flags=flags)
-    if args.tuning:
-        batch.set_tuning(args.tuning)
-    nv.zkvc_set_wait_timeout_ms(120000)
-    batch.prove(sets[0][0], sets[0][1], sets[0][2], Ys)  # autotune + capture
-    torch.cuda.synchronize()
-    tune_s = time.perf_counter() - t0
-    for i in range(args.warmup):
-        x = sets[i % 2]
-        batch.prove(x[0], x[1], x[2], Ys)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    clocks = ClockSampler(local)
-    clocks.start()
-    launches0 = nv.zkvc_kernel_launches()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist is not None:
         dist.barrier()
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        x = sets[i % 2]
-        flush.zero_()
-        evs[i][0].record()
-        batch.prove(x[0], x[1], x[2], Ys)
-        evs[i][1].record()
-    torch.cuda.synchronize()
+    r = batched_core(nv, shapes, keys, args.steps, args.warmup, local, tuning=args.tuning, eager=args.eager)
     if dist is not None:
         dist.barrier()
-    clk = clocks.stop()
-    launches = nv.zkvc_kernel_launches() - launches0
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    batch, sets, Ys, step_ms = r["batch"], r["sets"], r["Ys"], r["step_ms"]
     total_s = reduce_max(sum(step_ms) / 1e3, dist, "cuda")
     count = len(shapes)
     value = replica_value(count * args.steps, world, total_s)
-    terms = batch.terms()
+    terms = r["terms"]
 
     # end to end: pinned host matrices copied in, Y and proofs read back, every step
     Xh = [[x.cpu().pin_memory() for x in st[0]] for st in sets]
@@ -574,12 +830,12 @@ def run_batched(args):
         if dist is not None:
             dist.destroy_process_group()
         return 0
-    peak = SMS * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    imad = measure_imad_peak(nv, local)
+    peak = imad["imad_per_s"] / 1e12
     work = (terms["small"] + terms["main"]) * G1_MADD_PRODUCTS * MONT_IMAD + terms["g2"] * G2_MADD_PRODUCTS * MONT_IMAD
     per_step = total_s / args.steps
     srt = sorted(step_ms)
-    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
-    info = batch.info()
+    info = r["info"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -589,15 +845,17 @@ def run_batched(args):
                    "l2": "flushed by a 256 MiB write between steps", "parallelism": f"replicas x{world}",
                    "graph": not args.eager, "tuning": batch.get_tuning(),
                    "tuning_source": "imposed" if args.tuning else "autotuned on the first call"},
-        "latency_ms": {"p50_batch": statistics.median(step_ms), "p99_batch": p99, "min": srt[0], "max": srt[-1]},
+        "latency_ms": {"p50_batch": statistics.median(step_ms), "p99_batch": p99_of(step_ms), "min": srt[0],
+                       "max": srt[-1]},
         "e2e": {"value": replica_value(count * e2e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "batch_roofline": {"bound": "alu", "scope": "whole batch (all kernels, overlapped)",
                            "achieved": work / per_step / 1e12, "peak": peak, "unit": "TIMAD/s",
-                           "frac": work / per_step / 1e12 / peak, "bucket_terms": terms},
-        "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+                           "frac": work / per_step / 1e12 / peak, "bucket_terms": terms,
+                           "peak_source": "measured on this GPU by zkvc_imad_rate (of measured)"},
+        "gpu_launches": r["launches"], "gpu_launches_per_step": r["launches"] / args.steps,
         "graph_kernels": info["graph_launches"], "device_bytes": info["device_bytes"],
-        "clocks": clk, "setup_s": setup_s, "autotune_and_capture_s": tune_s,
+        "clocks": r["clocks"], "setup_s": setup_s, "autotune_and_capture_s": r["tune_s"],
         "spot_check_vs_one_proof_prover": proofs[0] == p0,
         "verify": {"gpu_batch_proofs_per_s": count / gpu_verify_s, "gpu_batch_s": gpu_verify_s,
                    "all_valid": all(vok), "host_ms_per_proof": host_verify_s * 1e3, "host_sample_valid": all(host_ok),
@@ -610,55 +868,23 @@ def run_batched(args):
 
 
 # ------------------------------------------------------------------ served workload
-def run_served(args):
-    """Poisson arrivals (seeded) of proof requests over the 32 [tokens, dim] x [dim, dim |
-    4 dim] shapes, all keys resident; the library's proof server admits requests by
-    memory footprint and overlaps them.  Per offered rate: achieved proofs/s and p50/p99
-    latency from submission to result.  The plain path (one proof at a time through
-    zkvc_prove, inputs already on the device) on the same request mix is reported beside
-    it.  One JSON line."""
-    import random
+def served_core(nv, pks, pool, rates, seconds_per_rate, max_requests, slots, budget, policy, local, rng):
+    """Poisson arrivals (seeded) of requests drawn from `pool` through the library's proof
+    server, one offered rate after the other.  Per rate: achieved proofs/s (requests over
+    the time from the first arrival to the last result) and p50/p99 latency from submit
+    to result (host wall clock, including the copies of X, W in and Y, the proof out)."""
     import threading
-
-    import numpy as np
-    import torch
-
-    from paper_2504_12217_gb300 import inputs
-    from paper_2504_12217_gb300 import native as nv
-
-    local = _env_int("LOCAL_RANK", 0)
-    rank = _env_int("RANK", 0)
-    world = _env_int("WORLD_SIZE", 1)
-    torch.cuda.set_device(local)
-    shapes = inputs.all_batch_shapes()
-    t0 = time.perf_counter()
-    pks = [nv.zkvc_setup(*s, inputs.to_bytes32(inputs.setup_values(shape_seed(inputs.SEED_CFG[5], s))))[0]
-           for s in shapes]
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
-    pool = []  # two pre-drawn instances per shape
-    for k, s in enumerate(shapes):
-        for v in range(2):
-            seed = inputs.SEED_CFG[5] + 100 * k + v + 1000 * rank
-            X, W = inputs.matrices(seed, *s)
-            pool.append((k, X, W, inputs.to_bytes32(inputs.prover_values(seed))))
-    rng = random.Random(inputs.SEED_CFG[5] + rank)
-    rates = args.rates
-    budget = args.server_budget_gib << 30
-    policy = {"adaptive": nv.ZKVC_SERVER_ADAPTIVE, "fold": nv.ZKVC_SERVER_FOLD, "chain": nv.ZKVC_SERVER_CHAIN}[
-        args.server_policy]
-    srv = nv.Server(pks, slots=args.server_slots, mem_budget=budget, policy=policy)
+    srv = nv.Server(pks, slots=slots, mem_budget=budget, policy=policy)
     nv.zkvc_set_wait_timeout_ms(600000)
-    # warm up every shape once (domain tables, side streams, caches)
-    for k in range(len(shapes)):
-        e = pool[2 * k]
+    for k in range(len(pks)):  # warm every key once (domain tables, side streams, caches)
+        e = next(p for p in pool if p[0] == k)
         srv.wait(srv.submit(*e), k)
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = nv.zkvc_kernel_launches()
     per_rate = []
     for rate in rates:
-        n_req = max(8, min(args.max_requests, int(rate * args.seconds_per_rate)))
+        n_req = max(8, min(max_requests, int(rate * seconds_per_rate)))
         arrivals, t = [], 0.0
         for _ in range(n_req):
             t += rng.expovariate(rate)
@@ -690,46 +916,109 @@ def run_served(args):
         ok = sum(1 for r in results if r[0] == nv.ZKVC_OK)
         per_rate.append({"offered_rps": rate, "requests": n_req, "ok": ok,
                          "achieved_proofs_per_s": n_req / (end - start),
-                         "p50_ms": statistics.median(lat), "p99_ms": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))],
-                         "max_ms": lat[-1], "queue_p50_ms": statistics.median(queue)})
+                         "p50_ms": statistics.median(lat), "p99_ms": p99_of(lat), "max_ms": lat[-1],
+                         "queue_p50_ms": statistics.median(queue)})
     clk = clocks.stop()
     launches = nv.zkvc_kernel_launches() - launches0
     st = srv.stats()
     srv.close()
-    # the plain one-proof path on the same mix: one request at a time, device-resident inputs
+    return {"per_rate": per_rate, "clocks": clk, "launches": launches, "stats": st}
+
+
+def served_pool(inputs, shapes, base_seed, rank=0):
+    """Two pre-drawn instances per shape: (key index, X, W, rs)."""
+    pool = []
+    for k, s in enumerate(shapes):
+        for v in range(2):
+            seed = base_seed + 100 * k + v + 1000 * rank
+            X, W = inputs.matrices(seed, *s)
+            pool.append((k, X, W, inputs.to_bytes32(inputs.prover_values(seed))))
+    return pool
+
+
+def served_section(nv, args, local):
+    """The served workload inside the default bench line: the 32 shapes' keys resident,
+    Poisson arrivals at three offered rates (the highest above saturation), the plain
+    one-proof path on the same mix beside it."""
+    import random
+
+    import torch
+
+    from paper_2504_12217_gb300 import inputs
+    shapes = inputs.all_batch_shapes()
+    t0 = time.perf_counter()
+    pks = [nv.zkvc_setup(*s, inputs.to_bytes32(inputs.setup_values(shape_seed(inputs.SEED_CFG[5], s))))[0]
+           for s in shapes]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    pool = served_pool(inputs, shapes, inputs.SEED_CFG[5])
+    rng = random.Random(inputs.SEED_CFG[5])
+    rates = args.served_rates
+    r = served_core(nv, pks, pool, rates, args.served_seconds, args.served_max_requests, args.server_slots,
+                    args.server_budget_gib << 30, nv.ZKVC_SERVER_CHAIN, local, rng)
     dev = [(k, torch.from_numpy(X).cuda(), torch.from_numpy(W).cuda(), rs) for k, X, W, rs in pool]
-    wss = {}
-    plain_ms = []
-    for i in range(min(64, len(dev))):
-        k, Xd, Wd, rs = dev[rng.randrange(len(dev))]
-        if k not in wss:
-            wss[k] = torch.empty(nv.zkvc_prove_workspace_bytes(pks[k]), dtype=torch.uint8, device="cuda")
-        nv.zkvc_prove(pks[k], Xd, Wd, rs, workspace=wss[k])  # warm
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        nv.zkvc_prove(pks[k], Xd, Wd, rs, workspace=wss[k])
-        e1.record()
-        torch.cuda.synchronize()
-        plain_ms.append(e0.elapsed_time(e1))
+    plain = plain_on_mix(nv, pks, dev, 64, rng)
+    del dev, pks
+    torch.cuda.empty_cache()
+    best = max(r["per_rate"], key=lambda x: x["achieved_proofs_per_s"])
+    return {"workload": "crpc_groth16_bn254_served_poisson", "shapes": len(shapes), "policy": "chain",
+            "slots": args.server_slots, "mem_budget_bytes": args.server_budget_gib << 30,
+            "rates": r["per_rate"], "ceiling_proofs_per_s": best["achieved_proofs_per_s"],
+            "plain_one_proof_path_same_mix": plain, "gpu_launches": r["launches"], "server_stats": r["stats"],
+            "setup_s": setup_s, "clocks": r["clocks"],
+            "latency": "host wall clock from submit to result (includes H2D of X, W and D2H of Y, proof)"}
+
+
+def run_served(args):
+    """Poisson arrivals (seeded) of proof requests over the 32 [tokens, dim] x [dim, dim |
+    4 dim] shapes, all keys resident; the library's proof server admits requests by
+    memory footprint and overlaps them.  Per offered rate: achieved proofs/s and p50/p99
+    latency from submission to result.  The plain path (one proof at a time through
+    zkvc_prove, inputs already on the device) on the same request mix is reported beside
+    it.  One JSON line."""
+    import random
+
+    import torch
+
+    from paper_2504_12217_gb300 import inputs
+    from paper_2504_12217_gb300 import native as nv
+
+    local = _env_int("LOCAL_RANK", 0)
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    torch.cuda.set_device(local)
+    shapes = inputs.all_batch_shapes()
+    t0 = time.perf_counter()
+    pks = [nv.zkvc_setup(*s, inputs.to_bytes32(inputs.setup_values(shape_seed(inputs.SEED_CFG[5], s))))[0]
+           for s in shapes]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    pool = served_pool(inputs, shapes, inputs.SEED_CFG[5], rank)
+    rng = random.Random(inputs.SEED_CFG[5] + rank)
+    policy = {"adaptive": nv.ZKVC_SERVER_ADAPTIVE, "fold": nv.ZKVC_SERVER_FOLD, "chain": nv.ZKVC_SERVER_CHAIN}[
+        args.server_policy]
+    budget = args.server_budget_gib << 30
+    r = served_core(nv, pks, pool, args.rates, args.seconds_per_rate, args.max_requests, args.server_slots, budget,
+                    policy, local, rng)
+    dev = [(k, torch.from_numpy(X).cuda(), torch.from_numpy(W).cuda(), rs) for k, X, W, rs in pool]
+    plain = plain_on_mix(nv, pks, dev, 64, rng)
     if rank != 0:
         return 0
-    best = max(per_rate, key=lambda r: r["achieved_proofs_per_s"])
-    ps = sorted(plain_ms)
+    per_rate = r["per_rate"]
+    best = max(per_rate, key=lambda x: x["achieved_proofs_per_s"])
     line = {
         "metric": METRIC, "value": best["achieved_proofs_per_s"], "unit": UNIT, "n_gpus": world,
-        "steps": sum(r["requests"] for r in per_rate), "warmup": len(shapes), "ms_per_step": None,
+        "steps": sum(x["requests"] for x in per_rate), "warmup": len(shapes), "ms_per_step": None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 limbs (exact Fr/Fp arithmetic)", "data": "synthetic",
         "config": {"workload": "crpc_groth16_bn254_served_poisson", "shapes": len(shapes),
-                   "rates_rps": rates, "slots": args.server_slots, "mem_budget_bytes": budget,
+                   "rates_rps": args.rates, "slots": args.server_slots, "mem_budget_bytes": budget,
                    "policy": {"adaptive": "adaptive (fold when idle, chain when shared)", "fold": "fold",
                               "chain": "chain"}[args.server_policy],
                    "latency": "host wall clock from submit to result (includes H2D of X, W and D2H of Y, proof)"},
         "served": per_rate,
-        "plain_one_proof_path": {"proofs_per_s": 1e3 / statistics.mean(plain_ms), "p50_ms": statistics.median(ps),
-                                 "p99_ms": ps[min(len(ps) - 1, int(round(0.99 * (len(ps) - 1))))],
-                                 "samples": len(ps)},
-        "server_stats": st, "gpu_launches": launches, "clocks": clk, "setup_s": setup_s,
+        "plain_one_proof_path": plain,
+        "server_stats": r["stats"], "gpu_launches": r["launches"], "clocks": r["clocks"], "setup_s": setup_s,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -838,6 +1127,12 @@ def main():
     ap.add_argument("--server-policy", choices=["adaptive", "fold", "chain"], default="chain",
                     help="served: prover mode per request")
     ap.add_argument("--batch-count", type=int, default=0, help="batched: only the K smallest instances")
+    ap.add_argument("--no-batched", action="store_true", help="plain: leave the batched section out of the line")
+    ap.add_argument("--no-served", action="store_true", help="plain: leave the served section out of the line")
+    ap.add_argument("--served-rates", type=float, nargs="*", default=[50, 200, 1000],
+                    help="plain: offered rates of the served section (the last above saturation)")
+    ap.add_argument("--served-seconds", type=float, default=3.0, help="plain: seconds of arrivals per served rate")
+    ap.add_argument("--served-max-requests", type=int, default=600, help="plain: request cap per served rate")
     ap.add_argument("--key-tuning", type=int, nargs=10, default=None,
                     help="plain: impose the key's launch shape (zkvc_pk_set_tuning), skip the autotuner")
     ap.add_argument("--tuning", type=int, nargs=7, default=None, help="batched: impose a tuning, skip the autotuner")

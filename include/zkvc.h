@@ -72,6 +72,18 @@ void zkvc_profile_enable(int on);
 int zkvc_profile_read(int stage, const char** name, double* ms, uint64_t* calls, uint64_t* units);
 int zkvc_profile_span(int stage, double* start_ms, double* end_ms);
 
+/* Integer-pipe throughput microbenchmark: the measured peak of the 32-bit multiply-add
+ * (IMAD) that every Montgomery product of the prover is made of (BN254 field arithmetic
+ * of the groth16 backend, Sec. IV; the roofline denominator of the MSM and NTT kernels).
+ * form 0: sixteen independent mad.lo.u32 chains per thread; form 1: the CIOS row of the
+ * field code (a carry chain of eight mad.lo and eight mad.hi).  A full-occupancy grid
+ * over every SM runs `iters` iterations of 16 IMADs per thread, once untimed (iters / 8)
+ * and once timed with CUDA events on `stream`; the call synchronises.  Outputs (any may be
+ * null): IMADs per second, the timed launch in ms and the SM count used.  ZKVC_EINVAL for a
+ * form other than 0 or 1 or iters outside [1, 2^24].
+ */
+int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int* sms, void* stream);
+
 /* ------------------------------------------------------------------ field kernels
  * Elementwise products of n canonical elements: d_out[i] = d_a[i] * d_b[i] mod the
  * field's modulus (Fr: scalar field r; Fp: base field p; Fp2: pairs c0 || c1, 64 bytes
@@ -86,10 +98,11 @@ int zkvc_fp2_mul(const uint8_t* d_a, const uint8_t* d_b, uint8_t* d_out, size_t 
 /* Elementwise inverses d_out[i] = d_a[i]^-1 mod r (fr) or mod p (fp), 0 -> 0, for n
  * canonical 32-byte little-endian elements in device memory; d_out may alias d_a.  The
  * inversion of the prover's affine conversions (the Groth16 proof encodes A, B and C in
- * affine coordinates, Sec. II): a binary GCD that takes 31 steps at a time on 64-bit
- * approximations of the operands.  Returns ZKVC_EINVAL on a null pointer with n > 0.
+ * affine coordinates, Sec. II): a binary GCD that takes 30 steps at a time on 62-bit
+ * stand-ins of the operands (17 rounds).  Returns ZKVC_EINVAL on a null pointer with n > 0.
  */
 int zkvc_fr_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream);
+int zkvc_fp_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream);
 
 /* The host-side GLV split of the chain-mode scalar multiplications (G1 of BN254 has the
  * endomorphism phi(x, y) = (beta x, y) = lambda (x, y)): k (32 bytes little-endian,
@@ -99,7 +112,6 @@ int zkvc_fr_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream);
  * its sign (34 bytes).  Host only; ZKVC_EINVAL on a null pointer.
  */
 int zkvc_glv_split(const uint8_t k[32], uint8_t out[34]);
-int zkvc_fp_inv(const uint8_t* d_a, uint8_t* d_out, size_t n, void* stream);
 
 /* ------------------------------------------------------------------ witness matmul
  * Y = X W for int8 X (a x n, row-major) and W (n x b, row-major) into int32 Y (a x b,
@@ -161,17 +173,19 @@ int zkvc_g2_generator_mul(const uint8_t* d_scalars, size_t n, uint8_t* d_points,
                           void* stream);
 
 /* Allocation-free variant of zkvc_msm_g1, for callers that cannot allocate device memory
- * (code inside a CUDA graph being captured, runtimes without an allocator, processes
- * whose device memory another framework has reserved).  The paper has no counterpart;
- * it is a deployment convenience of this library.
+ * (runtimes without a device allocator, or processes whose device memory another
+ * framework reserved up front for its own pool).  The paper has no counterpart; it is a
+ * deployment convenience of this library.
  *   - Same arguments and result as zkvc_msm_g1, minus the workspace: the scratch is one
  *     8 MiB array in device memory, part of the library image, held on every GPU that
  *     loads the library until the process exits.
  *   - n <= ZKVC_MSM_NOALLOC_MAX_POINTS; larger n returns ZKVC_EINVAL.
- *   - Calls no allocator (CUDA's or any framework's); the result is copied to `out` and
- *     `stream` is synchronised.
+ *   - Calls no allocator (CUDA's or any framework's).  Like zkvc_msm_g1 it uploads its
+ *     bucket tables from host memory, synchronises `stream` and copies the result to
+ *     `out` (host memory) before it returns.
  *   - The first call on a device (with that device current) looks up the array's device
- *     address and caches it; make that first call before any stream capture.
+ *     address and caches it per device and CUDA context; make that first call before any
+ *     stream capture.
  *   - All calls share the array, which keeps the previous call's contents (each call
  *     initialises what it reads).  Calls whose GPU work overlaps race on it: issue them
  *     one at a time.

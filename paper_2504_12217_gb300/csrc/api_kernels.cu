@@ -33,6 +33,27 @@ void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_
 void uncount_launches(unsigned long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+static std::atomic<int> g_sm_count[64];
+
+int device_sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev < 64) {
+    int c = g_sm_count[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int c = 0;
+  if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev < 64) g_sm_count[dev].store(c, std::memory_order_relaxed);
+  return c;
+}
+
 static std::atomic<int> g_wait_ms{60000};
 
 int wait_stream(cudaStream_t st, const char* what) {
@@ -224,6 +245,55 @@ int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d
 template int msm_api<Fp>(const uint8_t*, const uint8_t*, size_t, void*, size_t, uint8_t*, cudaStream_t);
 template size_t msm_api_ws<Fp>(size_t);
 
+// ------------------------------------------------------------------ integer-pipe rate
+// Throughput microbenchmark of the 32-bit multiply-add that Montgomery products are made
+// of.  Form 0: sixteen independent mad.lo.u32 chains per thread.  Form 1: the product's
+// own row, a carry chain of eight mad.lo.cc / madc.lo.cc and eight mad.hi.cc /
+// madc.hi.cc (sixteen IMADs), as in the CIOS rows of the field code.  Every thread
+// counts 16 IMADs per iteration; a full-occupancy grid of 256-thread blocks covers all
+// SMs.  The result xor goes to `sink` so that nothing is dead code.
+template <int FORM>
+__global__ void __launch_bounds__(256) k_imad_rate(uint32_t iters, uint32_t seed, uint32_t* sink) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t t[16];
+#pragma unroll
+  for (int j = 0; j < 16; j++) t[j] = g * 2654435761u + seed * (j + 1);
+  const uint32_t x = seed | 1u, y = g ^ 0x9e3779b9u;
+  for (uint32_t it = 0; it < iters; it++) {
+    if constexpr (FORM == 0) {
+#pragma unroll
+      for (int j = 0; j < 16; j++) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(t[j]) : "r"(x), "r"(y));
+    } else {
+      const uint32_t b = t[15] | 1u;
+      asm volatile(
+          "mad.lo.cc.u32  %0, %9,  %17, %0;\n\t"
+          "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"
+          "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"
+          "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"
+          "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"
+          "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"
+          "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"
+          "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"
+          "addc.u32       %8, %8, 0;\n\t"
+          "mad.hi.cc.u32  %1, %9,  %17, %1;\n\t"
+          "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"
+          "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"
+          "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"
+          "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"
+          "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"
+          "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"
+          "madc.hi.u32    %8, %16, %17, %8;"
+          : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+            "+r"(t[15])
+          : "r"(t[8]), "r"(t[9]), "r"(t[10]), "r"(t[11]), "r"(t[12]), "r"(t[13]), "r"(t[14]), "r"(x), "r"(b));
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < 16; j++) acc ^= t[j];
+  if (acc == 0x12345678u) sink[0] = acc;
+}
+
 }  // namespace zkvc
 
 using namespace zkvc;
@@ -387,6 +457,44 @@ int zkvc_msm_g2(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, voi
                 uint8_t out[128], void* stream) {
   clear_error();
   return msm_api<Fp2>(d_points, d_scalars, n, d_ws, ws_bytes, out, (cudaStream_t)stream);
+}
+
+int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int* sms, void* stream) {
+  clear_error();
+  ZK_CHECK(form == 0 || form == 1, ZKVC_EINVAL, "imad_rate: form %d", form);
+  ZK_CHECK(iters >= 1 && iters <= (1u << 24), ZKVC_EINVAL, "imad_rate: %u iterations outside [1, 2^24]", iters);
+  static thread_local uint32_t* t_sink = nullptr;
+  static thread_local int t_dev = -1;
+  int dev = 0;
+  ZK_CUDA(cudaGetDevice(&dev));
+  if (!t_sink || t_dev != dev) {
+    ZK_CUDA(cudaMalloc(&t_sink, sizeof(uint32_t)));
+    t_dev = dev;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int per_sm = 0;
+  auto kern = form == 0 ? k_imad_rate<0> : k_imad_rate<1>;
+  ZK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+  const int nsm = device_sm_count();
+  const unsigned blocks = (unsigned)(nsm * (per_sm > 0 ? per_sm : 1));
+  cudaEvent_t e0, e1;
+  ZK_CUDA(cudaEventCreate(&e0));
+  ZK_CUDA(cudaEventCreate(&e1));
+  kern<<<blocks, 256, 0, st>>>(iters / 8 + 1, 7u, t_sink); ZK_COUNT_LAUNCH();  // warm
+  ZK_CUDA(cudaEventRecord(e0, st));
+  kern<<<blocks, 256, 0, st>>>(iters, 7u, t_sink); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaEventRecord(e1, st));
+  ZK_CUDA(cudaGetLastError());
+  ZK_TRY(wait_stream(st, "imad_rate"));
+  float t = 0;
+  ZK_CUDA(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const double ops = double(blocks) * 256.0 * double(iters) * 16.0;
+  if (ms) *ms = t;
+  if (imad_per_s) *imad_per_s = t > 0 ? ops / (t * 1e-3) : 0.0;
+  if (sms) *sms = nsm;
+  return ZKVC_OK;
 }
 
 }  // extern "C"

@@ -24,6 +24,10 @@ unsigned long long launches_so_far();
 // ZKVC_ECUDA when the stream reports an error.
 int wait_stream(cudaStream_t st, const char* what);
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, cached
+// per device); 1 when no device answers.  Launch shapes that aim at whole waves use it.
+int device_sm_count();
+
 // Y = X W (int8 x int8 -> int32, exact) on the tensor cores (matmul_tc.cu); sets bit 8
 // of *flags if a tensor-core wait timed out.
 int matmul_i8(const int8_t* X, const int8_t* W, int32_t* Y, int a, int n, int b, int* flags, cudaStream_t st);

@@ -34,7 +34,7 @@ int matmul_i8(const int8_t* X, const int8_t* W, int32_t* Y, int a, int n, int b,
   ZK_TRY(matmul_init());
   const int gm = (b + MM_M - 1) / MM_M, gn = (a + MM_N - 1) / MM_N;
   const int ktiles = (n + MM_BK - 1) / MM_BK;
-  int splits = (152 + gm * gn - 1) / (gm * gn);
+  int splits = (device_sm_count() + gm * gn - 1) / (gm * gn);
   splits = std::max(1, std::min(splits, ktiles));
   const int per = (ktiles + splits - 1) / splits;
   splits = (ktiles + per - 1) / per;

@@ -583,7 +583,8 @@ template <class F>
 struct SliceBT {
   static constexpr int value = sizeof(F) > 32 ? 64 : 128;
 };
-constexpr uint32_t SLICE_WAVE = 456;  // 152 SMs x 3 resident slice blocks
+// one wave of slice blocks: three resident per SM
+static uint32_t slice_wave() { return 3u * (uint32_t)device_sm_count(); }
 
 // block per slice: the sum of up to `slice` buckets of one bit
 template <class F>
@@ -751,7 +752,7 @@ static void layout(const MsmPlan& p, Arena& a, Layout& L, HostTables& h) {
   L.chunk_key = a.take<uint32_t>(L.qmax);
   L.arrive = a.take<uint32_t>(L.qmax);
   L.part = a.take<XYZZ<F>>(L.qmax);
-  tables(p, SliceBT<F>::value, SLICE_WAVE, h, L);
+  tables(p, SliceBT<F>::value, slice_wave(), h, L);
   L.S = a.take<XYZZ<F>>(L.nslices);
   L.D = a.take<XYZZ<F>>(L.dtotal);
   L.segs = a.take<MsmSeg>(p.segs.size());

@@ -434,7 +434,8 @@ int ntt_quotient_chain(Fr* ev, int m, size_t N, const NttDomain* d, cudaStream_t
     // three times the threads where the grid is too small to fill the GPU (latency-bound),
     // one array's worth where it is large (more blocks per SM)
     const uint64_t blocks = uint64_t(sh.grid.x) * sh.grid.y;
-    const uint32_t threads = blocks < 2 * 152 ? std::min<uint32_t>(3 * sh.threads, 768) : sh.threads;
+    const uint32_t threads =
+        blocks < 2 * uint64_t(device_sm_count()) ? std::min<uint32_t>(3 * sh.threads, 768) : sh.threads;
     k_ntt_quotient_turn<<<sh.grid, threads, size_t(3) * sh.E * 32, st>>>(ev, (uint32_t)m, N, d->tw_fwd, d->tw_inv, L,
                                                                          k, sh.logG, tabs);
     ZK_COUNT_LAUNCH();

@@ -38,6 +38,8 @@ SIGNATURES = {
     "zkvc_profile_span": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "zkvc_profile_read": (_c_int, [_c_int, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "zkvc_imad_rate": (_c_int, [_c_int, _c_u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(_c_int), _c_p]),
     "zkvc_fr_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_fp_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
     "zkvc_fp2_mul": (_c_int, [_c_p, _c_p, _c_p, _c_sz, _c_p]),
@@ -191,6 +193,14 @@ def zkvc_profile_read():
         out[name.value.decode()] = {"ms": ms.value, "calls": calls.value, "units": units.value,
                                     "start_ms": t0.value, "end_ms": t1.value}
         stage += 1
+
+
+def zkvc_imad_rate(form=1, iters=1 << 14):
+    """The integer-pipe microbenchmark: {"imad_per_s", "ms", "sms"} (form 0: independent
+    mad.lo chains; form 1: the field code's CIOS carry-chain row)."""
+    rate, ms, sms = ctypes.c_double(), ctypes.c_double(), _c_int()
+    check(lib().zkvc_imad_rate(form, iters, ctypes.byref(rate), ctypes.byref(ms), ctypes.byref(sms), _stream()))
+    return {"imad_per_s": rate.value, "ms": ms.value, "sms": sms.value}
 
 
 def zkvc_fr_mul(a, b, out=None):

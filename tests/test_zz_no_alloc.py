@@ -39,6 +39,21 @@ def test_noalloc_matches_workspace_msm_twice():
         assert got != bytes(64)
 
 
+def test_noalloc_matches_oracle_msm():
+    """16 points: the allocation-free MSM equals the oracle's naive sum of scalar
+    multiples (independent of the library's MSM code), twice in a row."""
+    import torch
+    assert torch.cuda.is_available()
+    nv = _util.native()
+    rng = random.Random(16)
+    for _ in range(2):
+        pts = [bn.g1_mul(bn.G1_GEN, rng.randrange(1, bn.R)) for _ in range(16)]
+        sc = [rng.randrange(bn.R) for _ in range(16)]
+        sc[3] = bn.R - 1
+        got = nv.zkvc_msm_g1_noalloc(_util.to_cuda(_util.g1_rows(pts)), _util.to_cuda(_util.ints_to_u8(sc)))
+        assert got == bn.g1_bytes(bn.g1_msm(pts, sc))
+
+
 def test_noalloc_rejects_oversize():
     import torch
     nv = _util.native()
