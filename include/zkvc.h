@@ -379,6 +379,21 @@ int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t
  *                          x_ik w_kj = S_ijk - S_ij(k-1), closing on y_ij (a b n rows)
  *   ZKVC_CIRCUIT_VANILLA   x_ik w_kj = p_ijk per product (a b n rows, Sec. III-A's count)
  *                          and (sum_k p_ijk) * 1 = y_ij per output
+ *   ZKVC_CIRCUIT_SOFTMAX   CRPC + PSQ, then the nonlinear gadgets of Sec. III-C on each
+ *                          row of Y (read as fixed point with ZKVC_GADGET_FRAC_BITS
+ *                          fractional bits): the row maximum x_max verified by
+ *                          x_max >= y_ij (32-bit decompositions of d = x_max - y_ij) and
+ *                          prod_j (x_max - y_ij) = 0 (a chain of products), then e^x at
+ *                          x = -d approximated by 0 below T = -2^ZKVC_GADGET_EXP_SQUARINGS
+ *                          and by (1 + x/2^n)^(2^n), n = ZKVC_GADGET_EXP_SQUARINGS,
+ *                          above: a 33-bit decomposition compares with T, the bits of d
+ *                          from n up give the division by 2^n, n squarings give the
+ *                          power.  71 rows per entry plus max(1, b - 1) per row of Y.
+ *   ZKVC_CIRCUIT_GELU      CRPC + PSQ, then GELU(x) ~ x^2/8 + x/4 + 1/2 (Sec. III-C) on
+ *                          every entry of Y, exactly at scale 2^(2F + 3): one row
+ *                          y * y = G - 2^(F+1) y - 2^(2F+2) per entry.
+ *                          Requires |y| < 2^31 (int8 products with n < 2^16 are).
+ *                          The gadgets' outputs are auxiliary (private) variables.
  * and public_io ZKVC_PUBLIC_XY (X and Y public) or ZKVC_PUBLIC_NONE (only the constant
  * one is public; the verifier then takes no X or Y).  toxic and the error behaviour are
  * those of zkvc_setup (z is unused by the circuits without CRPC but still checked).
@@ -393,6 +408,10 @@ int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t
 #define ZKVC_CIRCUIT_CRPC 1
 #define ZKVC_CIRCUIT_PSQ 2
 #define ZKVC_CIRCUIT_VANILLA 3
+#define ZKVC_CIRCUIT_SOFTMAX 4
+#define ZKVC_CIRCUIT_GELU 5
+#define ZKVC_GADGET_FRAC_BITS 12
+#define ZKVC_GADGET_EXP_SQUARINGS 3
 #define ZKVC_PUBLIC_XY 0
 #define ZKVC_PUBLIC_NONE 1
 int zkvc_setup_circuit(int a, int n, int b, int circuit, int public_io, const uint8_t toxic[192], void* stream,

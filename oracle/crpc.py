@@ -36,13 +36,18 @@ auxiliary and differ in the auxiliary variables and rows (see CIRCUITS below); w
 public_io = "none" only the constant one is public (l = 0), so X and Y join the private
 variables and only one input-consistency row remains.
 
-Pins (tests/test_oracle_crpc.py, tests/test_oracle_circuits.py): the worked 3x2 . 2x2
+The gadget circuits of Sec. III-C ("crpc_psq_softmax", "crpc_psq_gelu") are the CRPC +
+PSQ rows followed by the gadget's rows on Y (oracle/gadgets.py); their auxiliary block
+follows the prefix sums.
+
+Pins (tests/test_oracle_crpc.py, tests/test_oracle_circuits.py, tests/test_oracle_gadgets.py): the worked 3x2 . 2x2
 example of Sec. III-A (golden exponents), the identity as integer polynomials in Z,
 constraint satisfaction against a direct integer matmul, the constraint counts (n vs
 a b n) and the PSQ left-wire counts (6 vs 3 for a 3-term dot product), the paper's two
 negative examples, and for every circuit and public-input choice: satisfaction, a
 tampered output failing, row and variable counts, and honest Groth16 proofs verifying.
 """
+from . import gadgets
 from .bn254 import R, fr_from_int
 
 # Circuit variants of the paper's ablation (Sec. V, Table II):
@@ -53,7 +58,16 @@ from .bn254 import R, fr_from_int
 #               count Sec. III-A starts from) and one summing row per output
 # and the public-input choice: "xy" (X and Y public, the default reading) or "none" (X and
 # Y private too; only the constant one is public).
-CIRCUITS = ("crpc_psq", "crpc", "psq", "vanilla")
+# The nonlinear gadgets of Sec. III-C on the matmul output (oracle/gadgets.py):
+#   "crpc_psq_softmax"  the zkVC circuit, then per row of Y the max verification and the
+#                       exponential approximation of SoftMax's numerators
+#   "crpc_psq_gelu"     the zkVC circuit, then the GELU polynomial on every entry of Y
+CIRCUITS = ("crpc_psq", "crpc", "psq", "vanilla", "crpc_psq_softmax", "crpc_psq_gelu")
+
+
+def gadget_of(circuit):
+    """The Sec. III-C gadget a circuit appends to the CRPC + PSQ rows, or None."""
+    return {"crpc_psq_softmax": "softmax", "crpc_psq_gelu": "gelu"}.get(circuit)
 PUBLIC_IO = ("xy", "none")
 
 
@@ -65,9 +79,16 @@ class Shape:
         self.circuit, self.public_io = circuit, public_io
         self.n_io = a * n + a * b                          # entries of X and Y
         self.n_public = self.n_io if public_io == "xy" else 0   # l
-        self.n_aux = {"crpc_psq": n - 1, "crpc": n, "psq": a * b * (n - 1), "vanilla": a * b * n}[circuit]
+        g = gadget_of(circuit)
+        self.gadget = g
+        if g:
+            self.n_aux = n - 1 + gadgets.aux_count(g, a, b)
+            self.n_circuit_rows = n + gadgets.row_count(g, a, b)
+        else:
+            self.n_aux = {"crpc_psq": n - 1, "crpc": n, "psq": a * b * (n - 1), "vanilla": a * b * n}[circuit]
+            self.n_circuit_rows = {"crpc_psq": n, "crpc": n + 1, "psq": a * b * n,
+                                   "vanilla": a * b * n + a * b}[circuit]
         self.n_vars = 1 + self.n_io + n * b + self.n_aux
-        self.n_circuit_rows = {"crpc_psq": n, "crpc": n + 1, "psq": a * b * n, "vanilla": a * b * n + a * b}[circuit]
         self.n_rows = self.n_circuit_rows + self.n_public + 1
         N = 1
         while N < self.n_rows:
@@ -88,8 +109,12 @@ class Shape:
         return 1 + self.n_io + self.n * self.b + idx
 
     def s(self, k):
-        """crpc_psq: prefix sum S_k, k < n - 1."""
+        """crpc_psq (and the gadget circuits): prefix sum S_k, k < n - 1."""
         return self.aux(k)
+
+    def gadget_aux0(self):
+        """First variable of the gadget's auxiliary block (after the n - 1 prefix sums)."""
+        return self.aux(self.n - 1)
 
     def p(self, k):
         """crpc: product p_k = a_k b_k, k < n."""
@@ -112,7 +137,7 @@ def build_r1cs(shape, z, with_input_rows=True):
     input-consistency rows of the public variables (z is used by the CRPC circuits)."""
     a, n, b = shape.a, shape.n, shape.b
     rows = []
-    if shape.circuit in ("crpc_psq", "crpc"):
+    if shape.circuit in ("crpc_psq", "crpc") or shape.gadget:
         for k in range(n):
             A = {shape.x(i, k): pow(z, i * b, R) for i in range(a)}
             B = {shape.w(k, j): pow(z, j, R) for j in range(b)}
@@ -133,6 +158,8 @@ def build_r1cs(shape, z, with_input_rows=True):
         if shape.circuit == "crpc":   # (p_0 + ... + p_(n-1)) * 1 = Y(z)
             C = {shape.y(i, j): pow(z, i * b + j, R) for i in range(a) for j in range(b)}
             rows.append(({shape.p(k): 1 for k in range(n)}, {0: 1}, C))
+        if shape.gadget:              # Sec. III-C on Y
+            rows += gadgets.gadget_rows(shape.gadget, a, b, shape.y, shape.gadget_aux0())
     else:
         for i in range(a):
             for j in range(b):
@@ -173,8 +200,9 @@ def crpc_y_at_z(Y, z):
     return sum(pow(z, i * b + j, R) * fr_from_int(Y[i][j]) for i in range(a) for j in range(b)) % R
 
 
-def witness(shape, X, W, z, Y=None):
-    """Full assignment w (length n_vars).  Y defaults to the true product X W."""
+def witness(shape, X, W, z, Y=None, x_max=None):
+    """Full assignment w (length n_vars).  Y defaults to the true product X W.  x_max
+    overrides the SoftMax gadget's per-row maxima (wrong witnesses for the pins)."""
     a, n, b = shape.a, shape.n, shape.b
     if Y is None:
         Y = matmul_int(X, W)
@@ -189,7 +217,7 @@ def witness(shape, X, W, z, Y=None):
     for k in range(n):
         for j in range(b):
             w[shape.w(k, j)] = fr_from_int(W[k][j])
-    if shape.circuit in ("crpc_psq", "crpc"):
+    if shape.circuit in ("crpc_psq", "crpc") or shape.gadget:
         ak, bk = crpc_evaluations(X, W, z)
         if shape.circuit == "crpc":
             for k in range(n):
@@ -210,6 +238,8 @@ def witness(shape, X, W, z, Y=None):
                     elif k < n - 1:
                         acc += prod
                         w[shape.s3(i, j, k)] = fr_from_int(acc)
+    if shape.gadget:                                    # Sec. III-C on Y
+        gadgets.gadget_witness(shape.gadget, Y, w, shape.gadget_aux0(), x_max)
     return w
 
 

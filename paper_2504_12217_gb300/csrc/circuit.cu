@@ -5,12 +5,16 @@
 //   ZKVC_CIRCUIT_CRPC      CRPC rows with product variables and one summing row
 //   ZKVC_CIRCUIT_PSQ       per output y_ij a prefix-sum chain over its n products
 //   ZKVC_CIRCUIT_VANILLA   one row per product x_ik w_kj = p_ijk, one summing row per y_ij
+//   ZKVC_CIRCUIT_SOFTMAX   CRPC + PSQ, then the Sec. III-C SoftMax gadgets on each row of Y
+//                          (max verification, exponential by clipping and squaring)
+//   ZKVC_CIRCUIT_GELU      CRPC + PSQ, then the Sec. III-C GELU polynomial on every entry
 //
 // with X and Y public (ZKVC_PUBLIC_XY) or private (ZKVC_PUBLIC_NONE).  The rows are built on
 // the host in the same order and with the same variable numbering as the specialised
 // CRPC + PSQ prover (one | X | Y | W | auxiliary; input-consistency rows last), stored on
 // the device by rows (the prover's domain evaluations) and by columns (setup's per-variable
-// sums).  Coefficients are indices into a small table: 1, -1 and the CRPC powers z^e.
+// sums).  Coefficients are indices into a small table: 1, -1, the CRPC powers z^e and,
+// for the gadget circuits, signed powers of two and three gadget constants.
 //
 // Setup evaluates L_k(tau) for every row, sums A_v(tau), B_v(tau), C_v(tau) per variable
 // over its column, and turns the query scalars into fixed-base points with the windows the
@@ -45,6 +49,40 @@ static constexpr uint32_t COEF_ONE = 0, COEF_NEG = 1, COEF_Z0 = 2;
 static constexpr uint32_t LONG_ROW = 64;
 static constexpr uint32_t C1 = 16, C2 = 8;
 
+// Sec. III-C gadgets on Y as fixed point with GF fractional bits: d = x_max - y in GD
+// bits, u = |T| - d + 2^32 in GU bits (top bit: d <= |T|), base beta = c (2^GF - d / 2^GM),
+// GM squarings.  Per entry: GD + GU bits, beta, GM powers.
+static constexpr uint32_t GF = ZKVC_GADGET_FRAC_BITS, GM = ZKVC_GADGET_EXP_SQUARINGS;
+static constexpr uint64_t GT = 1ull << (GF + GM);
+static constexpr uint32_t GD = 32, GU = 33;
+static constexpr uint32_t G_PER_ENTRY = GD + GU + 1 + GM;
+static constexpr uint32_t G_ROWS_PER_ENTRY = GD + 1 + GU + 1 + 1 + GM;
+
+static bool is_gadget(int circuit) { return circuit == ZKVC_CIRCUIT_SOFTMAX || circuit == ZKVC_CIRCUIT_GELU; }
+static bool uses_crpc(int circuit) {
+  return circuit == ZKVC_CIRCUIT_CRPC_PSQ || circuit == ZKVC_CIRCUIT_CRPC || is_gadget(circuit);
+}
+__host__ __device__ static inline uint64_t softmax_row_aux(uint64_t b) { return 1 + (b > 2 ? b - 2 : 0) + b * G_PER_ENTRY; }
+
+// Coefficient table: 1, -1, z^0 .. z^(nz-1); for the gadget circuits then 2^0 .. 2^GU-1
+// (pow2), -2^0 .. -2^(GD-GM-1) (npow2) and -(|T| + 2^32), -2^(GF+1), -2^(2GF+2) (consts).
+struct CoefLayout {
+  uint32_t nz = 0, pow2 = 0, npow2 = 0, consts = 0, total = 0;
+};
+
+static CoefLayout coef_layout(const GShape& s) {
+  CoefLayout L;
+  L.nz = uses_crpc(s.circuit) ? (uint32_t)(uint64_t(s.a) * s.b) : 0u;
+  L.total = COEF_Z0 + L.nz;
+  if (is_gadget(s.circuit)) {
+    L.pow2 = L.total;
+    L.npow2 = L.pow2 + GU;
+    L.consts = L.npow2 + (GD - GM);
+    L.total = L.consts + 3;
+  }
+  return L;
+}
+
 GenericKey::~GenericKey() {
   for (auto& c : csr) {
     cudaFree(c.rowptr);
@@ -67,7 +105,7 @@ static uint32_t windows_for(int kind, uint32_t c) {
 
 int make_gshape(int a, int n, int b, int circuit, int pub, GShape* s) {
   ZK_CHECK(a >= 1 && n >= 1 && b >= 1, ZKVC_EINVAL, "shape (%d, %d, %d): every dimension must be >= 1", a, n, b);
-  ZK_CHECK(circuit >= ZKVC_CIRCUIT_CRPC_PSQ && circuit <= ZKVC_CIRCUIT_VANILLA, ZKVC_EINVAL, "circuit %d", circuit);
+  ZK_CHECK(circuit >= ZKVC_CIRCUIT_CRPC_PSQ && circuit <= ZKVC_CIRCUIT_GELU, ZKVC_EINVAL, "circuit %d", circuit);
   ZK_CHECK(pub == ZKVC_PUBLIC_XY || pub == ZKVC_PUBLIC_NONE, ZKVC_EINVAL, "public-input mode %d", pub);
   const uint64_t A = a, Nn = n, B = b;
   GShape g;
@@ -83,6 +121,11 @@ int make_gshape(int a, int n, int b, int circuit, int pub, GShape* s) {
     case ZKVC_CIRCUIT_CRPC_PSQ: g.n_aux = Nn - 1; g.n_crows = Nn; break;
     case ZKVC_CIRCUIT_CRPC: g.n_aux = Nn; g.n_crows = Nn + 1; break;
     case ZKVC_CIRCUIT_PSQ: g.n_aux = A * B * (Nn - 1); g.n_crows = A * B * Nn; aux_kind = SK_I32; break;
+    case ZKVC_CIRCUIT_SOFTMAX:
+      g.n_aux = Nn - 1 + A * softmax_row_aux(B);
+      g.n_crows = Nn + A * (B * G_ROWS_PER_ENTRY + (B > 1 ? B - 1 : 1));
+      break;
+    case ZKVC_CIRCUIT_GELU: g.n_aux = Nn - 1 + A * B; g.n_crows = Nn + A * B; break;
     default: g.n_aux = A * B * Nn; g.n_crows = A * B * Nn + A * B; aux_kind = SK_I16; break;
   }
   g.n_vars = 1 + g.n_io + Nn * B + g.n_aux;
@@ -126,6 +169,96 @@ struct HostR1cs {
   }
 };
 
+// Rows of the Sec. III-C gadgets over Y; the gadget's auxiliary block starts at aux0.
+// SoftMax, per row i of Y (block: x_max, P_1 .. P_(b-2), then per entry the GD bits of d,
+// the GU bits of u, beta, the GM powers): per entry the bit rows b * b = b and the
+// recomposition of d = x_max - y, the same for u = |T| - d + 2^32, beta = c (2^GF - q)
+// with c the top bit of u and q the bits of d from GM up, e_t = e_(t-1)^2; then the chain
+// (x_max - y_0)(x_max - y_1) = P_1, P_(j-1) (x_max - y_j) = P_j, closing at 0.  GELU: per
+// entry y * y = G - 2^(GF+1) y - 2^(2GF+2).
+template <class YV>
+static void gadget_rows(const GShape& s, YV Yv, uint64_t aux0, HostR1cs& R) {
+  const uint64_t a = s.a, b = s.b;
+  const CoefLayout L = coef_layout(s);
+  if (s.circuit == ZKVC_CIRCUIT_GELU) {
+    for (uint64_t i = 0; i < a; i++)
+      for (uint64_t j = 0; j < b; j++) {
+        const uint64_t y = Yv(i, j);
+        R.row();
+        R.add(0, y, COEF_ONE);
+        R.add(1, y, COEF_ONE);
+        R.add(2, aux0 + i * b + j, COEF_ONE);
+        R.add(2, y, L.consts + 1);
+        R.add(2, 0, L.consts + 2);
+      }
+    return;
+  }
+  const uint64_t per_row = softmax_row_aux(b), nprod = b > 2 ? b - 2 : 0;
+  for (uint64_t i = 0; i < a; i++) {
+    const uint64_t mx = aux0 + i * per_row, p1 = mx + 1, ent0 = mx + 1 + nprod;
+    for (uint64_t j = 0; j < b; j++) {
+      const uint64_t y = Yv(i, j), e0 = ent0 + j * G_PER_ENTRY;
+      for (uint32_t k = 0; k < GD; k++) {
+        R.row();
+        R.add(0, e0 + k, COEF_ONE);
+        R.add(1, e0 + k, COEF_ONE);
+        R.add(2, e0 + k, COEF_ONE);
+      }
+      R.row();  // sum 2^k d_k - x_max + y = 0
+      for (uint32_t k = 0; k < GD; k++) R.add(0, e0 + k, L.pow2 + k);
+      R.add(0, mx, COEF_NEG);
+      R.add(0, y, COEF_ONE);
+      R.add(1, 0, COEF_ONE);
+      const uint64_t u0 = e0 + GD;
+      for (uint32_t k = 0; k < GU; k++) {
+        R.row();
+        R.add(0, u0 + k, COEF_ONE);
+        R.add(1, u0 + k, COEF_ONE);
+        R.add(2, u0 + k, COEF_ONE);
+      }
+      R.row();  // sum 2^k u_k - (|T| + 2^32) + x_max - y = 0
+      for (uint32_t k = 0; k < GU; k++) R.add(0, u0 + k, L.pow2 + k);
+      R.add(0, 0, L.consts);
+      R.add(0, mx, COEF_ONE);
+      R.add(0, y, COEF_NEG);
+      R.add(1, 0, COEF_ONE);
+      const uint64_t beta = u0 + GU;
+      R.row();  // c * (2^GF - q) = beta
+      R.add(0, u0 + GU - 1, COEF_ONE);
+      R.add(1, 0, L.pow2 + GF);
+      for (uint32_t k = GM; k < GD; k++) R.add(1, e0 + k, L.npow2 + (k - GM));
+      R.add(2, beta, COEF_ONE);
+      uint64_t prev = beta;
+      for (uint32_t t = 0; t < GM; t++) {  // e_t = e_(t-1)^2
+        R.row();
+        R.add(0, prev, COEF_ONE);
+        R.add(1, prev, COEF_ONE);
+        R.add(2, beta + 1 + t, COEF_ONE);
+        prev = beta + 1 + t;
+      }
+    }
+    if (b == 1) {  // (x_max - y_0) * 1 = 0
+      R.row();
+      R.add(0, mx, COEF_ONE);
+      R.add(0, Yv(i, 0), COEF_NEG);
+      R.add(1, 0, COEF_ONE);
+    } else {
+      for (uint64_t j = 1; j < b; j++) {
+        R.row();
+        if (j == 1) {
+          R.add(0, mx, COEF_ONE);
+          R.add(0, Yv(i, 0), COEF_NEG);
+        } else {
+          R.add(0, p1 + (j - 2), COEF_ONE);
+        }
+        R.add(1, mx, COEF_ONE);
+        R.add(1, Yv(i, j), COEF_NEG);
+        if (j + 1 < b) R.add(2, p1 + (j - 1), COEF_ONE);
+      }
+    }
+  }
+}
+
 // The rows of the circuit, in the order of the oracle's definition.
 static void build_rows(const GShape& s, HostR1cs& R) {
   const uint64_t a = s.a, n = s.n, b = s.b, an = a * n;
@@ -134,7 +267,7 @@ static void build_rows(const GShape& s, HostR1cs& R) {
   auto Wv = [&](uint64_t k, uint64_t j) { return 1 + s.n_io + k * b + j; };
   auto AUX = [&](uint64_t t) { return 1 + s.n_io + n * b + t; };
   for (auto& x : R.m) x.rowptr.reserve(s.n_rows + 1);
-  if (s.circuit == ZKVC_CIRCUIT_CRPC_PSQ || s.circuit == ZKVC_CIRCUIT_CRPC) {
+  if (uses_crpc(s.circuit)) {
     for (uint64_t k = 0; k < n; k++) {
       R.row();
       for (uint64_t i = 0; i < a; i++) R.add(0, X(i, k), COEF_Z0 + (uint32_t)(i * b));
@@ -157,6 +290,7 @@ static void build_rows(const GShape& s, HostR1cs& R) {
       for (uint64_t i = 0; i < a; i++)
         for (uint64_t j = 0; j < b; j++) R.add(2, Yv(i, j), COEF_Z0 + (uint32_t)(i * b + j));
     }
+    if (is_gadget(s.circuit)) gadget_rows(s, Yv, AUX(n - 1), R);
   } else {
     const bool van = s.circuit == ZKVC_CIRCUIT_VANILLA;
     for (uint64_t i = 0; i < a; i++)
@@ -227,16 +361,33 @@ static int upload(const std::vector<T>& h, T** d, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ setup kernels
-__global__ void k_gen_coef_tab(const SetupConsts* sc, Fr* tab, uint32_t n) {
+// 2^k in Montgomery form (k < 64)
+__device__ Fr fr_pow2(uint32_t k) {
+  Fr x = Fr::zero();
+  x.v[k >> 5] = 1u << (k & 31);
+  return f_to_mont(x);
+}
+
+__global__ void k_gen_coef_tab(const SetupConsts* sc, Fr* tab, CoefLayout L) {
   uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
+  if (t >= L.total) return;
   Fr v;
   if (t == COEF_ONE)
     v = Fr::one();
   else if (t == COEF_NEG)
     v = f_neg(Fr::one());
-  else
+  else if (t < COEF_Z0 + L.nz)
     v = pow_u32(sc->z, t - COEF_Z0);
+  else if (t < L.npow2)
+    v = fr_pow2(t - L.pow2);
+  else if (t < L.consts)
+    v = f_neg(fr_pow2(t - L.npow2));
+  else if (t == L.consts)
+    v = f_neg(f_add(fr_pow2(GF + GM), fr_pow2(GD)));
+  else if (t == L.consts + 1)
+    v = f_neg(fr_pow2(GF + 1));
+  else
+    v = f_neg(fr_pow2(2 * GF + 2));
   st_field(tab + t, v);
 }
 
@@ -454,15 +605,16 @@ int setup_generic(int a, int n, int b, int circuit, int pub, const uint8_t* toxi
     G->n_long = (uint32_t)long_rows.size();
     if ((rc = upload(long_rows, &G->long_rows, st)) != ZKVC_OK) break;
     // coefficient table and the CRPC powers used by the witness kernels
-    const bool crpc = circuit == ZKVC_CIRCUIT_CRPC_PSQ || circuit == ZKVC_CIRCUIT_CRPC;
-    G->n_coef = COEF_Z0 + (crpc ? (uint32_t)(sh.a * sh.b) : 0u);
+    const bool crpc = uses_crpc(circuit);
+    const CoefLayout CL = coef_layout(sh);
+    G->n_coef = CL.total;
     if (cudaMalloc(&G->coef_tab, G->n_coef * sizeof(Fr)) != cudaSuccess) {
       cudaGetLastError();
       set_error("setup: coefficient table allocation failed");
       rc = ZKVC_ENOMEM;
       break;
     }
-    k_gen_coef_tab<<<(G->n_coef + 255) / 256, 256, 0, st>>>(d_sc, G->coef_tab, G->n_coef); ZK_COUNT_LAUNCH();
+    k_gen_coef_tab<<<(G->n_coef + 255) / 256, 256, 0, st>>>(d_sc, G->coef_tab, CL); ZK_COUNT_LAUNCH();
     // zA[i] = z^(ib), zB[j] = z^j are entries of the table
     for (int i = 0; i < a && crpc; i++)
       ZK_CUDA(cudaMemcpyAsync(pk->zA + i, G->coef_tab + COEF_Z0 + size_t(i) * b, sizeof(Fr), cudaMemcpyDeviceToDevice, st));
@@ -606,6 +758,93 @@ __global__ void k_gen_products(const int8_t* __restrict__ X, const int8_t* __res
   if (t >= total) return;
   const uint64_t k = t % n, ij = t / n, j = ij % b, i = ij / b;
   P[t] = (int16_t)(int32_t(X[i * n + k]) * int32_t(W[k * b + j]));
+}
+
+// canonical v < 2^32 or |v| < 2^63 as Fr in Montgomery form
+__device__ __forceinline__ Fr fr_from_u32(uint32_t v) {
+  Fr x = Fr::zero();
+  x.v[0] = v;
+  return f_to_mont(x);
+}
+
+__device__ __forceinline__ Fr fr_from_i64(int64_t v) {
+  const uint64_t mag = v < 0 ? uint64_t(0) - uint64_t(v) : uint64_t(v);
+  Fr x = Fr::zero();
+  x.v[0] = (uint32_t)mag;
+  x.v[1] = (uint32_t)(mag >> 32);
+  x = f_to_mont(x);
+  return v < 0 ? f_neg(x) : x;
+}
+
+// GELU gadget (Sec. III-C): G = y^2 + 2^(GF+1) y + 2^(2GF+2) for every entry of Y
+// (= (y + 2^GF)^2 + 3 2^(2GF) < 2^63 for |y| < 2^31)
+__global__ void k_gen_gelu(const int32_t* __restrict__ Y, uint64_t count, Fr* __restrict__ g) {
+  uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t y = Y[t];
+  st_field(g + t, fr_from_i64(y * y + y * (int64_t(1) << (GF + 1)) + (int64_t(1) << (2 * GF + 2))));
+}
+
+// SoftMax gadget (Sec. III-C) for row blockIdx.x of Y (b entries), a block of 256 threads:
+// x_max by a block reduction; per entry the bits of d = x_max - y and of
+// u = |T| - d + 2^32, beta = [d <= |T|] (2^GF - d / 2^GM) and its GM squarings; then the
+// prefix products P_j = (x_max - y_0) .. (x_max - y_j), j = 1 .. b-2, by chunks: each
+// thread multiplies its chunk, a log-step scan over the 256 chunk products in shared
+// memory gives each chunk its prefix, and a second pass writes the products.
+constexpr int SM_THREADS = 256;
+__global__ void __launch_bounds__(SM_THREADS) k_gen_softmax(const int32_t* __restrict__ Y, uint32_t b,
+                                                            Fr* __restrict__ g) {
+  __shared__ int32_t wmax[SM_THREADS / 32];
+  __shared__ Fr scan[SM_THREADS];
+  const uint32_t tid = threadIdx.x;
+  const int32_t* y = Y + uint64_t(blockIdx.x) * b;
+  Fr* out = g + uint64_t(blockIdx.x) * softmax_row_aux(b);
+  int32_t m = INT32_MIN;
+  for (uint32_t j = tid; j < b; j += SM_THREADS) m = max(m, y[j]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) wmax[tid >> 5] = m;
+  __syncthreads();
+  m = wmax[0];
+  for (int w = 1; w < SM_THREADS / 32; w++) m = max(m, wmax[w]);
+  if (tid == 0) st_field(out, f_from_int<FrCfg>(m));
+  const uint32_t nprod = b > 2 ? b - 2 : 0;
+  Fr* ent = out + 1 + nprod;
+  const Fr one = Fr::one(), zero = Fr::zero();
+  for (uint32_t j = tid; j < b; j += SM_THREADS) {
+    const uint32_t d = (uint32_t)(int64_t(m) - int64_t(y[j]));
+    const uint64_t u = GT - uint64_t(d) + (1ull << GD);
+    Fr* e = ent + uint64_t(j) * G_PER_ENTRY;
+    for (uint32_t k = 0; k < GD; k++) st_field(e + k, (d >> k) & 1u ? one : zero);
+    for (uint32_t k = 0; k < GU; k++) st_field(e + GD + k, (u >> k) & 1ull ? one : zero);
+    const int32_t beta = uint64_t(d) <= GT ? (1 << GF) - int32_t(d >> GM) : 0;
+    Fr p = f_from_int<FrCfg>(beta);
+    st_field(e + GD + GU, p);
+    for (uint32_t t = 0; t < GM; t++) {
+      p = f_mul(p, p);
+      st_field(e + GD + GU + 1 + t, p);
+    }
+  }
+  if (nprod == 0) return;
+  // prefix products of d_0 .. d_(b-2) (P_j for j = 1 .. b-2)
+  const uint32_t len = b - 1, chunk = (len + SM_THREADS - 1) / SM_THREADS;
+  const uint32_t lo = min(len, tid * chunk), hi = min(len, lo + chunk);
+  auto dfr = [&](uint32_t j) { return fr_from_u32((uint32_t)(int64_t(m) - int64_t(y[j]))); };
+  Fr acc = one;
+  for (uint32_t j = lo; j < hi; j++) acc = f_mul(acc, dfr(j));
+  st_field(&scan[tid], acc);
+  __syncthreads();
+  for (uint32_t off = 1; off < SM_THREADS; off <<= 1) {  // inclusive scan of the chunk products
+    Fr v = ld_field(&scan[tid]);
+    if (tid >= off) v = f_mul(ld_field(&scan[tid - off]), v);
+    __syncthreads();
+    st_field(&scan[tid], v);
+    __syncthreads();
+  }
+  Fr pre = tid ? ld_field(&scan[tid - 1]) : one;
+  for (uint32_t j = lo; j < hi; j++) {
+    pre = f_mul(pre, dfr(j));
+    if (j >= 1) st_field(out + 1 + (j - 1), pre);
+  }
 }
 
 struct WSrc {
@@ -846,14 +1085,22 @@ int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const u
   switch (sh.circuit) {
     case ZKVC_CIRCUIT_CRPC_PSQ:
     case ZKVC_CIRCUIT_CRPC:
+    case ZKVC_CIRCUIT_SOFTMAX:
+    case ZKVC_CIRCUIT_GELU:
       k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
-      if (sh.circuit == ZKVC_CIRCUIT_CRPC_PSQ) {
+      if (sh.circuit != ZKVC_CIRCUIT_CRPC) {
         k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz); ZK_COUNT_LAUNCH();
         // prefix sums into the auxiliary array; the first n evaluations land in ev and are
         // rewritten identically by the matrix product below
         k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, reinterpret_cast<Fr*>(B.aux), Aev, Bev, Cev, B.flags); ZK_COUNT_LAUNCH();
       } else {
         k_gen_crpc_products<<<(sh.n + 255) / 256, 256, 0, st>>>(B.ak, B.bk, sh.n, reinterpret_cast<Fr*>(B.aux)); ZK_COUNT_LAUNCH();
+      }
+      if (sh.circuit == ZKVC_CIRCUIT_SOFTMAX) {  // the gadget block follows the n - 1 prefix sums
+        k_gen_softmax<<<sh.a, SM_THREADS, 0, st>>>(dY, (uint32_t)sh.b, reinterpret_cast<Fr*>(B.aux) + (sh.n - 1)); ZK_COUNT_LAUNCH();
+      } else if (sh.circuit == ZKVC_CIRCUIT_GELU) {
+        const uint64_t t = uint64_t(sh.a) * sh.b;
+        k_gen_gelu<<<(unsigned)((t + 255) / 256), 256, 0, st>>>(dY, t, reinterpret_cast<Fr*>(B.aux) + (sh.n - 1)); ZK_COUNT_LAUNCH();
       }
       break;
     case ZKVC_CIRCUIT_PSQ: {

@@ -397,7 +397,7 @@ def zkvc_setup(a, n, b, toxic):
 
 ZKVC_CIRCUIT_CRPC_PSQ, ZKVC_CIRCUIT_CRPC, ZKVC_CIRCUIT_PSQ, ZKVC_CIRCUIT_VANILLA = 0, 1, 2, 3
 ZKVC_PUBLIC_XY, ZKVC_PUBLIC_NONE = 0, 1
-CIRCUIT_NAMES = {"crpc_psq": 0, "crpc": 1, "psq": 2, "vanilla": 3}
+CIRCUIT_NAMES = {"crpc_psq": 0, "crpc": 1, "psq": 2, "vanilla": 3, "crpc_psq_softmax": 4, "crpc_psq_gelu": 5}
 PUBLIC_NAMES = {"xy": 0, "none": 1}
 
 

@@ -1,6 +1,7 @@
 """GPU parity of the generic sparse-R1CS prover over the ablation circuits (Sec. V,
-Table II: CRPC + PSQ, CRPC without PSQ, PSQ without CRPC, vanilla) and the private-input
-mode: every key entry, verifying-key entry and proof equals the oracle's byte for byte on
+Table II: CRPC + PSQ, CRPC without PSQ, PSQ without CRPC, vanilla), the nonlinear gadget
+circuits of Sec. III-C (SoftMax's max verification and exponential, GELU, on the matmul
+output) and the private-input mode: every key entry, verifying-key entry and proof equals the oracle's byte for byte on
 small shapes; the generic CRPC + PSQ key proves the same bytes as the specialised prover;
 at the full [49,320] x [320,512] size every circuit's proof verifies under the library's
 pairing verifier and a perturbed one does not."""
@@ -18,6 +19,9 @@ pytestmark = pytest.mark.gpu
 
 COMBOS = list(itertools.product(crpc.CIRCUITS, crpc.PUBLIC_IO))
 SHAPES = [(1, 1, 1), (2, 3, 2), (3, 5, 4)]
+# the Sec. III-C gadget circuits: rows of Y with one entry (the product chain's b = 1
+# row), two (no product variable) and five; 71 rows per entry keep the oracle's setup short
+GADGET_SHAPES = [(1, 1, 1), (2, 2, 2), (2, 3, 5)]
 
 
 @pytest.fixture(scope="module")
@@ -37,7 +41,7 @@ def _by_var(pk_list, var_list, n_vars, enc, width):
 @pytest.mark.parametrize("circuit,pub", COMBOS)
 def test_keys_and_proofs_match_oracle(nv, circuit, pub):
     import torch
-    for si, (a, n, b) in enumerate(SHAPES):
+    for si, (a, n, b) in enumerate(GADGET_SHAPES if crpc.gadget_of(circuit) else SHAPES):
         seed = 9000 + 100 * crpc.CIRCUITS.index(circuit) + 10 * crpc.PUBLIC_IO.index(pub) + si
         toxic = inputs.setup_values(seed)
         sh = crpc.Shape(a, n, b, circuit, pub)

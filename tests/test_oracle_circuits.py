@@ -31,7 +31,12 @@ def test_satisfaction_and_counts(circuit, pub):
         X, W = _mats(a, n, b, a * 100 + n * 10 + b)
         rows = crpc.build_r1cs(sh, z)
         assert len(rows) == sh.n_rows
-        circuit_rows = {"crpc_psq": n, "crpc": n + 1, "psq": a * b * n, "vanilla": a * b * n + a * b}[circuit]
+        # gadget rows (Sec. III-C): per SoftMax entry 32 + 1 bit/recomposition rows for d,
+        # 33 + 1 for u, the base and 3 squarings; a product chain of max(1, b - 1) rows per
+        # row of Y; one GELU row per entry
+        circuit_rows = {"crpc_psq": n, "crpc": n + 1, "psq": a * b * n, "vanilla": a * b * n + a * b,
+                        "crpc_psq_softmax": n + a * (b * 71 + max(1, b - 1)),
+                        "crpc_psq_gelu": n + a * b}[circuit]
         assert sh.n_rows == circuit_rows + (a * n + a * b if pub == "xy" else 0) + 1
         w = crpc.witness(sh, X, W, z)
         assert len(w) == sh.n_vars
