@@ -331,14 +331,20 @@ def nominal_imad_peak(sms, mhz):
 
 
 def measure_imad_peak(nv, local):
-    """The integer-pipe peak measured on this GPU (zkvc_imad_rate): the faster of the two
-    microbenchmark forms, with the SM clock sampled while it runs."""
+    """The integer-pipe peak measured on this GPU (zkvc_imad_rate): the fastest of the
+    microbenchmark forms (a 32 x 32 -> 64-bit product counted as two IMADs, as in the 264
+    of a Montgomery product), with the SM clock sampled while it runs."""
     clocks = ClockSampler(local)
     clocks.start()
-    forms = {"independent_mad_lo": nv.zkvc_imad_rate(0, 1 << 18), "cios_carry_row": nv.zkvc_imad_rate(1, 1 << 18)}
+    names = ("independent_mad_lo", "cios_carry_row", "independent_mad_hi", "independent_mad_wide",
+             "mad_lo_carry_chains")
+    forms = {name: nv.zkvc_imad_rate(f, 1 << 18) for f, name in enumerate(names)}
+    # whole Montgomery products (reported beside the peak, not candidates for it)
+    products = {"fp_mul_carry_chain": nv.zkvc_imad_rate(5, 1 << 11), "fp_mulc_64bit_acc": nv.zkvc_imad_rate(6, 1 << 11)}
     clk = clocks.stop()
     best = max(forms.values(), key=lambda f: f["imad_per_s"])
-    return {"imad_per_s": best["imad_per_s"], "sms": best["sms"], "forms": forms, "clocks": clk}
+    return {"imad_per_s": best["imad_per_s"], "sms": best["sms"], "forms": forms, "montgomery_products": products,
+            "clocks": clk}
 
 
 def ntt_passes(log_n):
@@ -593,7 +599,8 @@ def run_gpu(args):
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TIMAD/s",
                 "frac": achieved / peak, "traffic": H_ACCUM_TRAFFIC.get(tuning[2]) if dom.startswith("k_accum0<G1>")
                 else None, "traffic_unit": "bytes per launch",
-                "peak_source": "measured on this GPU by zkvc_imad_rate (of measured), the faster of two forms",
+                "peak_source": "measured on this GPU by zkvc_imad_rate (of measured), the fastest of five "
+                               "multiply-add forms",
                 "peak_nominal": nominal_imad_peak(imad["sms"], 2070.0) / 1e12,
                 "algorithmic_imad_per_launch": work / max(calls, 1),
                 "launch_ms": ms / max(calls, 1)}

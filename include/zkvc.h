@@ -75,12 +75,18 @@ int zkvc_profile_span(int stage, double* start_ms, double* end_ms);
 /* Integer-pipe throughput microbenchmark: the measured peak of the 32-bit multiply-add
  * (IMAD) that every Montgomery product of the prover is made of (BN254 field arithmetic
  * of the groth16 backend, Sec. IV; the roofline denominator of the MSM and NTT kernels).
- * form 0: sixteen independent mad.lo.u32 chains per thread; form 1: the CIOS row of the
- * field code (a carry chain of eight mad.lo and eight mad.hi).  A full-occupancy grid
- * over every SM runs `iters` iterations of 16 IMADs per thread, once untimed (iters / 8)
- * and once timed with CUDA events on `stream`; the call synchronises.  Outputs (any may be
- * null): IMADs per second, the timed launch in ms and the SM count used.  ZKVC_EINVAL for a
- * form other than 0 or 1 or iters outside [1, 2^24].
+ * A 32 x 32 -> 64-bit product counts as two IMADs (its low and high words), as in the
+ * 264 of a CIOS product.  form 0: sixteen independent mad.lo.u32 chains per thread;
+ * 1: the CIOS row of the field code (a carry chain of eight mad.lo and eight mad.hi);
+ * 2: sixteen independent mad.hi.u32 chains; 3: eight independent mad.wide.u32 chains
+ * (64-bit accumulators); 4: two carry chains of eight mad.lo; 5 and 6: two independent
+ * chains of whole Fp Montgomery products per thread (264 IMADs each), 5 with the inlined
+ * carry-chain product, 6 with the out-of-line 64-bit-accumulator product of the point
+ * formulas.  A full-occupancy grid over every SM runs `iters` iterations (16 IMADs per
+ * thread for forms 0 .. 4), once untimed (iters / 8) and once timed with CUDA events on
+ * `stream`; the call synchronises.  Outputs (any may be null): IMADs per second, the
+ * timed launch in ms and the SM count used.  ZKVC_EINVAL for a form outside 0 .. 6 or
+ * iters outside [1, 2^24].
  */
 int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int* sms, void* stream);
 

@@ -246,12 +246,20 @@ template int msm_api<Fp>(const uint8_t*, const uint8_t*, size_t, void*, size_t, 
 template size_t msm_api_ws<Fp>(size_t);
 
 // ------------------------------------------------------------------ integer-pipe rate
-// Throughput microbenchmark of the 32-bit multiply-add that Montgomery products are made
-// of.  Form 0: sixteen independent mad.lo.u32 chains per thread.  Form 1: the product's
-// own row, a carry chain of eight mad.lo.cc / madc.lo.cc and eight mad.hi.cc /
-// madc.hi.cc (sixteen IMADs), as in the CIOS rows of the field code.  Every thread
-// counts 16 IMADs per iteration; a full-occupancy grid of 256-thread blocks covers all
-// SMs.  The result xor goes to `sink` so that nothing is dead code.
+// Throughput microbenchmark of the 32-bit multiply-adds that Montgomery products are made
+// of, counted as the products' IMADs are (a 32 x 32 -> 64-bit product is two: its low
+// and its high word).  Every form runs 16 such IMADs per thread and iteration:
+//   0  sixteen independent mad.lo.u32 chains
+//   1  the CIOS row of the field code: a carry chain of eight mad.lo.cc / madc.lo.cc,
+//      then eight mad.hi.cc / madc.hi.cc
+//   2  sixteen independent mad.hi.u32 chains
+//   3  eight independent mad.wide.u32 chains (64-bit accumulators; two IMADs each)
+//   4  two carry chains of eight mad.lo.cc / madc.lo.cc
+//   5  whole Fp Montgomery products, the inlined carry-chain CIOS (f_mul): two independent
+//      product chains per thread, 264 IMADs per product
+//   6  the same with the out-of-line 64-bit-accumulator CIOS of the point formulas (f_mulc)
+// A full-occupancy grid of 256-thread blocks covers all SMs.  The result xor goes to
+// `sink` so that nothing is dead code.
 template <int FORM>
 __global__ void __launch_bounds__(256) k_imad_rate(uint32_t iters, uint32_t seed, uint32_t* sink) {
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -259,10 +267,39 @@ __global__ void __launch_bounds__(256) k_imad_rate(uint32_t iters, uint32_t seed
 #pragma unroll
   for (int j = 0; j < 16; j++) t[j] = g * 2654435761u + seed * (j + 1);
   const uint32_t x = seed | 1u, y = g ^ 0x9e3779b9u;
+  uint64_t w[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) w[j] = (uint64_t(t[j]) << 32) | t[j + 8];
   for (uint32_t it = 0; it < iters; it++) {
     if constexpr (FORM == 0) {
 #pragma unroll
       for (int j = 0; j < 16; j++) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(t[j]) : "r"(x), "r"(y));
+    } else if constexpr (FORM == 2) {
+#pragma unroll
+      for (int j = 0; j < 16; j++) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(t[j]) : "r"(x), "r"(y));
+    } else if constexpr (FORM == 3) {
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const uint32_t lo = (uint32_t)w[j];
+        asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[j]) : "r"(lo), "r"(x));
+      }
+    } else if constexpr (FORM == 4) {
+      const uint32_t b = (t[7] ^ t[15]) | 1u;  // changes every iteration: no product is invariant
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+        asm volatile(
+            "mad.lo.cc.u32  %0, %8,  %16, %0;\n\t"
+            "madc.lo.cc.u32 %1, %9,  %16, %1;\n\t"
+            "madc.lo.cc.u32 %2, %10, %16, %2;\n\t"
+            "madc.lo.cc.u32 %3, %11, %16, %3;\n\t"
+            "madc.lo.cc.u32 %4, %12, %16, %4;\n\t"
+            "madc.lo.cc.u32 %5, %13, %16, %5;\n\t"
+            "madc.lo.cc.u32 %6, %14, %16, %6;\n\t"
+            "madc.lo.u32    %7, %15, %16, %7;"
+            : "+r"(t[8 * h + 0]), "+r"(t[8 * h + 1]), "+r"(t[8 * h + 2]), "+r"(t[8 * h + 3]), "+r"(t[8 * h + 4]),
+              "+r"(t[8 * h + 5]), "+r"(t[8 * h + 6]), "+r"(t[8 * h + 7])
+            : "r"(t[8 - 8 * h]), "r"(t[9 - 8 * h]), "r"(t[10 - 8 * h]), "r"(t[11 - 8 * h]), "r"(t[12 - 8 * h]),
+              "r"(t[13 - 8 * h]), "r"(t[14 - 8 * h]), "r"(t[15 - 8 * h]), "r"(b));
     } else {
       const uint32_t b = t[15] | 1u;
       asm volatile(
@@ -291,6 +328,30 @@ __global__ void __launch_bounds__(256) k_imad_rate(uint32_t iters, uint32_t seed
   uint32_t acc = 0;
 #pragma unroll
   for (int j = 0; j < 16; j++) acc ^= t[j];
+#pragma unroll
+  for (int j = 0; j < 8; j++) acc ^= (uint32_t)w[j] ^ (uint32_t)(w[j] >> 32);
+  if (acc == 0x12345678u) sink[0] = acc;
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(256) k_mont_rate(uint32_t iters, uint32_t seed, uint32_t* sink) {
+  const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  Fp a = Fp::one(), b = Fp::one(), m = Fp::one();
+  a.v[0] ^= g;
+  b.v[1] ^= g * 7u;
+  m.v[2] ^= seed;
+  for (uint32_t it = 0; it < iters; it++) {
+    if constexpr (FORM == 5) {
+      a = f_mul(a, m);
+      b = f_mul(b, m);
+    } else {
+      a = f_mulc(a, m);
+      b = f_mulc(b, m);
+    }
+  }
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < 8; j++) acc ^= a.v[j] ^ b.v[j];
   if (acc == 0x12345678u) sink[0] = acc;
 }
 
@@ -461,7 +522,7 @@ int zkvc_msm_g2(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, voi
 
 int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int* sms, void* stream) {
   clear_error();
-  ZK_CHECK(form == 0 || form == 1, ZKVC_EINVAL, "imad_rate: form %d", form);
+  ZK_CHECK(form >= 0 && form <= 6, ZKVC_EINVAL, "imad_rate: form %d", form);
   ZK_CHECK(iters >= 1 && iters <= (1u << 24), ZKVC_EINVAL, "imad_rate: %u iterations outside [1, 2^24]", iters);
   static thread_local uint32_t* t_sink = nullptr;
   static thread_local int t_dev = -1;
@@ -473,7 +534,9 @@ int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int
   }
   cudaStream_t st = (cudaStream_t)stream;
   int per_sm = 0;
-  auto kern = form == 0 ? k_imad_rate<0> : k_imad_rate<1>;
+  auto kern = form == 0 ? k_imad_rate<0> : form == 1 ? k_imad_rate<1> : form == 2 ? k_imad_rate<2>
+              : form == 3 ? k_imad_rate<3> : form == 4 ? k_imad_rate<4> : form == 5 ? k_mont_rate<5>
+                                                                                    : k_mont_rate<6>;
   ZK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
   const int nsm = device_sm_count();
   const unsigned blocks = (unsigned)(nsm * (per_sm > 0 ? per_sm : 1));
@@ -490,7 +553,8 @@ int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int
   ZK_CUDA(cudaEventElapsedTime(&t, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  const double ops = double(blocks) * 256.0 * double(iters) * 16.0;
+  const double per_iter = form >= 5 ? 2.0 * 264.0 : 16.0;
+  const double ops = double(blocks) * 256.0 * double(iters) * per_iter;
   if (ms) *ms = t;
   if (imad_per_s) *imad_per_s = t > 0 ? ops / (t * 1e-3) : 0.0;
   if (sms) *sms = nsm;

@@ -4,12 +4,13 @@
 // Scalars are recoded into signed c-bit digits d in (-2^(c-1), 2^(c-1)], so a digit
 // selects bucket |d| and the sign negates the base's y coordinate.  Every nonzero digit
 // becomes one term (bucket key, base index | sign).  Terms are counting-sorted by key
-// (histogram, scan, atomic scatter), then each bucket's terms are summed by a
-// load-balanced segmented reduction: every chunk of T0 consecutive terms of a bucket goes
-// to one thread (mixed XYZZ + affine additions), and the chunk sums of a bucket are added
-// along a binary tree inside the same kernel -- of two sibling subtrees, the thread that
-// finishes second (an atomic counter per tree node tells it) adds both and climbs on, the
-// first one exits.  Heavily skewed buckets (int8 scalars put ~1300 terms in each of 128
+// (histogram, scan, atomic scatter), then the sorted terms are summed by a balanced
+// segmented reduction: every chunk of T0 consecutive sorted terms goes to one thread
+// (mixed XYZZ + affine additions), which stores a partial sum each time a bucket ends
+// inside its chunk, so every thread does the same number of additions whatever the
+// bucket sizes; the partial sums of a bucket are then added along a binary tree in one
+// launch -- of two sibling subtrees, the thread that finishes second (an atomic counter
+// per tree node tells it) adds both and climbs on, the first one exits.  Heavily skewed buckets (int8 scalars put ~1300 terms in each of 128
 // buckets) so cost only log2 of their chunk count in depth, with no extra launches.
 // A window's result sum_v v B_v is evaluated as sum_b 2^b U_b with U_b the sum of the
 // buckets whose index has bit b set: one block per slice of a bit's buckets reduces it
@@ -363,9 +364,24 @@ __global__ void __launch_bounds__(HB_THREADS) k_scatter(const uint32_t* __restri
   }
 }
 
-__global__ void k_chunks(const uint32_t* counts, uint32_t K, uint32_t T0, uint32_t* nch) {
+// Partial-sum slots of the balanced accumulation.  Chunk q covers the sorted terms
+// [q T0, (q + 1) T0); bucket k covers [offs[k], offs[k+1]).  A (chunk, bucket) pair that
+// overlaps stores its partial sum at slot q + k: walking the terms in order, each step to
+// the next overlapping pair moves to the next chunk, the next non-empty bucket or both, so
+// q + k strictly increases and the slots are distinct.  Bucket k (count > 0) owns the
+// contiguous slots [choff[k], choff[k] + nch[k]) with choff[k] = offs[k] / T0 + k and nch[k]
+// the chunks it overlaps; choff[K] bounds all slots.
+__global__ void k_chunk_layout(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offs, uint32_t K,
+                               uint32_t T0, uint32_t* nch, uint32_t* choff) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < K) nch[k] = (counts[k] + T0 - 1) / T0;
+  if (k > K) return;
+  if (k == K) {
+    choff[K] = (offs[K] + T0 - 1) / T0 + K;
+    return;
+  }
+  const uint32_t lo = offs[k] / T0;
+  choff[k] = lo + k;
+  nch[k] = counts[k] ? (offs[k + 1] - 1) / T0 - lo + 1 : 0u;
 }
 
 // largest k in [0, K) with off[k] <= q
@@ -379,10 +395,12 @@ __device__ __forceinline__ uint32_t find_key(const uint32_t* off, uint32_t K, ui
 }
 
 // ------------------------------------------------------------------ bucket sums
-__global__ void k_chunk_keys(const uint32_t* __restrict__ choff, uint32_t K, uint32_t* chunk_key) {
+// bucket of every partial-sum slot (slots no bucket owns keep KEY_NONE)
+__global__ void k_chunk_keys(const uint32_t* __restrict__ choff, const uint32_t* __restrict__ nch, uint32_t K,
+                             uint32_t* chunk_key) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
-  uint32_t a = choff[k], b = choff[k + 1];
+  const uint32_t a = choff[k], b = a + nch[k];
   for (uint32_t q = a; q < b; q++) chunk_key[q] = k;
 }
 
@@ -422,32 +440,81 @@ __device__ __forceinline__ XYZZ<F> madd_lanes(const XYZZ<F>& p, const Affine<F>&
   else return p_add_affine_quad(p, q);
 }
 
-// level 0: chunk q sums up to T0 consecutive terms of its bucket (mixed additions)
+#ifndef ZKVC_ACCUM_MINB
+#define ZKVC_ACCUM_MINB 1
+#endif
+template <class F>
+struct AccumMinB {
+  static constexpr int value = sizeof(F) > 32 ? 1 : ZKVC_ACCUM_MINB;
+};
+
+// level 0: chunk q sums the sorted terms [q T0, (q + 1) T0) with mixed additions, storing
+// its running sum at slot q + k whenever bucket k ends inside the chunk and at its end
 template <class F, int QL>
-__global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sorted, const uint32_t* __restrict__ offs,
-                                                const uint32_t* __restrict__ choff, const uint32_t* __restrict__ chunk_key,
-                                                uint32_t K, uint32_t T0, const Affine<F>* __restrict__ bases,
-                                                const Affine<F>* const* __restrict__ obases, int key_shift,
-                                                XYZZ<F>* part) {
-  uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
-  if (q >= choff[K]) return;  // uniform within a quad
-  uint32_t k = chunk_key[q];
-  uint32_t j = q - choff[k];
-  uint32_t start = offs[k] + j * T0;
-  uint32_t end = min(start + T0, offs[k + 1]);
+__global__ void __launch_bounds__(256, AccumMinB<F>::value) k_accum0(const uint32_t* __restrict__ sorted,
+                                                                    const uint32_t* __restrict__ offs, uint32_t K,
+                                                                    uint32_t T0, const Affine<F>* __restrict__ bases,
+                                                                    const Affine<F>* const* __restrict__ obases,
+                                                                    int key_shift, XYZZ<F>* part) {
+  const uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
+  const uint32_t S = offs[K];
+  const uint64_t start64 = uint64_t(q) * T0;
+  if (start64 >= S) return;  // uniform within a quad
+  const uint32_t start = (uint32_t)start64;
+  const uint64_t end64 = start64 + T0;
+  const uint32_t end = end64 < S ? (uint32_t)end64 : S;
+  uint32_t k = find_key(offs, K, start);  // the bucket holding term `start`
+  uint32_t next = offs[k + 1];
   if (key_shift >= 0) bases = obases[k >> key_shift];
+  const bool lead = QL == 1 || quad_lane() == 0;
   XYZZ<F> acc = XYZZ<F>::inf();
+  // one loop of exactly end - start additions for every lane (no divergence between
+  // lanes whose buckets end at different terms); a bucket's end stores the partial sum
+  // and restarts the sum at infinity (ZZ = 0)
   for (uint32_t p = start; p < end; p++) {
+    if (p >= next) {
+      if (lead) st_field(part + q + k, acc);
+      acc.ZZ = F::zero();
+      acc.ZZZ = F::zero();
+      do {  // the next non-empty bucket
+        k++;
+        next = offs[k + 1];
+      } while (p >= next);
+      if (key_shift >= 0) bases = obases[k >> key_shift];
+    }
     uint32_t v = sorted[p];
     Affine<F> P = ld_field(bases + (v & 0x7fffffffu));
     if (v >> 31) P.y = f_neg(P.y);
     acc = madd_lanes<QL>(acc, P);
   }
-  if (QL == 1 || quad_lane() == 0) st_field(part + q, acc);
+  if (lead) st_field(part + q + k, acc);
 }
 
-// The chunk sums of each bucket are added along the binary tree over chunk positions
-// 0..np-1, in one launch: at span s the subtree at position i (a multiple of s) pairs
+// Buckets with at most FOLD_SERIAL partial sums (the common case of a balanced
+// accumulation: a bucket split by one or two chunk boundaries) are folded by one thread
+// (or quad) per bucket, serially, without counters; k_fold_tree takes the larger ones.
+constexpr uint32_t FOLD_SERIAL = 4;
+template <class F, int QL>
+__global__ void __launch_bounds__(128) k_fold_serial(const uint32_t* __restrict__ choff,
+                                                     const uint32_t* __restrict__ nch, uint32_t K, XYZZ<F>* part) {
+  const uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
+  if (k >= K) return;  // uniform within a quad
+  const uint32_t np = nch[k];
+  if (np < 2 || np > FOLD_SERIAL) return;
+  const uint32_t base = choff[k];
+  XYZZ<F> acc = ld_field(part + base);
+  for (uint32_t i = 1; i < np; i++) {
+    const XYZZ<F> o = ld_field(part + base + i);
+    if (QL > 1)
+      acc = p_add_quad(acc, o);
+    else
+      acc = p_add(acc, o);
+  }
+  if (QL == 1 || quad_lane() == 0) st_field(part + base, acc);
+}
+
+// The partial sums of each bucket (its np = nch[k] slots from choff[k]) are added along
+// the binary tree over slot positions 0..np-1, in one launch: at span s the subtree at position i (a multiple of s) pairs
 // with the one at i ^ s.  Each sibling counts in at the node's counter (index: left
 // position + s - 1, distinct over all levels since it ends in exactly log2 s one-bits);
 // the first to arrive exits, the second adds both sums and climbs on.  A left subtree
@@ -457,14 +524,16 @@ __global__ void __launch_bounds__(256) k_accum0(const uint32_t* __restrict__ sor
 // zeroed counter per chunk.  The counter's fetch-and-add releases the climber's store
 // and acquires its sibling's.  QL lanes per chunk as in the accumulation.
 template <class F, int QL>
-__global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ choff,
+__global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ choff, const uint32_t* __restrict__ nch,
                                                    const uint32_t* __restrict__ chunk_key, uint32_t K,
                                                    XYZZ<F>* part, uint32_t* arrive) {
   const uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
   if (q >= choff[K]) return;  // uniform within a quad
-  const bool lead = QL == 1 || quad_lane() == 0;
   const uint32_t k = chunk_key[q];
-  const uint32_t base = choff[k], np = choff[k + 1] - base;
+  if (k == KEY_NONE) return;  // a slot no bucket owns
+  const uint32_t base = choff[k], np = nch[k];
+  if (np <= FOLD_SERIAL) return;  // k_fold_serial's
+  const bool lead = QL == 1 || quad_lane() == 0;
   uint32_t pos = q - base;
   XYZZ<F> acc;
   bool have = false;  // acc holds this subtree's sum (else it is only in part[])
@@ -875,12 +944,12 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
     k_scatter<<<sb, HB_THREADS, 0, st>>>(L.keys, L.vals, S, L.cursor, L.sorted); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
-  // chunks of T0 terms per bucket
-  k_chunks<<<(K + 255) / 256, 256, 0, st>>>(L.counts, K, T0, L.nch); ZK_COUNT_LAUNCH();
+  // chunks of T0 sorted terms and the buckets' partial-sum slots
+  k_chunk_layout<<<(K + 1 + 255) / 256, 256, 0, st>>>(L.counts, L.offs, K, T0, L.nch, L.choff); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  ZK_TRY(scan_u32(L.nch, L.choff, K, a, st));
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace too small for scans");
-  k_chunk_keys<<<(K + 255) / 256, 256, 0, st>>>(L.choff, K, L.chunk_key); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaMemsetAsync(L.chunk_key, 0xff, size_t(L.qmax) * sizeof(uint32_t), st));
+  k_chunk_keys<<<(K + 255) / 256, 256, 0, st>>>(L.choff, L.nch, K, L.chunk_key); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaMemsetAsync(L.arrive, 0, size_t(L.qmax) * sizeof(uint32_t), st));
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
   const uint32_t at = p.tune.accum_threads;
@@ -893,9 +962,9 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   if (accum_stage >= 0) prof_mark(accum_stage, true, st);
   const auto* ob = reinterpret_cast<const Affine<F>* const*>(L.obases);
   if (lanes == 4)
-    k_accum0<F, 4><<<qb, at, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases, ob, p.key_shift, part);
+    k_accum0<F, 4><<<qb, at, 0, st>>>(L.sorted, L.offs, K, T0, bases, ob, p.key_shift, part);
   else
-    k_accum0<F, 1><<<qb, at, 0, st>>>(L.sorted, L.offs, L.choff, L.chunk_key, K, T0, bases, ob, p.key_shift, part);
+    k_accum0<F, 1><<<qb, at, 0, st>>>(L.sorted, L.offs, K, T0, bases, ob, p.key_shift, part);
   ZK_COUNT_LAUNCH();
   if (accum_stage >= 0) {
     prof_mark(accum_stage, false, st);
@@ -903,10 +972,15 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   }
   ZK_CUDA(cudaGetLastError());
   if (after_accum) ZK_CUDA(cudaEventRecord(after_accum, st));
-  if (flanes == 4)
-    k_fold_tree<F, 4><<<fb, 128, 0, st>>>(L.choff, L.chunk_key, K, part, L.arrive);
-  else
-    k_fold_tree<F, 1><<<fb, 128, 0, st>>>(L.choff, L.chunk_key, K, part, L.arrive);
+  const unsigned sfb = (unsigned)((uint64_t(K) * flanes + 127) / 128);
+  if (flanes == 4) {
+    k_fold_serial<F, 4><<<sfb, 128, 0, st>>>(L.choff, L.nch, K, part);
+    k_fold_tree<F, 4><<<fb, 128, 0, st>>>(L.choff, L.nch, L.chunk_key, K, part, L.arrive);
+  } else {
+    k_fold_serial<F, 1><<<sfb, 128, 0, st>>>(L.choff, L.nch, K, part);
+    k_fold_tree<F, 1><<<fb, 128, 0, st>>>(L.choff, L.nch, L.chunk_key, K, part, L.arrive);
+  }
+  ZK_COUNT_LAUNCH();
   ZK_COUNT_LAUNCH();
   // sum_v v B_v per (output, window) by bit decomposition
   XYZZ<F>* Sl = reinterpret_cast<XYZZ<F>*>(L.S);

@@ -197,7 +197,8 @@ def zkvc_profile_read():
 
 def zkvc_imad_rate(form=1, iters=1 << 14):
     """The integer-pipe microbenchmark: {"imad_per_s", "ms", "sms"} (form 0: independent
-    mad.lo chains; form 1: the field code's CIOS carry-chain row)."""
+    mad.lo chains; 1: the field code's CIOS carry-chain row; 2: independent mad.hi; 3:
+    independent mad.wide (two IMADs each); 4: mad.lo carry chains)."""
     rate, ms, sms = ctypes.c_double(), ctypes.c_double(), _c_int()
     check(lib().zkvc_imad_rate(form, iters, ctypes.byref(rate), ctypes.byref(ms), ctypes.byref(sms), _stream()))
     return {"imad_per_s": rate.value, "ms": ms.value, "sms": sms.value}
