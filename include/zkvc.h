@@ -369,6 +369,19 @@ int zkvc_pk_get_tuning(const zkvc_pk* pk, uint32_t tuning[ZKVC_PK_TUNING_LEN]);
 #define ZKVC_PROVE_CHAIN 1
 #define ZKVC_PROVE_AUTO 2 /* zkvc_pk_autotune only: tune both modes, keep the faster */
 size_t zkvc_prove_workspace_bytes_mode(const zkvc_pk* pk, int mode);
+/* Proof of a claimed product: the statement of zkVC's use case (Sec. I; Gen / Prove of
+ * Sec. II) in which a server claims Y = X W and proves it.  Like zkvc_prove, but Y is an
+ * input: dY_claimed (int32, a x b, row-major, device, read only) enters the witness as it
+ * is, nothing computes X W.  If it is not X W the constraints cannot all hold: the call
+ * returns ZKVC_EUNSAT (the PSQ chain does not close against Y(z), or, for circuits
+ * without it, the quotient has degree N - 1) and the proof bytes are meaningless.  Works
+ * with keys of zkvc_setup (in the key's tuned mode, enqueued directly, never from the
+ * captured graph) and of zkvc_setup_circuit; workspace as for zkvc_prove.  Synchronises
+ * `stream`.
+ */
+int zkvc_prove_claimed(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const int32_t* d_Y_claimed,
+                       const uint8_t rs[64], void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream);
+
 int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64],
                     int32_t* d_Y, void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream);
 
@@ -519,6 +532,17 @@ int zkvc_server_wait(zkvc_server* server, uint64_t ticket, int timeout_ms, uint8
 int zkvc_server_stats(zkvc_server* server, uint64_t* completed, int* in_flight, int* queued, size_t* bytes_in_use,
                       size_t* peak_bytes, uint64_t* chain_mode);
 size_t zkvc_server_request_bytes(const zkvc_pk* pk, int mode);
+
+/* Diagnostic knob for the bounded device-side waits (the fault handling that a
+ * production prover needs; no counterpart in the paper): the time limit, in ns, of the
+ * tensor-core witness matmul's waits for its MMAs in kernels launched from now on (the
+ * one-proof and generic provers, the server and zkvc_matmul_i8; default 200 ms; captured
+ * graphs keep the value of their capture).  0 makes the first wait give up at once, which
+ * exercises the timeout path: the kernel flags the timeout, waits for its outstanding MMAs
+ * with the full 200 ms limit, frees its tensor memory and returns, and the call reports
+ * ZKVC_ETIMEOUT.  Always ZKVC_OK.
+ */
+int zkvc_set_device_wait_limit_ns(uint64_t ns);
 
 /* Deadline of the library's host-side waits for device work (batched proving and the
  * proof server), in milliseconds (default 60000).  A wait that runs out returns

@@ -15,6 +15,8 @@ int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, 
                void* ws, size_t ws_bytes, uint8_t* proof, cudaStream_t st);
 int prove_graph(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs, int32_t* dY,
                 void* ws, size_t ws_bytes, uint8_t* proof, cudaStream_t st);
+int prove_claimed(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs,
+                  const int32_t* dY, void* ws, size_t ws_bytes, uint8_t* proof, cudaStream_t st);
 template <class F>
 int export_points(const Affine<F>* src, const std::vector<uint64_t>& idx, uint8_t* host_out, cudaStream_t st);
 
@@ -474,6 +476,17 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint
   ZK_TRY(device_guard(pk->device));
   if (pk->gen) return prove_generic(pk, dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
   return prove_graph(pk, (int)pk->prove_tune[6], dX, dW, rs, dY, d_ws, ws_bytes, proof, (cudaStream_t)stream);
+}
+
+int zkvc_prove_claimed(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const int32_t* dY_claimed,
+                       const uint8_t rs[64], void* d_ws, size_t ws_bytes, uint8_t proof[256], void* stream) {
+  set_error("%s", "");
+  ZK_CHECK(pk && dY_claimed, ZKVC_EINVAL, "prove_claimed: null key or claimed Y");
+  ZK_TRY(device_guard(pk->device));
+  if (pk->gen)
+    return prove_generic(pk, dX, dW, rs, const_cast<int32_t*>(dY_claimed), d_ws, ws_bytes, proof,
+                         (cudaStream_t)stream, true);
+  return prove_claimed(pk, (int)pk->prove_tune[6], dX, dW, rs, dY_claimed, d_ws, ws_bytes, proof, (cudaStream_t)stream);
 }
 
 int zkvc_prove_mode(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t rs[64], int32_t* dY,

@@ -379,6 +379,12 @@ int zkvc_glv_split(const uint8_t k[32], uint8_t out[34]) {
 
 uint64_t zkvc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int zkvc_set_device_wait_limit_ns(uint64_t ns) {
+  clear_error();
+  set_matmul_first_wait_ns(ns);
+  return ZKVC_OK;
+}
+
 int zkvc_set_wait_timeout_ms(int ms) {
   clear_error();
   ZK_CHECK(ms > 0, ZKVC_EINVAL, "wait timeout of %d ms", ms);

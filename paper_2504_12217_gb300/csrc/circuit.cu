@@ -1050,7 +1050,7 @@ struct GenStreams {
 static thread_local GenStreams t_gen;
 
 int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host, int32_t* dY, void* ws,
-                  size_t ws_bytes, uint8_t* proof_host, cudaStream_t st) {
+                  size_t ws_bytes, uint8_t* proof_host, cudaStream_t st, bool y_given) {
   ZK_CHECK(pk && pk->gen && dX && dW && rs_host && dY && ws && proof_host, ZKVC_EINVAL, "prove: null argument");
   const GenericKey& G = *pk->gen;
   const GShape& sh = G.sh;
@@ -1080,8 +1080,8 @@ int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const u
     ZK_CUDA(cudaMemcpyAsync(B.glv, g, sizeof(g), cudaMemcpyHostToDevice, st));
   }
   k_randomness<<<1, 1, 0, st>>>(B.rs, B.flags); ZK_COUNT_LAUNCH();
-  // witness: Y, then the auxiliary variables
-  ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
+  // witness: Y (X W, or the caller's claimed Y), then the auxiliary variables
+  if (!y_given) ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
   switch (sh.circuit) {
     case ZKVC_CIRCUIT_CRPC_PSQ:
     case ZKVC_CIRCUIT_CRPC:

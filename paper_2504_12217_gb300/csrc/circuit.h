@@ -60,8 +60,10 @@ struct GenericKey {
 int setup_generic(int a, int n, int b, int circuit, int pub, const uint8_t* toxic, cudaStream_t st, zkvc_pk** pk,
                   zkvc_vk** vk);
 size_t prove_generic_workspace_bytes(const zkvc_pk* pk);
+// y_given: dY holds a claimed Y to prove instead of receiving X W (ZKVC_EUNSAT if the
+// circuit's rows then fail).
 int prove_generic(const zkvc_pk* pk, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host, int32_t* dY, void* ws,
-                  size_t ws_bytes, uint8_t* proof_host, cudaStream_t st);
+                  size_t ws_bytes, uint8_t* proof_host, cudaStream_t st, bool y_given = false);
 // Canonical encodings of query entries by variable index (infinity where the query has
 // no entry); H by position (bit-reversed storage undone), constants at index 0.
 int export_generic(const zkvc_pk* pk, int query, size_t first, size_t count, uint8_t* out);

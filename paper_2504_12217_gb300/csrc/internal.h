@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cstddef>
 #include <cstdint>
 
@@ -31,6 +33,8 @@ int device_sm_count();
 // Y = X W (int8 x int8 -> int32, exact) on the tensor cores (matmul_tc.cu); sets bit 8
 // of *flags if a tensor-core wait timed out.
 int matmul_i8(const int8_t* X, const int8_t* W, int32_t* Y, int a, int n, int b, int* flags, cudaStream_t st);
+// Limit of the matmul's first mbarrier waits for later launches (0: give up at once).
+void set_matmul_first_wait_ns(uint64_t ns);
 
 // Optional stage timers (CUDA events on the launching stream), enabled by
 // zkvc_profile_enable; collected after the synchronising end of a prove call.
@@ -46,6 +50,16 @@ enum ProfStage : int {
   PS_COUNT
 };
 void prof_mark(int stage, bool begin, cudaStream_t st);
+
+// NVTX range over the host-side enqueue of a prover stage ("zkvc/prove/ntt", ...), so that
+// a profiler can select a stage's kernels by range (ncu --nvtx --nvtx-include); free when
+// no tool is attached (NVTX is header-only and loads no library then).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 uint32_t* prof_units(int stage);  // pinned host slot for the stage's unit count, or null
 void prof_collect();
 bool prof_enabled();

@@ -23,9 +23,11 @@
 // the output grid is small, K is split over CTAs that add their exact int32 partial sums
 // into a zeroed Y with atomics.
 //
-// Every wait (the mbarriers of the MMAs) has a time limit; on expiry the kernel sets bit
-// MATMUL_TIMEOUT_FLAG in *flags, waits once more (again bounded) for its MMAs, frees its
-// tensor memory and leaves its part of Y unwritten.
+// Every wait (the mbarriers of the MMAs) has a time limit (first_wait_ns, normally
+// MATMUL_WAIT_NS; 0 makes the first wait give up at once, to exercise this path); on
+// expiry the kernel sets bit MATMUL_TIMEOUT_FLAG in *flags, waits once more for its MMAs
+// with the full MATMUL_WAIT_NS limit, frees its tensor memory and leaves its part of Y
+// unwritten.
 #pragma once
 #include <cstdint>
 
@@ -33,6 +35,7 @@ namespace zkvc {
 
 constexpr int MM_M = 128, MM_N = 64, MM_BK = 64, MM_KPASS = 256, MM_THREADS = 128;
 constexpr int MATMUL_TIMEOUT_FLAG = 8;
+constexpr uint64_t MATMUL_WAIT_NS = 200ull * 1000 * 1000;  // 200 ms
 
 // Dynamic shared memory of a matmul CTA (48 KB of tiles: at most 4 CTAs per SM, so at
 // most 4 x 64 of the 512 tensor-memory columns are held at once).
@@ -168,7 +171,8 @@ __device__ __forceinline__ void mm_fill(const int8_t* __restrict__ X, const int8
 // calls it.  accumulate_y: add into Y with atomics (K split over CTAs; Y zeroed before).
 __device__ __forceinline__ void matmul_tc_tile(const int8_t* __restrict__ X, const int8_t* __restrict__ W,
                                                int32_t* __restrict__ Y, int a, int n, int b, int j0, int i0,
-                                               int kb, int ke, bool accumulate_y, MatmulSmem& sm, int* flags) {
+                                               int kb, int ke, bool accumulate_y, MatmulSmem& sm, int* flags,
+                                               uint64_t first_wait_ns = MATMUL_WAIT_NS) {
   const int t = threadIdx.x, warp = t >> 5;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.taddr)),
@@ -184,7 +188,7 @@ __device__ __forceinline__ void matmul_tc_tile(const int8_t* __restrict__ X, con
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t taddr = sm.taddr;
-  const uint64_t limit = 200ull * 1000 * 1000;  // 200 ms
+  const uint64_t limit = MATMUL_WAIT_NS;
   const bool vec_w = (b % 4 == 0) && (reinterpret_cast<uintptr_t>(W) % 4 == 0);
   const bool vec_x = (n % 16 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
   int acc[MM_N];
@@ -197,7 +201,7 @@ __device__ __forceinline__ void matmul_tc_tile(const int8_t* __restrict__ X, con
   bool ok = true;
   auto wait_stage = [&](int s) {
     if (!pending[s] || !ok) return;  // (after a timeout the cleanup below waits for it)
-    ok = __syncthreads_and(mm_wait(smem_u32(&sm.bar[s]), waits[s] & 1, limit)) != 0;
+    ok = __syncthreads_and(first_wait_ns != 0 && mm_wait(smem_u32(&sm.bar[s]), waits[s] & 1, first_wait_ns)) != 0;
     if (!ok) return;
     waits[s]++;
     pending[s] = false;

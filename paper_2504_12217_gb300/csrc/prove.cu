@@ -23,6 +23,7 @@
 //  7. Affine conversion (one inversion per point, in parallel) and the canonical
 //     256-byte encoding A || B || C.
 #include <algorithm>
+#include <optional>
 #include <mutex>
 #include <new>
 #include <cstring>
@@ -393,9 +394,11 @@ static int fork_to(SideStreams* side, int i, cudaStream_t st) {
 // copies run asynchronously).  glv_host, when given (pinned, chain mode), supplies the
 // GLV halves of s and r as a copy source instead of a split made now: a captured graph
 // then reads whatever the host wrote there before each replay.
+// y_given: dY holds a claimed Y (the caller's) instead of receiving X W; the witness
+// takes it as is and the PSQ check and the quotient check decide whether it is X W.
 static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host,
                               const GlvScalar* glv_host, int32_t* dY, void* ws, size_t ws_bytes, uint8_t* proof_out,
-                              int* flags_out, cudaStream_t st) {
+                              int* flags_out, cudaStream_t st, bool y_given = false) {
   ZK_CHECK(pk && dX && dW && rs_host && dY && ws && proof_out && flags_out, ZKVC_EINVAL, "prove: null argument");
   ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN, ZKVC_EINVAL, "prove: mode %d", mode);
   size_t need = prove_workspace_bytes(pk, mode);
@@ -410,6 +413,9 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
   Fr* Cev = B.ev + 2 * N;
   Fr* Hev = B.ev + 3 * N;
 
+  NvtxRange nv_prove("zkvc/prove");
+  std::optional<NvtxRange> nv_stage;
+  nv_stage.emplace("zkvc/prove/witness");
   prof_mark(PS_WITNESS, true, st);
   ZK_CUDA(cudaMemsetAsync(B.flags, 0, 4 * sizeof(int), st));
   ZK_CUDA(cudaMemcpyAsync(B.rs, rs_host, 64, cudaMemcpyHostToDevice, st));
@@ -425,8 +431,8 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
   ZK_TRY(side_streams(&side));
   Plans P;
   plans(pk, mode, dX, dY, B.ak, B.bk, B.S, Hev, B.rs, B.sw, B.sa, B.rb, &P);
-  // 1. Y = X W (tensor cores);  2. the CRPC sums a_k, b_k
-  ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
+  // 1. Y = X W (tensor cores), unless a claimed Y is given;  2. the CRPC sums a_k, b_k
+  if (!y_given) ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
   k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   // The side streams may start at these points of the main stream (the events are
@@ -452,6 +458,8 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
   // 5-6. quotient and the H part of C on side stream 3 (the critical chain)
   ZK_TRY(fork_to(side, 3, st));
   cudaStream_t s3 = side->st[3];
+  nv_stage.reset();
+  nv_stage.emplace("zkvc/prove/ntt");
   prof_mark(PS_NTT, true, s3);
   const NttDomain* d = pk->dom;
   const int elog = pk->prove_tune[4] ? (int)pk->prove_tune[4] : 10;
@@ -461,6 +469,8 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
   prof_mark(PS_NTT, false, s3);
   ZK_CUDA(cudaEventRecord(side->ntt_done, s3));
   // the H MSM is the largest G1 run (N 16-bit digits): its stage and accumulation timers
+  nv_stage.reset();
+  nv_stage.emplace("zkvc/prove/msm_h");
   prof_mark(PS_MSM_G1, true, s3);
   ZK_TRY(msm_run<Fp>(P.h, pk->g1, B.ws_h, B.ws_h_bytes, B.res_h, s3, PS_ACCUM_G1, side->h_accum));
   prof_mark(PS_MSM_G1, false, s3);
@@ -469,6 +479,8 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
   // encoding of B
   ZK_CUDA(cudaStreamWaitEvent(side->st[0], side->fork[0], 0));
   if (pk->prove_tune[7] == 1) ZK_CUDA(cudaStreamWaitEvent(side->st[0], side->ntt_done, 0));
+  nv_stage.reset();
+  nv_stage.emplace("zkvc/prove/msm_g2");
   prof_mark(PS_MSM_G2, true, side->st[0]);
   ZK_TRY(msm_run<Fp2>(P.g2, pk->g2, B.ws2, B.ws2_bytes, B.res2, side->st[0], PS_ACCUM_G2));
   k_encode_b<<<1, 32, 0, side->st[0]>>>(B.res2, B.proof); ZK_COUNT_LAUNCH();
@@ -481,6 +493,8 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
   ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->fork[1], 0));
   if (chain && pk->prove_tune[5] == 1) ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->ntt_done, 0));
   if (chain && pk->prove_tune[5] == 2) ZK_CUDA(cudaStreamWaitEvent(side->st[1], side->h_accum, 0));
+  nv_stage.reset();
+  nv_stage.emplace("zkvc/prove/msm_small");
   prof_mark(PS_MSM_SMALL, true, side->st[1]);
   ZK_TRY(msm_run<Fp>(P.small, pk->g1, B.ws_small, B.ws_small_bytes, B.res_small, side->st[1]));
   if (chain) {
@@ -508,6 +522,8 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
     ZK_CUDA(cudaStreamWaitEvent(st, side->join[i], 0));
   }
   // 7. encode
+  nv_stage.reset();
+  nv_stage.emplace("zkvc/prove/encode");
   prof_mark(PS_COMBINE, true, st);
   k_encode_c<<<1, 32, 0, st>>>(B.cpart, B.res_h, B.proof); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
@@ -529,6 +545,17 @@ int prove_status(int flags) {
   ZK_CHECK(!(flags & 1), ZKVC_EUNSAT, "prove: the PSQ chain does not close against Y(z)");
   ZK_CHECK(!(flags & 2), ZKVC_EUNSAT, "prove: the quotient has degree N - 1 (QAP not satisfied)");
   return ZKVC_OK;
+}
+
+// A proof for a claimed Y (device memory, read only): direct enqueue, no graph.
+int prove_claimed(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host,
+                  const int32_t* dY, void* ws, size_t ws_bytes, uint8_t* proof_host, cudaStream_t st) {
+  int flags = 0;
+  ZK_TRY(prove_enqueue_impl(pk, mode, dX, dW, rs_host, nullptr, const_cast<int32_t*>(dY), ws, ws_bytes, proof_host,
+                            &flags, st, true));
+  ZK_CUDA(cudaStreamSynchronize(st));
+  prof_collect();
+  return prove_status(flags);
 }
 
 int prove_impl(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host, int32_t* dY,

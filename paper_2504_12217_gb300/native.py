@@ -89,6 +89,8 @@ SIGNATURES = {
     "zkvc_batch_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
     "zkvc_prove_batch": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_int, _c_p, _c_p, _c_p, _c_p]),
     "zkvc_set_wait_timeout_ms": (_c_int, [_c_int]),
+    "zkvc_set_device_wait_limit_ns": (_c_int, [ctypes.c_uint64]),
+    "zkvc_prove_claimed": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_verify_batch": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_int, _c_p, _c_p]),
     "zkvc_pairing": (_c_int, [_c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_server_create": (_c_int, [_c_p, _c_int, _c_int, _c_sz, _c_int, ctypes.POINTER(_c_p)]),
@@ -574,6 +576,27 @@ def zkvc_prove(pk, X, W, rs, Y=None, workspace=None):
     return proof.raw, Y
 
 
+def zkvc_prove_claimed(pk, X, W, Y_claimed, rs, workspace=None):
+    """Prove a claimed product: Y_claimed ([a, b] int32 CUDA tensor) enters the witness as
+    it is; raises ZkvcError(ZKVC_EUNSAT) if it is not X W.  Returns the proof bytes."""
+    torch = _torch()
+    a, n, b = pk.shape
+    if X.dtype != torch.int8 or tuple(X.shape) != (a, n) or W.dtype != torch.int8 or tuple(W.shape) != (n, b):
+        raise ValueError(f"expected X int8 [{a}, {n}] and W int8 [{n}, {b}]")
+    if Y_claimed.dtype != torch.int32 or tuple(Y_claimed.shape) != (a, b):
+        raise ValueError(f"expected Y int32 [{a}, {b}]")
+    if len(rs) != 64:
+        raise ValueError("rs must be 64 bytes")
+    need = zkvc_prove_workspace_bytes(pk)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=X.device)
+    proof = ctypes.create_string_buffer(256)
+    rsb = ctypes.create_string_buffer(bytes(rs), 64)
+    check(lib().zkvc_prove_claimed(pk.handle, _dev_ptr(X), _dev_ptr(W), _dev_ptr(Y_claimed), rsb, _dev_ptr(workspace),
+                                   workspace.numel(), proof, _stream()))
+    return proof.raw
+
+
 # ------------------------------------------------------------------ batched proving
 ZKVC_BATCH_AUTOTUNE = 1
 ZKVC_BATCH_EAGER = 2
@@ -584,6 +607,11 @@ TUNING_NAMES = ("small_chunk", "small_accum_threads", "main_chunk", "main_accum_
 
 def zkvc_set_wait_timeout_ms(ms):
     check(lib().zkvc_set_wait_timeout_ms(int(ms)))
+
+
+def zkvc_set_device_wait_limit_ns(ns):
+    """Limit of the tensor-core matmul's first waits (0: give up at once; default 200 ms)."""
+    check(lib().zkvc_set_device_wait_limit_ns(int(ns)))
 
 
 def _ptr_array(ptrs):
