@@ -23,6 +23,7 @@
 // windows share one bucket set and no doubling chain follows; variable-base MSMs keep
 // one bucket set per window and combine windows by Horner's rule.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -104,6 +105,10 @@ size_t scan_u32_temp_bytes(size_t n) {
 }
 
 // ------------------------------------------------------------------ planning
+// Threads of the G1 accumulation kernel resident on the whole GPU at `at` threads per
+// block (one per chunk), from the occupancy of its register use; cached per block size.
+static uint64_t accum_resident_threads(uint32_t at);
+
 int msm_plan_finalize(MsmPlan& p) {
   uint32_t key = 0;
   for (auto& o : p.outs) {
@@ -145,15 +150,20 @@ int msm_plan_finalize(MsmPlan& p) {
     p.max_nd = std::max(p.max_nd, nd);
   }
   ZK_CHECK(slot < 0xffffffffull, ZKVC_EINVAL, "msm: too many digit slots");
-  // default chunk: about two chunks per bucket (serial sums keep every lane busy, while
-  // the fold tree loses half its lanes per level), but at least ~40 k chunks so that the
-  // accumulation fills the GPU, and 16 at the least
+  // default chunk: about two chunks per bucket, but at least ~40 k chunks so that the
+  // accumulation fills the GPU, and 16 at the least; and at least the chunk that puts
+  // every term into one wave of resident accumulation threads (the chunks are balanced,
+  // so a second, partial wave would only add a tail)
   if (p.tune.chunk) {
     p.chunk = p.tune.chunk;
   } else {
     const uint64_t per_bucket = slot / (2ull * std::max<uint32_t>(key, 1u));
     const uint64_t fill = slot / 40960ull;
-    p.chunk = (uint32_t)std::max<uint64_t>(16, std::min<uint64_t>(std::min(per_bucket, fill), 1024));
+    // (7/8 of the resident threads: the prover's other streams hold some SM slots)
+    const uint64_t resident = accum_resident_threads(p.tune.accum_threads) * 7 / 8;
+    const uint64_t one_wave = resident ? (slot + resident - 1) / resident : 0;
+    p.chunk = (uint32_t)std::min<uint64_t>(
+        std::max<uint64_t>(std::max<uint64_t>(16, std::min(per_bucket, fill)), one_wave), 1024);
   }
   ZK_CHECK(p.chunk >= 1 && p.chunk <= 1024, ZKVC_EINVAL, "msm: chunk of %u terms", p.chunk);
   ZK_CHECK(p.tune.accum_threads >= 32 && p.tune.accum_threads <= 256 && p.tune.accum_threads % 32 == 0,
@@ -511,6 +521,20 @@ __global__ void __launch_bounds__(128) k_fold_serial(const uint32_t* __restrict_
       acc = p_add(acc, o);
   }
   if (QL == 1 || quad_lane() == 0) st_field(part + base, acc);
+}
+
+static uint64_t accum_resident_threads(uint32_t at) {
+  static std::atomic<int> per_sm[9];
+  if (at < 32 || at > 256 || at % 32) return 0;
+  int nb = per_sm[at / 32].load(std::memory_order_relaxed);
+  if (nb <= 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_accum0<Fp, 1>, (int)at, 0) != cudaSuccess || nb <= 0) {
+      cudaGetLastError();
+      return 0;
+    }
+    per_sm[at / 32].store(nb, std::memory_order_relaxed);
+  }
+  return uint64_t(nb) * at * (uint64_t)device_sm_count();
 }
 
 // The partial sums of each bucket (its np = nch[k] slots from choff[k]) are added along
