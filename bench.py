@@ -641,9 +641,9 @@ def run_gpu(args):
 
 
 # DRAM bytes (read + write) of one H-query accumulation launch of the [49,320]x[320,512]
-# proof, from one ncu capture per chunk setting (dram__bytes_read.sum +
-# dram__bytes_write.sum); keyed by the H run's chunk tuning
-H_ACCUM_TRAFFIC = {0: 75253248, 16: 75253248, 32: 74893568, 64: 74598400}
+# proof, from one ncu capture of the balanced accumulation with the default chunk rule
+# (dram__bytes_read.sum + dram__bytes_write.sum); other chunk settings: not captured
+H_ACCUM_TRAFFIC = {0: 76026112}
 
 
 # ------------------------------------------------------------------ batched workload
