@@ -655,14 +655,34 @@ __device__ XYZZ<F> block_sum(Get get, uint32_t m, XYZZ<F>* sh) {
 // Window result sum_{v=1}^{NB} v B_v = sum_b 2^b U_b with U_b = sum_{v : bit b of v} B_v.
 // One BitSeg per (output, window, bit); its cnt buckets are cut into slices, each summed
 // by one block (serial sums per thread first, then the block's tree).
+//
+// Large fixed-base windows (c >= SPLIT_MIN_C, one window per output) first split every
+// bucket index as v = 2^h hi + lo: sum_v v B_v = sum_lo lo C_lo + 2^h sum_hi hi D_hi with
+// C_lo = sum_{v : low h bits = lo} B_v and D_hi = sum_{v : v >> h = hi} B_v (each bucket
+// added twice, by k_split_gather), and the bit decomposition then runs over the two small
+// "pseudo-bucket" sets: lo in [1, 2^h) with bits 0 .. h-1, hi in [1, 2^(c-1-h)] with bits
+// 0 .. c-1-h whose terms are doubled b + h times.  For c = 16: 2 x 32 k additions to
+// gather and 1.5 k for the bits, instead of 246 k for the bits alone.
+constexpr uint32_t SPLIT_MIN_C = 12;
+constexpr uint32_t BS_PSEUDO = 0x100;  // BitSeg::mode: key0 indexes the pseudo-bucket array
 struct BitSeg {
-  uint32_t key0;    // key of bucket v = 1 of this (output, window)
-  uint32_t b, c;    // bit, window bits
+  uint32_t key0;    // key of bucket v = 1 of this (output, window), or of pseudo-bucket 1
+  uint32_t b, c;    // bit, window bits (of the pseudo set for pseudo-buckets)
   uint32_t cnt;     // buckets with bit b
   uint32_t soff;    // first slice in the slice-sum buffer
   uint32_t nsl;     // slices
-  uint32_t dslot;   // slot of 2^b U_b in the D buffer
-  uint32_t pad;
+  uint32_t dslot;   // slot of 2^shift U_b in the D buffer
+  uint32_t mode;    // bits 0-7: shift (doublings of U_b); BS_PSEUDO
+};
+
+// One split window: the pseudo-buckets C_1 .. C_(2^h - 1) then D_1 .. D_(2^(c-1-h)) at
+// P[pbase ...], one k_split_gather block each, blocks blk0 ...
+struct SplitWin {
+  uint32_t key0;  // key of bucket v = 1
+  uint32_t c, h;
+  uint32_t pbase;
+  uint32_t blk0;
+  uint32_t pad[3];
 };
 
 __device__ __forceinline__ uint32_t nth_with_bit(uint32_t b, uint32_t c, uint32_t idx) {
@@ -685,7 +705,8 @@ __global__ void __launch_bounds__(SliceBT<F>::value) k_bits_slices(const XYZZ<F>
                                                                     const uint32_t* __restrict__ counts,
                                                                     const uint32_t* __restrict__ choff,
                                                                     const BitSeg* __restrict__ segs, uint32_t nseg,
-                                                                    uint32_t slice, XYZZ<F>* S) {
+                                                                    uint32_t slice, const XYZZ<F>* __restrict__ P,
+                                                                    XYZZ<F>* S) {
   constexpr int BT = SliceBT<F>::value;
   __shared__ XYZZ<F> sh[BT];
   const uint32_t sl = blockIdx.x;
@@ -697,9 +718,45 @@ __global__ void __launch_bounds__(SliceBT<F>::value) k_bits_slices(const XYZZ<F>
   const BitSeg g = segs[lo];
   const uint32_t first = (sl - g.soff) * slice;
   const uint32_t m = min(slice, g.cnt - first);
-  auto get = [&](uint32_t i) { return bucket_at(fin, counts, choff, g.key0 + nth_with_bit(g.b, g.c, first + i) - 1); };
+  const bool pseudo = (g.mode & BS_PSEUDO) != 0;
+  auto get = [&](uint32_t i) {
+    const uint32_t v = nth_with_bit(g.b, g.c, first + i);
+    return pseudo ? ld_field(P + g.key0 + v - 1) : bucket_at(fin, counts, choff, g.key0 + v - 1);
+  };
   const XYZZ<F> r = block_sum<F, BT>(get, m, sh);
   if (threadIdx.x == 0) st_field(S + sl, r);
+}
+
+// block per pseudo-bucket of a split window: C_lo (members v = 2^h hi + lo, hi <
+// 2^(c-1-h)) or D_hi (members v = 2^h hi + lo, lo < 2^h, v <= 2^(c-1))
+template <class F>
+__global__ void __launch_bounds__(SliceBT<F>::value) k_split_gather(const XYZZ<F>* __restrict__ fin,
+                                                                     const uint32_t* __restrict__ counts,
+                                                                     const uint32_t* __restrict__ choff,
+                                                                     const SplitWin* __restrict__ wins, uint32_t nwin,
+                                                                     XYZZ<F>* P) {
+  constexpr int BT = SliceBT<F>::value;
+  __shared__ XYZZ<F> sh[BT];
+  uint32_t lo = 0, hi = nwin - 1;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi + 1) >> 1;
+    if (wins[mid].blk0 <= blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const SplitWin g = wins[lo];
+  const uint32_t cls = blockIdx.x - g.blk0, nlo = (1u << g.h) - 1u, nb = 1u << (g.c - 1);
+  uint32_t m, step, first;
+  if (cls < nlo) {  // C_(cls + 1)
+    first = cls + 1;
+    step = 1u << g.h;
+    m = 1u << (g.c - 1 - g.h);
+  } else {          // D_(cls - nlo + 1)
+    first = (cls - nlo + 1) << g.h;
+    step = 1;
+    m = min(1u << g.h, nb - first + 1);
+  }
+  auto get = [&](uint32_t i) { return bucket_at(fin, counts, choff, g.key0 + first + i * step - 1); };
+  const XYZZ<F> r = block_sum<F, BT>(get, m, sh);
+  if (threadIdx.x == 0) st_field(P + g.pbase + cls, r);
 }
 
 // block per bit: U_b = the sum of the bit's slices, then 2^b U_b by b doublings (G1: one
@@ -719,11 +776,13 @@ __global__ void __launch_bounds__(BITS_BT) k_bits_scale(const XYZZ<F>* __restric
     __syncthreads();
     if (threadIdx.x >= 32) return;
     SlG1 y = sl_ld(&xs);
-    for (uint32_t i = 0; i < g.b; i++) y = sl_pdbl(y);
+    const uint32_t shift = g.mode & 0xffu;
+    for (uint32_t i = 0; i < shift; i++) y = sl_pdbl(y);
     sl_st(D + g.dslot, y);
   } else {
     if (threadIdx.x >= 4) return;
-    for (uint32_t i = 0; i < g.b; i++) x = p_dbl_quad(x);
+    const uint32_t shift = g.mode & 0xffu;
+    for (uint32_t i = 0; i < shift; i++) x = p_dbl_quad(x);
     if (threadIdx.x == 0) st_field(D + g.dslot, x);
   }
 }
@@ -775,7 +834,9 @@ struct Layout {
   BitSeg* bsegs;
   TreeSeg* dseg;
   OutItem* oitems;
-  uint32_t qmax, nbits, nslices, dtotal, slice;
+  SplitWin* swins;
+  void* P;  // pseudo-buckets of the split windows
+  uint32_t qmax, nbits, nslices, dtotal, slice, nswin, ngather, npseudo;
 };
 
 struct HostTables {
@@ -783,6 +844,7 @@ struct HostTables {
   std::vector<TreeSeg> dsegs;
   std::vector<OutItem> oitems;
   std::vector<const void*> obases;
+  std::vector<SplitWin> swins;
 };
 
 struct MsmExecState {
@@ -797,9 +859,18 @@ MsmExec::~MsmExec() { delete st; }
 // Slices of bt * r buckets, r >= 2 chosen so that the slice kernel fills about one wave
 // of `wave` blocks (a lone wave's blocks each run their tree once; more buckets per
 // slice are serial sums, which the SMs run at full rate).
+static bool split_window(const MsmOut& o) { return o.win_keys == 1 && o.c >= SPLIT_MIN_C; }
+
+// additions of the bit decomposition of one window of c bits (plain or split)
+static uint64_t bit_work(const MsmOut& o) {
+  if (!split_window(o)) return (o.c - 1) * (1ull << (o.c - 2)) + 1;
+  const uint32_t h = o.c / 2, ch = o.c - h;
+  return uint64_t(h) * (1ull << (h - 1)) + (ch - 1) * (1ull << (ch - 2)) + 1;
+}
+
 static void tables(const MsmPlan& p, uint32_t bt, uint32_t wave, HostTables& h, Layout& L) {
   uint64_t total = 0;
-  for (const auto& o : p.outs) total += uint64_t(o.win_keys) * ((o.c - 1) * (1ull << (o.c - 2)) + 1);
+  for (const auto& o : p.outs) total += uint64_t(o.win_keys) * bit_work(o);
   uint64_t r = (total + uint64_t(bt) * wave - 1) / (uint64_t(bt) * wave);
   r = std::min<uint64_t>(std::max<uint64_t>(r, 2), 64);
   const uint32_t slice = (uint32_t)(bt * r);
@@ -808,18 +879,35 @@ static void tables(const MsmPlan& p, uint32_t bt, uint32_t wave, HostTables& h, 
   h.dsegs.clear();
   h.oitems.clear();
   h.obases.clear();
-  uint32_t soff = 0, dslot = 0;
+  h.swins.clear();
+  uint32_t soff = 0, dslot = 0, pbase = 0, blk = 0;
+  auto add_bits = [&](uint32_t key0, uint32_t c, uint32_t b_from, uint32_t b_to, uint32_t shift0, uint32_t slot0,
+                      uint32_t mode) {
+    for (uint32_t b = b_from; b < b_to; b++) {
+      const uint32_t cnt = (b == c - 1) ? 1u : (1u << (c - 2));
+      const uint32_t nsl = (cnt + slice - 1) / slice;
+      h.bsegs.push_back({key0, b, c, cnt, soff, nsl, slot0 + b - b_from, mode | (shift0 + b)});
+      soff += nsl;
+    }
+  };
   for (const auto& o : p.outs) {
     const uint32_t nb = 1u << (o.c - 1);
     h.oitems.push_back({dslot, o.c, o.win_keys, o.c});
     h.obases.push_back(o.bases);
     for (uint32_t w = 0; w < o.win_keys; w++) {
       h.dsegs.push_back({dslot, o.c});
-      for (uint32_t b = 0; b < o.c; b++) {
-        const uint32_t cnt = (b == o.c - 1) ? 1u : (1u << (o.c - 2));
-        const uint32_t nsl = (cnt + slice - 1) / slice;
-        h.bsegs.push_back({o.key_off + w * nb, b, o.c, cnt, soff, nsl, dslot + b, 0});
-        soff += nsl;
+      const uint32_t key0 = o.key_off + w * nb;
+      if (split_window(o)) {
+        // lo in [1, 2^h): bits 0 .. h-1 of a (h+1)-bit set; hi in [1, 2^(c-1-h)]: bits
+        // 0 .. c-h-1 of a (c-h)-bit set, doubled h more times; c slots in all
+        const uint32_t hh = o.c / 2, nlo = (1u << hh) - 1u, nhi = 1u << (o.c - 1 - hh);
+        h.swins.push_back({key0, o.c, hh, pbase, blk, {0, 0, 0}});
+        add_bits(pbase, hh + 1, 0, hh, 0, dslot, BS_PSEUDO);
+        add_bits(pbase + nlo, o.c - hh, 0, o.c - hh, hh, dslot + hh, BS_PSEUDO);
+        pbase += nlo + nhi;
+        blk += nlo + nhi;
+      } else {
+        add_bits(key0, o.c, 0, o.c, 0, dslot, 0);
       }
       dslot += o.c;
     }
@@ -827,6 +915,9 @@ static void tables(const MsmPlan& p, uint32_t bt, uint32_t wave, HostTables& h, 
   L.nbits = (uint32_t)h.bsegs.size();
   L.nslices = soff;
   L.dtotal = dslot;
+  L.nswin = (uint32_t)h.swins.size();
+  L.ngather = blk;
+  L.npseudo = pbase;
 }
 
 template <class F>
@@ -854,6 +945,8 @@ static void layout(const MsmPlan& p, Arena& a, Layout& L, HostTables& h) {
   L.bsegs = a.take<BitSeg>(h.bsegs.size());
   L.dseg = a.take<TreeSeg>(h.dsegs.size());
   L.oitems = a.take<OutItem>(h.oitems.size());
+  L.swins = a.take<SplitWin>(h.swins.size());
+  L.P = a.take<XYZZ<F>>(L.npseudo);
 }
 
 template <class F>
@@ -895,7 +988,7 @@ void msm_table_stage(uint8_t* host, size_t cap) {
   t_stage_off = 0;
 }
 
-// The tables are carved one after another (segs, outs, obases, bsegs, dseg, oitems), so
+// The tables are carved one after another (segs, outs, obases, bsegs, dseg, oitems, swins), so
 // one image of their span, with each table at its device offset, goes up in one copy.
 int msm_upload(MsmExec* ex, cudaStream_t st) {
   ZK_CHECK(ex && ex->st, ZKVC_EINVAL, "msm: exec not prepared");
@@ -903,7 +996,8 @@ int msm_upload(MsmExec* ex, cudaStream_t st) {
   Layout& L = ex->st->L;
   HostTables& h = ex->st->h;
   uint8_t* const dev0 = reinterpret_cast<uint8_t*>(L.segs);
-  uint8_t* const dev1 = reinterpret_cast<uint8_t*>(L.oitems) + h.oitems.size() * sizeof(OutItem);
+  uint8_t* const dev1 = h.swins.empty() ? reinterpret_cast<uint8_t*>(L.oitems) + h.oitems.size() * sizeof(OutItem)
+                                        : reinterpret_cast<uint8_t*>(L.swins) + h.swins.size() * sizeof(SplitWin);
   ZK_CHECK(dev0 && dev1 > dev0, ZKVC_EINVAL, "msm: tables not carved");
   const size_t span = size_t(dev1 - dev0);
   std::vector<uint8_t> tmp;
@@ -929,7 +1023,8 @@ int msm_upload(MsmExec* ex, cudaStream_t st) {
                   put(L.obases, h.obases.data(), h.obases.size() * sizeof(void*)) &&
                   put(L.bsegs, h.bsegs.data(), h.bsegs.size() * sizeof(BitSeg)) &&
                   put(L.dseg, h.dsegs.data(), h.dsegs.size() * sizeof(TreeSeg)) &&
-                  put(L.oitems, h.oitems.data(), h.oitems.size() * sizeof(OutItem));
+                  put(L.oitems, h.oitems.data(), h.oitems.size() * sizeof(OutItem)) &&
+                  put(L.swins, h.swins.data(), h.swins.size() * sizeof(SplitWin));
   ZK_CHECK(ok, ZKVC_EINVAL, "msm: tables outside their span");
   ZK_CUDA(cudaMemcpyAsync(dev0, img, span, cudaMemcpyHostToDevice, st));
   ex->st->uploaded = true;
@@ -1009,7 +1104,13 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   // sum_v v B_v per (output, window) by bit decomposition
   XYZZ<F>* Sl = reinterpret_cast<XYZZ<F>*>(L.S);
   XYZZ<F>* D = reinterpret_cast<XYZZ<F>*>(L.D);
-  k_bits_slices<F><<<L.nslices, SliceBT<F>::value, 0, st>>>(part, L.counts, L.choff, L.bsegs, L.nbits, L.slice, Sl);
+  XYZZ<F>* Pb = reinterpret_cast<XYZZ<F>*>(L.P);
+  if (L.ngather) {
+    k_split_gather<F><<<L.ngather, SliceBT<F>::value, 0, st>>>(part, L.counts, L.choff, L.swins, L.nswin, Pb);
+    ZK_COUNT_LAUNCH();
+  }
+  k_bits_slices<F><<<L.nslices, SliceBT<F>::value, 0, st>>>(part, L.counts, L.choff, L.bsegs, L.nbits, L.slice, Pb,
+                                                             Sl);
   ZK_COUNT_LAUNCH();
   k_bits_scale<F><<<L.nbits, BITS_BT, 0, st>>>(Sl, L.bsegs, D); ZK_COUNT_LAUNCH();
   k_bits_window<F><<<(unsigned)h.dsegs.size(), BITS_BT, 0, st>>>(D, L.dseg); ZK_COUNT_LAUNCH();
