@@ -403,6 +403,52 @@ def ntt_roofline(nv, prof, log_n_proof, imad_peak, hbm_peak, hbm_src):
     return out
 
 
+def msm_sweep_section(nv, imad_peak):
+    """Variable-base MSMs of the kernel sweep inside the default line: G1 at 2^20 and 2^24
+    points, G2 at 2^20, uniform Fr scalars, points = generator x uniform scalars (made by
+    the library's fixed-base kernel, untimed).  Fractions of the integer peak with the
+    method's work: N ceil(254/c) mixed additions + 2^c ceil(254/c) full additions for the
+    bucket sums (c = the library's window rule, 16 at these sizes)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(0x5A4B5643_00000003)
+
+    def rand_fr(n):
+        t = torch.randint(0, 256, (n, 32), dtype=torch.uint8, device="cuda", generator=g)
+        t[:, 31] &= 0x0F
+        return t
+
+    out = []
+    for group, logn in ((1, 20), (1, 24), (2, 20)):
+        n = 1 << logn
+        k = rand_fr(n)
+        pts = nv.zkvc_g1_generator_mul(k) if group == 1 else nv.zkvc_g2_generator_mul(k)
+        del k
+        sc = rand_fr(n)
+        ws = torch.empty(nv.zkvc_msm_workspace_bytes(n, group), dtype=torch.uint8, device="cuda")
+        fn = (lambda: nv.zkvc_msm_g1(pts, sc, ws)) if group == 1 else (lambda: nv.zkvc_msm_g2(pts, sc, ws))
+        fn()
+        torch.cuda.synchronize()
+        reps = 3 if logn < 24 else 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        c = min(16, max(4, logn - 3))
+        win = -(-254 // c)
+        madd = G1_MADD_PRODUCTS if group == 1 else G2_MADD_PRODUCTS
+        add = 14 if group == 1 else 42
+        work = (n * win * madd + (1 << c) * win * add) * MONT_IMAD
+        out.append({"group": f"G{group}", "log_n": logn, "ms": ms, "mpoints_per_s": n / ms / 1e3,
+                    "imad_frac": work / (ms / 1e3) / imad_peak, "window_bits": c})
+        del pts, sc, ws
+        torch.cuda.empty_cache()
+    return {"msms": out, "note": "each call synchronises and reads its result back (zkvc_msm_g1/g2); "
+                                  "inputs larger than L2 at 2^24 (1.5 GB)"}
+
+
 def run_sweep(args):
     """NTT / INTT / coset NTT at 2^16..2^24 and G1 (2^16..2^24) / G2 (2^16..2^20) MSMs on
     uniform random Fr data, points = generator x seeded random scalars.  One JSON line."""
@@ -607,6 +653,7 @@ def run_gpu(args):
     stages = {k: round(v["ms"] / max(v["calls"], 1), 4) for k, v in prof.items()}
     spans = {k: [round(v["start_ms"], 4), round(v["end_ms"], 4)] for k, v in prof.items() if v["calls"]}
     nttr = ntt_roofline(nv, prof, 16, imad["imad_per_s"], hbm, hbm_src)
+    msweep = msm_sweep_section(nv, imad["imad_per_s"]) if not args.no_msm_sweep else None
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -628,7 +675,7 @@ def run_gpu(args):
                    "chunk_source": "imposed (--key-tuning)" if args.key_tuning else
                    "default rule" if args.no_autotune else "zkvc_pk_autotune at setup"},
         "latency_ms": {"p50": statistics.median(step_ms), "p99": p99_of(step_ms), "min": srt[0], "max": srt[-1]},
-        "e2e": e2e, "roofline": roofline, "ntt_roofline": nttr, "imad_peak": imad,
+        "e2e": e2e, "roofline": roofline, "ntt_roofline": nttr, "msm_sweep": msweep, "imad_peak": imad,
         "batched": batched, "served": served, "cpu_baseline": cpu, "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps, "clocks": clk, "stage_ms": stages,
         "stage_span_ms": spans,
@@ -1136,6 +1183,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=0, help="batched: only the K smallest instances")
     ap.add_argument("--no-batched", action="store_true", help="plain: leave the batched section out of the line")
     ap.add_argument("--no-served", action="store_true", help="plain: leave the served section out of the line")
+    ap.add_argument("--no-msm-sweep", action="store_true", help="plain: leave the MSM sweep points out of the line")
     ap.add_argument("--served-rates", type=float, nargs="*", default=[50, 200, 1000],
                     help="plain: offered rates of the served section (the last above saturation)")
     ap.add_argument("--served-seconds", type=float, default=3.0, help="plain: seconds of arrivals per served rate")
