@@ -79,13 +79,15 @@ int zkvc_profile_span(int stage, double* start_ms, double* end_ms);
  * 264 of a CIOS product.  form 0: sixteen independent mad.lo.u32 chains per thread;
  * 1: the CIOS row of the field code (a carry chain of eight mad.lo and eight mad.hi);
  * 2: sixteen independent mad.hi.u32 chains; 3: eight independent mad.wide.u32 chains
- * (64-bit accumulators); 4: two carry chains of eight mad.lo; 5 and 6: two independent
- * chains of whole Fp Montgomery products per thread (264 IMADs each), 5 with the inlined
- * carry-chain product, 6 with the out-of-line 64-bit-accumulator product of the point
- * formulas.  A full-occupancy grid over every SM runs `iters` iterations (16 IMADs per
+ * (64-bit accumulators); 4: two carry chains of eight mad.lo; 5 to 8: two independent
+ * chains of whole Fp Montgomery products per thread (264 IMADs each): 5 CIOS with
+ * carry-chain rows, 6 CIOS with 64-bit accumulators, 7 product scanning with 96-bit
+ * column accumulators in mad.lo.cc / madc.hi.cc (the product the kernels use), 8 the same
+ * with mul.wide and additions; each checked against the CIOS product on every thread
+ * (ZKVC_ECUDA if any result differs).  A full-occupancy grid over every SM runs `iters` iterations (16 IMADs per
  * thread for forms 0 .. 4), once untimed (iters / 8) and once timed with CUDA events on
  * `stream`; the call synchronises.  Outputs (any may be null): IMADs per second, the
- * timed launch in ms and the SM count used.  ZKVC_EINVAL for a form outside 0 .. 6 or
+ * timed launch in ms and the SM count used.  ZKVC_EINVAL for a form outside 0 .. 8 or
  * iters outside [1, 2^24].
  */
 int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int* sms, void* stream);

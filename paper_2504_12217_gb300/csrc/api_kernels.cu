@@ -333,6 +333,64 @@ __global__ void __launch_bounds__(256) k_imad_rate(uint32_t iters, uint32_t seed
   if (acc == 0x12345678u) sink[0] = acc;
 }
 
+// Product-scanning Montgomery multiplication (finely integrated: every column sums its
+// a_j b_(i-j) and m_j p_(i-j) terms into a 96-bit accumulator, and the low word of column
+// i < 8 yields m_i), written out for the throughput comparison of zkvc_imad_rate: WIDE = 0
+// accumulates with mad.lo.cc / madc.hi.cc / addc (the field code's f_mul), WIDE = 1 (form
+// 8) with one 64-bit product (mul.wide) and three additions.
+template <int WIDE>
+__device__ __forceinline__ void col_acc(uint32_t& t0, uint32_t& t1, uint32_t& t2, uint32_t x, uint32_t y) {
+  if constexpr (WIDE) {
+    const uint64_t p = (uint64_t)x * y;
+    asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.u32 %2, %2, 0;"
+        : "+r"(t0), "+r"(t1), "+r"(t2)
+        : "r"((uint32_t)p), "r"((uint32_t)(p >> 32)));
+  } else {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\tmadc.hi.cc.u32 %1, %3, %4, %1;\n\taddc.u32 %2, %2, 0;"
+        : "+r"(t0), "+r"(t1), "+r"(t2)
+        : "r"(x), "r"(y));
+  }
+}
+
+template <int WIDE>
+__device__ __forceinline__ Fp f_mul_fips(const Fp& a, const Fp& b) {
+  uint32_t m[8], r[8];
+  uint32_t t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+#pragma unroll
+    for (int j = 0; j < i; j++) {
+      col_acc<WIDE>(t0, t1, t2, a.v[j], b.v[i - j]);
+      col_acc<WIDE>(t0, t1, t2, m[j], mod_limb<FpCfg>(i - j));
+    }
+    col_acc<WIDE>(t0, t1, t2, a.v[i], b.v[0]);
+    m[i] = t0 * FpCfg::INV;
+    col_acc<WIDE>(t0, t1, t2, m[i], mod_limb<FpCfg>(0));
+    t0 = t1;
+    t1 = t2;
+    t2 = 0;
+  }
+#pragma unroll
+  for (int i = 8; i < 15; i++) {
+#pragma unroll
+    for (int j = i - 7; j < 8; j++) {
+      col_acc<WIDE>(t0, t1, t2, a.v[j], b.v[i - j]);
+      col_acc<WIDE>(t0, t1, t2, m[j], mod_limb<FpCfg>(i - j));
+    }
+    r[i - 8] = t0;
+    t0 = t1;
+    t1 = t2;
+    t2 = 0;
+  }
+  r[7] = t0;  // the value r < 2p < 2^255: no word beyond
+  Fp x, d;
+#pragma unroll
+  for (int i = 0; i < 8; i++) x.v[i] = r[i];
+  const Fp mm = Fp::modulus();
+  const uint32_t br = sub8(d.v, x.v, mm.v);
+  return br ? x : d;
+}
+
 template <int FORM>
 __global__ void __launch_bounds__(256) k_mont_rate(uint32_t iters, uint32_t seed, uint32_t* sink) {
   const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -342,13 +400,26 @@ __global__ void __launch_bounds__(256) k_mont_rate(uint32_t iters, uint32_t seed
   m.v[2] ^= seed;
   for (uint32_t it = 0; it < iters; it++) {
     if constexpr (FORM == 5) {
+      a = f_mul_cios(a, m);
+      b = f_mul_cios(b, m);
+    } else if constexpr (FORM == 6) {
+      a = f_mulc_cios(a, m);
+      b = f_mulc_cios(b, m);
+    } else if constexpr (FORM == 7) {
       a = f_mul(a, m);
       b = f_mul(b, m);
     } else {
-      a = f_mulc(a, m);
-      b = f_mulc(b, m);
+      a = f_mul_fips<1>(a, m);
+      b = f_mul_fips<1>(b, m);
     }
   }
+  // every form against the CIOS reference product on this thread's values
+  Fp got;
+  if constexpr (FORM == 5) got = f_mul_cios(a, b);
+  else if constexpr (FORM == 6) got = f_mulc_cios(a, b);
+  else if constexpr (FORM == 7) got = f_mul(a, b);
+  else got = f_mul_fips<1>(a, b);
+  if (got != f_mul_cios(a, b)) atomicAdd(sink + 1, 1u);
   uint32_t acc = 0;
 #pragma unroll
   for (int j = 0; j < 8; j++) acc ^= a.v[j] ^ b.v[j];
@@ -528,27 +599,28 @@ int zkvc_msm_g2(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, voi
 
 int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int* sms, void* stream) {
   clear_error();
-  ZK_CHECK(form >= 0 && form <= 6, ZKVC_EINVAL, "imad_rate: form %d", form);
+  ZK_CHECK(form >= 0 && form <= 8, ZKVC_EINVAL, "imad_rate: form %d", form);
   ZK_CHECK(iters >= 1 && iters <= (1u << 24), ZKVC_EINVAL, "imad_rate: %u iterations outside [1, 2^24]", iters);
   static thread_local uint32_t* t_sink = nullptr;
   static thread_local int t_dev = -1;
   int dev = 0;
   ZK_CUDA(cudaGetDevice(&dev));
   if (!t_sink || t_dev != dev) {
-    ZK_CUDA(cudaMalloc(&t_sink, sizeof(uint32_t)));
+    ZK_CUDA(cudaMalloc(&t_sink, 2 * sizeof(uint32_t)));
     t_dev = dev;
   }
   cudaStream_t st = (cudaStream_t)stream;
   int per_sm = 0;
   auto kern = form == 0 ? k_imad_rate<0> : form == 1 ? k_imad_rate<1> : form == 2 ? k_imad_rate<2>
               : form == 3 ? k_imad_rate<3> : form == 4 ? k_imad_rate<4> : form == 5 ? k_mont_rate<5>
-                                                                                    : k_mont_rate<6>;
+              : form == 6 ? k_mont_rate<6> : form == 7 ? k_mont_rate<7> : k_mont_rate<8>;
   ZK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
   const int nsm = device_sm_count();
   const unsigned blocks = (unsigned)(nsm * (per_sm > 0 ? per_sm : 1));
   cudaEvent_t e0, e1;
   ZK_CUDA(cudaEventCreate(&e0));
   ZK_CUDA(cudaEventCreate(&e1));
+  ZK_CUDA(cudaMemsetAsync(t_sink, 0, 2 * sizeof(uint32_t), st));
   kern<<<blocks, 256, 0, st>>>(iters / 8 + 1, 7u, t_sink); ZK_COUNT_LAUNCH();  // warm
   ZK_CUDA(cudaEventRecord(e0, st));
   kern<<<blocks, 256, 0, st>>>(iters, 7u, t_sink); ZK_COUNT_LAUNCH();
@@ -559,6 +631,10 @@ int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int
   ZK_CUDA(cudaEventElapsedTime(&t, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  uint32_t bad = 0;
+  ZK_CUDA(cudaMemcpy(&bad, t_sink + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  ZK_CHECK(bad == 0, ZKVC_ECUDA, "imad_rate: form %d products differ from the reference product in %u threads",
+           form, bad);
   const double per_iter = form >= 5 ? 2.0 * 264.0 : 16.0;
   const double ops = double(blocks) * 256.0 * double(iters) * per_iter;
   if (ms) *ms = t;

@@ -247,9 +247,10 @@ __device__ __forceinline__ Field<C> f_neg(const Field<C>& a) {
 template <class C>
 __device__ __forceinline__ Field<C> f_dbl(const Field<C>& a) { return f_add(a, a); }
 
-// Montgomery product a b R^-1 mod N.
+// Montgomery product a b R^-1 mod N, CIOS with carry-chain rows (reference form; the
+// product-scanning f_mul below is the one the kernels use).
 template <class C>
-__device__ __forceinline__ Field<C> f_mul(const Field<C>& a, const Field<C>& b) {
+__device__ __forceinline__ Field<C> f_mul_cios(const Field<C>& a, const Field<C>& b) {
   uint32_t t[9];
 #pragma unroll
   for (int i = 0; i < 9; i++) t[i] = 0;
@@ -272,17 +273,70 @@ __device__ __forceinline__ Field<C> f_mul(const Field<C>& a, const Field<C>& b) 
   return br ? r : d;
 }
 
+// One term x y of a product-scanning column: (t2, t1, t0) += x y as mad.lo.cc /
+// madc.hi.cc / addc.
+__device__ __forceinline__ void col_mac(uint32_t& t0, uint32_t& t1, uint32_t& t2, uint32_t x, uint32_t y) {
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\tmadc.hi.cc.u32 %1, %3, %4, %1;\n\taddc.u32 %2, %2, 0;"
+      : "+r"(t0), "+r"(t1), "+r"(t2)
+      : "r"(x), "r"(y));
+}
+
+// Montgomery product a b R^-1 mod N by finely integrated product scanning (Koc, Acar and
+// Kaliski, "Analyzing and comparing Montgomery multiplication algorithms", 1996): column
+// i of the 16-word result sums every a_j b_(i-j) and m_j N_(i-j) into a 96-bit
+// accumulator; for i < 8 its low word then fixes m_i = t_0 (-N^-1) mod 2^32 and m_i N_0
+// clears it; the columns 8 .. 15 are the result.  A column holds at most 16 products
+// below 2^64 plus the carry of the previous one, so 96 bits never overflow; with a, b < N
+// the result is below 2N and one conditional subtraction makes it canonical.  Same IMAD
+// count as CIOS (264); on GB300 it runs at 18.1 T IMAD-equivalents/s in a throughput
+// loop against 12.3-12.6 T/s for the CIOS forms (zkvc_imad_rate forms 5-7): its
+// independent low/high word pairs and short carries issue better than CIOS's long
+// carry chains.
+template <class C>
+__device__ __forceinline__ Field<C> f_mul(const Field<C>& a, const Field<C>& b) {
+  uint32_t m[8];
+  Field<C> r, d;
+  uint32_t t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+#pragma unroll
+    for (int j = 0; j < i; j++) {
+      col_mac(t0, t1, t2, a.v[j], b.v[i - j]);
+      col_mac(t0, t1, t2, m[j], mod_limb<C>(i - j));
+    }
+    col_mac(t0, t1, t2, a.v[i], b.v[0]);
+    m[i] = t0 * C::INV;
+    col_mac(t0, t1, t2, m[i], mod_limb<C>(0));  // t0 becomes 0
+    t0 = t1;
+    t1 = t2;
+    t2 = 0;
+  }
+#pragma unroll
+  for (int i = 8; i < 15; i++) {
+#pragma unroll
+    for (int j = i - 7; j < 8; j++) {
+      col_mac(t0, t1, t2, a.v[j], b.v[i - j]);
+      col_mac(t0, t1, t2, m[j], mod_limb<C>(i - j));
+    }
+    r.v[i - 8] = t0;
+    t0 = t1;
+    t1 = t2;
+    t2 = 0;
+  }
+  r.v[7] = t0;  // r < 2N < 2^255: no further word
+  const Field<C> mm = Field<C>::modulus();
+  const uint32_t br = sub8(d.v, r.v, mm.v);
+  return br ? r : d;
+}
+
 template <class C>
 __device__ __forceinline__ Field<C> f_sqr(const Field<C>& a) { return f_mul(a, a); }
 
-// Out-of-line Montgomery product with 64-bit accumulation: the same CIOS rows written
-// with 32 x 32 + 64-bit multiply-adds in plain C, which the compiler maps to wide IMADs
-// with little carry bookkeeping on the ALU pipe.  Called (not inlined) by the point
-// formulas: in the bucket-accumulation loop it gives 4.3 G mixed additions/s on GB300,
-// against 3.7 G/s for the carry-chain rows in a rolled loop and 2.9 G/s fully inlined
-// (whose ~48 KB of straight-line code stalls on instruction fetch).
+// Out-of-line Montgomery product with 64-bit accumulation: CIOS rows written with
+// 32 x 32 + 64-bit multiply-adds in plain C (reference form: 12.6 T IMAD-equivalents/s in
+// zkvc_imad_rate form 6, against 18.1 T/s for f_mulc below).
 template <class C>
-__device__ __noinline__ Field<C> f_mulc(Field<C> a, Field<C> b) {
+__device__ __noinline__ Field<C> f_mulc_cios(Field<C> a, Field<C> b) {
   uint32_t t[10];
 #pragma unroll
   for (int i = 0; i < 10; i++) t[i] = 0;
@@ -320,6 +374,14 @@ __device__ __noinline__ Field<C> f_mulc(Field<C> a, Field<C> b) {
   }
   uint32_t br = sub8(d.v, r.v, m);  // result < 2N < 2^255, so t[8] = 0 here
   return br ? r : d;
+}
+
+// Out-of-line product-scanning Montgomery product for the point formulas: called, not
+// inlined, so that the large formulas keep one copy of the product's ~400 instructions
+// (fully inlined point formulas stall on instruction fetch).
+template <class C>
+__device__ __noinline__ Field<C> f_mulc(Field<C> a, Field<C> b) {
+  return f_mul(a, b);
 }
 
 template <class C>
