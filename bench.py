@@ -688,9 +688,10 @@ def run_gpu(args):
 
 
 # DRAM bytes (read + write) of one H-query accumulation launch of the [49,320]x[320,512]
-# proof, from one ncu capture of the balanced accumulation with the default chunk rule
+# proof, from one ncu capture of the balanced accumulation (product-scanning products)
+# with the default chunk rule
 # (dram__bytes_read.sum + dram__bytes_write.sum); other chunk settings: not captured
-H_ACCUM_TRAFFIC = {0: 76026112}
+H_ACCUM_TRAFFIC = {0: 76589568}
 
 
 # ------------------------------------------------------------------ batched workload

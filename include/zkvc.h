@@ -83,11 +83,12 @@ int zkvc_profile_span(int stage, double* start_ms, double* end_ms);
  * chains of whole Fp Montgomery products per thread (264 IMADs each): 5 CIOS with
  * carry-chain rows, 6 CIOS with 64-bit accumulators, 7 product scanning with 96-bit
  * column accumulators in mad.lo.cc / madc.hi.cc (the product the kernels use), 8 the same
- * with mul.wide and additions; each checked against the CIOS product on every thread
- * (ZKVC_ECUDA if any result differs).  A full-occupancy grid over every SM runs `iters` iterations (16 IMADs per
+ * with mul.wide and additions; 9 and 10: latency, one warp running one dependent chain
+ * of products per thread (9: the kernels' product, 10: the 64-bit-accumulator CIOS); each
+ * checked against the CIOS product on every thread (ZKVC_ECUDA if any result differs).  A full-occupancy grid over every SM runs `iters` iterations (16 IMADs per
  * thread for forms 0 .. 4), once untimed (iters / 8) and once timed with CUDA events on
  * `stream`; the call synchronises.  Outputs (any may be null): IMADs per second, the
- * timed launch in ms and the SM count used.  ZKVC_EINVAL for a form outside 0 .. 8 or
+ * timed launch in ms and the SM count used.  ZKVC_EINVAL for a form outside 0 .. 10 or
  * iters outside [1, 2^24].
  */
 int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int* sms, void* stream);

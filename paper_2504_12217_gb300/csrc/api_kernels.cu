@@ -408,16 +408,20 @@ __global__ void __launch_bounds__(256) k_mont_rate(uint32_t iters, uint32_t seed
     } else if constexpr (FORM == 7) {
       a = f_mul(a, m);
       b = f_mul(b, m);
-    } else {
+    } else if constexpr (FORM == 8) {
       a = f_mul_fips<1>(a, m);
       b = f_mul_fips<1>(b, m);
+    } else if constexpr (FORM == 9) {  // latency: one dependent chain
+      a = f_mul(a, m);
+    } else {
+      a = f_mulc_cios(a, m);
     }
   }
   // every form against the CIOS reference product on this thread's values
   Fp got;
   if constexpr (FORM == 5) got = f_mul_cios(a, b);
-  else if constexpr (FORM == 6) got = f_mulc_cios(a, b);
-  else if constexpr (FORM == 7) got = f_mul(a, b);
+  else if constexpr (FORM == 6 || FORM == 10) got = f_mulc_cios(a, b);
+  else if constexpr (FORM == 7 || FORM == 9) got = f_mul(a, b);
   else got = f_mul_fips<1>(a, b);
   if (got != f_mul_cios(a, b)) atomicAdd(sink + 1, 1u);
   uint32_t acc = 0;
@@ -599,7 +603,7 @@ int zkvc_msm_g2(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, voi
 
 int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int* sms, void* stream) {
   clear_error();
-  ZK_CHECK(form >= 0 && form <= 8, ZKVC_EINVAL, "imad_rate: form %d", form);
+  ZK_CHECK(form >= 0 && form <= 10, ZKVC_EINVAL, "imad_rate: form %d", form);
   ZK_CHECK(iters >= 1 && iters <= (1u << 24), ZKVC_EINVAL, "imad_rate: %u iterations outside [1, 2^24]", iters);
   static thread_local uint32_t* t_sink = nullptr;
   static thread_local int t_dev = -1;
@@ -613,17 +617,20 @@ int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int
   int per_sm = 0;
   auto kern = form == 0 ? k_imad_rate<0> : form == 1 ? k_imad_rate<1> : form == 2 ? k_imad_rate<2>
               : form == 3 ? k_imad_rate<3> : form == 4 ? k_imad_rate<4> : form == 5 ? k_mont_rate<5>
-              : form == 6 ? k_mont_rate<6> : form == 7 ? k_mont_rate<7> : k_mont_rate<8>;
+              : form == 6 ? k_mont_rate<6> : form == 7 ? k_mont_rate<7> : form == 8 ? k_mont_rate<8>
+              : form == 9 ? k_mont_rate<9> : k_mont_rate<10>;
   ZK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
   const int nsm = device_sm_count();
-  const unsigned blocks = (unsigned)(nsm * (per_sm > 0 ? per_sm : 1));
+  const bool latency = form >= 9;  // one warp, one dependent chain per thread
+  const unsigned blocks = latency ? 1u : (unsigned)(nsm * (per_sm > 0 ? per_sm : 1));
+  const unsigned threads = latency ? 32u : 256u;
   cudaEvent_t e0, e1;
   ZK_CUDA(cudaEventCreate(&e0));
   ZK_CUDA(cudaEventCreate(&e1));
   ZK_CUDA(cudaMemsetAsync(t_sink, 0, 2 * sizeof(uint32_t), st));
-  kern<<<blocks, 256, 0, st>>>(iters / 8 + 1, 7u, t_sink); ZK_COUNT_LAUNCH();  // warm
+  kern<<<blocks, threads, 0, st>>>(iters / 8 + 1, 7u, t_sink); ZK_COUNT_LAUNCH();  // warm
   ZK_CUDA(cudaEventRecord(e0, st));
-  kern<<<blocks, 256, 0, st>>>(iters, 7u, t_sink); ZK_COUNT_LAUNCH();
+  kern<<<blocks, threads, 0, st>>>(iters, 7u, t_sink); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaEventRecord(e1, st));
   ZK_CUDA(cudaGetLastError());
   ZK_TRY(wait_stream(st, "imad_rate"));
@@ -635,8 +642,8 @@ int zkvc_imad_rate(int form, uint32_t iters, double* imad_per_s, double* ms, int
   ZK_CUDA(cudaMemcpy(&bad, t_sink + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   ZK_CHECK(bad == 0, ZKVC_ECUDA, "imad_rate: form %d products differ from the reference product in %u threads",
            form, bad);
-  const double per_iter = form >= 5 ? 2.0 * 264.0 : 16.0;
-  const double ops = double(blocks) * 256.0 * double(iters) * per_iter;
+  const double per_iter = latency ? 264.0 : form >= 5 ? 2.0 * 264.0 : 16.0;
+  const double ops = double(blocks) * double(threads) * double(iters) * per_iter;
   if (ms) *ms = t;
   if (imad_per_s) *imad_per_s = t > 0 ? ops / (t * 1e-3) : 0.0;
   if (sms) *sms = nsm;

@@ -1073,9 +1073,10 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
   const uint32_t at = p.tune.accum_threads;
   const int lanes = p.lanes == 4 ? 4 : 1;
-  // the fold is latency-bound unless the run is large: quads there whatever the
-  // accumulation uses
-  const int flanes = (lanes == 4 || S / T0 < 40960) ? 4 : 1;
+  // the folds run on quads whatever the accumulation uses: after a balanced accumulation
+  // they only see a few partial sums per bucket (or few, large buckets), so they are
+  // latency-bound, and a quad's addition has a third of a lone thread's latency
+  const int flanes = 4;
   unsigned qb = (unsigned)((uint64_t(L.qmax) * lanes + at - 1) / at);
   unsigned fb = (unsigned)((uint64_t(L.qmax) * flanes + 127) / 128);
   if (accum_stage >= 0) prof_mark(accum_stage, true, st);
