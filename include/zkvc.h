@@ -361,12 +361,23 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const ui
  * more workspace).  zkvc_pk_set_tuning / zkvc_pk_get_tuning impose or read the setting
  * (ZKVC_EINVAL for a chunk above 1024, an NTT block outside 2^8..2^11, a start outside
  * its range or a mode other than fold or chain).  Proof bytes
- * never depend on it.  Keys of zkvc_setup only. */
+ * never depend on it.  Keys of zkvc_setup only.
+ * Tuning cache: every result is also stored in a process-wide cache keyed by the shape
+ * (a, n, b), the requested mode, the GPU's name and its SM count; zkvc_pk_autotune on a
+ * key with a cached entry applies it without timing (and returns it in tuning), unless
+ * `mode` carries ZKVC_TUNE_FRESH.  zkvc_tune_cache_save / zkvc_tune_cache_load write and
+ * merge a text file of entries (ZKVC_EIO for an unreadable or malformed file, which then
+ * changes nothing; entries are validated as zkvc_pk_set_tuning validates a setting);
+ * zkvc_tune_cache_clear empties the cache.  Host only, thread-safe. */
 #define ZKVC_PK_TUNING_LEN 10
+#define ZKVC_TUNE_FRESH 0x10 /* zkvc_pk_autotune: ignore the tuning cache, tune again */
 int zkvc_pk_autotune(zkvc_pk* pk, int mode, const int8_t* d_X, const int8_t* d_W, const uint8_t rs[64], void* stream,
                      uint32_t tuning[ZKVC_PK_TUNING_LEN]);
 int zkvc_pk_set_tuning(zkvc_pk* pk, const uint32_t tuning[ZKVC_PK_TUNING_LEN]);
 int zkvc_pk_get_tuning(const zkvc_pk* pk, uint32_t tuning[ZKVC_PK_TUNING_LEN]);
+int zkvc_tune_cache_save(const char* path);
+int zkvc_tune_cache_load(const char* path);
+int zkvc_tune_cache_clear(void);
 
 #define ZKVC_PROVE_FOLD 0
 #define ZKVC_PROVE_CHAIN 1

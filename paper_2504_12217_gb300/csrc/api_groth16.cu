@@ -1,5 +1,10 @@
 // C-ABI entry points of the Groth16 layer: setup, prove, key export and release.
 #include <algorithm>
+#include <tuple>
+#include <string>
+#include <mutex>
+#include <map>
+#include <array>
 #include <cstdio>
 #include <cstring>
 
@@ -26,6 +31,110 @@ template <class F>
 int generator_mul(const uint8_t* d_scalars, size_t n, uint8_t* d_out, void* ws, size_t ws_bytes, cudaStream_t st);
 
 int verify_impl(const zkvc_vk* vk, const int8_t* X, const int32_t* Y, const uint8_t* proof, int* ok);
+
+// ------------------------------------------------------------------ tuning cache
+// Results of the one-proof autotuner, keyed by the matmul shape, the requested mode and
+// the GPU (name and SM count): later keys of the same shape on the same kind of GPU take
+// the stored launch shape without timing.  Process-wide, guarded by a mutex; saved to and
+// loaded from a small text file (one entry per line: a n b mode sms tuning[0..9] name).
+struct TuneKey {
+  int a, n, b, mode, sms;
+  std::string gpu;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(a, n, b, mode, sms, gpu) < std::tie(o.a, o.n, o.b, o.mode, o.sms, o.gpu);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::array<uint32_t, ZKVC_PK_TUNING_LEN>> g_tune_cache;
+
+static int tune_key(const zkvc_pk* pk, int mode, TuneKey* k) {
+  cudaDeviceProp prop;
+  ZK_CUDA(cudaGetDeviceProperties(&prop, pk->device));
+  k->a = (int)pk->shape.a;
+  k->n = (int)pk->shape.n;
+  k->b = (int)pk->shape.b;
+  k->mode = mode;
+  k->sms = prop.multiProcessorCount;
+  k->gpu = prop.name;
+  for (char& c : k->gpu)
+    if (c == ' ' || c == '\t' || c == '\n') c = '_';
+  return ZKVC_OK;
+}
+
+static bool tune_cache_get(const TuneKey& k, uint32_t* t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune_cache.find(k);
+  if (it == g_tune_cache.end()) return false;
+  for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) t[i] = it->second[i];
+  return true;
+}
+
+static void tune_cache_put(const TuneKey& k, const uint32_t* t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto& v = g_tune_cache[k];
+  for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) v[i] = t[i];
+}
+
+static void tune_cache_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
+}
+
+static int tune_cache_save(const char* path) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE* f = std::fopen(path, "w");
+  ZK_CHECK(f, ZKVC_EIO, "tune_cache_save: cannot open %s", path);
+  std::fprintf(f, "zkvc-tune-cache 1\n");
+  for (const auto& e : g_tune_cache) {
+    const TuneKey& k = e.first;
+    std::fprintf(f, "%d %d %d %d %d", k.a, k.n, k.b, k.mode, k.sms);
+    for (uint32_t v : e.second) std::fprintf(f, " %u", v);
+    std::fprintf(f, " %s\n", k.gpu.c_str());
+  }
+  const bool ok = std::fclose(f) == 0;
+  ZK_CHECK(ok, ZKVC_EIO, "tune_cache_save: write to %s failed", path);
+  return ZKVC_OK;
+}
+
+// Entries are validated as zkvc_pk_set_tuning would; a malformed line rejects the file
+// (ZKVC_EIO) and leaves the cache as it was.
+static int tune_cache_load(const char* path) {
+  FILE* f = std::fopen(path, "r");
+  ZK_CHECK(f, ZKVC_EIO, "tune_cache_load: cannot open %s", path);
+  char line[1024];
+  std::map<TuneKey, std::array<uint32_t, ZKVC_PK_TUNING_LEN>> got;
+  int rc = ZKVC_OK;
+  if (!std::fgets(line, sizeof(line), f) || std::strncmp(line, "zkvc-tune-cache 1", 17) != 0) {
+    set_error("tune_cache_load: %s is not a tuning cache", path);
+    rc = ZKVC_EIO;
+  }
+  while (rc == ZKVC_OK && std::fgets(line, sizeof(line), f)) {
+    if (line[0] == '\n' || line[0] == 0) continue;
+    TuneKey k;
+    unsigned t[ZKVC_PK_TUNING_LEN];
+    char name[512];
+    const int nf = std::sscanf(line, "%d %d %d %d %d %u %u %u %u %u %u %u %u %u %u %511s", &k.a, &k.n, &k.b, &k.mode,
+                               &k.sms, &t[0], &t[1], &t[2], &t[3], &t[4], &t[5], &t[6], &t[7], &t[8], &t[9], name);
+    bool ok = nf == 16 && k.a >= 1 && k.n >= 1 && k.b >= 1 && k.mode >= ZKVC_PROVE_FOLD && k.mode <= ZKVC_PROVE_AUTO &&
+              k.sms >= 1;
+    for (int i = 0; ok && i < 4; i++) ok = t[i] <= 1024;
+    ok = ok && (t[4] == 0 || (t[4] >= 8 && t[4] <= 11)) && t[5] <= 2 && t[6] <= 1 && t[7] <= 1 && t[8] <= 1 &&
+         t[9] <= 1;
+    if (!ok) {
+      set_error("tune_cache_load: malformed entry in %s: %s", path, line);
+      rc = ZKVC_EIO;
+      break;
+    }
+    k.gpu = name;
+    auto& v = got[k];
+    for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) v[i] = t[i];
+  }
+  std::fclose(f);
+  if (rc != ZKVC_OK) return rc;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& e : got) g_tune_cache[e.first] = e.second;
+  return ZKVC_OK;
+}
 
 int vk_get(const zkvc_vk* vk, int* a, int* n, int* b, const uint8_t** alpha1, const uint8_t** beta2,
            const uint8_t** gamma2, const uint8_t** delta2, const uint8_t** ic, size_t* n_ic) {
@@ -162,10 +271,43 @@ int zkvc_pk_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, 
   set_error("%s", "");
   ZK_CHECK(pk && dX && dW && rs, ZKVC_EINVAL, "autotune: null argument");
   ZK_CHECK(!pk->gen, ZKVC_EINVAL, "autotune: keys of zkvc_setup_circuit are not tuned");
+  const bool fresh = (mode & ZKVC_TUNE_FRESH) != 0;
+  mode &= ~ZKVC_TUNE_FRESH;
   ZK_CHECK(mode == ZKVC_PROVE_FOLD || mode == ZKVC_PROVE_CHAIN || mode == ZKVC_PROVE_AUTO, ZKVC_EINVAL,
            "autotune: mode %d", mode);
   ZK_TRY(device_guard(pk->device));
-  return prove_autotune(pk, mode, dX, dW, rs, (cudaStream_t)stream, tuning);
+  TuneKey key;
+  ZK_TRY(tune_key(pk, mode, &key));
+  uint32_t t[ZKVC_PK_TUNING_LEN];
+  if (!fresh && tune_cache_get(key, t)) {
+    for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = t[i];
+    if (tuning)
+      for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) tuning[i] = t[i];
+    return ZKVC_OK;
+  }
+  ZK_TRY(prove_autotune(pk, mode, dX, dW, rs, (cudaStream_t)stream, t));
+  tune_cache_put(key, t);
+  if (tuning)
+    for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) tuning[i] = t[i];
+  return ZKVC_OK;
+}
+
+int zkvc_tune_cache_save(const char* path) {
+  set_error("%s", "");
+  ZK_CHECK(path, ZKVC_EINVAL, "tune_cache_save: null path");
+  return tune_cache_save(path);
+}
+
+int zkvc_tune_cache_load(const char* path) {
+  set_error("%s", "");
+  ZK_CHECK(path, ZKVC_EINVAL, "tune_cache_load: null path");
+  return tune_cache_load(path);
+}
+
+int zkvc_tune_cache_clear(void) {
+  set_error("%s", "");
+  tune_cache_clear();
+  return ZKVC_OK;
 }
 
 int zkvc_pk_set_tuning(zkvc_pk* pk, const uint32_t tuning[ZKVC_PK_TUNING_LEN]) {

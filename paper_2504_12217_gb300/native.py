@@ -73,6 +73,9 @@ SIGNATURES = {
     "zkvc_prove": (_c_int, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p, _c_p]),
     "zkvc_prove_workspace_bytes_mode": (_c_sz, [_c_p, _c_int]),
     "zkvc_pk_autotune": (_c_int, [_c_p, _c_int, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "zkvc_tune_cache_save": (_c_int, [ctypes.c_char_p]),
+    "zkvc_tune_cache_load": (_c_int, [ctypes.c_char_p]),
+    "zkvc_tune_cache_clear": (_c_int, []),
     "zkvc_pk_set_tuning": (_c_int, [_c_p, _c_p]),
     "zkvc_pk_get_tuning": (_c_int, [_c_p, _c_p]),
     "zkvc_setup_circuit": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _c_p, _c_p, ctypes.POINTER(_c_p),
@@ -510,14 +513,32 @@ ZKVC_PROVE_AUTO = 2
 ZKVC_PK_TUNING_LEN = 10
 
 
-def zkvc_pk_autotune(pk, X, W, rs, mode=0):
+ZKVC_TUNE_FRESH = 0x10
+
+
+def zkvc_pk_autotune(pk, X, W, rs, mode=0, fresh=False):
     """Tune the key's launch shape for one-proof latency on these inputs; returns the
     chosen [small, rest, h, g2 chunk terms, NTT log2 elements per block, side-MSM start,
-    prover mode, G2-MSM start, H-run quads, small-run quads].  mode: ZKVC_PROVE_FOLD, ZKVC_PROVE_CHAIN or ZKVC_PROVE_AUTO (both)."""
+    prover mode, G2-MSM start, H-run quads, small-run quads].  mode: ZKVC_PROVE_FOLD,
+    ZKVC_PROVE_CHAIN or ZKVC_PROVE_AUTO (both).  A cached result for the same shape, mode
+    and GPU is applied without timing unless fresh=True."""
     arr = (ctypes.c_uint32 * ZKVC_PK_TUNING_LEN)()
     rsb = ctypes.create_string_buffer(bytes(rs), 64)
-    check(lib().zkvc_pk_autotune(pk.handle, mode, _dev_ptr(X), _dev_ptr(W), rsb, _stream(), arr))
+    m = mode | (ZKVC_TUNE_FRESH if fresh else 0)
+    check(lib().zkvc_pk_autotune(pk.handle, m, _dev_ptr(X), _dev_ptr(W), rsb, _stream(), arr))
     return list(arr)
+
+
+def zkvc_tune_cache_save(path):
+    check(lib().zkvc_tune_cache_save(os.fsencode(path)))
+
+
+def zkvc_tune_cache_load(path):
+    check(lib().zkvc_tune_cache_load(os.fsencode(path)))
+
+
+def zkvc_tune_cache_clear():
+    check(lib().zkvc_tune_cache_clear())
 
 
 def zkvc_pk_set_tuning(pk, tuning):
