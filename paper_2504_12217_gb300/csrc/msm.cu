@@ -69,6 +69,45 @@ __global__ void k_scan_add(uint32_t* out, size_t n_out, const uint32_t* add) {
   if (i < n_out) out[i] += add[blockIdx.x];
 }
 
+// Exclusive scan of n_in values into n_out outputs by one block of 1024 threads, each
+// scanning a contiguous run of ceil(n_out / 1024) entries around one block-wide scan of
+// the runs' totals; also writes the first n_copy outputs to copy (if non-null).  For
+// outputs up to SCAN1_MAX: one launch instead of three.
+constexpr size_t SCAN1_MAX = 1024 * 64;
+__global__ void __launch_bounds__(1024) k_scan_single(const uint32_t* __restrict__ in, size_t n_in, uint32_t* out,
+                                                      size_t n_out, uint32_t* copy, size_t n_copy) {
+  __shared__ uint32_t wsum[32];
+  const size_t per = (n_out + 1023) / 1024;
+  const size_t lo = size_t(threadIdx.x) * per, hi = min(lo + per, n_out);
+  uint32_t tot = 0;
+  for (size_t i = lo; i < hi; i++) tot += i < n_in ? in[i] : 0u;
+  uint32_t x = tot;
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= (uint32_t)d) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = wsum[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= (uint32_t)d) w += y;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = x - tot + (wid ? wsum[wid - 1] : 0u);
+  for (size_t i = lo; i < hi; i++) {
+    out[i] = run;
+    if (copy && i < n_copy) copy[i] = run;
+    run += i < n_in ? in[i] : 0u;
+  }
+}
+
 static int scan_rec(const uint32_t* in, size_t n_in, uint32_t* out, size_t n_out, Arena& a, cudaStream_t st) {
   size_t blocks = (n_out + 1023) / 1024;
   if (blocks <= 1) {
@@ -93,8 +132,17 @@ static int scan_rec(const uint32_t* in, size_t n_in, uint32_t* out, size_t n_out
   return ZKVC_OK;
 }
 
-int scan_u32(const uint32_t* in, uint32_t* out, size_t n, Arena& a, cudaStream_t st) {
-  return scan_rec(in, n, out, n + 1, a, st);
+int scan_u32(const uint32_t* in, uint32_t* out, size_t n, Arena& a, cudaStream_t st, uint32_t* copy) {
+  if (n + 1 <= SCAN1_MAX) {
+    if (!a.measuring) {
+      k_scan_single<<<1, 1024, 0, st>>>(in, n, out, n + 1, copy, copy ? n : 0); ZK_COUNT_LAUNCH();
+      ZK_CUDA(cudaGetLastError());
+    }
+    return ZKVC_OK;
+  }
+  ZK_TRY(scan_rec(in, n, out, n + 1, a, st));
+  if (copy && !a.measuring) ZK_CUDA(cudaMemcpyAsync(copy, out, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+  return ZKVC_OK;
 }
 
 size_t scan_u32_temp_bytes(size_t n) {
@@ -382,7 +430,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_scatter(const uint32_t* __restri
 // contiguous slots [choff[k], choff[k] + nch[k]) with choff[k] = offs[k] / T0 + k and nch[k]
 // the chunks it overlaps; choff[K] bounds all slots.
 __global__ void k_chunk_layout(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offs, uint32_t K,
-                               uint32_t T0, uint32_t* nch, uint32_t* choff) {
+                               uint32_t T0, uint32_t* nch, uint32_t* choff, uint32_t* chunk_key) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > K) return;
   if (k == K) {
@@ -390,8 +438,10 @@ __global__ void k_chunk_layout(const uint32_t* __restrict__ counts, const uint32
     return;
   }
   const uint32_t lo = offs[k] / T0;
-  choff[k] = lo + k;
-  nch[k] = counts[k] ? (offs[k + 1] - 1) / T0 - lo + 1 : 0u;
+  const uint32_t c = lo + k, np = counts[k] ? (offs[k + 1] - 1) / T0 - lo + 1 : 0u;
+  choff[k] = c;
+  nch[k] = np;
+  for (uint32_t q = c; q < c + np; q++) chunk_key[q] = k;  // the bucket of each of its slots
 }
 
 // largest k in [0, K) with off[k] <= q
@@ -405,15 +455,6 @@ __device__ __forceinline__ uint32_t find_key(const uint32_t* off, uint32_t K, ui
 }
 
 // ------------------------------------------------------------------ bucket sums
-// bucket of every partial-sum slot (slots no bucket owns keep KEY_NONE)
-__global__ void k_chunk_keys(const uint32_t* __restrict__ choff, const uint32_t* __restrict__ nch, uint32_t K,
-                             uint32_t* chunk_key) {
-  uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const uint32_t a = choff[k], b = a + nch[k];
-  for (uint32_t q = a; q < b; q++) chunk_key[q] = k;
-}
-
 // fetch-and-add with release (this thread's earlier stores) and acquire (its later
 // loads) semantics at GPU scope
 __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
@@ -553,9 +594,12 @@ __global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ 
                                                    XYZZ<F>* part, uint32_t* arrive) {
   const uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
   if (q >= choff[K]) return;  // uniform within a quad
+  // chunk_key is written only for owned slots: any other value (a previous run's, or
+  // never written) fails the range check
   const uint32_t k = chunk_key[q];
-  if (k == KEY_NONE) return;  // a slot no bucket owns
+  if (k >= K) return;
   const uint32_t base = choff[k], np = nch[k];
+  if (q < base || q >= base + np) return;  // a slot no bucket owns
   if (np <= FOLD_SERIAL) return;  // k_fold_serial's
   const bool lead = QL == 1 || quad_lane() == 0;
   uint32_t pos = q - base;
@@ -1057,18 +1101,16 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
     k_hist<<<sb, HB_THREADS, 0, st>>>(L.keys, S, L.counts); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
-  ZK_TRY(scan_u32(L.counts, L.offs, K, a, st));
-  ZK_CUDA(cudaMemcpyAsync(L.cursor, L.offs, size_t(K) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+  ZK_TRY(scan_u32(L.counts, L.offs, K, a, st, L.cursor));
   if (S > 0) {
     k_scatter<<<sb, HB_THREADS, 0, st>>>(L.keys, L.vals, S, L.cursor, L.sorted); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
   // chunks of T0 sorted terms and the buckets' partial-sum slots
-  k_chunk_layout<<<(K + 1 + 255) / 256, 256, 0, st>>>(L.counts, L.offs, K, T0, L.nch, L.choff); ZK_COUNT_LAUNCH();
+  k_chunk_layout<<<(K + 1 + 255) / 256, 256, 0, st>>>(L.counts, L.offs, K, T0, L.nch, L.choff, L.chunk_key);
+  ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace too small for scans");
-  ZK_CUDA(cudaMemsetAsync(L.chunk_key, 0xff, size_t(L.qmax) * sizeof(uint32_t), st));
-  k_chunk_keys<<<(K + 255) / 256, 256, 0, st>>>(L.choff, L.nch, K, L.chunk_key); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaMemsetAsync(L.arrive, 0, size_t(L.qmax) * sizeof(uint32_t), st));
   XYZZ<F>* part = reinterpret_cast<XYZZ<F>*>(L.part);
   const uint32_t at = p.tune.accum_threads;

@@ -111,8 +111,9 @@ int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d
 template <class F>
 size_t msm_api_ws(size_t n);
 
-// Exclusive scan of n uint32 values into out[0..n] (out[n] = total); temp from the arena.
-int scan_u32(const uint32_t* in, uint32_t* out, size_t n, Arena& a, cudaStream_t st);
+// Exclusive scan of n uint32 values into out[0..n] (out[n] = total); temp from the arena;
+// copy (if non-null) receives out[0..n) as well.
+int scan_u32(const uint32_t* in, uint32_t* out, size_t n, Arena& a, cudaStream_t st, uint32_t* copy = nullptr);
 size_t scan_u32_temp_bytes(size_t n);
 
 }  // namespace zkvc
