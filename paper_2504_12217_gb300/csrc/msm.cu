@@ -429,8 +429,14 @@ __global__ void __launch_bounds__(HB_THREADS) k_scatter(const uint32_t* __restri
 // q + k strictly increases and the slots are distinct.  Bucket k (count > 0) owns the
 // contiguous slots [choff[k], choff[k] + nch[k]) with choff[k] = offs[k] / T0 + k and nch[k]
 // the chunks it overlaps; choff[K] bounds all slots.
+//
+// A bucket with 2 .. FOLD_SERIAL slots also names itself in flist at its first chunk
+// boundary (index offs[k] / T0 + 1, one bucket per boundary at most), so that sparse folds
+// can run over the boundaries instead of over every bucket.  Entries no bucket names keep
+// stale values, which the fold rejects.
+constexpr uint32_t FOLD_SERIAL = 4;
 __global__ void k_chunk_layout(const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offs, uint32_t K,
-                               uint32_t T0, uint32_t* nch, uint32_t* choff, uint32_t* chunk_key) {
+                               uint32_t T0, uint32_t* nch, uint32_t* choff, uint32_t* chunk_key, uint32_t* flist) {
   uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > K) return;
   if (k == K) {
@@ -442,6 +448,7 @@ __global__ void k_chunk_layout(const uint32_t* __restrict__ counts, const uint32
   choff[k] = c;
   nch[k] = np;
   for (uint32_t q = c; q < c + np; q++) chunk_key[q] = k;  // the bucket of each of its slots
+  if (np >= 2 && np <= FOLD_SERIAL) flist[lo + 1] = k;
 }
 
 // largest k in [0, K) with off[k] <= q
@@ -544,12 +551,23 @@ __global__ void __launch_bounds__(256, AccumMinB<F>::value) k_accum0(const uint3
 // Buckets with at most FOLD_SERIAL partial sums (the common case of a balanced
 // accumulation: a bucket split by one or two chunk boundaries) are folded by one thread
 // (or quad) per bucket, serially, without counters; k_fold_tree takes the larger ones.
-constexpr uint32_t FOLD_SERIAL = 4;
+// Where chunk boundaries are fewer than buckets (large chunks over many small buckets),
+// the quads go over the boundaries' fold list instead (flist non-null, nlist entries), so
+// that every launched quad has a bucket to fold.
 template <class F, int QL>
 __global__ void __launch_bounds__(128) k_fold_serial(const uint32_t* __restrict__ choff,
-                                                     const uint32_t* __restrict__ nch, uint32_t K, XYZZ<F>* part) {
-  const uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
-  if (k >= K) return;  // uniform within a quad
+                                                     const uint32_t* __restrict__ nch, uint32_t K, XYZZ<F>* part,
+                                                     const uint32_t* __restrict__ flist, uint32_t nlist,
+                                                     const uint32_t* __restrict__ offs, uint32_t T0) {
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
+  uint32_t k = i;
+  if (flist) {
+    if (i == 0 || i >= nlist) return;  // uniform within a quad
+    k = flist[i];
+    if (k >= K || offs[k] / T0 + 1 != i) return;  // no bucket's first boundary (stale entry)
+  } else if (k >= K) {
+    return;
+  }
   const uint32_t np = nch[k];
   if (np < 2 || np > FOLD_SERIAL) return;
   const uint32_t base = choff[k];
@@ -700,7 +718,8 @@ __device__ XYZZ<F> block_sum(Get get, uint32_t m, XYZZ<F>* sh) {
 // One BitSeg per (output, window, bit); its cnt buckets are cut into slices, each summed
 // by one block (serial sums per thread first, then the block's tree).
 //
-// Large fixed-base windows (c >= SPLIT_MIN_C, one window per output) first split every
+// Large windows (c >= SPLIT_MIN_C: the fixed-base outputs over stored multiples and every
+// window of a large variable-base MSM) first split every
 // bucket index as v = 2^h hi + lo: sum_v v B_v = sum_lo lo C_lo + 2^h sum_hi hi D_hi with
 // C_lo = sum_{v : low h bits = lo} B_v and D_hi = sum_{v : v >> h = hi} B_v (each bucket
 // added twice, by k_split_gather), and the bit decomposition then runs over the two small
@@ -846,8 +865,9 @@ __global__ void __launch_bounds__(BITS_BT) k_bits_window(XYZZ<F>* D, const TreeS
   if (threadIdx.x == 0) st_field(D + g.off, r);
 }
 
-// results[o] = sum_w 2^(c w) W[o][w] by Horner's rule (windows of variable-base outputs),
-// one quad per output.
+// results[o] = sum_w 2^(c w) W[o][w] by Horner's rule (windows of variable-base outputs):
+// a chain of c (nwin - 1) doublings, latency-bound, so G1 runs it on one warp in
+// limb-sliced arithmetic (about two thirds of a quad doubling's latency), G2 on one quad.
 struct OutItem {
   uint32_t first;     // index of window 0's result in D
   uint32_t stride;    // distance between windows' results
@@ -856,21 +876,33 @@ struct OutItem {
 };
 
 template <class F>
+constexpr int combine_lanes() { return sizeof(F) == sizeof(Fp) ? 32 : 4; }
+
+template <class F>
 __global__ void k_combine_windows(const XYZZ<F>* D, const OutItem* outs, uint32_t nouts, XYZZ<F>* results) {
-  uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
-  if (o >= nouts) return;
-  OutItem it = outs[o];
-  XYZZ<F> acc = ld_field(D + it.first + (it.nwin - 1) * it.stride);
-  for (int w = (int)it.nwin - 2; w >= 0; w--) {
-    for (uint32_t i = 0; i < it.c; i++) acc = p_dbl_quad(acc);
-    acc = p_add_quad(acc, ld_field(D + it.first + uint32_t(w) * it.stride));
+  const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) / combine_lanes<F>();
+  if (o >= nouts) return;  // uniform per warp (G1) or quad (G2)
+  const OutItem it = outs[o];
+  if constexpr (sizeof(F) == sizeof(Fp)) {
+    SlG1 acc = sl_ld(D + it.first + (it.nwin - 1) * it.stride);
+    for (int w = (int)it.nwin - 2; w >= 0; w--) {
+      for (uint32_t i = 0; i < it.c; i++) acc = sl_pdbl(acc);
+      acc = sl_padd(acc, sl_ld(D + it.first + uint32_t(w) * it.stride));
+    }
+    sl_st(results + o, acc);
+  } else {
+    XYZZ<F> acc = ld_field(D + it.first + (it.nwin - 1) * it.stride);
+    for (int w = (int)it.nwin - 2; w >= 0; w--) {
+      for (uint32_t i = 0; i < it.c; i++) acc = p_dbl_quad(acc);
+      acc = p_add_quad(acc, ld_field(D + it.first + uint32_t(w) * it.stride));
+    }
+    if (quad_lane() == 0) st_field(results + o, acc);
   }
-  if (quad_lane() == 0) st_field(results + o, acc);
 }
 
 // ------------------------------------------------------------------ driver
 struct Layout {
-  uint32_t *keys, *vals, *sorted, *counts, *offs, *cursor, *nch, *choff, *chunk_key, *arrive;
+  uint32_t *keys, *vals, *sorted, *counts, *offs, *cursor, *nch, *choff, *chunk_key, *arrive, *flist;
   void *part, *S, *D;
   MsmSeg* segs;
   MsmOut* outs;
@@ -903,7 +935,7 @@ MsmExec::~MsmExec() { delete st; }
 // Slices of bt * r buckets, r >= 2 chosen so that the slice kernel fills about one wave
 // of `wave` blocks (a lone wave's blocks each run their tree once; more buckets per
 // slice are serial sums, which the SMs run at full rate).
-static bool split_window(const MsmOut& o) { return o.win_keys == 1 && o.c >= SPLIT_MIN_C; }
+static bool split_window(const MsmOut& o) { return o.c >= SPLIT_MIN_C; }
 
 // additions of the bit decomposition of one window of c bits (plain or split)
 static uint64_t bit_work(const MsmOut& o) {
@@ -979,6 +1011,7 @@ static void layout(const MsmPlan& p, Arena& a, Layout& L, HostTables& h) {
   L.qmax = (uint32_t)(S / T0 + K + 1);
   L.chunk_key = a.take<uint32_t>(L.qmax);
   L.arrive = a.take<uint32_t>(L.qmax);
+  L.flist = a.take<uint32_t>(L.qmax);
   L.part = a.take<XYZZ<F>>(L.qmax);
   tables(p, SliceBT<F>::value, slice_wave(), h, L);
   L.S = a.take<XYZZ<F>>(L.nslices);
@@ -1107,7 +1140,8 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
     ZK_CUDA(cudaGetLastError());
   }
   // chunks of T0 sorted terms and the buckets' partial-sum slots
-  k_chunk_layout<<<(K + 1 + 255) / 256, 256, 0, st>>>(L.counts, L.offs, K, T0, L.nch, L.choff, L.chunk_key);
+  k_chunk_layout<<<(K + 1 + 255) / 256, 256, 0, st>>>(L.counts, L.offs, K, T0, L.nch, L.choff, L.chunk_key,
+                                                       L.flist);
   ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   ZK_CHECK(!a.overflow(), ZKVC_EINVAL, "msm: workspace too small for scans");
@@ -1134,12 +1168,16 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   }
   ZK_CUDA(cudaGetLastError());
   if (after_accum) ZK_CUDA(cudaEventRecord(after_accum, st));
-  const unsigned sfb = (unsigned)((uint64_t(K) * flanes + 127) / 128);
+  // chunk boundaries 1 .. chunks - 1 index the fold list (chunks <= slots / T0 + 1)
+  const uint64_t nlist = p.slots / T0 + 2;
+  const bool by_boundary = nlist < K;
+  const uint32_t* fl = by_boundary ? L.flist : nullptr;
+  const unsigned sfb = (unsigned)(((by_boundary ? nlist : uint64_t(K)) * flanes + 127) / 128);
   if (flanes == 4) {
-    k_fold_serial<F, 4><<<sfb, 128, 0, st>>>(L.choff, L.nch, K, part);
+    k_fold_serial<F, 4><<<sfb, 128, 0, st>>>(L.choff, L.nch, K, part, fl, (uint32_t)nlist, L.offs, T0);
     k_fold_tree<F, 4><<<fb, 128, 0, st>>>(L.choff, L.nch, L.chunk_key, K, part, L.arrive);
   } else {
-    k_fold_serial<F, 1><<<sfb, 128, 0, st>>>(L.choff, L.nch, K, part);
+    k_fold_serial<F, 1><<<sfb, 128, 0, st>>>(L.choff, L.nch, K, part, fl, (uint32_t)nlist, L.offs, T0);
     k_fold_tree<F, 1><<<fb, 128, 0, st>>>(L.choff, L.nch, L.chunk_key, K, part, L.arrive);
   }
   ZK_COUNT_LAUNCH();
@@ -1158,7 +1196,9 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   k_bits_scale<F><<<L.nbits, BITS_BT, 0, st>>>(Sl, L.bsegs, D); ZK_COUNT_LAUNCH();
   k_bits_window<F><<<(unsigned)h.dsegs.size(), BITS_BT, 0, st>>>(D, L.dseg); ZK_COUNT_LAUNCH();
   const uint32_t nouts = (uint32_t)p.outs.size();
-  k_combine_windows<F><<<(4 * nouts + 63) / 64, 64, 0, st>>>(D, L.oitems, nouts, results); ZK_COUNT_LAUNCH();
+  k_combine_windows<F><<<(unsigned)((uint64_t(combine_lanes<F>()) * nouts + 63) / 64), 64, 0, st>>>(D, L.oitems, nouts,
+                                                                                                  results);
+  ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
 }
