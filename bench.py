@@ -403,12 +403,24 @@ def ntt_roofline(nv, prof, log_n_proof, imad_peak, hbm_peak, hbm_src):
     return out
 
 
+def msm_work(group, logn):
+    """IMAD-equivalents of the library's variable-base MSM of 2^logn points, and its window
+    bits c (window rule: log2(points) - 3, within [4, 16]).  G1 runs the GLV split: 2N
+    points of 127-bit scalars, 2N ceil(128/c) mixed additions and 2^c ceil(128/c) full
+    additions for the bucket sums; G2: N ceil(254/c) and 2^c ceil(254/c)."""
+    pts_log, bits = (logn + 1, 128) if group == 1 else (logn, 254)
+    c = min(16, max(4, pts_log - 3))
+    win = -(-bits // c)
+    madd = G1_MADD_PRODUCTS if group == 1 else G2_MADD_PRODUCTS
+    add = 14 if group == 1 else 42
+    return ((1 << pts_log) * win * madd + (1 << c) * win * add) * MONT_IMAD, c
+
+
 def msm_sweep_section(nv, imad_peak):
     """Variable-base MSMs of the kernel sweep inside the default line: G1 at 2^20 and 2^24
     points, G2 at 2^20, uniform Fr scalars, points = generator x uniform scalars (made by
     the library's fixed-base kernel, untimed).  Fractions of the integer peak with the
-    method's work: N ceil(254/c) mixed additions + 2^c ceil(254/c) full additions for the
-    bucket sums (c = the library's window rule, 16 at these sizes)."""
+    method's work (msm_work)."""
     import torch
     g = torch.Generator(device="cuda").manual_seed(0x5A4B5643_00000003)
 
@@ -436,11 +448,7 @@ def msm_sweep_section(nv, imad_peak):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        c = min(16, max(4, logn - 3))
-        win = -(-254 // c)
-        madd = G1_MADD_PRODUCTS if group == 1 else G2_MADD_PRODUCTS
-        add = 14 if group == 1 else 42
-        work = (n * win * madd + (1 << c) * win * add) * MONT_IMAD
+        work, c = msm_work(group, logn)
         out.append({"group": f"G{group}", "log_n": logn, "ms": ms, "mpoints_per_s": n / ms / 1e3,
                     "imad_frac": work / (ms / 1e3) / imad_peak, "window_bits": c})
         del pts, sc, ws
@@ -501,7 +509,9 @@ def run_sweep(args):
             ws = torch.empty(nv.zkvc_msm_workspace_bytes(n, group), dtype=torch.uint8, device="cuda")
             fn = (lambda: nv.zkvc_msm_g1(pts, sc, ws)) if group == 1 else (lambda: nv.zkvc_msm_g2(pts, sc, ws))
             ms = time_it(fn, 3 if logn < 22 else 1)
-            out[key].append({"log_n": logn, "ms": ms, "mpoints_per_s": n / ms / 1e3})
+            work, c = msm_work(group, logn)
+            out[key].append({"log_n": logn, "ms": ms, "mpoints_per_s": n / ms / 1e3,
+                             "imad_frac": work / (ms / 1e3) / imad_peak, "window_bits": c})
             del pts, sc, ws
             torch.cuda.empty_cache()
     line = {"metric": "kernel sweep: NTT/INTT/coset-NTT and G1/G2 MSM over BN254", "unit": "ms",

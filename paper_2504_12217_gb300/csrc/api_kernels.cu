@@ -183,19 +183,27 @@ static uint32_t window_bits(size_t n) {
   return (uint32_t)c;
 }
 
-static MsmPlan variable_base_plan(size_t n, const void* scalars) {
+// G1 takes the GLV split: s P = k1 P + k2 phi(P) with |k1|, |k2| < 2^127, so the run has
+// 2n points of 127-bit scalars: as many bucket terms as n points of 254-bit scalars, but
+// half the windows, hence half the buckets to reduce and half of Horner's chain of
+// doublings over the windows (the latency-bound tail of a variable-base MSM).
+template <class F>
+constexpr bool msm_api_glv() { return sizeof(F) == sizeof(Fp); }
+
+static MsmPlan variable_base_plan(size_t n, const void* scalars, bool glv) {
   MsmPlan p;
-  uint32_t c = window_bits(n);
+  const size_t pts = glv ? 2 * n : n;
+  const uint32_t c = window_bits(pts);
   MsmOut o{};
   o.c = c;
-  o.win_keys = (255 + c - 1) / c;
+  o.win_keys = glv ? (128 + c - 1) / c : (255 + c - 1) / c;
   p.outs.push_back(o);
   MsmSeg s{};
   s.base_off = 0;
-  s.count = (uint32_t)n;
+  s.count = (uint32_t)pts;
   s.nwin = 1;
   s.out = 0;
-  s.kind = SK_FR_CANON;
+  s.kind = glv ? SK_SIGNED127 : SK_FR_CANON;
   s.scalars = scalars;
   s.skip = 0xffffffffu;
   p.segs.push_back(s);
@@ -203,18 +211,54 @@ static MsmPlan variable_base_plan(size_t n, const void* scalars) {
   return p;
 }
 
+static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
 template <class F>
 size_t msm_api_ws(size_t n) {
-  MsmPlan p = variable_base_plan(n, nullptr);
-  return msm_workspace_bytes<F>(p) + ((n * sizeof(Affine<F>) + 255) & ~size_t(255)) + 2 * 256 +
-         sizeof(XYZZ<F>) + sizeof(Affine<F>);
+  constexpr bool glv = msm_api_glv<F>();
+  const size_t pts = glv ? 2 * n : n;
+  MsmPlan p = variable_base_plan(n, nullptr, glv);
+  return msm_workspace_bytes<F>(p) + round256(pts * sizeof(Affine<F>)) + (glv ? round256(pts * sizeof(uint4)) : 0) +
+         2 * 256 + sizeof(XYZZ<F>) + sizeof(Affine<F>);
+}
+
+// bases[i] = P_i and bases[n + i] = phi(P_i) = (beta x_i, y_i) in Montgomery form;
+// halves[i], halves[n + i] = the GLV halves k1, k2 of s_i (reduced mod r first)
+__global__ void k_glv_prep(const Affine<Fp>* __restrict__ pts, const Fr* __restrict__ sc, size_t n,
+                           Affine<Fp>* bases, uint4* halves) {
+  const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Affine<Fp> p = ld_field(pts + i);
+  p.x = f_to_mont(p.x);
+  p.y = f_to_mont(p.y);
+  Fp beta;
+#pragma unroll
+  for (int l = 0; l < 8; l++) beta.v[l] = glv_beta_limb(l);
+  Affine<Fp> q;
+  q.x = f_mul(p.x, f_to_mont(beta));
+  q.y = p.y;
+  st_field(bases + i, p);
+  st_field(bases + n + i, q);
+  Fr k = ld_field(sc + i);
+  const Fr r = Fr::modulus();
+  for (int t = 0; t < 6; t++) {  // 2^256 < 6 r
+    uint32_t d[8];
+    if (sub8(d, k.v, r.v)) break;
+#pragma unroll
+    for (int l = 0; l < 8; l++) k.v[l] = d[l];
+  }
+  uint4 h1, h2;
+  glv_split_dev(k.v, &h1, &h2);
+  halves[i] = h1;
+  halves[n + i] = h2;
 }
 
 template <class F>
 int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
             uint8_t* out, cudaStream_t st) {
+  constexpr bool glv = msm_api_glv<F>();
   ZK_CHECK(out != nullptr, ZKVC_EINVAL, "msm: null output");
-  ZK_CHECK(n < (1ull << 31), ZKVC_EINVAL, "msm: n = %zu too large", n);
+  ZK_CHECK(n < (1ull << 30), ZKVC_EINVAL, "msm: n = %zu too large", n);
   if (n == 0) {
     memset(out, 0, sizeof(Affine<F>));
     return ZKVC_OK;
@@ -225,15 +269,23 @@ int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d
   Arena a;
   a.base = reinterpret_cast<uint8_t*>(d_ws);
   a.cap = ws_bytes;
-  Affine<F>* bases = a.take<Affine<F>>(n);
+  const size_t pts = glv ? 2 * n : n;
+  Affine<F>* bases = a.take<Affine<F>>(pts);
+  uint4* halves = glv ? a.take<uint4>(pts) : nullptr;
   XYZZ<F>* res = a.take<XYZZ<F>>(1);
   Affine<F>* aff = a.take<Affine<F>>(1);
   uint8_t* rest = a.base + a.off;
   size_t rest_bytes = ws_bytes - a.off;
-  k_points_to_mont<F><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-      reinterpret_cast<const Affine<F>*>(d_points), bases, n); ZK_COUNT_LAUNCH();
+  if constexpr (glv) {
+    k_glv_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const Affine<Fp>*>(d_points),
+                                                             reinterpret_cast<const Fr*>(d_scalars), n, bases, halves);
+  } else {
+    k_points_to_mont<F><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        reinterpret_cast<const Affine<F>*>(d_points), bases, n);
+  }
+  ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  MsmPlan p = variable_base_plan(n, d_scalars);
+  MsmPlan p = variable_base_plan(n, glv ? static_cast<const void*>(halves) : d_scalars, glv);
   ZK_TRY(msm_run<F>(p, bases, rest, rest_bytes, res, st));
   k_export_point<F><<<1, 32, 0, st>>>(res, aff); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());

@@ -135,4 +135,91 @@ inline GlvScalar glv_split(const uint8_t* k_le) {
   return g;
 }
 
+#ifdef __CUDACC__
+// The same split on the device, for one scalar per thread (the variable-base G1 MSM): the
+// halves packed as |k_i| in bits 0..126 of a uint4 and the sign in bit 127 (|k_i| < 2^127).
+// k: canonical little-endian 32-bit limbs, k < r.
+namespace glv_dev {
+// (t, carry) <- t + a b + carry
+__device__ __forceinline__ void mac(uint64_t a, uint64_t b, uint64_t& t, uint64_t& carry) {
+  uint64_t lo = a * b, hi = __umul64hi(a, b);
+  lo += t;
+  hi += lo < t;
+  lo += carry;
+  hi += lo < carry;
+  t = lo;
+  carry = hi;
+}
+template <int NG>
+__device__ __forceinline__ void mul_shift256(const uint64_t k[4], const uint64_t (&g)[NG], uint64_t out[2]) {
+  uint64_t t[4 + NG];
+#pragma unroll
+  for (int i = 0; i < 4 + NG; i++) t[i] = 0;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < NG; j++) mac(k[i], g[j], t[i + j], carry);
+    t[i + NG] = carry;
+  }
+  out[0] = t[4];
+  out[1] = t[5];
+}
+// r = x y mod 2^192, x of 2 limbs, y of NY limbs
+template <int NY>
+__device__ __forceinline__ void mul192(const uint64_t x[2], const uint64_t (&y)[NY], uint64_t r[3]) {
+  r[0] = r[1] = r[2] = 0;
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < NY && i + j < 3; j++) mac(x[i], y[j], r[i + j], carry);
+    if (i + NY < 3) r[i + NY] += carry;
+  }
+}
+__device__ __forceinline__ void sub192(uint64_t a[3], const uint64_t b[3]) {
+  uint64_t borrow = 0;
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    const uint64_t d = a[i] - b[i], e = d - borrow;
+    borrow = (a[i] < b[i]) | (d < borrow);
+    a[i] = e;
+  }
+}
+__device__ __forceinline__ uint4 pack(uint64_t v[3]) {
+  const uint32_t neg = (uint32_t)(v[2] >> 63);
+  if (neg) {
+    uint64_t z[3] = {0, 0, 0};
+    sub192(z, v);
+    v[0] = z[0];
+    v[1] = z[1];
+  }
+  return make_uint4((uint32_t)v[0], (uint32_t)(v[0] >> 32), (uint32_t)v[1],
+                    ((uint32_t)(v[1] >> 32) & 0x7fffffffu) | (neg << 31));
+}
+}  // namespace glv_dev
+
+__device__ __forceinline__ void glv_split_dev(const uint32_t k32[8], uint4* h1, uint4* h2) {
+  using namespace glv_dev;
+  const uint64_t g1[2] = {GLV_G1[0], GLV_G1[1]}, g2[3] = {GLV_G2[0], GLV_G2[1], GLV_G2[2]};
+  const uint64_t a1[1] = {GLV_A1}, a2[2] = {GLV_A2[0], GLV_A2[1]}, b1[2] = {GLV_B1[0], GLV_B1[1]}, b2[1] = {GLV_B2};
+  uint64_t k[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) k[i] = uint64_t(k32[2 * i]) | (uint64_t(k32[2 * i + 1]) << 32);
+  uint64_t c1[2], c2[2], t[3];
+  mul_shift256(k, g1, c1);
+  mul_shift256(k, g2, c2);
+  uint64_t k1[3] = {k[0], k[1], k[2]}, k2[3];  // k1 = k - c1 a1 - c2 a2, k2 = c1 b1 - c2 b2 (mod 2^192)
+  mul192(c1, a1, t);
+  sub192(k1, t);
+  mul192(c2, a2, t);
+  sub192(k1, t);
+  mul192(c1, b1, k2);
+  mul192(c2, b2, t);
+  sub192(k2, t);
+  *h1 = pack(k1);
+  *h2 = pack(k2);
+}
+#endif
+
 }  // namespace zkvc

@@ -181,6 +181,7 @@ int msm_plan_finalize(MsmPlan& p) {
       case SK_I16: nd = o.c >= 16 ? 1 : (16 + o.c) / o.c; break;  // |v| <= 2^15 needs c (nd) > 16
       case SK_FR_MONT:
       case SK_FR_CANON: nd = (255 + o.c - 1) / o.c; break;
+      case SK_SIGNED127: nd = (128 + o.c - 1) / o.c; break;  // nd c >= 128: the top window takes the last carry
       default: ZK_CHECK(false, ZKVC_EINVAL, "msm: scalar kind %d", s.kind);
     }
     if (s.kind == SK_I8 && o.c >= 8) nd = 1;
@@ -287,6 +288,15 @@ __global__ void k_digits(const MsmSeg* __restrict__ segs, int nsegs, const MsmOu
         int32_t v = reinterpret_cast<const int32_t*>(sg.scalars)[i];
         neg = v < 0;
         m[0] = v < 0 ? (uint32_t)(-(int64_t)v) : (uint32_t)v;
+        break;
+      }
+      case SK_SIGNED127: {
+        const uint4 v = reinterpret_cast<const uint4*>(sg.scalars)[i];
+        m[0] = v.x;
+        m[1] = v.y;
+        m[2] = v.z;
+        m[3] = v.w & 0x7fffffffu;
+        neg = (v.w >> 31) != 0;
         break;
       }
       case SK_FR_MONT: {

@@ -14,6 +14,7 @@ enum ScalarKind : int32_t {
   SK_FR_MONT = 3,   // Fr array in Montgomery form
   SK_FR_CANON = 4,  // Fr array, canonical little-endian 8 x u32
   SK_I16 = 5,       // int16 array, signed
+  SK_SIGNED127 = 6, // uint4 array: magnitude < 2^127 in bits 0..126, sign in bit 127
 };
 
 // One run of points sharing a scalar kind and an output.
