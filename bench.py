@@ -1003,8 +1003,10 @@ def served_pool(inputs, shapes, base_seed, rank=0):
 
 def served_section(nv, args, local):
     """The served workload inside the default bench line: the 32 shapes' keys resident,
-    Poisson arrivals at three offered rates (the highest above saturation), the plain
-    one-proof path on the same mix beside it."""
+    Poisson arrivals at three offered rates (the highest above saturation) under two
+    server policies -- chain (every request its own proof, overlapping on worker streams)
+    and merge (queued requests proven together as merged batches) -- and the plain
+    one-proof path on the same mix beside them."""
     import random
 
     import torch
@@ -1019,18 +1021,23 @@ def served_section(nv, args, local):
     pool = served_pool(inputs, shapes, inputs.SEED_CFG[5])
     rng = random.Random(inputs.SEED_CFG[5])
     rates = args.served_rates
-    r = served_core(nv, pks, pool, rates, args.served_seconds, args.served_max_requests, args.server_slots,
-                    args.server_budget_gib << 30, nv.ZKVC_SERVER_CHAIN, local, rng)
+    runs = {}
+    for name, policy, slots in (("chain", nv.ZKVC_SERVER_CHAIN, args.server_slots),
+                                ("merge", nv.ZKVC_SERVER_MERGE, args.server_merge_slots)):
+        r = served_core(nv, pks, pool, rates, args.served_seconds, args.served_max_requests, slots,
+                        args.server_budget_gib << 30, policy, local, rng)
+        best = max(r["per_rate"], key=lambda x: x["achieved_proofs_per_s"])
+        runs[name] = {"slots": slots, "rates": r["per_rate"], "ceiling_proofs_per_s": best["achieved_proofs_per_s"],
+                      "gpu_launches": r["launches"], "server_stats": r["stats"], "clocks": r["clocks"]}
     dev = [(k, torch.from_numpy(X).cuda(), torch.from_numpy(W).cuda(), rs) for k, X, W, rs in pool]
     plain = plain_on_mix(nv, pks, dev, 64, rng)
     del dev, pks
     torch.cuda.empty_cache()
-    best = max(r["per_rate"], key=lambda x: x["achieved_proofs_per_s"])
-    return {"workload": "crpc_groth16_bn254_served_poisson", "shapes": len(shapes), "policy": "chain",
-            "slots": args.server_slots, "mem_budget_bytes": args.server_budget_gib << 30,
-            "rates": r["per_rate"], "ceiling_proofs_per_s": best["achieved_proofs_per_s"],
-            "plain_one_proof_path_same_mix": plain, "gpu_launches": r["launches"], "server_stats": r["stats"],
-            "setup_s": setup_s, "clocks": r["clocks"],
+    top = max(runs, key=lambda n: runs[n]["ceiling_proofs_per_s"])
+    return {"workload": "crpc_groth16_bn254_served_poisson", "shapes": len(shapes),
+            "mem_budget_bytes": args.server_budget_gib << 30, "policies": runs,
+            "ceiling_proofs_per_s": runs[top]["ceiling_proofs_per_s"], "ceiling_policy": top,
+            "plain_one_proof_path_same_mix": plain, "setup_s": setup_s,
             "latency": "host wall clock from submit to result (includes H2D of X, W and D2H of Y, proof)"}
 
 
@@ -1060,8 +1067,8 @@ def run_served(args):
     setup_s = time.perf_counter() - t0
     pool = served_pool(inputs, shapes, inputs.SEED_CFG[5], rank)
     rng = random.Random(inputs.SEED_CFG[5] + rank)
-    policy = {"adaptive": nv.ZKVC_SERVER_ADAPTIVE, "fold": nv.ZKVC_SERVER_FOLD, "chain": nv.ZKVC_SERVER_CHAIN}[
-        args.server_policy]
+    policy = {"adaptive": nv.ZKVC_SERVER_ADAPTIVE, "fold": nv.ZKVC_SERVER_FOLD, "chain": nv.ZKVC_SERVER_CHAIN,
+              "merge": nv.ZKVC_SERVER_MERGE}[args.server_policy]
     budget = args.server_budget_gib << 30
     r = served_core(nv, pks, pool, args.rates, args.seconds_per_rate, args.max_requests, args.server_slots, budget,
                     policy, local, rng)
@@ -1079,7 +1086,8 @@ def run_served(args):
         "config": {"workload": "crpc_groth16_bn254_served_poisson", "shapes": len(shapes),
                    "rates_rps": args.rates, "slots": args.server_slots, "mem_budget_bytes": budget,
                    "policy": {"adaptive": "adaptive (fold when idle, chain when shared)", "fold": "fold",
-                              "chain": "chain"}[args.server_policy],
+                              "chain": "chain", "merge": "merge (queued requests in merged batches)"}[
+                                  args.server_policy],
                    "latency": "host wall clock from submit to result (includes H2D of X, W and D2H of Y, proof)"},
         "served": per_rate,
         "plain_one_proof_path": plain,
@@ -1189,8 +1197,10 @@ def main():
     ap.add_argument("--max-requests", type=int, default=1200)
     ap.add_argument("--server-slots", type=int, default=8)
     ap.add_argument("--server-budget-gib", type=int, default=48)
-    ap.add_argument("--server-policy", choices=["adaptive", "fold", "chain"], default="chain",
-                    help="served: prover mode per request")
+    ap.add_argument("--server-policy", choices=["adaptive", "fold", "chain", "merge"], default="chain",
+                    help="served: prover mode per request, or merged batches of queued requests")
+    ap.add_argument("--server-merge-slots", type=int, default=3,
+                    help="plain: workers of the merge-policy server in the served section")
     ap.add_argument("--batch-count", type=int, default=0, help="batched: only the K smallest instances")
     ap.add_argument("--no-batched", action="store_true", help="plain: leave the batched section out of the line")
     ap.add_argument("--no-served", action="store_true", help="plain: leave the served section out of the line")

@@ -519,8 +519,14 @@ int zkvc_prove_batch(const zkvc_pk* const* pks, const int8_t* const* d_X, const 
  * with them on the device.  A request that can never fit completes with ZKVC_ENOMEM.
  * Policy: ZKVC_SERVER_ADAPTIVE proves a request that finds the GPU idle with
  * ZKVC_PROVE_FOLD (lowest latency) and one admitted beside others with ZKVC_PROVE_CHAIN
- * (less work per proof); ZKVC_SERVER_FOLD / _CHAIN force one mode.  Results are the same
- * bytes as zkvc_prove's.
+ * (less work per proof); ZKVC_SERVER_FOLD / _CHAIN force one mode.  ZKVC_SERVER_MERGE
+ * adds batching across requests: a worker that finds two or more requests queued takes
+ * the longest prefix of the queue (at most 64 requests) whose batch fits in the largest
+ * free block of the budget and proves it with the batched prover's launch sequence
+ * (zkvc_batch_*: batched NTTs, merged multi-instance MSM runs; run eagerly with default
+ * launch shapes, over the server's own memory); a request alone in the queue takes the
+ * one-proof path as under ZKVC_SERVER_ADAPTIVE.  Results are the same bytes as
+ * zkvc_prove's under every policy.
  *
  * zkvc_server_submit copies X (a x n int8, host) and W (n x b int8, host) and rs (64
  * bytes, host) of key `key` and returns a ticket at once.  zkvc_server_wait blocks up to
@@ -535,6 +541,7 @@ typedef struct zkvc_server zkvc_server;
 #define ZKVC_SERVER_ADAPTIVE 0
 #define ZKVC_SERVER_FOLD 1
 #define ZKVC_SERVER_CHAIN 2
+#define ZKVC_SERVER_MERGE 3
 
 int zkvc_server_create(const zkvc_pk* const* pks, int npk, int slots, size_t mem_budget, int policy,
                        zkvc_server** server);
@@ -545,6 +552,8 @@ int zkvc_server_wait(zkvc_server* server, uint64_t ticket, int timeout_ms, uint8
                      double times_ms[3], int* status);
 int zkvc_server_stats(zkvc_server* server, uint64_t* completed, int* in_flight, int* queued, size_t* bytes_in_use,
                       size_t* peak_bytes, uint64_t* chain_mode);
+/* Requests proven in merged batches, and the batches (ZKVC_SERVER_MERGE), since creation. */
+int zkvc_server_merge_stats(zkvc_server* server, uint64_t* merged_requests, uint64_t* batches);
 size_t zkvc_server_request_bytes(const zkvc_pk* pk, int mode);
 
 /* Diagnostic knob for the bounded device-side waits (the fault handling that a

@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -199,6 +200,8 @@ struct zkvc_batch {
   cudaGraphExec_t graph = nullptr;
   unsigned long long graph_launches = 0;
   bool busy = false;  // a previous call timed out with work in flight
+  bool owns_mem = true;  // false for the proof server's transient batches
+  int cap_count = 0;     // instances the pinned staging holds
   ~zkvc_batch();
 };
 
@@ -216,7 +219,7 @@ zkvc_batch::~zkvc_batch() {
   if (ev_in) cudaEventDestroy(ev_in);
   if (ev_out) cudaEventDestroy(ev_out);
   if (cap) cudaStreamDestroy(cap);
-  if (mem) cudaFree(mem);
+  if (mem && owns_mem) cudaFree(mem);
   if (h_rs) cudaFreeHost(h_rs);
   if (h_flags) cudaFreeHost(h_flags);
   if (h_proofs) cudaFreeHost(h_proofs);
@@ -578,6 +581,44 @@ static int autotune(zkvc_batch* B) {
   return ZKVC_OK;
 }
 
+// Streams, events and pinned staging for up to cap instances.
+static int batch_resources(zkvc_batch* B, int cap) {
+  ZK_CUDA(cudaMallocHost(&B->h_rs, size_t(cap) * 64));
+  ZK_CUDA(cudaMallocHost(&B->h_flags, size_t(cap) * sizeof(int)));
+  ZK_CUDA(cudaMallocHost(&B->h_proofs, size_t(cap) * 256));
+  std::memset(B->h_rs, 0, size_t(cap) * 64);
+  B->cap_count = cap;
+  ZK_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  int lo = 0, hi = 0;
+  ZK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  for (int i = 0; i < 2; i++) {
+    ZK_CUDA(cudaStreamCreateWithPriority(&B->side[i], cudaStreamNonBlocking, hi));
+    ZK_CUDA(cudaEventCreateWithFlags(&B->fork[i], cudaEventDisableTiming));
+    ZK_CUDA(cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming));
+  }
+  ZK_CUDA(cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming));
+  ZK_CUDA(cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming));
+  return ZKVC_OK;
+}
+
+// Per-instance status codes from the device flags (bit 2: r or s not canonical; bit 3: a
+// tensor-core wait timed out; bits 0-1: unsatisfied constraints); returns the first
+// failing instance (-1: none) and its flags.
+static int decode_flags(const int* flags, int n, int* status, int* first_flag) {
+  int first_bad = -1;
+  *first_flag = 0;
+  for (int i = 0; i < n; i++) {
+    const int f = flags[i];
+    const int code = (f & 4) ? ZKVC_EINVAL : (f & 8) ? ZKVC_ETIMEOUT : (f & 3) ? ZKVC_EUNSAT : ZKVC_OK;
+    if (status) status[i] = code;
+    if (code != ZKVC_OK && first_bad < 0) {
+      first_bad = i;
+      *first_flag = f;
+    }
+  }
+  return first_bad;
+}
+
 static int batch_create(const zkvc_pk* const* pks, int count, int flags, zkvc_batch** out) {
   ZK_CHECK(pks && out, ZKVC_EINVAL, "batch: null argument");
   b_matmul_init();  // before any capture
@@ -606,20 +647,7 @@ static int batch_create(const zkvc_pk* const* pks, int count, int flags, zkvc_ba
       return ZKVC_ENOMEM;
     }
     carve(B, false);
-    ZK_CUDA(cudaMallocHost(&B->h_rs, size_t(count) * 64));
-    ZK_CUDA(cudaMallocHost(&B->h_flags, size_t(count) * sizeof(int)));
-    ZK_CUDA(cudaMallocHost(&B->h_proofs, size_t(count) * 256));
-    std::memset(B->h_rs, 0, size_t(count) * 64);
-    ZK_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
-    int lo = 0, hi = 0;
-    ZK_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    for (int i = 0; i < 2; i++) {
-      ZK_CUDA(cudaStreamCreateWithPriority(&B->side[i], cudaStreamNonBlocking, hi));
-      ZK_CUDA(cudaEventCreateWithFlags(&B->fork[i], cudaEventDisableTiming));
-      ZK_CUDA(cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming));
-    }
-    ZK_CUDA(cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming));
-    ZK_CUDA(cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming));
+    ZK_TRY(batch_resources(B, count));
     ZK_CUDA(cudaMemcpyAsync(B->dinst, B->hinst.data(), size_t(count) * sizeof(BInst), cudaMemcpyHostToDevice, B->cap));
     ZK_TRY(ntt_init());
     ZK_TRY(prepare_execs(B, B->cap));
@@ -673,16 +701,8 @@ static int batch_prove(zkvc_batch* B, const int8_t* const* dX, const int8_t* con
   if (rc == ZKVC_ETIMEOUT) B->busy = true;
   ZK_TRY(rc);
   std::memcpy(proofs, B->h_proofs, size_t(n) * 256);
-  int first_bad = -1, first_flag = 0;
-  for (int i = 0; i < n; i++) {
-    int f = B->h_flags[i];
-    int code = (f & 4) ? ZKVC_EINVAL : (f & 8) ? ZKVC_ETIMEOUT : (f & 3) ? ZKVC_EUNSAT : ZKVC_OK;
-    if (status) status[i] = code;
-    if (code != ZKVC_OK && first_bad < 0) {
-      first_bad = i;
-      first_flag = f;
-    }
-  }
+  int first_flag = 0;
+  const int first_bad = decode_flags(B->h_flags, n, status, &first_flag);
   ZK_CHECK(first_bad < 0 || !(first_flag & 4), ZKVC_EINVAL, "batch prove: instance %d: r or s is not a canonical Fr element",
            first_bad);
   ZK_CHECK(first_bad < 0 || !(first_flag & 8), ZKVC_ETIMEOUT, "batch prove: instance %d: a tensor-core wait timed out",
@@ -690,6 +710,88 @@ static int batch_prove(zkvc_batch* B, const int8_t* const* dX, const int8_t* con
   ZK_CHECK(first_bad < 0, ZKVC_EUNSAT, "batch prove: instance %d does not satisfy its constraints (flags %d)", first_bad,
            first_flag);
   return ZKVC_OK;
+}
+
+// ------------------------------------------------------------------ server batches
+// The proof server merges the requests waiting in its queue into one batch: the same
+// launch sequence as above, run eagerly (no capture: every dispatch has a new mix of
+// keys), laid over device memory the server owns (no allocation per dispatch), with the
+// default launch shapes (no autotuning).  One transient batch object per server worker
+// holds the streams, events and pinned staging, for up to `cap` instances.
+int batch_serve_open(int cap, zkvc_batch** out) {
+  ZK_CHECK(out && cap >= 1 && cap <= 4096, ZKVC_EINVAL, "server batch: capacity %d", cap);
+  *out = nullptr;
+  b_matmul_init();
+  ZK_TRY(ntt_init());
+  std::unique_ptr<zkvc_batch> B(new zkvc_batch());
+  ZK_CUDA(cudaGetDevice(&B->device));
+  B->flags = ZKVC_BATCH_EAGER;
+  B->owns_mem = false;
+  ZK_TRY(batch_resources(B.get(), cap));
+  *out = B.release();
+  return ZKVC_OK;
+}
+
+// Device bytes of a batch of these keys (host computation only).
+size_t batch_serve_bytes(const zkvc_pk* const* pks, int count) {
+  zkvc_batch B;
+  B.owns_mem = false;
+  cudaGetDevice(&B.device);
+  B.pks.assign(pks, pks + count);
+  B.count = count;
+  return carve(&B, true);
+}
+
+// Proves count requests of the given keys as one batch over [mem, mem + mem_bytes): host
+// X (a x n), W (n x b) and r || s in, host Y (a x b) and proofs (256 bytes each) out,
+// status[i] per instance.  Returns ZKVC_ETIMEOUT with work possibly still in flight (the
+// memory must not be reused until the object's next call has drained it).
+int batch_serve_run(zkvc_batch* B, const zkvc_pk* const* pks, int count, uint8_t* mem, size_t mem_bytes,
+                    const int8_t* const* hX, const int8_t* const* hW, const uint8_t* rs, int32_t* const* hY,
+                    uint8_t* proofs, int* status) {
+  ZK_CHECK(count >= 1 && count <= B->cap_count, ZKVC_EINVAL, "server batch: %d instances, capacity %d", count,
+           B->cap_count);
+  if (B->busy) {
+    ZK_TRY(wait_stream(B->cap, "server batch (previous call)"));
+    B->busy = false;
+  }
+  B->pks.assign(pks, pks + count);
+  B->count = count;
+  B->mem = nullptr;
+  const size_t need = carve(B, true);
+  ZK_CHECK(need <= mem_bytes, ZKVC_ENOMEM, "server batch: %zu bytes needed, %zu given", need, mem_bytes);
+  B->mem = mem;
+  B->mem_bytes = mem_bytes;
+  carve(B, false);
+  B->tune = BatchTune();
+  B->tuned = true;
+  cudaStream_t st = B->cap;
+  ZK_CUDA(cudaMemcpyAsync(B->dinst, B->hinst.data(), size_t(count) * sizeof(BInst), cudaMemcpyHostToDevice, st));
+  ZK_TRY(prepare_execs(B, st));
+  for (int i = 0; i < count; i++) {
+    const Shape& sh = pks[i]->shape;
+    ZK_CUDA(cudaMemcpyAsync(B->X + B->xo[i], hX[i], size_t(sh.a) * sh.n, cudaMemcpyHostToDevice, st));
+    ZK_CUDA(cudaMemcpyAsync(B->W + B->wo[i], hW[i], size_t(sh.n) * sh.b, cudaMemcpyHostToDevice, st));
+  }
+  std::memcpy(B->h_rs, rs, size_t(count) * 64);
+  ZK_TRY(enqueue(B));
+  for (int i = 0; i < count; i++) {
+    const Shape& sh = pks[i]->shape;
+    ZK_CUDA(cudaMemcpyAsync(hY[i], B->Y + B->yo[i], size_t(sh.a) * sh.b * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            st));
+  }
+  const int rc = wait_stream(st, "server batch");
+  if (rc == ZKVC_ETIMEOUT) B->busy = true;
+  ZK_TRY(rc);
+  std::memcpy(proofs, B->h_proofs, size_t(count) * 256);
+  int first_flag = 0;
+  decode_flags(B->h_flags, count, status, &first_flag);
+  return ZKVC_OK;
+}
+
+void batch_serve_drain(zkvc_batch* B) {
+  if (B && B->cap) cudaStreamSynchronize(B->cap);
+  if (B) B->busy = false;
 }
 
 static int device_guard_batch(int dev) {

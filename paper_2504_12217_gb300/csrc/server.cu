@@ -13,6 +13,11 @@
 // Mode policy: a request admitted onto an otherwise idle GPU uses the fold prover
 // (lowest latency); one admitted beside others uses the chain prover (about 2.5x less
 // MSM work), which raises throughput when proofs share the GPU.  Both give the same bytes.
+// The merge policy goes further: a worker that finds two or more requests waiting takes
+// the longest prefix of the queue whose batch fits in the largest free block (up to
+// merge_max requests) and proves it as one batch (batch.cu: one witness launch for all,
+// batched NTTs, merged multi-instance MSM runs), so that the GPU runs few large kernels
+// instead of many small ones; a lone request still takes the one-proof path.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -33,6 +38,12 @@ size_t prove_workspace_bytes(const zkvc_pk* pk, int mode);
 int prove_enqueue(const zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, const uint8_t* rs_host,
                   int32_t* dY, void* ws, size_t ws_bytes, uint8_t* proof_out, int* flags_out, cudaStream_t st);
 int prove_status(int flags);
+int batch_serve_open(int cap, zkvc_batch** out);
+size_t batch_serve_bytes(const zkvc_pk* const* pks, int count);
+int batch_serve_run(zkvc_batch* B, const zkvc_pk* const* pks, int count, uint8_t* mem, size_t mem_bytes,
+                    const int8_t* const* hX, const int8_t* const* hW, const uint8_t* rs, int32_t* const* hY,
+                    uint8_t* proofs, int* status);
+void batch_serve_drain(zkvc_batch* B);
 
 // First-fit allocator over [0, cap) in 256-byte units, with coalescing of free blocks.
 class ArenaAlloc {
@@ -76,6 +87,11 @@ class ArenaAlloc {
     }
   }
   size_t used() const { return used_; }
+  size_t largest() const {
+    size_t m = 0;
+    for (const auto& kv : free_) m = std::max(m, kv.second);
+    return m;
+  }
   size_t cap() const { return cap_; }
 
  private:
@@ -117,7 +133,9 @@ struct zkvc_server {
   std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
   uint64_t next_id = 1;
   int in_flight = 0;
-  uint64_t completed = 0, chain_count = 0;
+  uint64_t completed = 0, chain_count = 0, merged_count = 0, batch_count = 0;
+  int merge_max = 64;
+  std::vector<size_t> fp_batch;  // device bytes of a one-request batch per key (merge policy)
   bool stop = false;
   std::vector<std::thread> workers;
   std::string fatal;  // set if a worker could not start
@@ -145,8 +163,67 @@ struct WorkerRes {
   }
 };
 
+struct BatchFree {
+  void operator()(zkvc_batch* b) const { zkvc_batch_free(b); }
+};
+
+// Proves the requests grp (keys kp) as one batch over [off, off + bytes) of the arena and
+// completes them.
+static void run_merged(zkvc_server* S, zkvc_batch* MB, std::vector<Request*>& grp,
+                       const std::vector<const zkvc_pk*>& kp, size_t off, size_t bytes) {
+  const int m = (int)grp.size();
+  const auto t_admit = Clock::now();
+  std::vector<const int8_t*> hx(m), hw(m);
+  std::vector<int32_t*> hy(m);
+  std::vector<uint8_t> rs(size_t(m) * 64), proofs(size_t(m) * 256);
+  std::vector<int> st(m, ZKVC_OK);
+  for (int i = 0; i < m; i++) {
+    Request* q = grp[i];
+    const Shape& sh = kp[i]->shape;
+    q->t_admit = t_admit;
+    q->mode = -1;
+    q->Y.resize(size_t(sh.a) * sh.b);
+    hx[i] = q->X.data();
+    hw[i] = q->W.data();
+    hy[i] = q->Y.data();
+    std::memcpy(rs.data() + size_t(i) * 64, q->rs, 64);
+  }
+  const int rc = batch_serve_run(MB, kp.data(), m, S->arena + off, bytes, hx.data(), hw.data(), rs.data(),
+                                 hy.data(), proofs.data(), st.data());
+  const std::string err = rc != ZKVC_OK ? last_error_text() : std::string();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (rc != ZKVC_ETIMEOUT) S->alloc.release(off, bytes);
+    S->in_flight -= m;
+    S->completed += m;
+    const auto t_done = Clock::now();
+    for (int i = 0; i < m; i++) {
+      Request* q = grp[i];
+      q->status = rc != ZKVC_OK ? rc : st[i];
+      if (q->status == ZKVC_OK)
+        std::memcpy(q->proof, proofs.data() + size_t(i) * 256, 256);
+      else
+        q->err = rc != ZKVC_OK ? err
+                 : q->status == ZKVC_EUNSAT ? std::string("server: the request does not satisfy its constraints")
+                 : q->status == ZKVC_EINVAL ? std::string("server: r or s is not a canonical Fr element")
+                                            : std::string("server: a tensor-core wait timed out");
+      q->done = true;
+      q->t_done = t_done;
+    }
+  }
+  S->cv_work.notify_all();
+  S->cv_done.notify_all();
+  if (rc == ZKVC_ETIMEOUT) {  // the batch's streams may still run: drain before the memory is reused
+    batch_serve_drain(MB);
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->alloc.release(off, bytes);
+    S->cv_work.notify_all();
+  }
+}
+
 static void worker_main(zkvc_server* S) {
   WorkerRes R;
+  std::unique_ptr<zkvc_batch, BatchFree> MB;
   size_t max_x = 0, max_w = 0, max_y = 0;
   for (const zkvc_pk* pk : S->pks) {
     max_x = std::max(max_x, size_t(pk->shape.a) * pk->shape.n);
@@ -158,6 +235,11 @@ static void worker_main(zkvc_server* S) {
   bool ok = cudaSetDevice(S->device) == cudaSuccess &&
             cudaStreamCreateWithFlags(&R.st, cudaStreamNonBlocking) == cudaSuccess &&
             cudaMallocHost(&R.hx, R.hx_bytes) == cudaSuccess;
+  if (ok && S->policy == ZKVC_SERVER_MERGE) {
+    zkvc_batch* b = nullptr;
+    ok = batch_serve_open(S->merge_max, &b) == ZKVC_OK;
+    MB.reset(b);
+  }
   if (!ok) {
     cudaGetLastError();
     std::lock_guard<std::mutex> lk(S->mu);
@@ -169,15 +251,51 @@ static void worker_main(zkvc_server* S) {
     Request* q = nullptr;
     size_t off = 0, fp = 0;
     int mode = ZKVC_PROVE_FOLD;
+    std::vector<Request*> grp;
+    std::vector<const zkvc_pk*> kp;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       for (;;) {
         if (S->stop) return;
+        if (MB && S->queue.size() >= 2) {
+          // the longest queue prefix (up to merge_max) whose estimate fits the largest free
+          // block, then its exact size; shorter prefixes if that does not fit
+          const size_t largest = S->alloc.largest();
+          size_t est = 0;
+          kp.clear();
+          for (Request* h : S->queue) {
+            if ((int)kp.size() == S->merge_max) break;
+            const size_t f = S->fp_batch[h->key];
+            if (est + f > largest) break;
+            est += f;
+            kp.push_back(S->pks[h->key]);
+          }
+          while (kp.size() >= 2) {
+            const size_t exact = batch_serve_bytes(kp.data(), (int)kp.size());
+            if (S->alloc.alloc(exact, &off)) {
+              fp = exact;
+              break;
+            }
+            kp.pop_back();
+          }
+          if (kp.size() >= 2) {
+            for (size_t i = 0; i < kp.size(); i++) {
+              grp.push_back(S->queue.front());
+              S->queue.pop_front();
+            }
+            S->in_flight += (int)grp.size();
+            S->merged_count += grp.size();
+            S->batch_count++;
+            S->peak_used = std::max(S->peak_used, S->alloc.used());
+            break;
+          }
+          kp.clear();
+        }
         if (!S->queue.empty()) {
           Request* h = S->queue.front();
           mode = S->policy == ZKVC_SERVER_FOLD    ? ZKVC_PROVE_FOLD
                  : S->policy == ZKVC_SERVER_CHAIN ? ZKVC_PROVE_CHAIN
-                 : (S->in_flight == 0 ? ZKVC_PROVE_FOLD : ZKVC_PROVE_CHAIN);
+                 : (S->in_flight == 0 ? ZKVC_PROVE_FOLD : ZKVC_PROVE_CHAIN);  // adaptive, merge
           fp = mode == ZKVC_PROVE_CHAIN ? S->fp_chain[h->key] : S->fp_fold[h->key];
           if (fp > S->alloc.cap() && mode == ZKVC_PROVE_FOLD) {
             mode = ZKVC_PROVE_CHAIN;  // the chain prover needs less workspace
@@ -203,6 +321,10 @@ static void worker_main(zkvc_server* S) {
         }
         S->cv_work.wait(lk);
       }
+    }
+    if (!grp.empty()) {
+      run_merged(S, MB.get(), grp, kp, off, fp);
+      continue;
     }
     q->t_admit = Clock::now();
     q->mode = mode;
@@ -286,8 +408,9 @@ int zkvc_server_create(const zkvc_pk* const* pks, int npk, int slots, size_t mem
   *out = nullptr;
   ZK_CHECK(npk >= 1, ZKVC_EINVAL, "server: no keys");
   ZK_CHECK(slots >= 1 && slots <= 64, ZKVC_EINVAL, "server: %d slots outside [1, 64]", slots);
-  ZK_CHECK(policy == ZKVC_SERVER_ADAPTIVE || policy == ZKVC_SERVER_FOLD || policy == ZKVC_SERVER_CHAIN, ZKVC_EINVAL,
-           "server: policy %d", policy);
+  ZK_CHECK(policy == ZKVC_SERVER_ADAPTIVE || policy == ZKVC_SERVER_FOLD || policy == ZKVC_SERVER_CHAIN ||
+               policy == ZKVC_SERVER_MERGE,
+           ZKVC_EINVAL, "server: policy %d", policy);
   ZK_CHECK(mem_budget >= (1u << 20), ZKVC_EINVAL, "server: budget of %zu bytes", mem_budget);
   int dev = 0;
   ZK_CUDA(cudaGetDevice(&dev));
@@ -311,6 +434,7 @@ int zkvc_server_create(const zkvc_pk* const* pks, int npk, int slots, size_t mem
   for (const zkvc_pk* pk : S->pks) {
     S->fp_fold.push_back(footprint(pk, ZKVC_PROVE_FOLD));
     S->fp_chain.push_back(footprint(pk, ZKVC_PROVE_CHAIN));
+    if (policy == ZKVC_SERVER_MERGE) S->fp_batch.push_back(batch_serve_bytes(&pk, 1));
   }
   for (int i = 0; i < slots; i++) S->workers.emplace_back(worker_main, S.get());
   *out = S.release();
@@ -388,6 +512,15 @@ int zkvc_server_stats(zkvc_server* s, uint64_t* completed, int* in_flight, int* 
   if (bytes_in_use) *bytes_in_use = s->alloc.used();
   if (peak_bytes) *peak_bytes = s->peak_used;
   if (chain_mode) *chain_mode = s->chain_count;
+  return ZKVC_OK;
+}
+
+int zkvc_server_merge_stats(zkvc_server* s, uint64_t* merged_requests, uint64_t* batches) {
+  set_error("%s", "");
+  ZK_CHECK(s, ZKVC_EINVAL, "server merge stats: null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (merged_requests) *merged_requests = s->merged_count;
+  if (batches) *batches = s->batch_count;
   return ZKVC_OK;
 }
 

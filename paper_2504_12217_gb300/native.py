@@ -104,6 +104,7 @@ SIGNATURES = {
                                    ctypes.POINTER(_c_int), ctypes.POINTER(_c_sz), ctypes.POINTER(_c_sz),
                                    ctypes.POINTER(ctypes.c_uint64)]),
     "zkvc_server_request_bytes": (_c_sz, [_c_p, _c_int]),
+    "zkvc_server_merge_stats": (_c_int, [_c_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 ZKVC_Q_A, ZKVC_Q_B1, ZKVC_Q_B2, ZKVC_Q_L, ZKVC_Q_H = 0, 1, 2, 3, 4
@@ -729,6 +730,7 @@ def zkvc_prove_batch(pks, Xs, Ws, rs_list):
 ZKVC_SERVER_ADAPTIVE = 0
 ZKVC_SERVER_FOLD = 1
 ZKVC_SERVER_CHAIN = 2
+ZKVC_SERVER_MERGE = 3
 
 
 def zkvc_server_request_bytes(pk, mode):
@@ -789,8 +791,10 @@ class Server:
         c, f, q, u, p, ch = ctypes.c_uint64(), _c_int(), _c_int(), _c_sz(), _c_sz(), ctypes.c_uint64()
         check(lib().zkvc_server_stats(self.handle, ctypes.byref(c), ctypes.byref(f), ctypes.byref(q), ctypes.byref(u),
                                       ctypes.byref(p), ctypes.byref(ch)))
+        mr, nb = ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib().zkvc_server_merge_stats(self.handle, ctypes.byref(mr), ctypes.byref(nb)))
         return {"completed": c.value, "in_flight": f.value, "queued": q.value, "bytes_in_use": u.value,
-                "peak_bytes": p.value, "chain_mode": ch.value}
+                "peak_bytes": p.value, "chain_mode": ch.value, "merged_requests": mr.value, "merged_batches": nb.value}
 
 
 # ------------------------------------------------------------------ GPU verification

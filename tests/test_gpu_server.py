@@ -1,8 +1,9 @@
 """GPU parity of the chain-mode prover and of the proof server: every proof equals the
 oracle's (small shapes) and the one-proof fold prover's; a request's result is the same
-alone and in a mix of concurrent requests of other shapes; memory admission never lets
-the requests in flight exceed the budget; a request that can never fit, a bad key index
-and a bad (r, s) are reported per request; waits are bounded."""
+alone and in a mix of concurrent requests of other shapes, under every policy (the merge
+policy proves queued requests together as one batch); memory admission never lets the
+requests in flight exceed the budget; a request that can never fit, a bad key index and
+a bad (r, s) are reported per request, also inside a merged batch; waits are bounded."""
 import threading
 
 import numpy as np
@@ -74,11 +75,12 @@ def test_chain_mode_config2(nv):
     assert nv.zkvc_verify(vk, inst["X"], Y.cpu().numpy(), proof)
 
 
-@pytest.mark.parametrize("policy", [0, 1, 2])
+@pytest.mark.parametrize("policy", [0, 1, 2, 3])
 def test_server_mix_equals_alone(nv, keys, policy):
     """Requests of all shapes submitted from two threads at once; each result equals the
-    oracle's proof and Y for the same inputs."""
-    srv = nv.Server([k[0] for k in keys], slots=4, mem_budget=256 << 20, policy=policy)
+    oracle's proof and Y for the same inputs.  Under the merge policy one worker takes the
+    first request alone and the rest queue behind it, so most are proven in merged batches."""
+    srv = nv.Server([k[0] for k in keys], slots=1 if policy == 3 else 4, mem_budget=256 << 20, policy=policy)
     reqs = [(i % len(SHAPES), _request(900 + 31 * i + policy, SHAPES[i % len(SHAPES)])) for i in range(24)]
     tickets = [None] * len(reqs)
 
@@ -106,6 +108,40 @@ def test_server_mix_equals_alone(nv, keys, policy):
         assert st["chain_mode"] == 0
     if policy == nv.ZKVC_SERVER_CHAIN:
         assert st["chain_mode"] == len(reqs)
+    if policy == nv.ZKVC_SERVER_MERGE:
+        assert st["merged_requests"] >= 2 and st["merged_batches"] >= 1
+    else:
+        assert st["merged_requests"] == 0
+    srv.close()
+
+
+def test_server_merge_status_and_admission(nv, keys):
+    """Merge policy: a bad (r, s) inside a merged batch fails its own request only; with a
+    budget that holds one request of the largest shape (as a one-request batch), batches
+    shrink to what fits and everything completes within the budget."""
+    srv = nv.Server([k[0] for k in keys], slots=1, mem_budget=256 << 20, policy=nv.ZKVC_SERVER_MERGE)
+    reqs = [(i % len(SHAPES), _request(700 + i, SHAPES[i % len(SHAPES)])) for i in range(12)]
+    tickets = []
+    for i, (k, (X, W, rs)) in enumerate(reqs):
+        tickets.append(srv.submit(k, X, W, inputs.to_bytes32([bn.R, 1] if i == 7 else rs)))
+    for i, (t, (k, (X, W, rs))) in enumerate(zip(tickets, reqs)):
+        status, proof, _, _ = srv.wait(t, k)
+        if i == 7:
+            assert status == nv.ZKVC_EINVAL and proof is None
+        else:
+            assert status == nv.ZKVC_OK and proof == _oracle(SHAPES[k], keys[k][2], X, W, rs)[0], i
+    assert srv.stats()["merged_requests"] >= 2
+    srv.close()
+    big = max(range(len(SHAPES)), key=lambda k: nv.zkvc_server_request_bytes(keys[k][0], nv.ZKVC_PROVE_FOLD))
+    budget = 3 * nv.zkvc_server_request_bytes(keys[big][0], nv.ZKVC_PROVE_FOLD) + (1 << 20)
+    srv = nv.Server([k[0] for k in keys], slots=2, mem_budget=budget, policy=nv.ZKVC_SERVER_MERGE)
+    reqs = [(big, _request(750 + i, SHAPES[big])) for i in range(10)]
+    tickets = [srv.submit(k, X, W, inputs.to_bytes32(rs)) for k, (X, W, rs) in reqs]
+    for t, (k, (X, W, rs)) in zip(tickets, reqs):
+        status, proof, _, _ = srv.wait(t, k)
+        assert status == nv.ZKVC_OK and proof == _oracle(SHAPES[k], keys[k][2], X, W, rs)[0]
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["bytes_in_use"] == 0 and st["peak_bytes"] <= budget
     srv.close()
 
 
@@ -157,13 +193,15 @@ def test_server_rejections_and_timeouts(nv, keys):
     srv.close()
 
 
-def test_server_config4_shapes(nv):
+@pytest.mark.parametrize("policy", [0, 3])
+def test_server_config4_shapes(nv, policy):
     """Three [tokens, dim] x [dim, *] shapes of the served workload at full size, 12
-    requests in flight together: each proof equals the one-proof prover's on its own."""
+    requests in flight together (merge policy: in merged batches of mixed shapes): each
+    proof equals the one-proof prover's on its own."""
     import torch
     shapes = [(49, 192, 192), (64, 192, 768), (49, 320, 320)]
     pks = [nv.zkvc_setup(*s, inputs.to_bytes32(inputs.setup_values(8000 + i)))[0] for i, s in enumerate(shapes)]
-    srv = nv.Server(pks, slots=4, mem_budget=8 << 30)
+    srv = nv.Server(pks, slots=1 if policy == 3 else 4, mem_budget=8 << 30, policy=policy)
     reqs = []
     for i in range(12):
         k = i % 3
@@ -176,4 +214,6 @@ def test_server_config4_shapes(nv):
         alone, Ya = nv.zkvc_prove(pks[k], torch.from_numpy(X).cuda(), torch.from_numpy(W).cuda(), rs)
         assert proof == alone
         assert np.array_equal(Y, Ya.cpu().numpy())
+    if policy == 3:
+        assert srv.stats()["merged_requests"] >= 2
     srv.close()
