@@ -183,12 +183,14 @@ static uint32_t window_bits(size_t n) {
   return (uint32_t)c;
 }
 
-// G1 takes the GLV split: s P = k1 P + k2 phi(P) with |k1|, |k2| < 2^127, so the run has
-// 2n points of 127-bit scalars: as many bucket terms as n points of 254-bit scalars, but
-// half the windows, hence half the buckets to reduce and half of Horner's chain of
-// doublings over the windows (the latency-bound tail of a variable-base MSM).
+// Both groups take a two-way endomorphism split of every scalar (glv.h): in G1
+// s P = k1 P + k2 phi(P) (GLV, |k1|, |k2| < 2^127), in G2 s Q = k1 Q + k2 psi(Q)
+// (k1, k2 in [0, 2^127)).  The run then has 2n points of 127-bit scalars: as many bucket
+// terms as n points of 254-bit scalars, but half the windows, hence half the buckets to
+// reduce and half of Horner's chain of doublings over the windows (the latency-bound
+// tail of a variable-base MSM).
 template <class F>
-constexpr bool msm_api_glv() { return sizeof(F) == sizeof(Fp); }
+constexpr bool msm_api_glv() { return true; }
 
 static MsmPlan variable_base_plan(size_t n, const void* scalars, bool glv) {
   MsmPlan p;
@@ -226,16 +228,21 @@ size_t msm_api_ws(size_t n) {
 // halves[i], halves[n + i] = the GLV halves k1, k2 of s_i (reduced mod r first)
 __global__ void k_glv_prep(const Affine<Fp>* __restrict__ pts, const Fr* __restrict__ sc, size_t n,
                            Affine<Fp>* bases, uint4* halves) {
+  __shared__ Fp beta_m;  // beta in Montgomery form, converted once per block
+  if (threadIdx.x == 0) {
+    Fp beta;
+#pragma unroll
+    for (int l = 0; l < 8; l++) beta.v[l] = glv_beta_limb(l);
+    beta_m = f_to_mont(beta);
+  }
+  __syncthreads();
   const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   Affine<Fp> p = ld_field(pts + i);
   p.x = f_to_mont(p.x);
   p.y = f_to_mont(p.y);
-  Fp beta;
-#pragma unroll
-  for (int l = 0; l < 8; l++) beta.v[l] = glv_beta_limb(l);
   Affine<Fp> q;
-  q.x = f_mul(p.x, f_to_mont(beta));
+  q.x = f_mul(p.x, beta_m);
   q.y = p.y;
   st_field(bases + i, p);
   st_field(bases + n + i, q);
@@ -249,6 +256,51 @@ __global__ void k_glv_prep(const Affine<Fp>* __restrict__ pts, const Fr* __restr
   }
   uint4 h1, h2;
   glv_split_dev(k.v, &h1, &h2);
+  halves[i] = h1;
+  halves[n + i] = h2;
+}
+
+// bases[i] = Q_i and bases[n + i] = psi(Q_i) = (conj(x_i) gx, conj(y_i) gy) in Montgomery
+// form; halves[i], halves[n + i] = k1, k2 of s_i = k1 + k2 lambda2 (reduced mod r first)
+__global__ void k_psi_prep(const Affine<Fp2>* __restrict__ pts, const Fr* __restrict__ sc, size_t n,
+                           Affine<Fp2>* bases, uint4* halves) {
+  __shared__ Fp2 g_m[2];  // gx, gy in Montgomery form, converted once per block
+  if (threadIdx.x == 0) {
+    Fp2 gx, gy;
+#pragma unroll
+    for (int l = 0; l < 8; l++) {
+      gx.c0.v[l] = psi_gx_limb(0, l);
+      gx.c1.v[l] = psi_gx_limb(1, l);
+      gy.c0.v[l] = psi_gy_limb(0, l);
+      gy.c1.v[l] = psi_gy_limb(1, l);
+    }
+    g_m[0] = f_to_mont(gx);
+    g_m[1] = f_to_mont(gy);
+  }
+  __syncthreads();
+  const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Affine<Fp2> p = ld_field(pts + i);
+  p.x = f_to_mont(p.x);
+  p.y = f_to_mont(p.y);
+  Affine<Fp2> q;
+  Fp2 cx = p.x, cy = p.y;
+  cx.c1 = f_neg(cx.c1);
+  cy.c1 = f_neg(cy.c1);
+  q.x = f_mul(cx, g_m[0]);
+  q.y = f_mul(cy, g_m[1]);
+  st_field(bases + i, p);
+  st_field(bases + n + i, q);
+  Fr k = ld_field(sc + i);
+  const Fr r = Fr::modulus();
+  for (int t = 0; t < 6; t++) {  // 2^256 < 6 r
+    uint32_t d[8];
+    if (sub8(d, k.v, r.v)) break;
+#pragma unroll
+    for (int l = 0; l < 8; l++) k.v[l] = d[l];
+  }
+  uint4 h1, h2;
+  psi_split_dev(k.v, &h1, &h2);
   halves[i] = h1;
   halves[n + i] = h2;
 }
@@ -276,8 +328,11 @@ int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d
   Affine<F>* aff = a.take<Affine<F>>(1);
   uint8_t* rest = a.base + a.off;
   size_t rest_bytes = ws_bytes - a.off;
-  if constexpr (glv) {
+  if constexpr (glv && sizeof(F) == sizeof(Fp)) {
     k_glv_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const Affine<Fp>*>(d_points),
+                                                             reinterpret_cast<const Fr*>(d_scalars), n, bases, halves);
+  } else if constexpr (glv) {
+    k_psi_prep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const Affine<Fp2>*>(d_points),
                                                              reinterpret_cast<const Fr*>(d_scalars), n, bases, halves);
   } else {
     k_points_to_mont<F><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(

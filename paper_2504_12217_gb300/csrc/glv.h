@@ -33,6 +33,31 @@ constexpr uint64_t GLV_B2 = 0x89d3256894d213e3ull;                              
 constexpr uint64_t GLV_G1[2] = {0xd91d232ec7e0b3d7ull, 0x2ull};                  // g1
 constexpr uint64_t GLV_G2[3] = {0x7a7bd9d4391eb18dull, 0x4ccef014a773d2cfull, 0x2ull};  // g2
 
+// G2 has the endomorphism psi = (twist)^-1 o Frobenius o twist: for the D-type twist
+// y^2 = x^3 + 3/xi (xi = 9 + i) it is psi(x, y) = (conj(x) gx, conj(y) gy) with
+// gx = xi^((p-1)/3) and gy = xi^((p-1)/2) in Fp2, and on the order-r subgroup it acts as
+// multiplication by lambda2 = p mod r = 6 u^2 (a 127-bit number close to sqrt(r)).  A
+// scalar k < r therefore splits as k = k1 + k2 lambda2 with k2 = floor(k / lambda2) and
+// k1 = k mod lambda2, both non-negative and below 2^127 (k2 <= (r - 1) / lambda2 =
+// 6u^2 + 6u + 3).  The quotient is k g / 2^256 (g = floor(2^256 / lambda2)), low by at
+// most one, then corrected.  Checked by a CPU test against the oracle's G2 arithmetic.
+constexpr uint64_t PSI_LAMBDA[2] = {0xf83e9682e87cfd46ull, 0x6f4d8248eeb859fbull};  // 6 u^2
+constexpr uint64_t PSI_G[3] = {0x2cb62031c8e01941ull, 0x4ccef014a773d2d5ull, 0x2ull};  // floor(2^256 / (6 u^2))
+// gx (c = 0: real part, 1: imaginary part), canonical little-endian 32-bit limbs
+__host__ __device__ constexpr uint32_t psi_gx_limb(int c, int i) {
+  constexpr uint32_t v[2][8] = {
+      {0x176f553du, 0x99e39557u, 0xc2c3330cu, 0xb78cc310u, 0xf559b143u, 0x4c0bec3cu, 0x4f7911f7u, 0x2fb34798u},
+      {0x640fcba2u, 0x1665d51cu, 0x0b7c9dceu, 0x32ae2a1du, 0xd75a0794u, 0x4ba4cc8bu, 0x61ebae20u, 0x16c9e550u}};
+  return v[c][i];
+}
+// gy
+__host__ __device__ constexpr uint32_t psi_gy_limb(int c, int i) {
+  constexpr uint32_t v[2][8] = {
+      {0x71a0135au, 0xdc540146u, 0xa9c95998u, 0xdbaae0edu, 0xb6e2f9b9u, 0xdc5ec698u, 0x489af5dcu, 0x063cf305u},
+      {0x2623b0e3u, 0x82d37f63u, 0x8fa25bd2u, 0x21807dc9u, 0xec796f2bu, 0x0704b5a7u, 0xac41049au, 0x07c03cbcu}};
+  return v[c][i];
+}
+
 // One half of a split scalar: |k_i| as four 32-bit limbs and its sign.
 struct GlvHalf {
   uint32_t mag[4];
@@ -217,6 +242,29 @@ __device__ __forceinline__ void glv_split_dev(const uint32_t k32[8], uint4* h1, 
   mul192(c1, b1, k2);
   mul192(c2, b2, t);
   sub192(k2, t);
+  *h1 = pack(k1);
+  *h2 = pack(k2);
+}
+// The G2 split k = k1 + k2 lambda2 (both halves non-negative, sign bits 0).
+__device__ __forceinline__ void psi_split_dev(const uint32_t k32[8], uint4* h1, uint4* h2) {
+  using namespace glv_dev;
+  const uint64_t g[3] = {PSI_G[0], PSI_G[1], PSI_G[2]}, lam[2] = {PSI_LAMBDA[0], PSI_LAMBDA[1]};
+  uint64_t k[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) k[i] = uint64_t(k32[2 * i]) | (uint64_t(k32[2 * i + 1]) << 32);
+  uint64_t q[2], t[3];
+  mul_shift256(k, g, q);  // floor(k / lambda2) or one less
+  uint64_t k1[3] = {k[0], k[1], k[2]};  // k - q lambda2 < 2 lambda2 (mod 2^192)
+  mul192(q, lam, t);
+  sub192(k1, t);
+  const uint64_t lam3[3] = {lam[0], lam[1], 0};
+  const bool ge = k1[2] != 0 || k1[1] > lam[1] || (k1[1] == lam[1] && k1[0] >= lam[0]);
+  if (ge) {
+    sub192(k1, lam3);
+    q[0] += 1;
+    q[1] += q[0] == 0;
+  }
+  uint64_t k2[3] = {q[0], q[1], 0};
   *h1 = pack(k1);
   *h2 = pack(k2);
 }
