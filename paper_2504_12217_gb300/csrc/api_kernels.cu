@@ -228,21 +228,16 @@ size_t msm_api_ws(size_t n) {
 // halves[i], halves[n + i] = the GLV halves k1, k2 of s_i (reduced mod r first)
 __global__ void k_glv_prep(const Affine<Fp>* __restrict__ pts, const Fr* __restrict__ sc, size_t n,
                            Affine<Fp>* bases, uint4* halves) {
-  __shared__ Fp beta_m;  // beta in Montgomery form, converted once per block
-  if (threadIdx.x == 0) {
-    Fp beta;
-#pragma unroll
-    for (int l = 0; l < 8; l++) beta.v[l] = glv_beta_limb(l);
-    beta_m = f_to_mont(beta);
-  }
-  __syncthreads();
   const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   Affine<Fp> p = ld_field(pts + i);
   p.x = f_to_mont(p.x);
   p.y = f_to_mont(p.y);
+  Fp beta;
+#pragma unroll
+  for (int l = 0; l < 8; l++) beta.v[l] = glv_beta_limb(l);
   Affine<Fp> q;
-  q.x = f_mul(p.x, beta_m);
+  q.x = f_mul(p.x, f_to_mont(beta));
   q.y = p.y;
   st_field(bases + i, p);
   st_field(bases + n + i, q);
@@ -264,31 +259,25 @@ __global__ void k_glv_prep(const Affine<Fp>* __restrict__ pts, const Fr* __restr
 // form; halves[i], halves[n + i] = k1, k2 of s_i = k1 + k2 lambda2 (reduced mod r first)
 __global__ void k_psi_prep(const Affine<Fp2>* __restrict__ pts, const Fr* __restrict__ sc, size_t n,
                            Affine<Fp2>* bases, uint4* halves) {
-  __shared__ Fp2 g_m[2];  // gx, gy in Montgomery form, converted once per block
-  if (threadIdx.x == 0) {
-    Fp2 gx, gy;
-#pragma unroll
-    for (int l = 0; l < 8; l++) {
-      gx.c0.v[l] = psi_gx_limb(0, l);
-      gx.c1.v[l] = psi_gx_limb(1, l);
-      gy.c0.v[l] = psi_gy_limb(0, l);
-      gy.c1.v[l] = psi_gy_limb(1, l);
-    }
-    g_m[0] = f_to_mont(gx);
-    g_m[1] = f_to_mont(gy);
-  }
-  __syncthreads();
   const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   Affine<Fp2> p = ld_field(pts + i);
   p.x = f_to_mont(p.x);
   p.y = f_to_mont(p.y);
+  Fp2 gx, gy;
+#pragma unroll
+  for (int l = 0; l < 8; l++) {
+    gx.c0.v[l] = psi_gx_limb(0, l);
+    gx.c1.v[l] = psi_gx_limb(1, l);
+    gy.c0.v[l] = psi_gy_limb(0, l);
+    gy.c1.v[l] = psi_gy_limb(1, l);
+  }
   Affine<Fp2> q;
   Fp2 cx = p.x, cy = p.y;
   cx.c1 = f_neg(cx.c1);
   cy.c1 = f_neg(cy.c1);
-  q.x = f_mul(cx, g_m[0]);
-  q.y = f_mul(cy, g_m[1]);
+  q.x = f_mul(cx, f_to_mont(gx));
+  q.y = f_mul(cy, f_to_mont(gy));
   st_field(bases + i, p);
   st_field(bases + n + i, q);
   Fr k = ld_field(sc + i);
