@@ -405,12 +405,13 @@ def ntt_roofline(nv, prof, log_n_proof, imad_peak, hbm_peak, hbm_src):
 
 def msm_work(group, logn):
     """IMAD-equivalents of the library's variable-base MSM of 2^logn points, and its window
-    bits c (window rule: log2(points) - 3, within [4, 16]).  Both groups run an
-    endomorphism split (G1: GLV with phi, G2: psi): 2N points of 127-bit scalars, 2N
-    ceil(128/c) mixed additions and 2^c ceil(128/c) full additions for the bucket sums."""
+    bits c (window rule: log2(points) - 3 within [4, 16], then the smallest c with the
+    same window count).  Both groups run an endomorphism split (G1: GLV with phi, G2:
+    psi): 2N points of 127-bit scalars, 2N ceil(128/c) mixed additions and 2^c
+    ceil(128/c) full additions for the bucket sums."""
     pts_log, bits = logn + 1, 128
-    c = min(16, max(4, pts_log - 3))
-    win = -(-bits // c)
+    win = -(-bits // min(16, max(4, pts_log - 3)))
+    c = -(-bits // win)
     madd = G1_MADD_PRODUCTS if group == 1 else G2_MADD_PRODUCTS
     add = 14 if group == 1 else 42
     return ((1 << pts_log) * win * madd + (1 << c) * win * add) * MONT_IMAD, c

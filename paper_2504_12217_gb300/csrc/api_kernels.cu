@@ -195,10 +195,14 @@ constexpr bool msm_api_glv() { return true; }
 static MsmPlan variable_base_plan(size_t n, const void* scalars, bool glv) {
   MsmPlan p;
   const size_t pts = glv ? 2 * n : n;
-  const uint32_t c = window_bits(pts);
+  const uint32_t bits = glv ? 128 : 255;
+  // the window rule's c, then the smallest c with the same window count, so that the top
+  // window is not left with a bit or two (all of its terms in one or two huge buckets)
+  const uint32_t nd = (bits + window_bits(pts) - 1) / window_bits(pts);
+  const uint32_t c = (bits + nd - 1) / nd;
   MsmOut o{};
   o.c = c;
-  o.win_keys = glv ? (128 + c - 1) / c : (255 + c - 1) / c;
+  o.win_keys = nd;
   p.outs.push_back(o);
   MsmSeg s{};
   s.base_off = 0;

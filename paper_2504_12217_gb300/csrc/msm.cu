@@ -69,42 +69,73 @@ __global__ void k_scan_add(uint32_t* out, size_t n_out, const uint32_t* add) {
   if (i < n_out) out[i] += add[blockIdx.x];
 }
 
-// Exclusive scan of n_in values into n_out outputs by one block of 1024 threads, each
-// scanning a contiguous run of ceil(n_out / 1024) entries around one block-wide scan of
-// the runs' totals; also writes the first n_copy outputs to copy (if non-null).  For
-// outputs up to SCAN1_MAX: one launch instead of three.
+// Exclusive scan of n_in values into n_out outputs by one block of 1024 threads, in
+// tiles of 4096 consecutive entries (each thread four of them, loaded and stored as one
+// 16-byte vector where the tile is whole, so every warp access is coalesced), with a
+// block-wide scan per tile and the running total carried between tiles; also writes the
+// first n_copy outputs to copy (if non-null).  in, out and copy are 16-byte aligned (the
+// MSM workspace's).  For outputs up to SCAN1_MAX: one launch instead of three.
 constexpr size_t SCAN1_MAX = 1024 * 64;
 __global__ void __launch_bounds__(1024) k_scan_single(const uint32_t* __restrict__ in, size_t n_in, uint32_t* out,
                                                       size_t n_out, uint32_t* copy, size_t n_copy) {
   __shared__ uint32_t wsum[32];
-  const size_t per = (n_out + 1023) / 1024;
-  const size_t lo = size_t(threadIdx.x) * per, hi = min(lo + per, n_out);
-  uint32_t tot = 0;
-  for (size_t i = lo; i < hi; i++) tot += i < n_in ? in[i] : 0u;
-  uint32_t x = tot;
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t carry = 0;
+  for (size_t t0 = 0; t0 < n_out; t0 += 4096) {
+    const size_t i0 = t0 + size_t(threadIdx.x) * 4;
+    uint32_t v[4];
+    if (i0 + 4 <= n_in) {
+      const uint4 q = *reinterpret_cast<const uint4*>(in + i0);
+      v[0] = q.x;
+      v[1] = q.y;
+      v[2] = q.z;
+      v[3] = q.w;
+    } else {
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= (uint32_t)d) x += y;
-  }
-  if (lane == 31) wsum[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t w = wsum[lane];
+      for (int j = 0; j < 4; j++) v[j] = i0 + j < n_in ? in[i0 + j] : 0u;
+    }
+    const uint32_t tot = v[0] + v[1] + v[2] + v[3];
+    uint32_t x = tot;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
-      if (lane >= (uint32_t)d) w += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= (uint32_t)d) x += y;
     }
-    wsum[lane] = w;
-  }
-  __syncthreads();
-  uint32_t run = x - tot + (wid ? wsum[wid - 1] : 0u);
-  for (size_t i = lo; i < hi; i++) {
-    out[i] = run;
-    if (copy && i < n_copy) copy[i] = run;
-    run += i < n_in ? in[i] : 0u;
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t w = wsum[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, d);
+        if (lane >= (uint32_t)d) w += y;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t e[4];
+    e[0] = carry + x - tot + (wid ? wsum[wid - 1] : 0u);
+    e[1] = e[0] + v[0];
+    e[2] = e[1] + v[1];
+    e[3] = e[2] + v[2];
+    if (i0 + 4 <= n_out) {
+      *reinterpret_cast<uint4*>(out + i0) = make_uint4(e[0], e[1], e[2], e[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        if (i0 + j < n_out) out[i0 + j] = e[j];
+    }
+    if (copy) {
+      if (i0 + 4 <= n_copy) {
+        *reinterpret_cast<uint4*>(copy + i0) = make_uint4(e[0], e[1], e[2], e[3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+          if (i0 + j < n_copy) copy[i0 + j] = e[j];
+      }
+    }
+    carry += wsum[31];
+    __syncthreads();  // every thread has read wsum before the next tile writes it
   }
 }
 
@@ -133,7 +164,9 @@ static int scan_rec(const uint32_t* in, size_t n_in, uint32_t* out, size_t n_out
 }
 
 int scan_u32(const uint32_t* in, uint32_t* out, size_t n, Arena& a, cudaStream_t st, uint32_t* copy) {
-  if (n + 1 <= SCAN1_MAX) {
+  const bool aligned16 = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) |
+                           reinterpret_cast<uintptr_t>(copy)) & 15u) == 0;  // k_scan_single's vector accesses
+  if (n + 1 <= SCAN1_MAX && (aligned16 || a.measuring)) {
     if (!a.measuring) {
       k_scan_single<<<1, 1024, 0, st>>>(in, n, out, n + 1, copy, copy ? n : 0); ZK_COUNT_LAUNCH();
       ZK_CUDA(cudaGetLastError());
