@@ -210,19 +210,76 @@ __device__ __forceinline__ void pass_store(Fr* arr, const PassGeo& g, size_t gid
   }
 }
 
-// The pass's k stages on NPOLY staged arrays (8 E words apart); barriers between stages
-// (the first one orders the loads before it).
-template <bool DIT, int NPOLY>
+// The pass's k stages on NPOLY staged arrays (8 E words apart).  Radix 2 (R4 false):
+// one stage per shared-memory round trip, one butterfly per element pair.  R4: two stages
+// at a time: a radix-4 unit reads four elements, runs their four butterflies of stages t
+// and t + 1 in registers (two independent products per stage) and writes them back, so a
+// pair of stages costs one round trip and one barrier instead of two; an odd last stage
+// runs as radix 2.  R4 holds more registers (112 against 64: two blocks of 256 per SM
+// instead of four), which pays where the grid is too small to fill the GPU (the latency of
+// a thread's serial stages decides) and costs a few per cent where it is large.  Barriers
+// between rounds (the first one orders the loads before it).
+//   DIF, stage t of half h (block 2h), then h/2: a unit is j0 = blk 2h + off (off < h/2)
+//     and j0 + h/2, j0 + h, j0 + 3h/2; twiddles w_t(off), w_t(off + h/2), w_(t+1)(off).
+//   DIT, stage t of half h (block 2h), then 2h: a unit is j0 = blk 4h + off (off < h) and
+//     j0 + h, j0 + 2h, j0 + 3h; twiddles w_t(off), w_(t+1)(off), w_(t+1)(off + h).
+// w_t(q) is the table entry of the radix-2 form: DIF ((q << sbits) + lo) << s, DIT
+// ((q << s0) + lo) << (L - 1 - s), lo the group's low index bits, s = s0 + t.
+template <bool DIT, int NPOLY, bool R4>
 __device__ __forceinline__ void pass_stages(uint32_t* sm, const PassGeo& g, size_t gid0, const Fr* tw) {
   const uint32_t G = 1u << g.logG, E = G << g.k, L = g.L, logG = g.logG;
   const uint32_t sbits = DIT ? g.s0 : (L - g.s0 - g.k);
   const size_t smask = (size_t(1) << sbits) - 1;
-  const uint32_t nbf = E >> 1;
+  auto twi = [&](uint32_t s, uint32_t q, size_t lo) -> size_t {
+    return DIT ? ((((size_t)q << g.s0) + lo) << (L - 1 - s)) : ((((size_t)q << sbits) + lo) << s);
+  };
   __syncthreads();
-  for (uint32_t t = 0; t < g.k; t++) {
+  uint32_t t = 0;
+  const uint32_t nq = E >> 2;
+  for (; R4 && t + 1 < g.k; t += 2) {
     const uint32_t s = g.s0 + t;
-    const uint32_t logh = DIT ? t : (g.k - 1 - t);
-    const uint32_t h = 1u << logh;
+    for (uint32_t ua = threadIdx.x; ua < nq * (uint32_t)NPOLY; ua += blockDim.x) {
+      const uint32_t poly = NPOLY == 1 ? 0u : ua / nq, u = ua - poly * nq;
+      uint32_t* smp = sm + size_t(poly) * 8 * E;
+      const uint32_t gg = u & (G - 1), q = u >> logG;
+      const size_t lo = (gid0 + gg) & smask;
+      if (DIT) {
+        const uint32_t lh = t, h = 1u << lh;  // stage t: half h; stage t + 1: half 2h
+        const uint32_t off = q & (h - 1), j0 = ((q >> lh) << (lh + 2)) + off;
+        const uint32_t p0 = (j0 << logG) + gg, p1 = ((j0 + h) << logG) + gg, p2 = ((j0 + 2 * h) << logG) + gg,
+                       p3 = ((j0 + 3 * h) << logG) + gg;
+        const Fr w0 = ld_field(tw + twi(s, off, lo));
+        Fr x0 = sm_get(smp, E, p0), x1 = sm_get(smp, E, p1), x2 = sm_get(smp, E, p2), x3 = sm_get(smp, E, p3);
+        x1 = f_mul(x1, w0);
+        x3 = f_mul(x3, w0);
+        const Fr a = f_add(x0, x1), b = f_sub(x0, x1), c = f_add(x2, x3), d = f_sub(x2, x3);
+        const Fr w1 = ld_field(tw + twi(s + 1, off, lo)), w2 = ld_field(tw + twi(s + 1, off + h, lo));
+        const Fr vc = f_mul(c, w1), vd = f_mul(d, w2);
+        sm_put(smp, E, p0, f_add(a, vc));
+        sm_put(smp, E, p2, f_sub(a, vc));
+        sm_put(smp, E, p1, f_add(b, vd));
+        sm_put(smp, E, p3, f_sub(b, vd));
+      } else {
+        const uint32_t lh = g.k - 1 - t, h = 1u << lh, hq = h >> 1;  // stage t: half h; t + 1: h/2
+        const uint32_t off = q & (hq - 1), j0 = ((q >> (lh - 1)) << (lh + 1)) + off;
+        const uint32_t p0 = (j0 << logG) + gg, p1 = ((j0 + hq) << logG) + gg, p2 = ((j0 + h) << logG) + gg,
+                       p3 = ((j0 + h + hq) << logG) + gg;
+        const Fr w0 = ld_field(tw + twi(s, off, lo)), w1 = ld_field(tw + twi(s, off + hq, lo));
+        const Fr x0 = sm_get(smp, E, p0), x1 = sm_get(smp, E, p1), x2 = sm_get(smp, E, p2), x3 = sm_get(smp, E, p3);
+        const Fr a = f_add(x0, x2), b = f_mul(f_sub(x0, x2), w0);
+        const Fr c = f_add(x1, x3), d = f_mul(f_sub(x1, x3), w1);
+        const Fr w2 = ld_field(tw + twi(s + 1, off, lo));
+        sm_put(smp, E, p0, f_add(a, c));
+        sm_put(smp, E, p1, f_mul(f_sub(a, c), w2));
+        sm_put(smp, E, p2, f_add(b, d));
+        sm_put(smp, E, p3, f_mul(f_sub(b, d), w2));
+      }
+    }
+    __syncthreads();
+  }
+  for (; t < g.k; t++) {  // radix 2: every stage, or the last of an odd count
+    const uint32_t s = g.s0 + t, nbf = E >> 1;
+    const uint32_t logh = DIT ? t : (g.k - 1 - t), h = 1u << logh;
     for (uint32_t bfa = threadIdx.x; bfa < nbf * (uint32_t)NPOLY; bfa += blockDim.x) {
       const uint32_t poly = NPOLY == 1 ? 0u : bfa / nbf, bf = bfa - poly * nbf;
       uint32_t* smp = sm + size_t(poly) * 8 * E;
@@ -231,8 +288,7 @@ __device__ __forceinline__ void pass_stages(uint32_t* sm, const PassGeo& g, size
       const uint32_t ju = ((q >> logh) << (logh + 1)) + qh;
       const uint32_t pu = (ju << logG) + gg, pv = ((ju + h) << logG) + gg;
       const size_t lo = (gid0 + gg) & smask;
-      const size_t etw = DIT ? ((((size_t)qh << g.s0) + lo) << (L - 1 - s)) : ((((size_t)qh << sbits) + lo) << s);
-      const Fr w = ld_field(tw + etw);
+      const Fr w = ld_field(tw + twi(s, qh, lo));
       Fr u = sm_get(smp, E, pu), v = sm_get(smp, E, pv);
       Fr a, b;
       if (DIT) {
@@ -251,7 +307,7 @@ __device__ __forceinline__ void pass_stages(uint32_t* sm, const PassGeo& g, size
 }
 
 // One pass of k stages over G groups per block; see the file comment.
-template <bool DIT>
+template <bool DIT, bool R4>
 __global__ void __launch_bounds__(256) k_ntt_pass(Fr* data, size_t bstride, const Fr* __restrict__ tw,
                                                   uint32_t logN, uint32_t s0, uint32_t k, uint32_t logG,
                                                   int load_scale, int store_scale, int to_mont, ScaleTabs tabs) {
@@ -260,7 +316,7 @@ __global__ void __launch_bounds__(256) k_ntt_pass(Fr* data, size_t bstride, cons
   Fr* arr = data + size_t(blockIdx.y) * bstride;
   const size_t gid0 = size_t(blockIdx.x) << logG;
   pass_load<DIT>(arr, g, gid0, sm, load_scale, to_mont, tabs);
-  pass_stages<DIT, 1>(sm, g, gid0, tw);
+  pass_stages<DIT, 1, R4>(sm, g, gid0, tw);
   pass_store<DIT>(arr, g, gid0, sm, store_scale, tabs);
 }
 
@@ -268,6 +324,7 @@ __global__ void __launch_bounds__(256) k_ntt_pass(Fr* data, size_t bstride, cons
 // DIF's last pass (its k stages end at stage L - 1, groups of 2^k consecutive elements),
 // the inverse's scaling by the factor of each element's natural index, and the DIT's
 // first pass over the same groups.  Saves a global round trip and a launch.
+template <bool R4>
 __global__ void __launch_bounds__(256) k_ntt_turn(Fr* data, size_t bstride, const Fr* __restrict__ tw_inv,
                                                   const Fr* __restrict__ tw_fwd, uint32_t L, uint32_t k,
                                                   uint32_t logG, int mid_scale, ScaleTabs tabs) {
@@ -277,12 +334,12 @@ __global__ void __launch_bounds__(256) k_ntt_turn(Fr* data, size_t bstride, cons
   const size_t gid0 = size_t(blockIdx.x) << logG;
   const uint32_t E = 1u << (logG + k);
   pass_load<false>(arr, gdif, gid0, sm, SC_NONE, 0, tabs);
-  pass_stages<false, 1>(sm, gdif, gid0, tw_inv);
+  pass_stages<false, 1, R4>(sm, gdif, gid0, tw_inv);
   for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
     const size_t idx = pass_index<false>(gdif, gid0, e);
     sm_put(sm, E, e, f_mul(sm_get(sm, E, e), scale_factor(tabs, mid_scale, brev_bits((uint32_t)idx, L))));
   }
-  pass_stages<true, 1>(sm, gdit, gid0, tw_fwd);
+  pass_stages<true, 1, R4>(sm, gdit, gid0, tw_fwd);
   pass_store<true>(arr, gdit, gid0, sm, SC_NONE, tabs);
 }
 
@@ -292,6 +349,7 @@ __global__ void __launch_bounds__(256) k_ntt_turn(Fr* data, size_t bstride, cons
 // inverse transform of h over the same groups; only H is written.  Small grids get up
 // to three times the threads of a single-array pass (the three forward passes side by
 // side), large ones one array's worth.
+template <bool R4>
 __global__ void __launch_bounds__(768) k_ntt_quotient_turn(Fr* ev, uint32_t m, size_t N, const Fr* __restrict__ tw_fwd,
                                                            const Fr* __restrict__ tw_inv, uint32_t L, uint32_t k,
                                                            uint32_t logG, ScaleTabs tabs) {
@@ -302,13 +360,13 @@ __global__ void __launch_bounds__(768) k_ntt_quotient_turn(Fr* ev, uint32_t m, s
   const size_t i = blockIdx.y;
   for (int p = 0; p < 3; p++)
     pass_load<true>(ev + (size_t(p) * m + i) * N, gdit, gid0, sm + size_t(p) * 8 * E, SC_NONE, 0, tabs);
-  pass_stages<true, 3>(sm, gdit, gid0, tw_fwd);
+  pass_stages<true, 3, R4>(sm, gdit, gid0, tw_fwd);
   const Fr zinv = ld_field(tabs.consts + 1);
   for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
     const Fr a = sm_get(sm, E, e), b = sm_get(sm + 8 * E, E, e), c = sm_get(sm + 16 * E, E, e);
     sm_put(sm, E, e, f_mul(f_sub(f_mul(a, b), c), zinv));
   }
-  pass_stages<false, 1>(sm, gdif, gid0, tw_inv);
+  pass_stages<false, 1, R4>(sm, gdif, gid0, tw_inv);
   pass_store<false>(ev + (size_t(3) * m + i) * N, gdif, gid0, sm, SC_NONE, tabs);
 }
 
@@ -316,10 +374,14 @@ static std::once_flag g_smem_once;
 
 static void ntt_smem_attrs() {
   std::call_once(g_smem_once, [] {
-    cudaFuncSetAttribute(k_ntt_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
-    cudaFuncSetAttribute(k_ntt_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
-    cudaFuncSetAttribute(k_ntt_turn, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
-    cudaFuncSetAttribute(k_ntt_quotient_turn, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 << 10);
+    cudaFuncSetAttribute(k_ntt_pass<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_ntt_pass<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_ntt_pass<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_ntt_pass<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_ntt_turn<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_ntt_turn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+    cudaFuncSetAttribute(k_ntt_quotient_turn<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 << 10);
+    cudaFuncSetAttribute(k_ntt_quotient_turn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 << 10);
   });
 }
 
@@ -356,16 +418,26 @@ static PassShape pass_shape(uint32_t L, uint32_t k, int elog, int batch) {
   return sh;
 }
 
+// Radix 4 for grids below four blocks per SM (latency-bound: fewer, longer-lived threads
+// with two independent products per stage finish sooner), radix 2 above (throughput:
+// twice the resident warps).
+static bool radix4(dim3 grid) { return uint64_t(grid.x) * grid.y < 4ull * (uint64_t)device_sm_count(); }
+
 static int launch_pass(bool dit, Fr* data, int batch, size_t bstride, const NttDomain* d, const Fr* tw, uint32_t s0,
                        uint32_t k, int elog, int ls, int ss, int tm, cudaStream_t st) {
   const uint32_t L = d->logN;
   const PassShape sh = pass_shape(L, k, elog, batch);
   const size_t smem = size_t(sh.E) * 32;
   const ScaleTabs tabs = tabs_of(d);
-  if (dit)
-    k_ntt_pass<true><<<sh.grid, sh.threads, smem, st>>>(data, bstride, tw, L, s0, k, sh.logG, ls, ss, tm, tabs);
+  const bool r4 = radix4(sh.grid);
+  if (dit && r4)
+    k_ntt_pass<true, true><<<sh.grid, sh.threads, smem, st>>>(data, bstride, tw, L, s0, k, sh.logG, ls, ss, tm, tabs);
+  else if (dit)
+    k_ntt_pass<true, false><<<sh.grid, sh.threads, smem, st>>>(data, bstride, tw, L, s0, k, sh.logG, ls, ss, tm, tabs);
+  else if (r4)
+    k_ntt_pass<false, true><<<sh.grid, sh.threads, smem, st>>>(data, bstride, tw, L, s0, k, sh.logG, ls, ss, tm, tabs);
   else
-    k_ntt_pass<false><<<sh.grid, sh.threads, smem, st>>>(data, bstride, tw, L, s0, k, sh.logG, ls, ss, tm, tabs);
+    k_ntt_pass<false, false><<<sh.grid, sh.threads, smem, st>>>(data, bstride, tw, L, s0, k, sh.logG, ls, ss, tm, tabs);
   ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
@@ -415,7 +487,12 @@ int ntt_quotient_chain(Fr* ev, int m, size_t N, const NttDomain* d, cudaStream_t
   {
     const uint32_t k = ks[P - 1];
     const PassShape sh = pass_shape(L, k, elog, 3 * m);
-    k_ntt_turn<<<sh.grid, sh.threads, size_t(sh.E) * 32, st>>>(ev, N, d->tw_inv, d->tw_fwd, L, k, sh.logG, SC_NG, tabs);
+    if (radix4(sh.grid))
+      k_ntt_turn<true><<<sh.grid, sh.threads, size_t(sh.E) * 32, st>>>(ev, N, d->tw_inv, d->tw_fwd, L, k, sh.logG,
+                                                                      SC_NG, tabs);
+    else
+      k_ntt_turn<false><<<sh.grid, sh.threads, size_t(sh.E) * 32, st>>>(ev, N, d->tw_inv, d->tw_fwd, L, k, sh.logG,
+                                                                       SC_NG, tabs);
     ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
@@ -436,8 +513,12 @@ int ntt_quotient_chain(Fr* ev, int m, size_t N, const NttDomain* d, cudaStream_t
     const uint64_t blocks = uint64_t(sh.grid.x) * sh.grid.y;
     const uint32_t threads =
         blocks < 2 * uint64_t(device_sm_count()) ? std::min<uint32_t>(3 * sh.threads, 768) : sh.threads;
-    k_ntt_quotient_turn<<<sh.grid, threads, size_t(3) * sh.E * 32, st>>>(ev, (uint32_t)m, N, d->tw_fwd, d->tw_inv, L,
-                                                                         k, sh.logG, tabs);
+    if (radix4(sh.grid))
+      k_ntt_quotient_turn<true><<<sh.grid, threads, size_t(3) * sh.E * 32, st>>>(ev, (uint32_t)m, N, d->tw_fwd,
+                                                                                 d->tw_inv, L, k, sh.logG, tabs);
+    else
+      k_ntt_quotient_turn<false><<<sh.grid, threads, size_t(3) * sh.E * 32, st>>>(ev, (uint32_t)m, N, d->tw_fwd,
+                                                                                  d->tw_inv, L, k, sh.logG, tabs);
     ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
