@@ -353,10 +353,12 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const ui
  * after the NTTs, 2 after the H MSM's bucket accumulation), the mode zkvc_prove uses
  * (ZKVC_PROVE_FOLD or ZKVC_PROVE_CHAIN), when the G2 MSM starts (0, 1), and whether the H
  * and the small-digit runs accumulate on quads of lanes (0, 1) --
- * keeps the fastest in the key and writes it to tuning (may be NULL).  `mode` is the
- * mode to tune, or ZKVC_PROVE_AUTO to tune both and keep the faster.  It allocates and
- * frees its own workspace and synchronises `stream`; the key must not be proving
- * meanwhile.
+ * keeps the fastest in the key and writes it to tuning (may be NULL): a joint grid over
+ * the small-digit and G2 chunks first, then two sweeps of coordinate descent over all
+ * values.  Each candidate is the median of nine proofs, each started after a 256 MiB
+ * write (a cold L2, as for a proof of fresh inputs).  `mode` is the mode to tune, or ZKVC_PROVE_AUTO to tune both and keep
+ * the faster.  It allocates and frees its own workspace and the 256 MiB buffer and
+ * synchronises `stream`; the key must not be proving meanwhile.
  * Afterwards zkvc_prove_workspace_bytes reflects the chosen chunks (smaller chunks need
  * more workspace).  zkvc_pk_set_tuning / zkvc_pk_get_tuning impose or read the setting
  * (ZKVC_EINVAL for a chunk above 1024, an NTT block outside 2^8..2^11, a start outside
