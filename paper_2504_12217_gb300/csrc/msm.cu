@@ -195,6 +195,8 @@ int msm_plan_finalize(MsmPlan& p) {
   for (auto& o : p.outs) {
     ZK_CHECK(o.c >= 2 && o.c <= 20, ZKVC_EINVAL, "msm: window of %u bits", o.c);
     ZK_CHECK(o.win_keys >= 1, ZKVC_EINVAL, "msm: win_keys = 0");
+    // k_bits_chain stages an output's window sums in its shared array (64 points in G2)
+    ZK_CHECK(o.win_keys <= 64, ZKVC_EINVAL, "msm: %u windows in one output (at most 64)", o.win_keys);
     o.key_off = key;
     o.nkeys = o.win_keys << (o.c - 1);
     key += o.nkeys;
@@ -593,16 +595,16 @@ __global__ void __launch_bounds__(256, AccumMinB<F>::value) k_accum0(const uint3
 
 // Buckets with at most FOLD_SERIAL partial sums (the common case of a balanced
 // accumulation: a bucket split by one or two chunk boundaries) are folded by one thread
-// (or quad) per bucket, serially, without counters; k_fold_tree takes the larger ones.
+// (or quad) per bucket, serially, without counters; the tree (fold_tree_at) takes the
+// larger ones.
 // Where chunk boundaries are fewer than buckets (large chunks over many small buckets),
 // the quads go over the boundaries' fold list instead (flist non-null, nlist entries), so
 // that every launched quad has a bucket to fold.
 template <class F, int QL>
-__global__ void __launch_bounds__(128) k_fold_serial(const uint32_t* __restrict__ choff,
-                                                     const uint32_t* __restrict__ nch, uint32_t K, XYZZ<F>* part,
-                                                     const uint32_t* __restrict__ flist, uint32_t nlist,
-                                                     const uint32_t* __restrict__ offs, uint32_t T0) {
-  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
+__device__ __forceinline__ void fold_serial_at(uint32_t i, const uint32_t* __restrict__ choff,
+                                               const uint32_t* __restrict__ nch, uint32_t K, XYZZ<F>* part,
+                                               const uint32_t* __restrict__ flist, uint32_t nlist,
+                                               const uint32_t* __restrict__ offs, uint32_t T0) {
   uint32_t k = i;
   if (flist) {
     if (i == 0 || i >= nlist) return;  // uniform within a quad
@@ -650,10 +652,9 @@ static uint64_t accum_resident_threads(uint32_t at) {
 // zeroed counter per chunk.  The counter's fetch-and-add releases the climber's store
 // and acquires its sibling's.  QL lanes per chunk as in the accumulation.
 template <class F, int QL>
-__global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ choff, const uint32_t* __restrict__ nch,
-                                                   const uint32_t* __restrict__ chunk_key, uint32_t K,
-                                                   XYZZ<F>* part, uint32_t* arrive) {
-  const uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
+__device__ __forceinline__ void fold_tree_at(uint32_t q, const uint32_t* __restrict__ choff,
+                                             const uint32_t* __restrict__ nch, const uint32_t* __restrict__ chunk_key,
+                                             uint32_t K, XYZZ<F>* part, uint32_t* arrive) {
   if (q >= choff[K]) return;  // uniform within a quad
   // chunk_key is written only for owned slots: any other value (a previous run's, or
   // never written) fails the range check
@@ -661,7 +662,7 @@ __global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ 
   if (k >= K) return;
   const uint32_t base = choff[k], np = nch[k];
   if (q < base || q >= base + np) return;  // a slot no bucket owns
-  if (np <= FOLD_SERIAL) return;  // k_fold_serial's
+  if (np <= FOLD_SERIAL) return;  // folded serially
   const bool lead = QL == 1 || quad_lane() == 0;
   uint32_t pos = q - base;
   XYZZ<F> acc;
@@ -690,6 +691,19 @@ __global__ void __launch_bounds__(128) k_fold_tree(const uint32_t* __restrict__ 
     pos = left ? pos : sib;
   }
   if (have && lead) st_field(part + base, acc);
+}
+
+// Both folds in one launch (disjoint buckets: at most FOLD_SERIAL partials go serially,
+// more along the tree): quad (or thread) i takes serial entry i (bucket i, or boundary i
+// of the fold list) and tree slot i.
+template <class F, int QL>
+__global__ void __launch_bounds__(128) k_fold(const uint32_t* __restrict__ choff, const uint32_t* __restrict__ nch,
+                                              const uint32_t* __restrict__ chunk_key, uint32_t K, XYZZ<F>* part,
+                                              uint32_t* arrive, const uint32_t* __restrict__ flist, uint32_t nlist,
+                                              const uint32_t* __restrict__ offs, uint32_t T0, uint32_t n_serial) {
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) / QL;
+  if (i < n_serial) fold_serial_at<F, QL>(i, choff, nch, K, part, flist, nlist, offs, T0);
+  fold_tree_at<F, QL>(i, choff, nch, chunk_key, K, part, arrive);
 }
 
 template <class F>
@@ -779,6 +793,7 @@ struct BitSeg {
   uint32_t nsl;     // slices
   uint32_t dslot;   // slot of 2^shift U_b in the D buffer
   uint32_t mode;    // bits 0-7: shift (doublings of U_b); BS_PSEUDO
+  uint32_t win;     // the window's TreeSeg
 };
 
 // One split window: the pseudo-buckets C_1 .. C_(2^h - 1) then D_1 .. D_(2^(c-1-h)) at
@@ -804,34 +819,6 @@ struct SliceBT {
 };
 // one wave of slice blocks: three resident per SM
 static uint32_t slice_wave() { return 3u * (uint32_t)device_sm_count(); }
-
-// block per slice: the sum of up to `slice` buckets of one bit
-template <class F>
-__global__ void __launch_bounds__(SliceBT<F>::value) k_bits_slices(const XYZZ<F>* __restrict__ fin,
-                                                                    const uint32_t* __restrict__ counts,
-                                                                    const uint32_t* __restrict__ choff,
-                                                                    const BitSeg* __restrict__ segs, uint32_t nseg,
-                                                                    uint32_t slice, const XYZZ<F>* __restrict__ P,
-                                                                    XYZZ<F>* S) {
-  constexpr int BT = SliceBT<F>::value;
-  __shared__ XYZZ<F> sh[BT];
-  const uint32_t sl = blockIdx.x;
-  uint32_t lo = 0, hi = nseg - 1;
-  while (lo < hi) {
-    uint32_t mid = (lo + hi + 1) >> 1;
-    if (segs[mid].soff <= sl) lo = mid; else hi = mid - 1;
-  }
-  const BitSeg g = segs[lo];
-  const uint32_t first = (sl - g.soff) * slice;
-  const uint32_t m = min(slice, g.cnt - first);
-  const bool pseudo = (g.mode & BS_PSEUDO) != 0;
-  auto get = [&](uint32_t i) {
-    const uint32_t v = nth_with_bit(g.b, g.c, first + i);
-    return pseudo ? ld_field(P + g.key0 + v - 1) : bucket_at(fin, counts, choff, g.key0 + v - 1);
-  };
-  const XYZZ<F> r = block_sum<F, BT>(get, m, sh);
-  if (threadIdx.x == 0) st_field(S + sl, r);
-}
 
 // block per pseudo-bucket of a split window: C_lo (members v = 2^h hi + lo, hi <
 // 2^(c-1-h)) or D_hi (members v = 2^h hi + lo, lo < 2^h, v <= 2^(c-1))
@@ -865,52 +852,15 @@ __global__ void __launch_bounds__(SliceBT<F>::value) k_split_gather(const XYZZ<F
   if (threadIdx.x == 0) st_field(P + g.pbase + cls, r);
 }
 
-// block per bit: U_b = the sum of the bit's slices, then 2^b U_b by b doublings (G1: one
-// warp in limb-sliced arithmetic, about two thirds of a quad doubling's latency; G2: one
-// quad)
-constexpr int BITS_BT = 64;
-template <class F>
-__global__ void __launch_bounds__(BITS_BT) k_bits_scale(const XYZZ<F>* __restrict__ S, const BitSeg* __restrict__ segs,
-                                                         XYZZ<F>* D) {
-  __shared__ XYZZ<F> sh[BITS_BT];
-  const BitSeg g = segs[blockIdx.x];
-  auto get = [&](uint32_t i) { return ld_field(S + g.soff + i); };
-  XYZZ<F> x = block_sum<F, BITS_BT>(get, g.nsl, sh);
-  if constexpr (sizeof(F) == sizeof(Fp)) {
-    __shared__ G1J xs;
-    if (threadIdx.x == 0) st_field(&xs, x);
-    __syncthreads();
-    if (threadIdx.x >= 32) return;
-    SlG1 y = sl_ld(&xs);
-    const uint32_t shift = g.mode & 0xffu;
-    for (uint32_t i = 0; i < shift; i++) y = sl_pdbl(y);
-    sl_st(D + g.dslot, y);
-  } else {
-    if (threadIdx.x >= 4) return;
-    const uint32_t shift = g.mode & 0xffu;
-    for (uint32_t i = 0; i < shift; i++) x = p_dbl_quad(x);
-    if (threadIdx.x == 0) st_field(D + g.dslot, x);
-  }
-}
-
 // block per (output, window): the window's c terms 2^b U_b, summed into the first slot
 struct TreeSeg {
   uint32_t off;  // first element
   uint32_t len;  // elements
+  uint32_t out;  // its output
 };
 
-template <class F>
-__global__ void __launch_bounds__(BITS_BT) k_bits_window(XYZZ<F>* D, const TreeSeg* __restrict__ segs) {
-  __shared__ XYZZ<F> sh[BITS_BT];
-  const TreeSeg g = segs[blockIdx.x];
-  auto get = [&](uint32_t i) { return ld_field(D + g.off + i); };
-  const XYZZ<F> r = block_sum<F, BITS_BT>(get, g.len, sh);
-  if (threadIdx.x == 0) st_field(D + g.off, r);
-}
-
-// results[o] = sum_w 2^(c w) W[o][w] by Horner's rule (windows of variable-base outputs):
-// a chain of c (nwin - 1) doublings, latency-bound, so G1 runs it on one warp in
-// limb-sliced arithmetic (about two thirds of a quad doubling's latency), G2 on one quad.
+// results[o] = sum_w 2^(c w) W[o][w] by Horner's rule for variable-base outputs (a chain
+// of c (nwin - 1) doublings), the window's sum itself for the rest.
 struct OutItem {
   uint32_t first;     // index of window 0's result in D
   uint32_t stride;    // distance between windows' results
@@ -918,28 +868,116 @@ struct OutItem {
   uint32_t c;
 };
 
+// The bucket sums after the folds, in one launch whose levels hand over through counters
+// instead of launch boundaries:
+//   slice  block per slice of one bit's buckets: the slice's sum (serial per thread, then
+//          the block's tree) into S;
+//   bit    the last slice block of a bit to finish sums the bit's slices (U_b) and doubles
+//          it b times (2^b U_b; G1 on one warp in limb-sliced arithmetic, G2 on a quad);
+//   window the last bit of a window sums the window's c terms 2^b U_b;
+//   output the last window of an output applies Horner's rule over the output's windows
+//          (variable base; G1 on a sliced warp, G2 on a quad) or copies its one window.
+// Each hand-over: the finishing block's stores, a fence, then a fetch-and-add on the
+// level's counter (zeroed before the launch); the block that brings the count to the
+// total goes on, after a fence, reading the others' results around L1.  No block waits.
 template <class F>
-constexpr int combine_lanes() { return sizeof(F) == sizeof(Fp) ? 32 : 4; }
-
-template <class F>
-__global__ void k_combine_windows(const XYZZ<F>* D, const OutItem* outs, uint32_t nouts, XYZZ<F>* results) {
-  const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) / combine_lanes<F>();
-  if (o >= nouts) return;  // uniform per warp (G1) or quad (G2)
-  const OutItem it = outs[o];
+__global__ void __launch_bounds__(SliceBT<F>::value) k_bits_chain(
+    const XYZZ<F>* __restrict__ fin, const uint32_t* __restrict__ counts, const uint32_t* __restrict__ choff,
+    const BitSeg* __restrict__ segs, uint32_t nseg, uint32_t slice, const XYZZ<F>* __restrict__ P, XYZZ<F>* S,
+    XYZZ<F>* D, const TreeSeg* __restrict__ dsegs, const OutItem* __restrict__ oitems, XYZZ<F>* results,
+    uint32_t* cnt_bit, uint32_t* cnt_win, uint32_t* cnt_out) {
+  constexpr int BT = SliceBT<F>::value;
+  __shared__ XYZZ<F> sh[BT];
+  __shared__ XYZZ<F> xs;
+  __shared__ uint32_t last;
+  const uint32_t sl = blockIdx.x;
+  uint32_t lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi + 1) >> 1;
+    if (segs[mid].soff <= sl) lo = mid; else hi = mid - 1;
+  }
+  const BitSeg g = segs[lo];
+  // slice
+  {
+    const uint32_t first = (sl - g.soff) * slice;
+    const uint32_t m = min(slice, g.cnt - first);
+    const bool pseudo = (g.mode & BS_PSEUDO) != 0;
+    auto get = [&](uint32_t i) {
+      const uint32_t v = nth_with_bit(g.b, g.c, first + i);
+      return pseudo ? ld_field(P + g.key0 + v - 1) : bucket_at(fin, counts, choff, g.key0 + v - 1);
+    };
+    const XYZZ<F> r = block_sum<F, BT>(get, m, sh);
+    if (threadIdx.x == 0) {
+      st_field(S + sl, r);
+      __threadfence();
+      last = atomicAdd(cnt_bit + lo, 1u) == g.nsl - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+  }
+  // bit
+  {
+    auto get = [&](uint32_t i) { return ld_point_cg(S + g.soff + i); };
+    XYZZ<F> x = block_sum<F, BT>(get, g.nsl, sh);
+    const uint32_t shift = g.mode & 0xffu;
+    if constexpr (sizeof(F) == sizeof(Fp)) {
+      if (threadIdx.x == 0) st_field(&xs, x);
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        SlG1 y = sl_ld(&xs);
+        for (uint32_t i = 0; i < shift; i++) y = sl_pdbl(y);
+        sl_st(D + g.dslot, y);
+      }
+    } else {
+      if (threadIdx.x < 4) {
+        for (uint32_t i = 0; i < shift; i++) x = p_dbl_quad(x);
+        if (threadIdx.x == 0) st_field(D + g.dslot, x);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      last = atomicAdd(cnt_win + g.win, 1u) == dsegs[g.win].len - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+  }
+  // window
+  const TreeSeg w = dsegs[g.win];
+  {
+    auto get = [&](uint32_t i) { return ld_point_cg(D + w.off + i); };
+    const XYZZ<F> r = block_sum<F, BT>(get, w.len, sh);
+    if (threadIdx.x == 0) {
+      st_field(D + w.off, r);
+      __threadfence();
+      last = atomicAdd(cnt_out + w.out, 1u) == oitems[w.out].nwin - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+  }
+  // output (at most SliceBT windows: checked by the planner)
+  const OutItem it = oitems[w.out];
+  for (uint32_t i = threadIdx.x; i < it.nwin; i += BT) st_field(sh + i, ld_point_cg(D + it.first + i * it.stride));
+  __syncthreads();
   if constexpr (sizeof(F) == sizeof(Fp)) {
-    SlG1 acc = sl_ld(D + it.first + (it.nwin - 1) * it.stride);
-    for (int w = (int)it.nwin - 2; w >= 0; w--) {
+    if (threadIdx.x >= 32) return;
+    SlG1 acc = sl_ld(sh + it.nwin - 1);
+    for (int v = (int)it.nwin - 2; v >= 0; v--) {
       for (uint32_t i = 0; i < it.c; i++) acc = sl_pdbl(acc);
-      acc = sl_padd(acc, sl_ld(D + it.first + uint32_t(w) * it.stride));
+      acc = sl_padd(acc, sl_ld(sh + v));
     }
-    sl_st(results + o, acc);
+    sl_st(results + w.out, acc);
   } else {
-    XYZZ<F> acc = ld_field(D + it.first + (it.nwin - 1) * it.stride);
-    for (int w = (int)it.nwin - 2; w >= 0; w--) {
+    if (threadIdx.x >= 4) return;
+    XYZZ<F> acc = ld_field(sh + it.nwin - 1);
+    for (int v = (int)it.nwin - 2; v >= 0; v--) {
       for (uint32_t i = 0; i < it.c; i++) acc = p_dbl_quad(acc);
-      acc = p_add_quad(acc, ld_field(D + it.first + uint32_t(w) * it.stride));
+      acc = p_add_quad(acc, ld_field(sh + v));
     }
-    if (quad_lane() == 0) st_field(results + o, acc);
+    if (threadIdx.x == 0) st_field(results + w.out, acc);
   }
 }
 
@@ -954,7 +992,8 @@ struct Layout {
   TreeSeg* dseg;
   OutItem* oitems;
   SplitWin* swins;
-  void* P;  // pseudo-buckets of the split windows
+  void* P;         // pseudo-buckets of the split windows
+  uint32_t* cnt;   // k_bits_chain's counters: per bit, per window, per output
   uint32_t qmax, nbits, nslices, dtotal, slice, nswin, ngather, npseudo;
 };
 
@@ -1005,7 +1044,8 @@ static void tables(const MsmPlan& p, uint32_t bt, uint32_t wave, HostTables& h, 
     for (uint32_t b = b_from; b < b_to; b++) {
       const uint32_t cnt = (b == c - 1) ? 1u : (1u << (c - 2));
       const uint32_t nsl = (cnt + slice - 1) / slice;
-      h.bsegs.push_back({key0, b, c, cnt, soff, nsl, slot0 + b - b_from, mode | (shift0 + b)});
+      h.bsegs.push_back(
+          {key0, b, c, cnt, soff, nsl, slot0 + b - b_from, mode | (shift0 + b), (uint32_t)h.dsegs.size() - 1});
       soff += nsl;
     }
   };
@@ -1014,7 +1054,7 @@ static void tables(const MsmPlan& p, uint32_t bt, uint32_t wave, HostTables& h, 
     h.oitems.push_back({dslot, o.c, o.win_keys, o.c});
     h.obases.push_back(o.bases);
     for (uint32_t w = 0; w < o.win_keys; w++) {
-      h.dsegs.push_back({dslot, o.c});
+      h.dsegs.push_back({dslot, o.c, (uint32_t)h.oitems.size() - 1});
       const uint32_t key0 = o.key_off + w * nb;
       if (split_window(o)) {
         // lo in [1, 2^h): bits 0 .. h-1 of a (h+1)-bit set; hi in [1, 2^(c-1-h)]: bits
@@ -1067,6 +1107,7 @@ static void layout(const MsmPlan& p, Arena& a, Layout& L, HostTables& h) {
   L.oitems = a.take<OutItem>(h.oitems.size());
   L.swins = a.take<SplitWin>(h.swins.size());
   L.P = a.take<XYZZ<F>>(L.npseudo);
+  L.cnt = a.take<uint32_t>(h.bsegs.size() + h.dsegs.size() + h.oitems.size());
 }
 
 template <class F>
@@ -1215,15 +1256,15 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   const uint64_t nlist = p.slots / T0 + 2;
   const bool by_boundary = nlist < K;
   const uint32_t* fl = by_boundary ? L.flist : nullptr;
-  const unsigned sfb = (unsigned)(((by_boundary ? nlist : uint64_t(K)) * flanes + 127) / 128);
-  if (flanes == 4) {
-    k_fold_serial<F, 4><<<sfb, 128, 0, st>>>(L.choff, L.nch, K, part, fl, (uint32_t)nlist, L.offs, T0);
-    k_fold_tree<F, 4><<<fb, 128, 0, st>>>(L.choff, L.nch, L.chunk_key, K, part, L.arrive);
-  } else {
-    k_fold_serial<F, 1><<<sfb, 128, 0, st>>>(L.choff, L.nch, K, part, fl, (uint32_t)nlist, L.offs, T0);
-    k_fold_tree<F, 1><<<fb, 128, 0, st>>>(L.choff, L.nch, L.chunk_key, K, part, L.arrive);
-  }
-  ZK_COUNT_LAUNCH();
+  const uint64_t n_serial = by_boundary ? nlist : uint64_t(K);
+  const unsigned sfb = (unsigned)((n_serial * flanes + 127) / 128);
+  const unsigned fab = std::max(sfb, fb);
+  if (flanes == 4)
+    k_fold<F, 4><<<fab, 128, 0, st>>>(L.choff, L.nch, L.chunk_key, K, part, L.arrive, fl, (uint32_t)nlist, L.offs, T0,
+                                      (uint32_t)n_serial);
+  else
+    k_fold<F, 1><<<fab, 128, 0, st>>>(L.choff, L.nch, L.chunk_key, K, part, L.arrive, fl, (uint32_t)nlist, L.offs, T0,
+                                      (uint32_t)n_serial);
   ZK_COUNT_LAUNCH();
   // sum_v v B_v per (output, window) by bit decomposition
   XYZZ<F>* Sl = reinterpret_cast<XYZZ<F>*>(L.S);
@@ -1233,14 +1274,11 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
     k_split_gather<F><<<L.ngather, SliceBT<F>::value, 0, st>>>(part, L.counts, L.choff, L.swins, L.nswin, Pb);
     ZK_COUNT_LAUNCH();
   }
-  k_bits_slices<F><<<L.nslices, SliceBT<F>::value, 0, st>>>(part, L.counts, L.choff, L.bsegs, L.nbits, L.slice, Pb,
-                                                             Sl);
-  ZK_COUNT_LAUNCH();
-  k_bits_scale<F><<<L.nbits, BITS_BT, 0, st>>>(Sl, L.bsegs, D); ZK_COUNT_LAUNCH();
-  k_bits_window<F><<<(unsigned)h.dsegs.size(), BITS_BT, 0, st>>>(D, L.dseg); ZK_COUNT_LAUNCH();
-  const uint32_t nouts = (uint32_t)p.outs.size();
-  k_combine_windows<F><<<(unsigned)((uint64_t(combine_lanes<F>()) * nouts + 63) / 64), 64, 0, st>>>(D, L.oitems, nouts,
-                                                                                                  results);
+  const size_t nbits = h.bsegs.size(), nwins = h.dsegs.size(), nouts = h.oitems.size();
+  ZK_CUDA(cudaMemsetAsync(L.cnt, 0, (nbits + nwins + nouts) * sizeof(uint32_t), st));
+  k_bits_chain<F><<<L.nslices, SliceBT<F>::value, 0, st>>>(part, L.counts, L.choff, L.bsegs, L.nbits, L.slice, Pb, Sl, D,
+                                                            L.dseg, L.oitems, results, L.cnt, L.cnt + nbits,
+                                                            L.cnt + nbits + nwins);
   ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
   return ZKVC_OK;
