@@ -355,8 +355,9 @@ int zkvc_prove(const zkvc_pk* pk, const int8_t* d_X, const int8_t* d_W, const ui
  * and the small-digit runs accumulate on quads of lanes (0, 1) --
  * keeps the fastest in the key and writes it to tuning (may be NULL): a joint grid over
  * the small-digit and G2 chunks first, then two sweeps of coordinate descent over all
- * values.  Each candidate is the median of nine proofs, each started after a 256 MiB
- * write (a cold L2, as for a proof of fresh inputs).  `mode` is the mode to tune, or ZKVC_PROVE_AUTO to tune both and keep
+ * values, then the four fastest settings seen timed twice more (the lowest mean of three
+ * wins).  Each timing is the median of nine proofs, each started after a 256 MiB write (a
+ * cold L2, as for a proof of fresh inputs).  `mode` is the mode to tune, or ZKVC_PROVE_AUTO to tune both and keep
  * the faster.  It allocates and frees its own workspace and the 256 MiB buffer and
  * synchronises `stream`; the key must not be proving meanwhile.
  * Afterwards zkvc_prove_workspace_bytes reflects the chosen chunks (smaller chunks need

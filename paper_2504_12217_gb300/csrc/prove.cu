@@ -23,6 +23,7 @@
 //  7. Affine conversion (one inversion per point, in parallel) and the canonical
 //     256-byte encoding A || B || C.
 #include <algorithm>
+#include <array>
 #include <optional>
 #include <mutex>
 #include <new>
@@ -807,9 +808,24 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
   // best size of each depends on the other; one knob at a time missed the joint optimum
   // by about 5 %), then coordinate descent over every knob: two sweeps, the incumbent
   // re-timed at the start of each (timings on a shared GPU drift)
+  // every timed setting of the current mode, for the confirmation round
+  struct Seen {
+    float ms;
+    std::array<uint32_t, ZKVC_PK_TUNING_LEN> t;
+  };
+  std::vector<Seen> seen;
+  auto timed = [&](int m, float* ms) -> int {
+    ZK_TRY(measure(m, ms));
+    Seen e;
+    e.ms = *ms;
+    for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) e.t[i] = pk->prove_tune[i];
+    seen.push_back(e);
+    return ZKVC_OK;
+  };
   auto tune = [&](int m, float* best_ms) -> int {
+    seen.clear();
     {
-      ZK_TRY(measure(m, best_ms));
+      ZK_TRY(timed(m, best_ms));
       uint32_t bs = pk->prove_tune[0], bg = pk->prove_tune[3];
       for (int i = -1; i < 6; i++) {
         for (int j = -1; j < 6; j++) {
@@ -818,7 +834,7 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
           pk->prove_tune[0] = cs;
           pk->prove_tune[3] = cg;
           float ms = 0;
-          ZK_TRY(measure(m, &ms));
+          ZK_TRY(timed(m, &ms));
           if (ms < 0.99f * *best_ms) {
             *best_ms = ms;
             bs = cs;
@@ -831,7 +847,7 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
     }
     const int order[4] = {3, 0, 2, 1};  // g2, small, h, rest
     for (int sweep = 0; sweep < 2; sweep++) {
-    ZK_TRY(measure(m, best_ms));
+    ZK_TRY(timed(m, best_ms));
     for (int oi = 0; oi < 9; oi++) {
       // then the NTT block, the side MSM's start, the G2 MSM's start, quads for the H and
       // small-digit accumulations (index 6 is the mode)
@@ -844,7 +860,7 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
         if (c == best || (r == 4 && best == 0 && c == 10)) continue;
         pk->prove_tune[r] = c;
         float ms = 0;
-        ZK_TRY(measure(m, &ms));
+        ZK_TRY(timed(m, &ms));
         if (ms < 0.99f * *best_ms) {  // a gain within timing noise does not move the setting
           *best_ms = ms;
           best = c;
@@ -852,6 +868,34 @@ int prove_autotune(zkvc_pk* pk, int mode, const int8_t* dX, const int8_t* dW, co
       }
       pk->prove_tune[r] = best;
     }
+    }
+    // confirmation: the four fastest distinct settings seen, each timed twice more; the
+    // lowest mean of three medians wins (one median of nine proofs drifts by a few per
+    // cent between calls, which is as much as the knobs' differences near the optimum)
+    std::sort(seen.begin(), seen.end(), [](const Seen& x, const Seen& y) { return x.ms < y.ms; });
+    std::vector<Seen> top;
+    for (const Seen& e : seen) {
+      bool dup = false;
+      for (const Seen& t : top) dup = dup || t.t == e.t;
+      if (!dup) top.push_back(e);
+      if (top.size() == 4) break;
+    }
+    float best_mean = 1e30f;
+    std::array<uint32_t, ZKVC_PK_TUNING_LEN> pick = top.empty() ? std::array<uint32_t, ZKVC_PK_TUNING_LEN>{} : top[0].t;
+    for (const Seen& e : top) {
+      for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = e.t[i];
+      float a = 0, b = 0;
+      ZK_TRY(measure(m, &a));
+      ZK_TRY(measure(m, &b));
+      const float mean = (e.ms + a + b) / 3;
+      if (mean < best_mean) {
+        best_mean = mean;
+        pick = e.t;
+      }
+    }
+    if (!top.empty()) {
+      for (int i = 0; i < ZKVC_PK_TUNING_LEN; i++) pk->prove_tune[i] = pick[i];
+      *best_ms = best_mean;
     }
     return ZKVC_OK;
   };
