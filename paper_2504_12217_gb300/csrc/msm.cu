@@ -290,8 +290,10 @@ __device__ __forceinline__ uint32_t bits_at(const uint32_t (&m)[8], uint32_t pos
   return (uint32_t)(x >> sh) & ((1u << c) - 1u);
 }
 
+// counts (non-null): also counts each key (global atomics), for runs whose terms spread
+// over many buckets, where k_hist's shared-memory window would not help anyway.
 __global__ void k_digits(const MsmSeg* __restrict__ segs, int nsegs, const MsmOut* __restrict__ outs,
-                         uint32_t total_points, uint32_t* keys, uint32_t* vals) {
+                         uint32_t total_points, uint32_t* keys, uint32_t* vals, uint32_t* counts) {
   uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total_points) return;
   int lo = 0, hi = nsegs - 1;
@@ -371,6 +373,7 @@ __global__ void k_digits(const MsmSeg* __restrict__ segs, int nsegs, const MsmOu
     uint64_t base = sg.base_off + uint64_t(i) * sg.nwin + (o.win_keys > 1 ? 0u : w);
     keys[slot] = key;
     vals[slot] = (uint32_t)base | (sign << 31);
+    if (counts) atomicAdd(counts + key, 1u);
   }
 }
 
@@ -1206,15 +1209,20 @@ int msm_launch(const MsmExec* ex, const Affine<F>* bases, XYZZ<F>* results, cuda
   ZK_CHECK(T0 >= 1, ZKVC_EINVAL, "msm: plan not finalized");
   ZK_CHECK(p.key_shift >= 0 || bases, ZKVC_EINVAL, "msm: no base array");
 
-  // digits -> terms
+  // digits -> terms, and the bucket counts of the counting sort: counted by the digits
+  // kernel itself where every output has at least 2^11 buckets per window (random digits
+  // then rarely repeat a key within a tile), else by k_hist
+  bool spread = true;
+  for (const auto& o : p.outs) spread = spread && o.c >= 12;
+  ZK_CUDA(cudaMemsetAsync(L.counts, 0, size_t(K) * sizeof(uint32_t), st));
   if (p.points > 0) {
-    k_digits<<<(p.points + 255) / 256, 256, 0, st>>>(L.segs, (int)p.segs.size(), L.outs, p.points, L.keys, L.vals); ZK_COUNT_LAUNCH();
+    k_digits<<<(p.points + 255) / 256, 256, 0, st>>>(L.segs, (int)p.segs.size(), L.outs, p.points, L.keys, L.vals,
+                                                     spread ? L.counts : nullptr);
+    ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
-  // counting sort by bucket key
-  ZK_CUDA(cudaMemsetAsync(L.counts, 0, size_t(K) * sizeof(uint32_t), st));
   unsigned sb = (unsigned)((S + HB_TILE - 1) / HB_TILE);
-  if (S > 0) {
+  if (S > 0 && !spread) {
     k_hist<<<sb, HB_THREADS, 0, st>>>(L.keys, S, L.counts); ZK_COUNT_LAUNCH();
     ZK_CUDA(cudaGetLastError());
   }
