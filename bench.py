@@ -700,9 +700,10 @@ def run_gpu(args):
 
 # DRAM bytes (read + write) of one H-query accumulation launch of the [49,320]x[320,512]
 # proof, from one ncu capture of the balanced accumulation (product-scanning products)
-# with the default chunk rule
-# (dram__bytes_read.sum + dram__bytes_write.sum); other chunk settings: not captured
-H_ACCUM_TRAFFIC = {0: 76589568}
+# with the default chunk rule, which gives this run 16 terms per chunk, so an imposed
+# chunk of 16 is the same launch (dram__bytes_read.sum + dram__bytes_write.sum); other
+# chunk settings: not captured
+H_ACCUM_TRAFFIC = {0: 76589568, 16: 76589568}
 
 
 # ------------------------------------------------------------------ batched workload
