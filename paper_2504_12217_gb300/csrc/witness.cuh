@@ -54,12 +54,38 @@ __device__ __forceinline__ void crpc_y_row(const int32_t* __restrict__ Y, const 
 // Block body (1024 threads, sh of 1024 entries): c_k = a_k b_k, the prefix sums
 // S_k = c_0 + ... + c_k for k <= n - 2, the closing check against Y(z) (flag bit 1), and
 // the first n domain evaluations A_ev = a, B_ev = b, C_ev = c.
+// Fr value of lane src (shuffle of the eight words); every lane of the warp calls it
+__device__ __forceinline__ Fr fr_shfl_up(const Fr& x, int d) {
+  Fr r;
+#pragma unroll
+  for (int i = 0; i < 8; i++) r.v[i] = __shfl_up_sync(0xffffffffu, x.v[i], d);
+  return r;
+}
+__device__ __forceinline__ Fr fr_shfl_down(const Fr& x, int d) {
+  Fr r;
+#pragma unroll
+  for (int i = 0; i < 8; i++) r.v[i] = __shfl_down_sync(0xffffffffu, x.v[i], d);
+  return r;
+}
+
+// Inclusive scan of Fr sums over a warp (five shuffle rounds); every lane calls it.
+__device__ __forceinline__ Fr warp_scan_fr(Fr v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const Fr u = fr_shfl_up(v, d);
+    if (lane >= d) v = f_add(v, u);
+  }
+  return v;
+}
+
 __device__ __forceinline__ void psq_chain(const Fr* __restrict__ ak, const Fr* __restrict__ bk,
                                           const Fr* __restrict__ ypart, int a, int n, Fr* S, Fr* Aev, Fr* Bev, Fr* Cev,
                                           int* flags, Fr* sh) {
   const int T = blockDim.x;
   const int per = (n + T - 1) / T;
   const int k0 = threadIdx.x * per;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   Fr local = Fr::zero();
   for (int k = k0; k < k0 + per && k < n; k++) {
     Fr a_ = ld_field(ak + k), b_ = ld_field(bk + k);
@@ -69,26 +95,33 @@ __device__ __forceinline__ void psq_chain(const Fr* __restrict__ ak, const Fr* _
     st_field(Cev + k, c);
     local = f_add(local, c);
   }
-  // inclusive scan of the per-thread sums (Hillis-Steele)
-  st_field(sh + threadIdx.x, local);
+  // inclusive scan of the per-thread sums: within each warp by shuffles, then over the
+  // warps' totals by warp 0
+  const Fr incl = warp_scan_fr(local);
+  if (lane == 31) st_field(sh + wid, incl);
   __syncthreads();
-  for (int d = 1; d < T; d <<= 1) {
-    Fr v = ld_field(sh + threadIdx.x);
-    if ((int)threadIdx.x >= d) v = f_add(v, ld_field(sh + threadIdx.x - d));
-    __syncthreads();
-    st_field(sh + threadIdx.x, v);
-    __syncthreads();
+  if (wid == 0) {
+    Fr t = lane < T / 32 ? ld_field(sh + lane) : Fr::zero();
+    t = warp_scan_fr(t);
+    st_field(sh + 32 + lane, t);  // inclusive totals of warps 0 .. lane
   }
-  Fr run = threadIdx.x ? ld_field(sh + threadIdx.x - 1) : Fr::zero();
+  __syncthreads();
+  Fr run = f_sub(incl, local);  // this thread's exclusive prefix within its warp
+  if (wid) run = f_add(run, ld_field(sh + 32 + wid - 1));
   for (int k = k0; k < k0 + per && k < n; k++) {
-    run = f_add(run, f_mul(ld_field(ak + k), ld_field(bk + k)));
+    run = f_add(run, ld_field(Cev + k));  // c_k as this thread stored it above
     if (k < n - 1) st_field(S + k, run);
   }
-  if (threadIdx.x == 0) {
-    Fr total = ld_field(sh + T - 1);  // S_(n-2) + c_(n-1)
+  // closing check against Y(z) = sum_i ypart_i (warp 1: strided sums, then a shuffle tree)
+  if (wid == (T > 32 ? 1 : 0)) {
     Fr yz = Fr::zero();
-    for (int i = 0; i < a; i++) yz = f_add(yz, ld_field(ypart + i));
-    if (total != yz) atomicOr(flags, 1);
+    for (int i = lane; i < a; i += 32) yz = f_add(yz, ld_field(ypart + i));
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) yz = f_add(yz, fr_shfl_down(yz, d));
+    if (lane == 0) {
+      const Fr total = ld_field(sh + 32 + (T / 32) - 1);  // S_(n-2) + c_(n-1)
+      if (total != yz) atomicOr(flags, 1);
+    }
   }
 }
 
