@@ -352,6 +352,7 @@ struct SideStreams {
   cudaStream_t st[NSIDE] = {};
   cudaEvent_t fork[NSIDE] = {}, join[NSIDE] = {};
   cudaEvent_t ntt_done = nullptr, h_accum = nullptr;  // points where the rest MSM may start
+  cudaEvent_t wit_y = nullptr, wit_psq = nullptr;     // Y = X W done; PSQ chain done
 };
 static thread_local SideStreams t_side;
 
@@ -373,6 +374,8 @@ static int side_streams(SideStreams** out) {
     }
     ZK_CUDA(cudaEventCreateWithFlags(&t_side.ntt_done, cudaEventDisableTiming));
     ZK_CUDA(cudaEventCreateWithFlags(&t_side.h_accum, cudaEventDisableTiming));
+    ZK_CUDA(cudaEventCreateWithFlags(&t_side.wit_y, cudaEventDisableTiming));
+    ZK_CUDA(cudaEventCreateWithFlags(&t_side.wit_psq, cudaEventDisableTiming));
   }
   *out = &t_side;
   return ZKVC_OK;
@@ -432,16 +435,23 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
   ZK_TRY(side_streams(&side));
   Plans P;
   plans(pk, mode, dX, dY, B.ak, B.bk, B.S, Hev, B.rs, B.sw, B.sa, B.rb, &P);
-  // 1. Y = X W (tensor cores), unless a claimed Y is given;  2. the CRPC sums a_k, b_k
-  if (!y_given) ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
-  k_crpc_ab<<<sh.n, 256, 0, st>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
+  // The witness runs on two streams: the CRPC sums a_k, b_k (X, W only) and the domain
+  // evaluations past row n (X, Y) on side stream 3, which then carries the critical
+  // NTT -> H chain; Y = X W, Y(z) and the PSQ chain on the main stream.  The side streams
+  // may start at the points recorded below; their work is enqueued after the critical
+  // chain's, so that the host reaches that chain's launches as early as possible.
+  ZK_TRY(fork_to(side, 3, st));
+  cudaStream_t s3 = side->st[3];
+  // 1. the CRPC sums a_k, b_k (side stream 3);  2. Y = X W (tensor cores), unless a
+  // claimed Y is given
+  k_crpc_ab<<<sh.n, 256, 0, s3>>>(dX, dW, pk->zA, pk->zB, sh.a, sh.n, sh.b, B.ak, B.bk); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  // The side streams may start at these points of the main stream (the events are
-  // recorded now); their work is enqueued after the critical NTT -> H chain's, so that
-  // the host reaches that chain's launches as early as possible.
-  ZK_CUDA(cudaEventRecord(side->fork[0], st));  // G2 MSM: needs b_k and s
+  ZK_CUDA(cudaEventRecord(side->fork[0], s3));  // G2 MSM: needs b_k and s
+  if (!y_given) ZK_TRY(matmul_i8(dX, dW, dY, sh.a, sh.n, sh.b, B.flags, st));
+  ZK_CUDA(cudaEventRecord(side->wit_y, st));
   // 3. Y(z) and the PSQ prefix sums; in fold mode the scalars s w_v, s a_k, r b_k
   k_crpc_y<<<sh.a, 256, 0, st>>>(dY, pk->zA, pk->zB, sh.b, B.yz); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaStreamWaitEvent(st, side->fork[0], 0));  // a_k, b_k
   k_psq<<<1, 1024, 0, st>>>(B.ak, B.bk, B.yz, sh.a, sh.n, B.S, Aev, Bev, Cev, B.flags); ZK_COUNT_LAUNCH();
   if (!chain) {
     uint32_t nsc = sh.l + 1 + 2 * uint32_t(sh.n);
@@ -450,15 +460,17 @@ static int prove_enqueue_impl(const zkvc_pk* pk, int mode, const int8_t* dX, con
   }
   ZK_CUDA(cudaGetLastError());
   ZK_CUDA(cudaEventRecord(side->fork[1], st));  // small-digit G1 MSM
-  // 4. remaining domain evaluations
-  size_t rest = N - sh.n;
-  k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, st>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev); ZK_COUNT_LAUNCH();
-  ZK_CUDA(cudaGetLastError());
-  prof_mark(PS_WITNESS, false, st);
   ZK_CUDA(cudaEventRecord(side->fork[2], st));  // rest MSM
-  // 5-6. quotient and the H part of C on side stream 3 (the critical chain)
-  ZK_TRY(fork_to(side, 3, st));
-  cudaStream_t s3 = side->st[3];
+  prof_mark(PS_WITNESS, false, st);
+  ZK_CUDA(cudaEventRecord(side->wit_psq, st));
+  // 4. remaining domain evaluations (side stream 3, once Y exists)
+  size_t rest = N - sh.n;
+  ZK_CUDA(cudaStreamWaitEvent(s3, side->wit_y, 0));
+  k_domain_rest<<<(unsigned)((rest + 255) / 256), 256, 0, s3>>>(dX, dY, sh.n, sh.a * sh.n, sh.l, N, Aev, Bev, Cev); ZK_COUNT_LAUNCH();
+  ZK_CUDA(cudaGetLastError());
+  // 5-6. quotient and the H part of C on side stream 3 (the critical chain), after the
+  // PSQ chain's first n evaluations
+  ZK_CUDA(cudaStreamWaitEvent(s3, side->wit_psq, 0));
   nv_stage.reset();
   nv_stage.emplace("zkvc/prove/ntt");
   prof_mark(PS_NTT, true, s3);
