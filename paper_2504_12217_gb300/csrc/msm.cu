@@ -880,9 +880,10 @@ struct OutItem {
 //   window the last bit of a window sums the window's c terms 2^b U_b;
 //   output the last window of an output applies Horner's rule over the output's windows
 //          (variable base; G1 on a sliced warp, G2 on a quad) or copies its one window.
-// Each hand-over: the finishing block's stores, a fence, then a fetch-and-add on the
-// level's counter (zeroed before the launch); the block that brings the count to the
-// total goes on, after a fence, reading the others' results around L1.  No block waits.
+// Each hand-over: the finishing block's stores, a fence by every storing thread, a
+// barrier, then a fetch-and-add on the level's counter (zeroed before the launch) by one
+// thread; the block that brings the count to the total goes on, after a fence, reading
+// the others' results around L1.  No block waits.
 template <class F>
 __global__ void __launch_bounds__(SliceBT<F>::value) k_bits_chain(
     const XYZZ<F>* __restrict__ fin, const uint32_t* __restrict__ counts, const uint32_t* __restrict__ choff,
@@ -930,7 +931,7 @@ __global__ void __launch_bounds__(SliceBT<F>::value) k_bits_chain(
       if (threadIdx.x < 32) {
         SlG1 y = sl_ld(&xs);
         for (uint32_t i = 0; i < shift; i++) y = sl_pdbl(y);
-        sl_st(D + g.dslot, y);
+        sl_st(D + g.dslot, y);  // eight lanes store a word of each coordinate
       }
     } else {
       if (threadIdx.x < 4) {
@@ -938,6 +939,7 @@ __global__ void __launch_bounds__(SliceBT<F>::value) k_bits_chain(
         if (threadIdx.x == 0) st_field(D + g.dslot, x);
       }
     }
+    __threadfence();  // by every storing lane, before the barrier and the count below
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -961,7 +963,7 @@ __global__ void __launch_bounds__(SliceBT<F>::value) k_bits_chain(
     if (!last) return;
     __threadfence();
   }
-  // output (at most SliceBT windows: checked by the planner)
+  // output (at most 64 windows, which the shared array holds: checked by the planner)
   const OutItem it = oitems[w.out];
   for (uint32_t i = threadIdx.x; i < it.nwin; i += BT) st_field(sh + i, ld_point_cg(D + it.first + i * it.stride));
   __syncthreads();
