@@ -417,11 +417,12 @@ def msm_work(group, logn):
     return ((1 << pts_log) * win * madd + (1 << c) * win * add) * MONT_IMAD, c
 
 
-def msm_sweep_section(nv, imad_peak):
+def msm_sweep_section(nv, imad_peak, local=0):
     """Variable-base MSMs of the kernel sweep inside the default line: G1 at 2^20 and 2^24
     points, G2 at 2^20, uniform Fr scalars, points = generator x uniform scalars (made by
     the library's fixed-base kernel, untimed).  Fractions of the integer peak with the
-    method's work (msm_work)."""
+    method's work (msm_work).  Each call is timed on its own (CUDA events); `ms` is the
+    median call, with every call's time and the SM clocks sampled meanwhile beside it."""
     import torch
     g = torch.Generator(device="cuda").manual_seed(0x5A4B5643_00000003)
 
@@ -441,17 +442,22 @@ def msm_sweep_section(nv, imad_peak):
         fn = (lambda: nv.zkvc_msm_g1(pts, sc, ws)) if group == 1 else (lambda: nv.zkvc_msm_g2(pts, sc, ws))
         fn()
         torch.cuda.synchronize()
-        reps = 3 if logn < 24 else 2
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+        reps = 3
+        clocks = ClockSampler(local)
+        clocks.start()
+        calls = []
         for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
             fn()
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+            e1.record()
+            torch.cuda.synchronize()
+            calls.append(e0.elapsed_time(e1))
+        clk = clocks.stop()
+        ms = statistics.median(calls)
         work, c = msm_work(group, logn)
-        out.append({"group": f"G{group}", "log_n": logn, "ms": ms, "mpoints_per_s": n / ms / 1e3,
-                    "imad_frac": work / (ms / 1e3) / imad_peak, "window_bits": c})
+        out.append({"group": f"G{group}", "log_n": logn, "ms": ms, "calls_ms": calls, "mpoints_per_s": n / ms / 1e3,
+                    "imad_frac": work / (ms / 1e3) / imad_peak, "window_bits": c, "clocks": clk})
         del pts, sc, ws
         torch.cuda.empty_cache()
     return {"msms": out, "note": "each call synchronises and reads its result back (zkvc_msm_g1/g2); "
@@ -664,7 +670,7 @@ def run_gpu(args):
     stages = {k: round(v["ms"] / max(v["calls"], 1), 4) for k, v in prof.items()}
     spans = {k: [round(v["start_ms"], 4), round(v["end_ms"], 4)] for k, v in prof.items() if v["calls"]}
     nttr = ntt_roofline(nv, prof, 16, imad["imad_per_s"], hbm, hbm_src)
-    msweep = msm_sweep_section(nv, imad["imad_per_s"]) if not args.no_msm_sweep else None
+    msweep = msm_sweep_section(nv, imad["imad_per_s"], local) if not args.no_msm_sweep else None
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
