@@ -41,3 +41,23 @@ def test_argument_errors_need_no_gpu():
     assert bytes(out) == bytes(64)
     assert lib.zkvc_msm_workspace_bytes(1000, 1) > 1000 * 64
     assert lib.zkvc_msm_workspace_bytes(1000, 2) > lib.zkvc_msm_workspace_bytes(1000, 1)
+
+
+def test_msm_plans_fit_on_the_host():
+    """The variable-base MSM's planner runs on the host alone (zkvc_msm_workspace_bytes):
+    from 1 to 2^24 points the workspace holds at least the 2n endomorphism-split bases
+    (64 bytes each in G1, 128 in G2) and their 16-byte half scalars, grows with n, and at
+    the allocation-free entry's largest n fits its fixed 8 MiB scratch (the host has no
+    occupancy data, so its chunks are the planner's smallest and this bound is the loose
+    one)."""
+    nv = _util.native()
+    lib = nv.lib()
+    prev = {1: 0, 2: 0}
+    for lg in range(0, 25, 2):
+        n = 1 << lg
+        for group, pt in ((1, 64), (2, 128)):
+            b = lib.zkvc_msm_workspace_bytes(n, group)
+            assert b >= 2 * n * (pt + 16), (n, group, b)
+            assert b >= prev[group], (n, group, b, prev[group])
+            prev[group] = b
+    assert lib.zkvc_msm_workspace_bytes(nv.ZKVC_MSM_NOALLOC_MAX_POINTS, 1) <= 8 << 20
