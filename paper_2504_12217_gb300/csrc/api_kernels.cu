@@ -217,8 +217,6 @@ static MsmPlan variable_base_plan(size_t n, const void* scalars, bool glv) {
   return p;
 }
 
-static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
-
 template <class F>
 size_t msm_api_ws(size_t n) {
   constexpr bool glv = msm_api_glv<F>();

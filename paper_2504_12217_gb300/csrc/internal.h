@@ -88,6 +88,9 @@ bool prof_enabled();
   } while (0)
 
 // Bump allocator over a caller-provided device workspace (256-byte aligned slices).
+// bytes rounded up to a multiple of 256 (the alignment of every device buffer carved here)
+inline size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
 struct Arena {
   uint8_t* base = nullptr;
   size_t cap = 0;

@@ -145,8 +145,6 @@ struct zkvc_server {
 
 namespace zkvc {
 
-static size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
-
 static size_t footprint(const zkvc_pk* pk, int mode) {
   const Shape& sh = pk->shape;
   return prove_workspace_bytes(pk, mode) + round256(size_t(sh.a) * sh.n) + round256(size_t(sh.n) * sh.b) +
