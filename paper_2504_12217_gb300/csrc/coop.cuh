@@ -141,39 +141,4 @@ __device__ __forceinline__ G2J p_dbl_quad(const G2J& p) { return p_dbl_quad_g2(p
 __device__ __forceinline__ G1J p_add_quad(const G1J& p, const G1J& q) { return p_add_quad_g1(p, q); }
 __device__ __forceinline__ G2J p_add_quad(const G2J& p, const G2J& q) { return p_add_quad_g2(p, q); }
 
-// k P for one half of a GLV-split scalar (|k| < 2^128 with its sign; glv.h), on a quad:
-// the 15 multiples of +-P in shared memory T[1..15] (this quad's own table), then 4-bit
-// windows from the top: four doublings and at most one addition per window, about 124
-// doublings and 32 additions in all.
-template <class Half>
-__device__ __forceinline__ G1J p_mul_half_quad(const G1J& P, const Half& h, G1J* T) {
-  const bool lead = quad_lane() == 0;
-  G1J Q = P;
-  if (h.neg) Q.Y = f_neg(Q.Y);
-  G1J prev = Q;
-  if (lead) st_field(T + 1, Q);
-  for (int i = 2; i < 16; i++) {
-    prev = p_add_quad(prev, Q);
-    if (lead) st_field(T + i, prev);
-  }
-  __syncwarp(quad_mask());
-  G1J acc = G1J::inf();
-  bool started = false;
-  for (int w = 31; w >= 0; w--) {
-    if (started) {
-      acc = p_dbl_quad(acc);
-      acc = p_dbl_quad(acc);
-      acc = p_dbl_quad(acc);
-      acc = p_dbl_quad(acc);
-    }
-    const uint32_t nib = (h.mag[w >> 3] >> ((w & 7) * 4)) & 15u;
-    if (nib) {
-      const G1J t = ld_field(T + nib);
-      acc = started ? p_add_quad(acc, t) : t;
-      started = true;
-    }
-  }
-  return acc;
-}
-
 }  // namespace zkvc

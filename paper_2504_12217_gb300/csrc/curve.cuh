@@ -157,20 +157,6 @@ __device__ __forceinline__ Affine<F> p_to_affine(const XYZZ<F>& p) {
   return {f_mul(p.X, izz), f_mul(p.Y, izzz)};
 }
 
-// Variable-base scalar multiplication by a canonical 8-limb scalar (MSB-first
-// double-and-add).  Used only off the bulk path (a handful of points per proof).
-template <class F>
-__device__ __noinline__ XYZZ<F> p_mul_scalar(const XYZZ<F>& p, const uint32_t (&k)[8]) {
-  XYZZ<F> acc = XYZZ<F>::inf();
-  for (int i = 7; i >= 0; i--) {
-    for (int bit = 31; bit >= 0; bit--) {
-      acc = p_dbl(acc);
-      if ((k[i] >> bit) & 1u) acc = p_add(acc, p);
-    }
-  }
-  return acc;
-}
-
 // Variable-base scalar multiplication with fixed 4-bit windows: a table of the 15
 // multiples, then per window four doublings and at most one addition (254 doublings and
 // <= 64 additions for a 254-bit scalar instead of double-and-add's ~127 additions).

@@ -62,17 +62,6 @@ constexpr uint32_t cx_neg_inv32(uint32_t m0) {
   return 0u - x;
 }
 
-constexpr U256c cx_sub1(U256c m) {  // m - 2, used for Fermat exponents
-  U256c r = m;
-  uint64_t br = 2;
-  for (int i = 0; i < 8; i++) {
-    uint64_t v = (uint64_t)r.w[i] - br;
-    r.w[i] = (uint32_t)v;
-    br = (v >> 63) & 1;
-  }
-  return r;
-}
-
 // ------------------------------------------------------------------ field parameters
 // p and r of BN254 (alt_bn128), little-endian 32-bit limbs.
 struct FpCfg {
@@ -81,7 +70,6 @@ struct FpCfg {
   static constexpr U256c R1 = cx_pow2_mod(256, MOD);
   static constexpr U256c R2 = cx_pow2_mod(512, MOD);
   static constexpr U256c R3 = cx_pow2_mod(768, MOD);
-  static constexpr U256c MOD_M2 = cx_sub1(MOD);
   static constexpr uint32_t INV = cx_neg_inv32(MOD.w[0]);
 };
 
@@ -91,7 +79,6 @@ struct FrCfg {
   static constexpr U256c R1 = cx_pow2_mod(256, MOD);
   static constexpr U256c R2 = cx_pow2_mod(512, MOD);
   static constexpr U256c R3 = cx_pow2_mod(768, MOD);
-  static constexpr U256c MOD_M2 = cx_sub1(MOD);
   static constexpr uint32_t INV = cx_neg_inv32(MOD.w[0]);
 };
 
@@ -113,8 +100,6 @@ template <class C>
 __host__ __device__ __forceinline__ constexpr uint32_t r1_limb(int i) { ZKVC_LIMB_SWITCH(C::R1, i) }
 template <class C>
 __host__ __device__ __forceinline__ constexpr uint32_t r2_limb(int i) { ZKVC_LIMB_SWITCH(C::R2, i) }
-template <class C>
-__host__ __device__ __forceinline__ constexpr uint32_t modm2_limb(int i) { ZKVC_LIMB_SWITCH(C::MOD_M2, i) }
 template <class C>
 __host__ __device__ __forceinline__ constexpr uint32_t r3_limb(int i) { ZKVC_LIMB_SWITCH(C::R3, i) }
 
