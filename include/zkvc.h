@@ -156,8 +156,10 @@ int zkvc_ntt(uint8_t* d_data, uint32_t log_n, int kind, void* stream);
  * c-bit windows, bucket sort and parallel reduction) -- the kernel behind the A, B, L
  * and H queries of Groth16 Prove (Sec. II).
  *   d_points   n affine points (64 bytes each for G1, 128 for G2), canonical, on the curve
- *              (not checked); infinity allowed
- *   d_scalars  n canonical Fr scalars (32 bytes each)
+ *              (not checked); infinity allowed, as all-zero bytes
+ *   d_scalars  n scalars, 32-byte little-endian integers; values at or above r are
+ *              reduced mod r (an endomorphism split follows in both groups: GLV with
+ *              phi(x, y) = (beta x, y) on G1, psi on G2, halves below 2^127)
  *   d_ws       device workspace of zkvc_msm_workspace_bytes(n, group) bytes
  *   out        host buffer of 64 (G1) or 128 (G2) bytes; the call synchronises `stream`
  * group = 1 for G1, 2 for G2.  n may be 0 (out = infinity).
