@@ -162,8 +162,12 @@ int zkvc_ntt(uint8_t* d_data, uint32_t log_n, int kind, void* stream);
  *              phi(x, y) = (beta x, y) on G1, psi on G2, halves below 2^127)
  *   d_ws       device workspace of zkvc_msm_workspace_bytes(n, group) bytes
  *   out        host buffer of 64 (G1) or 128 (G2) bytes; the call synchronises `stream`
- * group = 1 for G1, 2 for G2.  n may be 0 (out = infinity).
+ * group = 1 for G1, 2 for G2.  n may be 0 (out = infinity); n above ZKVC_MSM_MAX_POINTS
+ * returns ZKVC_EINVAL (there the 2n split scalars take eight 16-bit windows each: 16 n
+ * digits, whose 32-bit term indices must stay at or below 2^31), and
+ * zkvc_msm_workspace_bytes returns 0 for it.
  */
+#define ZKVC_MSM_MAX_POINTS (1u << 27)
 size_t zkvc_msm_workspace_bytes(size_t n, int group);
 int zkvc_msm_g1(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d_ws, size_t ws_bytes,
                 uint8_t out[64], void* stream);

@@ -192,8 +192,8 @@ static uint32_t window_bits(size_t n) {
 template <class F>
 constexpr bool msm_api_glv() { return true; }
 
-static MsmPlan variable_base_plan(size_t n, const void* scalars, bool glv) {
-  MsmPlan p;
+static int variable_base_plan(size_t n, const void* scalars, bool glv, MsmPlan* out) {
+  MsmPlan& p = *out;
   const size_t pts = glv ? 2 * n : n;
   const uint32_t bits = glv ? 128 : 255;
   // the window rule's c, then the smallest c with the same window count, so that the top
@@ -213,15 +213,15 @@ static MsmPlan variable_base_plan(size_t n, const void* scalars, bool glv) {
   s.scalars = scalars;
   s.skip = 0xffffffffu;
   p.segs.push_back(s);
-  msm_plan_finalize(p);
-  return p;
+  return msm_plan_finalize(p);
 }
 
 template <class F>
 size_t msm_api_ws(size_t n) {
   constexpr bool glv = msm_api_glv<F>();
   const size_t pts = glv ? 2 * n : n;
-  MsmPlan p = variable_base_plan(n, nullptr, glv);
+  MsmPlan p;
+  if (n > ZKVC_MSM_MAX_POINTS || variable_base_plan(n, nullptr, glv, &p) != ZKVC_OK) return 0;
   return msm_workspace_bytes<F>(p) + round256(pts * sizeof(Affine<F>)) + (glv ? round256(pts * sizeof(uint4)) : 0) +
          2 * 256 + sizeof(XYZZ<F>) + sizeof(Affine<F>);
 }
@@ -301,12 +301,14 @@ int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d
             uint8_t* out, cudaStream_t st) {
   constexpr bool glv = msm_api_glv<F>();
   ZK_CHECK(out != nullptr, ZKVC_EINVAL, "msm: null output");
-  ZK_CHECK(n < (1ull << 30), ZKVC_EINVAL, "msm: n = %zu too large", n);
+  ZK_CHECK(n <= ZKVC_MSM_MAX_POINTS, ZKVC_EINVAL, "msm: n = %zu above %u", n, (unsigned)ZKVC_MSM_MAX_POINTS);
   if (n == 0) {
     memset(out, 0, sizeof(Affine<F>));
     return ZKVC_OK;
   }
   ZK_CHECK(d_points && d_scalars && d_ws, ZKVC_EINVAL, "msm: null device pointer");
+  MsmPlan p;
+  ZK_TRY(variable_base_plan(n, nullptr, glv, &p));
   size_t need = msm_api_ws<F>(n);
   ZK_CHECK(ws_bytes >= need, ZKVC_EINVAL, "msm: workspace %zu < %zu bytes", ws_bytes, need);
   Arena a;
@@ -331,7 +333,7 @@ int msm_api(const uint8_t* d_points, const uint8_t* d_scalars, size_t n, void* d
   }
   ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());
-  MsmPlan p = variable_base_plan(n, glv ? static_cast<const void*>(halves) : d_scalars, glv);
+  p.segs[0].scalars = glv ? static_cast<const void*>(halves) : d_scalars;
   ZK_TRY(msm_run<F>(p, bases, rest, rest_bytes, res, st));
   k_export_point<F><<<1, 32, 0, st>>>(res, aff); ZK_COUNT_LAUNCH();
   ZK_CUDA(cudaGetLastError());

@@ -233,7 +233,9 @@ int msm_plan_finalize(MsmPlan& p) {
     pts += s.count;
     p.max_nd = std::max(p.max_nd, nd);
   }
-  ZK_CHECK(slot < 0xffffffffull, ZKVC_EINVAL, "msm: too many digit slots");
+  // term indices, bucket offsets and chunk bounds are 32-bit: 2^31 slots leave every sum
+  // of an index and a chunk length below 2^32
+  ZK_CHECK(slot <= (1ull << 31), ZKVC_EINVAL, "msm: %llu digit slots (at most 2^31)", (unsigned long long)slot);
   // default chunk: about two chunks per bucket, but at least ~40 k chunks so that the
   // accumulation fills the GPU, and 16 at the least; and at least the chunk that puts
   // every term into one wave of resident accumulation threads (the chunks are balanced,

@@ -291,6 +291,9 @@ def zkvc_ntt(data, kind):
     return data
 
 
+ZKVC_MSM_MAX_POINTS = 1 << 27
+
+
 def zkvc_msm_workspace_bytes(n, group):
     return lib().zkvc_msm_workspace_bytes(n, group)
 

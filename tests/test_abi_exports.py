@@ -61,3 +61,21 @@ def test_msm_plans_fit_on_the_host():
             assert b >= prev[group], (n, group, b, prev[group])
             prev[group] = b
     assert lib.zkvc_msm_workspace_bytes(nv.ZKVC_MSM_NOALLOC_MAX_POINTS, 1) <= 8 << 20
+
+
+def test_msm_size_limit():
+    """Up to ZKVC_MSM_MAX_POINTS (2^27) the planner sizes a workspace; one point more is
+    rejected before any device work: the workspace query answers 0 and the call
+    ZKVC_EINVAL (the 16 n window digits of the split scalars would pass 2^31)."""
+    nv = _util.native()
+    lib = nv.lib()
+    m = nv.ZKVC_MSM_MAX_POINTS
+    assert m == 1 << 27
+    for group, pt in ((1, 64), (2, 128)):
+        assert lib.zkvc_msm_workspace_bytes(m, group) >= 2 * m * (pt + 16 + 8)
+        assert lib.zkvc_msm_workspace_bytes(m + 1, group) == 0
+    out = (ctypes.c_uint8 * 128)()
+    for fn in (lib.zkvc_msm_g1, lib.zkvc_msm_g2):
+        assert fn(ctypes.c_void_p(256), ctypes.c_void_p(256), m + 1, ctypes.c_void_p(256), 1 << 40, out,
+                  None) == nv.ZKVC_EINVAL
+        assert b"above" in lib.zkvc_last_error()

@@ -12,6 +12,13 @@
   [sum s_i k_i] G; NTTs of 2^24 points by round trips and sampled outputs evaluated one
   by one as polynomial values at powers of the root of unity.
 
+* The largest sizes the library accepts: G1 and G2 MSMs of ZKVC_MSM_MAX_POINTS (2^27)
+  points, tiled from 256 points of known discrete logs with uniform scalars, so that the
+  expected [sum_j k_j t_j] G needs only the scalars' sums t_j over each tile class
+  (exact byte-column sums on the device); and NTTs of 2^28 points (the domain's maximum):
+  round trips of both kinds and the outputs at k = 0 and N/2 (the coefficients' sum and
+  alternating sum).
+
 All comparisons are exact."""
 import os
 import random
@@ -152,5 +159,61 @@ def test_ntt_2_24(nv):
     nv.zkvc_ntt(t, 2)
     k = 12345
     assert int.from_bytes(t[k].cpu().numpy().tobytes(), "little") == _poly_at(a, 5 * pow(w, k, R) % R)
+    del t, x
+    torch.cuda.empty_cache()
+
+
+def _class_sums(s_u8, classes):
+    """[sum of s_i over i = j mod classes for j < classes] as integers: exact, from int64
+    sums of each byte column on the device."""
+    import torch
+    n = s_u8.shape[0]
+    cols = s_u8.view(n // classes, classes, 32).sum(dim=0, dtype=torch.int64).cpu().tolist()
+    return [sum(v << (8 * b) for b, v in enumerate(row)) for row in cols]
+
+
+@pytest.mark.parametrize("group", [1, 2])
+def test_msm_max_size(nv, group):
+    import torch
+    n, classes = nv.ZKVC_MSM_MAX_POINTS, 256
+    rng = random.Random(4242 + group)
+    if group == 1:
+        mul, enc, rows, call, gen_pt = bn.g1_mul, bn.g1_bytes, _util.g1_rows, nv.zkvc_msm_g1, bn.G1_GEN
+    else:
+        mul, enc, rows, call, gen_pt = bn.g2_mul, bn.g2_bytes, _util.g2_rows, nv.zkvc_msm_g2, bn.G2_GEN
+    logs = [rng.randrange(1, R) for _ in range(classes)]
+    tile = torch.from_numpy(rows([mul(gen_pt, k) for k in logs])).cuda()
+    pts = tile.repeat(n // classes, 1)  # point i = [logs[i mod classes]] G
+    del tile
+    g = torch.Generator(device="cuda").manual_seed(0x5A4B0000 + group)
+    s = torch.randint(0, 256, (n, 32), dtype=torch.uint8, device="cuda", generator=g)
+    s[:, 31] &= 0x0F
+    s[7] = 0
+    ws = torch.empty(nv.zkvc_msm_workspace_bytes(n, group), dtype=torch.uint8, device="cuda")
+    got = call(pts, s, ws)
+    del pts, ws
+    torch.cuda.empty_cache()
+    sums = _class_sums(s, classes)
+    assert got == enc(mul(gen_pt, sum(k * t for k, t in zip(logs, sums)) % R))
+    del s
+    torch.cuda.empty_cache()
+
+
+def test_ntt_max_size_2_28(nv):
+    import torch
+    n = 1 << 28
+    g = torch.Generator(device="cuda").manual_seed(28)
+    x = torch.randint(0, 256, (n, 32), dtype=torch.uint8, device="cuda", generator=g)
+    x[:, 31] &= 0x0F
+    even, odd = _class_sums(x, 2)
+    t = x.clone()
+    nv.zkvc_ntt(t, 0)
+    assert int.from_bytes(t[0].cpu().numpy().tobytes(), "little") == (even + odd) % R
+    assert int.from_bytes(t[n // 2].cpu().numpy().tobytes(), "little") == (even - odd) % R
+    nv.zkvc_ntt(t, 1)
+    assert torch.equal(t, x)
+    nv.zkvc_ntt(t, 2)
+    nv.zkvc_ntt(t, 3)
+    assert torch.equal(t, x)
     del t, x
     torch.cuda.empty_cache()
