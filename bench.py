@@ -456,8 +456,14 @@ def msm_sweep_section(nv, imad_peak, local=0):
         clk = clocks.stop()
         ms = statistics.median(calls)
         work, c = msm_work(group, logn)
-        out.append({"group": f"G{group}", "log_n": logn, "ms": ms, "calls_ms": calls, "mpoints_per_s": n / ms / 1e3,
-                    "imad_frac": work / (ms / 1e3) / imad_peak, "window_bits": c, "clocks": clk})
+        point = {"group": f"G{group}", "log_n": logn, "ms": ms, "calls_ms": calls, "mpoints_per_s": n / ms / 1e3,
+                 "imad_frac": work / (ms / 1e3) / imad_peak, "window_bits": c, "clocks": clk}
+        if (group, logn) in MSM_ACCUM_TRAFFIC:
+            terms = (2 * n) * -(-128 // c)
+            point["accum_traffic"] = {"dram_bytes": MSM_ACCUM_TRAFFIC[(group, logn)],
+                                      "algorithmic_bytes": terms * (64 * group + 4),
+                                      "source": "one ncu capture of the accumulation launch at this size"}
+        out.append(point)
         del pts, sc, ws
         torch.cuda.empty_cache()
     return {"msms": out, "note": "each call synchronises and reads its result back (zkvc_msm_g1/g2); "
@@ -710,6 +716,12 @@ def run_gpu(args):
 # chunk of 16 is the same launch (dram__bytes_read.sum + dram__bytes_write.sum); other
 # chunk settings: not captured
 H_ACCUM_TRAFFIC = {0: 76589568, 16: 76589568}
+
+# DRAM bytes (read + write) of the accumulation launch of the variable-base MSMs of the
+# sweep points, from one ncu capture per size (dram__bytes_read.sum +
+# dram__bytes_write.sum), beside the launch's algorithmic bytes: one 64-byte base and one
+# 4-byte sorted index per bucket term (2^(log_n + 1) split points x 8 windows)
+MSM_ACCUM_TRAFFIC = {(1, 20): 1104113000 + 41336576}
 
 
 # ------------------------------------------------------------------ batched workload
